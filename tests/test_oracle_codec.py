@@ -1,0 +1,157 @@
+"""Pins of the FP64 oracle's codec pieces: rounding against library conversions,
+the block layout against coordinate-encoded fields, GELU identities, the training
+gradient against finite differences, LAMB's trust-ratio invariant, and the linear
+autoencoder reaching the Eckart-Young (PCA) optimum (Sec. 1).  CPU only."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import codec as C
+
+
+def test_round_bf16_matches_torch_on_fp32_values():
+    rng = np.random.default_rng(0)
+    x = (rng.standard_normal(20000) * np.exp(rng.uniform(-20, 20, 20000))).astype(np.float32)
+    want = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(C.round_bf16(x.astype(np.float64)), want)
+
+
+def test_round_bf16_ties_to_even():
+    u = 2.0 ** -8   # half an ulp of bf16 at 1.0
+    assert C.round_bf16(1.0 + u) == 1.0
+    assert C.round_bf16(1.0 + 3 * u) == 1.0 + 4 * u
+    assert C.round_bf16(-(1.0 + u * 1.0000001)) == -(1.0 + 2 * u)
+
+
+def test_round_fp16_matches_numpy():
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal(20000) * np.exp(rng.uniform(-18, 11, 20000))
+    want = x.astype(np.float16).astype(np.float64)
+    np.testing.assert_array_equal(C.round_fp16(x), want)
+
+
+def test_block_layout_from_coordinate_encoded_fields():
+    nz, ny, nx = 16, 24, 8
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    fields = [f * 1e6 + k * 1e4 + j * 1e2 + i for f in range(4)]
+    X = C.pack_blocks(fields)
+    NBy, NBx = ny // 8, nx // 8
+    rng = np.random.default_rng(2)
+    for _ in range(200):
+        b = rng.integers(X.shape[0]); kk = rng.integers(2048)
+        v = X[b, kk]
+        f, rest = divmod(v, 1e6); kz, rest = divmod(rest, 1e4); jy, ix = divmod(rest, 1e2)
+        z, r = divmod(kk, 256); ff, r = divmod(r, 64); y, x = divmod(r, 8)
+        bz, r = divmod(b, NBy * NBx); by, bx = divmod(r, NBx)
+        assert (f, kz, jy, ix) == (ff, 8 * bz + z, 8 * by + y, 8 * bx + x)
+    for f in range(4):
+        np.testing.assert_array_equal(C.unpack_field(X, (nz, ny, nx), f), fields[f])
+
+
+def test_normalise_bounds_and_zero_scale():
+    st = [np.random.default_rng(f).standard_normal((8, 8, 16)) * 10 ** f for f in range(4)]
+    s = C.running_scales([st])[0]
+    Y = C.normalise(C.pack_blocks(st), s)
+    assert np.abs(Y).max() <= 1.0
+    assert np.isclose(np.abs(Y).max(), 1.0)
+    Y0 = C.normalise(C.pack_blocks(st), np.array([0.0, s[1], s[2], s[3]]))
+    assert np.all(Y0[:, C.field_columns(0)] == 0)
+
+
+def test_running_scale_is_monotone_prefix_max():
+    rng = np.random.default_rng(3)
+    states = [[rng.standard_normal((8, 8, 8)) * rng.uniform(0, 2) for _ in range(4)] for _ in range(6)]
+    s = C.running_scales(states)
+    assert np.all(np.diff(s, axis=0) >= 0)
+    for f in range(4):
+        assert s[-1, f] == max(np.abs(st[f]).max() for st in states)
+
+
+def test_gelu_identities():
+    x = np.linspace(-6, 6, 1001)
+    assert C.gelu(0.0) == 0.0
+    np.testing.assert_allclose(C.gelu(x) - C.gelu(-x), x, atol=1e-14)   # x Phi(x) + x Phi(-x) = x
+    assert C.gelu(10.0) == pytest.approx(10.0, abs=1e-15)
+    assert C.gelu_prime(0.0) == 0.5
+    fd = (C.gelu(x + 1e-6) - C.gelu(x - 1e-6)) / 2e-6
+    np.testing.assert_allclose(C.gelu_prime(x), fd, atol=1e-8)
+
+
+def _small_weights(rng, d=16, hdim=8, k=4):
+    return {"W1": rng.uniform(-.5, .5, (d, hdim)), "b1": rng.uniform(-.1, .1, hdim),
+            "W2": rng.uniform(-.5, .5, (hdim, k)), "b2": rng.uniform(-.1, .1, k),
+            "W3": rng.uniform(-.5, .5, (k, hdim)), "b3": rng.uniform(-.1, .1, hdim),
+            "W4": rng.uniform(-.5, .5, (hdim, d)), "b4": rng.uniform(-.1, .1, d)}
+
+
+def test_training_gradient_matches_finite_differences():
+    rng = np.random.default_rng(4)
+    Wt = _small_weights(rng)
+    Y = rng.uniform(-1, 1, (32, 16))
+    _, g = C.loss_and_grad(Wt, Y)
+    eps = 1e-6
+    for name in C.PARAMS:
+        flat = Wt[name].ravel()
+        for idx in rng.choice(flat.size, size=min(5, flat.size), replace=False):
+            Wp = {k: v.copy() for k, v in Wt.items()}; Wm = {k: v.copy() for k, v in Wt.items()}
+            Wp[name].ravel()[idx] += eps; Wm[name].ravel()[idx] -= eps
+            fd = (C.loss_and_grad(Wp, Y)[0] - C.loss_and_grad(Wm, Y)[0]) / (2 * eps)
+            assert fd == pytest.approx(g[name].ravel()[idx], rel=1e-6, abs=1e-10), (name, idx)
+
+
+def test_lamb_update_norm_is_lr_times_weight_norm():
+    """With zero weight decay the LAMB step of every tensor has norm lr |w|."""
+    rng = np.random.default_rng(5)
+    Wt = _small_weights(rng)
+    opt = C.Lamb(Wt)
+    for t in range(5):
+        g = {k: rng.standard_normal(v.shape) for k, v in Wt.items()}
+        new = opt.step(Wt, g, lr=1e-2)
+        for k in Wt:
+            step = np.linalg.norm(new[k] - Wt[k])
+            assert step == pytest.approx(1e-2 * np.linalg.norm(Wt[k]), rel=1e-12)
+        Wt = new
+    # first step: bias-corrected moments give u = g / (|g| + eps), i.e. ~ sign(g)
+    opt = C.Lamb(Wt)
+    g = {k: rng.standard_normal(v.shape) for k, v in Wt.items()}
+    new = opt.step(Wt, g, lr=1e-3)
+    d = -(new["W1"] - Wt["W1"])
+    assert np.all(np.sign(d) == np.sign(g["W1"]))
+
+
+def test_linear_autoencoder_reaches_pca_optimum():
+    """Sec. 1: a linear autoencoder learns the PCA subspace; trained with the oracle's
+    gradient and LAMB it must reach the Eckart-Young error of a rank-k truncated SVD of
+    the centred data, and can never go below it."""
+    rng = np.random.default_rng(0)
+    d, k, B = 32, 4, 256
+    U = np.linalg.qr(rng.standard_normal((d, d)))[0]
+    Y = (rng.standard_normal((B, d)) * np.exp(-np.arange(d) / 3.0)) @ U.T + 0.3
+    s = np.linalg.svd(Y - Y.mean(0), compute_uv=False)
+    opt_mse = np.sum(s[k:] ** 2) / (B * d)
+    Wt = {"W1": rng.uniform(-.3, .3, (d, 8)), "b1": np.zeros(8), "W2": rng.uniform(-.3, .3, (8, k)),
+          "b2": np.zeros(k), "W3": rng.uniform(-.3, .3, (k, 8)), "b3": np.zeros(8),
+          "W4": rng.uniform(-.3, .3, (8, d)), "b4": np.zeros(d)}
+    opt = C.Lamb(Wt)
+    for it in range(4000):
+        L, g = C.loss_and_grad(Wt, Y, act="linear")
+        Wt = opt.step(Wt, g, 2e-2 * 0.5 ** (it // 1500))
+    L, _ = C.loss_and_grad(Wt, Y, act="linear")
+    assert opt_mse * (1 - 1e-9) <= L <= 1.05 * opt_mse
+
+
+def test_emulated_codec_close_to_exact_and_rounded():
+    rng = np.random.default_rng(6)
+    from paper_2304_04781_gb300 import inputs
+    Wt = inputs.codec_init(seed=1)
+    Y = rng.uniform(-1, 1, (16, 2048))
+    z_exact = C.encode(Wt, Y)
+    z_emul = C.encode(Wt, Y, emulate=True)
+    assert np.all(C.round_fp16(z_emul) == z_emul)
+    rel = np.linalg.norm(z_emul - z_exact) / np.linalg.norm(z_exact)
+    assert 1e-5 < rel < 2e-2
+    out_e = C.decode(Wt, z_emul, emulate=True)
+    out_x = C.decode(Wt, z_emul)
+    assert np.linalg.norm(out_e - out_x) / np.linalg.norm(out_x) < 2e-2
+    cols = C.field_columns(0)
+    np.testing.assert_allclose(C.decode(Wt, z_emul, cols=cols), out_x[:, cols], rtol=1e-12, atol=1e-12)
