@@ -1,0 +1,234 @@
+/*
+ * aewave -- autoencoder-compressed adjoint gradients and Gauss-Newton Hessian-vector
+ * products for the 3-D acoustic velocity-strain wave equation, on one GB300 (sm_103a).
+ *
+ * The operations follow the statement of the inverse problem in Sec. 2 of
+ * "An Autoencoder Compression Approach for Accelerating Large-scale Inverse Problems"
+ * (arXiv 2304.04781):
+ *   forward  : c -> d = F(c) = B A(c)                 (parameter-to-observable map, Sec. 2)
+ *   gradient : c, d_obs -> J, dJ/dc, J = 1/2 |F(c) - d_obs|^2   (Eq. (3), misfit term)
+ *   hessvec  : dc -> J_F^T J_F dc                      (incremental forward + incremental
+ *                                                       adjoint, Sec. 4)
+ * with the forward history kept in one of three ways: full storage, binomial
+ * recompute-checkpointing, or per-block autoencoder latents (compression in space,
+ * Sec. 3.1; architecture and training of Sec. 3.3; data generation of Algorithm 1).
+ *
+ * Discretisation (the same in every mode): nodes [k][j][i] = (z, y, x), row-major with
+ * x fastest, spacing h, rho = 1, m = c^2.  e lives on nodes and is 0 on boundary
+ * nodes; vx lives on x-faces (i+1/2, j, k) stored at [k][j][i] (the last face,
+ * i = nx-1, is unused and 0); vy, vz likewise.  One step n -> n+1:
+ *     v^{n+1} = v^n + dt (G(m e^n) + s^n),   e^{n+1} = e^n + dt D v^{n+1},
+ *     d^{n+1} = B v^{n+1},
+ * G = forward differences, D = backward differences on interior nodes (D = -G^T),
+ * dt = cfl * h / cmax, s^n a force on the z-face of the source node.
+ *
+ * Conventions for every call:
+ *  - Array arguments named *_dev are DEVICE pointers owned by the caller (for example
+ *    a torch tensor's data_ptr()), contiguous, FP32 unless stated.  Grid fields are
+ *    [nz][ny][nx].  Receiver data are [nt+1][nrec][3] (row n = d^n, component x,y,z).
+ *    Arguments named *_host are host pointers.  The library never frees caller memory.
+ *  - The handle owns every internal buffer (states, stored history, latents,
+ *    checkpoints, workspace) and frees them in aew_destroy.
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL = the legacy default stream).
+ *    Calls that return a host scalar (misfit, dot) synchronise that stream.
+ *  - Return value: AEW_OK (0) or a negative AEW_E_* code; aew_last_error() then gives
+ *    a message.  A failed call leaves the handle usable.
+ *  - A handle is not thread-safe: one call at a time per handle.
+ */
+#ifndef AEWAVE_H
+#define AEWAVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct aew_handle aew_handle;
+
+/* Storage of the forward history used by the adjoint and incremental solves. */
+enum {
+  AEW_FULL = 0,     /* every strain e^n kept in HBM (FP32, nt * nx*ny*nz floats)       */
+  AEW_REVOLVE = 1,  /* binomial recompute-checkpointing with n_checkpoints state slots  */
+  AEW_AE = 2        /* every state encoded to FP16 latents by the per-block codec       */
+};
+
+/* Error codes. */
+enum {
+  AEW_OK = 0,
+  AEW_E_CONFIG = -1,      /* invalid configuration (sizes, spacing, receivers, ...)    */
+  AEW_E_CFL = -2,         /* max c violates the stability bound c dt / h <= 1/sqrt(3)  */
+  AEW_E_NONFINITE = -3,   /* NaN or Inf in an input field                              */
+  AEW_E_NOCODEC = -4,     /* AE storage requested before codec weights were set        */
+  AEW_E_NOGRADIENT = -5,  /* hessvec/jvp with no stored forward history for this c     */
+  AEW_E_NOMEM = -6,       /* device allocation failed                                  */
+  AEW_E_CUDA = -7,        /* a CUDA runtime call or kernel launch failed               */
+  AEW_E_OVERFLOW = -8,    /* a latent overflowed FP16                                  */
+  AEW_E_ARG = -9,         /* NULL pointer or out-of-range argument                     */
+  AEW_E_IO = -10,         /* file could not be read or written                         */
+  AEW_E_TIMEOUT = -11     /* a bounded device-side wait gave up                        */
+};
+
+typedef struct {
+  int nx, ny, nz;         /* nodes per axis, each >= 4 and a multiple of 4
+                             (a multiple of 8 for AEW_AE: 8x8x8-node codec blocks)   */
+  double h;               /* grid spacing [m]                                         */
+  double cfl;             /* dt = cfl * h / cmax                                      */
+  double cmax;            /* wave speed used for dt [m/s]                             */
+  int nt;                 /* number of time steps (>= 1)                              */
+  int src[3];             /* source node (i, j, k); the force acts on its z-face      */
+  double f0, t0;          /* default source: s^n = -R(n dt), Ricker wavelet of Sec. 4.1
+                             with peak frequency f0 [Hz] centred at t0 [s]            */
+  int nrec;               /* number of receivers (>= 0)                               */
+  const int* rec_ijk;     /* host [nrec][3] receiver nodes (i, j, k); all receivers
+                             must share one k (a node plane), copied at create time   */
+  int storage;            /* AEW_FULL, AEW_REVOLVE or AEW_AE                          */
+  int n_checkpoints;      /* AEW_REVOLVE: number of state slots (>= 0)                */
+  int accum_window;       /* steps summed in FP32 before each FP64 flush of the
+                             gradient accumulator (>= 1; 8 is a good default)         */
+  int n_lat;              /* codec latent width: 64 (32x compression) or 32 (64x)     */
+} aew_config;
+
+typedef struct {
+  size_t device_bytes;          /* bytes of device memory held by the handle         */
+  size_t latent_bytes;          /* of which latent store (AEW_AE)                    */
+  size_t history_bytes;         /* of which stored e^n (AEW_FULL) or checkpoints     */
+  long long forward_steps;      /* forward leapfrog steps run by the last gradient   */
+  long long adjoint_steps;      /* adjoint steps run by the last gradient            */
+  long long hvp_forward_steps;  /* forward-type steps run by the last hessvec        */
+  double last_misfit;           /* J of the last gradient                            */
+  int latent_overflow;          /* 1 if a latent overflowed FP16 in the last encode  */
+  long long kernel_launches;    /* kernels launched by this handle since creation    */
+} aew_stats_t;
+
+/* ---------------------------------------------------------------------------------
+ * Handle lifetime
+ * ------------------------------------------------------------------------------- */
+
+/* Validate `cfg`, allocate every buffer the storage mode needs on the current
+ * device, and return a handle in *out.  Returns AEW_E_CONFIG / AEW_E_NOMEM on
+ * failure (*out is then NULL).  The handle records the device that was current. */
+int aew_create(const aew_config* cfg, aew_handle** out);
+
+/* Free every buffer of the handle (synchronising the device first).  NULL is a no-op. */
+void aew_destroy(aew_handle* h);
+
+/* Message describing the last error on this handle ("" if none); valid until the
+ * next call on the handle.  With h == NULL: the last error of aew_create. */
+const char* aew_last_error(const aew_handle* h);
+
+/* Counters and memory of the handle (host struct filled in). */
+int aew_stats(const aew_handle* h, aew_stats_t* out);
+
+/* ---------------------------------------------------------------------------------
+ * Codec: the per-block autoencoder of Sec. 3.1 / Sec. 3.3 (dense layers sigma(yW+b),
+ * Eq. (5)).  Encoder 2048 -> 512 (GELU) -> n_lat; decoder n_lat -> 512 (GELU) -> 2048.
+ * Block vector order: k = z*256 + f*64 + y*8 + x, f = 0:e, 1:vx, 2:vy, 3:vz (x, y, z
+ * node offsets inside the 8x8x8 block); block b = (bz*NBy + by)*NBx + bx.
+ * Precision: BF16 operands (FP16 for the decoder's first layer, whose input is the
+ * FP16 latent) with FP32 accumulation on tcgen05 tensor cores; FP32 biases and GELU.
+ * ------------------------------------------------------------------------------- */
+
+/* Set the codec weights from host FP32 arrays, row-major, layer y -> y W + b:
+ * W1 [2048][512], b1 [512], W2 [512][n_lat], b2 [n_lat],
+ * W3 [n_lat][512], b3 [512], W4 [512][2048], b4 [2048].  Copied; not retained. */
+int aew_codec_set(aew_handle* h, const float* W1_host, const float* b1_host,
+                  const float* W2_host, const float* b2_host,
+                  const float* W3_host, const float* b3_host,
+                  const float* W4_host, const float* b4_host);
+
+/* Copy the current FP32 master weights out (same shapes as aew_codec_set). */
+int aew_codec_get(const aew_handle* h, float* W1_host, float* b1_host,
+                  float* W2_host, float* b2_host,
+                  float* W3_host, float* b3_host,
+                  float* W4_host, float* b4_host);
+
+/* Encode one state.  fields_dev = {e, vx, vy, vz} device [nz][ny][nx];
+ * scale_host[4] = the per-field divisors s_f (0 means the field is fed as 0);
+ * latents_dev: device FP16 [nblocks][n_lat] (written). */
+int aew_codec_encode(aew_handle* h, const float* const fields_dev[4], const float* scale_host,
+                     uint16_t* latents_dev, void* stream);
+
+/* Decode latents.  out_dev: device FP32 [nblocks][2048] normalised block vectors
+ * (all four fields, not multiplied by any scale). */
+int aew_codec_decode(aew_handle* h, const uint16_t* latents_dev, float* out_dev, void* stream);
+
+/* Decode latents to the strain field only: e_dev[nz][ny][nx] = s_e * (decoded e part),
+ * with boundary nodes set to 0 (the boundary condition of Sec. 2). */
+int aew_codec_decode_e(aew_handle* h, const uint16_t* latents_dev, float scale_e,
+                       float* e_dev, void* stream);
+
+/* ---------------------------------------------------------------------------------
+ * Solves
+ * ------------------------------------------------------------------------------- */
+
+/* d = F(c): forward solve from zero initial state.  c_dev [nz][ny][nx] in m/s;
+ * wavelet_host: s^n for n = 0..nt-1 (NULL = the default Ricker force);
+ * d_dev: [nt+1][nrec][3] (written; row 0 = B v^0 = 0). */
+int aew_forward(aew_handle* h, const float* c_dev, const float* wavelet_host,
+                float* d_dev, void* stream);
+
+/* Advance a caller-owned state {e, vx, vy, vz} (device, in place) by nsteps leapfrog
+ * steps starting at time index n0, with source s^n = wavelet_host[n - n0] (NULL =
+ * no source) and receiver record d_dev[nsteps+1][nrec][3] (NULL = none). */
+int aew_propagate(aew_handle* h, const float* c_dev, float* const state_dev[4], int n0,
+                  int nsteps, const float* wavelet_host, float* d_dev, void* stream);
+
+/* Gradient of J(c) = 1/2 sum_{n=1..nt} |d^n - d_obs^n|^2 with respect to c:
+ * forward solve (storing the history per the storage mode), misfit, adjoint solve
+ * with FP64 time accumulation of dJ/dm, g = 2 c dJ/dm.
+ * d_obs_dev [nt+1][nrec][3]; g_dev [nz][ny][nx] (written); misfit_host (may be NULL)
+ * receives J (this synchronises the stream).  Keeps the forward history for later
+ * aew_hessvec / aew_jvp calls at the same c. */
+int aew_gradient(aew_handle* h, const float* c_dev, const float* d_obs_dev,
+                 float* g_dev, double* misfit_host, void* stream);
+
+/* Gauss-Newton Hessian-vector product at the c of the last aew_gradient:
+ * hdc_dev = J_F^T J_F dc_dev (incremental forward with dm = 2 c dc, then the
+ * incremental adjoint with residual B dv).  AEW_E_NOGRADIENT if no gradient ran. */
+int aew_hessvec(aew_handle* h, const float* dc_dev, float* hdc_dev, void* stream);
+
+/* Jacobian-vector product dd_dev = J_F dc_dev [nt+1][nrec][3] (incremental forward
+ * alone) at the c of the last aew_gradient. */
+int aew_jvp(aew_handle* h, const float* dc_dev, float* dd_dev, void* stream);
+
+/* Algorithm 1 (data generation): run the forward solve for c_dev and pack every
+ * `every`-th state n (n = every, 2*every, ... < nt) into BF16 block vectors, each
+ * field divided by its running maximum.  out_dev: device BF16 (uint16 bit patterns)
+ * [max_vectors][2048]; *n_written receives the number of vectors written (at most
+ * max_vectors).  The history storage of the handle is not touched. */
+int aew_snapshots(aew_handle* h, const float* c_dev, int every, uint16_t* out_dev,
+                  long long max_vectors, long long* n_written, void* stream);
+
+/* One training step of the codec on a minibatch: batch_dev = BF16 [batch][2048]
+ * normalised vectors; loss = mean squared reconstruction error (Sec. 3.3); LAMB
+ * update (You et al. 2019; beta1 0.9, beta2 0.999, eps 1e-6, no weight decay) of the
+ * FP32 master weights with learning rate lr.  loss_host (may be NULL) receives the
+ * loss before the update (this synchronises the stream). */
+int aew_codec_train_step(aew_handle* h, const uint16_t* batch_dev, int batch, float lr,
+                         float* loss_host, void* stream);
+
+/* ---------------------------------------------------------------------------------
+ * Checks and host logic
+ * ------------------------------------------------------------------------------- */
+
+/* FP64 inner product sum a[i] b[i] of two device FP32 arrays of n elements
+ * (for the adjoint-identity and finite-difference checks).  Synchronises `stream`. */
+int aew_dot(const float* a_dev, const float* b_dev, size_t n, double* out_host, void* stream);
+
+/* The binomial checkpointing plan the library runs for nt steps with s state slots
+ * (host only, no device work).  ops/args (host, capacity `cap`) receive the actions:
+ * op 0 = advance args steps, 1 = store in slot args, 2 = restore slot args (-1 = the
+ * zero initial state), 3 = final step nt-1 -> nt (its receiver record only; the live
+ * state stays nt-1), 4 = adjoint step args.  *n_ops = number of actions (also when
+ * it exceeds cap, in which case nothing beyond cap is written); *fwd_steps = forward
+ * steps of the plan. */
+int aew_revolve_plan(int nt, int s, int* ops, int* args, long long cap,
+                     long long* n_ops, long long* fwd_steps);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AEWAVE_H */

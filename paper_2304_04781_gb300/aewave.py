@@ -1,0 +1,331 @@
+"""Python binding of the aewave C-ABI library (include/aewave.h).
+
+Argument marshalling only: every step of the computation runs in the library's CUDA
+kernels.  PyTorch supplies device memory (tensors' data pointers) and the current
+CUDA stream.  There is no CPU fallback: if the library cannot be loaded or built,
+every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, byref, c_double, c_float, c_int, c_longlong, c_size_t, c_void_p
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+AEW_FULL, AEW_REVOLVE, AEW_AE = 0, 1, 2
+STORAGE = {"full": AEW_FULL, "revolve": AEW_REVOLVE, "ae": AEW_AE}
+
+_ERRORS = {
+    -1: "AEW_E_CONFIG", -2: "AEW_E_CFL", -3: "AEW_E_NONFINITE", -4: "AEW_E_NOCODEC",
+    -5: "AEW_E_NOGRADIENT", -6: "AEW_E_NOMEM", -7: "AEW_E_CUDA", -8: "AEW_E_OVERFLOW",
+    -9: "AEW_E_ARG", -10: "AEW_E_IO", -11: "AEW_E_TIMEOUT",
+}
+
+
+class AewError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class aew_config(ctypes.Structure):
+    _fields_ = [
+        ("nx", c_int), ("ny", c_int), ("nz", c_int),
+        ("h", c_double), ("cfl", c_double), ("cmax", c_double),
+        ("nt", c_int), ("src", c_int * 3), ("f0", c_double), ("t0", c_double),
+        ("nrec", c_int), ("rec_ijk", POINTER(c_int)),
+        ("storage", c_int), ("n_checkpoints", c_int), ("accum_window", c_int), ("n_lat", c_int),
+    ]
+
+
+class aew_stats_t(ctypes.Structure):
+    _fields_ = [
+        ("device_bytes", c_size_t), ("latent_bytes", c_size_t), ("history_bytes", c_size_t),
+        ("forward_steps", c_longlong), ("adjoint_steps", c_longlong),
+        ("hvp_forward_steps", c_longlong), ("last_misfit", c_double), ("latent_overflow", c_int),
+        ("kernel_launches", c_longlong),
+    ]
+
+
+_LIB = None
+
+# (name, restype, argtypes) of every exported entry point
+_SIGS = [
+    ("aew_create", c_int, [POINTER(aew_config), POINTER(c_void_p)]),
+    ("aew_destroy", None, [c_void_p]),
+    ("aew_last_error", ctypes.c_char_p, [c_void_p]),
+    ("aew_stats", c_int, [c_void_p, POINTER(aew_stats_t)]),
+    ("aew_codec_set", c_int, [c_void_p] + [c_void_p] * 8),
+    ("aew_codec_get", c_int, [c_void_p] + [c_void_p] * 8),
+    ("aew_codec_encode", c_int, [c_void_p, POINTER(c_void_p), POINTER(c_float), c_void_p, c_void_p]),
+    ("aew_codec_decode", c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("aew_codec_decode_e", c_int, [c_void_p, c_void_p, c_float, c_void_p, c_void_p]),
+    ("aew_forward", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("aew_propagate", c_int, [c_void_p, c_void_p, POINTER(c_void_p), c_int, c_int, c_void_p,
+                              c_void_p, c_void_p]),
+    ("aew_gradient", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_double), c_void_p]),
+    ("aew_hessvec", c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("aew_jvp", c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("aew_snapshots", c_int, [c_void_p, c_void_p, c_int, c_void_p, c_longlong,
+                              POINTER(c_longlong), c_void_p]),
+    ("aew_codec_train_step", c_int, [c_void_p, c_void_p, c_int, c_float, POINTER(c_float),
+                                     c_void_p]),
+    ("aew_dot", c_int, [c_void_p, c_void_p, c_size_t, POINTER(c_double), c_void_p]),
+    ("aew_revolve_plan", c_int, [c_int, c_int, c_void_p, c_void_p, c_longlong,
+                                 POINTER(c_longlong), POINTER(c_longlong)]),
+]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libaewave.so (building it first if it is missing or stale)."""
+    global _LIB
+    if _LIB is None:
+        if not _build.up_to_date():
+            _build.build()
+        L = ctypes.CDLL(_build.LIB)
+        for name, res, args in _SIGS:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return c_void_p(t.data_ptr())
+
+
+def _stream():
+    return c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _host_f32(a) -> Optional[np.ndarray]:
+    if a is None:
+        return None
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+def dot(a: torch.Tensor, b: torch.Tensor) -> float:
+    """FP64 inner product of two CUDA FP32 tensors (aew_dot)."""
+    assert a.numel() == b.numel() and a.dtype == torch.float32 and b.dtype == torch.float32
+    out = c_double(0.0)
+    rc = lib().aew_dot(_ptr(a), _ptr(b), a.numel(), byref(out), _stream())
+    if rc != 0:
+        raise AewError(rc, "aew_dot failed")
+    return out.value
+
+
+def revolve_plan(nt: int, s: int):
+    """The library's checkpointing plan: (list of (op, arg), forward steps)."""
+    L = lib()
+    n = c_longlong(0)
+    f = c_longlong(0)
+    rc = L.aew_revolve_plan(nt, s, None, None, 0, byref(n), byref(f))
+    if rc != 0:
+        raise AewError(rc, "aew_revolve_plan failed")
+    ops = (c_int * n.value)()
+    args = (c_int * n.value)()
+    L.aew_revolve_plan(nt, s, ops, args, n.value, byref(n), byref(f))
+    names = {0: "advance", 1: "store", 2: "restore", 3: "final", 4: "reverse"}
+    return [(names[ops[i]], args[i]) for i in range(n.value)], f.value
+
+
+class Solver:
+    """Owns one aew_handle: grid, time stepping, receivers and history storage."""
+
+    def __init__(self, shape, h: float, nt: int, rec, storage: str = "full",
+                 n_checkpoints: int = 20, accum_window: int = 8, n_lat: int = 64,
+                 cfl: float = 0.5, cmax: float = 3000.0, src=None, f0: float = 25.0,
+                 t0: Optional[float] = None):
+        nz, ny, nx = shape
+        self.shape = (nz, ny, nx)
+        self.nt = nt
+        rec = np.ascontiguousarray(np.asarray(rec, dtype=np.int32).reshape(-1, 3))
+        self.nrec = rec.shape[0]
+        self._rec = rec
+        cfg = aew_config()
+        cfg.nx, cfg.ny, cfg.nz = nx, ny, nz
+        cfg.h, cfg.cfl, cfg.cmax = h, cfl, cmax
+        cfg.nt = nt
+        s = src if src is not None else (nx // 2, ny // 2, nz // 2)
+        cfg.src[0], cfg.src[1], cfg.src[2] = s
+        cfg.f0 = f0
+        cfg.t0 = t0 if t0 is not None else 1.0 / f0
+        cfg.nrec = self.nrec
+        cfg.rec_ijk = rec.ctypes.data_as(POINTER(c_int)) if self.nrec else None
+        cfg.storage = STORAGE[storage]
+        cfg.n_checkpoints = n_checkpoints
+        cfg.accum_window = accum_window
+        cfg.n_lat = n_lat
+        self.n_lat = n_lat
+        self.dt = cfl * h / cmax
+        self._h = c_void_p()
+        L = lib()
+        rc = L.aew_create(byref(cfg), byref(self._h))
+        if rc != 0:
+            raise AewError(rc, L.aew_last_error(None).decode())
+
+    # ------------------------------------------------------------------ helpers
+    def _check(self, rc: int):
+        if rc != 0:
+            raise AewError(rc, lib().aew_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().aew_destroy(self._h)
+            self._h = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def nblocks(self) -> int:
+        nz, ny, nx = self.shape
+        return (nz // 8) * (ny // 8) * (nx // 8)
+
+    def _drec(self) -> torch.Tensor:
+        return torch.empty((self.nt + 1, self.nrec, 3), device="cuda", dtype=torch.float32)
+
+    # ------------------------------------------------------------------ solves
+    def forward(self, c: torch.Tensor, wavelet=None) -> torch.Tensor:
+        d = self._drec()
+        w = _host_f32(wavelet)
+        self._check(lib().aew_forward(self._h, _ptr(c), w.ctypes.data if w is not None else None,
+                                      _ptr(d), _stream()))
+        return d
+
+    def propagate(self, c: torch.Tensor, state, n0: int, nsteps: int, wavelet=None,
+                  record: bool = False):
+        """Advance the (e, vx, vy, vz) CUDA tensors in place; returns receiver data or None."""
+        arr = (c_void_p * 4)(*[t.data_ptr() for t in state])
+        for t in state:
+            _ptr(t)
+        d = torch.empty((nsteps + 1, self.nrec, 3), device="cuda") if record else None
+        w = _host_f32(wavelet)
+        self._check(lib().aew_propagate(self._h, _ptr(c), arr, n0, nsteps,
+                                        w.ctypes.data if w is not None else None, _ptr(d), _stream()))
+        return d
+
+    def gradient(self, c: torch.Tensor, d_obs: torch.Tensor, g: Optional[torch.Tensor] = None):
+        """(J, dJ/dc) for J = 1/2 sum_{n>=1} |d^n - d_obs^n|^2."""
+        if g is None:
+            g = torch.empty_like(c)
+        J = c_double(0.0)
+        self._check(lib().aew_gradient(self._h, _ptr(c), _ptr(d_obs), _ptr(g), byref(J), _stream()))
+        return J.value, g
+
+    def hessvec(self, dc: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty_like(dc)
+        self._check(lib().aew_hessvec(self._h, _ptr(dc), _ptr(out), _stream()))
+        return out
+
+    def jvp(self, dc: torch.Tensor) -> torch.Tensor:
+        dd = self._drec()
+        self._check(lib().aew_jvp(self._h, _ptr(dc), _ptr(dd), _stream()))
+        return dd
+
+    def stats(self) -> dict:
+        s = aew_stats_t()
+        self._check(lib().aew_stats(self._h, byref(s)))
+        return {k: getattr(s, k) for k, _ in aew_stats_t._fields_}
+
+    # ------------------------------------------------------------------ codec
+    def codec_set(self, W: dict):
+        arrs = [_host_f32(W[k]) for k in ("W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4")]
+        self._codec_host = arrs
+        self._check(lib().aew_codec_set(self._h, *[a.ctypes.data for a in arrs]))
+
+    def codec_get(self) -> dict:
+        nl = self.n_lat
+        shapes = {"W1": (2048, 512), "b1": (512,), "W2": (512, nl), "b2": (nl,),
+                  "W3": (nl, 512), "b3": (512,), "W4": (512, 2048), "b4": (2048,)}
+        out = {k: np.empty(v, np.float32) for k, v in shapes.items()}
+        self._check(lib().aew_codec_get(self._h, *[out[k].ctypes.data for k in shapes]))
+        return out
+
+    def codec_encode(self, fields, scale) -> torch.Tensor:
+        lat = torch.empty((self.nblocks, self.n_lat), device="cuda", dtype=torch.float16)
+        arr = (c_void_p * 4)(*[f.data_ptr() for f in fields])
+        for f in fields:
+            _ptr(f)
+        s = (c_float * 4)(*[float(x) for x in scale])
+        self._check(lib().aew_codec_encode(self._h, arr, s, _ptr(lat), _stream()))
+        return lat
+
+    def codec_decode(self, lat: torch.Tensor) -> torch.Tensor:
+        out = torch.empty((lat.shape[0], 2048), device="cuda", dtype=torch.float32)
+        self._check(lib().aew_codec_decode(self._h, _ptr(lat), _ptr(out), _stream()))
+        return out
+
+    def codec_decode_e(self, lat: torch.Tensor, scale_e: float) -> torch.Tensor:
+        e = torch.empty(self.shape, device="cuda", dtype=torch.float32)
+        self._check(lib().aew_codec_decode_e(self._h, _ptr(lat), c_float(scale_e), _ptr(e), _stream()))
+        return e
+
+    def snapshots(self, c: torch.Tensor, every: int, max_vectors: int,
+                  out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Algorithm 1: BF16 block vectors of every `every`-th state (as int16 bit patterns)."""
+        if out is None:
+            out = torch.empty((max_vectors, 2048), device="cuda", dtype=torch.bfloat16)
+        n = c_longlong(0)
+        self._check(lib().aew_snapshots(self._h, _ptr(c), every, _ptr(out), max_vectors, byref(n),
+                                        _stream()))
+        return out[: n.value]
+
+    def train_step(self, batch: torch.Tensor, lr: float, want_loss: bool = True) -> Optional[float]:
+        loss = c_float(0.0)
+        self._check(lib().aew_codec_train_step(self._h, _ptr(batch), batch.shape[0], c_float(lr),
+                                               byref(loss) if want_loss else None, _stream()))
+        return loss.value if want_loss else None
+
+
+class Misfit(torch.autograd.Function):
+    """J(c) = 1/2 |F(c) - d_obs|^2 with dJ/dc from the library's adjoint solve."""
+
+    @staticmethod
+    def forward(ctx, c: torch.Tensor, d_obs: torch.Tensor, solver: Solver):
+        J, g = solver.gradient(c.contiguous(), d_obs.contiguous())
+        ctx.save_for_backward(g)
+        return torch.tensor(J, dtype=torch.float64, device=c.device)
+
+    @staticmethod
+    def backward(ctx, gJ):
+        (g,) = ctx.saved_tensors
+        return (gJ.to(g.dtype) * g, None, None)
+
+
+class ForwardMap(torch.autograd.Function):
+    """d = F(c) with the vector-Jacobian product J_F^T r from the adjoint solve."""
+
+    @staticmethod
+    def forward(ctx, c: torch.Tensor, solver: Solver):
+        d = solver.forward(c.contiguous())
+        ctx.solver = solver
+        ctx.save_for_backward(c, d)
+        return d
+
+    @staticmethod
+    def backward(ctx, r):
+        c, d = ctx.saved_tensors
+        # the gradient of 1/2 |F(c) - (d - r)|^2 is J_F^T r
+        _, g = ctx.solver.gradient(c, (d - r).contiguous())
+        return g, None

@@ -1,0 +1,907 @@
+// C-ABI of the aewave library: handle lifetime, the forward / adjoint / incremental
+// time loops, the three history-storage modes and the checkpointing executor.
+//
+// Everything runs on the caller's stream; the host only sequences kernel launches.
+// Operations (see include/aewave.h): forward solve d = B A(c) (Sec. 2), gradient of the
+// misfit of Eq. (3), Gauss-Newton Hessian-vector product via the incremental forward
+// and incremental adjoint problems (Sec. 4), with the forward history either stored,
+// recomputed from binomial checkpoints (Sec. 1), or compressed to autoencoder latents
+// once per gradient and decoded by every later adjoint-type solve (Sec. 3, Sec. 4).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/aewave.h"
+#include "aew_codec.cuh"
+#include "aew_internal.cuh"
+#include "aew_revolve.h"
+
+using aew::Codec;
+
+struct aew_handle {
+  aew_config cfg{};
+  std::vector<int> rec;
+  int krec = -1;
+  int device = 0;
+  double dt = 0.0;
+  float dth = 0.f;
+  size_t C = 0;
+  int kc = 1;
+  size_t nrow = 0;   // nrec * 3
+  std::string err;
+  aew_stats_t stats{};
+
+  float* c = nullptr;
+  float* m = nullptr;
+  float* dm = nullptr;
+  float* st[2][4] = {};
+  float* ad[2][4] = {};
+  float* acc32 = nullptr;
+  double* acc64 = nullptr;
+  float* estore = nullptr;
+  float* ckpt = nullptr;
+  uint16_t* lat = nullptr;
+  float* edec = nullptr;
+  unsigned* amax = nullptr;
+  float* scales = nullptr;
+  int* ovf = nullptr;
+  float* d = nullptr;
+  float* R = nullptr;
+  float* dd = nullptr;
+  int* rec_map = nullptr;
+  double* part = nullptr;
+  aew::FieldCheck* chk = nullptr;
+  float* scale_tmp = nullptr;
+  std::vector<float> wav;
+  bool have_grad = false;
+  Codec* codec = nullptr;
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+int fail(aew_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+int cuda_fail(aew_handle* h, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  return fail(h, AEW_E_CUDA, m);
+}
+
+#define AEW_CK(expr)                                     \
+  do {                                                   \
+    cudaError_t _e = (expr);                             \
+    if (_e != cudaSuccess) return cuda_fail(h, _e, #expr); \
+  } while (0)
+
+template <class T>
+bool dalloc(aew_handle* h, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return true;
+  void* q = nullptr;
+  if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  h->allocs.push_back(q);
+  h->bytes += count * sizeof(T);
+  *p = static_cast<T*>(q);
+  return true;
+}
+
+double ricker(double t, double f0, double t0) {
+  const double sig = 1.0 / (std::sqrt(2.0) * M_PI * f0);
+  const double tau = t - t0;
+  return (1.0 - tau * tau / (sig * sig)) * std::exp(-tau * tau / (2.0 * sig * sig));
+}
+
+cudaStream_t S(void* s) { return static_cast<cudaStream_t>(s); }
+
+size_t nblocks_of(const aew_handle* h) {
+  return (size_t)(h->cfg.nx / 8) * (h->cfg.ny / 8) * (h->cfg.nz / 8);
+}
+
+// ---------------------------------------------------------------------------------
+// Single steps
+// ---------------------------------------------------------------------------------
+int fwd_step(aew_handle* h, int n, float* const in[4], float* const out[4], const float* wav,
+             float* d_row, unsigned* amax, cudaStream_t s) {
+  aew::FwdStep a{};
+  a.m = h->m;
+  a.e = in[0];
+  a.vx = in[1];
+  a.vy = in[2];
+  a.vz = in[3];
+  a.e1 = out[0];
+  a.vx1 = out[1];
+  a.vy1 = out[2];
+  a.vz1 = out[3];
+  a.nx = h->cfg.nx;
+  a.ny = h->cfg.ny;
+  a.nz = h->cfg.nz;
+  a.kc = h->kc;
+  a.dth = h->dth;
+  a.dts = wav ? (float)(h->dt * (double)wav[n]) : 0.f;
+  a.si = h->cfg.src[0];
+  a.sj = h->cfg.src[1];
+  a.sk = wav ? h->cfg.src[2] : -1;
+  a.krec = d_row ? h->krec : -1;
+  a.rec_map = h->rec_map;
+  a.d_out = d_row;
+  a.amax = amax;
+  AEW_CK(aew::launch_fwd_step(a, false, s));
+  ++h->stats.kernel_launches;
+  return AEW_OK;
+}
+
+int incr_step(aew_handle* h, float* const in[4], float* const out[4], const float* en,
+              float* d_row, cudaStream_t s) {
+  aew::FwdStep a{};
+  a.m = h->m;
+  a.e = in[0];
+  a.vx = in[1];
+  a.vy = in[2];
+  a.vz = in[3];
+  a.e1 = out[0];
+  a.vx1 = out[1];
+  a.vy1 = out[2];
+  a.vz1 = out[3];
+  a.dm = h->dm;
+  a.ef = en;
+  a.nx = h->cfg.nx;
+  a.ny = h->cfg.ny;
+  a.nz = h->cfg.nz;
+  a.kc = h->kc;
+  a.dth = h->dth;
+  a.dts = 0.f;
+  a.sk = -1;
+  a.krec = d_row ? h->krec : -1;
+  a.rec_map = h->rec_map;
+  a.d_out = d_row;
+  AEW_CK(aew::launch_fwd_step(a, true, s));
+  ++h->stats.kernel_launches;
+  return AEW_OK;
+}
+
+// reverse step n: (lam, mu) in ad[cur] -> ad[cur ^ 1]
+int adj_step(aew_handle* h, int n, int cur, const float* resid, const float* en,
+             cudaStream_t s) {
+  aew::AdjStep a{};
+  a.m = h->m;
+  a.mu = h->ad[cur][0];
+  a.lx = h->ad[cur][1];
+  a.ly = h->ad[cur][2];
+  a.lz = h->ad[cur][3];
+  a.mu1 = h->ad[cur ^ 1][0];
+  a.lx1 = h->ad[cur ^ 1][1];
+  a.ly1 = h->ad[cur ^ 1][2];
+  a.lz1 = h->ad[cur ^ 1][3];
+  a.en = en;
+  a.acc32 = h->acc32;
+  a.acc64 = h->acc64;
+  const int W = h->cfg.accum_window;
+  const int w = (h->cfg.nt - 1 - n) % W;
+  a.acc_mode = (w == 0 ? aew::kAccFirst : 0) | ((w == W - 1 || n == 0) ? aew::kAccLast : 0);
+  a.nx = h->cfg.nx;
+  a.ny = h->cfg.ny;
+  a.nz = h->cfg.nz;
+  a.kc = h->kc;
+  a.dth = h->dth;
+  a.krec = h->krec;
+  a.rec_map = h->rec_map;
+  a.resid = (resid && h->nrow) ? resid + (size_t)(n + 1) * h->nrow : nullptr;
+  AEW_CK(aew::launch_adj_step(a, s));
+  ++h->stats.kernel_launches;
+  return AEW_OK;
+}
+
+int zero_state(aew_handle* h, float* const f[4], cudaStream_t s) {
+  for (int i = 0; i < 4; ++i) AEW_CK(cudaMemsetAsync(f[i], 0, h->C * sizeof(float), s));
+  return AEW_OK;
+}
+
+int copy_state(aew_handle* h, float* const dst[4], float* const src[4], cudaStream_t s) {
+  for (int i = 0; i < 4; ++i)
+    AEW_CK(cudaMemcpyAsync(dst[i], src[i], h->C * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  return AEW_OK;
+}
+
+// m = c^2 with checks of c (synchronises the stream to read the checks)
+int prepare_c(aew_handle* h, const float* c_dev, cudaStream_t s) {
+  if (!c_dev) return fail(h, AEW_E_ARG, "c is NULL");
+  AEW_CK(cudaMemsetAsync(h->chk, 0, sizeof(aew::FieldCheck), s));
+  AEW_CK(cudaMemcpyAsync(h->c, c_dev, h->C * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  AEW_CK(aew::launch_prep_m(h->c, h->m, h->C, h->chk, s));
+  ++h->stats.kernel_launches;
+  aew::FieldCheck ck{};
+  AEW_CK(cudaMemcpyAsync(&ck, h->chk, sizeof(ck), cudaMemcpyDeviceToHost, s));
+  AEW_CK(cudaStreamSynchronize(s));
+  if (ck.nonfinite) return fail(h, AEW_E_NONFINITE, "c contains NaN or Inf");
+  if (ck.cneg) return fail(h, AEW_E_CONFIG, "c must be positive everywhere");
+  float cmax;
+  std::memcpy(&cmax, &ck.cmax_bits, sizeof(float));
+  if ((double)cmax * h->dt / h->cfg.h > 1.0 / std::sqrt(3.0)) {
+    char buf[160];
+    std::snprintf(buf, sizeof buf, "max c = %.6g violates c dt / h <= 1/sqrt(3) (dt = %.6g)",
+                  (double)cmax, h->dt);
+    return fail(h, AEW_E_CFL, buf);
+  }
+  return AEW_OK;
+}
+
+// residual R = d - d_obs (rows 1..nt) and misfit J (device double part[kRedBlocks])
+int residual_and_misfit(aew_handle* h, const float* d_obs, cudaStream_t s) {
+  const size_t n = (size_t)(h->cfg.nt + 1) * h->nrow;
+  if (n == 0) {
+    AEW_CK(cudaMemsetAsync(h->part + aew::kRedBlocks, 0, sizeof(double), s));
+    return AEW_OK;
+  }
+  AEW_CK(aew::launch_residual(h->d, d_obs, h->R, h->nrow, n, h->part, aew::kRedBlocks, s));
+  AEW_CK(aew::launch_sum_partials(h->part, aew::kRedBlocks, 0.5, h->part + aew::kRedBlocks, s));
+  h->stats.kernel_launches += 2;
+  return AEW_OK;
+}
+
+int begin_adjoint(aew_handle* h, cudaStream_t s) {
+  for (int i = 0; i < 4; ++i) AEW_CK(cudaMemsetAsync(h->ad[0][i], 0, h->C * sizeof(float), s));
+  AEW_CK(cudaMemsetAsync(h->acc64, 0, h->C * sizeof(double), s));
+  return AEW_OK;
+}
+
+const float* wav_or_default(aew_handle* h, const float* w) { return w ? w : h->wav.data(); }
+
+float* drow(aew_handle* h, float* d, int n) {
+  return h->nrow ? d + (size_t)n * h->nrow : nullptr;
+}
+
+// ---------------------------------------------------------------------------------
+// AE helpers
+// ---------------------------------------------------------------------------------
+int encode_state(aew_handle* h, int n, float* const f[4], cudaStream_t s) {
+  const size_t nb = nblocks_of(h);
+  cudaError_t e = aew::codec_encode_grid(
+      h->codec, f, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->scales + 4 * (size_t)(n - 1),
+      h->amax + 4 * (size_t)n, h->scales + 4 * (size_t)n,
+      h->lat + (size_t)n * nb * h->cfg.n_lat, h->ovf, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "codec_encode_grid");
+  h->stats.kernel_launches += 3;
+  return AEW_OK;
+}
+
+int decode_e(aew_handle* h, int n, cudaStream_t s) {
+  const size_t nb = nblocks_of(h);
+  cudaError_t e = aew::codec_decode_grid_e(h->codec, h->lat + (size_t)n * nb * h->cfg.n_lat,
+                                           h->cfg.nx, h->cfg.ny, h->cfg.nz,
+                                           h->scales + 4 * (size_t)n, h->edec, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "codec_decode_grid_e");
+  h->stats.kernel_launches += 2;
+  return AEW_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// Gradient drivers
+// ---------------------------------------------------------------------------------
+int gradient_full(aew_handle* h, const float* d_obs, const float* wav, cudaStream_t s) {
+  const int nt = h->cfg.nt;
+  float* vb[2][3] = {{h->st[0][1], h->st[0][2], h->st[0][3]},
+                     {h->st[1][1], h->st[1][2], h->st[1][3]}};
+  for (int i = 0; i < 3; ++i) AEW_CK(cudaMemsetAsync(vb[0][i], 0, h->C * sizeof(float), s));
+  AEW_CK(cudaMemsetAsync(h->estore, 0, h->C * sizeof(float), s));
+  AEW_CK(cudaMemsetAsync(h->d, 0, h->nrow * sizeof(float), s));
+  for (int n = 0; n < nt; ++n) {
+    const int a = n & 1;
+    float* eout = (n + 1 < nt) ? h->estore + (size_t)(n + 1) * h->C : h->st[0][0];
+    float* in[4] = {h->estore + (size_t)n * h->C, vb[a][0], vb[a][1], vb[a][2]};
+    float* out[4] = {eout, vb[a ^ 1][0], vb[a ^ 1][1], vb[a ^ 1][2]};
+    int rc = fwd_step(h, n, in, out, wav, drow(h, h->d, n + 1), nullptr, s);
+    if (rc) return rc;
+  }
+  int rc = residual_and_misfit(h, d_obs, s);
+  if (rc) return rc;
+  if ((rc = begin_adjoint(h, s))) return rc;
+  int cur = 0;
+  for (int n = nt - 1; n >= 0; --n) {
+    const float* en = n > 0 ? h->estore + (size_t)n * h->C : nullptr;
+    if ((rc = adj_step(h, n, cur, h->R, en, s))) return rc;
+    cur ^= 1;
+  }
+  h->stats.forward_steps = nt;
+  h->stats.adjoint_steps = nt;
+  return AEW_OK;
+}
+
+// Execute a checkpointing plan.  mode 0: gradient (first pass records d, 'final'
+// computes the misfit); mode 1: incremental adjoint of the GN-HVP (residual given).
+int run_revolve(aew_handle* h, const float* d_obs, const float* resid, const float* wav,
+                bool gradient, cudaStream_t s, long long* fwd_out) {
+  const int nt = h->cfg.nt;
+  const int ns = h->cfg.n_checkpoints;
+  std::vector<aew::RevAction> plan;
+  aew::revolve_plan(nt, ns, plan);
+  int cur = 0, live = 0, acur = 0, rc;
+  long long fwd = 0;
+  if ((rc = zero_state(h, h->st[0], s))) return rc;
+  if (gradient) AEW_CK(cudaMemsetAsync(h->d, 0, h->nrow * sizeof(float), s));
+  if ((rc = begin_adjoint(h, s))) return rc;
+  std::vector<int> slot_step(ns > 0 ? ns : 1, -1);
+  const float* R = resid;
+  for (const aew::RevAction& act : plan) {
+    switch (act.op) {
+      case aew::kOpAdvance:
+        for (int k = 0; k < act.arg; ++k) {
+          rc = fwd_step(h, live, h->st[cur], h->st[cur ^ 1], wav,
+                        gradient ? drow(h, h->d, live + 1) : nullptr, nullptr, s);
+          if (rc) return rc;
+          cur ^= 1;
+          ++live;
+          ++fwd;
+        }
+        break;
+      case aew::kOpStore: {
+        float* dst[4];
+        for (int i = 0; i < 4; ++i) dst[i] = h->ckpt + ((size_t)act.arg * 4 + i) * h->C;
+        if ((rc = copy_state(h, dst, h->st[cur], s))) return rc;
+        slot_step[act.arg] = live;
+        break;
+      }
+      case aew::kOpRestore:
+        if (act.arg < 0) {
+          if ((rc = zero_state(h, h->st[cur], s))) return rc;
+          live = 0;
+        } else {
+          float* src[4];
+          for (int i = 0; i < 4; ++i) src[i] = h->ckpt + ((size_t)act.arg * 4 + i) * h->C;
+          if ((rc = copy_state(h, h->st[cur], src, s))) return rc;
+          live = slot_step[act.arg];
+        }
+        break;
+      case aew::kOpFinal:
+        if (gradient) {
+          // last step into the other buffer: records d^{nt}, keeps state nt-1 live
+          rc = fwd_step(h, live, h->st[cur], h->st[cur ^ 1], wav, drow(h, h->d, live + 1),
+                        nullptr, s);
+          if (rc) return rc;
+          ++fwd;
+          if ((rc = residual_and_misfit(h, d_obs, s))) return rc;
+          R = h->R;
+        }
+        break;
+      case aew::kOpReverse:
+        if ((rc = adj_step(h, act.arg, acur, R, act.arg > 0 ? h->st[cur][0] : nullptr, s)))
+          return rc;
+        acur ^= 1;
+        break;
+    }
+  }
+  *fwd_out = fwd;
+  return AEW_OK;
+}
+
+int gradient_ae(aew_handle* h, const float* d_obs, const float* wav, cudaStream_t s) {
+  const int nt = h->cfg.nt;
+  int rc;
+  if ((rc = zero_state(h, h->st[0], s))) return rc;
+  AEW_CK(cudaMemsetAsync(h->amax, 0, (size_t)(nt + 1) * 4 * sizeof(unsigned), s));
+  AEW_CK(cudaMemsetAsync(h->scales, 0, (size_t)(nt + 1) * 4 * sizeof(float), s));
+  AEW_CK(cudaMemsetAsync(h->ovf, 0, sizeof(int), s));
+  AEW_CK(cudaMemsetAsync(h->d, 0, h->nrow * sizeof(float), s));
+  int cur = 0;
+  for (int n = 0; n < nt; ++n) {
+    rc = fwd_step(h, n, h->st[cur], h->st[cur ^ 1], wav, drow(h, h->d, n + 1),
+                  h->amax + 4 * (size_t)(n + 1), s);
+    if (rc) return rc;
+    cur ^= 1;
+    // state n+1 is the input of adjoint step n+1 (only states 1..nt-1 are needed)
+    if (n + 1 < nt && (rc = encode_state(h, n + 1, h->st[cur], s))) return rc;
+  }
+  if ((rc = residual_and_misfit(h, d_obs, s))) return rc;
+  if ((rc = begin_adjoint(h, s))) return rc;
+  int acur = 0;
+  for (int n = nt - 1; n >= 0; --n) {
+    const float* en = nullptr;
+    if (n > 0) {
+      if ((rc = decode_e(h, n, s))) return rc;
+      en = h->edec;
+    }
+    if ((rc = adj_step(h, n, acur, h->R, en, s))) return rc;
+    acur ^= 1;
+  }
+  h->stats.forward_steps = nt;
+  h->stats.adjoint_steps = nt;
+  return AEW_OK;
+}
+
+}  // namespace
+
+// =================================================================================
+// C ABI
+// =================================================================================
+extern "C" {
+
+int aew_create(const aew_config* cfg, aew_handle** out) {
+  g_create_err.clear();
+  if (!out) return AEW_E_ARG;
+  *out = nullptr;
+  if (!cfg) {
+    g_create_err = "cfg is NULL";
+    return AEW_E_ARG;
+  }
+  auto bad = [&](const char* m) {
+    g_create_err = m;
+    return AEW_E_CONFIG;
+  };
+  const aew_config& c = *cfg;
+  if (c.nx < 4 || c.ny < 4 || c.nz < 4 || c.nx % 4 || c.ny % 4 || c.nz % 4)
+    return bad("nx, ny, nz must be >= 4 and multiples of 4");
+  if (!(c.h > 0) || !(c.cfl > 0) || !(c.cmax > 0)) return bad("h, cfl, cmax must be > 0");
+  if (c.cfl > 1.0 / std::sqrt(3.0)) return bad("cfl must be <= 1/sqrt(3)");
+  if (c.nt < 1) return bad("nt must be >= 1");
+  if (c.src[0] < 0 || c.src[0] >= c.nx || c.src[1] < 0 || c.src[1] >= c.ny || c.src[2] < 0 ||
+      c.src[2] >= c.nz)
+    return bad("source node outside the grid");
+  if (c.nrec < 0 || (c.nrec > 0 && !c.rec_ijk)) return bad("bad receiver list");
+  if (c.storage != AEW_FULL && c.storage != AEW_REVOLVE && c.storage != AEW_AE)
+    return bad("storage must be AEW_FULL, AEW_REVOLVE or AEW_AE");
+  if (c.storage == AEW_REVOLVE && c.n_checkpoints < 0) return bad("n_checkpoints must be >= 0");
+  if (c.accum_window < 1) return bad("accum_window must be >= 1");
+  if (c.storage == AEW_AE && (c.nx % 8 || c.ny % 8 || c.nz % 8))
+    return bad("AE storage needs nx, ny, nz multiples of 8");
+  if (c.n_lat != 64 && c.n_lat != 32) return bad("n_lat must be 64 or 32");
+
+  aew_handle* h = new aew_handle();
+  h->cfg = c;
+  h->cfg.rec_ijk = nullptr;
+  h->rec.assign(c.rec_ijk, c.rec_ijk + 3 * (size_t)c.nrec);
+  for (int r = 0; r < c.nrec; ++r) {
+    const int i = h->rec[3 * r], j = h->rec[3 * r + 1], k = h->rec[3 * r + 2];
+    if (i < 0 || i >= c.nx || j < 0 || j >= c.ny || k < 0 || k >= c.nz) {
+      delete h;
+      return bad("receiver outside the grid");
+    }
+    if (r == 0) h->krec = k;
+    if (k != h->krec) {
+      delete h;
+      return bad("all receivers must lie on one node plane k");
+    }
+  }
+  cudaGetDevice(&h->device);
+  h->dt = c.cfl * c.h / c.cmax;
+  h->dth = (float)(h->dt / c.h);
+  h->C = (size_t)c.nx * c.ny * c.nz;
+  h->kc = aew::default_kc(c.nx, c.ny, c.nz);
+  h->nrow = (size_t)c.nrec * 3;
+  h->wav.resize(c.nt);
+  for (int n = 0; n < c.nt; ++n) h->wav[n] = (float)(-ricker(n * h->dt, c.f0, c.t0));
+
+  const size_t C = h->C, nt = (size_t)c.nt;
+  bool ok = dalloc(h, &h->c, C) && dalloc(h, &h->m, C) && dalloc(h, &h->dm, C) &&
+            dalloc(h, &h->acc32, C) && dalloc(h, &h->acc64, C) &&
+            dalloc(h, &h->d, (nt + 1) * h->nrow) && dalloc(h, &h->R, (nt + 1) * h->nrow) &&
+            dalloc(h, &h->dd, (nt + 1) * h->nrow) &&
+            dalloc(h, &h->rec_map, (size_t)c.nx * c.ny) &&
+            dalloc(h, &h->part, aew::kRedBlocks + 8) && dalloc(h, &h->chk, 1) &&
+            dalloc(h, &h->scale_tmp, 8);
+  for (int b = 0; ok && b < 2; ++b)
+    for (int i = 0; ok && i < 4; ++i) ok = dalloc(h, &h->st[b][i], C) && dalloc(h, &h->ad[b][i], C);
+  if (ok && c.storage == AEW_FULL) ok = dalloc(h, &h->estore, nt * C);
+  if (ok && c.storage == AEW_REVOLVE && c.n_checkpoints > 0)
+    ok = dalloc(h, &h->ckpt, (size_t)c.n_checkpoints * 4 * C);
+  if (ok && c.storage == AEW_AE) {
+    const size_t nb = (size_t)(c.nx / 8) * (c.ny / 8) * (c.nz / 8);
+    ok = dalloc(h, &h->lat, nt * nb * c.n_lat) && dalloc(h, &h->edec, C) &&
+         dalloc(h, &h->amax, (nt + 1) * 4) && dalloc(h, &h->scales, (nt + 1) * 4) &&
+         dalloc(h, &h->ovf, 1);
+  }
+  if (!ok) {
+    g_create_err = "device allocation failed (" + std::to_string(h->bytes) + " bytes held)";
+    aew_destroy(h);
+    return AEW_E_NOMEM;
+  }
+  std::vector<int> map((size_t)c.nx * c.ny, -1);
+  for (int r = 0; r < c.nrec; ++r) map[(size_t)h->rec[3 * r + 1] * c.nx + h->rec[3 * r]] = r;
+  if (cudaMemcpy(h->rec_map, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice) !=
+      cudaSuccess) {
+    g_create_err = "copy of the receiver map failed";
+    aew_destroy(h);
+    return AEW_E_CUDA;
+  }
+  h->codec = aew::codec_new(c.n_lat);
+  if (!h->codec) {
+    g_create_err = "codec allocation failed";
+    aew_destroy(h);
+    return AEW_E_NOMEM;
+  }
+  h->stats.device_bytes = h->bytes + aew::codec_device_bytes(h->codec);
+  h->stats.latent_bytes =
+      c.storage == AEW_AE ? nt * (size_t)(c.nx / 8) * (c.ny / 8) * (c.nz / 8) * c.n_lat * 2 : 0;
+  h->stats.history_bytes = c.storage == AEW_FULL      ? nt * C * 4
+                           : c.storage == AEW_REVOLVE ? (size_t)c.n_checkpoints * 4 * C * 4
+                                                      : h->stats.latent_bytes;
+  *out = h;
+  return AEW_OK;
+}
+
+void aew_destroy(aew_handle* h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->codec) aew::codec_free(h->codec);
+  delete h;
+}
+
+const char* aew_last_error(const aew_handle* h) {
+  return h ? h->err.c_str() : g_create_err.c_str();
+}
+
+int aew_stats(const aew_handle* h, aew_stats_t* out) {
+  if (!h || !out) return AEW_E_ARG;
+  *out = h->stats;
+  return AEW_OK;
+}
+
+int aew_forward(aew_handle* h, const float* c_dev, const float* wavelet_host, float* d_dev,
+                void* stream) {
+  if (!h) return AEW_E_ARG;
+  h->err.clear();
+  cudaStream_t s = S(stream);
+  int rc = prepare_c(h, c_dev, s);
+  if (rc) return rc;
+  h->have_grad = false;  // m changed: stored history no longer matches
+  const float* wav = wav_or_default(h, wavelet_host);
+  if ((rc = zero_state(h, h->st[0], s))) return rc;
+  if (d_dev && h->nrow) AEW_CK(cudaMemsetAsync(d_dev, 0, h->nrow * sizeof(float), s));
+  int cur = 0;
+  for (int n = 0; n < h->cfg.nt; ++n) {
+    rc = fwd_step(h, n, h->st[cur], h->st[cur ^ 1], wav, d_dev ? drow(h, d_dev, n + 1) : nullptr,
+                  nullptr, s);
+    if (rc) return rc;
+    cur ^= 1;
+  }
+  return AEW_OK;
+}
+
+int aew_propagate(aew_handle* h, const float* c_dev, float* const state_dev[4], int n0,
+                  int nsteps, const float* wavelet_host, float* d_dev, void* stream) {
+  if (!h || !state_dev || nsteps < 0) return AEW_E_ARG;
+  for (int i = 0; i < 4; ++i)
+    if (!state_dev[i]) return fail(h, AEW_E_ARG, "state pointer is NULL");
+  h->err.clear();
+  cudaStream_t s = S(stream);
+  int rc = prepare_c(h, c_dev, s);
+  if (rc) return rc;
+  h->have_grad = false;
+  if (d_dev && h->nrow) AEW_CK(cudaMemsetAsync(d_dev, 0, h->nrow * sizeof(float), s));
+  float* tmp[4] = {h->st[0][0], h->st[0][1], h->st[0][2], h->st[0][3]};
+  float* bufs[2][4] = {{state_dev[0], state_dev[1], state_dev[2], state_dev[3]},
+                       {tmp[0], tmp[1], tmp[2], tmp[3]}};
+  std::vector<float> w(wavelet_host ? (size_t)nsteps + (size_t)n0 : 0, 0.f);
+  for (int k = 0; wavelet_host && k < nsteps; ++k) w[(size_t)n0 + k] = wavelet_host[k];
+  int cur = 0;
+  for (int k = 0; k < nsteps; ++k) {
+    rc = fwd_step(h, n0 + k, bufs[cur], bufs[cur ^ 1], wavelet_host ? w.data() : nullptr,
+                  d_dev ? drow(h, d_dev, k + 1) : nullptr, nullptr, s);
+    if (rc) return rc;
+    cur ^= 1;
+  }
+  if (cur == 1) {
+    if ((rc = copy_state(h, bufs[0], bufs[1], s))) return rc;
+  }
+  return AEW_OK;
+}
+
+int aew_gradient(aew_handle* h, const float* c_dev, const float* d_obs_dev, float* g_dev,
+                 double* misfit_host, void* stream) {
+  if (!h) return AEW_E_ARG;
+  if (!d_obs_dev && h->nrow) return fail(h, AEW_E_ARG, "d_obs is NULL");
+  if (!g_dev) return fail(h, AEW_E_ARG, "g is NULL");
+  h->err.clear();
+  cudaStream_t s = S(stream);
+  h->have_grad = false;
+  if (h->cfg.storage == AEW_AE && !aew::codec_ready(h->codec))
+    return fail(h, AEW_E_NOCODEC, "AE storage needs codec weights (aew_codec_set)");
+  int rc = prepare_c(h, c_dev, s);
+  if (rc) return rc;
+  const float* wav = h->wav.data();
+  if (h->cfg.storage == AEW_FULL) {
+    rc = gradient_full(h, d_obs_dev, wav, s);
+  } else if (h->cfg.storage == AEW_REVOLVE) {
+    long long fwd = 0;
+    rc = run_revolve(h, d_obs_dev, nullptr, wav, true, s, &fwd);
+    h->stats.forward_steps = fwd;
+    h->stats.adjoint_steps = h->cfg.nt;
+  } else {
+    rc = gradient_ae(h, d_obs_dev, wav, s);
+  }
+  if (rc) return rc;
+  AEW_CK(aew::launch_finalize_grad(h->c, h->acc64, g_dev, h->C, s));
+  ++h->stats.kernel_launches;
+  if (misfit_host || h->cfg.storage == AEW_AE) {
+    double J = 0.0;
+    int ovf = 0;
+    AEW_CK(cudaMemcpyAsync(&J, h->part + aew::kRedBlocks, sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (h->cfg.storage == AEW_AE)
+      AEW_CK(cudaMemcpyAsync(&ovf, h->ovf, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AEW_CK(cudaStreamSynchronize(s));
+    h->stats.last_misfit = J;
+    h->stats.latent_overflow = ovf;
+    if (misfit_host) *misfit_host = J;
+    if (ovf) return fail(h, AEW_E_OVERFLOW, "a latent overflowed FP16 during encoding");
+  }
+  h->have_grad = true;
+  return AEW_OK;
+}
+
+// incremental forward at the stored c: dd = J_F dc  (dm must be prepared)
+static int incremental_forward(aew_handle* h, float* dd_out, cudaStream_t s, long long* fwd) {
+  const int nt = h->cfg.nt;
+  int rc;
+  // incremental state in ad[] buffers (free until the incremental adjoint)
+  if ((rc = zero_state(h, h->ad[0], s))) return rc;
+  if (h->nrow) AEW_CK(cudaMemsetAsync(dd_out, 0, h->nrow * sizeof(float), s));
+  int cur = 0, fcur = 0;
+  *fwd = 0;
+  if (h->cfg.storage == AEW_REVOLVE && (rc = zero_state(h, h->st[0], s))) return rc;
+  for (int n = 0; n < nt; ++n) {
+    const float* en = nullptr;
+    if (n > 0) {
+      if (h->cfg.storage == AEW_FULL) {
+        en = h->estore + (size_t)n * h->C;
+      } else if (h->cfg.storage == AEW_AE) {
+        if ((rc = decode_e(h, n, s))) return rc;
+        en = h->edec;
+      }
+    }
+    if (h->cfg.storage == AEW_REVOLVE) {
+      if (n > 0) {  // lockstep forward recompute: state n from state n-1
+        rc = fwd_step(h, n - 1, h->st[fcur], h->st[fcur ^ 1], h->wav.data(), nullptr, nullptr, s);
+        if (rc) return rc;
+        fcur ^= 1;
+        ++*fwd;
+        en = h->st[fcur][0];
+      }
+    }
+    if ((rc = incr_step(h, h->ad[cur], h->ad[cur ^ 1], en, drow(h, dd_out, n + 1), s))) return rc;
+    cur ^= 1;
+    ++*fwd;
+  }
+  return AEW_OK;
+}
+
+static int prepare_dc(aew_handle* h, const float* dc_dev, cudaStream_t s) {
+  if (!dc_dev) return fail(h, AEW_E_ARG, "dc is NULL");
+  if (!h->have_grad)
+    return fail(h, AEW_E_NOGRADIENT, "no forward history: call aew_gradient first");
+  AEW_CK(cudaMemsetAsync(h->chk, 0, sizeof(aew::FieldCheck), s));
+  AEW_CK(aew::launch_prep_dm(h->c, dc_dev, h->dm, h->C, h->chk, s));
+  ++h->stats.kernel_launches;
+  aew::FieldCheck ck{};
+  AEW_CK(cudaMemcpyAsync(&ck, h->chk, sizeof(ck), cudaMemcpyDeviceToHost, s));
+  AEW_CK(cudaStreamSynchronize(s));
+  if (ck.nonfinite) return fail(h, AEW_E_NONFINITE, "dc contains NaN or Inf");
+  return AEW_OK;
+}
+
+int aew_jvp(aew_handle* h, const float* dc_dev, float* dd_dev, void* stream) {
+  if (!h) return AEW_E_ARG;
+  if (!dd_dev && h->nrow) return fail(h, AEW_E_ARG, "dd is NULL");
+  h->err.clear();
+  cudaStream_t s = S(stream);
+  int rc = prepare_dc(h, dc_dev, s);
+  if (rc) return rc;
+  long long fwd = 0;
+  return incremental_forward(h, dd_dev, s, &fwd);
+}
+
+int aew_hessvec(aew_handle* h, const float* dc_dev, float* hdc_dev, void* stream) {
+  if (!h) return AEW_E_ARG;
+  if (!hdc_dev) return fail(h, AEW_E_ARG, "hdc is NULL");
+  h->err.clear();
+  cudaStream_t s = S(stream);
+  int rc = prepare_dc(h, dc_dev, s);
+  if (rc) return rc;
+  long long fwd = 0;
+  if ((rc = incremental_forward(h, h->dd, s, &fwd))) return rc;
+  // incremental adjoint: the adjoint solve with residual dd (row 0 unused)
+  const int nt = h->cfg.nt;
+  if (h->cfg.storage == AEW_REVOLVE) {
+    long long f2 = 0;
+    if ((rc = run_revolve(h, nullptr, h->dd, h->wav.data(), false, s, &f2))) return rc;
+    fwd += f2;
+  } else {
+    if ((rc = begin_adjoint(h, s))) return rc;
+    int acur = 0;
+    for (int n = nt - 1; n >= 0; --n) {
+      const float* en = nullptr;
+      if (n > 0) {
+        if (h->cfg.storage == AEW_FULL) {
+          en = h->estore + (size_t)n * h->C;
+        } else {
+          if ((rc = decode_e(h, n, s))) return rc;
+          en = h->edec;
+        }
+      }
+      if ((rc = adj_step(h, n, acur, h->dd, en, s))) return rc;
+      acur ^= 1;
+    }
+  }
+  h->stats.hvp_forward_steps = fwd;
+  AEW_CK(aew::launch_finalize_grad(h->c, h->acc64, hdc_dev, h->C, s));
+  ++h->stats.kernel_launches;
+  return AEW_OK;
+}
+
+int aew_dot(const float* a_dev, const float* b_dev, size_t n, double* out_host, void* stream) {
+  if (!a_dev || !b_dev || !out_host) return AEW_E_ARG;
+  cudaStream_t s = S(stream);
+  double* part = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&part), (aew::kRedBlocks + 1) * sizeof(double), s) !=
+      cudaSuccess)
+    return AEW_E_NOMEM;
+  int rc = AEW_OK;
+  if (aew::launch_dot_partials(a_dev, b_dev, n, part, aew::kRedBlocks, s) != cudaSuccess ||
+      aew::launch_sum_partials(part, aew::kRedBlocks, 1.0, part + aew::kRedBlocks, s) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(out_host, part + aew::kRedBlocks, sizeof(double), cudaMemcpyDeviceToHost,
+                      s) != cudaSuccess)
+    rc = AEW_E_CUDA;
+  cudaFreeAsync(part, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) rc = AEW_E_CUDA;
+  return rc;
+}
+
+int aew_revolve_plan(int nt, int s, int* ops, int* args, long long cap, long long* n_ops,
+                     long long* fwd_steps) {
+  if (nt < 1 || s < 0 || !n_ops || !fwd_steps) return AEW_E_ARG;
+  std::vector<aew::RevAction> plan;
+  const long long f = aew::revolve_plan(nt, s, plan);
+  if (f < 0) return AEW_E_ARG;
+  *n_ops = (long long)plan.size();
+  *fwd_steps = f;
+  for (long long i = 0; i < (long long)plan.size() && i < cap; ++i) {
+    if (ops) ops[i] = plan[i].op;
+    if (args) args[i] = plan[i].arg;
+  }
+  return AEW_OK;
+}
+
+// ------------------------------------------------------------------------------ codec
+int aew_codec_set(aew_handle* h, const float* W1, const float* b1, const float* W2,
+                  const float* b2, const float* W3, const float* b3, const float* W4,
+                  const float* b4) {
+  if (!h) return AEW_E_ARG;
+  const float* w[8] = {W1, b1, W2, b2, W3, b3, W4, b4};
+  for (const float* p : w)
+    if (!p) return fail(h, AEW_E_ARG, "weight pointer is NULL");
+  cudaError_t e = aew::codec_set_weights(h->codec, w);
+  if (e != cudaSuccess) return cuda_fail(h, e, "codec_set_weights");
+  return AEW_OK;
+}
+
+int aew_codec_get(const aew_handle* h, float* W1, float* b1, float* W2, float* b2, float* W3,
+                  float* b3, float* W4, float* b4) {
+  if (!h) return AEW_E_ARG;
+  float* w[8] = {W1, b1, W2, b2, W3, b3, W4, b4};
+  for (float* p : w)
+    if (!p) return AEW_E_ARG;
+  if (!aew::codec_ready(h->codec)) return AEW_E_NOCODEC;
+  return aew::codec_get_weights(h->codec, w) == cudaSuccess ? AEW_OK : AEW_E_CUDA;
+}
+
+int aew_codec_encode(aew_handle* h, const float* const fields_dev[4], const float* scale_host,
+                     uint16_t* latents_dev, void* stream) {
+  if (!h) return AEW_E_ARG;
+  if (!fields_dev || !scale_host || !latents_dev) return fail(h, AEW_E_ARG, "NULL argument");
+  if (h->cfg.nx % 8 || h->cfg.ny % 8 || h->cfg.nz % 8)
+    return fail(h, AEW_E_CONFIG, "codec needs nx, ny, nz multiples of 8");
+  if (!aew::codec_ready(h->codec)) return fail(h, AEW_E_NOCODEC, "codec weights not set");
+  h->err.clear();
+  cudaStream_t s = S(stream);
+  AEW_CK(cudaMemcpyAsync(h->scale_tmp, scale_host, 4 * sizeof(float), cudaMemcpyHostToDevice, s));
+  AEW_CK(cudaMemsetAsync(h->scale_tmp + 4, 0, sizeof(int), s));
+  const float* f[4] = {fields_dev[0], fields_dev[1], fields_dev[2], fields_dev[3]};
+  cudaError_t e = aew::codec_encode_grid(h->codec, f, h->cfg.nx, h->cfg.ny, h->cfg.nz,
+                                         h->scale_tmp, nullptr, nullptr, latents_dev,
+                                         reinterpret_cast<int*>(h->scale_tmp + 4), s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "codec_encode_grid");
+  int ovf = 0;
+  AEW_CK(cudaMemcpyAsync(&ovf, h->scale_tmp + 4, sizeof(int), cudaMemcpyDeviceToHost, s));
+  AEW_CK(cudaStreamSynchronize(s));
+  if (ovf) return fail(h, AEW_E_OVERFLOW, "a latent overflowed FP16");
+  return AEW_OK;
+}
+
+int aew_codec_decode(aew_handle* h, const uint16_t* latents_dev, float* out_dev, void* stream) {
+  if (!h) return AEW_E_ARG;
+  if (!latents_dev || !out_dev) return fail(h, AEW_E_ARG, "NULL argument");
+  if (h->cfg.nx % 8 || h->cfg.ny % 8 || h->cfg.nz % 8)
+    return fail(h, AEW_E_CONFIG, "codec needs nx, ny, nz multiples of 8");
+  if (!aew::codec_ready(h->codec)) return fail(h, AEW_E_NOCODEC, "codec weights not set");
+  h->err.clear();
+  cudaError_t e =
+      aew::codec_decode_vectors(h->codec, latents_dev, (long long)nblocks_of(h), out_dev, S(stream));
+  if (e != cudaSuccess) return cuda_fail(h, e, "codec_decode_vectors");
+  return AEW_OK;
+}
+
+int aew_codec_decode_e(aew_handle* h, const uint16_t* latents_dev, float scale_e, float* e_dev,
+                       void* stream) {
+  if (!h) return AEW_E_ARG;
+  if (!latents_dev || !e_dev) return fail(h, AEW_E_ARG, "NULL argument");
+  if (h->cfg.nx % 8 || h->cfg.ny % 8 || h->cfg.nz % 8)
+    return fail(h, AEW_E_CONFIG, "codec needs nx, ny, nz multiples of 8");
+  if (!aew::codec_ready(h->codec)) return fail(h, AEW_E_NOCODEC, "codec weights not set");
+  h->err.clear();
+  cudaStream_t s = S(stream);
+  AEW_CK(cudaMemcpyAsync(h->scale_tmp, &scale_e, sizeof(float), cudaMemcpyHostToDevice, s));
+  cudaError_t e = aew::codec_decode_grid_e(h->codec, latents_dev, h->cfg.nx, h->cfg.ny,
+                                           h->cfg.nz, h->scale_tmp, e_dev, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "codec_decode_grid_e");
+  AEW_CK(cudaStreamSynchronize(s));
+  return AEW_OK;
+}
+
+int aew_snapshots(aew_handle* h, const float* c_dev, int every, uint16_t* out_dev,
+                  long long max_vectors, long long* n_written, void* stream) {
+  if (!h) return AEW_E_ARG;
+  if (!out_dev || !n_written || every < 1 || max_vectors < 0)
+    return fail(h, AEW_E_ARG, "bad argument");
+  if (h->cfg.nx % 8 || h->cfg.ny % 8 || h->cfg.nz % 8)
+    return fail(h, AEW_E_CONFIG, "snapshots need nx, ny, nz multiples of 8");
+  h->err.clear();
+  cudaStream_t s = S(stream);
+  int rc = prepare_c(h, c_dev, s);
+  if (rc) return rc;
+  h->have_grad = false;
+  const size_t nb = nblocks_of(h);
+  // running maxima in the first 8 floats of the partials buffer
+  unsigned* amax = reinterpret_cast<unsigned*>(h->part);
+  float* scale = reinterpret_cast<float*>(h->part) + 4;
+  AEW_CK(cudaMemsetAsync(h->part, 0, 8 * sizeof(float), s));
+  if ((rc = zero_state(h, h->st[0], s))) return rc;
+  int cur = 0;
+  long long written = 0;
+  for (int n = 0; n + 1 < h->cfg.nt; ++n) {
+    if ((rc = fwd_step(h, n, h->st[cur], h->st[cur ^ 1], h->wav.data(), nullptr, amax, s)))
+      return rc;
+    cur ^= 1;
+    const int step = n + 1;
+    if (step % every == 0 && written + (long long)nb <= max_vectors) {
+      AEW_CK(cudaMemcpyAsync(scale, amax, 4 * sizeof(float), cudaMemcpyDeviceToDevice, s));
+      const float* f[4] = {h->st[cur][0], h->st[cur][1], h->st[cur][2], h->st[cur][3]};
+      AEW_CK(aew::snapshot_pack(f, h->cfg.nx, h->cfg.ny, h->cfg.nz, scale,
+                                out_dev + (size_t)written * aew::kNIn, s));
+      written += (long long)nb;
+    }
+  }
+  AEW_CK(cudaStreamSynchronize(s));
+  *n_written = written;
+  return AEW_OK;
+}
+
+int aew_codec_train_step(aew_handle* h, const uint16_t* batch_dev, int batch, float lr,
+                         float* loss_host, void* stream) {
+  if (!h) return AEW_E_ARG;
+  if (!batch_dev || batch < 1) return fail(h, AEW_E_ARG, "bad batch");
+  if (!aew::codec_ready(h->codec)) return fail(h, AEW_E_NOCODEC, "codec weights not set");
+  h->err.clear();
+  cudaStream_t s = S(stream);
+  float* loss_dev = h->scale_tmp;
+  cudaError_t e = aew::codec_train_step(h->codec, batch_dev, batch, lr, loss_dev, s, &h->err);
+  if (e != cudaSuccess) return cuda_fail(h, e, "codec_train_step");
+  if (loss_host) {
+    AEW_CK(cudaMemcpyAsync(loss_host, loss_dev, sizeof(float), cudaMemcpyDeviceToHost, s));
+    AEW_CK(cudaStreamSynchronize(s));
+  }
+  return AEW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,417 @@
+// Per-block autoencoder codec on tcgen05 tensor cores (compression in space, Sec. 3.1;
+// dense layers sigma(y W + b) of Eq. (5), Sec. 3.3), plus the snapshot packing of
+// Algorithm 1.
+//
+// Block vector of an 8x8x8-node block: k = z*256 + f*64 + y*8 + x (f = e, vx, vy, vz);
+// block b = (bz*NBy + by)*NBx + bx.  Each field is divided by its scale s_f (the
+// running maximum of |f|).
+//
+// Encoder: A = normalised block vectors gathered straight from the four FP32 grid
+// fields (BF16, RNE), times W1 (2048 x 512) -> +b1, GELU -> H (BF16), times W2
+// (512 x n_lat) -> +b2 -> FP16 latent.  Decoder: latent (FP16) times W3 (FP16,
+// n_lat x 512) -> +b3, GELU -> H (BF16), times W4 (BF16, 512 x 2048, or only its 512
+// strain columns inside the adjoint) -> +b4, times s_e, scattered back to the grid.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cstring>
+#include <vector>
+
+#include "aew_codec.cuh"
+#include "aew_codec_state.cuh"
+#include "aew_gemm.cuh"
+
+namespace aew {
+
+
+namespace {
+
+__global__ void transpose_to16_kernel(const float* __restrict__ src, int rows, int cols,
+                                      uint16_t* __restrict__ dst, int fp16) {
+  // dst[c][r] = round(src[r][c])
+  __shared__ float tile[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    tile[i][threadIdx.x] = (r < rows && c < cols) ? src[(size_t)r * cols + c] : 0.f;
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (c < cols && r < rows) {
+      const float v = tile[threadIdx.x][i];
+      uint16_t b;
+      if (fp16) {
+        __half hv = __float2half_rn(v);
+        b = *reinterpret_cast<uint16_t*>(&hv);
+      } else {
+        b = gemm::bf16_bits(v);
+      }
+      dst[(size_t)c * rows + r] = b;
+    }
+  }
+}
+
+cudaError_t transpose16(const float* src, int rows, int cols, uint16_t* dst, bool fp16,
+                        cudaStream_t s) {
+  dim3 grid((cols + 31) / 32, (rows + 31) / 32), block(32, 8);
+  transpose_to16_kernel<<<grid, block, 0, s>>>(src, rows, cols, dst, fp16 ? 1 : 0);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
+// Encoder A-operand: block vectors gathered from the grid, normalised, BF16.
+// ---------------------------------------------------------------------------------
+struct LdGrid {
+  const float* f0;
+  const float* f1;
+  const float* f2;
+  const float* f3;
+  int nx, ny, NBx, NBy;
+  long long nblk;
+  const float* sprev;
+  const unsigned* amax;
+  template <int NROWS>
+  __device__ __forceinline__ void load(uint8_t* tile, long long r0, int k0, int tid) const {
+    static_assert(NROWS == gemm::kBM, "A tile");
+    const int c = k0 >> 6, z = c >> 2, fi = c & 3;
+    const float* src = fi == 0 ? f0 : (fi == 1 ? f1 : (fi == 2 ? f2 : f3));
+    float sc = 0.f;
+    if (sprev) sc = __ldg(sprev + fi);
+    if (amax) sc = fmaxf(sc, __uint_as_float(__ldg(amax + fi)));
+    const int r = tid >> 1, half = tid & 1;
+    const long long b = r0 + r;
+    float4 v[8];
+    if (b < nblk) {
+      const long long bx = b % NBx, t = b / NBx;
+      const long long by = t % NBy, bz = t / NBy;
+      const size_t base =
+          ((size_t)(8 * bz + z) * ny + (size_t)(8 * by)) * nx + (size_t)(8 * bx) + 4 * half;
+#pragma unroll
+      for (int y = 0; y < 8; ++y)
+        v[y] = __ldg(reinterpret_cast<const float4*>(src + base + (size_t)y * nx));
+    } else {
+#pragma unroll
+      for (int y = 0; y < 8; ++y) v[y] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const bool live = sc > 0.f;
+#pragma unroll
+    for (int y = 0; y < 8; ++y) {
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+      if (live) {
+        a0 = __fdiv_rn(v[y].x, sc);
+        a1 = __fdiv_rn(v[y].y, sc);
+        a2 = __fdiv_rn(v[y].z, sc);
+        a3 = __fdiv_rn(v[y].w, sc);
+      }
+      uint2 p = make_uint2(gemm::pack_bf16(a0, a1), gemm::pack_bf16(a2, a3));
+      *reinterpret_cast<uint2*>(tile + (r >> 3) * 1024 + y * 128 + (r & 7) * 16 + half * 8) = p;
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------------
+// Epilogues
+// ---------------------------------------------------------------------------------
+// H[row][col..] = bf16(gelu(acc + bias))
+struct EpBiasGeluH {
+  const float* bias;
+  uint16_t* H;
+  long long M;
+  __device__ __forceinline__ void operator()(long long row, int col, const float (&v)[32]) const {
+    if (row >= M) return;
+    uint32_t pk[16];
+#pragma unroll
+    for (int j = 0; j < 32; j += 2) {
+      const float a0 = v[j] + __ldg(bias + col + j), a1 = v[j + 1] + __ldg(bias + col + j + 1);
+      pk[j / 2] = gemm::pack_bf16(gemm::gelu_f(a0), gemm::gelu_f(a1));
+    }
+    uint4* dst = reinterpret_cast<uint4*>(H + row * kNHid + col);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+  }
+};
+
+// latent = fp16(acc + bias), flag overflow
+struct EpLatent {
+  const float* bias;
+  uint16_t* lat;
+  int nl;
+  long long M;
+  int* ovf;
+  __device__ __forceinline__ void operator()(long long row, int col, const float (&v)[32]) const {
+    if (row >= M || col >= nl) return;
+    uint32_t pk[16];
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < 32; j += 2) {
+      const float a0 = v[j] + __ldg(bias + col + j), a1 = v[j + 1] + __ldg(bias + col + j + 1);
+      const __half2 hv = __floats2half2_rn(a0, a1);
+      bad |= !(fabsf(a0) <= 65504.f) || !(fabsf(a1) <= 65504.f);
+      pk[j / 2] = *reinterpret_cast<const uint32_t*>(&hv);
+    }
+    if (bad) atomicOr(ovf, 1);
+    uint4* dst = reinterpret_cast<uint4*>(lat + row * nl + col);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+  }
+};
+
+// strain part of the decoder output, scattered to the grid:
+// column n = z*64 + y*8 + x of block row -> node (8bz+z, 8by+y, 8bx+x);
+// e = (acc + b4[z*256 + y*8 + x]) * s_e, 0 on boundary nodes
+struct EpDecGrid {
+  const float* b4;
+  const float* scale_e;
+  float* e;
+  int nx, ny, nz, NBx, NBy;
+  long long M;
+  __device__ __forceinline__ void operator()(long long row, int col, const float (&v)[32]) const {
+    if (row >= M) return;
+    const float s = __ldg(scale_e);
+    const long long bx = row % NBx, t = row / NBx;
+    const long long by = t % NBy, bz = t / NBy;
+    const int z = col >> 6, y0 = (col & 63) >> 3;
+    const int kz = (int)(8 * bz) + z;
+    const bool zb = (kz == 0 || kz == nz - 1);
+#pragma unroll
+    for (int yy = 0; yy < 4; ++yy) {
+      const int jy = (int)(8 * by) + y0 + yy;
+      const bool yb = zb || jy == 0 || jy == ny - 1;
+      float o[8];
+#pragma unroll
+      for (int x = 0; x < 8; ++x) {
+        const int ix = (int)(8 * bx) + x;
+        const float bv = __ldg(b4 + z * 256 + (y0 + yy) * 8 + x);
+        const float val = (v[yy * 8 + x] + bv) * s;
+        o[x] = (yb || ix == 0 || ix == nx - 1) ? 0.f : val;
+      }
+      float4* dst = reinterpret_cast<float4*>(e + ((size_t)kz * ny + jy) * nx + 8 * bx);
+      dst[0] = make_float4(o[0], o[1], o[2], o[3]);
+      dst[1] = make_float4(o[4], o[5], o[6], o[7]);
+    }
+  }
+};
+
+// out[row][col..] = acc + bias (FP32 vectors)
+struct EpVec {
+  const float* bias;
+  float* out;
+  long long ld;
+  long long M;
+  __device__ __forceinline__ void operator()(long long row, int col, const float (&v)[32]) const {
+    if (row >= M) return;
+    float4* dst = reinterpret_cast<float4*>(out + row * ld + col);
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      dst[q] = make_float4(v[4 * q] + __ldg(bias + col + 4 * q), v[4 * q + 1] + __ldg(bias + col + 4 * q + 1),
+                           v[4 * q + 2] + __ldg(bias + col + 4 * q + 2), v[4 * q + 3] + __ldg(bias + col + 4 * q + 3));
+  }
+};
+
+// rows of W4t holding the strain outputs: e-output n = z*64 + j -> vector index z*256 + j
+struct RowsStrain {
+  __device__ __forceinline__ long long operator()(long long r) const {
+    return ((r >> 6) * 256 + (r & 63)) * (long long)kNHid;
+  }
+};
+
+using LdKLin = gemm::LdK16<gemm::RowsLinear>;
+
+bool ensure_H(Codec* c, size_t rows) {
+  if (c->H_rows >= rows) return true;
+  if (c->H) cudaFree(c->H);
+  c->H = nullptr;
+  c->H_rows = 0;
+  if (cudaMalloc(&c->H, rows * kNHid * sizeof(uint16_t)) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  c->H_rows = rows;
+  return true;
+}
+
+// ---------------------------------------------------------------------------------
+// Algorithm 1 packing: BF16 normalised block vectors
+// ---------------------------------------------------------------------------------
+__global__ void snapshot_pack_kernel(const float* f0, const float* f1, const float* f2,
+                                     const float* f3, int nx, int ny, int NBx, int NBy,
+                                     long long nblk, const float* scale, uint16_t* out) {
+  // one thread per (block, z, f, y): 8 values
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= nblk * 256) return;
+  const int y = (int)(t & 7), f = (int)((t >> 3) & 3), z = (int)((t >> 5) & 7);
+  const long long b = t >> 8;
+  const float* src = f == 0 ? f0 : (f == 1 ? f1 : (f == 2 ? f2 : f3));
+  const float sc = scale[f];
+  const long long bx = b % NBx, r = b / NBx;
+  const long long by = r % NBy, bz = r / NBy;
+  const size_t base = ((size_t)(8 * bz + z) * ny + (size_t)(8 * by + y)) * nx + (size_t)(8 * bx);
+  const float4 a = *reinterpret_cast<const float4*>(src + base);
+  const float4 c = *reinterpret_cast<const float4*>(src + base + 4);
+  float q[8] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w};
+  uint32_t pk[4];
+#pragma unroll
+  for (int i = 0; i < 8; i += 2) {
+    const float u0 = sc > 0.f ? __fdiv_rn(q[i], sc) : 0.f;
+    const float u1 = sc > 0.f ? __fdiv_rn(q[i + 1], sc) : 0.f;
+    pk[i / 2] = gemm::pack_bf16(u0, u1);
+  }
+  *reinterpret_cast<uint4*>(out + b * kNIn + z * 256 + f * 64 + y * 8) =
+      make_uint4(pk[0], pk[1], pk[2], pk[3]);
+}
+
+__global__ void update_scale_kernel(const float* p, const unsigned* a, float* o) {
+  const int i = threadIdx.x;
+  float v = p ? p[i] : 0.f;
+  if (a) v = fmaxf(v, __uint_as_float(a[i]));
+  o[i] = v;
+}
+
+}  // namespace
+
+// =================================================================================
+Codec* codec_new(int n_lat) {
+  Codec* c = new Codec();
+  c->n_lat = n_lat;
+  const size_t nl = (size_t)n_lat;
+  const size_t sz[8] = {(size_t)kNIn * kNHid, kNHid, kNHid * nl, nl, nl * kNHid, kNHid,
+                        (size_t)kNHid * kNIn, kNIn};
+  bool ok = true;
+  for (int i = 0; i < 8 && ok; ++i) {
+    c->wn[i] = sz[i];
+    ok = cudaMalloc(&c->w[i], sz[i] * sizeof(float)) == cudaSuccess;
+    c->bytes += sz[i] * sizeof(float);
+  }
+  ok = ok && cudaMalloc(&c->W1t, (size_t)kNIn * kNHid * 2) == cudaSuccess &&
+       cudaMalloc(&c->W2t, nl * kNHid * 2) == cudaSuccess &&
+       cudaMalloc(&c->W3t, nl * kNHid * 2) == cudaSuccess &&
+       cudaMalloc(&c->W4t, (size_t)kNIn * kNHid * 2) == cudaSuccess &&
+       cudaMalloc(&c->err, sizeof(int)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    codec_free(c);
+    return nullptr;
+  }
+  cudaMemset(c->err, 0, sizeof(int));
+  c->bytes += ((size_t)2 * kNIn * kNHid + 2 * nl * kNHid) * 2;
+  return c;
+}
+
+void codec_free(Codec* c) {
+  if (!c) return;
+  for (float* p : c->w) cudaFree(p);
+  cudaFree(c->W1t);
+  cudaFree(c->W2t);
+  cudaFree(c->W3t);
+  cudaFree(c->W4t);
+  cudaFree(c->H);
+  cudaFree(c->err);
+  if (c->train) train_state_free(c->train);
+  delete c;
+}
+
+int codec_nlat(const Codec* c) { return c->n_lat; }
+size_t codec_device_bytes(const Codec* c) {
+  return c->bytes + c->H_rows * kNHid * 2 + (c->train ? train_state_bytes(c->train) : 0);
+}
+bool codec_ready(const Codec* c) { return c && c->ready; }
+
+// refresh the tensor-core operand copies from the FP32 masters
+cudaError_t codec_refresh(Codec* c, cudaStream_t s) {
+  const int nl = c->n_lat;
+  cudaError_t e;
+  if ((e = transpose16(c->w[0], kNIn, kNHid, c->W1t, false, s)) != cudaSuccess) return e;
+  if ((e = transpose16(c->w[2], kNHid, nl, c->W2t, false, s)) != cudaSuccess) return e;
+  if ((e = transpose16(c->w[4], nl, kNHid, c->W3t, true, s)) != cudaSuccess) return e;
+  return transpose16(c->w[6], kNHid, kNIn, c->W4t, false, s);
+}
+
+cudaError_t codec_set_weights(Codec* c, const float* const w[8]) {
+  for (int i = 0; i < 8; ++i) {
+    cudaError_t e = cudaMemcpy(c->w[i], w[i], c->wn[i] * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e = codec_refresh(c, 0);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamSynchronize(0);
+  if (e == cudaSuccess) c->ready = true;
+  return e;
+}
+
+cudaError_t codec_get_weights(const Codec* c, float* const w[8]) {
+  cudaError_t e = cudaDeviceSynchronize();
+  for (int i = 0; i < 8 && e == cudaSuccess; ++i)
+    e = cudaMemcpy(w[i], c->w[i], c->wn[i] * sizeof(float), cudaMemcpyDeviceToHost);
+  return e;
+}
+
+cudaError_t codec_encode_grid(Codec* c, const float* const f[4], int nx, int ny, int nz,
+                              const float* scale_prev, const unsigned* amax, float* scale_out,
+                              uint16_t* lat, int* overflow, cudaStream_t s) {
+  const int NBx = nx / 8, NBy = ny / 8, NBz = nz / 8;
+  const long long nb = (long long)NBx * NBy * NBz;
+  if (!ensure_H(c, (size_t)nb)) return cudaErrorMemoryAllocation;
+  LdGrid al{f[0], f[1], f[2], f[3], nx, ny, NBx, NBy, nb, scale_prev, amax};
+  LdKLin bl{c->W1t, gemm::RowsLinear{kNIn}, kNHid, kNIn};
+  EpBiasGeluH ep{c->w[1], c->H, nb};
+  cudaError_t e = gemm::launch<256, true>(nb, kNHid, kNIn, al, bl, ep, c->err, s);
+  if (e != cudaSuccess) return e;
+  if (scale_out) {
+    // s_f = max(prev, amax) for later decodes (same values the loader used)
+    update_scale_kernel<<<1, 4, 0, s>>>(scale_prev, amax, scale_out);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  const int nl = c->n_lat;
+  LdKLin a2{c->H, gemm::RowsLinear{kNHid}, nb, kNHid};
+  LdKLin b2{c->W2t, gemm::RowsLinear{kNHid}, nl, kNHid};
+  EpLatent e2{c->w[3], lat, nl, nb, overflow};
+  if (nl == 64)
+    e = gemm::launch<64, true>(nb, nl, kNHid, a2, b2, e2, c->err, s);
+  else
+    e = gemm::launch<32, true>(nb, nl, kNHid, a2, b2, e2, c->err, s);
+  return e;
+}
+
+static cudaError_t decode_hidden(Codec* c, const uint16_t* lat, long long nb, cudaStream_t s) {
+  if (!ensure_H(c, (size_t)nb)) return cudaErrorMemoryAllocation;
+  const int nl = c->n_lat;
+  LdKLin a1{lat, gemm::RowsLinear{nl}, nb, nl};
+  LdKLin b1{c->W3t, gemm::RowsLinear{nl}, kNHid, nl};
+  EpBiasGeluH ep{c->w[5], c->H, nb};
+  return gemm::launch<256, false>(nb, kNHid, nl, a1, b1, ep, c->err, s);
+}
+
+cudaError_t codec_decode_grid_e(Codec* c, const uint16_t* lat, int nx, int ny, int nz,
+                                const float* scale_e, float* e_out, cudaStream_t s) {
+  const int NBx = nx / 8, NBy = ny / 8, NBz = nz / 8;
+  const long long nb = (long long)NBx * NBy * NBz;
+  cudaError_t e = decode_hidden(c, lat, nb, s);
+  if (e != cudaSuccess) return e;
+  LdKLin a2{c->H, gemm::RowsLinear{kNHid}, nb, kNHid};
+  gemm::LdK16<RowsStrain> b2{c->W4t, RowsStrain{}, 512, kNHid};
+  EpDecGrid ep{c->w[7], scale_e, e_out, nx, ny, nz, NBx, NBy, nb};
+  return gemm::launch<256, true>(nb, 512, kNHid, a2, b2, ep, c->err, s);
+}
+
+cudaError_t codec_decode_vectors(Codec* c, const uint16_t* lat, long long nvec, float* out,
+                                 cudaStream_t s) {
+  cudaError_t e = decode_hidden(c, lat, nvec, s);
+  if (e != cudaSuccess) return e;
+  LdKLin a2{c->H, gemm::RowsLinear{kNHid}, nvec, kNHid};
+  LdKLin b2{c->W4t, gemm::RowsLinear{kNHid}, kNIn, kNHid};
+  EpVec ep{c->w[7], out, kNIn, nvec};
+  return gemm::launch<256, true>(nvec, kNIn, kNHid, a2, b2, ep, c->err, s);
+}
+
+cudaError_t snapshot_pack(const float* const f[4], int nx, int ny, int nz, const float* scale,
+                          uint16_t* out, cudaStream_t s) {
+  const int NBx = nx / 8, NBy = ny / 8, NBz = nz / 8;
+  const long long nb = (long long)NBx * NBy * NBz;
+  const long long threads = nb * 256;
+  snapshot_pack_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+      f[0], f[1], f[2], f[3], nx, ny, NBx, NBy, nb, scale, out);
+  return cudaGetLastError();
+}
+
+}  // namespace aew

@@ -1,0 +1,34 @@
+// Definition of the codec state shared by the codec and training translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+namespace aew {
+
+struct Codec {
+  int n_lat = 64;
+  bool ready = false;
+  // FP32 master weights: W1 [2048][512], b1, W2 [512][nl], b2, W3 [nl][512], b3,
+  // W4 [512][2048], b4
+  float* w[8] = {};
+  size_t wn[8] = {};
+  // operand copies (K-major rows): W1t [512][2048] bf16, W2t [nl][512] bf16,
+  // W3t [512][nl] fp16, W4t [2048][512] bf16
+  uint16_t* W1t = nullptr;
+  uint16_t* W2t = nullptr;
+  uint16_t* W3t = nullptr;
+  uint16_t* W4t = nullptr;
+  // workspace: hidden activations H [rows][512] bf16
+  uint16_t* H = nullptr;
+  size_t H_rows = 0;
+  int* err = nullptr;
+  size_t bytes = 0;
+  // training state (allocated by the training unit)
+  void* train = nullptr;
+};
+
+void train_state_free(void* t);
+size_t train_state_bytes(const void* t);
+
+}  // namespace aew

@@ -1,0 +1,105 @@
+// Internal declarations shared by the translation units of the aewave library.
+// Nothing here is part of the public C ABI (include/aewave.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+namespace aew {
+
+// x cells handled by one CTA row (32 lanes x float4)
+constexpr int kTXW = 128;
+
+// ------------------------------------------------------------------------------
+// Forward-type leapfrog step (forward solve and incremental forward solve).
+//   v' = v + dt/h (me[+1] - me) (+ dt s at the source z-face),
+//   e' = interior ? e + dt/h (div of v') : 0,
+// with me = m*e (forward) or m*e + dm*ef (incremental forward, no source).
+// ------------------------------------------------------------------------------
+struct FwdStep {
+  const float* m;
+  const float* e;
+  const float* vx;
+  const float* vy;
+  const float* vz;
+  float* e1;
+  float* vx1;
+  float* vy1;
+  float* vz1;
+  const float* dm;   // incremental only
+  const float* ef;   // incremental only: forward strain e^n
+  int nx, ny, nz;
+  int kc;            // z planes per CTA
+  float dth;         // dt / h
+  float dts;         // dt * s^n added to the source z-face
+  int si, sj, sk;    // source node (sk < 0: none)
+  int krec;          // receiver node plane (-1: none)
+  const int* rec_map;  // [ny][nx] receiver index or -1
+  float* d_out;        // receiver record row [nrec][3] (or null)
+  unsigned int* amax;  // [4] running |field| maxima of the new state (or null)
+};
+
+// ------------------------------------------------------------------------------
+// Adjoint step (reverse of one forward step) with gradient accumulation.
+//   lam' = lam + B^T r - dt/h (mu[+1] - mu),
+//   dtq  = interior ? -dt/h (div of lam') : 0          (= dt * G^T lam')
+//   mu'  = interior ? mu + m * dtq : 0,
+//   acc += e^n * dtq                                   (FP32 window, FP64 flush)
+// ------------------------------------------------------------------------------
+struct AdjStep {
+  const float* m;
+  const float* mu;
+  const float* lx;
+  const float* ly;
+  const float* lz;
+  float* mu1;
+  float* lx1;
+  float* ly1;
+  float* lz1;
+  const float* en;     // forward strain e^n (null: zero)
+  float* acc32;        // FP32 window accumulator
+  double* acc64;       // FP64 accumulator
+  int acc_mode;        // bit0: first step of a window, bit1: last step of a window
+  int nx, ny, nz;
+  int kc;
+  float dth;
+  int krec;
+  const int* rec_map;
+  const float* resid;  // residual row r^{n+1} [nrec][3] (or null)
+};
+
+enum { kAccFirst = 1, kAccLast = 2 };
+
+cudaError_t launch_fwd_step(const FwdStep& a, bool incremental, cudaStream_t s);
+cudaError_t launch_adj_step(const AdjStep& a, cudaStream_t s);
+int default_kc(int nx, int ny, int nz);
+
+// ------------------------------------------------------------------------------
+// Reductions and elementwise helpers (aew_reduce.cu)
+// ------------------------------------------------------------------------------
+struct FieldCheck {
+  unsigned int nonfinite;
+  unsigned int cmax_bits;   // max c as float bits (c >= 0 expected)
+  unsigned int cneg;        // count of c <= 0
+};
+// m = c^2 and checks; writes *chk (device)
+cudaError_t launch_prep_m(const float* c, float* m, size_t n, FieldCheck* chk, cudaStream_t s);
+// dm = 2 c dc and checks of dc
+cudaError_t launch_prep_dm(const float* c, const float* dc, float* dm, size_t n,
+                           FieldCheck* chk, cudaStream_t s);
+// r = d - d_obs (rows 1..nt; row 0 zero); FP64 partial sums of r^2 into part[nblk]
+cudaError_t launch_residual(const float* d, const float* dobs, float* r, size_t n_row0,
+                            size_t n, double* part, int nblk, cudaStream_t s);
+// FP64 partial dot products of a and b into part[nblk]
+cudaError_t launch_dot_partials(const float* a, const float* b, size_t n, double* part,
+                                int nblk, cudaStream_t s);
+// out[0] = scale * sum part[0..nblk)
+cudaError_t launch_sum_partials(const double* part, int nblk, double scale, double* out,
+                                cudaStream_t s);
+// g = 2 c acc64 (FP32 output)
+cudaError_t launch_finalize_grad(const float* c, const double* acc64, float* g, size_t n,
+                                 cudaStream_t s);
+constexpr int kRedBlocks = 1024;
+
+}  // namespace aew

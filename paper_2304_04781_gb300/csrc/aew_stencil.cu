@@ -1,0 +1,474 @@
+// Leapfrog stencil kernels for the velocity-strain acoustic system (Sec. 2, Eq. (1),
+// rho = 1) and its discrete adjoint.
+//
+// Layout: every field is an FP32 [nz][ny][nx] array (x fastest).  Each CTA owns a
+// 128 (x) x TY (y) column of nodes and marches through a chunk of kc z-planes
+// ("2.5-D" blocking).  A thread owns 4 consecutive x nodes, loaded and stored as one
+// 128-bit float4 (every row access of a warp is one contiguous 512-byte segment).
+// Neighbours along x come from the adjacent lane by warp shuffle, neighbours along y
+// from a shared-memory copy of the plane (with one halo row on each side and one halo
+// column for the warp edges), neighbours along z stay in registers from the previous
+// plane.  The next plane's inputs are loaded before the current plane is computed.
+//
+// One fused pass per time step: each thread computes the new face velocities of its
+// own nodes, takes the low-side faces from its x/y neighbours' results (recomputing
+// them only at CTA edges, with the identical expression, so results are bitwise
+// independent of the tiling), and then updates the strain of its nodes.  Algorithmic
+// HBM traffic of the forward step: 5 fields read + 4 written = 36 bytes per node.
+#include "aew_internal.cuh"
+
+namespace aew {
+namespace {
+
+constexpr int TY = 8;            // rows (warps) per CTA
+constexpr int NTHR = 32 * TY;
+constexpr int W4 = kTXW / 4;     // float4 per CTA row
+
+__device__ __forceinline__ float4 ld4(const float* p, size_t i) {
+  return __ldg(reinterpret_cast<const float4*>(p + i));
+}
+__device__ __forceinline__ void st4(float* p, size_t i, float4 v) {
+  *reinterpret_cast<float4*>(p + i) = v;
+}
+__device__ __forceinline__ float& comp(float4& v, int c) {
+  return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ float4 z4() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+
+// m e (+ dm ef) for one float4 of nodes whose strain e4 is already loaded
+template <bool INCR>
+__device__ __forceinline__ float4 me_of(const FwdStep& a, size_t i, float4 e4) {
+  float4 m4 = ld4(a.m, i);
+  float4 r = make_float4(m4.x * e4.x, m4.y * e4.y, m4.z * e4.z, m4.w * e4.w);
+  if (INCR) {
+    float4 d = ld4(a.dm, i), f = ld4(a.ef, i);
+    r.x = fmaf(d.x, f.x, r.x);
+    r.y = fmaf(d.y, f.y, r.y);
+    r.z = fmaf(d.z, f.z, r.z);
+    r.w = fmaf(d.w, f.w, r.w);
+  }
+  return r;
+}
+template <bool INCR>
+__device__ __forceinline__ float me_one(const FwdStep& a, size_t i) {
+  float r = __ldg(a.m + i) * __ldg(a.e + i);
+  if (INCR) r = fmaf(__ldg(a.dm + i), __ldg(a.ef + i), r);
+  return r;
+}
+// face update v' = v + dth (hi - lo)
+__device__ __forceinline__ float fupd(float dth, float hi, float lo, float v) {
+  return fmaf(dth, hi - lo, v);
+}
+__device__ __forceinline__ float4 fupd4(float dth, float4 hi, float4 lo, float4 v) {
+  return make_float4(fupd(dth, hi.x, lo.x, v.x), fupd(dth, hi.y, lo.y, v.y),
+                     fupd(dth, hi.z, lo.z, v.z), fupd(dth, hi.w, lo.w, v.w));
+}
+__device__ __forceinline__ float4 amax4(float4 a) {
+  return make_float4(fabsf(a.x), fabsf(a.y), fabsf(a.z), fabsf(a.w));
+}
+__device__ __forceinline__ float hmax4(float4 a) {
+  return fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w)));
+}
+
+// ---------------------------------------------------------------------------------
+// Forward-type step
+// ---------------------------------------------------------------------------------
+template <bool INCR, bool AMAX>
+__global__ void __launch_bounds__(NTHR) fwd_step_kernel(const FwdStep a) {
+  __shared__ float4 sme[2][TY + 2][W4 + 2];
+  __shared__ float4 svy[TY][W4];
+  __shared__ float sred[4][TY];
+
+  const int lane = threadIdx.x, ty = threadIdx.y;
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const int x0 = blockIdx.x * kTXW;
+  const int i0 = x0 + 4 * lane;
+  const int y = blockIdx.y * TY + ty;
+  const int kbeg = blockIdx.z * a.kc;
+  const int kend = min(kbeg + a.kc, nz);
+  const bool act = (i0 < nx) && (y < ny);
+  const size_t P = (size_t)nx * ny;
+  const size_t row = (size_t)y * nx + i0;
+  const float dth = a.dth;
+
+  float4 e_c = z4(), me_c = z4(), e_n = z4(), me_n = z4();
+  float4 vx_c = z4(), vy_c = z4(), vz_c = z4(), vzl = z4();
+  if (act) {
+    const size_t i = (size_t)kbeg * P + row;
+    e_c = ld4(a.e, i);
+    me_c = me_of<INCR>(a, i, e_c);
+    if (kbeg + 1 < nz) {
+      e_n = ld4(a.e, i + P);
+      me_n = me_of<INCR>(a, i + P, e_n);
+    }
+    vx_c = ld4(a.vx, i);
+    vy_c = ld4(a.vy, i);
+    vz_c = ld4(a.vz, i);
+    if (kbeg >= 1) {  // z-face below the chunk, recomputed exactly as its owner does
+      const float4 e_m = ld4(a.e, i - P);
+      const float4 me_m = me_of<INCR>(a, i - P, e_m);
+      vzl = fupd4(dth, me_c, me_m, ld4(a.vz, i - P));
+      if (kbeg - 1 == a.sk && y == a.sj) {
+        const int d = a.si - i0;
+        if (d >= 0 && d < 4) comp(vzl, d) += a.dts;
+      }
+    }
+  }
+  float mx_e = 0.f, mx_vx = 0.f, mx_vy = 0.f, mx_vz = 0.f;
+
+  for (int k = kbeg; k < kend; ++k) {
+    const int b = k & 1;
+    const size_t i = (size_t)k * P + row;
+    // inputs of the next plane, in flight while this plane is computed
+    float4 vx_x = z4(), vy_x = z4(), vz_x = z4(), e_x = z4(), me_x = z4();
+    if (act && k + 1 < kend) {
+      vx_x = ld4(a.vx, i + P);
+      vy_x = ld4(a.vy, i + P);
+      vz_x = ld4(a.vz, i + P);
+      if (k + 2 < nz) {
+        e_x = ld4(a.e, i + 2 * P);
+        me_x = me_of<INCR>(a, i + 2 * P, e_x);
+      }
+    }
+    // stage m e of this plane for the y neighbours and the warp-edge x neighbours
+    sme[b][ty + 1][lane + 1] = me_c;
+    if (ty == 0) {
+      float4 h = z4();
+      if (i0 < nx && y >= 1 && y <= ny) h = me_of<INCR>(a, i - nx, ld4(a.e, i - nx));
+      sme[b][0][lane + 1] = h;
+    }
+    if (ty == TY - 1) {
+      float4 h = z4();
+      if (i0 < nx && y + 1 < ny) h = me_of<INCR>(a, i + nx, ld4(a.e, i + nx));
+      sme[b][TY + 1][lane + 1] = h;
+    }
+    if (lane == 0) sme[b][ty + 1][0].w = (y < ny && x0 >= 1) ? me_one<INCR>(a, i - 1) : 0.f;
+    if (lane == 31) {
+      const size_t ih = (size_t)k * P + (size_t)y * nx + x0 + kTXW;
+      sme[b][ty + 1][W4 + 1].x = (y < ny && x0 + kTXW < nx) ? me_one<INCR>(a, ih) : 0.f;
+    }
+    __syncthreads();
+
+    // x-faces of the own nodes; the face x+3 -> x+4 takes m e from the next lane
+    float mx1 = __shfl_down_sync(0xffffffffu, me_c.x, 1);
+    if (lane == 31) mx1 = sme[b][ty + 1][W4 + 1].x;
+    float4 vx1;
+    vx1.x = fupd(dth, me_c.y, me_c.x, vx_c.x);
+    vx1.y = fupd(dth, me_c.z, me_c.y, vx_c.y);
+    vx1.z = fupd(dth, me_c.w, me_c.z, vx_c.z);
+    vx1.w = fupd(dth, mx1, me_c.w, vx_c.w);
+    if (i0 + 4 == nx) vx1.w = 0.f;  // unused last face
+    float vxl = __shfl_up_sync(0xffffffffu, vx1.w, 1);
+    if (lane == 0) {
+      vxl = 0.f;
+      if (act && i0 >= 1) vxl = fupd(dth, me_c.x, sme[b][ty + 1][0].w, __ldg(a.vx + i - 1));
+    }
+    // y-faces
+    float4 vy1 = fupd4(dth, sme[b][ty + 2][lane + 1], me_c, vy_c);
+    if (y == ny - 1) vy1 = z4();
+    svy[ty][lane] = vy1;
+    // z-faces
+    float4 vz1 = fupd4(dth, me_n, me_c, vz_c);
+    if (k == nz - 1) vz1 = z4();
+    if (k == a.sk && y == a.sj) {
+      const int d = a.si - i0;
+      if (d >= 0 && d < 4) comp(vz1, d) += a.dts;
+    }
+    __syncthreads();
+    float4 vyl;
+    if (ty > 0) {
+      vyl = svy[ty - 1][lane];
+    } else {
+      vyl = z4();
+      if (act && y >= 1) vyl = fupd4(dth, me_c, sme[b][0][lane + 1], ld4(a.vy, i - nx));
+    }
+    // strain update on interior nodes
+    float4 e1;
+    e1.x = fmaf(dth, ((vx1.x - vxl) + (vy1.x - vyl.x)) + (vz1.x - vzl.x), e_c.x);
+    e1.y = fmaf(dth, ((vx1.y - vx1.x) + (vy1.y - vyl.y)) + (vz1.y - vzl.y), e_c.y);
+    e1.z = fmaf(dth, ((vx1.z - vx1.y) + (vy1.z - vyl.z)) + (vz1.z - vzl.z), e_c.z);
+    e1.w = fmaf(dth, ((vx1.w - vx1.z) + (vy1.w - vyl.w)) + (vz1.w - vzl.w), e_c.w);
+    if (k == 0 || k == nz - 1 || y == 0 || y == ny - 1) {
+      e1 = z4();
+    } else {
+      if (i0 == 0) e1.x = 0.f;
+      if (i0 + 4 == nx) e1.w = 0.f;
+    }
+    if (act) {
+      st4(a.e1, i, e1);
+      st4(a.vx1, i, vx1);
+      st4(a.vy1, i, vy1);
+      st4(a.vz1, i, vz1);
+      if (k == a.krec && a.d_out) {
+        const int4 r = __ldg(reinterpret_cast<const int4*>(a.rec_map + (size_t)y * nx + i0));
+        const int rr[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          if (rr[c] >= 0) {
+            a.d_out[3 * rr[c] + 0] = comp(vx1, c);
+            a.d_out[3 * rr[c] + 1] = comp(vy1, c);
+            a.d_out[3 * rr[c] + 2] = comp(vz1, c);
+          }
+        }
+      }
+      if (AMAX) {
+        mx_e = fmaxf(mx_e, hmax4(e1));
+        mx_vx = fmaxf(mx_vx, hmax4(vx1));
+        mx_vy = fmaxf(mx_vy, hmax4(vy1));
+        mx_vz = fmaxf(mx_vz, hmax4(vz1));
+      }
+    }
+    vzl = vz1;
+    e_c = e_n;
+    me_c = me_n;
+    e_n = e_x;
+    me_n = me_x;
+    vx_c = vx_x;
+    vy_c = vy_x;
+    vz_c = vz_x;
+  }
+
+  if (AMAX) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mx_e = fmaxf(mx_e, __shfl_xor_sync(0xffffffffu, mx_e, o));
+      mx_vx = fmaxf(mx_vx, __shfl_xor_sync(0xffffffffu, mx_vx, o));
+      mx_vy = fmaxf(mx_vy, __shfl_xor_sync(0xffffffffu, mx_vy, o));
+      mx_vz = fmaxf(mx_vz, __shfl_xor_sync(0xffffffffu, mx_vz, o));
+    }
+    if (lane == 0) {
+      sred[0][ty] = mx_e;
+      sred[1][ty] = mx_vx;
+      sred[2][ty] = mx_vy;
+      sred[3][ty] = mx_vz;
+    }
+    __syncthreads();
+    if (ty == 0 && lane < 4) {
+      float v = 0.f;
+      for (int w = 0; w < TY; ++w) v = fmaxf(v, sred[lane][w]);
+      // non-negative floats order like their bit patterns
+      atomicMax(a.amax + lane, __float_as_uint(v));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Adjoint step
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ float inj_one(const AdjStep& a, int comp3, int x, int y, int k) {
+  if (k != a.krec || a.resid == nullptr) return 0.f;
+  const int r = __ldg(a.rec_map + (size_t)y * a.nx + x);
+  return r >= 0 ? __ldg(a.resid + 3 * r + comp3) : 0.f;
+}
+// add B^T r to the three face fields of a float4 of nodes on the receiver plane
+__device__ __forceinline__ void inj4(const AdjStep& a, int y, int i0, float4& lx, float4& ly,
+                                     float4& lz) {
+  const int4 r = __ldg(reinterpret_cast<const int4*>(a.rec_map + (size_t)y * a.nx + i0));
+  const int rr[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    if (rr[c] >= 0) {
+      comp(lx, c) += __ldg(a.resid + 3 * rr[c] + 0);
+      comp(ly, c) += __ldg(a.resid + 3 * rr[c] + 1);
+      comp(lz, c) += __ldg(a.resid + 3 * rr[c] + 2);
+    }
+  }
+}
+// lam' = (lam + inj) + dth (mu - mu_hi)
+__device__ __forceinline__ float lupd(float dth, float mu_hi, float mu, float l) {
+  return fmaf(dth, mu - mu_hi, l);
+}
+__device__ __forceinline__ float4 lupd4(float dth, float4 hi, float4 lo, float4 l) {
+  return make_float4(lupd(dth, hi.x, lo.x, l.x), lupd(dth, hi.y, lo.y, l.y),
+                     lupd(dth, hi.z, lo.z, l.z), lupd(dth, hi.w, lo.w, l.w));
+}
+
+__global__ void __launch_bounds__(NTHR) adj_step_kernel(const AdjStep a) {
+  __shared__ float4 smu[2][TY + 2][W4 + 2];
+  __shared__ float4 sly[TY][W4];
+
+  const int lane = threadIdx.x, ty = threadIdx.y;
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const int x0 = blockIdx.x * kTXW;
+  const int i0 = x0 + 4 * lane;
+  const int y = blockIdx.y * TY + ty;
+  const int kbeg = blockIdx.z * a.kc;
+  const int kend = min(kbeg + a.kc, nz);
+  const bool act = (i0 < nx) && (y < ny);
+  const size_t P = (size_t)nx * ny;
+  const size_t row = (size_t)y * nx + i0;
+  const float dth = a.dth;
+  const bool has_r = a.resid != nullptr && a.krec >= 0;
+
+  float4 mu_c = z4(), mu_n = z4(), lx_c = z4(), ly_c = z4(), lz_c = z4(), lzl = z4();
+  if (act) {
+    const size_t i = (size_t)kbeg * P + row;
+    mu_c = ld4(a.mu, i);
+    if (kbeg + 1 < nz) mu_n = ld4(a.mu, i + P);
+    lx_c = ld4(a.lx, i);
+    ly_c = ld4(a.ly, i);
+    lz_c = ld4(a.lz, i);
+    if (kbeg >= 1) {
+      float4 lzm = ld4(a.lz, i - P);
+      if (has_r && kbeg - 1 == a.krec) {
+        float4 dx = z4(), dy = z4();
+        inj4(a, y, i0, dx, dy, lzm);
+      }
+      lzl = lupd4(dth, mu_c, ld4(a.mu, i - P), lzm);
+    }
+  }
+
+  for (int k = kbeg; k < kend; ++k) {
+    const int b = k & 1;
+    const size_t i = (size_t)k * P + row;
+    float4 lx_x = z4(), ly_x = z4(), lz_x = z4(), mu_x = z4();
+    if (act && k + 1 < kend) {
+      lx_x = ld4(a.lx, i + P);
+      ly_x = ld4(a.ly, i + P);
+      lz_x = ld4(a.lz, i + P);
+      if (k + 2 < nz) mu_x = ld4(a.mu, i + 2 * P);
+    }
+    float4 m4 = z4(), en4 = z4();
+    if (act) {
+      m4 = ld4(a.m, i);
+      if (a.en) en4 = ld4(a.en, i);
+    }
+    const bool rplane = has_r && k == a.krec;
+    if (rplane && act) inj4(a, y, i0, lx_c, ly_c, lz_c);
+
+    smu[b][ty + 1][lane + 1] = mu_c;
+    if (ty == 0) smu[b][0][lane + 1] = (i0 < nx && y >= 1 && y <= ny) ? ld4(a.mu, i - nx) : z4();
+    if (ty == TY - 1) smu[b][TY + 1][lane + 1] = (i0 < nx && y + 1 < ny) ? ld4(a.mu, i + nx) : z4();
+    if (lane == 0) smu[b][ty + 1][0].w = (y < ny && x0 >= 1) ? __ldg(a.mu + i - 1) : 0.f;
+    if (lane == 31) {
+      const size_t ih = (size_t)k * P + (size_t)y * nx + x0 + kTXW;
+      smu[b][ty + 1][W4 + 1].x = (y < ny && x0 + kTXW < nx) ? __ldg(a.mu + ih) : 0.f;
+    }
+    __syncthreads();
+
+    float mx1 = __shfl_down_sync(0xffffffffu, mu_c.x, 1);
+    if (lane == 31) mx1 = smu[b][ty + 1][W4 + 1].x;
+    float4 lx1;
+    lx1.x = lupd(dth, mu_c.y, mu_c.x, lx_c.x);
+    lx1.y = lupd(dth, mu_c.z, mu_c.y, lx_c.y);
+    lx1.z = lupd(dth, mu_c.w, mu_c.z, lx_c.z);
+    lx1.w = lupd(dth, mx1, mu_c.w, lx_c.w);
+    if (i0 + 4 == nx) lx1.w = 0.f;
+    float lxl = __shfl_up_sync(0xffffffffu, lx1.w, 1);
+    if (lane == 0) {
+      lxl = 0.f;
+      if (act && i0 >= 1) {
+        float l = __ldg(a.lx + i - 1);
+        if (rplane) l += inj_one(a, 0, i0 - 1, y, k);
+        lxl = lupd(dth, mu_c.x, smu[b][ty + 1][0].w, l);
+      }
+    }
+    float4 ly1 = lupd4(dth, smu[b][ty + 2][lane + 1], mu_c, ly_c);
+    if (y == ny - 1) ly1 = z4();
+    sly[ty][lane] = ly1;
+    float4 lz1 = lupd4(dth, mu_n, mu_c, lz_c);
+    if (k == nz - 1) lz1 = z4();
+    __syncthreads();
+    float4 lyl;
+    if (ty > 0) {
+      lyl = sly[ty - 1][lane];
+    } else {
+      lyl = z4();
+      if (act && y >= 1) {
+        float4 l = ld4(a.ly, i - nx);
+        if (rplane) {
+          l.x += inj_one(a, 1, i0 + 0, y - 1, k);
+          l.y += inj_one(a, 1, i0 + 1, y - 1, k);
+          l.z += inj_one(a, 1, i0 + 2, y - 1, k);
+          l.w += inj_one(a, 1, i0 + 3, y - 1, k);
+        }
+        lyl = lupd4(dth, mu_c, smu[b][0][lane + 1], l);
+      }
+    }
+    // dt q = dt G^T lam' = -dt/h (div lam') on interior nodes
+    float4 dq;
+    dq.x = -dth * (((lx1.x - lxl) + (ly1.x - lyl.x)) + (lz1.x - lzl.x));
+    dq.y = -dth * (((lx1.y - lx1.x) + (ly1.y - lyl.y)) + (lz1.y - lzl.y));
+    dq.z = -dth * (((lx1.z - lx1.y) + (ly1.z - lyl.z)) + (lz1.z - lzl.z));
+    dq.w = -dth * (((lx1.w - lx1.z) + (ly1.w - lyl.w)) + (lz1.w - lzl.w));
+    if (k == 0 || k == nz - 1 || y == 0 || y == ny - 1) {
+      dq = z4();
+    } else {
+      if (i0 == 0) dq.x = 0.f;
+      if (i0 + 4 == nx) dq.w = 0.f;
+    }
+    float4 mu1 = make_float4(fmaf(m4.x, dq.x, mu_c.x), fmaf(m4.y, dq.y, mu_c.y),
+                             fmaf(m4.z, dq.z, mu_c.z), fmaf(m4.w, dq.w, mu_c.w));
+    if (act) {
+      st4(a.mu1, i, mu1);
+      st4(a.lx1, i, lx1);
+      st4(a.ly1, i, ly1);
+      st4(a.lz1, i, lz1);
+      // dJ/dm += dt e^n q
+      const float4 g = make_float4(en4.x * dq.x, en4.y * dq.y, en4.z * dq.z, en4.w * dq.w);
+      const int mode = a.acc_mode;
+      if (mode & kAccLast) {
+        float4 s = g;
+        if (!(mode & kAccFirst)) {
+          const float4 w = *reinterpret_cast<const float4*>(a.acc32 + i);
+          s = make_float4(w.x + g.x, w.y + g.y, w.z + g.z, w.w + g.w);
+        }
+        double2* p = reinterpret_cast<double2*>(a.acc64 + i);
+        double2 lo = p[0], hi = p[1];
+        lo.x += (double)s.x;
+        lo.y += (double)s.y;
+        hi.x += (double)s.z;
+        hi.y += (double)s.w;
+        p[0] = lo;
+        p[1] = hi;
+      } else if (mode & kAccFirst) {
+        st4(a.acc32, i, g);
+      } else {
+        const float4 w = *reinterpret_cast<const float4*>(a.acc32 + i);
+        st4(a.acc32, i, make_float4(w.x + g.x, w.y + g.y, w.z + g.z, w.w + g.w));
+      }
+    }
+    lzl = lz1;
+    mu_c = mu_n;
+    mu_n = mu_x;
+    lx_c = lx_x;
+    ly_c = ly_x;
+    lz_c = lz_x;
+  }
+}
+
+}  // namespace
+
+int default_kc(int nx, int ny, int nz) {
+  const long long cxy = (long long)((nx + kTXW - 1) / kTXW) * ((ny + TY - 1) / TY);
+  // aim for ~4 resident CTAs on each of the 152 SMs
+  long long nzc = (4LL * 152 + cxy - 1) / cxy;
+  if (nzc < 1) nzc = 1;
+  if (nzc > nz) nzc = nz;
+  int kc = (int)((nz + nzc - 1) / nzc);
+  return kc < 1 ? 1 : kc;
+}
+
+static dim3 grid_of(int nx, int ny, int nz, int kc) {
+  return dim3((nx + kTXW - 1) / kTXW, (ny + TY - 1) / TY, (nz + kc - 1) / kc);
+}
+
+cudaError_t launch_fwd_step(const FwdStep& a, bool incremental, cudaStream_t s) {
+  const dim3 grid = grid_of(a.nx, a.ny, a.nz, a.kc), block(32, TY);
+  if (incremental) {
+    fwd_step_kernel<true, false><<<grid, block, 0, s>>>(a);
+  } else if (a.amax) {
+    fwd_step_kernel<false, true><<<grid, block, 0, s>>>(a);
+  } else {
+    fwd_step_kernel<false, false><<<grid, block, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_step(const AdjStep& a, cudaStream_t s) {
+  const dim3 grid = grid_of(a.nx, a.ny, a.nz, a.kc), block(32, TY);
+  adj_step_kernel<<<grid, block, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace aew

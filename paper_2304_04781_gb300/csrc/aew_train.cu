@@ -1,0 +1,409 @@
+// Training of the per-block autoencoder (Sec. 3.3, Table 2): mean-squared
+// reconstruction error on normalised block vectors, back-propagation through both
+// GELU layers with a straight-through FP16 latent, and the LAMB optimiser
+// (You et al. 2019) with one trust ratio per parameter tensor.
+//
+// Every product is a tcgen05 GEMM (aew_gemm.cuh) with BF16 operands and FP32
+// accumulation (the decoder's first forward product uses FP16 operands, as in
+// inference).  Activations are written both row-major and transposed by the producing
+// epilogue, so every weight-gradient product (K = batch) reads K-contiguous operands.
+// FP32 master weights; LAMB moments in FP32; norms and the loss in FP64.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cmath>
+#include <string>
+
+#include "aew_codec.cuh"
+#include "aew_codec_state.cuh"
+#include "aew_gemm.cuh"
+
+namespace aew {
+
+
+namespace {
+
+struct TrainState {
+  int B = 0;       // batch capacity
+  int nl = 64;
+  int t = 0;       // LAMB step count
+  size_t bytes = 0;
+  // activations
+  float *a1, *a3, *d1, *d2, *d3, *d4;
+  uint16_t *h1, *h1T, *z16, *zbT, *h3, *h3T, *d4b, *d4T, *d3b, *d3T, *d2b, *d2T, *d1T, *YT;
+  // gradients and moments (8 tensors)
+  float* g[8];
+  float* m[8];
+  float* v[8];
+  // backward weight copies (natural layout, BF16)
+  uint16_t *W4b, *W3b, *W2b;
+  double* red;  // [0] loss, [1 + 2t], [2 + 2t]: |w|^2, |u|^2 of tensor t
+  void* allocs[64];
+  int nalloc = 0;
+};
+
+template <class T>
+bool talloc(TrainState* s, T** p, size_t n) {
+  void* q = nullptr;
+  if (cudaMalloc(&q, n * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  s->allocs[s->nalloc++] = q;
+  s->bytes += n * sizeof(T);
+  *p = static_cast<T*>(q);
+  return true;
+}
+
+TrainState* train_new(Codec* c, int B) {
+  TrainState* s = new TrainState();
+  s->B = B;
+  s->nl = c->n_lat;
+  const size_t b = (size_t)B, nl = (size_t)c->n_lat, H = kNHid, I = kNIn;
+  bool ok = talloc(s, &s->a1, b * H) && talloc(s, &s->a3, b * H) && talloc(s, &s->d1, b * H) &&
+            talloc(s, &s->d2, b * nl) && talloc(s, &s->d3, b * H) && talloc(s, &s->d4, b * I) &&
+            talloc(s, &s->h1, b * H) && talloc(s, &s->h1T, b * H) && talloc(s, &s->z16, b * nl) &&
+            talloc(s, &s->zbT, b * nl) && talloc(s, &s->h3, b * H) && talloc(s, &s->h3T, b * H) &&
+            talloc(s, &s->d4b, b * I) && talloc(s, &s->d4T, b * I) && talloc(s, &s->d3b, b * H) &&
+            talloc(s, &s->d3T, b * H) && talloc(s, &s->d2b, b * nl) && talloc(s, &s->d2T, b * nl) &&
+            talloc(s, &s->d1T, b * H) && talloc(s, &s->YT, b * I) &&
+            talloc(s, &s->W4b, H * I) && talloc(s, &s->W3b, nl * H) && talloc(s, &s->W2b, H * nl) &&
+            talloc(s, &s->red, 32);
+  for (int i = 0; i < 8 && ok; ++i)
+    ok = talloc(s, &s->g[i], c->wn[i]) && talloc(s, &s->m[i], c->wn[i]) &&
+         talloc(s, &s->v[i], c->wn[i]);
+  if (!ok) {
+    for (int i = 0; i < s->nalloc; ++i) cudaFree(s->allocs[i]);
+    delete s;
+    return nullptr;
+  }
+  for (int i = 0; i < 8; ++i) {
+    cudaMemset(s->m[i], 0, c->wn[i] * sizeof(float));
+    cudaMemset(s->v[i], 0, c->wn[i] * sizeof(float));
+  }
+  return s;
+}
+
+// ---------------------------------------------------------------------------------
+// Epilogues
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ void store_row16(uint16_t* dst, const uint32_t (&pk)[16]) {
+  uint4* d = reinterpret_cast<uint4*>(dst);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) d[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+}
+
+// a = acc + bias -> pre (FP32), h = bf16(gelu(a)) row-major and transposed
+struct EpFwdGelu {
+  const float* bias;
+  float* pre;
+  uint16_t* h;
+  uint16_t* hT;
+  int N;
+  long long M;
+  __device__ __forceinline__ void operator()(long long row, int col, const float (&v)[32]) const {
+    if (row >= M) return;
+    uint32_t pk[16];
+    float4* pd = reinterpret_cast<float4*>(pre + row * N + col);
+#pragma unroll
+    for (int j = 0; j < 32; j += 4) {
+      float a[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) a[q] = v[j + q] + __ldg(bias + col + j + q);
+      pd[j / 4] = make_float4(a[0], a[1], a[2], a[3]);
+      const float g0 = gemm::gelu_f(a[0]), g1 = gemm::gelu_f(a[1]);
+      const float g2 = gemm::gelu_f(a[2]), g3 = gemm::gelu_f(a[3]);
+      pk[j / 2] = gemm::pack_bf16(g0, g1);
+      pk[j / 2 + 1] = gemm::pack_bf16(g2, g3);
+      hT[(size_t)(col + j + 0) * M + row] = gemm::bf16_bits(g0);
+      hT[(size_t)(col + j + 1) * M + row] = gemm::bf16_bits(g1);
+      hT[(size_t)(col + j + 2) * M + row] = gemm::bf16_bits(g2);
+      hT[(size_t)(col + j + 3) * M + row] = gemm::bf16_bits(g3);
+    }
+    store_row16(h + row * N + col, pk);
+  }
+};
+
+// latent: z = fp16(acc + b2) row-major; bf16(z) transposed for dW3
+struct EpFwdLatent {
+  const float* bias;
+  uint16_t* z16;
+  uint16_t* zbT;
+  int nl;
+  long long M;
+  __device__ __forceinline__ void operator()(long long row, int col, const float (&v)[32]) const {
+    if (row >= M || col >= nl) return;
+    uint32_t pk[16];
+#pragma unroll
+    for (int j = 0; j < 32; j += 2) {
+      const __half2 hv = __floats2half2_rn(v[j] + __ldg(bias + col + j), v[j + 1] + __ldg(bias + col + j + 1));
+      pk[j / 2] = *reinterpret_cast<const uint32_t*>(&hv);
+      zbT[(size_t)(col + j) * M + row] = gemm::bf16_bits(__low2float(hv));
+      zbT[(size_t)(col + j + 1) * M + row] = gemm::bf16_bits(__high2float(hv));
+    }
+    store_row16(z16 + row * nl + col, pk);
+  }
+};
+
+// reconstruction: a4 = acc + b4; diff = a4 - y; d4 = 2 diff / (B*2048)
+struct EpMse {
+  const float* bias;
+  const uint16_t* Y;
+  float* d4;
+  uint16_t* d4b;
+  uint16_t* d4T;
+  double* loss;
+  float scale;
+  long long M;
+  __device__ __forceinline__ void operator()(long long row, int col, const float (&v)[32]) const {
+    if (row >= M) return;
+    double acc = 0.0;
+    uint32_t pk[16];
+    float dd[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const float a = v[j] + __ldg(bias + col + j);
+      const float diff = a - gemm::bf16_val(__ldg(Y + row * kNIn + col + j));
+      acc += (double)diff * (double)diff;
+      dd[j] = scale * diff;
+      d4T[(size_t)(col + j) * M + row] = gemm::bf16_bits(dd[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 32; j += 2) pk[j / 2] = gemm::pack_bf16(dd[j], dd[j + 1]);
+    float4* pd = reinterpret_cast<float4*>(d4 + row * kNIn + col);
+#pragma unroll
+    for (int j = 0; j < 32; j += 4) pd[j / 4] = make_float4(dd[j], dd[j + 1], dd[j + 2], dd[j + 3]);
+    store_row16(d4b + row * kNIn + col, pk);
+    atomicAdd(loss, acc);
+  }
+};
+
+// backward through an activation: d = acc * act'(pre) (or d = acc), stored FP32,
+// BF16 row-major (optional) and BF16 transposed
+struct EpBack {
+  const float* pre;  // null: straight-through
+  float* d;
+  uint16_t* db;
+  uint16_t* dT;
+  int N;
+  long long M;
+  __device__ __forceinline__ void operator()(long long row, int col, const float (&v)[32]) const {
+    if (row >= M || col >= N) return;
+    float dd[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      dd[j] = pre ? v[j] * gemm::gelu_prime_f(pre[row * N + col + j]) : v[j];
+      dT[(size_t)(col + j) * M + row] = gemm::bf16_bits(dd[j]);
+    }
+    float4* pd = reinterpret_cast<float4*>(d + row * N + col);
+#pragma unroll
+    for (int j = 0; j < 32; j += 4) pd[j / 4] = make_float4(dd[j], dd[j + 1], dd[j + 2], dd[j + 3]);
+    if (db) {
+      uint32_t pk[16];
+#pragma unroll
+      for (int j = 0; j < 32; j += 2) pk[j / 2] = gemm::pack_bf16(dd[j], dd[j + 1]);
+      store_row16(db + row * N + col, pk);
+    }
+  }
+};
+
+// weight gradient: G[row][col..] = acc (FP32)
+struct EpStore {
+  float* G;
+  int N;
+  long long M;
+  __device__ __forceinline__ void operator()(long long row, int col, const float (&v)[32]) const {
+    if (row >= M || col >= N) return;
+    float4* pd = reinterpret_cast<float4*>(G + row * N + col);
+#pragma unroll
+    for (int j = 0; j < 32; j += 4) pd[j / 4] = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+  }
+};
+
+// ---------------------------------------------------------------------------------
+// Small kernels
+// ---------------------------------------------------------------------------------
+__global__ void transpose16_kernel(const uint16_t* __restrict__ src, int rows, int cols,
+                                   uint16_t* __restrict__ dst) {
+  __shared__ uint16_t tile[32][34];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    tile[i][threadIdx.x] = (r < rows && c < cols) ? src[(size_t)r * cols + c] : (uint16_t)0;
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (c < cols && r < rows) dst[(size_t)c * rows + r] = tile[threadIdx.x][i];
+  }
+}
+
+__global__ void colsum_kernel(const float* __restrict__ d, int rows, int cols, float* __restrict__ out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  double s = 0.0;
+  for (int r = 0; r < rows; ++r) s += d[(size_t)r * cols + c];
+  out[c] = (float)s;
+}
+
+__global__ void to_bf16_kernel(const float* __restrict__ w, size_t n, uint16_t* __restrict__ o) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    o[i] = gemm::bf16_bits(w[i]);
+}
+
+__global__ void loss_kernel(const double* red, double inv_n, float* out) { out[0] = (float)(red[0] * inv_n); }
+
+// LAMB pass 1: moments, u (written over g), partial norms |w|^2 and |u|^2
+__global__ void lamb1_kernel(const float* __restrict__ w, float* __restrict__ g, float* __restrict__ m,
+                             float* __restrict__ v, size_t n, float b1, float b2, float c1, float c2,
+                             float eps, double* norms) {
+  double sw = 0.0, su = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float u = (mi / c1) / (sqrtf(vi / c2) + eps);
+    g[i] = u;
+    sw += (double)w[i] * (double)w[i];
+    su += (double)u * (double)u;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sw += __shfl_xor_sync(0xffffffffu, sw, o);
+    su += __shfl_xor_sync(0xffffffffu, su, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(norms, sw);
+    atomicAdd(norms + 1, su);
+  }
+}
+
+// LAMB pass 2: w -= lr * (|w| / |u|) * u
+__global__ void lamb2_kernel(float* __restrict__ w, const float* __restrict__ u, size_t n, float lr,
+                             const double* norms) {
+  const double wn = sqrt(norms[0]), un = sqrt(norms[1]);
+  const float r = (wn > 0.0 && un > 0.0) ? (float)(wn / un) : 1.f;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    w[i] -= lr * r * u[i];
+}
+
+int nblk(size_t n) {
+  size_t b = (n + 255) / 256;
+  if (b > 1216) b = 1216;
+  return b < 1 ? 1 : (int)b;
+}
+
+using LdKLin = gemm::LdK16<gemm::RowsLinear>;
+
+LdKLin ld(const uint16_t* p, long long ldim, long long rows, int K) {
+  return LdKLin{p, gemm::RowsLinear{ldim}, rows, K};
+}
+
+#define TCK(x)                              \
+  do {                                      \
+    cudaError_t _e = (x);                   \
+    if (_e != cudaSuccess) return _e;       \
+  } while (0)
+
+}  // namespace
+
+void train_state_free(void* t) {
+  TrainState* s = static_cast<TrainState*>(t);
+  if (!s) return;
+  for (int i = 0; i < s->nalloc; ++i) cudaFree(s->allocs[i]);
+  delete s;
+}
+size_t train_state_bytes(const void* t) { return t ? static_cast<const TrainState*>(t)->bytes : 0; }
+
+cudaError_t codec_train_step(Codec* c, const uint16_t* Y, int B, float lr, float* loss_dev,
+                             cudaStream_t st, std::string* err) {
+  if (B % 8 != 0) {
+    if (err) *err = "batch must be a multiple of 8";
+    return cudaErrorInvalidValue;
+  }
+  TrainState* s = static_cast<TrainState*>(c->train);
+  if (!s || s->B < B) {
+    if (s) train_state_free(s);
+    c->train = nullptr;
+    s = train_new(c, B);
+    if (!s) return cudaErrorMemoryAllocation;
+    c->train = s;
+  }
+  const int nl = c->n_lat;
+  const long long Bm = B;
+  const int H = kNHid, I = kNIn;
+  int* e = c->err;
+  TCK(cudaMemsetAsync(s->red, 0, 32 * sizeof(double), st));
+  // backward weight copies of the current masters
+  TCK((to_bf16_kernel<<<nblk((size_t)H * I), 256, 0, st>>>(c->w[6], (size_t)H * I, s->W4b), cudaGetLastError()));
+  TCK((to_bf16_kernel<<<nblk((size_t)nl * H), 256, 0, st>>>(c->w[4], (size_t)nl * H, s->W3b), cudaGetLastError()));
+  TCK((to_bf16_kernel<<<nblk((size_t)H * nl), 256, 0, st>>>(c->w[2], (size_t)H * nl, s->W2b), cudaGetLastError()));
+  {
+    dim3 grid((I + 31) / 32, (B + 31) / 32), block(32, 8);
+    transpose16_kernel<<<grid, block, 0, st>>>(Y, B, I, s->YT);
+    TCK(cudaGetLastError());
+  }
+  // ---- forward
+  TCK((gemm::launch<256, true>(Bm, H, I, ld(Y, I, Bm, I), ld(c->W1t, I, H, I),
+                               EpFwdGelu{c->w[1], s->a1, s->h1, s->h1T, H, Bm}, e, st)));
+  if (nl == 64)
+    TCK((gemm::launch<64, true>(Bm, nl, H, ld(s->h1, H, Bm, H), ld(c->W2t, H, nl, H),
+                                EpFwdLatent{c->w[3], s->z16, s->zbT, nl, Bm}, e, st)));
+  else
+    TCK((gemm::launch<32, true>(Bm, nl, H, ld(s->h1, H, Bm, H), ld(c->W2t, H, nl, H),
+                                EpFwdLatent{c->w[3], s->z16, s->zbT, nl, Bm}, e, st)));
+  TCK((gemm::launch<256, false>(Bm, H, nl, ld(s->z16, nl, Bm, nl), ld(c->W3t, nl, H, nl),
+                                EpFwdGelu{c->w[5], s->a3, s->h3, s->h3T, H, Bm}, e, st)));
+  TCK((gemm::launch<256, true>(Bm, I, H, ld(s->h3, H, Bm, H), ld(c->W4t, H, I, H),
+                               EpMse{c->w[7], Y, s->d4, s->d4b, s->d4T, s->red,
+                                     2.0f / (float)((double)B * I), Bm},
+                               e, st)));
+  // ---- backward
+  TCK((gemm::launch<256, true>((long long)H, I, B, ld(s->h3T, B, H, B), ld(s->d4T, B, I, B),
+                               EpStore{s->g[6], I, H}, e, st)));
+  TCK((gemm::launch<256, true>(Bm, H, I, ld(s->d4b, I, Bm, I), ld(s->W4b, I, H, I),
+                               EpBack{s->a3, s->d3, s->d3b, s->d3T, H, Bm}, e, st)));
+  TCK((gemm::launch<256, true>((long long)nl, H, B, ld(s->zbT, B, nl, B), ld(s->d3T, B, H, B),
+                               EpStore{s->g[4], H, nl}, e, st)));
+  if (nl == 64)
+    TCK((gemm::launch<64, true>(Bm, nl, H, ld(s->d3b, H, Bm, H), ld(s->W3b, H, nl, H),
+                                EpBack{nullptr, s->d2, s->d2b, s->d2T, nl, Bm}, e, st)));
+  else
+    TCK((gemm::launch<32, true>(Bm, nl, H, ld(s->d3b, H, Bm, H), ld(s->W3b, H, nl, H),
+                                EpBack{nullptr, s->d2, s->d2b, s->d2T, nl, Bm}, e, st)));
+  if (nl == 64)
+    TCK((gemm::launch<64, true>((long long)H, nl, B, ld(s->h1T, B, H, B), ld(s->d2T, B, nl, B),
+                                EpStore{s->g[2], nl, H}, e, st)));
+  else
+    TCK((gemm::launch<32, true>((long long)H, nl, B, ld(s->h1T, B, H, B), ld(s->d2T, B, nl, B),
+                                EpStore{s->g[2], nl, H}, e, st)));
+  TCK((gemm::launch<256, true>(Bm, H, nl, ld(s->d2b, nl, Bm, nl), ld(s->W2b, nl, H, nl),
+                               EpBack{s->a1, s->d1, nullptr, s->d1T, H, Bm}, e, st)));
+  TCK((gemm::launch<256, true>((long long)I, H, B, ld(s->YT, B, I, B), ld(s->d1T, B, H, B),
+                               EpStore{s->g[0], H, I}, e, st)));
+  // bias gradients
+  TCK((colsum_kernel<<<(H + 255) / 256, 256, 0, st>>>(s->d1, B, H, s->g[1]), cudaGetLastError()));
+  TCK((colsum_kernel<<<(nl + 255) / 256, 256, 0, st>>>(s->d2, B, nl, s->g[3]), cudaGetLastError()));
+  TCK((colsum_kernel<<<(H + 255) / 256, 256, 0, st>>>(s->d3, B, H, s->g[5]), cudaGetLastError()));
+  TCK((colsum_kernel<<<(I + 255) / 256, 256, 0, st>>>(s->d4, B, I, s->g[7]), cudaGetLastError()));
+  if (loss_dev) {
+    loss_kernel<<<1, 1, 0, st>>>(s->red, 1.0 / ((double)B * I), loss_dev);
+    TCK(cudaGetLastError());
+  }
+  // ---- LAMB
+  s->t += 1;
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-6f;
+  const float c1 = (float)(1.0 - std::pow(0.9, s->t)), c2 = (float)(1.0 - std::pow(0.999, s->t));
+  for (int i = 0; i < 8; ++i) {
+    const size_t n = c->wn[i];
+    lamb1_kernel<<<nblk(n), 256, 0, st>>>(c->w[i], s->g[i], s->m[i], s->v[i], n, b1, b2, c1, c2, eps,
+                                          s->red + 1 + 2 * i);
+    TCK(cudaGetLastError());
+    lamb2_kernel<<<nblk(n), 256, 0, st>>>(c->w[i], s->g[i], n, lr, s->red + 1 + 2 * i);
+    TCK(cudaGetLastError());
+  }
+  return codec_refresh(c, st);
+}
+
+}  // namespace aew

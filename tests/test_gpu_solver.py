@@ -1,0 +1,220 @@
+"""GPU parity of the CUDA solver path against the FP64 oracle: seismograms, misfit,
+full-storage gradient, Gauss-Newton HVP, exact eigenmode, energy, the adjoint
+identity, finite differences through the autograd Function, checkpointing (bitwise
+equal to full storage), ragged and multi-tile grids, and error handling."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import wave as W
+from paper_2304_04781_gb300 import inputs
+
+from .helpers import cuda, host, relerr, setup, solver
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4  # rel-L2 of FP32 GPU vs FP64 oracle (seismograms, gradients)
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    """32^3, 200 steps, 16 receivers; observed data from the +5% bump model."""
+    prob, c, rec = setup((32, 32, 32), 200, 16, seed=0)
+    ctrue = inputs.bump_model(c, prob.h).astype(np.float32).astype(np.float64)
+    d_obs, _, _ = W.forward(prob, ctrue)
+    return prob, c, d_obs
+
+
+def test_seismograms_match_oracle(cfg1):
+    prob, c, _ = cfg1
+    s = solver(prob)
+    d = host(s.forward(cuda(c)))
+    d_ref, _, _ = W.forward(prob, c)
+    assert np.abs(d_ref).max() > 0
+    assert relerr(d, d_ref) < TOL
+
+
+def test_full_storage_gradient_matches_oracle(cfg1):
+    prob, c, d_obs = cfg1
+    s = solver(prob)
+    J, g = s.gradient(cuda(c), cuda(d_obs))
+    J_ref, g_ref, _ = W.gradient(prob, c, d_obs)
+    assert abs(J - J_ref) / J_ref < TOL
+    assert relerr(host(g), g_ref) < TOL
+    st = s.stats()
+    assert st["forward_steps"] == prob.nt and st["adjoint_steps"] == prob.nt
+
+
+def test_gn_hessvec_matches_oracle(cfg1):
+    prob, c, d_obs = cfg1
+    s = solver(prob)
+    s.gradient(cuda(c), cuda(d_obs))
+    dc = inputs.direction(prob.shape, prob.h, seed=20).astype(np.float32).astype(np.float64)
+    H = host(s.hessvec(cuda(dc)))
+    _, states = W.forward_states(prob, c)
+    H_ref = W.hessvec_gn(prob, c, dc, lambda n: states[n][0])
+    assert relerr(H, H_ref) < TOL
+    dd = host(s.jvp(cuda(dc)))
+    dd_ref = W.incremental_forward(prob, c, dc, lambda n: states[n][0])
+    assert relerr(dd, dd_ref) < TOL
+
+
+@pytest.mark.parametrize("shape", [(20, 36, 132), (24, 20, 260), (16, 16, 16)])
+def test_ragged_and_multitile_grids(shape):
+    """x tiles of 128 with a ragged tail, y tiles of 8 with a ragged tail, z chunks."""
+    prob, c, _ = setup(shape, 60, 16, seed=1)
+    prob.src = (shape[2] // 3, shape[1] // 2, shape[0] // 2)
+    s = solver(prob)
+    d_ref, _, states = W.forward(prob, c, keep_states=True)
+    d = host(s.forward(cuda(c)))
+    assert relerr(d, d_ref) < TOL
+    r = np.random.default_rng(0).standard_normal(d_ref.shape) * np.abs(d_ref).max()
+    r[0] = 0
+    _, g = s.gradient(cuda(c), cuda(d_ref - r))
+    g_ref = W.jacobian_transpose(prob, c, r, lambda n: states[n][0])
+    assert relerr(host(g), g_ref) < TOL
+
+
+def test_exact_eigenmode_on_gpu():
+    from .test_oracle_wave import eigenmode_setup
+    shape, h, c = (24, 20, 28), 10.0, 2100.0
+    prob, S, state = eigenmode_setup(shape, h, c, (2, 1, 3), nt=200)
+    s = solver(prob)
+    st = [cuda(a) for a in state(0)]
+    s.propagate(cuda(np.full(shape, c)), st, 0, prob.nt)
+    for got, want in zip(st, state(prob.nt)):
+        assert relerr(host(got), want) < 1e-5
+
+
+def test_energy_conserved_on_gpu():
+    from paper_2304_04781_gb300 import aewave
+    shape, h = (24, 20, 28), 10.0
+    prob = W.Problem(shape=shape, h=h, nt=200, rec=np.zeros((0, 3), int))
+    c = inputs.velocity_model(shape, h, seed=5)
+    m = cuda(c * c)
+    st0 = inputs.smooth_state(shape, h, seed=3)
+    st = [cuda(W.interior(st0[0] * 1e-3)), cuda(st0[1]), cuda(st0[2]), cuda(st0[3])]
+    s = solver(prob)
+    cc = cuda(c)
+    E = []
+    for n in range(prob.nt):
+        prev = [t.clone() for t in st]
+        s.propagate(cc, st, n, 1)
+        e_m = prev[0] * m
+        E.append(0.5 * aewave.dot(e_m, prev[0]) + 0.5 * sum(aewave.dot(a, b) for a, b in zip(prev[1:], st[1:])))
+    E = np.array(E)
+    assert np.max(np.abs(E - E[0])) / abs(E[0]) < 1e-5
+
+
+def test_adjoint_identity_on_gpu():
+    from paper_2304_04781_gb300 import aewave
+    prob, c, _ = setup((32, 32, 32), 200, 16, seed=0)
+    s = solver(prob)
+    cc = cuda(c)
+    d = s.forward(cc)
+    r = torch.randn_like(d) * d.abs().max()
+    r[0] = 0
+    _, JTr = s.gradient(cc, (d - r).contiguous())
+    dc = cuda(inputs.direction(prob.shape, prob.h, seed=11))
+    Jdc = s.jvp(dc)
+    lhs = aewave.dot(Jdc, r)
+    rhs = aewave.dot(dc, JTr)
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
+def test_gradient_matches_central_differences_through_autograd():
+    """J(c) behind torch.autograd.Function; FD of the FP64 misfit in 8 GRF directions."""
+    from paper_2304_04781_gb300 import aewave
+    prob, c, _ = setup((16, 16, 16), 120, 16, seed=0)
+    ctrue = inputs.bump_model(c, prob.h)
+    s = solver(prob)
+    d_obs = s.forward(cuda(ctrue))
+    cc = cuda(c).requires_grad_(True)
+    J = aewave.Misfit.apply(cc, d_obs, s)
+    J.backward()
+    g = cc.grad.detach()
+    eps = 1e-3 * float(np.abs(c).max())
+    for k in range(8):
+        dc = cuda(inputs.direction(prob.shape, prob.h, seed=10 + k))
+        Jp, _ = s.gradient((cc.detach() + eps * dc).contiguous(), d_obs)
+        Jm, _ = s.gradient((cc.detach() - eps * dc).contiguous(), d_obs)
+        fd = (Jp - Jm) / (2 * eps)
+        ad = aewave.dot(g, dc)
+        assert abs(fd - ad) <= 1e-2 * abs(ad), (k, fd, ad)
+
+
+def test_forward_map_vjp():
+    from paper_2304_04781_gb300 import aewave
+    prob, c, _ = setup((16, 16, 16), 80, 16, seed=2)
+    s = solver(prob)
+    cc = cuda(c).requires_grad_(True)
+    d = aewave.ForwardMap.apply(cc, s)
+    r = torch.randn_like(d)
+    r[0] = 0
+    (d * r).sum().backward()
+    _, states = W.forward_states(prob, c)
+    ref = W.jacobian_transpose(prob, c, host(r), lambda n: states[n][0])
+    assert relerr(host(cc.grad), ref) < TOL
+
+
+@pytest.mark.parametrize("nt,s_slots", [(200, 0), (200, 3), (200, 20), (57, 5)])
+def test_revolve_bitwise_equals_full_storage(cfg1, nt, s_slots):
+    prob, c, d_obs = cfg1
+    prob2 = W.Problem(shape=prob.shape, h=prob.h, nt=nt, rec=prob.rec)
+    full = solver(prob2)
+    rev = solver(prob2, storage="revolve", n_checkpoints=s_slots)
+    Jf, gf = full.gradient(cuda(c), cuda(d_obs[: nt + 1]))
+    Jr, gr = rev.gradient(cuda(c), cuda(d_obs[: nt + 1]))
+    assert Jf == Jr
+    assert torch.equal(gf, gr)
+    from oracle import revolve as R
+    assert rev.stats()["forward_steps"] == R.gradient_forward_steps(nt, s_slots)
+    dc = cuda(inputs.direction(prob.shape, prob.h, seed=3))
+    assert torch.equal(full.hessvec(dc), rev.hessvec(dc))
+
+
+def test_config2_full_vs_revolve_and_fd():
+    """128^3, 1000 steps, 64 receivers: full storage vs revolve(20) bitwise, FD in 8 directions."""
+    from paper_2304_04781_gb300 import aewave
+    prob, c, _ = setup((128, 128, 128), 1000, 64, seed=1)
+    full = solver(prob)
+    rev = solver(prob, storage="revolve", n_checkpoints=20)
+    cc = cuda(c)
+    d_obs = full.forward(cuda(inputs.bump_model(c, prob.h)))
+    Jf, gf = full.gradient(cc, d_obs)
+    Jr, gr = rev.gradient(cc, d_obs)
+    assert Jf == Jr and torch.equal(gf, gr)
+    eps = 1e-3 * float(np.abs(c).max())
+    for k in range(8):
+        dc = cuda(inputs.direction(prob.shape, prob.h, seed=10 + k))
+        Jp, _ = full.gradient((cc + eps * dc).contiguous(), d_obs)
+        Jm, _ = full.gradient((cc - eps * dc).contiguous(), d_obs)
+        fd = (Jp - Jm) / (2 * eps)
+        ad = aewave.dot(gf, dc)
+        assert abs(fd - ad) <= 1e-2 * abs(ad), (k, fd, ad)
+
+
+def test_error_paths():
+    from paper_2304_04781_gb300 import aewave
+    prob, c, _ = setup((16, 16, 16), 20, 16)
+    s = solver(prob)
+    with pytest.raises(aewave.AewError) as ei:
+        s.hessvec(cuda(c))
+    assert ei.value.code == -5
+    bad = c.copy()
+    bad[3, 4, 5] = np.nan
+    with pytest.raises(aewave.AewError) as ei:
+        s.forward(cuda(bad))
+    assert ei.value.code == -3
+    with pytest.raises(aewave.AewError) as ei:
+        s.forward(cuda(c * 2.0))   # c up to 6 km/s with dt set for 3 km/s
+    assert ei.value.code == -2
+    ae = solver(prob, storage="ae")
+    with pytest.raises(aewave.AewError) as ei:
+        ae.gradient(cuda(c), torch.zeros((21, 16, 3), device="cuda"))
+    assert ei.value.code == -4
+    # the handle stays usable after errors
+    d = s.forward(cuda(c))
+    assert torch.isfinite(d).all()
