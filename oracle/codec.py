@@ -176,7 +176,10 @@ def decode(W: dict, Z: np.ndarray, emulate: bool = False, cols=None) -> np.ndarr
 
 
 def roundtrip_e(W: dict, state, s4, emulate: bool = False) -> np.ndarray:
-    """Encode one state with scales s4 and decode its strain field: e-hat (unnormalised)."""
+    """Encode one state with scales s4 and decode its strain field: e-hat (unnormalised).
+
+    The decoded strain is set to 0 on boundary nodes, where the boundary condition of
+    Sec. 2 fixes e = 0 exactly (the stored forward strain is 0 there too)."""
     shape = state[0].shape
     Y = normalise(pack_blocks(state), s4)
     Z = encode(W, Y, emulate)
@@ -184,7 +187,10 @@ def roundtrip_e(W: dict, state, s4, emulate: bool = False) -> np.ndarray:
     E = decode(W, Z, emulate, cols=cols) * s4[0]
     Xe = np.zeros((E.shape[0], NIN))
     Xe[:, cols] = E
-    return unpack_field(Xe, shape, 0)
+    e = unpack_field(Xe, shape, 0)
+    inner = np.zeros_like(e)
+    inner[1:-1, 1:-1, 1:-1] = e[1:-1, 1:-1, 1:-1]
+    return inner
 
 
 def compressed_e_history(W: dict, states, emulate: bool = False):
