@@ -150,6 +150,12 @@ int aew_codec_get(const aew_handle* h, float* W1_host, float* b1_host,
 int aew_codec_encode(aew_handle* h, const float* const fields_dev[4], const float* scale_host,
                      uint16_t* latents_dev, void* stream);
 
+/* Encode normalised block vectors (e.g. training snapshots): vectors_dev = device
+ * BF16 bit patterns [n][2048] in the block-vector order above; latents_dev: device
+ * FP16 [n][n_lat] (written). */
+int aew_codec_encode_vectors(aew_handle* h, const uint16_t* vectors_dev, long long n,
+                             uint16_t* latents_dev, void* stream);
+
 /* Decode latents.  out_dev: device FP32 [nblocks][2048] normalised block vectors
  * (all four fields, not multiplied by any scale). */
 int aew_codec_decode(aew_handle* h, const uint16_t* latents_dev, float* out_dev, void* stream);
@@ -197,9 +203,12 @@ int aew_jvp(aew_handle* h, const float* dc_dev, float* dd_dev, void* stream);
  * `every`-th state n (n = every, 2*every, ... < nt) into BF16 block vectors, each
  * field divided by its running maximum.  out_dev: device BF16 (uint16 bit patterns)
  * [max_vectors][2048]; *n_written receives the number of vectors written (at most
- * max_vectors).  The history storage of the handle is not touched. */
+ * max_vectors; whole states only).  scales_dev (may be NULL): device FP32 [k][4]
+ * receiving the four field scales of each packed state k.  The history storage of
+ * the handle is not touched. */
 int aew_snapshots(aew_handle* h, const float* c_dev, int every, uint16_t* out_dev,
-                  long long max_vectors, long long* n_written, void* stream);
+                  long long max_vectors, float* scales_dev, long long* n_written,
+                  void* stream);
 
 /* One training step of the codec on a minibatch: batch_dev = BF16 [batch][2048]
  * normalised vectors; loss = mean squared reconstruction error (Sec. 3.3); LAMB

@@ -63,6 +63,7 @@ _SIGS = [
     ("aew_codec_set", c_int, [c_void_p] + [c_void_p] * 8),
     ("aew_codec_get", c_int, [c_void_p] + [c_void_p] * 8),
     ("aew_codec_encode", c_int, [c_void_p, POINTER(c_void_p), POINTER(c_float), c_void_p, c_void_p]),
+    ("aew_codec_encode_vectors", c_int, [c_void_p, c_void_p, c_longlong, c_void_p, c_void_p]),
     ("aew_codec_decode", c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     ("aew_codec_decode_e", c_int, [c_void_p, c_void_p, c_float, c_void_p, c_void_p]),
     ("aew_forward", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
@@ -71,7 +72,7 @@ _SIGS = [
     ("aew_gradient", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_double), c_void_p]),
     ("aew_hessvec", c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     ("aew_jvp", c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
-    ("aew_snapshots", c_int, [c_void_p, c_void_p, c_int, c_void_p, c_longlong,
+    ("aew_snapshots", c_int, [c_void_p, c_void_p, c_int, c_void_p, c_longlong, c_void_p,
                               POINTER(c_longlong), c_void_p]),
     ("aew_codec_train_step", c_int, [c_void_p, c_void_p, c_int, c_float, POINTER(c_float),
                                      c_void_p]),
@@ -271,6 +272,14 @@ class Solver:
         self._check(lib().aew_codec_encode(self._h, arr, s, _ptr(lat), _stream()))
         return lat
 
+    def codec_encode_vectors(self, vec: torch.Tensor) -> torch.Tensor:
+        """BF16 normalised block vectors [n][2048] -> FP16 latents [n][n_lat]."""
+        assert vec.dtype == torch.bfloat16 and vec.shape[-1] == 2048
+        lat = torch.empty((vec.shape[0], self.n_lat), device="cuda", dtype=torch.float16)
+        self._check(lib().aew_codec_encode_vectors(self._h, _ptr(vec), vec.shape[0], _ptr(lat),
+                                                   _stream()))
+        return lat
+
     def codec_decode(self, lat: torch.Tensor) -> torch.Tensor:
         out = torch.empty((lat.shape[0], 2048), device="cuda", dtype=torch.float32)
         self._check(lib().aew_codec_decode(self._h, _ptr(lat), _ptr(out), _stream()))
@@ -282,13 +291,18 @@ class Solver:
         return e
 
     def snapshots(self, c: torch.Tensor, every: int, max_vectors: int,
-                  out: Optional[torch.Tensor] = None) -> torch.Tensor:
-        """Algorithm 1: BF16 block vectors of every `every`-th state (as int16 bit patterns)."""
+                  out: Optional[torch.Tensor] = None, with_scales: bool = False):
+        """Algorithm 1: BF16 normalised block vectors of every `every`-th state.
+
+        Returns the [n][2048] bfloat16 tensor (and the [n / nblocks][4] field scales)."""
         if out is None:
             out = torch.empty((max_vectors, 2048), device="cuda", dtype=torch.bfloat16)
+        sc = torch.zeros((max(1, max_vectors // self.nblocks), 4), device="cuda") if with_scales else None
         n = c_longlong(0)
-        self._check(lib().aew_snapshots(self._h, _ptr(c), every, _ptr(out), max_vectors, byref(n),
-                                        _stream()))
+        self._check(lib().aew_snapshots(self._h, _ptr(c), every, _ptr(out), max_vectors, _ptr(sc),
+                                        byref(n), _stream()))
+        if with_scales:
+            return out[: n.value], sc[: n.value // self.nblocks]
         return out[: n.value]
 
     def train_step(self, batch: torch.Tensor, lr: float, want_loss: bool = True) -> Optional[float]:

@@ -155,7 +155,9 @@ int incr_step(aew_handle* h, float* const in[4], float* const out[4], const floa
   a.vx1 = out[1];
   a.vy1 = out[2];
   a.vz1 = out[3];
-  a.dm = h->dm;
+  // with e^n = 0 (n = 0) the extra source G(dm e^n) vanishes: plain step, no source
+  const bool incr = en != nullptr;
+  a.dm = incr ? h->dm : nullptr;
   a.ef = en;
   a.nx = h->cfg.nx;
   a.ny = h->cfg.ny;
@@ -167,7 +169,7 @@ int incr_step(aew_handle* h, float* const in[4], float* const out[4], const floa
   a.krec = d_row ? h->krec : -1;
   a.rec_map = h->rec_map;
   a.d_out = d_row;
-  AEW_CK(aew::launch_fwd_step(a, true, s));
+  AEW_CK(aew::launch_fwd_step(a, incr, s));
   ++h->stats.kernel_launches;
   return AEW_OK;
 }
@@ -849,8 +851,28 @@ int aew_codec_decode_e(aew_handle* h, const uint16_t* latents_dev, float scale_e
   return AEW_OK;
 }
 
+int aew_codec_encode_vectors(aew_handle* h, const uint16_t* vectors_dev, long long n,
+                             uint16_t* latents_dev, void* stream) {
+  if (!h) return AEW_E_ARG;
+  if (!vectors_dev || !latents_dev || n < 0) return fail(h, AEW_E_ARG, "bad argument");
+  if (!aew::codec_ready(h->codec)) return fail(h, AEW_E_NOCODEC, "codec weights not set");
+  h->err.clear();
+  if (n == 0) return AEW_OK;
+  cudaStream_t s = S(stream);
+  int* ovf = reinterpret_cast<int*>(h->scale_tmp + 4);
+  AEW_CK(cudaMemsetAsync(ovf, 0, sizeof(int), s));
+  cudaError_t e = aew::codec_encode_vectors(h->codec, vectors_dev, n, latents_dev, ovf, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "codec_encode_vectors");
+  int o = 0;
+  AEW_CK(cudaMemcpyAsync(&o, ovf, sizeof(int), cudaMemcpyDeviceToHost, s));
+  AEW_CK(cudaStreamSynchronize(s));
+  if (o) return fail(h, AEW_E_OVERFLOW, "a latent overflowed FP16");
+  return AEW_OK;
+}
+
 int aew_snapshots(aew_handle* h, const float* c_dev, int every, uint16_t* out_dev,
-                  long long max_vectors, long long* n_written, void* stream) {
+                  long long max_vectors, float* scales_dev, long long* n_written,
+                  void* stream) {
   if (!h) return AEW_E_ARG;
   if (!out_dev || !n_written || every < 1 || max_vectors < 0)
     return fail(h, AEW_E_ARG, "bad argument");
@@ -879,6 +901,10 @@ int aew_snapshots(aew_handle* h, const float* c_dev, int every, uint16_t* out_de
       const float* f[4] = {h->st[cur][0], h->st[cur][1], h->st[cur][2], h->st[cur][3]};
       AEW_CK(aew::snapshot_pack(f, h->cfg.nx, h->cfg.ny, h->cfg.nz, scale,
                                 out_dev + (size_t)written * aew::kNIn, s));
+      if (scales_dev)
+        AEW_CK(cudaMemcpyAsync(scales_dev + 4 * (size_t)(written / (long long)nb), scale,
+                               4 * sizeof(float), cudaMemcpyDeviceToDevice, s));
+      h->stats.kernel_launches += 1;
       written += (long long)nb;
     }
   }

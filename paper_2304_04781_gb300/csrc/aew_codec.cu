@@ -373,6 +373,22 @@ cudaError_t codec_encode_grid(Codec* c, const float* const f[4], int nx, int ny,
   return e;
 }
 
+cudaError_t codec_encode_vectors(Codec* c, const uint16_t* vec, long long n, uint16_t* lat,
+                                 int* overflow, cudaStream_t s) {
+  if (!ensure_H(c, (size_t)n)) return cudaErrorMemoryAllocation;
+  LdKLin al{vec, gemm::RowsLinear{kNIn}, n, kNIn};
+  LdKLin bl{c->W1t, gemm::RowsLinear{kNIn}, kNHid, kNIn};
+  EpBiasGeluH ep{c->w[1], c->H, n};
+  cudaError_t e = gemm::launch<256, true>(n, kNHid, kNIn, al, bl, ep, c->err, s);
+  if (e != cudaSuccess) return e;
+  const int nl = c->n_lat;
+  LdKLin a2{c->H, gemm::RowsLinear{kNHid}, n, kNHid};
+  LdKLin b2{c->W2t, gemm::RowsLinear{kNHid}, nl, kNHid};
+  EpLatent e2{c->w[3], lat, nl, n, overflow};
+  if (nl == 64) return gemm::launch<64, true>(n, nl, kNHid, a2, b2, e2, c->err, s);
+  return gemm::launch<32, true>(n, nl, kNHid, a2, b2, e2, c->err, s);
+}
+
 static cudaError_t decode_hidden(Codec* c, const uint16_t* lat, long long nb, cudaStream_t s) {
   if (!ensure_H(c, (size_t)nb)) return cudaErrorMemoryAllocation;
   const int nl = c->n_lat;

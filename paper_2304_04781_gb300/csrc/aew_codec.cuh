@@ -32,6 +32,10 @@ cudaError_t codec_encode_grid(Codec* c, const float* const f[4], int nx, int ny,
                               const float* scale_prev, const unsigned* amax, float* scale_out,
                               uint16_t* lat, int* overflow, cudaStream_t s);
 
+// Encode BF16 block vectors [n][2048] into FP16 latents [n][n_lat].
+cudaError_t codec_encode_vectors(Codec* c, const uint16_t* vec, long long n, uint16_t* lat,
+                                 int* overflow, cudaStream_t s);
+
 // Decode the strain part of latents into the grid: e = s_e * dec_e(z), 0 on boundary.
 cudaError_t codec_decode_grid_e(Codec* c, const uint16_t* lat, int nx, int ny, int nz,
                                 const float* scale_e, float* e_out, cudaStream_t s);

@@ -85,9 +85,10 @@ def test_snapshots_bitwise_match_packing():
     run_max = np.zeros(4, np.float32)
     got = snaps.view(torch.int16).cpu().numpy().view(np.uint16)
     for q in range(4):
-        s.propagate(cc, st, 10 * q, 10, wavelet=wav[10 * q: 10 * q + 10])
-        hs = [host(t).astype(np.float32) for t in st]
-        run_max = np.maximum(run_max, np.array([np.abs(a).max() for a in hs], np.float32))
+        for n in range(10 * q, 10 * q + 10):   # running maximum over every state
+            s.propagate(cc, st, n, 1, wavelet=wav[n:n + 1])
+            hs = [host(t).astype(np.float32) for t in st]
+            run_max = np.maximum(run_max, np.array([np.abs(a).max() for a in hs], np.float32))
         X = C.pack_blocks([a.astype(np.float64) for a in hs]).astype(np.float32)
         sv = C.scale_vector(run_max).astype(np.float32)
         Y = np.where(sv > 0, X / np.where(sv > 0, sv, 1), 0).astype(np.float32)
