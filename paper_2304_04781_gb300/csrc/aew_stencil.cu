@@ -15,6 +15,8 @@
 // them only at CTA edges, with the identical expression, so results are bitwise
 // independent of the tiling), and then updates the strain of its nodes.  Algorithmic
 // HBM traffic of the forward step: 5 fields read + 4 written = 36 bytes per node.
+#include <cstdlib>
+
 #include "aew_internal.cuh"
 
 namespace aew {
@@ -300,9 +302,15 @@ __global__ void __launch_bounds__(NTHR) adj_step_kernel(const AdjStep a) {
   const float dth = a.dth;
   const bool has_r = a.resid != nullptr && a.krec >= 0;
 
+  const int mode = a.acc_mode;
+  const bool need_acc32 = !(mode & kAccFirst);
   float4 mu_c = z4(), mu_n = z4(), lx_c = z4(), ly_c = z4(), lz_c = z4(), lzl = z4();
+  float4 m_c = z4(), en_c = z4(), w_c = z4();
   if (act) {
     const size_t i = (size_t)kbeg * P + row;
+    m_c = ld4(a.m, i);
+    if (a.en) en_c = ld4(a.en, i);
+    if (need_acc32) w_c = ld4(a.acc32, i);
     mu_c = ld4(a.mu, i);
     if (kbeg + 1 < nz) mu_n = ld4(a.mu, i + P);
     lx_c = ld4(a.lx, i);
@@ -322,17 +330,17 @@ __global__ void __launch_bounds__(NTHR) adj_step_kernel(const AdjStep a) {
     const int b = k & 1;
     const size_t i = (size_t)k * P + row;
     float4 lx_x = z4(), ly_x = z4(), lz_x = z4(), mu_x = z4();
+    float4 m_x = z4(), en_x = z4(), w_x = z4();
     if (act && k + 1 < kend) {
       lx_x = ld4(a.lx, i + P);
       ly_x = ld4(a.ly, i + P);
       lz_x = ld4(a.lz, i + P);
+      m_x = ld4(a.m, i + P);
+      if (a.en) en_x = ld4(a.en, i + P);
+      if (need_acc32) w_x = ld4(a.acc32, i + P);
       if (k + 2 < nz) mu_x = ld4(a.mu, i + 2 * P);
     }
-    float4 m4 = z4(), en4 = z4();
-    if (act) {
-      m4 = ld4(a.m, i);
-      if (a.en) en4 = ld4(a.en, i);
-    }
+    const float4 m4 = m_c, en4 = en_c;
     const bool rplane = has_r && k == a.krec;
     if (rplane && act) inj4(a, y, i0, lx_c, ly_c, lz_c);
 
@@ -406,11 +414,10 @@ __global__ void __launch_bounds__(NTHR) adj_step_kernel(const AdjStep a) {
       st4(a.lz1, i, lz1);
       // dJ/dm += dt e^n q
       const float4 g = make_float4(en4.x * dq.x, en4.y * dq.y, en4.z * dq.z, en4.w * dq.w);
-      const int mode = a.acc_mode;
       if (mode & kAccLast) {
         float4 s = g;
-        if (!(mode & kAccFirst)) {
-          const float4 w = *reinterpret_cast<const float4*>(a.acc32 + i);
+        if (need_acc32) {
+          const float4 w = w_c;
           s = make_float4(w.x + g.x, w.y + g.y, w.z + g.z, w.w + g.w);
         }
         double2* p = reinterpret_cast<double2*>(a.acc64 + i);
@@ -424,11 +431,14 @@ __global__ void __launch_bounds__(NTHR) adj_step_kernel(const AdjStep a) {
       } else if (mode & kAccFirst) {
         st4(a.acc32, i, g);
       } else {
-        const float4 w = *reinterpret_cast<const float4*>(a.acc32 + i);
+        const float4 w = w_c;
         st4(a.acc32, i, make_float4(w.x + g.x, w.y + g.y, w.z + g.z, w.w + g.w));
       }
     }
     lzl = lz1;
+    m_c = m_x;
+    en_c = en_x;
+    w_c = w_x;
     mu_c = mu_n;
     mu_n = mu_x;
     lx_c = lx_x;
@@ -440,12 +450,29 @@ __global__ void __launch_bounds__(NTHR) adj_step_kernel(const AdjStep a) {
 }  // namespace
 
 int default_kc(int nx, int ny, int nz) {
+  // Split z so that all CTAs are resident at once (one full wave): resident CTAs =
+  // SMs x CTAs per SM of the heaviest step kernel.
   const long long cxy = (long long)((nx + kTXW - 1) / kTXW) * ((ny + TY - 1) / TY);
-  // aim for ~4 resident CTAs on each of the 152 SMs
-  long long nzc = (4LL * 152 + cxy - 1) / cxy;
+  int dev = 0, sms = 152, per_sm = 3;
+  if (cudaGetDevice(&dev) == cudaSuccess) {
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int a = 0, b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, adj_step_kernel, NTHR, 0) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fwd_step_kernel<true, false>, NTHR, 0) ==
+            cudaSuccess)
+      per_sm = a < b ? a : b;
+    cudaGetLastError();
+  }
+  if (per_sm < 1) per_sm = 1;
+  const long long resident = (long long)sms * per_sm;
+  long long nzc = resident / cxy;
   if (nzc < 1) nzc = 1;
   if (nzc > nz) nzc = nz;
   int kc = (int)((nz + nzc - 1) / nzc);
+  if (const char* env = getenv("AEW_STENCIL_KC")) {   // tuning override
+    const int v = atoi(env);
+    if (v > 0) kc = v;
+  }
   return kc < 1 ? 1 : kc;
 }
 
