@@ -30,7 +30,8 @@ struct aew_handle {
   double dt = 0.0;
   float dth = 0.f;
   size_t C = 0;
-  int kc = 1;
+  int kc = 1;       // z planes per CTA, forward-type steps
+  int kc_adj = 1;   // z planes per CTA, adjoint steps
   size_t nrow = 0;   // nrec * 3
   std::string err;
   aew_stats_t stats{};
@@ -196,7 +197,7 @@ int adj_step(aew_handle* h, int n, int cur, const float* resid, const float* en,
   a.nx = h->cfg.nx;
   a.ny = h->cfg.ny;
   a.nz = h->cfg.nz;
-  a.kc = h->kc;
+  a.kc = h->kc_adj;
   a.dth = h->dth;
   a.krec = h->krec;
   a.rec_map = h->rec_map;
@@ -275,7 +276,7 @@ int encode_state(aew_handle* h, int n, float* const f[4], cudaStream_t s) {
       h->amax + 4 * (size_t)n, h->scales + 4 * (size_t)n,
       h->lat + (size_t)n * nb * h->cfg.n_lat, h->ovf, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "codec_encode_grid");
-  h->stats.kernel_launches += 3;
+  h->stats.kernel_launches += 4;
   return AEW_OK;
 }
 
@@ -479,7 +480,8 @@ int aew_create(const aew_config* cfg, aew_handle** out) {
   h->dt = c.cfl * c.h / c.cmax;
   h->dth = (float)(h->dt / c.h);
   h->C = (size_t)c.nx * c.ny * c.nz;
-  h->kc = aew::default_kc(c.nx, c.ny, c.nz);
+  h->kc = aew::default_kc(c.nx, c.ny, c.nz, false);
+  h->kc_adj = aew::default_kc(c.nx, c.ny, c.nz, true);
   h->nrow = (size_t)c.nrec * 3;
   h->wav.resize(c.nt);
   for (int n = 0; n < c.nt; ++n) h->wav[n] = (float)(-ricker(n * h->dt, c.f0, c.t0));

@@ -60,57 +60,6 @@ cudaError_t transpose16(const float* src, int rows, int cols, uint16_t* dst, boo
 }
 
 // ---------------------------------------------------------------------------------
-// Encoder A-operand: block vectors gathered from the grid, normalised, BF16.
-// ---------------------------------------------------------------------------------
-struct LdGrid {
-  const float* f0;
-  const float* f1;
-  const float* f2;
-  const float* f3;
-  int nx, ny, NBx, NBy;
-  long long nblk;
-  const float* sprev;
-  const unsigned* amax;
-  template <int NROWS>
-  __device__ __forceinline__ void load(uint8_t* tile, long long r0, int k0, int tid) const {
-    static_assert(NROWS == gemm::kBM, "A tile");
-    const int c = k0 >> 6, z = c >> 2, fi = c & 3;
-    const float* src = fi == 0 ? f0 : (fi == 1 ? f1 : (fi == 2 ? f2 : f3));
-    float sc = 0.f;
-    if (sprev) sc = __ldg(sprev + fi);
-    if (amax) sc = fmaxf(sc, __uint_as_float(__ldg(amax + fi)));
-    const int r = tid >> 1, half = tid & 1;
-    const long long b = r0 + r;
-    float4 v[8];
-    if (b < nblk) {
-      const long long bx = b % NBx, t = b / NBx;
-      const long long by = t % NBy, bz = t / NBy;
-      const size_t base =
-          ((size_t)(8 * bz + z) * ny + (size_t)(8 * by)) * nx + (size_t)(8 * bx) + 4 * half;
-#pragma unroll
-      for (int y = 0; y < 8; ++y)
-        v[y] = __ldg(reinterpret_cast<const float4*>(src + base + (size_t)y * nx));
-    } else {
-#pragma unroll
-      for (int y = 0; y < 8; ++y) v[y] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    const bool live = sc > 0.f;
-#pragma unroll
-    for (int y = 0; y < 8; ++y) {
-      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-      if (live) {
-        a0 = __fdiv_rn(v[y].x, sc);
-        a1 = __fdiv_rn(v[y].y, sc);
-        a2 = __fdiv_rn(v[y].z, sc);
-        a3 = __fdiv_rn(v[y].w, sc);
-      }
-      uint2 p = make_uint2(gemm::pack_bf16(a0, a1), gemm::pack_bf16(a2, a3));
-      *reinterpret_cast<uint2*>(tile + (r >> 3) * 1024 + y * 128 + (r & 7) * 16 + half * 8) = p;
-    }
-  }
-};
-
-// ---------------------------------------------------------------------------------
 // Epilogues
 // ---------------------------------------------------------------------------------
 // H[row][col..] = bf16(gelu(acc + bias))
@@ -218,6 +167,19 @@ struct RowsStrain {
 
 using LdKLin = gemm::LdK16<gemm::RowsLinear>;
 
+bool ensure_X(Codec* c, size_t rows) {
+  if (c->X_rows >= rows) return true;
+  if (c->X) cudaFree(c->X);
+  c->X = nullptr;
+  c->X_rows = 0;
+  if (cudaMalloc(&c->X, rows * kNIn * sizeof(uint16_t)) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  c->X_rows = rows;
+  return true;
+}
+
 bool ensure_H(Codec* c, size_t rows) {
   if (c->H_rows >= rows) return true;
   if (c->H) cudaFree(c->H);
@@ -287,7 +249,8 @@ Codec* codec_new(int n_lat) {
        cudaMalloc(&c->W2t, nl * kNHid * 2) == cudaSuccess &&
        cudaMalloc(&c->W3t, nl * kNHid * 2) == cudaSuccess &&
        cudaMalloc(&c->W4t, (size_t)kNIn * kNHid * 2) == cudaSuccess &&
-       cudaMalloc(&c->err, sizeof(int)) == cudaSuccess;
+       cudaMalloc(&c->err, sizeof(int)) == cudaSuccess &&
+       cudaMalloc(&c->sc_tmp, 4 * sizeof(float)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     codec_free(c);
@@ -306,6 +269,8 @@ void codec_free(Codec* c) {
   cudaFree(c->W3t);
   cudaFree(c->W4t);
   cudaFree(c->H);
+  cudaFree(c->X);
+  cudaFree(c->sc_tmp);
   cudaFree(c->err);
   if (c->train) train_state_free(c->train);
   delete c;
@@ -313,7 +278,8 @@ void codec_free(Codec* c) {
 
 int codec_nlat(const Codec* c) { return c->n_lat; }
 size_t codec_device_bytes(const Codec* c) {
-  return c->bytes + c->H_rows * kNHid * 2 + (c->train ? train_state_bytes(c->train) : 0);
+  return c->bytes + c->H_rows * kNHid * 2 + c->X_rows * kNIn * 2 +
+         (c->train ? train_state_bytes(c->train) : 0);
 }
 bool codec_ready(const Codec* c) { return c && c->ready; }
 
@@ -346,31 +312,23 @@ cudaError_t codec_get_weights(const Codec* c, float* const w[8]) {
   return e;
 }
 
+cudaError_t snapshot_pack(const float* const f[4], int nx, int ny, int nz, const float* scale,
+                          uint16_t* out, cudaStream_t s);
+
 cudaError_t codec_encode_grid(Codec* c, const float* const f[4], int nx, int ny, int nz,
                               const float* scale_prev, const unsigned* amax, float* scale_out,
                               uint16_t* lat, int* overflow, cudaStream_t s) {
   const int NBx = nx / 8, NBy = ny / 8, NBz = nz / 8;
   const long long nb = (long long)NBx * NBy * NBz;
-  if (!ensure_H(c, (size_t)nb)) return cudaErrorMemoryAllocation;
-  LdGrid al{f[0], f[1], f[2], f[3], nx, ny, NBx, NBy, nb, scale_prev, amax};
-  LdKLin bl{c->W1t, gemm::RowsLinear{kNIn}, kNHid, kNIn};
-  EpBiasGeluH ep{c->w[1], c->H, nb};
-  cudaError_t e = gemm::launch<256, true>(nb, kNHid, kNIn, al, bl, ep, c->err, s);
+  if (!ensure_X(c, (size_t)nb)) return cudaErrorMemoryAllocation;
+  // s_f = max(prev, amax): the scales this state is normalised with (kept for decoding)
+  float* sc = scale_out ? scale_out : c->sc_tmp;
+  update_scale_kernel<<<1, 4, 0, s>>>(scale_prev, amax, sc);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (scale_out) {
-    // s_f = max(prev, amax) for later decodes (same values the loader used)
-    update_scale_kernel<<<1, 4, 0, s>>>(scale_prev, amax, scale_out);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  const int nl = c->n_lat;
-  LdKLin a2{c->H, gemm::RowsLinear{kNHid}, nb, kNHid};
-  LdKLin b2{c->W2t, gemm::RowsLinear{kNHid}, nl, kNHid};
-  EpLatent e2{c->w[3], lat, nl, nb, overflow};
-  if (nl == 64)
-    e = gemm::launch<64, true>(nb, nl, kNHid, a2, b2, e2, c->err, s);
-  else
-    e = gemm::launch<32, true>(nb, nl, kNHid, a2, b2, e2, c->err, s);
-  return e;
+  // normalised BF16 block vectors (the packing of Algorithm 1), then the encoder GEMMs
+  if ((e = snapshot_pack(f, nx, ny, nz, sc, c->X, s)) != cudaSuccess) return e;
+  return codec_encode_vectors(c, c->X, nb, lat, overflow, s);
 }
 
 cudaError_t codec_encode_vectors(Codec* c, const uint16_t* vec, long long n, uint16_t* lat,

@@ -19,9 +19,12 @@ struct Codec {
   uint16_t* W2t = nullptr;
   uint16_t* W3t = nullptr;
   uint16_t* W4t = nullptr;
-  // workspace: hidden activations H [rows][512] bf16
+  // workspace: hidden activations H [rows][512] bf16, packed inputs X [rows][2048] bf16
   uint16_t* H = nullptr;
   size_t H_rows = 0;
+  uint16_t* X = nullptr;
+  size_t X_rows = 0;
+  float* sc_tmp = nullptr;
   int* err = nullptr;
   size_t bytes = 0;
   // training state (allocated by the training unit)

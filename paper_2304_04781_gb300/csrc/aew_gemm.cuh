@@ -1,12 +1,18 @@
 // Generic tcgen05 GEMM building block for the codec and its training:
 //   D[M][N] = sum_k A(m, k) B(n, k)      (FP32 accumulate in TMEM)
-// with pluggable operand loaders (global memory -> canonical K-major shared-memory
-// tiles) and epilogues (TMEM -> registers -> fused bias / activation / store).
+// A and B are 16-bit (BF16 or FP16) matrices with K contiguous in global memory,
+// D goes through a pluggable epilogue (TMEM -> registers -> fused bias / activation /
+// store).
 //
-// CTA tile: 128 rows (one TMEM lane per row) x BN columns, K in chunks of 64, two
-// shared-memory stages so that the loads of chunk c+1 overlap the MMAs of chunk c.
-// One thread issues the MMAs (4 K-steps of 16 per chunk) and commits them to the
-// stage's mbarrier; all waits are bounded in time and set an error flag on timeout.
+// CTA tile: 128 rows (one TMEM lane per row) x BN columns, K in chunks of 64 through a
+// ring of `ns` shared-memory stages.  Warp-specialised:
+//   warps 0-3  producers: cp.async (16-byte, zero-filling) of the A and B chunks into
+//              the canonical K-major layout, then the epilogue;
+//   warp 4     TMEM allocation and, on one lane, the MMA issue loop;
+// synchronised by mbarriers: full[s] (128 producer arrivals once chunk data has landed
+// and been made visible to the async proxy) and empty[s] (tcgen05.commit once the MMAs
+// reading stage s are done).  Every wait is bounded in time; on timeout the kernel
+// drains its own copies, sets an error flag and returns.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -22,22 +28,36 @@ namespace gemm {
 
 constexpr int kBM = 128;
 constexpr int kBK = 64;
-constexpr int kStages = 2;
-constexpr int kThreads = 256;
+constexpr int kProducers = 128;
+constexpr int kThreads = 160;
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s
-
-// byte offset of element (r, k) of a kBK-wide tile in the canonical layout
-__device__ __forceinline__ uint32_t tile_off(int r, int k) {
-  return (uint32_t)((r >> 3) * 1024 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
-}
+constexpr int kSmemBudget = 200 * 1024;
 
 template <int BN>
-constexpr size_t smem_bytes() {
-  return (size_t)kStages * (kBM * kBK * 2 + BN * kBK * 2) + 128 + 1024;
+__host__ __device__ constexpr int stage_bytes() {
+  return kBM * kBK * 2 + BN * kBK * 2;
+}
+template <int BN>
+__host__ __device__ constexpr int max_stages() {
+  return kSmemBudget / stage_bytes<BN>() > 8 ? 8 : kSmemBudget / stage_bytes<BN>();
+}
+inline size_t smem_bytes_for(int stage_b, int ns) { return (size_t)ns * stage_b + 256 + 1024; }
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
 }
 
 // ---------------------------------------------------------------------------------
-// Loader: 16-bit matrix with K contiguous, row r at base + row_off(r).
+// Operand: 16-bit matrix with K contiguous, row r at base + row_off(r).
 // ---------------------------------------------------------------------------------
 struct RowsLinear {
   long long ld;
@@ -50,33 +70,22 @@ struct LdK16 {
   RowFn rows;
   long long R;  // valid rows
   int K;        // valid K (multiple of 8)
+  // issue the cp.async copies of one NROWS x 64 chunk (t = producer thread 0..127)
   template <int NROWS>
-  __device__ __forceinline__ void load(uint8_t* tile, long long r0, int k0, int tid) const {
-    const int warp = tid >> 5, lane = tid & 31;
-    constexpr int NG = NROWS / 8;                 // row groups of 8
-    constexpr int IT = (NG + 7) / 8;              // per warp
-    uint4 v[IT][2];
+  __device__ __forceinline__ void issue(uint8_t* tile, long long r0, int k0, int t) const {
+    const int warp = t >> 5, lane = t & 31;
+    constexpr int NG = NROWS / 8;
+    const uint32_t base = tc::smem_u32(tile) + (lane & 7) * 16;
 #pragma unroll
-    for (int it = 0; it < IT; ++it) {
-      const int g = warp + 8 * it;
+    for (int g = warp; g < NG; g += 4) {
       const long long gr = r0 + g * 8 + (lane & 7);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int k = k0 + ((lane >> 3) + 4 * h) * 8;
-        v[it][h] = make_uint4(0u, 0u, 0u, 0u);
-        if (g < NG && gr < R && k < K)
-          v[it][h] = __ldg(reinterpret_cast<const uint4*>(p + rows(gr) + k));
-      }
-    }
-#pragma unroll
-    for (int it = 0; it < IT; ++it) {
-      const int g = warp + 8 * it;
-      if (g < NG) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int kc = (lane >> 3) + 4 * h;
-          *reinterpret_cast<uint4*>(tile + g * 1024 + kc * 128 + (lane & 7) * 16) = v[it][h];
-        }
+        const int kc = (lane >> 3) + 4 * h;
+        const int k = k0 + kc * 8;
+        const bool ok = gr < R && k < K;
+        const uint16_t* src = ok ? p + rows(gr) + k : p;
+        cp_async16(base + g * 1024 + kc * 128, src, ok ? 16u : 0u);
       }
     }
   }
@@ -105,33 +114,41 @@ __device__ __forceinline__ float gelu_prime_f(float a) {
 // The kernel
 // ---------------------------------------------------------------------------------
 template <int BN, bool BF16, class AL, class BL, class EP>
-__global__ void __launch_bounds__(kThreads) gemm_kernel(long long M, int N, int K, AL al, BL bl,
-                                                        EP ep, int* err) {
+__global__ void __launch_bounds__(kThreads) gemm_kernel(long long M, int N, int K, int ns, AL al,
+                                                        BL bl, EP ep, int* err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   constexpr int A_BYTES = kBM * kBK * 2;
-  constexpr int B_BYTES = BN * kBK * 2;
-  constexpr int STAGE = A_BYTES + B_BYTES;
+  constexpr int STAGE = stage_bytes<BN>();
   constexpr uint32_t TCOLS = BN < 32 ? 32 : BN;
   constexpr int NSUB = BN > 256 ? BN / 256 : 1;
   constexpr int NMMA = BN > 256 ? 256 : BN;
   constexpr uint32_t IDESC = tc::idesc_f16(kBM, NMMA, BF16);
   static_assert(BN % 32 == 0 && BN <= 512, "BN");
 
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + kStages * STAGE);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + kStages);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + ns * STAGE);
+  uint64_t* empty = full + ns;
+  uint64_t* done = empty + ns;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  int* abort_flag = reinterpret_cast<int*>(tslot + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long m0 = (long long)blockIdx.y * kBM;
   const int n0 = blockIdx.x * BN;
+  const int nK = (K + kBK - 1) / kBK;
 
-  if (warp == 0) {
+  if (warp == 4) {
     tc::tmem_alloc(tc::smem_u32(tslot), TCOLS);
     tc::tmem_relinquish();
   }
-  if (tid == 32) {
-    for (int s = 0; s < kStages; ++s) tc::mbar_init(tc::smem_u32(&mbar[s]), 1);
+  if (tid == 0) {
+    for (int s = 0; s < ns; ++s) {
+      tc::mbar_init(tc::smem_u32(&full[s]), kProducers);
+      tc::mbar_init(tc::smem_u32(&empty[s]), 1);
+    }
+    tc::mbar_init(tc::smem_u32(done), 1);
+    *abort_flag = 0;
     tc::mbar_fence_init();
   }
   tc::fence_before_sync();
@@ -139,24 +156,46 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(long long M, int N, int 
   tc::fence_after_sync();
   const uint32_t tmem = *tslot;
 
-  const int nK = (K + kBK - 1) / kBK;
-  bool ok = true;
-  for (int c = 0; c < nK; ++c) {
-    const int s = c % kStages;
-    uint8_t* sa = smem + s * STAGE;
-    uint8_t* sb = sa + A_BYTES;
-    if (c >= kStages) ok = tc::mbar_wait(tc::smem_u32(&mbar[s]), ((c / kStages) - 1) & 1, kWaitNs);
-    if (__syncthreads_or(!ok)) {
-      ok = false;
-      break;
+  if (warp < 4) {
+    // ------------------------------------------------------------- producers
+    const int D = ns >= 3 ? 2 : ns - 1;   // chunks kept in flight beyond the newest
+    int c = 0;
+    for (; c < nK; ++c) {
+      const int s = c % ns;
+      if (c >= ns && !tc::mbar_wait(tc::smem_u32(&empty[s]), ((c / ns) - 1) & 1, kWaitNs)) {
+        atomicExch(abort_flag, 1);
+        break;
+      }
+      if (*reinterpret_cast<volatile int*>(abort_flag)) break;
+      uint8_t* sa = smem + s * STAGE;
+      al.template issue<kBM>(sa, m0, c * kBK, tid);
+      bl.template issue<BN>(sa + A_BYTES, n0, c * kBK, tid);
+      cp_async_commit();
+      if (c >= D) {
+        if (D == 2) cp_async_wait<2>();
+        else if (D == 1) cp_async_wait<1>();
+        else cp_async_wait<0>();
+        tc::fence_proxy_async();
+        mbar_arrive(tc::smem_u32(&full[(c - D) % ns]));
+      }
     }
-    al.template load<kBM>(sa, m0, c * kBK, tid);
-    bl.template load<BN>(sb, n0, c * kBK, tid);
+    cp_async_wait<0>();
     tc::fence_proxy_async();
-    __syncthreads();
-    if (tid == 0) {
+    if (c == nK) {
+      for (int q = (nK - D > 0 ? nK - D : 0); q < nK; ++q) mbar_arrive(tc::smem_u32(&full[q % ns]));
+    }
+  } else if (lane == 0) {
+    // ------------------------------------------------------------- MMA issuer
+    bool ok = true;
+    for (int c = 0; c < nK; ++c) {
+      const int s = c % ns;
+      if (!tc::mbar_wait(tc::smem_u32(&full[s]), (c / ns) & 1, kWaitNs)) {
+        atomicExch(abort_flag, 1);
+        ok = false;
+        break;
+      }
       tc::fence_after_sync();
-      const uint32_t a0 = tc::smem_u32(sa), b0 = tc::smem_u32(sb);
+      const uint32_t a0 = tc::smem_u32(smem + s * STAGE), b0 = a0 + A_BYTES;
 #pragma unroll
       for (int kk = 0; kk < kBK / 16; ++kk) {
 #pragma unroll
@@ -166,49 +205,49 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(long long M, int N, int 
           tc::mma_f16(tmem + h * 256, ad, bd, IDESC, (c > 0 || kk > 0) ? 1u : 0u);
         }
       }
-      tc::mma_commit(tc::smem_u32(&mbar[s]));
+      tc::mma_commit(tc::smem_u32(&empty[s]));
     }
+    if (ok) tc::mma_commit(tc::smem_u32(done));
   }
-  if (ok && nK > 0) {
-    const int cl = nK - 1;
-    ok = tc::mbar_wait(tc::smem_u32(&mbar[cl % kStages]), (cl / kStages) & 1, kWaitNs);
-  }
-  ok = !__syncthreads_or(!ok);
-  tc::fence_after_sync();
-  if (ok) {
-    const int q = warp & 3, hh = warp >> 2;
-    const long long row = m0 + q * 32 + lane;
-    constexpr int CPW = BN >= 64 ? BN / 2 : BN;
-    if (BN >= 64 || hh == 0) {
+
+  // ------------------------------------------------------------- epilogue
+  if (warp < 4) {
+    bool ok = tc::mbar_wait(tc::smem_u32(done), 0, kWaitNs) && nK > 0;
+    tc::fence_after_sync();
+    if (ok && !*reinterpret_cast<volatile int*>(abort_flag)) {
+      const long long row = m0 + warp * 32 + lane;
 #pragma unroll 1
-      for (int cc = 0; cc < CPW; cc += 32) {
-        const int col = (BN >= 64 ? hh * (BN / 2) : 0) + cc;
+      for (int col = 0; col < BN; col += 32) {
         float v[32];
-        tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col, v);
+        tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)col, v);
         ep(row, n0 + col, v);
       }
+    } else if (lane == 0) {
+      atomicExch(err, 1);
     }
-  } else if (tid == 0) {
-    atomicExch(err, 1);
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, TCOLS);
+  if (warp == 4) tc::tmem_dealloc(tmem, TCOLS);
 }
 
 template <int BN, bool BF16, class AL, class BL, class EP>
 cudaError_t launch(long long M, int N, int K, const AL& al, const BL& bl, const EP& ep, int* err,
                    cudaStream_t s) {
   auto kern = gemm_kernel<BN, BF16, AL, BL, EP>;
-  const size_t smem = smem_bytes<BN>();
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int nK = (K + kBK - 1) / kBK;
+  int ns = max_stages<BN>();
+  if (ns > nK) ns = nK < 1 ? 1 : nK;
+  const size_t smem = smem_bytes_for(stage_bytes<BN>(), ns);
+  static size_t configured = 0;
+  if (configured < smem) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_bytes_for(stage_bytes<BN>(), max_stages<BN>()));
     if (e != cudaSuccess) return e;
-    configured = true;
+    configured = smem_bytes_for(stage_bytes<BN>(), max_stages<BN>());
   }
   const dim3 grid((N + BN - 1) / BN, (unsigned)((M + kBM - 1) / kBM));
-  kern<<<grid, kThreads, smem, s>>>(M, N, K, al, bl, ep, err);
+  kern<<<grid, kThreads, smem, s>>>(M, N, K, ns, al, bl, ep, err);
   return cudaGetLastError();
 }
 

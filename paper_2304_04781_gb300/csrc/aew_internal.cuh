@@ -73,7 +73,7 @@ enum { kAccFirst = 1, kAccLast = 2 };
 
 cudaError_t launch_fwd_step(const FwdStep& a, bool incremental, cudaStream_t s);
 cudaError_t launch_adj_step(const AdjStep& a, cudaStream_t s);
-int default_kc(int nx, int ny, int nz);
+int default_kc(int nx, int ny, int nz, bool adjoint);
 
 // ------------------------------------------------------------------------------
 // Reductions and elementwise helpers (aew_reduce.cu)

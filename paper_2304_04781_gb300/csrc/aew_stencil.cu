@@ -76,7 +76,7 @@ __device__ __forceinline__ float hmax4(float4 a) {
 // Forward-type step
 // ---------------------------------------------------------------------------------
 template <bool INCR, bool AMAX>
-__global__ void __launch_bounds__(NTHR) fwd_step_kernel(const FwdStep a) {
+__global__ void __launch_bounds__(NTHR, 3) fwd_step_kernel(const FwdStep a) {
   __shared__ float4 sme[2][TY + 2][W4 + 2];
   __shared__ float4 svy[TY][W4];
   __shared__ float sred[4][TY];
@@ -285,7 +285,7 @@ __device__ __forceinline__ float4 lupd4(float dth, float4 hi, float4 lo, float4 
                      lupd(dth, hi.z, lo.z, l.z), lupd(dth, hi.w, lo.w, l.w));
 }
 
-__global__ void __launch_bounds__(NTHR) adj_step_kernel(const AdjStep a) {
+__global__ void __launch_bounds__(NTHR, 3) adj_step_kernel(const AdjStep a) {
   __shared__ float4 smu[2][TY + 2][W4 + 2];
   __shared__ float4 sly[TY][W4];
 
@@ -449,27 +449,27 @@ __global__ void __launch_bounds__(NTHR) adj_step_kernel(const AdjStep a) {
 
 }  // namespace
 
-int default_kc(int nx, int ny, int nz) {
-  // Split z so that all CTAs are resident at once (one full wave): resident CTAs =
-  // SMs x CTAs per SM of the heaviest step kernel.
+int default_kc(int nx, int ny, int nz, bool adjoint) {
+  // Split z so that all CTAs of a step kernel are resident at once (one full wave):
+  // resident CTAs = SMs x CTAs per SM of that kernel.
   const long long cxy = (long long)((nx + kTXW - 1) / kTXW) * ((ny + TY - 1) / TY);
   int dev = 0, sms = 152, per_sm = 3;
   if (cudaGetDevice(&dev) == cudaSuccess) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int a = 0, b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, adj_step_kernel, NTHR, 0) == cudaSuccess &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fwd_step_kernel<true, false>, NTHR, 0) ==
-            cudaSuccess)
-      per_sm = a < b ? a : b;
+    int a = 0;
+    cudaError_t e = adjoint
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, adj_step_kernel, NTHR, 0)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, fwd_step_kernel<true, false>, NTHR, 0);
+    if (e == cudaSuccess && a > 0) per_sm = a;
     cudaGetLastError();
   }
-  if (per_sm < 1) per_sm = 1;
   const long long resident = (long long)sms * per_sm;
   long long nzc = resident / cxy;
   if (nzc < 1) nzc = 1;
   if (nzc > nz) nzc = nz;
   int kc = (int)((nz + nzc - 1) / nzc);
-  if (const char* env = getenv("AEW_STENCIL_KC")) {   // tuning override
+  // tuning override (planes per CTA)
+  if (const char* env = getenv(adjoint ? "AEW_STENCIL_KC_ADJ" : "AEW_STENCIL_KC_FWD")) {
     const int v = atoi(env);
     if (v > 0) kc = v;
   }
