@@ -83,16 +83,22 @@ _SIGS = [
 
 
 def library_path() -> str:
-    return _build.LIB
+    return os.environ.get("AEW_LIBRARY") or _build.LIB
 
 
 def lib():
-    """Load libaewave.so (building it first if it is missing or stale)."""
+    """Load libaewave.so (building it first if it is missing or stale).
+
+    The environment variable AEW_LIBRARY may name another build of the same library
+    (for A/B comparisons of build options); it is loaded as is."""
     global _LIB
     if _LIB is None:
-        if not _build.up_to_date():
-            _build.build()
-        L = ctypes.CDLL(_build.LIB)
+        path = os.environ.get("AEW_LIBRARY")
+        if not path:
+            if not _build.up_to_date():
+                _build.build()
+            path = _build.LIB
+        L = ctypes.CDLL(path)
         for name, res, args in _SIGS:
             f = getattr(L, name)
             f.restype = res

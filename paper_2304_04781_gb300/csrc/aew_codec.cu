@@ -13,6 +13,7 @@
 // strain columns inside the adjoint) -> +b4, times s_e, scattered back to the grid.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cudaTypedefs.h>
 
 #include <cstring>
 #include <vector>
@@ -158,14 +159,6 @@ struct EpVec {
   }
 };
 
-// rows of W4t holding the strain outputs: e-output n = z*64 + j -> vector index z*256 + j
-struct RowsStrain {
-  __device__ __forceinline__ long long operator()(long long r) const {
-    return ((r >> 6) * 256 + (r & 63)) * (long long)kNHid;
-  }
-};
-
-using LdKLin = gemm::LdK16<gemm::RowsLinear>;
 
 bool ensure_X(Codec* c, size_t rows) {
   if (c->X_rows >= rows) return true;
@@ -223,6 +216,13 @@ __global__ void snapshot_pack_kernel(const float* f0, const float* f1, const flo
       make_uint4(pk[0], pk[1], pk[2], pk[3]);
 }
 
+// strain rows of W4t (vector index z*256 + j, j < 64) packed as W4e [512][512]
+__global__ void strain_rows_kernel(const uint16_t* __restrict__ W4t, uint16_t* __restrict__ W4e) {
+  const int r = blockIdx.x, k = threadIdx.x;
+  const int src = (r >> 6) * 256 + (r & 63);
+  for (int q = k; q < kNHid; q += blockDim.x) W4e[(size_t)r * kNHid + q] = W4t[(size_t)src * kNHid + q];
+}
+
 __global__ void update_scale_kernel(const float* p, const unsigned* a, float* o) {
   const int i = threadIdx.x;
   float v = p ? p[i] : 0.f;
@@ -233,6 +233,34 @@ __global__ void update_scale_kernel(const float* p, const unsigned* a, float* o)
 }  // namespace
 
 // =================================================================================
+namespace gemm {
+
+CUresult make_tmap(CUtensorMap* map, const void* base, bool fp16, long long rows, int K,
+                   long long ld, int box_rows, bool swizzle128) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        fn == nullptr || q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return CUDA_ERROR_NOT_FOUND;
+    }
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const cuuint32_t box[2] = {swizzle128 ? 64u : 8u, (cuuint32_t)box_rows};
+  const cuuint32_t es[2] = {1, 1};
+  return encode(map, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+}
+
+}  // namespace gemm
+
 Codec* codec_new(int n_lat) {
   Codec* c = new Codec();
   c->n_lat = n_lat;
@@ -249,6 +277,7 @@ Codec* codec_new(int n_lat) {
        cudaMalloc(&c->W2t, nl * kNHid * 2) == cudaSuccess &&
        cudaMalloc(&c->W3t, nl * kNHid * 2) == cudaSuccess &&
        cudaMalloc(&c->W4t, (size_t)kNIn * kNHid * 2) == cudaSuccess &&
+       cudaMalloc(&c->W4e, (size_t)512 * kNHid * 2) == cudaSuccess &&
        cudaMalloc(&c->err, sizeof(int)) == cudaSuccess &&
        cudaMalloc(&c->sc_tmp, 4 * sizeof(float)) == cudaSuccess;
   if (!ok) {
@@ -268,6 +297,7 @@ void codec_free(Codec* c) {
   cudaFree(c->W2t);
   cudaFree(c->W3t);
   cudaFree(c->W4t);
+  cudaFree(c->W4e);
   cudaFree(c->H);
   cudaFree(c->X);
   cudaFree(c->sc_tmp);
@@ -290,7 +320,9 @@ cudaError_t codec_refresh(Codec* c, cudaStream_t s) {
   if ((e = transpose16(c->w[0], kNIn, kNHid, c->W1t, false, s)) != cudaSuccess) return e;
   if ((e = transpose16(c->w[2], kNHid, nl, c->W2t, false, s)) != cudaSuccess) return e;
   if ((e = transpose16(c->w[4], nl, kNHid, c->W3t, true, s)) != cudaSuccess) return e;
-  return transpose16(c->w[6], kNHid, kNIn, c->W4t, false, s);
+  if ((e = transpose16(c->w[6], kNHid, kNIn, c->W4t, false, s)) != cudaSuccess) return e;
+  strain_rows_kernel<<<512, 128, 0, s>>>(c->W4t, c->W4e);
+  return cudaGetLastError();
 }
 
 cudaError_t codec_set_weights(Codec* c, const float* const w[8]) {
@@ -334,15 +366,13 @@ cudaError_t codec_encode_grid(Codec* c, const float* const f[4], int nx, int ny,
 cudaError_t codec_encode_vectors(Codec* c, const uint16_t* vec, long long n, uint16_t* lat,
                                  int* overflow, cudaStream_t s) {
   if (!ensure_H(c, (size_t)n)) return cudaErrorMemoryAllocation;
-  LdKLin al{vec, gemm::RowsLinear{kNIn}, n, kNIn};
-  LdKLin bl{c->W1t, gemm::RowsLinear{kNIn}, kNHid, kNIn};
   EpBiasGeluH ep{c->w[1], c->H, n};
-  cudaError_t e = gemm::launch<256, true>(n, kNHid, kNIn, al, bl, ep, c->err, s);
+  cudaError_t e = gemm::launch<256, true>(n, kNHid, kNIn, gemm::Mat{vec, n, kNIn},
+                                          gemm::Mat{c->W1t, kNHid, kNIn}, ep, c->err, s);
   if (e != cudaSuccess) return e;
   const int nl = c->n_lat;
-  LdKLin a2{c->H, gemm::RowsLinear{kNHid}, n, kNHid};
-  LdKLin b2{c->W2t, gemm::RowsLinear{kNHid}, nl, kNHid};
   EpLatent e2{c->w[3], lat, nl, n, overflow};
+  const gemm::Mat a2{c->H, n, kNHid}, b2{c->W2t, nl, kNHid};
   if (nl == 64) return gemm::launch<64, true>(n, nl, kNHid, a2, b2, e2, c->err, s);
   return gemm::launch<32, true>(n, nl, kNHid, a2, b2, e2, c->err, s);
 }
@@ -350,10 +380,9 @@ cudaError_t codec_encode_vectors(Codec* c, const uint16_t* vec, long long n, uin
 static cudaError_t decode_hidden(Codec* c, const uint16_t* lat, long long nb, cudaStream_t s) {
   if (!ensure_H(c, (size_t)nb)) return cudaErrorMemoryAllocation;
   const int nl = c->n_lat;
-  LdKLin a1{lat, gemm::RowsLinear{nl}, nb, nl};
-  LdKLin b1{c->W3t, gemm::RowsLinear{nl}, kNHid, nl};
   EpBiasGeluH ep{c->w[5], c->H, nb};
-  return gemm::launch<256, false>(nb, kNHid, nl, a1, b1, ep, c->err, s);
+  return gemm::launch<256, false>(nb, kNHid, nl, gemm::Mat{lat, nb, nl},
+                                  gemm::Mat{c->W3t, kNHid, nl}, ep, c->err, s);
 }
 
 cudaError_t codec_decode_grid_e(Codec* c, const uint16_t* lat, int nx, int ny, int nz,
@@ -362,20 +391,18 @@ cudaError_t codec_decode_grid_e(Codec* c, const uint16_t* lat, int nx, int ny, i
   const long long nb = (long long)NBx * NBy * NBz;
   cudaError_t e = decode_hidden(c, lat, nb, s);
   if (e != cudaSuccess) return e;
-  LdKLin a2{c->H, gemm::RowsLinear{kNHid}, nb, kNHid};
-  gemm::LdK16<RowsStrain> b2{c->W4t, RowsStrain{}, 512, kNHid};
   EpDecGrid ep{c->w[7], scale_e, e_out, nx, ny, nz, NBx, NBy, nb};
-  return gemm::launch<256, true>(nb, 512, kNHid, a2, b2, ep, c->err, s);
+  return gemm::launch<256, true>(nb, 512, kNHid, gemm::Mat{c->H, nb, kNHid},
+                                 gemm::Mat{c->W4e, 512, kNHid}, ep, c->err, s);
 }
 
 cudaError_t codec_decode_vectors(Codec* c, const uint16_t* lat, long long nvec, float* out,
                                  cudaStream_t s) {
   cudaError_t e = decode_hidden(c, lat, nvec, s);
   if (e != cudaSuccess) return e;
-  LdKLin a2{c->H, gemm::RowsLinear{kNHid}, nvec, kNHid};
-  LdKLin b2{c->W4t, gemm::RowsLinear{kNHid}, kNIn, kNHid};
   EpVec ep{c->w[7], out, kNIn, nvec};
-  return gemm::launch<256, true>(nvec, kNIn, kNHid, a2, b2, ep, c->err, s);
+  return gemm::launch<256, true>(nvec, kNIn, kNHid, gemm::Mat{c->H, nvec, kNHid},
+                                 gemm::Mat{c->W4t, kNIn, kNHid}, ep, c->err, s);
 }
 
 cudaError_t snapshot_pack(const float* const f[4], int nx, int ny, int nz, const float* scale,

@@ -19,6 +19,7 @@ struct Codec {
   uint16_t* W2t = nullptr;
   uint16_t* W3t = nullptr;
   uint16_t* W4t = nullptr;
+  uint16_t* W4e = nullptr;   // the 512 strain rows of W4t, [512][512]
   // workspace: hidden activations H [rows][512] bf16, packed inputs X [rows][2048] bf16
   uint16_t* H = nullptr;
   size_t H_rows = 0;

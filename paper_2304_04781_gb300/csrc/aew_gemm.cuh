@@ -1,20 +1,23 @@
 // Generic tcgen05 GEMM building block for the codec and its training:
 //   D[M][N] = sum_k A(m, k) B(n, k)      (FP32 accumulate in TMEM)
-// A and B are 16-bit (BF16 or FP16) matrices with K contiguous in global memory,
-// D goes through a pluggable epilogue (TMEM -> registers -> fused bias / activation /
-// store).
+// A and B are 16-bit (BF16 or FP16) row-major matrices with K contiguous, described by
+// TMA tensor maps; D goes through a pluggable epilogue (TMEM -> registers -> fused
+// bias / activation / store).
 //
 // CTA tile: 128 rows (one TMEM lane per row) x BN columns, K in chunks of 64 through a
-// ring of `ns` shared-memory stages.  Warp-specialised:
-//   warps 0-3  producers: cp.async (16-byte, zero-filling) of the A and B chunks into
-//              the canonical K-major layout, then the epilogue;
-//   warp 4     TMEM allocation and, on one lane, the MMA issue loop;
-// synchronised by mbarriers: full[s] (128 producer arrivals once chunk data has landed
-// and been made visible to the async proxy) and empty[s] (tcgen05.commit once the MMAs
-// reading stage s are done).  Every wait is bounded in time; on timeout the kernel
-// drains its own copies, sets an error flag and returns.
+// ring of `ns` shared-memory stages.  Four warps:
+//   warp 0, one lane  TMA producer: per chunk one cp.async.bulk.tensor per operand
+//                      (128-byte-swizzled tile; or, with SW = false, eight 16-byte-wide
+//                      boxes into the unswizzled canonical layout), completion counted
+//                      in bytes on the stage's `full` mbarrier;
+//   warp 1, one lane  MMA issuer: 4 x tcgen05.mma (K = 16) per chunk, then
+//                      tcgen05.commit to the stage's `empty` mbarrier;
+//   warp 2            TMEM allocation / release;
+//   warps 0-3         epilogue, one TMEM lane quarter each, after the `done` mbarrier.
+// Every wait is bounded in time; on timeout the kernel records an error and returns.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -28,8 +31,7 @@ namespace gemm {
 
 constexpr int kBM = 128;
 constexpr int kBK = 64;
-constexpr int kProducers = 128;
-constexpr int kThreads = 160;
+constexpr int kThreads = 128;
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s
 constexpr int kSmemBudget = 200 * 1024;
 
@@ -43,53 +45,41 @@ __host__ __device__ constexpr int max_stages() {
 }
 inline size_t smem_bytes_for(int stage_b, int ns) { return (size_t)ns * stage_b + 256 + 1024; }
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes)
+// ---------------------------------------------------------------------------------
+// TMA
+// ---------------------------------------------------------------------------------
+// Tensor map of a row-major 16-bit matrix [rows][K] (row stride ld elements); box =
+// (64 K x box_rows) with 128-byte swizzle, or (8 K x box_rows) unswizzled.
+CUresult make_tmap(CUtensorMap* map, const void* base, bool fp16, long long rows, int K,
+                   long long ld, int box_rows, bool swizzle128);
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(mbar)
+      : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes)
                : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+__device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
-// ---------------------------------------------------------------------------------
-// Operand: 16-bit matrix with K contiguous, row r at base + row_off(r).
-// ---------------------------------------------------------------------------------
-struct RowsLinear {
-  long long ld;
-  __device__ __forceinline__ long long operator()(long long r) const { return r * ld; }
-};
-
-template <class RowFn>
-struct LdK16 {
-  const uint16_t* p;
-  RowFn rows;
-  long long R;  // valid rows
-  int K;        // valid K (multiple of 8)
-  // issue the cp.async copies of one NROWS x 64 chunk (t = producer thread 0..127)
-  template <int NROWS>
-  __device__ __forceinline__ void issue(uint8_t* tile, long long r0, int k0, int t) const {
-    const int warp = t >> 5, lane = t & 31;
-    constexpr int NG = NROWS / 8;
-    const uint32_t base = tc::smem_u32(tile) + (lane & 7) * 16;
-#pragma unroll
-    for (int g = warp; g < NG; g += 4) {
-      const long long gr = r0 + g * 8 + (lane & 7);
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int kc = (lane >> 3) + 4 * h;
-        const int k = k0 + kc * 8;
-        const bool ok = gr < R && k < K;
-        const uint16_t* src = ok ? p + rows(gr) + k : p;
-        cp_async16(base + g * 1024 + kc * 128, src, ok ? 16u : 0u);
-      }
-    }
-  }
-};
+// shared-memory descriptor of a K-major tile with 128-byte swizzle: rows of 128 bytes,
+// 8-row groups 1024 bytes apart; K steps of 16 elements advance the start by 32 bytes
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;                 // leading byte offset (unused when swizzled)
+  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                 // fixed 0b001
+  d |= (uint64_t)2 << 61;                 // 128-byte swizzle
+  return d;
+}
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   __nv_bfloat162 t = __floats2bfloat162_rn(a, b);
@@ -113,19 +103,19 @@ __device__ __forceinline__ float gelu_prime_f(float a) {
 // ---------------------------------------------------------------------------------
 // The kernel
 // ---------------------------------------------------------------------------------
-template <int BN, bool BF16, class AL, class BL, class EP>
-__global__ void __launch_bounds__(kThreads) gemm_kernel(long long M, int N, int K, int ns, AL al,
-                                                        BL bl, EP ep, int* err) {
+template <int BN, bool BF16, bool SW, class EP>
+__global__ void __launch_bounds__(kThreads) gemm_kernel(const __grid_constant__ CUtensorMap ta,
+                                                        const __grid_constant__ CUtensorMap tb,
+                                                        int K, int ns, EP ep, int* err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   constexpr int A_BYTES = kBM * kBK * 2;
-  constexpr int STAGE = stage_bytes<BN>();
+  constexpr int B_BYTES = BN * kBK * 2;
+  constexpr int STAGE = A_BYTES + B_BYTES;
   constexpr uint32_t TCOLS = BN < 32 ? 32 : BN;
-  constexpr int NSUB = BN > 256 ? BN / 256 : 1;
-  constexpr int NMMA = BN > 256 ? 256 : BN;
-  constexpr uint32_t IDESC = tc::idesc_f16(kBM, NMMA, BF16);
-  static_assert(BN % 32 == 0 && BN <= 512, "BN");
+  constexpr uint32_t IDESC = tc::idesc_f16(kBM, BN, BF16);
+  static_assert(BN % 32 == 0 && BN <= 256, "BN");
 
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + ns * STAGE);
   uint64_t* empty = full + ns;
@@ -134,17 +124,19 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(long long M, int N, int 
   int* abort_flag = reinterpret_cast<int*>(tslot + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const long long m0 = (long long)blockIdx.y * kBM;
+  const int m0 = blockIdx.y * kBM;
   const int n0 = blockIdx.x * BN;
   const int nK = (K + kBK - 1) / kBK;
 
-  if (warp == 4) {
+  if (warp == 2) {
     tc::tmem_alloc(tc::smem_u32(tslot), TCOLS);
     tc::tmem_relinquish();
   }
   if (tid == 0) {
+    prefetch_tmap(&ta);
+    prefetch_tmap(&tb);
     for (int s = 0; s < ns; ++s) {
-      tc::mbar_init(tc::smem_u32(&full[s]), kProducers);
+      tc::mbar_init(tc::smem_u32(&full[s]), 1);
       tc::mbar_init(tc::smem_u32(&empty[s]), 1);
     }
     tc::mbar_init(tc::smem_u32(done), 1);
@@ -156,35 +148,29 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(long long M, int N, int 
   tc::fence_after_sync();
   const uint32_t tmem = *tslot;
 
-  if (warp < 4) {
-    // ------------------------------------------------------------- producers
-    const int D = ns >= 3 ? 2 : ns - 1;   // chunks kept in flight beyond the newest
-    int c = 0;
-    for (; c < nK; ++c) {
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------------------- TMA producer
+    for (int c = 0; c < nK; ++c) {
       const int s = c % ns;
       if (c >= ns && !tc::mbar_wait(tc::smem_u32(&empty[s]), ((c / ns) - 1) & 1, kWaitNs)) {
         atomicExch(abort_flag, 1);
         break;
       }
-      if (*reinterpret_cast<volatile int*>(abort_flag)) break;
-      uint8_t* sa = smem + s * STAGE;
-      al.template issue<kBM>(sa, m0, c * kBK, tid);
-      bl.template issue<BN>(sa + A_BYTES, n0, c * kBK, tid);
-      cp_async_commit();
-      if (c >= D) {
-        if (D == 2) cp_async_wait<2>();
-        else if (D == 1) cp_async_wait<1>();
-        else cp_async_wait<0>();
-        tc::fence_proxy_async();
-        mbar_arrive(tc::smem_u32(&full[(c - D) % ns]));
+      const uint32_t fb = tc::smem_u32(&full[s]);
+      const uint32_t sa = tc::smem_u32(smem + s * STAGE), sb = sa + A_BYTES;
+      mbar_expect_tx(fb, STAGE);
+      if (SW) {
+        tma_load_2d(sa, &ta, c * kBK, m0, fb);
+        tma_load_2d(sb, &tb, c * kBK, n0, fb);
+      } else {
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+          tma_load_2d(sa + g * (kBM * 16), &ta, c * kBK + 8 * g, m0, fb);
+          tma_load_2d(sb + g * (BN * 16), &tb, c * kBK + 8 * g, n0, fb);
+        }
       }
     }
-    cp_async_wait<0>();
-    tc::fence_proxy_async();
-    if (c == nK) {
-      for (int q = (nK - D > 0 ? nK - D : 0); q < nK; ++q) mbar_arrive(tc::smem_u32(&full[q % ns]));
-    }
-  } else if (lane == 0) {
+  } else if (warp == 1 && lane == 0) {
     // ------------------------------------------------------------- MMA issuer
     bool ok = true;
     for (int c = 0; c < nK; ++c) {
@@ -198,56 +184,74 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(long long M, int N, int 
       const uint32_t a0 = tc::smem_u32(smem + s * STAGE), b0 = a0 + A_BYTES;
 #pragma unroll
       for (int kk = 0; kk < kBK / 16; ++kk) {
-#pragma unroll
-        for (int h = 0; h < NSUB; ++h) {
-          const uint64_t ad = tc::sdesc(a0 + kk * 256, 128, 1024);
-          const uint64_t bd = tc::sdesc(b0 + h * (256 / 8) * 1024 + kk * 256, 128, 1024);
-          tc::mma_f16(tmem + h * 256, ad, bd, IDESC, (c > 0 || kk > 0) ? 1u : 0u);
+        uint64_t ad, bd;
+        if (SW) {
+          ad = sdesc_sw128(a0 + kk * 32);
+          bd = sdesc_sw128(b0 + kk * 32);
+        } else {
+          ad = tc::sdesc(a0 + kk * 2 * (kBM * 16), kBM * 16, 128);
+          bd = tc::sdesc(b0 + kk * 2 * (BN * 16), BN * 16, 128);
         }
+        tc::mma_f16(tmem, ad, bd, IDESC, (c > 0 || kk > 0) ? 1u : 0u);
       }
       tc::mma_commit(tc::smem_u32(&empty[s]));
     }
     if (ok) tc::mma_commit(tc::smem_u32(done));
   }
+  __syncwarp();
 
   // ------------------------------------------------------------- epilogue
-  if (warp < 4) {
-    bool ok = tc::mbar_wait(tc::smem_u32(done), 0, kWaitNs) && nK > 0;
-    tc::fence_after_sync();
-    if (ok && !*reinterpret_cast<volatile int*>(abort_flag)) {
-      const long long row = m0 + warp * 32 + lane;
+  const bool ok = tc::mbar_wait(tc::smem_u32(done), 0, kWaitNs) && nK > 0;
+  tc::fence_after_sync();
+  if (ok && !*reinterpret_cast<volatile int*>(abort_flag)) {
+    const long long row = (long long)m0 + warp * 32 + lane;
 #pragma unroll 1
-      for (int col = 0; col < BN; col += 32) {
-        float v[32];
-        tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)col, v);
-        ep(row, n0 + col, v);
-      }
-    } else if (lane == 0) {
-      atomicExch(err, 1);
+    for (int col = 0; col < BN; col += 32) {
+      float v[32];
+      tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)col, v);
+      ep(row, n0 + col, v);
     }
+  } else if (lane == 0) {
+    atomicExch(err, 1);
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 4) tc::tmem_dealloc(tmem, TCOLS);
+  if (warp == 2) tc::tmem_dealloc(tmem, TCOLS);
 }
 
-template <int BN, bool BF16, class AL, class BL, class EP>
-cudaError_t launch(long long M, int N, int K, const AL& al, const BL& bl, const EP& ep, int* err,
+// Operand description for launch(): row-major [rows][K] 16-bit matrix, row stride ld.
+struct Mat {
+  const void* p;
+  long long rows;
+  long long ld;
+};
+
+#ifndef AEW_GEMM_SWIZZLE
+#define AEW_GEMM_SWIZZLE 1
+#endif
+
+template <int BN, bool BF16, class EP>
+cudaError_t launch(long long M, int N, int K, const Mat& A, const Mat& B, const EP& ep, int* err,
                    cudaStream_t s) {
-  auto kern = gemm_kernel<BN, BF16, AL, BL, EP>;
+  constexpr bool SW = AEW_GEMM_SWIZZLE != 0;
+  auto kern = gemm_kernel<BN, BF16, SW, EP>;
   const int nK = (K + kBK - 1) / kBK;
   int ns = max_stages<BN>();
   if (ns > nK) ns = nK < 1 ? 1 : nK;
   const size_t smem = smem_bytes_for(stage_bytes<BN>(), ns);
-  static size_t configured = 0;
-  if (configured < smem) {
+  static bool configured = false;
+  if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem_bytes_for(stage_bytes<BN>(), max_stages<BN>()));
     if (e != cudaSuccess) return e;
-    configured = smem_bytes_for(stage_bytes<BN>(), max_stages<BN>());
+    configured = true;
   }
+  CUtensorMap ta, tb;
+  if (make_tmap(&ta, A.p, !BF16, A.rows, K, A.ld, kBM, SW) != CUDA_SUCCESS ||
+      make_tmap(&tb, B.p, !BF16, B.rows, K, B.ld, BN, SW) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
   const dim3 grid((N + BN - 1) / BN, (unsigned)((M + kBM - 1) / kBM));
-  kern<<<grid, kThreads, smem, s>>>(M, N, K, ns, al, bl, ep, err);
+  kern<<<grid, kThreads, smem, s>>>(ta, tb, K, ns, ep, err);
   return cudaGetLastError();
 }
 

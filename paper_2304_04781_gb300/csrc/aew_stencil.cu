@@ -450,27 +450,13 @@ __global__ void __launch_bounds__(NTHR, 3) adj_step_kernel(const AdjStep a) {
 }  // namespace
 
 int default_kc(int nx, int ny, int nz, bool adjoint) {
-  // Split z so that all CTAs of a step kernel are resident at once (one full wave):
-  // resident CTAs = SMs x CTAs per SM of that kernel.
-  const long long cxy = (long long)((nx + kTXW - 1) / kTXW) * ((ny + TY - 1) / TY);
-  int dev = 0, sms = 152, per_sm = 3;
-  if (cudaGetDevice(&dev) == cudaSuccess) {
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int a = 0;
-    cudaError_t e = adjoint
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, adj_step_kernel, NTHR, 0)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, fwd_step_kernel<true, false>, NTHR, 0);
-    if (e == cudaSuccess && a > 0) per_sm = a;
-    cudaGetLastError();
-  }
-  const long long resident = (long long)sms * per_sm;
-  long long nzc = resident / cxy;
-  if (nzc < 1) nzc = 1;
-  if (nzc > nz) nzc = nz;
-  int kc = (int)((nz + nzc - 1) / nzc);
-  // tuning override (planes per CTA)
+  // z planes per CTA: short chunks give many CTAs (several waves, good balance) at the
+  // cost of re-reading one plane per chunk; 8 measured best at 256^3 on GB300.
+  (void)nx;
+  (void)ny;
+  int kc = nz < 8 ? nz : 8;
   if (const char* env = getenv(adjoint ? "AEW_STENCIL_KC_ADJ" : "AEW_STENCIL_KC_FWD")) {
-    const int v = atoi(env);
+    const int v = atoi(env);   // tuning override
     if (v > 0) kc = v;
   }
   return kc < 1 ? 1 : kc;

@@ -294,10 +294,9 @@ int nblk(size_t n) {
   return b < 1 ? 1 : (int)b;
 }
 
-using LdKLin = gemm::LdK16<gemm::RowsLinear>;
-
-LdKLin ld(const uint16_t* p, long long ldim, long long rows, int K) {
-  return LdKLin{p, gemm::RowsLinear{ldim}, rows, K};
+gemm::Mat ld(const uint16_t* p, long long ldim, long long rows, int K) {
+  (void)K;
+  return gemm::Mat{p, rows, ldim};
 }
 
 #define TCK(x)                              \
