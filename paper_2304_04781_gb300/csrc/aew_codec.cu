@@ -192,28 +192,29 @@ bool ensure_H(Codec* c, size_t rows) {
 __global__ void snapshot_pack_kernel(const float* f0, const float* f1, const float* f2,
                                      const float* f3, int nx, int ny, int NBx, int NBy,
                                      long long nblk, const float* scale, uint16_t* out) {
-  // one thread per (block, z, f, y): 8 values
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= nblk * 256) return;
-  const int y = (int)(t & 7), f = (int)((t >> 3) & 3), z = (int)((t >> 5) & 7);
-  const long long b = t >> 8;
-  const float* src = f == 0 ? f0 : (f == 1 ? f1 : (f == 2 ? f2 : f3));
-  const float sc = scale[f];
-  const long long bx = b % NBx, r = b / NBx;
-  const long long by = r % NBy, bz = r / NBy;
-  const size_t base = ((size_t)(8 * bz + z) * ny + (size_t)(8 * by + y)) * nx + (size_t)(8 * bx);
-  const float4 a = *reinterpret_cast<const float4*>(src + base);
-  const float4 c = *reinterpret_cast<const float4*>(src + base + 4);
-  float q[8] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w};
-  uint32_t pk[4];
-#pragma unroll
-  for (int i = 0; i < 8; i += 2) {
-    const float u0 = sc > 0.f ? __fdiv_rn(q[i], sc) : 0.f;
-    const float u1 = sc > 0.f ? __fdiv_rn(q[i + 1], sc) : 0.f;
-    pk[i / 2] = gemm::pack_bf16(u0, u1);
+  // One thread per float4 of a grid row; consecutive threads read consecutive x
+  // (coalesced) and write 8-byte pieces of the block vectors.
+  const int xq_n = nx >> 2;
+  const long long total = nblk / NBx * 256LL * xq_n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int xq = (int)(t % xq_n);
+    long long r = t / xq_n;
+    const int y = (int)(r & 7), f = (int)((r >> 3) & 3), z = (int)((r >> 5) & 7);
+    const long long slab = r >> 8;               // (bz, by)
+    const long long by = slab % NBy, bz = slab / NBy;
+    const float* src = f == 0 ? f0 : (f == 1 ? f1 : (f == 2 ? f2 : f3));
+    const float sc = scale[f];
+    const float4 a = *reinterpret_cast<const float4*>(
+        src + ((size_t)(8 * bz + z) * ny + (size_t)(8 * by + y)) * nx + 4 * (size_t)xq);
+    const float u0 = sc > 0.f ? __fdiv_rn(a.x, sc) : 0.f;
+    const float u1 = sc > 0.f ? __fdiv_rn(a.y, sc) : 0.f;
+    const float u2 = sc > 0.f ? __fdiv_rn(a.z, sc) : 0.f;
+    const float u3 = sc > 0.f ? __fdiv_rn(a.w, sc) : 0.f;
+    const long long b = slab * NBx + (xq >> 1);
+    *reinterpret_cast<uint2*>(out + b * kNIn + z * 256 + f * 64 + y * 8 + 4 * (xq & 1)) =
+        make_uint2(gemm::pack_bf16(u0, u1), gemm::pack_bf16(u2, u3));
   }
-  *reinterpret_cast<uint4*>(out + b * kNIn + z * 256 + f * 64 + y * 8) =
-      make_uint4(pk[0], pk[1], pk[2], pk[3]);
 }
 
 // strain rows of W4t (vector index z*256 + j, j < 64) packed as W4e [512][512]
@@ -409,8 +410,10 @@ cudaError_t snapshot_pack(const float* const f[4], int nx, int ny, int nz, const
                           uint16_t* out, cudaStream_t s) {
   const int NBx = nx / 8, NBy = ny / 8, NBz = nz / 8;
   const long long nb = (long long)NBx * NBy * NBz;
-  const long long threads = nb * 256;
-  snapshot_pack_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+  const long long threads = nb * 256 * 2;
+  long long blocks = (threads + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  snapshot_pack_kernel<<<(unsigned)blocks, 256, 0, s>>>(
       f[0], f[1], f[2], f[3], nx, ny, NBx, NBy, nb, scale, out);
   return cudaGetLastError();
 }

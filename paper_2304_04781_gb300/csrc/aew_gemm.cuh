@@ -4,16 +4,19 @@
 // TMA tensor maps; D goes through a pluggable epilogue (TMEM -> registers -> fused
 // bias / activation / store).
 //
-// CTA tile: 128 rows (one TMEM lane per row) x BN columns, K in chunks of 64 through a
-// ring of `ns` shared-memory stages.  Four warps:
-//   warp 0, one lane  TMA producer: per chunk one cp.async.bulk.tensor per operand
+// Persistent CTAs (one per SM) walk 128 x BN output tiles; K runs in chunks of 64
+// through a ring of `ns` shared-memory stages.  Ten warps:
+//   warp 8, one lane  TMA producer: per chunk one cp.async.bulk.tensor per operand
 //                      (128-byte-swizzled tile; or, with SW = false, eight 16-byte-wide
 //                      boxes into the unswizzled canonical layout), completion counted
 //                      in bytes on the stage's `full` mbarrier;
-//   warp 1, one lane  MMA issuer: 4 x tcgen05.mma (K = 16) per chunk, then
-//                      tcgen05.commit to the stage's `empty` mbarrier;
-//   warp 2            TMEM allocation / release;
-//   warps 0-3         epilogue, one TMEM lane quarter each, after the `done` mbarrier.
+//   warp 9            TMEM allocation (two BN-column accumulators) and, on one lane,
+//                      the MMA issuer: 4 x tcgen05.mma (K = 16) per chunk,
+//                      tcgen05.commit to the stage's `empty` mbarrier, and per tile to
+//                      the accumulator's `accf` mbarrier;
+//   warps 0-7         epilogue (two warps per TMEM lane quarter, one column half each),
+//                      which drains accumulator a while the MMAs fill the other one,
+//                      then arrives on `acce[a]`.
 // Every wait is bounded in time; on timeout the kernel records an error and returns.
 #pragma once
 
@@ -31,7 +34,11 @@ namespace gemm {
 
 constexpr int kBM = 128;
 constexpr int kBK = 64;
-constexpr int kThreads = 128;
+constexpr int kEpiWarps = 8;                 // warps 0-7: epilogue
+constexpr int kEpiThreads = kEpiWarps * 32;
+constexpr int kTmaWarp = 8;
+constexpr int kMmaWarp = 9;
+constexpr int kThreads = 320;
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s
 constexpr int kSmemBudget = 200 * 1024;
 
@@ -101,34 +108,36 @@ __device__ __forceinline__ float gelu_prime_f(float a) {
 }
 
 // ---------------------------------------------------------------------------------
-// The kernel
+// The kernel (persistent: each CTA walks tiles blockIdx.x, +gridDim.x, ...)
 // ---------------------------------------------------------------------------------
 template <int BN, bool BF16, bool SW, class EP>
-__global__ void __launch_bounds__(kThreads) gemm_kernel(const __grid_constant__ CUtensorMap ta,
-                                                        const __grid_constant__ CUtensorMap tb,
-                                                        int K, int ns, EP ep, int* err) {
+__global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant__ CUtensorMap ta,
+                                                           const __grid_constant__ CUtensorMap tb,
+                                                           int M, int N, int K, int ns, EP ep,
+                                                           int* err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   constexpr int A_BYTES = kBM * kBK * 2;
   constexpr int B_BYTES = BN * kBK * 2;
   constexpr int STAGE = A_BYTES + B_BYTES;
-  constexpr uint32_t TCOLS = BN < 32 ? 32 : BN;
+  constexpr uint32_t TCOLS = 2 * BN < 32 ? 32 : 2 * BN;   // two accumulators
   constexpr uint32_t IDESC = tc::idesc_f16(kBM, BN, BF16);
   static_assert(BN % 32 == 0 && BN <= 256, "BN");
 
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + ns * STAGE);
   uint64_t* empty = full + ns;
-  uint64_t* done = empty + ns;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* accf = empty + ns;     // accumulator a ready for the epilogue
+  uint64_t* acce = accf + 2;       // accumulator a drained by the epilogue
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(acce + 2);
   int* abort_flag = reinterpret_cast<int*>(tslot + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.y * kBM;
-  const int n0 = blockIdx.x * BN;
   const int nK = (K + kBK - 1) / kBK;
+  const int tn = (N + BN - 1) / BN;
+  const int T = ((M + kBM - 1) / kBM) * tn;
 
-  if (warp == 2) {
+  if (warp == kMmaWarp) {
     tc::tmem_alloc(tc::smem_u32(tslot), TCOLS);
     tc::tmem_relinquish();
   }
@@ -139,7 +148,10 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(const __grid_constant__ 
       tc::mbar_init(tc::smem_u32(&full[s]), 1);
       tc::mbar_init(tc::smem_u32(&empty[s]), 1);
     }
-    tc::mbar_init(tc::smem_u32(done), 1);
+    for (int a = 0; a < 2; ++a) {
+      tc::mbar_init(tc::smem_u32(&accf[a]), 1);
+      tc::mbar_init(tc::smem_u32(&acce[a]), kEpiThreads);
+    }
     *abort_flag = 0;
     tc::mbar_fence_init();
   }
@@ -148,75 +160,108 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(const __grid_constant__ 
   tc::fence_after_sync();
   const uint32_t tmem = *tslot;
 
-  if (warp == 0 && lane == 0) {
-    // ------------------------------------------------------------- TMA producer
-    for (int c = 0; c < nK; ++c) {
-      const int s = c % ns;
-      if (c >= ns && !tc::mbar_wait(tc::smem_u32(&empty[s]), ((c / ns) - 1) & 1, kWaitNs)) {
-        atomicExch(abort_flag, 1);
-        break;
-      }
-      const uint32_t fb = tc::smem_u32(&full[s]);
-      const uint32_t sa = tc::smem_u32(smem + s * STAGE), sb = sa + A_BYTES;
-      mbar_expect_tx(fb, STAGE);
-      if (SW) {
-        tma_load_2d(sa, &ta, c * kBK, m0, fb);
-        tma_load_2d(sb, &tb, c * kBK, n0, fb);
-      } else {
+  if (warp == kTmaWarp) {
+    if (lane == 0) {
+      // ----------------------------------------------------------- TMA producer
+      int it = 0;
+      for (int t = blockIdx.x; t < T; t += gridDim.x) {
+        const int m0 = (t / tn) * kBM, n0 = (t % tn) * BN;
+        for (int c = 0; c < nK; ++c, ++it) {
+          const int s = it % ns;
+          if (it >= ns && !tc::mbar_wait(tc::smem_u32(&empty[s]), ((it / ns) - 1) & 1, kWaitNs)) {
+            atomicExch(abort_flag, 1);
+            t = T;
+            break;
+          }
+          const uint32_t fb = tc::smem_u32(&full[s]);
+          const uint32_t sa = tc::smem_u32(smem + s * STAGE), sb = sa + A_BYTES;
+          mbar_expect_tx(fb, STAGE);
+          if (SW) {
+            tma_load_2d(sa, &ta, c * kBK, m0, fb);
+            tma_load_2d(sb, &tb, c * kBK, n0, fb);
+          } else {
 #pragma unroll
-        for (int g = 0; g < 8; ++g) {
-          tma_load_2d(sa + g * (kBM * 16), &ta, c * kBK + 8 * g, m0, fb);
-          tma_load_2d(sb + g * (BN * 16), &tb, c * kBK + 8 * g, n0, fb);
+            for (int g = 0; g < 8; ++g) {
+              tma_load_2d(sa + g * (kBM * 16), &ta, c * kBK + 8 * g, m0, fb);
+              tma_load_2d(sb + g * (BN * 16), &tb, c * kBK + 8 * g, n0, fb);
+            }
+          }
         }
       }
     }
-  } else if (warp == 1 && lane == 0) {
-    // ------------------------------------------------------------- MMA issuer
-    bool ok = true;
-    for (int c = 0; c < nK; ++c) {
-      const int s = c % ns;
-      if (!tc::mbar_wait(tc::smem_u32(&full[s]), (c / ns) & 1, kWaitNs)) {
-        atomicExch(abort_flag, 1);
-        ok = false;
-        break;
+    __syncwarp();
+  } else if (warp == kMmaWarp) {
+    if (lane == 0) {
+      // ----------------------------------------------------------- MMA issuer
+      int it = 0, tl = 0;
+      for (int t = blockIdx.x; t < T; t += gridDim.x, ++tl) {
+        const int a = tl & 1;
+        if (tl >= 2 && !tc::mbar_wait(tc::smem_u32(&acce[a]), ((tl >> 1) - 1) & 1, kWaitNs)) {
+          atomicExch(abort_flag, 1);
+          break;
+        }
+        tc::fence_after_sync();
+        const uint32_t acc = tmem + (uint32_t)(a * BN);
+        bool ok = true;
+        for (int c = 0; c < nK; ++c, ++it) {
+          const int s = it % ns;
+          if (!tc::mbar_wait(tc::smem_u32(&full[s]), (it / ns) & 1, kWaitNs)) {
+            atomicExch(abort_flag, 1);
+            ok = false;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t a0 = tc::smem_u32(smem + s * STAGE), b0 = a0 + A_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < kBK / 16; ++kk) {
+            uint64_t ad, bd;
+            if (SW) {
+              ad = sdesc_sw128(a0 + kk * 32);
+              bd = sdesc_sw128(b0 + kk * 32);
+            } else {
+              ad = tc::sdesc(a0 + kk * 2 * (kBM * 16), kBM * 16, 128);
+              bd = tc::sdesc(b0 + kk * 2 * (BN * 16), BN * 16, 128);
+            }
+            tc::mma_f16(acc, ad, bd, IDESC, (c > 0 || kk > 0) ? 1u : 0u);
+          }
+          tc::mma_commit(tc::smem_u32(&empty[s]));
+        }
+        if (!ok) break;
+        tc::mma_commit(tc::smem_u32(&accf[a]));
       }
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------- epilogue warps
+    const int q = warp & 3, hh = warp >> 2;
+    constexpr int CW = BN >= 64 ? BN / 2 : BN;   // columns per warp
+    int tl = 0;
+    for (int t = blockIdx.x; t < T; t += gridDim.x, ++tl) {
+      const int a = tl & 1;
+      const bool ok = tc::mbar_wait(tc::smem_u32(&accf[a]), (tl >> 1) & 1, kWaitNs);
       tc::fence_after_sync();
-      const uint32_t a0 = tc::smem_u32(smem + s * STAGE), b0 = a0 + A_BYTES;
-#pragma unroll
-      for (int kk = 0; kk < kBK / 16; ++kk) {
-        uint64_t ad, bd;
-        if (SW) {
-          ad = sdesc_sw128(a0 + kk * 32);
-          bd = sdesc_sw128(b0 + kk * 32);
-        } else {
-          ad = tc::sdesc(a0 + kk * 2 * (kBM * 16), kBM * 16, 128);
-          bd = tc::sdesc(b0 + kk * 2 * (BN * 16), BN * 16, 128);
-        }
-        tc::mma_f16(tmem, ad, bd, IDESC, (c > 0 || kk > 0) ? 1u : 0u);
+      if (!ok || *reinterpret_cast<volatile int*>(abort_flag)) {
+        if (lane == 0) atomicExch(err, 1);
+        break;
       }
-      tc::mma_commit(tc::smem_u32(&empty[s]));
-    }
-    if (ok) tc::mma_commit(tc::smem_u32(done));
-  }
-  __syncwarp();
-
-  // ------------------------------------------------------------- epilogue
-  const bool ok = tc::mbar_wait(tc::smem_u32(done), 0, kWaitNs) && nK > 0;
-  tc::fence_after_sync();
-  if (ok && !*reinterpret_cast<volatile int*>(abort_flag)) {
-    const long long row = (long long)m0 + warp * 32 + lane;
+      const int m0 = (t / tn) * kBM, n0 = (t % tn) * BN;
+      const long long row = (long long)m0 + q * 32 + lane;
+      if (BN >= 64 || hh == 0) {
 #pragma unroll 1
-    for (int col = 0; col < BN; col += 32) {
-      float v[32];
-      tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)col, v);
-      ep(row, n0 + col, v);
+        for (int cc = 0; cc < CW; cc += 32) {
+          const int col = (BN >= 64 ? hh * CW : 0) + cc;
+          float v[32];
+          tc::tmem_ld32(tmem + (uint32_t)(a * BN) + ((uint32_t)(q * 32) << 16) + (uint32_t)col, v);
+          ep(row, n0 + col, v);
+        }
+      }
+      tc::fence_before_sync();
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&acce[a])) : "memory");
     }
-  } else if (lane == 0) {
-    atomicExch(err, 1);
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 2) tc::tmem_dealloc(tmem, TCOLS);
+  if (warp == kMmaWarp) tc::tmem_dealloc(tmem, TCOLS);
 }
 
 // Operand description for launch(): row-major [rows][K] 16-bit matrix, row stride ld.
@@ -237,21 +282,27 @@ cudaError_t launch(long long M, int N, int K, const Mat& A, const Mat& B, const 
   auto kern = gemm_kernel<BN, BF16, SW, EP>;
   const int nK = (K + kBK - 1) / kBK;
   int ns = max_stages<BN>();
-  if (ns > nK) ns = nK < 1 ? 1 : nK;
+  if (ns > nK + 2) ns = nK + 2;   // a few chunks of the next tile may be in flight
+  if (ns < 2) ns = 2;
   const size_t smem = smem_bytes_for(stage_bytes<BN>(), ns);
+  static int sms = 0;
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem_bytes_for(stage_bytes<BN>(), max_stages<BN>()));
     if (e != cudaSuccess) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     configured = true;
   }
   CUtensorMap ta, tb;
   if (make_tmap(&ta, A.p, !BF16, A.rows, K, A.ld, kBM, SW) != CUDA_SUCCESS ||
       make_tmap(&tb, B.p, !BF16, B.rows, K, B.ld, BN, SW) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
-  const dim3 grid((N + BN - 1) / BN, (unsigned)((M + kBM - 1) / kBM));
-  kern<<<grid, kThreads, smem, s>>>(ta, tb, K, ns, ep, err);
+  const long long tiles = ((M + kBM - 1) / kBM) * (long long)((N + BN - 1) / BN);
+  const int grid = (int)(tiles < sms ? tiles : sms);
+  kern<<<grid, kThreads, smem, s>>>(ta, tb, (int)M, N, K, ns, ep, err);
   return cudaGetLastError();
 }
 
