@@ -47,6 +47,14 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--shape", type=int, nargs=3, default=list(SHAPE))
     p.add_argument("--nt", type=int, default=NT)
+    p.add_argument("--nrec", type=int, default=NREC)
+    p.add_argument("--n-lat", type=int, default=64)
+    p.add_argument("--weights", default="")
+    p.add_argument("--accuracy", action="store_true",
+                   help="instead of timing: AE gradient / GN-HVP errors against full storage "
+                        "(or checkpointing with --ref revolve), decoded-state error")
+    p.add_argument("--ref", default="full", choices=["full", "revolve"])
+    p.add_argument("--hvps", type=int, default=1)
     return p.parse_args()
 
 
@@ -218,12 +226,7 @@ def run_ours(args):
     c_np = inputs.velocity_model(shape, H, seed=seed).astype(np.float32)
     ctrue = inputs.bump_model(c_np.astype(np.float64), H).astype(np.float32)
     c = torch.from_numpy(c_np).cuda()
-    Wt = inputs.codec_init(seed=0)
-    weights = os.path.join(ROOT, "paper_2304_04781_gb300", "weights", "codec_64.npz")
-    trained = os.path.exists(weights)
-    if trained:
-        z = np.load(weights)
-        Wt = {k: z[k] for k in Wt}
+    Wt, trained = load_weights(args.weights or default_weights(64), 64)
 
     ae = aewave.Solver(shape, H, nt, rec, storage="ae")
     ae.codec_set(Wt)
@@ -336,9 +339,107 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def default_weights(n_lat: int) -> str:
+    return os.path.join(ROOT, "paper_2304_04781_gb300", "weights", f"codec_{n_lat}.npz")
+
+
+def load_weights(path: str, n_lat: int):
+    from paper_2304_04781_gb300 import inputs
+    W = inputs.codec_init(seed=0, n_lat=n_lat)
+    if path and os.path.exists(path):
+        z = np.load(path)
+        return {k: z[k] for k in W}, True
+    return W, False
+
+
+def run_accuracy(args):
+    """Errors of the compressed gradient / GN-HVP against an uncompressed reference on
+    the same GPU, decoded-state error, adjoint identity and checkpointing equality at the
+    full size.  Prints one JSON line."""
+    import torch
+    from paper_2304_04781_gb300 import aewave, inputs, train
+    shape, nt = tuple(args.shape), args.nt
+    nz, ny, nx = shape
+    rec = inputs.receiver_grid(nx, ny, args.nrec)
+    W, trained = load_weights(args.weights or default_weights(args.n_lat), args.n_lat)
+    c_np = inputs.velocity_model(shape, H, seed=2).astype(np.float32)
+    c = torch.from_numpy(c_np).cuda()
+    ctrue = torch.from_numpy(inputs.bump_model(c_np.astype(np.float64), H).astype(np.float32)).cuda()
+    dirs = [torch.from_numpy(inputs.direction(shape, H, seed=(20 if args.hvps == 1 else 30) + k)
+                             .astype(np.float32)).cuda() for k in range(args.hvps)]
+    out = {"config": workload(shape, nt), "codec_weights": "trained" if trained else "random-init",
+           "n_lat": args.n_lat, "reference": args.ref}
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    ae = aewave.Solver(shape, H, nt, rec, storage="ae", n_lat=args.n_lat)
+    ae.codec_set(W)
+    d_obs = ae.forward(ctrue)
+    a, b = ev(), ev(); a.record()
+    J_ae, g_ae = ae.gradient(c, d_obs)
+    b.record(); torch.cuda.synchronize()
+    out["ae_gradient_ms"] = a.elapsed_time(b)
+    H_ae, t_hvp = [], []
+    for dc in dirs:
+        a, b = ev(), ev(); a.record()
+        H_ae.append(ae.hessvec(dc).cpu())
+        b.record(); torch.cuda.synchronize()
+        t_hvp.append(a.elapsed_time(b))
+    out["ae_hvp_ms"] = float(np.mean(t_hvp))
+    st = ae.stats()
+    out["ae_memory"] = {"device_bytes": st["device_bytes"], "latent_bytes": st["latent_bytes"],
+                        "torch_peak_bytes": int(torch.cuda.max_memory_allocated())}
+    g_ae = g_ae.cpu()
+    del ae
+    torch.cuda.empty_cache()
+
+    if args.ref == "full":
+        ref = aewave.Solver(shape, H, nt, rec, storage="full")
+    else:
+        ref = aewave.Solver(shape, H, nt, rec, storage="revolve", n_checkpoints=20)
+    a, b = ev(), ev(); a.record()
+    J_ref, g_ref = ref.gradient(c, d_obs)
+    b.record(); torch.cuda.synchronize()
+    out["ref_gradient_ms"] = a.elapsed_time(b)
+    rel = lambda x, y: float(torch.linalg.vector_norm((x - y).double()) / torch.linalg.vector_norm(y.double()))
+    out["misfit"] = {"ae": J_ae, "ref": J_ref}
+    out["gradient_rel_err"] = rel(g_ae, g_ref.cpu())
+    errs, t_ref = [], []
+    for k, dc in enumerate(dirs):
+        a, b = ev(), ev(); a.record()
+        Hr = ref.hessvec(dc).cpu()
+        b.record(); torch.cuda.synchronize()
+        t_ref.append(a.elapsed_time(b))
+        errs.append(rel(H_ae[k], Hr))
+    out["hvp_rel_err"] = errs
+    out["ref_hvp_ms"] = float(np.mean(t_ref))
+    # adjoint identity at the full size: <J dc, r> = <dc, J^T r>
+    d = ref.forward(c)
+    r = torch.randn(d.shape, device="cuda", generator=torch.Generator(device="cuda").manual_seed(5)) * d.abs().max()
+    r[0] = 0
+    _, JTr = ref.gradient(c, (d - r).contiguous())
+    Jdc = ref.jvp(dirs[0])
+    lhs, rhs = aewave.dot(Jdc, r), aewave.dot(dirs[0], JTr)
+    out["adjoint_identity_rel"] = abs(lhs - rhs) / abs(lhs)
+    out["ref_memory_bytes"] = ref.stats()["device_bytes"]
+    del ref
+    torch.cuda.empty_cache()
+
+    # decoded-state error on states of this run (every 50th step)
+    tr = train.make_handle(shape, nt=nt, n_lat=args.n_lat)
+    tr.codec_set(W)
+    every = max(1, nt // 40)
+    snaps, sc = train.generate(tr, [2], every)
+    out["decoded_state_error"] = train.decoded_error(tr, snaps, sc)
+    out["decoded_state_sample"] = f"states n = {every}, {2 * every}, ... of this run, all blocks"
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.accuracy:
+        run_accuracy(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -205,12 +205,12 @@ __global__ void snapshot_pack_kernel(const float* f0, const float* f1, const flo
     const long long by = slab % NBy, bz = slab / NBy;
     const float* src = f == 0 ? f0 : (f == 1 ? f1 : (f == 2 ? f2 : f3));
     const float sc = scale[f];
+    // y = x * (1/s): one correctly rounded reciprocal per field, then a product
+    const float inv = sc > 0.f ? __frcp_rn(sc) : 0.f;
     const float4 a = *reinterpret_cast<const float4*>(
         src + ((size_t)(8 * bz + z) * ny + (size_t)(8 * by + y)) * nx + 4 * (size_t)xq);
-    const float u0 = sc > 0.f ? __fdiv_rn(a.x, sc) : 0.f;
-    const float u1 = sc > 0.f ? __fdiv_rn(a.y, sc) : 0.f;
-    const float u2 = sc > 0.f ? __fdiv_rn(a.z, sc) : 0.f;
-    const float u3 = sc > 0.f ? __fdiv_rn(a.w, sc) : 0.f;
+    const float u0 = __fmul_rn(a.x, inv), u1 = __fmul_rn(a.y, inv);
+    const float u2 = __fmul_rn(a.z, inv), u3 = __fmul_rn(a.w, inv);
     const long long b = slab * NBx + (xq >> 1);
     *reinterpret_cast<uint2*>(out + b * kNIn + z * 256 + f * 64 + y * 8 + 4 * (xq & 1)) =
         make_uint2(gemm::pack_bf16(u0, u1), gemm::pack_bf16(u2, u3));

@@ -73,7 +73,8 @@ def test_decode_matches_oracle(n_lat):
 def test_snapshots_bitwise_match_packing():
     """Algorithm 1: every 10th state packed with the running per-field maximum; the
     BF16 codes are compared bit for bit with a packing of the same FP32 states done on
-    the host (division in FP32, then RNE to BF16, as on the GPU)."""
+    the host (FP32 reciprocal of the scale, FP32 product, then RNE to BF16, the same
+    operations in the same precision as on the GPU)."""
     shape = (32, 32, 32)
     prob, c, _ = setup(shape, 41, 16)
     s = solver(prob, storage="ae")
@@ -91,7 +92,8 @@ def test_snapshots_bitwise_match_packing():
             run_max = np.maximum(run_max, np.array([np.abs(a).max() for a in hs], np.float32))
         X = C.pack_blocks([a.astype(np.float64) for a in hs]).astype(np.float32)
         sv = C.scale_vector(run_max).astype(np.float32)
-        Y = np.where(sv > 0, X / np.where(sv > 0, sv, 1), 0).astype(np.float32)
+        inv = np.where(sv > 0, np.float32(1) / np.where(sv > 0, sv, np.float32(1)), np.float32(0))
+        Y = (X * inv.astype(np.float32)).astype(np.float32)
         want = torch.from_numpy(Y).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
         np.testing.assert_array_equal(got[64 * q: 64 * (q + 1)], want)
 
