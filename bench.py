@@ -165,8 +165,7 @@ def cpu_sample(shape, nt, steps_in_sample=1):
     for n in range(steps_in_sample):
         st = W.forward_step(prob, m, *st, -1.0)
         states.append(st)
-    s4 = C.running_scales(states)
-    ehat = [C.roundtrip_e(Wt, s, s4[k]) for k, s in enumerate(states)]
+    ehat = [C.roundtrip_e(Wt, s) for s in states]
     resid = np.zeros((steps_in_sample + 1, prob.nrec, 3))
     W.adjoint(prob, c, lambda n: ehat[n], resid)
     dt = time.perf_counter() - t0

@@ -12,9 +12,11 @@ used here (and by the CUDA path, as a layout definition) is
     k = z*256 + f*64 + y*8 + x      (x, y, z the node offsets inside the block,
                                      f = 0:e, 1:vx, 2:vy, 3:vz)
 
-Block b = (bz*NBy + by)*NBx + bx.  Each field is divided by its running maximum
-s_f^n = max_{k<=n} max_x |f^k| (the normalisation of Sec. 3.3, in the per-field
-running-max form; a field with s = 0 is identically zero and is fed as 0).
+Block b = (bz*NBy + by)*NBx + bx.  Normalisation (Sec. 3.3: every vector is scaled to
+O(1) before encoding and its scale is kept at higher precision): each field of each
+block is divided by s_{b,f} = 2^e, the power of two with max_x |f| in [s/2, s), so the
+normalised values lie in (-1, 1) and scaling by s is exact in any binary format.  A
+block-field that is identically zero has s = 0 and is fed (and decoded) as 0.
 
 Dense layers act as sigma(y W + b) (Sec. 3.3, Eq. (5)).  Shapes:
     encoder 2048 -> 512 (GELU) -> n_lat (linear),
@@ -114,30 +116,29 @@ def field_columns(f: int) -> np.ndarray:
     return np.concatenate([np.arange(z * 256 + f * 64, z * 256 + f * 64 + 64) for z in range(BLK)])
 
 
-def scale_vector(s4) -> np.ndarray:
-    """Per-entry scale of the 2048-vector from the four field scales."""
-    out = np.empty(NIN)
+def block_scales(fields) -> np.ndarray:
+    """s[b][f] = 2^e with max_{x in block b} |f(x)| = m 2^e, m in [0.5, 1) (0 for a zero
+    block-field); returns [nblocks][4]."""
+    X = np.abs(pack_blocks(fields))
+    s = np.zeros((X.shape[0], NFIELD))
     for f in range(NFIELD):
-        out[field_columns(f)] = s4[f]
-    return out
+        mx = X[:, field_columns(f)].max(axis=1)
+        _, e = np.frexp(mx)
+        s[:, f] = np.where(mx > 0, np.ldexp(1.0, e), 0.0)
+    return s
 
 
-def normalise(X: np.ndarray, s4) -> np.ndarray:
-    """y = x / s_f, with y = 0 for a field whose scale is 0."""
-    sv = scale_vector(s4)
+def normalise(X: np.ndarray, s) -> np.ndarray:
+    """y = x / s_{b,f}; s is [nblocks][4] (per block) or [4] (one scale per field);
+    y = 0 where s = 0."""
+    s = np.asarray(s, dtype=np.float64)
+    if s.ndim == 1:
+        s = np.broadcast_to(s, (X.shape[0], NFIELD))
+    sv = np.empty_like(X)
+    for f in range(NFIELD):
+        sv[:, field_columns(f)] = s[:, f:f + 1]
     safe = np.where(sv > 0, sv, 1.0)
     return np.where(sv > 0, X / safe, 0.0)
-
-
-def running_scales(states) -> np.ndarray:
-    """s[n][f] = max_{k<=n} max |f^k| for a list of states (e, vx, vy, vz)."""
-    s = np.zeros((len(states), NFIELD))
-    cur = np.zeros(NFIELD)
-    for n, st in enumerate(states):
-        for f in range(NFIELD):
-            cur[f] = max(cur[f], float(np.abs(st[f]).max()))
-        s[n] = cur
-    return s
 
 
 # --------------------------------------------------------------------------------------
@@ -175,16 +176,16 @@ def decode(W: dict, Z: np.ndarray, emulate: bool = False, cols=None) -> np.ndarr
     return h @ W4 + b4
 
 
-def roundtrip_e(W: dict, state, s4, emulate: bool = False) -> np.ndarray:
-    """Encode one state with scales s4 and decode its strain field: e-hat (unnormalised).
-
-    The decoded strain is set to 0 on boundary nodes, where the boundary condition of
-    Sec. 2 fixes e = 0 exactly (the stored forward strain is 0 there too)."""
+def roundtrip_e(W: dict, state, emulate: bool = False) -> np.ndarray:
+    """Encode one state (per-block scales) and decode its strain field: e-hat, in physical
+    units, set to 0 on boundary nodes, where the boundary condition of Sec. 2 fixes e = 0
+    exactly (the stored forward strain is 0 there too)."""
     shape = state[0].shape
-    Y = normalise(pack_blocks(state), s4)
+    s = block_scales(state)
+    Y = normalise(pack_blocks(state), s)
     Z = encode(W, Y, emulate)
     cols = field_columns(0)
-    E = decode(W, Z, emulate, cols=cols) * s4[0]
+    E = decode(W, Z, emulate, cols=cols) * s[:, 0:1]
     Xe = np.zeros((E.shape[0], NIN))
     Xe[:, cols] = E
     e = unpack_field(Xe, shape, 0)
@@ -194,9 +195,8 @@ def roundtrip_e(W: dict, state, s4, emulate: bool = False) -> np.ndarray:
 
 
 def compressed_e_history(W: dict, states, emulate: bool = False):
-    """Decoded strain history e-hat^n, n = 0..nt-1, and the scales used."""
-    s = running_scales(states)
-    return [roundtrip_e(W, st, s[n], emulate) for n, st in enumerate(states)], s
+    """Decoded strain history e-hat^n, n = 0..nt-1."""
+    return [roundtrip_e(W, st, emulate) for st in states]
 
 
 # --------------------------------------------------------------------------------------

@@ -48,23 +48,39 @@ def test_block_layout_from_coordinate_encoded_fields():
         np.testing.assert_array_equal(C.unpack_field(X, (nz, ny, nx), f), fields[f])
 
 
-def test_normalise_bounds_and_zero_scale():
-    st = [np.random.default_rng(f).standard_normal((8, 8, 16)) * 10 ** f for f in range(4)]
-    s = C.running_scales([st])[0]
-    Y = C.normalise(C.pack_blocks(st), s)
-    assert np.abs(Y).max() <= 1.0
-    assert np.isclose(np.abs(Y).max(), 1.0)
-    Y0 = C.normalise(C.pack_blocks(st), np.array([0.0, s[1], s[2], s[3]]))
-    assert np.all(Y0[:, C.field_columns(0)] == 0)
-
-
-def test_running_scale_is_monotone_prefix_max():
+def test_block_scales_are_powers_of_two_bracketing_the_block_max():
     rng = np.random.default_rng(3)
-    states = [[rng.standard_normal((8, 8, 8)) * rng.uniform(0, 2) for _ in range(4)] for _ in range(6)]
-    s = C.running_scales(states)
-    assert np.all(np.diff(s, axis=0) >= 0)
+    st = [rng.standard_normal((16, 8, 24)) * 10.0 ** rng.uniform(-20, 5) for _ in range(4)]
+    st[2][:8, :, 8:16] = 0.0                     # one all-zero block-field
+    s = C.block_scales(st)
+    X = C.pack_blocks(st)
+    # brute force: loop over blocks and fields
+    for b in range(X.shape[0]):
+        for f in range(4):
+            m = max(abs(v) for v in X[b, C.field_columns(f)])
+            if m == 0:
+                assert s[b, f] == 0
+            else:
+                e = np.log2(s[b, f])
+                assert e == np.round(e)              # a power of two
+                assert s[b, f] / 2 <= m < s[b, f]
+
+
+def test_normalise_per_block_bounds_and_zero_blocks():
+    rng = np.random.default_rng(4)
+    st = [rng.standard_normal((8, 8, 16)) * 10.0 ** (-3 * f) for f in range(4)]
+    st[1][:, :, :8] = 0.0
+    s = C.block_scales(st)
+    Y = C.normalise(C.pack_blocks(st), s)
     for f in range(4):
-        assert s[-1, f] == max(np.abs(st[f]).max() for st in states)
+        blk = np.abs(Y[:, C.field_columns(f)]).max(axis=1)
+        live = s[:, f] > 0
+        assert np.all((blk[live] >= 0.5) & (blk[live] < 1.0))
+        assert np.all(blk[~live] == 0)
+    # scaling by a power of two commutes with BF16 rounding (exactness of the scale)
+    X = C.pack_blocks(st)
+    sv = C.normalise(np.ones_like(X), s)         # 1/s per entry (0 where s = 0)
+    np.testing.assert_array_equal(C.round_bf16(X) * sv, C.round_bf16(X * sv))
 
 
 def test_gelu_identities():
