@@ -126,6 +126,8 @@ int aew_stats(const aew_handle* h, aew_stats_t* out);
  * Eq. (5)).  Encoder 2048 -> 512 (GELU) -> n_lat; decoder n_lat -> 512 (GELU) -> 2048.
  * Block vector order: k = z*256 + f*64 + y*8 + x, f = 0:e, 1:vx, 2:vy, 3:vz (x, y, z
  * node offsets inside the 8x8x8 block); block b = (bz*NBy + by)*NBx + bx.
+ * Normalisation: each field of each block is divided by its power-of-two scale
+ * (aew_codec_encode), so encoder inputs lie in (-1, 1) whatever the amplitude.
  * Precision: BF16 operands (FP16 for the decoder's first layer, whose input is the
  * FP16 latent) with FP32 accumulation on tcgen05 tensor cores; FP32 biases and GELU.
  * ------------------------------------------------------------------------------- */
@@ -145,10 +147,13 @@ int aew_codec_get(const aew_handle* h, float* W1_host, float* b1_host,
                   float* W4_host, float* b4_host);
 
 /* Encode one state.  fields_dev = {e, vx, vy, vz} device [nz][ny][nx];
- * scale_host[4] = the per-field divisors s_f (0 means the field is fed as 0);
- * latents_dev: device FP16 [nblocks][n_lat] (written). */
-int aew_codec_encode(aew_handle* h, const float* const fields_dev[4], const float* scale_host,
-                     uint16_t* latents_dev, void* stream);
+ * latents_dev: device FP16 [nblocks][n_lat] (written).  Each field of each block is
+ * normalised by its own power-of-two scale s = 2^e, where max |f| over the block is
+ * m 2^e with m in [0.5, 1) (the per-vector normalisation of Sec. 3.3); block_max_dev
+ * (may be NULL): device FP32 [nblocks][4] receiving the block maxima m 2^e from which
+ * the scales follow. */
+int aew_codec_encode(aew_handle* h, const float* const fields_dev[4], uint16_t* latents_dev,
+                     float* block_max_dev, void* stream);
 
 /* Encode normalised block vectors (e.g. training snapshots): vectors_dev = device
  * BF16 bit patterns [n][2048] in the block-vector order above; latents_dev: device
@@ -160,9 +165,11 @@ int aew_codec_encode_vectors(aew_handle* h, const uint16_t* vectors_dev, long lo
  * (all four fields, not multiplied by any scale). */
 int aew_codec_decode(aew_handle* h, const uint16_t* latents_dev, float* out_dev, void* stream);
 
-/* Decode latents to the strain field only: e_dev[nz][ny][nx] = s_e * (decoded e part),
- * with boundary nodes set to 0 (the boundary condition of Sec. 2). */
-int aew_codec_decode_e(aew_handle* h, const uint16_t* latents_dev, float scale_e,
+/* Decode latents to the strain field only: e_dev[nz][ny][nx] = s_b * (decoded strain
+ * part) with the block's power-of-two scale from block_max_dev (device FP32
+ * [nblocks][4], as written by aew_codec_encode; field 0 is used), boundary nodes 0
+ * (the boundary condition of Sec. 2). */
+int aew_codec_decode_e(aew_handle* h, const uint16_t* latents_dev, const float* block_max_dev,
                        float* e_dev, void* stream);
 
 /* ---------------------------------------------------------------------------------
@@ -201,13 +208,13 @@ int aew_jvp(aew_handle* h, const float* dc_dev, float* dd_dev, void* stream);
 
 /* Algorithm 1 (data generation): run the forward solve for c_dev and pack every
  * `every`-th state n (n = every, 2*every, ... < nt) into BF16 block vectors, each
- * field divided by its running maximum.  out_dev: device BF16 (uint16 bit patterns)
- * [max_vectors][2048]; *n_written receives the number of vectors written (at most
- * max_vectors; whole states only).  scales_dev (may be NULL): device FP32 [k][4]
- * receiving the four field scales of each packed state k.  The history storage of
- * the handle is not touched. */
+ * field of each block divided by its power-of-two scale (see aew_codec_encode).
+ * out_dev: device BF16 (uint16 bit patterns) [max_vectors][2048]; *n_written receives
+ * the number of vectors written (whole states only, at most max_vectors).
+ * block_max_dev (may be NULL): device FP32 [max_vectors][4] receiving the block maxima
+ * of each written vector.  The history storage of the handle is not touched. */
 int aew_snapshots(aew_handle* h, const float* c_dev, int every, uint16_t* out_dev,
-                  long long max_vectors, float* scales_dev, long long* n_written,
+                  long long max_vectors, float* block_max_dev, long long* n_written,
                   void* stream);
 
 /* One training step of the codec on a minibatch: batch_dev = BF16 [batch][2048]

@@ -62,10 +62,10 @@ _SIGS = [
     ("aew_stats", c_int, [c_void_p, POINTER(aew_stats_t)]),
     ("aew_codec_set", c_int, [c_void_p] + [c_void_p] * 8),
     ("aew_codec_get", c_int, [c_void_p] + [c_void_p] * 8),
-    ("aew_codec_encode", c_int, [c_void_p, POINTER(c_void_p), POINTER(c_float), c_void_p, c_void_p]),
+    ("aew_codec_encode", c_int, [c_void_p, POINTER(c_void_p), c_void_p, c_void_p, c_void_p]),
     ("aew_codec_encode_vectors", c_int, [c_void_p, c_void_p, c_longlong, c_void_p, c_void_p]),
     ("aew_codec_decode", c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
-    ("aew_codec_decode_e", c_int, [c_void_p, c_void_p, c_float, c_void_p, c_void_p]),
+    ("aew_codec_decode_e", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("aew_forward", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("aew_propagate", c_int, [c_void_p, c_void_p, POINTER(c_void_p), c_int, c_int, c_void_p,
                               c_void_p, c_void_p]),
@@ -269,14 +269,16 @@ class Solver:
         self._check(lib().aew_codec_get(self._h, *[out[k].ctypes.data for k in shapes]))
         return out
 
-    def codec_encode(self, fields, scale) -> torch.Tensor:
+    def codec_encode(self, fields):
+        """Encode one state (e, vx, vy, vz CUDA tensors): returns (FP16 latents
+        [nblocks][n_lat], FP32 block maxima [nblocks][4] that fix the scales)."""
         lat = torch.empty((self.nblocks, self.n_lat), device="cuda", dtype=torch.float16)
+        bmax = torch.empty((self.nblocks, 4), device="cuda", dtype=torch.float32)
         arr = (c_void_p * 4)(*[f.data_ptr() for f in fields])
         for f in fields:
             _ptr(f)
-        s = (c_float * 4)(*[float(x) for x in scale])
-        self._check(lib().aew_codec_encode(self._h, arr, s, _ptr(lat), _stream()))
-        return lat
+        self._check(lib().aew_codec_encode(self._h, arr, _ptr(lat), _ptr(bmax), _stream()))
+        return lat, bmax
 
     def codec_encode_vectors(self, vec: torch.Tensor) -> torch.Tensor:
         """BF16 normalised block vectors [n][2048] -> FP16 latents [n][n_lat]."""
@@ -291,24 +293,26 @@ class Solver:
         self._check(lib().aew_codec_decode(self._h, _ptr(lat), _ptr(out), _stream()))
         return out
 
-    def codec_decode_e(self, lat: torch.Tensor, scale_e: float) -> torch.Tensor:
+    def codec_decode_e(self, lat: torch.Tensor, block_max: torch.Tensor) -> torch.Tensor:
+        """Strain field decoded from latents with the blocks' scales (from block maxima)."""
         e = torch.empty(self.shape, device="cuda", dtype=torch.float32)
-        self._check(lib().aew_codec_decode_e(self._h, _ptr(lat), c_float(scale_e), _ptr(e), _stream()))
+        self._check(lib().aew_codec_decode_e(self._h, _ptr(lat), _ptr(block_max.contiguous()),
+                                             _ptr(e), _stream()))
         return e
 
     def snapshots(self, c: torch.Tensor, every: int, max_vectors: int,
                   out: Optional[torch.Tensor] = None, with_scales: bool = False):
-        """Algorithm 1: BF16 normalised block vectors of every `every`-th state.
+        """Algorithm 1: normalised BF16 block vectors of every `every`-th state.
 
-        Returns the [n][2048] bfloat16 tensor (and the [n / nblocks][4] field scales)."""
+        Returns the [n][2048] bfloat16 tensor (and the [n][4] block maxima)."""
         if out is None:
             out = torch.empty((max_vectors, 2048), device="cuda", dtype=torch.bfloat16)
-        sc = torch.zeros((max(1, max_vectors // self.nblocks), 4), device="cuda") if with_scales else None
+        bm = torch.zeros((max_vectors, 4), device="cuda") if with_scales else None
         n = c_longlong(0)
-        self._check(lib().aew_snapshots(self._h, _ptr(c), every, _ptr(out), max_vectors, _ptr(sc),
+        self._check(lib().aew_snapshots(self._h, _ptr(c), every, _ptr(out), max_vectors, _ptr(bm),
                                         byref(n), _stream()))
         if with_scales:
-            return out[: n.value], sc[: n.value // self.nblocks]
+            return out[: n.value], bm[: n.value]
         return out[: n.value]
 
     def train_step(self, batch: torch.Tensor, lr: float, want_loss: bool = True) -> Optional[float]:

@@ -45,10 +45,9 @@ struct aew_handle {
   double* acc64 = nullptr;
   float* estore = nullptr;
   float* ckpt = nullptr;
+  float* zst[4] = {};   // REVOLVE: the zero initial state
   uint16_t* lat = nullptr;
-  float* edec = nullptr;
-  unsigned* amax = nullptr;
-  float* scales = nullptr;
+  unsigned* bmx = nullptr;   // AE: per step, block and field max |f| (float bits) [nt][nb][4]
   int* ovf = nullptr;
   float* d = nullptr;
   float* R = nullptr;
@@ -57,6 +56,14 @@ struct aew_handle {
   double* part = nullptr;
   aew::FieldCheck* chk = nullptr;
   float* scale_tmp = nullptr;
+  unsigned* bm_tmp = nullptr;    // block maxima of a standalone encode / a snapshot
+  uint16_t* raw_tmp = nullptr;   // raw BF16 block vectors of a snapshot
+  // AE mode: side stream running the codec GEMMs concurrently with the stencil steps,
+  // double-buffered packed inputs and decoded strains, and the events ordering them
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_a[2] = {}, ev_b[2] = {}, ev_sync = nullptr, ev_sync2 = nullptr;
+  uint16_t* xpk[2] = {};
+  float* edb[2] = {};
   std::vector<float> wav;
   bool have_grad = false;
   Codec* codec = nullptr;
@@ -115,8 +122,12 @@ size_t nblocks_of(const aew_handle* h) {
 // Single steps
 // ---------------------------------------------------------------------------------
 int fwd_step(aew_handle* h, int n, float* const in[4], float* const out[4], const float* wav,
-             float* d_row, unsigned* amax, cudaStream_t s) {
+             float* d_row, cudaStream_t s, uint16_t* xpack = nullptr) {
   aew::FwdStep a{};
+  if (xpack) {  // pack the input state n (AE forward, n >= 1) and its block maxima
+    a.xpack = xpack;
+    a.bmax = h->bmx + (size_t)n * nblocks_of(h) * 4;
+  }
   a.m = h->m;
   a.e = in[0];
   a.vx = in[1];
@@ -138,7 +149,6 @@ int fwd_step(aew_handle* h, int n, float* const in[4], float* const out[4], cons
   a.krec = d_row ? h->krec : -1;
   a.rec_map = h->rec_map;
   a.d_out = d_row;
-  a.amax = amax;
   AEW_CK(aew::launch_fwd_step(a, false, s));
   ++h->stats.kernel_launches;
   return AEW_OK;
@@ -269,25 +279,61 @@ float* drow(aew_handle* h, float* d, int n) {
 // ---------------------------------------------------------------------------------
 // AE helpers
 // ---------------------------------------------------------------------------------
-int encode_state(aew_handle* h, int n, float* const f[4], cudaStream_t s) {
+// encoder GEMMs of packed state n (xpk[n % 2]) into latents[n]
+int encode_packed(aew_handle* h, int n, cudaStream_t s) {
   const size_t nb = nblocks_of(h);
-  cudaError_t e = aew::codec_encode_grid(
-      h->codec, f, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->scales + 4 * (size_t)(n - 1),
-      h->amax + 4 * (size_t)n, h->scales + 4 * (size_t)n,
-      h->lat + (size_t)n * nb * h->cfg.n_lat, h->ovf, s);
-  if (e != cudaSuccess) return cuda_fail(h, e, "codec_encode_grid");
-  h->stats.kernel_launches += 4;
+  cudaError_t e = aew::codec_encode_raw(h->codec, h->xpk[n & 1], h->bmx + (size_t)n * nb * 4,
+                                        (long long)nb, h->lat + (size_t)n * nb * h->cfg.n_lat,
+                                        h->ovf, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "codec_encode_raw");
+  h->stats.kernel_launches += 2;
   return AEW_OK;
 }
 
-int decode_e(aew_handle* h, int n, cudaStream_t s) {
+// decoded strain of step n into buf
+int decode_e(aew_handle* h, int n, float* buf, cudaStream_t s) {
   const size_t nb = nblocks_of(h);
   cudaError_t e = aew::codec_decode_grid_e(h->codec, h->lat + (size_t)n * nb * h->cfg.n_lat,
                                            h->cfg.nx, h->cfg.ny, h->cfg.nz,
-                                           h->scales + 4 * (size_t)n, h->edec, s);
+                                           h->bmx + (size_t)n * nb * 4, buf, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "codec_decode_grid_e");
   h->stats.kernel_launches += 2;
   return AEW_OK;
+}
+
+// make stream `to` wait for all work enqueued so far on stream `from`
+int join(aew_handle* h, cudaStream_t from, cudaStream_t to, cudaEvent_t ev) {
+  AEW_CK(cudaEventRecord(ev, from));
+  AEW_CK(cudaStreamWaitEvent(to, ev, 0));
+  return AEW_OK;
+}
+
+// Adjoint sweep in AE mode: the decode of step n-1 runs on the side stream while the
+// adjoint step n runs on s.  edb[m % 2] holds the decoded strain of step m; its
+// previous reader is adjoint step m + 2.  ev_b[m % 2]: decode m done; ev_a[m % 2]:
+// adjoint step m done.
+int ae_adjoint_sweep(aew_handle* h, const float* resid, cudaStream_t s) {
+  const int nt = h->cfg.nt;
+  int rc;
+  if ((rc = begin_adjoint(h, s))) return rc;
+  if ((rc = join(h, s, h->side, h->ev_sync))) return rc;
+  if (nt - 1 >= 1) {
+    if ((rc = decode_e(h, nt - 1, h->edb[(nt - 1) & 1], h->side))) return rc;
+    AEW_CK(cudaEventRecord(h->ev_b[(nt - 1) & 1], h->side));
+  }
+  int acur = 0;
+  for (int n = nt - 1; n >= 0; --n) {
+    if (n - 1 >= 1) {
+      if (n + 1 <= nt - 1) AEW_CK(cudaStreamWaitEvent(h->side, h->ev_a[(n + 1) & 1], 0));
+      if ((rc = decode_e(h, n - 1, h->edb[(n - 1) & 1], h->side))) return rc;
+      AEW_CK(cudaEventRecord(h->ev_b[(n - 1) & 1], h->side));
+    }
+    if (n >= 1) AEW_CK(cudaStreamWaitEvent(s, h->ev_b[n & 1], 0));
+    if ((rc = adj_step(h, n, acur, resid, n >= 1 ? h->edb[n & 1] : nullptr, s))) return rc;
+    AEW_CK(cudaEventRecord(h->ev_a[n & 1], s));
+    acur ^= 1;
+  }
+  return join(h, h->side, s, h->ev_sync2);
 }
 
 // ---------------------------------------------------------------------------------
@@ -305,7 +351,7 @@ int gradient_full(aew_handle* h, const float* d_obs, const float* wav, cudaStrea
     float* eout = (n + 1 < nt) ? h->estore + (size_t)(n + 1) * h->C : h->st[0][0];
     float* in[4] = {h->estore + (size_t)n * h->C, vb[a][0], vb[a][1], vb[a][2]};
     float* out[4] = {eout, vb[a ^ 1][0], vb[a ^ 1][1], vb[a ^ 1][2]};
-    int rc = fwd_step(h, n, in, out, wav, drow(h, h->d, n + 1), nullptr, s);
+    int rc = fwd_step(h, n, in, out, wav, drow(h, h->d, n + 1), s);
     if (rc) return rc;
   }
   int rc = residual_and_misfit(h, d_obs, s);
@@ -322,56 +368,82 @@ int gradient_full(aew_handle* h, const float* d_obs, const float* wav, cudaStrea
   return AEW_OK;
 }
 
-// Execute a checkpointing plan.  mode 0: gradient (first pass records d, 'final'
-// computes the misfit); mode 1: incremental adjoint of the GN-HVP (residual given).
+// Execute a checkpointing plan.  mode gradient: the first pass records d and the
+// 'final' action computes the misfit; otherwise (incremental adjoint of the GN-HVP) the
+// residual is given.  The live state is a set of field pointers: a restore just points
+// at the slot (or at the zero state), and a store is written by the last step of the
+// preceding advance directly into the slot, so no state is ever copied.
 int run_revolve(aew_handle* h, const float* d_obs, const float* resid, const float* wav,
                 bool gradient, cudaStream_t s, long long* fwd_out) {
   const int nt = h->cfg.nt;
   const int ns = h->cfg.n_checkpoints;
   std::vector<aew::RevAction> plan;
   aew::revolve_plan(nt, ns, plan);
-  int cur = 0, live = 0, acur = 0, rc;
+  int live_n = 0, acur = 0, rc;
   long long fwd = 0;
-  if ((rc = zero_state(h, h->st[0], s))) return rc;
+  auto slot = [&](int k, float** f) {
+    for (int i = 0; i < 4; ++i) f[i] = h->ckpt + ((size_t)k * 4 + i) * h->C;
+  };
+  float* live[4];
+  for (int i = 0; i < 4; ++i) live[i] = h->zst[i];
+  int live_buf = -1;  // 0/1: ping-pong buffer, -1: zero state or a slot
   if (gradient) AEW_CK(cudaMemsetAsync(h->d, 0, h->nrow * sizeof(float), s));
   if ((rc = begin_adjoint(h, s))) return rc;
   std::vector<int> slot_step(ns > 0 ? ns : 1, -1);
   const float* R = resid;
-  for (const aew::RevAction& act : plan) {
+  for (size_t a = 0; a < plan.size(); ++a) {
+    const aew::RevAction& act = plan[a];
     switch (act.op) {
-      case aew::kOpAdvance:
+      case aew::kOpAdvance: {
+        const bool to_slot = a + 1 < plan.size() && plan[a + 1].op == aew::kOpStore;
         for (int k = 0; k < act.arg; ++k) {
-          rc = fwd_step(h, live, h->st[cur], h->st[cur ^ 1], wav,
-                        gradient ? drow(h, h->d, live + 1) : nullptr, nullptr, s);
+          float* out[4];
+          int out_buf;
+          if (to_slot && k == act.arg - 1) {
+            slot(plan[a + 1].arg, out);
+            out_buf = -1;
+          } else {
+            out_buf = live_buf == 0 ? 1 : 0;
+            for (int i = 0; i < 4; ++i) out[i] = h->st[out_buf][i];
+          }
+          rc = fwd_step(h, live_n, live, out, wav, gradient ? drow(h, h->d, live_n + 1) : nullptr,
+                        s);
           if (rc) return rc;
-          cur ^= 1;
-          ++live;
+          for (int i = 0; i < 4; ++i) live[i] = out[i];
+          live_buf = out_buf;
+          ++live_n;
           ++fwd;
         }
         break;
+      }
       case aew::kOpStore: {
         float* dst[4];
-        for (int i = 0; i < 4; ++i) dst[i] = h->ckpt + ((size_t)act.arg * 4 + i) * h->C;
-        if ((rc = copy_state(h, dst, h->st[cur], s))) return rc;
-        slot_step[act.arg] = live;
+        slot(act.arg, dst);
+        if (live[0] != dst[0]) {   // not produced in place by the previous advance
+          if ((rc = copy_state(h, dst, live, s))) return rc;
+          for (int i = 0; i < 4; ++i) live[i] = dst[i];
+          live_buf = -1;
+        }
+        slot_step[act.arg] = live_n;
         break;
       }
       case aew::kOpRestore:
         if (act.arg < 0) {
-          if ((rc = zero_state(h, h->st[cur], s))) return rc;
-          live = 0;
+          for (int i = 0; i < 4; ++i) live[i] = h->zst[i];
+          live_n = 0;
         } else {
-          float* src[4];
-          for (int i = 0; i < 4; ++i) src[i] = h->ckpt + ((size_t)act.arg * 4 + i) * h->C;
-          if ((rc = copy_state(h, h->st[cur], src, s))) return rc;
-          live = slot_step[act.arg];
+          slot(act.arg, live);
+          live_n = slot_step[act.arg];
         }
+        live_buf = -1;
         break;
       case aew::kOpFinal:
         if (gradient) {
-          // last step into the other buffer: records d^{nt}, keeps state nt-1 live
-          rc = fwd_step(h, live, h->st[cur], h->st[cur ^ 1], wav, drow(h, h->d, live + 1),
-                        nullptr, s);
+          // last step into a scratch buffer: records d^{nt}, keeps state nt-1 live
+          float* out[4];
+          const int ob = live_buf == 0 ? 1 : 0;
+          for (int i = 0; i < 4; ++i) out[i] = h->st[ob][i];
+          rc = fwd_step(h, live_n, live, out, wav, drow(h, h->d, live_n + 1), s);
           if (rc) return rc;
           ++fwd;
           if ((rc = residual_and_misfit(h, d_obs, s))) return rc;
@@ -379,8 +451,7 @@ int run_revolve(aew_handle* h, const float* d_obs, const float* resid, const flo
         }
         break;
       case aew::kOpReverse:
-        if ((rc = adj_step(h, act.arg, acur, R, act.arg > 0 ? h->st[cur][0] : nullptr, s)))
-          return rc;
+        if ((rc = adj_step(h, act.arg, acur, R, act.arg > 0 ? live[0] : nullptr, s))) return rc;
         acur ^= 1;
         break;
     }
@@ -389,35 +460,34 @@ int run_revolve(aew_handle* h, const float* d_obs, const float* resid, const flo
   return AEW_OK;
 }
 
+// AE gradient: forward step n packs its input state n into xpk[n % 2]; the encoder of
+// state n runs on the side stream while step n + 1 runs on s.  ev_a[n % 2]: step n
+// done; ev_b[n % 2]: encoder of state n done (xpk[n % 2] free again for step n + 2).
 int gradient_ae(aew_handle* h, const float* d_obs, const float* wav, cudaStream_t s) {
   const int nt = h->cfg.nt;
   int rc;
   if ((rc = zero_state(h, h->st[0], s))) return rc;
-  AEW_CK(cudaMemsetAsync(h->amax, 0, (size_t)(nt + 1) * 4 * sizeof(unsigned), s));
-  AEW_CK(cudaMemsetAsync(h->scales, 0, (size_t)(nt + 1) * 4 * sizeof(float), s));
+  AEW_CK(cudaMemsetAsync(h->bmx, 0, (size_t)nt * nblocks_of(h) * 4 * sizeof(unsigned), s));
   AEW_CK(cudaMemsetAsync(h->ovf, 0, sizeof(int), s));
   AEW_CK(cudaMemsetAsync(h->d, 0, h->nrow * sizeof(float), s));
+  if ((rc = join(h, s, h->side, h->ev_sync))) return rc;
   int cur = 0;
   for (int n = 0; n < nt; ++n) {
-    rc = fwd_step(h, n, h->st[cur], h->st[cur ^ 1], wav, drow(h, h->d, n + 1),
-                  h->amax + 4 * (size_t)(n + 1), s);
+    if (n >= 3) AEW_CK(cudaStreamWaitEvent(s, h->ev_b[n & 1], 0));
+    rc = fwd_step(h, n, h->st[cur], h->st[cur ^ 1], wav, drow(h, h->d, n + 1), s,
+                  n >= 1 ? h->xpk[n & 1] : nullptr);
     if (rc) return rc;
     cur ^= 1;
-    // state n+1 is the input of adjoint step n+1 (only states 1..nt-1 are needed)
-    if (n + 1 < nt && (rc = encode_state(h, n + 1, h->st[cur], s))) return rc;
-  }
-  if ((rc = residual_and_misfit(h, d_obs, s))) return rc;
-  if ((rc = begin_adjoint(h, s))) return rc;
-  int acur = 0;
-  for (int n = nt - 1; n >= 0; --n) {
-    const float* en = nullptr;
-    if (n > 0) {
-      if ((rc = decode_e(h, n, s))) return rc;
-      en = h->edec;
+    if (n >= 1) {
+      AEW_CK(cudaEventRecord(h->ev_a[n & 1], s));
+      AEW_CK(cudaStreamWaitEvent(h->side, h->ev_a[n & 1], 0));
+      if ((rc = encode_packed(h, n, h->side))) return rc;
+      AEW_CK(cudaEventRecord(h->ev_b[n & 1], h->side));
     }
-    if ((rc = adj_step(h, n, acur, h->R, en, s))) return rc;
-    acur ^= 1;
   }
+  if ((rc = join(h, h->side, s, h->ev_sync2))) return rc;
+  if ((rc = residual_and_misfit(h, d_obs, s))) return rc;
+  if ((rc = ae_adjoint_sweep(h, h->R, s))) return rc;
   h->stats.forward_steps = nt;
   h->stats.adjoint_steps = nt;
   return AEW_OK;
@@ -499,11 +569,21 @@ int aew_create(const aew_config* cfg, aew_handle** out) {
   if (ok && c.storage == AEW_FULL) ok = dalloc(h, &h->estore, nt * C);
   if (ok && c.storage == AEW_REVOLVE && c.n_checkpoints > 0)
     ok = dalloc(h, &h->ckpt, (size_t)c.n_checkpoints * 4 * C);
+  for (int i = 0; ok && c.storage == AEW_REVOLVE && i < 4; ++i) {
+    ok = dalloc(h, &h->zst[i], C) && cudaMemset(h->zst[i], 0, C * sizeof(float)) == cudaSuccess;
+  }
   if (ok && c.storage == AEW_AE) {
     const size_t nb = (size_t)(c.nx / 8) * (c.ny / 8) * (c.nz / 8);
-    ok = dalloc(h, &h->lat, nt * nb * c.n_lat) && dalloc(h, &h->edec, C) &&
-         dalloc(h, &h->amax, (nt + 1) * 4) && dalloc(h, &h->scales, (nt + 1) * 4) &&
-         dalloc(h, &h->ovf, 1);
+    ok = dalloc(h, &h->lat, nt * nb * c.n_lat) && dalloc(h, &h->bmx, nt * nb * 4) &&
+         dalloc(h, &h->ovf, 1) && dalloc(h, &h->xpk[0], nb * aew::kNIn) &&
+         dalloc(h, &h->xpk[1], nb * aew::kNIn) && dalloc(h, &h->edb[0], C) &&
+         dalloc(h, &h->edb[1], C);
+    ok = ok && cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) == cudaSuccess;
+    for (int i = 0; ok && i < 2; ++i)
+      ok = cudaEventCreateWithFlags(&h->ev_a[i], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&h->ev_b[i], cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&h->ev_sync, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&h->ev_sync2, cudaEventDisableTiming) == cudaSuccess;
   }
   if (!ok) {
     g_create_err = "device allocation failed (" + std::to_string(h->bytes) + " bytes held)";
@@ -537,6 +617,13 @@ int aew_create(const aew_config* cfg, aew_handle** out) {
 void aew_destroy(aew_handle* h) {
   if (!h) return;
   cudaDeviceSynchronize();
+  for (int i = 0; i < 2; ++i) {
+    if (h->ev_a[i]) cudaEventDestroy(h->ev_a[i]);
+    if (h->ev_b[i]) cudaEventDestroy(h->ev_b[i]);
+  }
+  if (h->ev_sync) cudaEventDestroy(h->ev_sync);
+  if (h->ev_sync2) cudaEventDestroy(h->ev_sync2);
+  if (h->side) cudaStreamDestroy(h->side);
   for (void* p : h->allocs) cudaFree(p);
   if (h->codec) aew::codec_free(h->codec);
   delete h;
@@ -566,7 +653,7 @@ int aew_forward(aew_handle* h, const float* c_dev, const float* wavelet_host, fl
   int cur = 0;
   for (int n = 0; n < h->cfg.nt; ++n) {
     rc = fwd_step(h, n, h->st[cur], h->st[cur ^ 1], wav, d_dev ? drow(h, d_dev, n + 1) : nullptr,
-                  nullptr, s);
+                  s);
     if (rc) return rc;
     cur ^= 1;
   }
@@ -592,7 +679,7 @@ int aew_propagate(aew_handle* h, const float* c_dev, float* const state_dev[4], 
   int cur = 0;
   for (int k = 0; k < nsteps; ++k) {
     rc = fwd_step(h, n0 + k, bufs[cur], bufs[cur ^ 1], wavelet_host ? w.data() : nullptr,
-                  d_dev ? drow(h, d_dev, k + 1) : nullptr, nullptr, s);
+                  d_dev ? drow(h, d_dev, k + 1) : nullptr, s);
     if (rc) return rc;
     cur ^= 1;
   }
@@ -654,19 +741,34 @@ static int incremental_forward(aew_handle* h, float* dd_out, cudaStream_t s, lon
   int cur = 0, fcur = 0;
   *fwd = 0;
   if (h->cfg.storage == AEW_REVOLVE && (rc = zero_state(h, h->st[0], s))) return rc;
+  const bool ae = h->cfg.storage == AEW_AE;
+  if (ae) {
+    // decode of step n+1 on the side stream while incremental step n runs on s;
+    // edb[m % 2] is next read by incremental step m, previously by step m - 2
+    if ((rc = join(h, s, h->side, h->ev_sync))) return rc;
+    if (nt - 1 >= 1) {
+      if ((rc = decode_e(h, 1, h->edb[1], h->side))) return rc;
+      AEW_CK(cudaEventRecord(h->ev_b[1], h->side));
+    }
+  }
   for (int n = 0; n < nt; ++n) {
     const float* en = nullptr;
-    if (n > 0) {
-      if (h->cfg.storage == AEW_FULL) {
-        en = h->estore + (size_t)n * h->C;
-      } else if (h->cfg.storage == AEW_AE) {
-        if ((rc = decode_e(h, n, s))) return rc;
-        en = h->edec;
+    if (ae) {
+      if (n + 1 <= nt - 1 && n + 1 >= 2) {
+        AEW_CK(cudaStreamWaitEvent(h->side, h->ev_a[(n + 1) & 1], 0));
+        if ((rc = decode_e(h, n + 1, h->edb[(n + 1) & 1], h->side))) return rc;
+        AEW_CK(cudaEventRecord(h->ev_b[(n + 1) & 1], h->side));
       }
+      if (n >= 1) {
+        AEW_CK(cudaStreamWaitEvent(s, h->ev_b[n & 1], 0));
+        en = h->edb[n & 1];
+      }
+    } else if (n > 0 && h->cfg.storage == AEW_FULL) {
+      en = h->estore + (size_t)n * h->C;
     }
     if (h->cfg.storage == AEW_REVOLVE) {
       if (n > 0) {  // lockstep forward recompute: state n from state n-1
-        rc = fwd_step(h, n - 1, h->st[fcur], h->st[fcur ^ 1], h->wav.data(), nullptr, nullptr, s);
+        rc = fwd_step(h, n - 1, h->st[fcur], h->st[fcur ^ 1], h->wav.data(), nullptr, s);
         if (rc) return rc;
         fcur ^= 1;
         ++*fwd;
@@ -674,9 +776,11 @@ static int incremental_forward(aew_handle* h, float* dd_out, cudaStream_t s, lon
       }
     }
     if ((rc = incr_step(h, h->ad[cur], h->ad[cur ^ 1], en, drow(h, dd_out, n + 1), s))) return rc;
+    if (ae) AEW_CK(cudaEventRecord(h->ev_a[n & 1], s));
     cur ^= 1;
     ++*fwd;
   }
+  if (ae) return join(h, h->side, s, h->ev_sync2);
   return AEW_OK;
 }
 
@@ -720,19 +824,13 @@ int aew_hessvec(aew_handle* h, const float* dc_dev, float* hdc_dev, void* stream
     long long f2 = 0;
     if ((rc = run_revolve(h, nullptr, h->dd, h->wav.data(), false, s, &f2))) return rc;
     fwd += f2;
+  } else if (h->cfg.storage == AEW_AE) {
+    if ((rc = ae_adjoint_sweep(h, h->dd, s))) return rc;
   } else {
     if ((rc = begin_adjoint(h, s))) return rc;
     int acur = 0;
     for (int n = nt - 1; n >= 0; --n) {
-      const float* en = nullptr;
-      if (n > 0) {
-        if (h->cfg.storage == AEW_FULL) {
-          en = h->estore + (size_t)n * h->C;
-        } else {
-          if ((rc = decode_e(h, n, s))) return rc;
-          en = h->edec;
-        }
-      }
+      const float* en = n > 0 ? h->estore + (size_t)n * h->C : nullptr;
       if ((rc = adj_step(h, n, acur, h->dd, en, s))) return rc;
       acur ^= 1;
     }
@@ -800,26 +898,30 @@ int aew_codec_get(const aew_handle* h, float* W1, float* b1, float* W2, float* b
   return aew::codec_get_weights(h->codec, w) == cudaSuccess ? AEW_OK : AEW_E_CUDA;
 }
 
-int aew_codec_encode(aew_handle* h, const float* const fields_dev[4], const float* scale_host,
-                     uint16_t* latents_dev, void* stream) {
+int aew_codec_encode(aew_handle* h, const float* const fields_dev[4], uint16_t* latents_dev,
+                     float* block_max_dev, void* stream) {
   if (!h) return AEW_E_ARG;
-  if (!fields_dev || !scale_host || !latents_dev) return fail(h, AEW_E_ARG, "NULL argument");
+  if (!fields_dev || !latents_dev) return fail(h, AEW_E_ARG, "NULL argument");
   if (h->cfg.nx % 8 || h->cfg.ny % 8 || h->cfg.nz % 8)
     return fail(h, AEW_E_CONFIG, "codec needs nx, ny, nz multiples of 8");
   if (!aew::codec_ready(h->codec)) return fail(h, AEW_E_NOCODEC, "codec weights not set");
   h->err.clear();
   cudaStream_t s = S(stream);
-  AEW_CK(cudaMemcpyAsync(h->scale_tmp, scale_host, 4 * sizeof(float), cudaMemcpyHostToDevice, s));
-  AEW_CK(cudaMemsetAsync(h->scale_tmp + 4, 0, sizeof(int), s));
+  const size_t nb = nblocks_of(h);
+  if (!h->bm_tmp && !dalloc(h, &h->bm_tmp, nb * 4)) return fail(h, AEW_E_NOMEM, "workspace");
+  int* ovf = reinterpret_cast<int*>(h->scale_tmp + 4);
+  AEW_CK(cudaMemsetAsync(ovf, 0, sizeof(int), s));
   const float* f[4] = {fields_dev[0], fields_dev[1], fields_dev[2], fields_dev[3]};
-  cudaError_t e = aew::codec_encode_grid(h->codec, f, h->cfg.nx, h->cfg.ny, h->cfg.nz,
-                                         h->scale_tmp, nullptr, nullptr, latents_dev,
-                                         reinterpret_cast<int*>(h->scale_tmp + 4), s);
+  cudaError_t e = aew::codec_encode_grid(h->codec, f, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->bm_tmp,
+                                         latents_dev, ovf, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "codec_encode_grid");
-  int ovf = 0;
-  AEW_CK(cudaMemcpyAsync(&ovf, h->scale_tmp + 4, sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (block_max_dev)
+    AEW_CK(cudaMemcpyAsync(block_max_dev, h->bm_tmp, nb * 4 * sizeof(float),
+                           cudaMemcpyDeviceToDevice, s));
+  int o = 0;
+  AEW_CK(cudaMemcpyAsync(&o, ovf, sizeof(int), cudaMemcpyDeviceToHost, s));
   AEW_CK(cudaStreamSynchronize(s));
-  if (ovf) return fail(h, AEW_E_OVERFLOW, "a latent overflowed FP16");
+  if (o) return fail(h, AEW_E_OVERFLOW, "a latent overflowed FP16");
   return AEW_OK;
 }
 
@@ -836,20 +938,18 @@ int aew_codec_decode(aew_handle* h, const uint16_t* latents_dev, float* out_dev,
   return AEW_OK;
 }
 
-int aew_codec_decode_e(aew_handle* h, const uint16_t* latents_dev, float scale_e, float* e_dev,
-                       void* stream) {
+int aew_codec_decode_e(aew_handle* h, const uint16_t* latents_dev, const float* block_max_dev,
+                       float* e_dev, void* stream) {
   if (!h) return AEW_E_ARG;
-  if (!latents_dev || !e_dev) return fail(h, AEW_E_ARG, "NULL argument");
+  if (!latents_dev || !block_max_dev || !e_dev) return fail(h, AEW_E_ARG, "NULL argument");
   if (h->cfg.nx % 8 || h->cfg.ny % 8 || h->cfg.nz % 8)
     return fail(h, AEW_E_CONFIG, "codec needs nx, ny, nz multiples of 8");
   if (!aew::codec_ready(h->codec)) return fail(h, AEW_E_NOCODEC, "codec weights not set");
   h->err.clear();
-  cudaStream_t s = S(stream);
-  AEW_CK(cudaMemcpyAsync(h->scale_tmp, &scale_e, sizeof(float), cudaMemcpyHostToDevice, s));
-  cudaError_t e = aew::codec_decode_grid_e(h->codec, latents_dev, h->cfg.nx, h->cfg.ny,
-                                           h->cfg.nz, h->scale_tmp, e_dev, s);
+  cudaError_t e = aew::codec_decode_grid_e(h->codec, latents_dev, h->cfg.nx, h->cfg.ny, h->cfg.nz,
+                                           reinterpret_cast<const unsigned*>(block_max_dev), e_dev,
+                                           S(stream));
   if (e != cudaSuccess) return cuda_fail(h, e, "codec_decode_grid_e");
-  AEW_CK(cudaStreamSynchronize(s));
   return AEW_OK;
 }
 
@@ -873,7 +973,7 @@ int aew_codec_encode_vectors(aew_handle* h, const uint16_t* vectors_dev, long lo
 }
 
 int aew_snapshots(aew_handle* h, const float* c_dev, int every, uint16_t* out_dev,
-                  long long max_vectors, float* scales_dev, long long* n_written,
+                  long long max_vectors, float* block_max_dev, long long* n_written,
                   void* stream) {
   if (!h) return AEW_E_ARG;
   if (!out_dev || !n_written || every < 1 || max_vectors < 0)
@@ -886,27 +986,24 @@ int aew_snapshots(aew_handle* h, const float* c_dev, int every, uint16_t* out_de
   if (rc) return rc;
   h->have_grad = false;
   const size_t nb = nblocks_of(h);
-  // running maxima in the first 8 floats of the partials buffer
-  unsigned* amax = reinterpret_cast<unsigned*>(h->part);
-  float* scale = reinterpret_cast<float*>(h->part) + 4;
-  AEW_CK(cudaMemsetAsync(h->part, 0, 8 * sizeof(float), s));
+  if (!h->bm_tmp && !dalloc(h, &h->bm_tmp, nb * 4)) return fail(h, AEW_E_NOMEM, "workspace");
+  if (!h->raw_tmp && !dalloc(h, &h->raw_tmp, nb * aew::kNIn))
+    return fail(h, AEW_E_NOMEM, "workspace");
   if ((rc = zero_state(h, h->st[0], s))) return rc;
   int cur = 0;
   long long written = 0;
   for (int n = 0; n + 1 < h->cfg.nt; ++n) {
-    if ((rc = fwd_step(h, n, h->st[cur], h->st[cur ^ 1], h->wav.data(), nullptr, amax, s)))
-      return rc;
+    if ((rc = fwd_step(h, n, h->st[cur], h->st[cur ^ 1], h->wav.data(), nullptr, s))) return rc;
     cur ^= 1;
     const int step = n + 1;
     if (step % every == 0 && written + (long long)nb <= max_vectors) {
-      AEW_CK(cudaMemcpyAsync(scale, amax, 4 * sizeof(float), cudaMemcpyDeviceToDevice, s));
       const float* f[4] = {h->st[cur][0], h->st[cur][1], h->st[cur][2], h->st[cur][3]};
-      AEW_CK(aew::snapshot_pack(f, h->cfg.nx, h->cfg.ny, h->cfg.nz, scale,
+      AEW_CK(aew::snapshot_pack(f, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->bm_tmp, h->raw_tmp,
                                 out_dev + (size_t)written * aew::kNIn, s));
-      if (scales_dev)
-        AEW_CK(cudaMemcpyAsync(scales_dev + 4 * (size_t)(written / (long long)nb), scale,
-                               4 * sizeof(float), cudaMemcpyDeviceToDevice, s));
-      h->stats.kernel_launches += 1;
+      if (block_max_dev)
+        AEW_CK(cudaMemcpyAsync(block_max_dev + (size_t)written * 4, h->bm_tmp,
+                               nb * 4 * sizeof(float), cudaMemcpyDeviceToDevice, s));
+      h->stats.kernel_launches += 2;
       written += (long long)nb;
     }
   }

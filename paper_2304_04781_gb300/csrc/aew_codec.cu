@@ -15,6 +15,7 @@
 #include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -109,16 +110,22 @@ struct EpLatent {
 
 // strain part of the decoder output, scattered to the grid:
 // column n = z*64 + y*8 + x of block row -> node (8bz+z, 8by+y, 8bx+x);
-// e = (acc + b4[z*256 + y*8 + x]) * s_e, 0 on boundary nodes
+// e = (acc + b4[z*256 + y*8 + x]) * s_b (power-of-two block scale), 0 on boundary nodes
 struct EpDecGrid {
   const float* b4;
-  const float* scale_e;
+  const unsigned* bmax;   // [nblocks][4] maxima of |f| (float bits); field 0 = strain
   float* e;
   int nx, ny, nz, NBx, NBy;
   long long M;
   __device__ __forceinline__ void operator()(long long row, int col, const float (&v)[32]) const {
     if (row >= M) return;
-    const float s = __ldg(scale_e);
+    const float mx = __uint_as_float(__ldg(bmax + row * 4));
+    float s = 0.f;
+    if (mx > 0.f) {
+      int ex;
+      frexpf(mx, &ex);
+      s = ldexpf(1.f, ex);
+    }
     const long long bx = row % NBx, t = row / NBx;
     const long long by = t % NBy, bz = t / NBy;
     const int z = col >> 6, y0 = (col & 63) >> 3;
@@ -189,31 +196,63 @@ bool ensure_H(Codec* c, size_t rows) {
 // ---------------------------------------------------------------------------------
 // Algorithm 1 packing: BF16 normalised block vectors
 // ---------------------------------------------------------------------------------
-__global__ void snapshot_pack_kernel(const float* f0, const float* f1, const float* f2,
-                                     const float* f3, int nx, int ny, int NBx, int NBy,
-                                     long long nblk, const float* scale, uint16_t* out) {
-  // One thread per float4 of a grid row; consecutive threads read consecutive x
-  // (coalesced) and write 8-byte pieces of the block vectors.
+// Raw BF16 block vectors of a grid state and the per-block, per-field maxima of |f|.
+// One thread per float4 of a grid row: consecutive threads read consecutive x
+// (coalesced) and write 8-byte pieces; the two threads of a block row combine their
+// maxima by shuffle before the atomicMax.
+__global__ void pack_raw_kernel(const float* f0, const float* f1, const float* f2,
+                                const float* f3, int nx, int ny, int NBx, int NBy,
+                                long long nblk, unsigned* bmax, uint16_t* out) {
   const int xq_n = nx >> 2;
   const long long total = nblk / NBx * 256LL * xq_n;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int xq = (int)(t % xq_n);
-    long long r = t / xq_n;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long iters = (total + stride - 1) / stride;
+  for (long long q = 0; q < iters; ++q) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x + q * stride;
+    const bool live = t < total;
+    const int xq = live ? (int)(t % xq_n) : 0;
+    const long long r = live ? t / xq_n : 0;
     const int y = (int)(r & 7), f = (int)((r >> 3) & 3), z = (int)((r >> 5) & 7);
     const long long slab = r >> 8;               // (bz, by)
     const long long by = slab % NBy, bz = slab / NBy;
-    const float* src = f == 0 ? f0 : (f == 1 ? f1 : (f == 2 ? f2 : f3));
-    const float sc = scale[f];
-    // y = x * (1/s): one correctly rounded reciprocal per field, then a product
-    const float inv = sc > 0.f ? __frcp_rn(sc) : 0.f;
-    const float4 a = *reinterpret_cast<const float4*>(
-        src + ((size_t)(8 * bz + z) * ny + (size_t)(8 * by + y)) * nx + 4 * (size_t)xq);
-    const float u0 = __fmul_rn(a.x, inv), u1 = __fmul_rn(a.y, inv);
-    const float u2 = __fmul_rn(a.z, inv), u3 = __fmul_rn(a.w, inv);
     const long long b = slab * NBx + (xq >> 1);
-    *reinterpret_cast<uint2*>(out + b * kNIn + z * 256 + f * 64 + y * 8 + 4 * (xq & 1)) =
-        make_uint2(gemm::pack_bf16(u0, u1), gemm::pack_bf16(u2, u3));
+    float m = 0.f;
+    if (live) {
+      const float* src = f == 0 ? f0 : (f == 1 ? f1 : (f == 2 ? f2 : f3));
+      const float4 a = *reinterpret_cast<const float4*>(
+          src + ((size_t)(8 * bz + z) * ny + (size_t)(8 * by + y)) * nx + 4 * (size_t)xq);
+      *reinterpret_cast<uint2*>(out + b * kNIn + z * 256 + f * 64 + y * 8 + 4 * (xq & 1)) =
+          make_uint2(gemm::pack_bf16(a.x, a.y), gemm::pack_bf16(a.z, a.w));
+      m = fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w)));
+    }
+    // xq and xq ^ 1 are adjacent lanes (xq_n is even) and share block b and field f
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+    if (live && (xq & 1) == 0 && m > 0.f) atomicMax(bmax + b * 4 + f, __float_as_uint(m));
+  }
+}
+
+// y = x * 2^-e per block-field (exact), from raw BF16 vectors and block maxima
+__global__ void normalise_kernel(const uint16_t* __restrict__ raw, const unsigned* __restrict__ bmax,
+                                 long long n, uint16_t* __restrict__ out) {
+  const long long total = n * (kNIn / 8);   // 16-byte pieces
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long b = t / (kNIn / 8);
+    const int k = (int)(t % (kNIn / 8)) * 8;
+    const int f = (k >> 6) & 3;
+    const float mx = __uint_as_float(bmax[b * 4 + f]);
+    float sc = 0.f;
+    if (mx > 0.f) {
+      int e;
+      frexpf(mx, &e);
+      sc = ldexpf(1.f, -e);
+    }
+    uint4 v = *reinterpret_cast<const uint4*>(raw + b * kNIn + k);
+    uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      w[j] = gemm::pack_bf16(__uint_as_float(w[j] << 16) * sc, __uint_as_float(w[j] & 0xffff0000u) * sc);
+    *reinterpret_cast<uint4*>(out + b * kNIn + k) = make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
 
@@ -224,12 +263,6 @@ __global__ void strain_rows_kernel(const uint16_t* __restrict__ W4t, uint16_t* _
   for (int q = k; q < kNHid; q += blockDim.x) W4e[(size_t)r * kNHid + q] = W4t[(size_t)src * kNHid + q];
 }
 
-__global__ void update_scale_kernel(const float* p, const unsigned* a, float* o) {
-  const int i = threadIdx.x;
-  float v = p ? p[i] : 0.f;
-  if (a) v = fmaxf(v, __uint_as_float(a[i]));
-  o[i] = v;
-}
 
 }  // namespace
 
@@ -287,6 +320,7 @@ Codec* codec_new(int n_lat) {
     return nullptr;
   }
   cudaMemset(c->err, 0, sizeof(int));
+  if (const char* env = getenv("AEW_GEMM_CTAS")) c->max_ctas = atoi(env);   // tuning override
   c->bytes += ((size_t)2 * kNIn * kNHid + 2 * nl * kNHid) * 2;
   return c;
 }
@@ -345,37 +379,43 @@ cudaError_t codec_get_weights(const Codec* c, float* const w[8]) {
   return e;
 }
 
-cudaError_t snapshot_pack(const float* const f[4], int nx, int ny, int nz, const float* scale,
-                          uint16_t* out, cudaStream_t s);
-
 cudaError_t codec_encode_grid(Codec* c, const float* const f[4], int nx, int ny, int nz,
-                              const float* scale_prev, const unsigned* amax, float* scale_out,
-                              uint16_t* lat, int* overflow, cudaStream_t s) {
-  const int NBx = nx / 8, NBy = ny / 8, NBz = nz / 8;
-  const long long nb = (long long)NBx * NBy * NBz;
+                              unsigned* bmax, uint16_t* lat, int* overflow, cudaStream_t s) {
+  const long long nb = (long long)(nx / 8) * (ny / 8) * (nz / 8);
   if (!ensure_X(c, (size_t)nb)) return cudaErrorMemoryAllocation;
-  // s_f = max(prev, amax): the scales this state is normalised with (kept for decoding)
-  float* sc = scale_out ? scale_out : c->sc_tmp;
-  update_scale_kernel<<<1, 4, 0, s>>>(scale_prev, amax, sc);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = snapshot_pack(f, nx, ny, nz, bmax, c->X, nullptr, s);
   if (e != cudaSuccess) return e;
-  // normalised BF16 block vectors (the packing of Algorithm 1), then the encoder GEMMs
-  if ((e = snapshot_pack(f, nx, ny, nz, sc, c->X, s)) != cudaSuccess) return e;
-  return codec_encode_vectors(c, c->X, nb, lat, overflow, s);
+  return codec_encode_raw(c, c->X, bmax, nb, lat, overflow, s);
 }
+
+cudaError_t codec_encode_raw(Codec* c, const uint16_t* X, const unsigned* bmax, long long n,
+                             uint16_t* lat, int* overflow, cudaStream_t s) {
+  if (!ensure_H(c, (size_t)n)) return cudaErrorMemoryAllocation;
+  EpBiasGeluH ep{c->w[1], c->H, n};
+  cudaError_t e = gemm::launch<256, true, EpBiasGeluH, true>(
+      n, kNHid, kNIn, gemm::Mat{X, n, kNIn}, gemm::Mat{c->W1t, kNHid, kNIn}, ep, c->err, s,
+      c->max_ctas, bmax);
+  if (e != cudaSuccess) return e;
+  const int nl = c->n_lat;
+  EpLatent e2{c->w[3], lat, nl, n, overflow};
+  const gemm::Mat a2{c->H, n, kNHid}, b2{c->W2t, nl, kNHid};
+  if (nl == 64) return gemm::launch<64, true>(n, nl, kNHid, a2, b2, e2, c->err, s, c->max_ctas);
+  return gemm::launch<32, true>(n, nl, kNHid, a2, b2, e2, c->err, s, c->max_ctas);
+}
+
 
 cudaError_t codec_encode_vectors(Codec* c, const uint16_t* vec, long long n, uint16_t* lat,
                                  int* overflow, cudaStream_t s) {
   if (!ensure_H(c, (size_t)n)) return cudaErrorMemoryAllocation;
   EpBiasGeluH ep{c->w[1], c->H, n};
   cudaError_t e = gemm::launch<256, true>(n, kNHid, kNIn, gemm::Mat{vec, n, kNIn},
-                                          gemm::Mat{c->W1t, kNHid, kNIn}, ep, c->err, s);
+                                          gemm::Mat{c->W1t, kNHid, kNIn}, ep, c->err, s, c->max_ctas);
   if (e != cudaSuccess) return e;
   const int nl = c->n_lat;
   EpLatent e2{c->w[3], lat, nl, n, overflow};
   const gemm::Mat a2{c->H, n, kNHid}, b2{c->W2t, nl, kNHid};
-  if (nl == 64) return gemm::launch<64, true>(n, nl, kNHid, a2, b2, e2, c->err, s);
-  return gemm::launch<32, true>(n, nl, kNHid, a2, b2, e2, c->err, s);
+  if (nl == 64) return gemm::launch<64, true>(n, nl, kNHid, a2, b2, e2, c->err, s, c->max_ctas);
+  return gemm::launch<32, true>(n, nl, kNHid, a2, b2, e2, c->err, s, c->max_ctas);
 }
 
 static cudaError_t decode_hidden(Codec* c, const uint16_t* lat, long long nb, cudaStream_t s) {
@@ -383,18 +423,18 @@ static cudaError_t decode_hidden(Codec* c, const uint16_t* lat, long long nb, cu
   const int nl = c->n_lat;
   EpBiasGeluH ep{c->w[5], c->H, nb};
   return gemm::launch<256, false>(nb, kNHid, nl, gemm::Mat{lat, nb, nl},
-                                  gemm::Mat{c->W3t, kNHid, nl}, ep, c->err, s);
+                                  gemm::Mat{c->W3t, kNHid, nl}, ep, c->err, s, c->max_ctas);
 }
 
 cudaError_t codec_decode_grid_e(Codec* c, const uint16_t* lat, int nx, int ny, int nz,
-                                const float* scale_e, float* e_out, cudaStream_t s) {
+                                const unsigned* bmax, float* e_out, cudaStream_t s) {
   const int NBx = nx / 8, NBy = ny / 8, NBz = nz / 8;
   const long long nb = (long long)NBx * NBy * NBz;
   cudaError_t e = decode_hidden(c, lat, nb, s);
   if (e != cudaSuccess) return e;
-  EpDecGrid ep{c->w[7], scale_e, e_out, nx, ny, nz, NBx, NBy, nb};
+  EpDecGrid ep{c->w[7], bmax, e_out, nx, ny, nz, NBx, NBy, nb};
   return gemm::launch<256, true>(nb, 512, kNHid, gemm::Mat{c->H, nb, kNHid},
-                                 gemm::Mat{c->W4e, 512, kNHid}, ep, c->err, s);
+                                 gemm::Mat{c->W4e, 512, kNHid}, ep, c->err, s, c->max_ctas);
 }
 
 cudaError_t codec_decode_vectors(Codec* c, const uint16_t* lat, long long nvec, float* out,
@@ -403,19 +443,26 @@ cudaError_t codec_decode_vectors(Codec* c, const uint16_t* lat, long long nvec, 
   if (e != cudaSuccess) return e;
   EpVec ep{c->w[7], out, kNIn, nvec};
   return gemm::launch<256, true>(nvec, kNIn, kNHid, gemm::Mat{c->H, nvec, kNHid},
-                                 gemm::Mat{c->W4t, kNIn, kNHid}, ep, c->err, s);
+                                 gemm::Mat{c->W4t, kNIn, kNHid}, ep, c->err, s, c->max_ctas);
 }
 
-cudaError_t snapshot_pack(const float* const f[4], int nx, int ny, int nz, const float* scale,
-                          uint16_t* out, cudaStream_t s) {
+cudaError_t snapshot_pack(const float* const f[4], int nx, int ny, int nz, unsigned* bmax,
+                          uint16_t* raw, uint16_t* out, cudaStream_t s) {
   const int NBx = nx / 8, NBy = ny / 8, NBz = nz / 8;
   const long long nb = (long long)NBx * NBy * NBz;
+  cudaError_t e = cudaMemsetAsync(bmax, 0, (size_t)nb * 4 * sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
   const long long threads = nb * 256 * 2;
   long long blocks = (threads + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  snapshot_pack_kernel<<<(unsigned)blocks, 256, 0, s>>>(
-      f[0], f[1], f[2], f[3], nx, ny, NBx, NBy, nb, scale, out);
-  return cudaGetLastError();
+  pack_raw_kernel<<<(unsigned)blocks, 256, 0, s>>>(f[0], f[1], f[2], f[3], nx, ny, NBx, NBy, nb,
+                                                   bmax, raw);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (out) {
+    normalise_kernel<<<152 * 8, 256, 0, s>>>(raw, bmax, nb, out);
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 }  // namespace aew

@@ -26,27 +26,34 @@ cudaError_t codec_get_weights(const Codec* c, float* const w[8]);
 // Rebuild the tensor-core operand copies of the weights from the FP32 masters.
 cudaError_t codec_refresh(Codec* c, cudaStream_t s);
 
-// Encode one grid state.  s_f = max(scale_prev[f], amax[f]) (either may be null: 0),
-// written to scale_out[f] (may be null).  latents FP16 [nblocks][n_lat].
+// Encode one grid state: raw BF16 block vectors plus per-block, per-field maxima of |f|
+// (bmax, float bits [nblocks][4], written), then the encoder with the power-of-two
+// per-block normalisation applied to its input.  latents FP16 [nblocks][n_lat].
 cudaError_t codec_encode_grid(Codec* c, const float* const f[4], int nx, int ny, int nz,
-                              const float* scale_prev, const unsigned* amax, float* scale_out,
-                              uint16_t* lat, int* overflow, cudaStream_t s);
+                              unsigned* bmax, uint16_t* lat, int* overflow, cudaStream_t s);
 
-// Encode BF16 block vectors [n][2048] into FP16 latents [n][n_lat].
+// Encoder on raw BF16 block vectors X [n][2048] with block maxima bmax [n][4].
+cudaError_t codec_encode_raw(Codec* c, const uint16_t* X, const unsigned* bmax, long long n,
+                             uint16_t* lat, int* overflow, cudaStream_t s);
+
+// Encode already normalised BF16 block vectors [n][2048] into FP16 latents [n][n_lat].
 cudaError_t codec_encode_vectors(Codec* c, const uint16_t* vec, long long n, uint16_t* lat,
                                  int* overflow, cudaStream_t s);
 
-// Decode the strain part of latents into the grid: e = s_e * dec_e(z), 0 on boundary.
+// Decode the strain part of latents into the grid: e = s_b * dec_e(z) with the block's
+// power-of-two scale s_b from bmax[b][0]; 0 on boundary nodes.
 cudaError_t codec_decode_grid_e(Codec* c, const uint16_t* lat, int nx, int ny, int nz,
-                                const float* scale_e, float* e_out, cudaStream_t s);
+                                const unsigned* bmax, float* e_out, cudaStream_t s);
 
 // Decode latents to normalised vectors FP32 [nvec][2048].
 cudaError_t codec_decode_vectors(Codec* c, const uint16_t* lat, long long nvec, float* out,
                                  cudaStream_t s);
 
-// Algorithm 1 packing: normalised BF16 block vectors of one grid state.
-cudaError_t snapshot_pack(const float* const f[4], int nx, int ny, int nz, const float* scale,
-                          uint16_t* out, cudaStream_t s);
+// Algorithm 1 packing of one grid state: normalised BF16 block vectors [nblocks][2048]
+// (each block-field divided by its power-of-two scale) and the block maxima (bmax,
+// float bits [nblocks][4], written; work buffer X [nblocks][2048] for the raw values).
+cudaError_t snapshot_pack(const float* const f[4], int nx, int ny, int nz, unsigned* bmax,
+                          uint16_t* raw, uint16_t* out, cudaStream_t s);
 
 // One training step (MSE + LAMB); loss (device float) written if loss_dev != null.
 cudaError_t codec_train_step(Codec* c, const uint16_t* batch, int B, float lr, float* loss_dev,

@@ -27,6 +27,7 @@ struct Codec {
   size_t X_rows = 0;
   float* sc_tmp = nullptr;
   int* err = nullptr;
+  int max_ctas = 0;          // CTA cap of the codec GEMMs (0: one per SM)
   size_t bytes = 0;
   // training state (allocated by the training unit)
   void* train = nullptr;

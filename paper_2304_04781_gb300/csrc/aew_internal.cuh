@@ -37,7 +37,11 @@ struct FwdStep {
   int krec;          // receiver node plane (-1: none)
   const int* rec_map;  // [ny][nx] receiver index or -1
   float* d_out;        // receiver record row [nrec][3] (or null)
-  unsigned int* amax;  // [4] running |field| maxima of the new state (or null)
+  // Optional packing of the INPUT state n into BF16 block vectors [nblocks][2048]
+  // (order z*256 + f*64 + y*8 + x, not yet normalised) and the per-block, per-field
+  // maxima of |f| (float bits, atomicMax into bmax[nblocks][4], zeroed beforehand).
+  uint16_t* xpack;
+  unsigned int* bmax;
 };
 
 // ------------------------------------------------------------------------------

@@ -15,6 +15,8 @@
 // them only at CTA edges, with the identical expression, so results are bitwise
 // independent of the tiling), and then updates the strain of its nodes.  Algorithmic
 // HBM traffic of the forward step: 5 fields read + 4 written = 36 bytes per node.
+#include <cuda_bf16.h>
+
 #include <cstdlib>
 
 #include "aew_internal.cuh"
@@ -36,6 +38,10 @@ __device__ __forceinline__ float& comp(float4& v, int c) {
   return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
 }
 __device__ __forceinline__ float4 z4() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+__device__ __forceinline__ uint32_t pack2bf(float a, float b) {
+  __nv_bfloat162 t = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&t);
+}
 
 // m e (+ dm ef) for one float4 of nodes whose strain e4 is already loaded
 template <bool INCR>
@@ -75,11 +81,10 @@ __device__ __forceinline__ float hmax4(float4 a) {
 // ---------------------------------------------------------------------------------
 // Forward-type step
 // ---------------------------------------------------------------------------------
-template <bool INCR, bool AMAX>
+template <bool INCR, bool PACK>
 __global__ void __launch_bounds__(NTHR, 3) fwd_step_kernel(const FwdStep a) {
   __shared__ float4 sme[2][TY + 2][W4 + 2];
   __shared__ float4 svy[TY][W4];
-  __shared__ float sred[4][TY];
 
   const int lane = threadIdx.x, ty = threadIdx.y;
   const int nx = a.nx, ny = a.ny, nz = a.nz;
@@ -116,11 +121,35 @@ __global__ void __launch_bounds__(NTHR, 3) fwd_step_kernel(const FwdStep a) {
       }
     }
   }
-  float mx_e = 0.f, mx_vx = 0.f, mx_vy = 0.f, mx_vz = 0.f;
+  // block-vector packing of the input state: raw BF16 values and the running maxima
+  // of |f| over the planes of the current 8-plane block layer
+  float pm[4] = {0.f, 0.f, 0.f, 0.f};
+  const int NBx = nx >> 3, NBy = ny >> 3;
 
   for (int k = kbeg; k < kend; ++k) {
     const int b = k & 1;
     const size_t i = (size_t)k * P + row;
+    if (PACK) {
+      const size_t blk = ((size_t)(k >> 3) * NBy + (y >> 3)) * NBx + (i0 >> 3);
+      if (act) {
+        uint16_t* dst = a.xpack + blk * 2048 + (k & 7) * 256 + (y & 7) * 8 + (i0 & 7);
+        const float4 fv[4] = {e_c, vx_c, vy_c, vz_c};
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          *reinterpret_cast<uint2*>(dst + f * 64) =
+              make_uint2(pack2bf(fv[f].x, fv[f].y), pack2bf(fv[f].z, fv[f].w));
+          pm[f] = fmaxf(pm[f], hmax4(fv[f]));
+        }
+      }
+      if ((k & 7) == 7 || k == kend - 1) {   // block layer complete within this CTA
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          const float v = fmaxf(pm[f], __shfl_xor_sync(0xffffffffu, pm[f], 1));
+          if (act && (lane & 1) == 0 && v > 0.f) atomicMax(a.bmax + blk * 4 + f, __float_as_uint(v));
+          pm[f] = 0.f;
+        }
+      }
+    }
     // inputs of the next plane, in flight while this plane is computed
     float4 vx_x = z4(), vy_x = z4(), vz_x = z4(), e_x = z4(), me_x = z4();
     if (act && k + 1 < kend) {
@@ -213,12 +242,6 @@ __global__ void __launch_bounds__(NTHR, 3) fwd_step_kernel(const FwdStep a) {
           }
         }
       }
-      if (AMAX) {
-        mx_e = fmaxf(mx_e, hmax4(e1));
-        mx_vx = fmaxf(mx_vx, hmax4(vx1));
-        mx_vy = fmaxf(mx_vy, hmax4(vy1));
-        mx_vz = fmaxf(mx_vz, hmax4(vz1));
-      }
     }
     vzl = vz1;
     e_c = e_n;
@@ -230,28 +253,6 @@ __global__ void __launch_bounds__(NTHR, 3) fwd_step_kernel(const FwdStep a) {
     vz_c = vz_x;
   }
 
-  if (AMAX) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      mx_e = fmaxf(mx_e, __shfl_xor_sync(0xffffffffu, mx_e, o));
-      mx_vx = fmaxf(mx_vx, __shfl_xor_sync(0xffffffffu, mx_vx, o));
-      mx_vy = fmaxf(mx_vy, __shfl_xor_sync(0xffffffffu, mx_vy, o));
-      mx_vz = fmaxf(mx_vz, __shfl_xor_sync(0xffffffffu, mx_vz, o));
-    }
-    if (lane == 0) {
-      sred[0][ty] = mx_e;
-      sred[1][ty] = mx_vx;
-      sred[2][ty] = mx_vy;
-      sred[3][ty] = mx_vz;
-    }
-    __syncthreads();
-    if (ty == 0 && lane < 4) {
-      float v = 0.f;
-      for (int w = 0; w < TY; ++w) v = fmaxf(v, sred[lane][w]);
-      // non-negative floats order like their bit patterns
-      atomicMax(a.amax + lane, __float_as_uint(v));
-    }
-  }
 }
 
 // ---------------------------------------------------------------------------------
@@ -470,7 +471,7 @@ cudaError_t launch_fwd_step(const FwdStep& a, bool incremental, cudaStream_t s) 
   const dim3 grid = grid_of(a.nx, a.ny, a.nz, a.kc), block(32, TY);
   if (incremental) {
     fwd_step_kernel<true, false><<<grid, block, 0, s>>>(a);
-  } else if (a.amax) {
+  } else if (a.xpack) {
     fwd_step_kernel<false, true><<<grid, block, 0, s>>>(a);
   } else {
     fwd_step_kernel<false, false><<<grid, block, 0, s>>>(a);

@@ -2,8 +2,9 @@
 
 Data (Algorithm 1): for each prior draw of the wave speed (a seeded Gaussian random
 field), run the forward solve and keep every `every`-th state, cut into 8x8x8-node
-blocks of the four fields (2048 values each, every field divided by its running
-maximum), as BF16 vectors resident in HBM.  Training (Table 2): mean-squared
+blocks of the four fields (2048 values each, every field of every block divided by its
+power-of-two scale, the per-vector normalisation of Sec. 3.3), as BF16 vectors resident
+in HBM.  Training (Table 2): mean-squared
 reconstruction error, LAMB, learning rate 1e-3 halved every 5 epochs, batch 512, a
 fresh seeded shuffle per epoch.  All arithmetic runs in the library's kernels
 (aew_snapshots, aew_codec_train_step, aew_codec_encode_vectors, aew_codec_decode);
@@ -35,23 +36,37 @@ def make_handle(shape, h=10.0, nt=1000, n_lat=64, nrec=64) -> aewave.Solver:
     return aewave.Solver(shape, h, nt, rec, storage="revolve", n_checkpoints=0, n_lat=n_lat)
 
 
-def generate(solver: aewave.Solver, seeds, every: int = 10, h: float = 10.0):
-    """Algorithm 1 over several prior draws; returns (BF16 [N][2048], scales [N/nblocks][4])."""
+def block_scale(bmax: torch.Tensor) -> torch.Tensor:
+    """Power-of-two scales s = 2^e of block maxima m 2^e, m in [0.5, 1) (0 for 0)."""
+    _, e = torch.frexp(bmax)
+    return torch.where(bmax > 0, torch.ldexp(torch.ones_like(bmax), e), torch.zeros_like(bmax))
+
+
+def generate(solver: aewave.Solver, seeds, every: int = 10, h: float = 10.0,
+             drop_zero: bool = True):
+    """Algorithm 1 over several prior draws.  Returns (BF16 [N][2048] normalised vectors,
+    FP32 [N][4] block maxima).  Vectors of blocks that are still entirely at rest (all four
+    fields zero) encode and decode to zero whatever the weights, and are dropped."""
     per_seed = solver.nblocks * ((solver.nt - 1) // every)
     data = torch.empty((per_seed * len(seeds), 2048), device="cuda", dtype=torch.bfloat16)
-    scales = []
+    bmax = torch.empty((per_seed * len(seeds), 4), device="cuda")
     n = 0
     for s in seeds:
         c = torch.from_numpy(inputs.velocity_model(solver.shape, h, seed=s).astype(np.float32)).cuda()
-        v, sc = solver.snapshots(c, every, per_seed, out=data[n:n + per_seed], with_scales=True)
+        v, bm = solver.snapshots(c, every, per_seed, out=data[n:n + per_seed], with_scales=True)
+        bmax[n:n + v.shape[0]] = bm
         n += v.shape[0]
-        scales.append(sc)
-    return data[:n], torch.cat(scales)
+    data, bmax = data[:n], bmax[:n]
+    if drop_zero:
+        keep = torch.nonzero(bmax.amax(dim=1) > 0).squeeze(1)
+        data, bmax = data.index_select(0, keep), bmax.index_select(0, keep)
+    return data, bmax
 
 
 def train(solver: aewave.Solver, data: torch.Tensor, epochs: int = 20, batch: int = 512,
           lr0: float = 1e-3, halve_every: int = 5, seed: int = 0, log_every: int = 0):
-    """Train the handle's codec in place on `data`; returns the per-epoch mean losses."""
+    """Train the handle's codec in place on `data`; returns per-epoch mean losses (over
+    about 16 sampled minibatches per epoch, each loss taken before its update)."""
     g = torch.Generator(device="cuda")
     g.manual_seed(seed)
     N = data.shape[0]
@@ -62,11 +77,11 @@ def train(solver: aewave.Solver, data: torch.Tensor, epochs: int = 20, batch: in
         perm = torch.randperm(N, device="cuda", generator=g)
         tot = 0.0
         cnt = 0
+        every = log_every or max(1, nb // 16)
         for i in range(nb):
             idx = perm[i * batch:(i + 1) * batch]
             mb = data.index_select(0, idx)
-            want = log_every and (i % log_every == 0 or i == nb - 1)
-            loss = solver.train_step(mb, lr, want_loss=bool(want) or i == nb - 1)
+            loss = solver.train_step(mb, lr, want_loss=(i % every == 0) or i == nb - 1)
             if loss is not None:
                 tot += loss
                 cnt += 1
@@ -74,32 +89,35 @@ def train(solver: aewave.Solver, data: torch.Tensor, epochs: int = 20, batch: in
     return hist
 
 
-def decoded_error(solver: aewave.Solver, data: torch.Tensor, scales: torch.Tensor, chunk: int = 65536):
-    """Relative L2 error of decode(encode(y)) over all blocks and states, per field and
-    overall, both in normalised units and in physical units (x = y * s)."""
-    nb = solver.nblocks
+def decoded_error(solver: aewave.Solver, data: torch.Tensor, bmax: torch.Tensor, chunk: int = 65536):
+    """Relative L2 error of decode(encode(y)) over all vectors, per field and overall, in
+    normalised units and in physical units (x = y * s_{b,f})."""
     num = torch.zeros(4, dtype=torch.float64, device="cuda")
     den = torch.zeros(4, dtype=torch.float64, device="cuda")
     pnum = torch.zeros(4, dtype=torch.float64, device="cuda")
     pden = torch.zeros(4, dtype=torch.float64, device="cuda")
     cols = [field_columns(f).cuda() for f in range(4)]
+    scale = block_scale(bmax)
     for i in range(0, data.shape[0], chunk):
         y = data[i:i + chunk]
         yh = solver.codec_decode(solver.codec_encode_vectors(y))
         yf = y.float()
-        st = torch.arange(i, i + y.shape[0], device="cuda") // nb
         for f in range(4):
             d = (yh[:, cols[f]] - yf[:, cols[f]]).double().pow(2).sum(1)
             r = yf[:, cols[f]].double().pow(2).sum(1)
-            s2 = scales[st, f].double() ** 2
+            s2 = scale[i:i + chunk, f].double() ** 2
             num[f] += d.sum(); den[f] += r.sum()
             pnum[f] += (d * s2).sum(); pden[f] += (r * s2).sum()
     names = ["e", "vx", "vy", "vz"]
     out = {"normalised": {names[f]: float((num[f] / den[f]).sqrt()) for f in range(4)},
            "physical": {names[f]: float((pnum[f] / pden[f]).sqrt()) for f in range(4)}}
     out["normalised"]["all"] = float((num.sum() / den.sum()).sqrt())
-    out["physical_per_field_mean"] = float(np.mean(list(out["physical"].values())))
+    out["vectors"] = int(data.shape[0])
     return out
+
+
+def weights_finite(W: dict) -> bool:
+    return all(np.isfinite(np.asarray(v)).all() for v in W.values())
 
 
 def save(W: dict, path: str):
@@ -123,7 +141,8 @@ def main():
     solver = make_handle(shape, nt=a.nt, n_lat=a.n_lat)
     solver.codec_set(inputs.codec_init(seed=a.init_seed, n_lat=a.n_lat))
     t0 = time.time()
-    data, scales = generate(solver, a.seeds, a.every)
+    data, _ = generate(solver, a.seeds, a.every)
+    nvec = data.shape[0]
     torch.cuda.synchronize()
     t1 = time.time()
     hist = train(solver, data, a.epochs, a.batch)
@@ -132,11 +151,12 @@ def main():
     del data
     hold, hsc = generate(solver, [a.holdout], a.every)
     err = decoded_error(solver, hold, hsc)
-    res = {"vectors": int(scales.shape[0] * solver.nblocks), "gen_s": t1 - t0, "train_s": t2 - t1,
-           "epochs": a.epochs, "loss": hist, "holdout_decoded_error": err}
+    W = solver.codec_get()
+    res = {"vectors": int(nvec), "gen_s": t1 - t0, "train_s": t2 - t1, "epochs": a.epochs,
+           "loss": hist, "holdout_decoded_error": err, "weights_finite": weights_finite(W)}
     print(json.dumps(res))
     if a.out:
-        save(solver.codec_get(), a.out)
+        save(W, a.out)
 
 
 if __name__ == "__main__":

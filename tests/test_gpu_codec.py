@@ -38,13 +38,19 @@ def test_encode_matches_oracle(shape, n_lat):
     Wt = inputs.codec_init(seed=1, n_lat=n_lat)
     s.codec_set(Wt)
     st = _state(shape, seed=4)
-    scale = [float(np.abs(a).max()) for a in st]
-    scale[2] = 0.0   # a field whose scale is 0 is fed as zeros
-    lat = s.codec_encode([cuda(a) for a in st], scale)
+    st[2][:8, :8, :] = 0.0          # block-fields that are exactly zero (scale 0)
+    st[3] *= 1e-12                  # a field many orders of magnitude smaller
+    st = [a.astype(np.float32).astype(np.float64) for a in st]
+    lat, bm = s.codec_encode([cuda(a) for a in st])
     z = lat.float().cpu().numpy().astype(np.float64)
-    z_ref = C.encode(Wt, C.normalise(C.pack_blocks(st), scale), emulate=True)
+    sc = C.block_scales(st)
+    z_ref = C.encode(Wt, C.normalise(C.pack_blocks(st), sc), emulate=True)
     assert z.shape == z_ref.shape
     assert relerr(z, z_ref) < CODEC_TOL
+    # block maxima are exact (max of the same FP32 values)
+    Xa = np.abs(C.pack_blocks(st))
+    bm_ref = np.stack([Xa[:, C.field_columns(f)].max(1) for f in range(4)], 1)
+    np.testing.assert_array_equal(host(bm), bm_ref)
 
 
 @pytest.mark.parametrize("n_lat", [64, 32])
@@ -59,43 +65,48 @@ def test_decode_matches_oracle(n_lat):
     out = host(s.codec_decode(lat))
     ref = C.decode(Wt, Z, emulate=True)
     assert relerr(out, ref) < CODEC_TOL
-    # strain part scattered to the grid, scaled, zero on the boundary
-    se = 3.5e-4
-    e = host(s.codec_decode_e(lat, se))
+    # strain part scattered to the grid, times each block's power-of-two scale, zero on
+    # the boundary
+    rng = np.random.default_rng(9)
+    bm = (rng.uniform(0.5, 1.0, (s.nblocks, 4)) * 10.0 ** rng.integers(-12, 3, (s.nblocks, 4))).astype(np.float32)
+    bm[3, 0] = 0.0
+    e = host(s.codec_decode_e(lat, cuda(bm)))
+    _, ex = np.frexp(bm[:, 0].astype(np.float64))
+    sb = np.where(bm[:, 0] > 0, np.ldexp(1.0, ex), 0.0)
     Xe = np.zeros_like(ref)
     cols = C.field_columns(0)
-    Xe[:, cols] = ref[:, cols] * se
+    Xe[:, cols] = ref[:, cols] * sb[:, None]
     e_ref = W.interior(C.unpack_field(Xe, shape, 0))
     assert relerr(e, e_ref) < CODEC_TOL
     assert np.all(e[0] == 0) and np.all(e[:, :, -1] == 0)
 
 
 def test_snapshots_bitwise_match_packing():
-    """Algorithm 1: every 10th state packed with the running per-field maximum; the
-    BF16 codes are compared bit for bit with a packing of the same FP32 states done on
-    the host (FP32 reciprocal of the scale, FP32 product, then RNE to BF16, the same
-    operations in the same precision as on the GPU)."""
+    """Algorithm 1: every 10th state cut into blocks, each field of each block divided by
+    its power-of-two scale.  The BF16 codes are compared bit for bit with the same
+    packing of the same FP32 states done on the host (BF16 rounding, then the exact
+    power-of-two scaling)."""
     shape = (32, 32, 32)
     prob, c, _ = setup(shape, 41, 16)
     s = solver(prob, storage="ae")
-    snaps = s.snapshots(cuda(c), every=10, max_vectors=4 * 64)
+    snaps, bm = s.snapshots(cuda(c), every=10, max_vectors=4 * 64, with_scales=True)
     assert snaps.shape == (4 * 64, 2048)
     st = [torch.zeros(shape, device="cuda") for _ in range(4)]
     cc = cuda(c)
     wav = W.default_wavelet(prob)
-    run_max = np.zeros(4, np.float32)
     got = snaps.view(torch.int16).cpu().numpy().view(np.uint16)
     for q in range(4):
-        for n in range(10 * q, 10 * q + 10):   # running maximum over every state
-            s.propagate(cc, st, n, 1, wavelet=wav[n:n + 1])
-            hs = [host(t).astype(np.float32) for t in st]
-            run_max = np.maximum(run_max, np.array([np.abs(a).max() for a in hs], np.float32))
-        X = C.pack_blocks([a.astype(np.float64) for a in hs]).astype(np.float32)
-        sv = C.scale_vector(run_max).astype(np.float32)
-        inv = np.where(sv > 0, np.float32(1) / np.where(sv > 0, sv, np.float32(1)), np.float32(0))
-        Y = (X * inv.astype(np.float32)).astype(np.float32)
+        s.propagate(cc, st, 10 * q, 10, wavelet=wav[10 * q: 10 * q + 10])
+        hs = [host(t) for t in st]
+        X = C.pack_blocks(hs)
+        sc = C.block_scales(hs)
+        Xb = torch.from_numpy(X.astype(np.float32)).to(torch.bfloat16).double().numpy()
+        Y = C.normalise(Xb, sc)                      # exact: scales are powers of two
         want = torch.from_numpy(Y).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
         np.testing.assert_array_equal(got[64 * q: 64 * (q + 1)], want)
+        Xa = np.abs(X)
+        bm_ref = np.stack([Xa[:, C.field_columns(f)].max(1) for f in range(4)], 1)
+        np.testing.assert_array_equal(host(bm[64 * q: 64 * (q + 1)]), bm_ref)
 
 
 def test_training_steps_match_oracle():
@@ -137,14 +148,15 @@ def ae_case():
 
 def test_ae_gradient_matches_oracle_ae_gradient(ae_case):
     """Same weights on both sides; the oracle decodes its own FP64 states (emulated
-    rounding).  This checks the compressed pipeline (encode with running scales,
-    latent store, decode, accumulation) end to end."""
+    rounding).  This checks the compressed pipeline (packing and block maxima inside the
+    forward step, encoder on the side stream, latent store, decode, accumulation) end to
+    end."""
     prob, c, d_obs, Wt = ae_case
     s = solver(prob, storage="ae")
     s.codec_set(Wt)
     J, g = s.gradient(cuda(c), cuda(d_obs))
     d, states = W.forward_states(prob, c)
-    ehat, scales = C.compressed_e_history(Wt, states, emulate=True)
+    ehat = C.compressed_e_history(Wt, states, emulate=True)
     J_ref, g_ref, _ = W.gradient(prob, c, d_obs, e_of=lambda n: ehat[n])
     assert abs(J - J_ref) / J_ref < 1e-4
     assert relerr(host(g), g_ref) < 1e-2
@@ -157,18 +169,14 @@ def test_ae_gradient_matches_oracle_ae_gradient(ae_case):
     assert st["latent_bytes"] == prob.nt * 64 * 64 * 2
 
 
-def test_latent_store_and_scales_consistent(ae_case):
-    """Decoding stored latents with the stored scales reproduces the oracle's decoded
-    strain of the same step (checks the 1-step-lag bookkeeping of the forward loop)."""
+def test_roundtrip_of_one_state_matches_oracle(ae_case):
+    """Encode then decode the strain of one state with per-block scales (standalone path)."""
     prob, c, d_obs, Wt = ae_case
     s = solver(prob, storage="ae")
     s.codec_set(Wt)
-    s.gradient(cuda(c), cuda(d_obs))
     _, states = W.forward_states(prob, c)
     n = 150
-    sc = C.running_scales(states[: n + 1])[n]
-    e_ref = C.roundtrip_e(Wt, states[n], sc, emulate=True)
-    # re-encode the oracle's state n on the GPU and decode it there
-    lat = s.codec_encode([cuda(a) for a in states[n]], sc)
-    e = host(s.codec_decode_e(lat, float(sc[0])))
+    e_ref = C.roundtrip_e(Wt, states[n], emulate=True)
+    lat, bm = s.codec_encode([cuda(a) for a in states[n]])
+    e = host(s.codec_decode_e(lat, bm))
     assert relerr(e, e_ref) < 1e-2
