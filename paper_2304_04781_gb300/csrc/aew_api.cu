@@ -713,6 +713,8 @@ int aew_gradient(aew_handle* h, const float* c_dev, const float* d_obs_dev, floa
     rc = gradient_ae(h, d_obs_dev, wav, s);
   }
   if (rc) return rc;
+  if (h->cfg.storage == AEW_AE && aew::codec_take_error(h->codec, s))
+    return fail(h, AEW_E_TIMEOUT, "a codec kernel gave up waiting (bounded mbarrier wait)");
   AEW_CK(aew::launch_finalize_grad(h->c, h->acc64, g_dev, h->C, s));
   ++h->stats.kernel_launches;
   if (misfit_host || h->cfg.storage == AEW_AE) {
@@ -836,6 +838,8 @@ int aew_hessvec(aew_handle* h, const float* dc_dev, float* hdc_dev, void* stream
     }
   }
   h->stats.hvp_forward_steps = fwd;
+  if (h->cfg.storage == AEW_AE && aew::codec_take_error(h->codec, s))
+    return fail(h, AEW_E_TIMEOUT, "a codec kernel gave up waiting (bounded mbarrier wait)");
   AEW_CK(aew::launch_finalize_grad(h->c, h->acc64, hdc_dev, h->C, s));
   ++h->stats.kernel_launches;
   return AEW_OK;
@@ -918,6 +922,8 @@ int aew_codec_encode(aew_handle* h, const float* const fields_dev[4], uint16_t* 
   if (block_max_dev)
     AEW_CK(cudaMemcpyAsync(block_max_dev, h->bm_tmp, nb * 4 * sizeof(float),
                            cudaMemcpyDeviceToDevice, s));
+  if (aew::codec_take_error(h->codec, s))
+    return fail(h, AEW_E_TIMEOUT, "a codec kernel gave up waiting (bounded mbarrier wait)");
   int o = 0;
   AEW_CK(cudaMemcpyAsync(&o, ovf, sizeof(int), cudaMemcpyDeviceToHost, s));
   AEW_CK(cudaStreamSynchronize(s));
@@ -935,6 +941,8 @@ int aew_codec_decode(aew_handle* h, const uint16_t* latents_dev, float* out_dev,
   cudaError_t e =
       aew::codec_decode_vectors(h->codec, latents_dev, (long long)nblocks_of(h), out_dev, S(stream));
   if (e != cudaSuccess) return cuda_fail(h, e, "codec_decode_vectors");
+  if (aew::codec_take_error(h->codec, S(stream)))
+    return fail(h, AEW_E_TIMEOUT, "a codec kernel gave up waiting (bounded mbarrier wait)");
   return AEW_OK;
 }
 
@@ -950,6 +958,8 @@ int aew_codec_decode_e(aew_handle* h, const uint16_t* latents_dev, const float* 
                                            reinterpret_cast<const unsigned*>(block_max_dev), e_dev,
                                            S(stream));
   if (e != cudaSuccess) return cuda_fail(h, e, "codec_decode_grid_e");
+  if (aew::codec_take_error(h->codec, S(stream)))
+    return fail(h, AEW_E_TIMEOUT, "a codec kernel gave up waiting (bounded mbarrier wait)");
   return AEW_OK;
 }
 
@@ -965,6 +975,8 @@ int aew_codec_encode_vectors(aew_handle* h, const uint16_t* vectors_dev, long lo
   AEW_CK(cudaMemsetAsync(ovf, 0, sizeof(int), s));
   cudaError_t e = aew::codec_encode_vectors(h->codec, vectors_dev, n, latents_dev, ovf, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "codec_encode_vectors");
+  if (aew::codec_take_error(h->codec, s))
+    return fail(h, AEW_E_TIMEOUT, "a codec kernel gave up waiting (bounded mbarrier wait)");
   int o = 0;
   AEW_CK(cudaMemcpyAsync(&o, ovf, sizeof(int), cudaMemcpyDeviceToHost, s));
   AEW_CK(cudaStreamSynchronize(s));
@@ -1022,6 +1034,8 @@ int aew_codec_train_step(aew_handle* h, const uint16_t* batch_dev, int batch, fl
   float* loss_dev = h->scale_tmp;
   cudaError_t e = aew::codec_train_step(h->codec, batch_dev, batch, lr, loss_dev, s, &h->err);
   if (e != cudaSuccess) return cuda_fail(h, e, "codec_train_step");
+  if (loss_host && aew::codec_take_error(h->codec, s))
+    return fail(h, AEW_E_TIMEOUT, "a codec kernel gave up waiting (bounded mbarrier wait)");
   if (loss_host) {
     AEW_CK(cudaMemcpyAsync(loss_host, loss_dev, sizeof(float), cudaMemcpyDeviceToHost, s));
     AEW_CK(cudaStreamSynchronize(s));

@@ -342,6 +342,15 @@ void codec_free(Codec* c) {
 }
 
 int codec_nlat(const Codec* c) { return c->n_lat; }
+
+bool codec_take_error(Codec* c, cudaStream_t s) {
+  int v = 0;
+  if (cudaMemcpyAsync(&v, c->err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return true;
+  if (v) cudaMemsetAsync(c->err, 0, sizeof(int), s);
+  return v != 0;
+}
 size_t codec_device_bytes(const Codec* c) {
   return c->bytes + c->H_rows * kNHid * 2 + c->X_rows * kNIn * 2 +
          (c->train ? train_state_bytes(c->train) : 0);

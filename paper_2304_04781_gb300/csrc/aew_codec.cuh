@@ -55,6 +55,10 @@ cudaError_t codec_decode_vectors(Codec* c, const uint16_t* lat, long long nvec, 
 cudaError_t snapshot_pack(const float* const f[4], int nx, int ny, int nz, unsigned* bmax,
                           uint16_t* raw, uint16_t* out, cudaStream_t s);
 
+// Device error flag of the codec kernels (set by a bounded wait that gave up); read and
+// clear it (synchronises the stream).  Returns true if it was set.
+bool codec_take_error(Codec* c, cudaStream_t s);
+
 // One training step (MSE + LAMB); loss (device float) written if loss_dev != null.
 cudaError_t codec_train_step(Codec* c, const uint16_t* batch, int B, float lr, float* loss_dev,
                              cudaStream_t s, std::string* err);

@@ -41,7 +41,7 @@ constexpr int kMmaWarp = 9;
 constexpr int kThreads = 320;
 constexpr int kXfWarp0 = 10;                 // warps 10-13: A-operand scaling (SCALE only)
 constexpr int kThreadsScaled = 448;
-constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s
+constexpr uint64_t kWaitNs = 200000000ull;   // 200 ms (a healthy wait takes microseconds)
 constexpr int kSmemBudget = 200 * 1024;
 
 template <int BN, bool SCALE = false>
@@ -138,6 +138,8 @@ __global__ void __launch_bounds__(SCALE ? kThreadsScaled : kThreads, 1)
   uint32_t* tslot = reinterpret_cast<uint32_t*>(acce + 2);
   int* abort_flag = reinterpret_cast<int*>(tslot + 1);
 
+  // a previous launch already failed: do nothing (the host reports the error)
+  if (*reinterpret_cast<volatile int*>(err) != 0) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nK = (K + kBK - 1) / kBK;
   const int tn = (N + BN - 1) / BN;
@@ -182,7 +184,7 @@ __global__ void __launch_bounds__(SCALE ? kThreadsScaled : kThreads, 1)
           }
           const uint32_t fb = tc::smem_u32(&full[s]);
           const uint32_t sa = tc::smem_u32(smem + s * STAGE), sb = sa + A_BYTES;
-          mbar_expect_tx(fb, STAGE);
+          mbar_expect_tx(fb, A_BYTES + B_BYTES);   // bytes the two TMA loads deliver
           if (SW) {
             tma_load_2d(sa, &ta, c * kBK, m0, fb);
             tma_load_2d(sb, &tb, c * kBK, n0, fb);
