@@ -15,8 +15,9 @@ used here (and by the CUDA path, as a layout definition) is
 Block b = (bz*NBy + by)*NBx + bx.  Normalisation (Sec. 3.3: every vector is scaled to
 O(1) before encoding and its scale is kept at higher precision): each field of each
 block is divided by s_{b,f} = 2^e, the power of two with max_x |f| in [s/2, s), so the
-normalised values lie in (-1, 1) and scaling by s is exact in any binary format.  A
-block-field that is identically zero has s = 0 and is fed (and decoded) as 0.
+normalised values lie in (-1, 1) and scaling by s is exact in any binary format
+(e >= -100, so that 1/s is finite in FP32).  A block-field that is identically zero has
+s = 0 and is fed (and decoded) as 0.
 
 Dense layers act as sigma(y W + b) (Sec. 3.3, Eq. (5)).  Shapes:
     encoder 2048 -> 512 (GELU) -> n_lat (linear),
@@ -116,15 +117,20 @@ def field_columns(f: int) -> np.ndarray:
     return np.concatenate([np.arange(z * 256 + f * 64, z * 256 + f * 64 + 64) for z in range(BLK)])
 
 
+EXP_MIN = -100   # smallest scale exponent: 2^-e must stay finite in FP32
+
+
 def block_scales(fields) -> np.ndarray:
-    """s[b][f] = 2^e with max_{x in block b} |f(x)| = m 2^e, m in [0.5, 1) (0 for a zero
-    block-field); returns [nblocks][4]."""
+    """s[b][f] = 2^max(e, EXP_MIN) with max_{x in block b} |f(x)| = m 2^e, m in [0.5, 1)
+    (0 for a zero block-field); returns [nblocks][4].  The clamp only affects blocks
+    whose largest magnitude is below 2^-101 (ahead of the numerical wavefront), which are
+    then normalised to values far below 1 instead of overflowing the scale."""
     X = np.abs(pack_blocks(fields))
     s = np.zeros((X.shape[0], NFIELD))
     for f in range(NFIELD):
         mx = X[:, field_columns(f)].max(axis=1)
         _, e = np.frexp(mx)
-        s[:, f] = np.where(mx > 0, np.ldexp(1.0, e), 0.0)
+        s[:, f] = np.where(mx > 0, np.ldexp(1.0, np.maximum(e, EXP_MIN)), 0.0)
     return s
 
 
