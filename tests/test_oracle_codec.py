@@ -70,7 +70,7 @@ def test_block_scale_exponent_is_clamped_for_tiny_blocks():
     st = [np.full((8, 8, 8), v) for v in (1e-40, -3e-35, 1e-28, 0.0)]
     s = C.block_scales(st)
     assert s[0, 0] == s[0, 1] == 2.0 ** -100      # clamped (maxima below 2^-101)
-    assert s[0, 2] == 2.0 ** -92                  # 1e-28 = 0.63 * 2^-92: not clamped
+    assert s[0, 2] == 2.0 ** -93                  # 1e-28 = 0.99 * 2^-93: not clamped
     assert s[0, 3] == 0
     assert np.isfinite(1.0 / np.float32(s[0, 0]))
 
