@@ -119,13 +119,7 @@ struct EpDecGrid {
   long long M;
   __device__ __forceinline__ void operator()(long long row, int col, const float (&v)[32]) const {
     if (row >= M) return;
-    const float mx = __uint_as_float(__ldg(bmax + row * 4));
-    float s = 0.f;
-    if (mx > 0.f) {
-      int ex;
-      frexpf(mx, &ex);
-      s = ldexpf(1.f, ex);
-    }
+    const float s = gemm::block_scale(__uint_as_float(__ldg(bmax + row * 4)));
     const long long bx = row % NBx, t = row / NBx;
     const long long by = t % NBy, bz = t / NBy;
     const int z = col >> 6, y0 = (col & 63) >> 3;
@@ -240,13 +234,7 @@ __global__ void normalise_kernel(const uint16_t* __restrict__ raw, const unsigne
     const long long b = t / (kNIn / 8);
     const int k = (int)(t % (kNIn / 8)) * 8;
     const int f = (k >> 6) & 3;
-    const float mx = __uint_as_float(bmax[b * 4 + f]);
-    float sc = 0.f;
-    if (mx > 0.f) {
-      int e;
-      frexpf(mx, &e);
-      sc = ldexpf(1.f, -e);
-    }
+    const float sc = gemm::block_inv_scale(__uint_as_float(bmax[b * 4 + f]));
     uint4 v = *reinterpret_cast<const uint4*>(raw + b * kNIn + k);
     uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll

@@ -90,6 +90,21 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
   return d;
 }
 
+// Power-of-two block scale s = 2^max(e, -100) of a block maximum m 2^e (m in [0.5, 1)),
+// 0 for m = 0; the clamp keeps 1/s finite in FP32 for blocks of subnormal values.
+constexpr int kExpMin = -100;
+__device__ __forceinline__ int block_exp(float mx) {
+  int e = 0;
+  frexpf(mx, &e);
+  return e < kExpMin ? kExpMin : e;
+}
+__device__ __forceinline__ float block_scale(float mx) {
+  return mx > 0.f ? ldexpf(1.f, block_exp(mx)) : 0.f;
+}
+__device__ __forceinline__ float block_inv_scale(float mx) {
+  return mx > 0.f ? ldexpf(1.f, -block_exp(mx)) : 0.f;
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   __nv_bfloat162 t = __floats2bfloat162_rn(a, b);
   return *reinterpret_cast<uint32_t*>(&t);
@@ -263,12 +278,7 @@ __global__ void __launch_bounds__(SCALE ? kThreadsScaled : kThreads, 1)
           const int r = (t >> 3) + 16 * q;
           float sc = 0.f;
           if (m0 + r < M) {
-            const float mx = __uint_as_float(__ldg(ascale + (size_t)(m0 + r) * 4 + f));
-            int e = 0;
-            if (mx > 0.f) {
-              frexpf(mx, &e);
-              sc = ldexpf(1.f, -e);
-            }
+            sc = block_inv_scale(__uint_as_float(__ldg(ascale + (size_t)(m0 + r) * 4 + f)));
           }
           uint4 v = *reinterpret_cast<const uint4*>(src + r * 128 + piece * 16);
           uint32_t w[4] = {v.x, v.y, v.z, v.w};

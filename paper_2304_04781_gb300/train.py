@@ -37,8 +37,10 @@ def make_handle(shape, h=10.0, nt=1000, n_lat=64, nrec=64) -> aewave.Solver:
 
 
 def block_scale(bmax: torch.Tensor) -> torch.Tensor:
-    """Power-of-two scales s = 2^e of block maxima m 2^e, m in [0.5, 1) (0 for 0)."""
+    """Power-of-two scales s = 2^max(e, -100) of block maxima m 2^e, m in [0.5, 1)
+    (0 for 0), as the library applies them."""
     _, e = torch.frexp(bmax)
+    e = torch.clamp(e, min=-100)
     return torch.where(bmax > 0, torch.ldexp(torch.ones_like(bmax), e), torch.zeros_like(bmax))
 
 

@@ -40,6 +40,7 @@ def test_encode_matches_oracle(shape, n_lat):
     st = _state(shape, seed=4)
     st[2][:8, :8, :] = 0.0          # block-fields that are exactly zero (scale 0)
     st[3] *= 1e-12                  # a field many orders of magnitude smaller
+    st[1][8:16, :8, :8] *= 1e-36    # a block of FP32 subnormals (clamped scale)
     st = [a.astype(np.float32).astype(np.float64) for a in st]
     lat, bm = s.codec_encode([cuda(a) for a in st])
     z = lat.float().cpu().numpy().astype(np.float64)
@@ -72,7 +73,7 @@ def test_decode_matches_oracle(n_lat):
     bm[3, 0] = 0.0
     e = host(s.codec_decode_e(lat, cuda(bm)))
     _, ex = np.frexp(bm[:, 0].astype(np.float64))
-    sb = np.where(bm[:, 0] > 0, np.ldexp(1.0, ex), 0.0)
+    sb = np.where(bm[:, 0] > 0, np.ldexp(1.0, np.maximum(ex, C.EXP_MIN)), 0.0)
     Xe = np.zeros_like(ref)
     cols = C.field_columns(0)
     Xe[:, cols] = ref[:, cols] * sb[:, None]
