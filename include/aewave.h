@@ -161,9 +161,10 @@ int aew_codec_encode(aew_handle* h, const float* const fields_dev[4], uint16_t* 
 int aew_codec_encode_vectors(aew_handle* h, const uint16_t* vectors_dev, long long n,
                              uint16_t* latents_dev, void* stream);
 
-/* Decode latents.  out_dev: device FP32 [nblocks][2048] normalised block vectors
- * (all four fields, not multiplied by any scale). */
-int aew_codec_decode(aew_handle* h, const uint16_t* latents_dev, float* out_dev, void* stream);
+/* Decode n latent vectors (FP16 [n][n_lat]).  out_dev: device FP32 [n][2048]
+ * normalised block vectors (all four fields, not multiplied by any scale). */
+int aew_codec_decode(aew_handle* h, const uint16_t* latents_dev, long long n, float* out_dev,
+                     void* stream);
 
 /* Decode latents to the strain field only: e_dev[nz][ny][nx] = s_b * (decoded strain
  * part) with the block's power-of-two scale from block_max_dev (device FP32

@@ -64,7 +64,7 @@ _SIGS = [
     ("aew_codec_get", c_int, [c_void_p] + [c_void_p] * 8),
     ("aew_codec_encode", c_int, [c_void_p, POINTER(c_void_p), c_void_p, c_void_p, c_void_p]),
     ("aew_codec_encode_vectors", c_int, [c_void_p, c_void_p, c_longlong, c_void_p, c_void_p]),
-    ("aew_codec_decode", c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("aew_codec_decode", c_int, [c_void_p, c_void_p, c_longlong, c_void_p, c_void_p]),
     ("aew_codec_decode_e", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("aew_forward", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("aew_propagate", c_int, [c_void_p, c_void_p, POINTER(c_void_p), c_int, c_int, c_void_p,
@@ -290,7 +290,7 @@ class Solver:
 
     def codec_decode(self, lat: torch.Tensor) -> torch.Tensor:
         out = torch.empty((lat.shape[0], 2048), device="cuda", dtype=torch.float32)
-        self._check(lib().aew_codec_decode(self._h, _ptr(lat), _ptr(out), _stream()))
+        self._check(lib().aew_codec_decode(self._h, _ptr(lat), lat.shape[0], _ptr(out), _stream()))
         return out
 
     def codec_decode_e(self, lat: torch.Tensor, block_max: torch.Tensor) -> torch.Tensor:

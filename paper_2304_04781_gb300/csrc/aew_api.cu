@@ -931,15 +931,14 @@ int aew_codec_encode(aew_handle* h, const float* const fields_dev[4], uint16_t* 
   return AEW_OK;
 }
 
-int aew_codec_decode(aew_handle* h, const uint16_t* latents_dev, float* out_dev, void* stream) {
+int aew_codec_decode(aew_handle* h, const uint16_t* latents_dev, long long n, float* out_dev,
+                     void* stream) {
   if (!h) return AEW_E_ARG;
-  if (!latents_dev || !out_dev) return fail(h, AEW_E_ARG, "NULL argument");
-  if (h->cfg.nx % 8 || h->cfg.ny % 8 || h->cfg.nz % 8)
-    return fail(h, AEW_E_CONFIG, "codec needs nx, ny, nz multiples of 8");
+  if (!latents_dev || !out_dev || n < 0) return fail(h, AEW_E_ARG, "bad argument");
   if (!aew::codec_ready(h->codec)) return fail(h, AEW_E_NOCODEC, "codec weights not set");
   h->err.clear();
-  cudaError_t e =
-      aew::codec_decode_vectors(h->codec, latents_dev, (long long)nblocks_of(h), out_dev, S(stream));
+  if (n == 0) return AEW_OK;
+  cudaError_t e = aew::codec_decode_vectors(h->codec, latents_dev, n, out_dev, S(stream));
   if (e != cudaSuccess) return cuda_fail(h, e, "codec_decode_vectors");
   if (aew::codec_take_error(h->codec, S(stream)))
     return fail(h, AEW_E_TIMEOUT, "a codec kernel gave up waiting (bounded mbarrier wait)");
