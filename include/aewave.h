@@ -234,6 +234,20 @@ int aew_codec_train_step(aew_handle* h, const uint16_t* batch_dev, int batch, fl
  * (for the adjoint-identity and finite-difference checks).  Synchronises `stream`. */
 int aew_dot(const float* a_dev, const float* b_dev, size_t n, double* out_host, void* stream);
 
+/* aew_dot without any device allocation, for callers that cannot allocate device
+ * memory (an application whose allocations all go through its own pool, or a hook that
+ * must not change the device memory footprint).  No counterpart in the paper: it is a
+ * service variant of aew_dot.  The per-block partial sums live in a fixed array in
+ * device memory inside the library (512 KiB per GPU, held until the process exits);
+ * n must be at most 2^32 (AEW_E_ARG otherwise, before any device work).
+ * out_dev: device FP64 scalar receiving sum a[i] b[i] (written on `stream`; the call
+ * does not synchronise).  The first call on a device looks up the array's device
+ * address, so it must not be made during stream capture.  All calls share the array:
+ * calls that overlap on the GPU race and must be serialised by the caller.  Returns
+ * AEW_E_ARG for NULL pointers, AEW_E_CUDA if a launch fails. */
+int aew_dot_noalloc(const float* a_dev, const float* b_dev, size_t n, double* out_dev,
+                    void* stream);
+
 /* The binomial checkpointing plan the library runs for nt steps with s state slots
  * (host only, no device work).  ops/args (host, capacity `cap`) receive the actions:
  * op 0 = advance args steps, 1 = store in slot args, 2 = restore slot args (-1 = the

@@ -77,6 +77,7 @@ _SIGS = [
     ("aew_codec_train_step", c_int, [c_void_p, c_void_p, c_int, c_float, POINTER(c_float),
                                      c_void_p]),
     ("aew_dot", c_int, [c_void_p, c_void_p, c_size_t, POINTER(c_double), c_void_p]),
+    ("aew_dot_noalloc", c_int, [c_void_p, c_void_p, c_size_t, c_void_p, c_void_p]),
     ("aew_revolve_plan", c_int, [c_int, c_int, c_void_p, c_void_p, c_longlong,
                                  POINTER(c_longlong), POINTER(c_longlong)]),
 ]
@@ -135,6 +136,16 @@ def dot(a: torch.Tensor, b: torch.Tensor) -> float:
     if rc != 0:
         raise AewError(rc, "aew_dot failed")
     return out.value
+
+
+def dot_noalloc(a: torch.Tensor, b: torch.Tensor, out: torch.Tensor) -> None:
+    """aew_dot_noalloc: FP64 inner product into the CUDA FP64 scalar `out`, with no
+    device allocation (asynchronous on the current stream)."""
+    assert a.numel() == b.numel() and a.dtype == torch.float32 and b.dtype == torch.float32
+    assert out.dtype == torch.float64 and out.numel() == 1
+    rc = lib().aew_dot_noalloc(_ptr(a), _ptr(b), a.numel(), _ptr(out), _stream())
+    if rc != 0:
+        raise AewError(rc, "aew_dot_noalloc failed")
 
 
 def revolve_plan(nt: int, s: int):
