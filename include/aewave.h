@@ -33,6 +33,11 @@
  *    Calls that return a host scalar (misfit, dot) synchronise that stream.
  *  - Return value: AEW_OK (0) or a negative AEW_E_* code; aew_last_error() then gives
  *    a message.  A failed call leaves the handle usable.
+ *  - Device waits are bounded.  A kernel whose wait gives up sets the handle's sticky
+ *    device error flag and returns; later kernels of the handle see the flag and return
+ *    at once.  Calls that synchronise (aew_gradient, aew_hessvec, the codec calls) and
+ *    aew_sync_check read and clear the flag and report AEW_E_TIMEOUT; the asynchronous
+ *    solves (aew_forward, aew_propagate, aew_jvp) leave it for the next such call.
  *  - A handle is not thread-safe: one call at a time per handle.
  */
 #ifndef AEWAVE_H
@@ -177,6 +182,15 @@ int aew_codec_decode_e(aew_handle* h, const uint16_t* latents_dev, const float* 
  * Solves
  * ------------------------------------------------------------------------------- */
 
+/* Synchronise `stream` and report (and clear) a timed-out device wait of any earlier
+ * call of this handle: AEW_OK or AEW_E_TIMEOUT. */
+int aew_sync_check(aew_handle* h, void* stream);
+
+/* Test hook for the failure path: enqueue one kernel whose bounded wait (wait_ns,
+ * 1 ns .. 1 s) runs out because nothing completes it; it sets the handle's sticky
+ * error flag exactly as a timed-out stencil or codec kernel would.  Nothing faults. */
+int aew_test_wait_timeout(aew_handle* h, unsigned long long wait_ns, void* stream);
+
 /* d = F(c): forward solve from zero initial state.  c_dev [nz][ny][nx] in m/s;
  * wavelet_host: s^n for n = 0..nt-1 (NULL = the default Ricker force);
  * d_dev: [nt+1][nrec][3] (written; row 0 = B v^0 = 0). */
@@ -185,7 +199,8 @@ int aew_forward(aew_handle* h, const float* c_dev, const float* wavelet_host,
 
 /* Advance a caller-owned state {e, vx, vy, vz} (device, in place) by nsteps leapfrog
  * steps starting at time index n0, with source s^n = wavelet_host[n - n0] (NULL =
- * no source) and receiver record d_dev[nsteps+1][nrec][3] (NULL = none). */
+ * no source) and receiver record d_dev[nsteps+1][nrec][3] (NULL = none).  The four
+ * state pointers must be 16-byte aligned (AEW_E_ARG otherwise). */
 int aew_propagate(aew_handle* h, const float* c_dev, float* const state_dev[4], int n0,
                   int nsteps, const float* wavelet_host, float* d_dev, void* stream);
 

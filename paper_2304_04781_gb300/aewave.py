@@ -66,6 +66,8 @@ _SIGS = [
     ("aew_codec_encode_vectors", c_int, [c_void_p, c_void_p, c_longlong, c_void_p, c_void_p]),
     ("aew_codec_decode", c_int, [c_void_p, c_void_p, c_longlong, c_void_p, c_void_p]),
     ("aew_codec_decode_e", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("aew_sync_check", c_int, [c_void_p, c_void_p]),
+    ("aew_test_wait_timeout", c_int, [c_void_p, ctypes.c_ulonglong, c_void_p]),
     ("aew_forward", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("aew_propagate", c_int, [c_void_p, c_void_p, POINTER(c_void_p), c_int, c_int, c_void_p,
                               c_void_p, c_void_p]),
@@ -260,6 +262,15 @@ class Solver:
         dd = self._drec()
         self._check(lib().aew_jvp(self._h, _ptr(dc), _ptr(dd), _stream()))
         return dd
+
+    def sync_check(self):
+        """Synchronise the current stream; raise AewError if a kernel of this handle gave
+        up a bounded device wait since the last check."""
+        self._check(lib().aew_sync_check(self._h, _stream()))
+
+    def test_wait_timeout(self, wait_ns: int = 1_000_000):
+        """Enqueue a kernel whose bounded wait runs out (failure-path test hook)."""
+        self._check(lib().aew_test_wait_timeout(self._h, int(wait_ns), _stream()))
 
     def stats(self) -> dict:
         s = aew_stats_t()

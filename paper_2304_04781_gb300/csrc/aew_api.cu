@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -149,6 +150,7 @@ int fwd_step(aew_handle* h, int n, float* const in[4], float* const out[4], cons
   a.krec = d_row ? h->krec : -1;
   a.rec_map = h->rec_map;
   a.d_out = d_row;
+  a.err = aew::codec_err_flag(h->codec);
   AEW_CK(aew::launch_fwd_step(a, false, s));
   ++h->stats.kernel_launches;
   return AEW_OK;
@@ -180,6 +182,7 @@ int incr_step(aew_handle* h, float* const in[4], float* const out[4], const floa
   a.krec = d_row ? h->krec : -1;
   a.rec_map = h->rec_map;
   a.d_out = d_row;
+  a.err = aew::codec_err_flag(h->codec);
   AEW_CK(aew::launch_fwd_step(a, incr, s));
   ++h->stats.kernel_launches;
   return AEW_OK;
@@ -212,6 +215,7 @@ int adj_step(aew_handle* h, int n, int cur, const float* resid, const float* en,
   a.krec = h->krec;
   a.rec_map = h->rec_map;
   a.resid = (resid && h->nrow) ? resid + (size_t)(n + 1) * h->nrow : nullptr;
+  a.err = aew::codec_err_flag(h->codec);
   AEW_CK(aew::launch_adj_step(a, s));
   ++h->stats.kernel_launches;
   return AEW_OK;
@@ -279,13 +283,12 @@ float* drow(aew_handle* h, float* d, int n) {
 // ---------------------------------------------------------------------------------
 // AE helpers
 // ---------------------------------------------------------------------------------
-// encoder GEMMs of packed state n (xpk[n % 2]) into latents[n]
+// encoder GEMMs of the packed, normalised state n (xpk[n % 2]) into latents[n]
 int encode_packed(aew_handle* h, int n, cudaStream_t s) {
   const size_t nb = nblocks_of(h);
-  cudaError_t e = aew::codec_encode_raw(h->codec, h->xpk[n & 1], h->bmx + (size_t)n * nb * 4,
-                                        (long long)nb, h->lat + (size_t)n * nb * h->cfg.n_lat,
-                                        h->ovf, s);
-  if (e != cudaSuccess) return cuda_fail(h, e, "codec_encode_raw");
+  cudaError_t e = aew::codec_encode_vectors(h->codec, h->xpk[n & 1], (long long)nb,
+                                            h->lat + (size_t)n * nb * h->cfg.n_lat, h->ovf, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "codec_encode_vectors");
   h->stats.kernel_launches += 2;
   return AEW_OK;
 }
@@ -467,7 +470,8 @@ int gradient_ae(aew_handle* h, const float* d_obs, const float* wav, cudaStream_
   const int nt = h->cfg.nt;
   int rc;
   if ((rc = zero_state(h, h->st[0], s))) return rc;
-  AEW_CK(cudaMemsetAsync(h->bmx, 0, (size_t)nt * nblocks_of(h) * 4 * sizeof(unsigned), s));
+  // block maxima of every packed state are stored whole by its step; state 0 is zero
+  AEW_CK(cudaMemsetAsync(h->bmx, 0, nblocks_of(h) * 4 * sizeof(unsigned), s));
   AEW_CK(cudaMemsetAsync(h->ovf, 0, sizeof(int), s));
   AEW_CK(cudaMemsetAsync(h->d, 0, h->nrow * sizeof(float), s));
   if ((rc = join(h, s, h->side, h->ev_sync))) return rc;
@@ -578,7 +582,10 @@ int aew_create(const aew_config* cfg, aew_handle** out) {
          dalloc(h, &h->ovf, 1) && dalloc(h, &h->xpk[0], nb * aew::kNIn) &&
          dalloc(h, &h->xpk[1], nb * aew::kNIn) && dalloc(h, &h->edb[0], C) &&
          dalloc(h, &h->edb[1], C);
-    ok = ok && cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) == cudaSuccess;
+    int prio = 0, lo = 0, hi = 0;
+    if (const char* env = getenv("AEW_SIDE_PRIORITY"))   // tuning override: codec stream first
+      if (atoi(env) != 0 && cudaDeviceGetStreamPriorityRange(&lo, &hi) == cudaSuccess) prio = hi;
+    ok = ok && cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, prio) == cudaSuccess;
     for (int i = 0; ok && i < 2; ++i)
       ok = cudaEventCreateWithFlags(&h->ev_a[i], cudaEventDisableTiming) == cudaSuccess &&
            cudaEventCreateWithFlags(&h->ev_b[i], cudaEventDisableTiming) == cudaSuccess;
@@ -660,11 +667,30 @@ int aew_forward(aew_handle* h, const float* c_dev, const float* wavelet_host, fl
   return AEW_OK;
 }
 
+int aew_sync_check(aew_handle* h, void* stream) {
+  if (!h) return AEW_E_ARG;
+  h->err.clear();
+  if (aew::codec_take_error(h->codec, S(stream)))
+    return fail(h, AEW_E_TIMEOUT, "a kernel gave up waiting (bounded mbarrier wait)");
+  return AEW_OK;
+}
+
+int aew_test_wait_timeout(aew_handle* h, unsigned long long wait_ns, void* stream) {
+  if (!h || wait_ns == 0 || wait_ns > 1000000000ull) return AEW_E_ARG;
+  h->err.clear();
+  AEW_CK(aew::launch_wait_probe(aew::codec_err_flag(h->codec), wait_ns, S(stream)));
+  ++h->stats.kernel_launches;
+  return AEW_OK;
+}
+
 int aew_propagate(aew_handle* h, const float* c_dev, float* const state_dev[4], int n0,
                   int nsteps, const float* wavelet_host, float* d_dev, void* stream) {
   if (!h || !state_dev || nsteps < 0) return AEW_E_ARG;
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 4; ++i) {
     if (!state_dev[i]) return fail(h, AEW_E_ARG, "state pointer is NULL");
+    if (reinterpret_cast<uintptr_t>(state_dev[i]) & 15)
+      return fail(h, AEW_E_ARG, "state pointers must be 16-byte aligned");
+  }
   h->err.clear();
   cudaStream_t s = S(stream);
   int rc = prepare_c(h, c_dev, s);
@@ -713,8 +739,8 @@ int aew_gradient(aew_handle* h, const float* c_dev, const float* d_obs_dev, floa
     rc = gradient_ae(h, d_obs_dev, wav, s);
   }
   if (rc) return rc;
-  if (h->cfg.storage == AEW_AE && aew::codec_take_error(h->codec, s))
-    return fail(h, AEW_E_TIMEOUT, "a codec kernel gave up waiting (bounded mbarrier wait)");
+  if (aew::codec_take_error(h->codec, s))
+    return fail(h, AEW_E_TIMEOUT, "a kernel gave up waiting (bounded mbarrier wait)");
   AEW_CK(aew::launch_finalize_grad(h->c, h->acc64, g_dev, h->C, s));
   ++h->stats.kernel_launches;
   if (misfit_host || h->cfg.storage == AEW_AE) {
@@ -838,8 +864,8 @@ int aew_hessvec(aew_handle* h, const float* dc_dev, float* hdc_dev, void* stream
     }
   }
   h->stats.hvp_forward_steps = fwd;
-  if (h->cfg.storage == AEW_AE && aew::codec_take_error(h->codec, s))
-    return fail(h, AEW_E_TIMEOUT, "a codec kernel gave up waiting (bounded mbarrier wait)");
+  if (aew::codec_take_error(h->codec, s))
+    return fail(h, AEW_E_TIMEOUT, "a kernel gave up waiting (bounded mbarrier wait)");
   AEW_CK(aew::launch_finalize_grad(h->c, h->acc64, hdc_dev, h->C, s));
   ++h->stats.kernel_launches;
   return AEW_OK;

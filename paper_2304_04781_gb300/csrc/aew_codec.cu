@@ -3,20 +3,23 @@
 // Algorithm 1.
 //
 // Block vector of an 8x8x8-node block: k = z*256 + f*64 + y*8 + x (f = e, vx, vy, vz);
-// block b = (bz*NBy + by)*NBx + bx.  Each field is divided by its scale s_f (the
-// running maximum of |f|).
+// block b = (bz*NBy + by)*NBx + bx.  Each field of each block is divided by its
+// power-of-two scale s_{b,f} = 2^max(e, -100), m 2^e (m in [1/2, 1)) the block's max |f|
+// (exact in BF16).  Inside the gradient the forward step packs and normalises the
+// vectors itself; the entry points here pack a given state (pack_raw_kernel, then
+// normalise_kernel).
 //
-// Encoder: A = normalised block vectors gathered straight from the four FP32 grid
-// fields (BF16, RNE), times W1 (2048 x 512) -> +b1, GELU -> H (BF16), times W2
-// (512 x n_lat) -> +b2 -> FP16 latent.  Decoder: latent (FP16) times W3 (FP16,
-// n_lat x 512) -> +b3, GELU -> H (BF16), times W4 (BF16, 512 x 2048, or only its 512
-// strain columns inside the adjoint) -> +b4, times s_e, scattered back to the grid.
+// Encoder: A = normalised BF16 block vectors, times W1 (2048 x 512) -> +b1, GELU -> H
+// (BF16), times W2 (512 x n_lat) -> +b2 -> FP16 latent.  Decoder: latent (FP16) times W3
+// (FP16, n_lat x 512) -> +b3, GELU -> H (BF16), times W4 (BF16, 512 x 2048, or only its
+// 512 strain columns inside the adjoint) -> +b4, times s_{b,e}, scattered back to the grid.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "aew_codec.cuh"
@@ -225,9 +228,10 @@ __global__ void pack_raw_kernel(const float* f0, const float* f1, const float* f
   }
 }
 
-// y = x * 2^-e per block-field (exact), from raw BF16 vectors and block maxima
-__global__ void normalise_kernel(const uint16_t* __restrict__ raw, const unsigned* __restrict__ bmax,
-                                 long long n, uint16_t* __restrict__ out) {
+// y = x * 2^-e per block-field (exact), from raw BF16 vectors and block maxima; out may
+// be raw itself (each thread rewrites only the 16 bytes it read)
+__global__ void normalise_kernel(const uint16_t* raw, const unsigned* __restrict__ bmax,
+                                 long long n, uint16_t* out) {
   const long long total = n * (kNIn / 8);   // 16-byte pieces
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
@@ -257,20 +261,27 @@ __global__ void strain_rows_kernel(const uint16_t* __restrict__ W4t, uint16_t* _
 // =================================================================================
 namespace gemm {
 
-CUresult make_tmap(CUtensorMap* map, const void* base, bool fp16, long long rows, int K,
-                   long long ld, int box_rows, bool swizzle128) {
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  if (!encode) {
+  static std::once_flag once;
+  std::call_once(once, [] {
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
                                          &q) != cudaSuccess ||
         fn == nullptr || q != cudaDriverEntryPointSuccess) {
       cudaGetLastError();
-      return CUDA_ERROR_NOT_FOUND;
+      return;
     }
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  }
+  });
+  return encode;
+}
+
+CUresult make_tmap(CUtensorMap* map, const void* base, bool fp16, long long rows, int K,
+                   long long ld, int box_rows, bool swizzle128) {
+  PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+  if (!encode) return CUDA_ERROR_NOT_FOUND;
   const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
   const cuuint32_t box[2] = {swizzle128 ? 64u : 8u, (cuuint32_t)box_rows};
@@ -309,6 +320,7 @@ Codec* codec_new(int n_lat) {
   }
   cudaMemset(c->err, 0, sizeof(int));
   if (const char* env = getenv("AEW_GEMM_CTAS")) c->max_ctas = atoi(env);   // tuning override
+  if (const char* env = getenv("AEW_GEMM_STAGES")) c->max_stages = atoi(env);   // tuning override
   c->bytes += ((size_t)2 * kNIn * kNHid + 2 * nl * kNHid) * 2;
   return c;
 }
@@ -330,6 +342,8 @@ void codec_free(Codec* c) {
 }
 
 int codec_nlat(const Codec* c) { return c->n_lat; }
+
+int* codec_err_flag(Codec* c) { return c->err; }
 
 bool codec_take_error(Codec* c, cudaStream_t s) {
   int v = 0;
@@ -380,24 +394,10 @@ cudaError_t codec_encode_grid(Codec* c, const float* const f[4], int nx, int ny,
                               unsigned* bmax, uint16_t* lat, int* overflow, cudaStream_t s) {
   const long long nb = (long long)(nx / 8) * (ny / 8) * (nz / 8);
   if (!ensure_X(c, (size_t)nb)) return cudaErrorMemoryAllocation;
-  cudaError_t e = snapshot_pack(f, nx, ny, nz, bmax, c->X, nullptr, s);
+  // raw BF16 block vectors and block maxima, then normalised in place
+  cudaError_t e = snapshot_pack(f, nx, ny, nz, bmax, c->X, c->X, s);
   if (e != cudaSuccess) return e;
-  return codec_encode_raw(c, c->X, bmax, nb, lat, overflow, s);
-}
-
-cudaError_t codec_encode_raw(Codec* c, const uint16_t* X, const unsigned* bmax, long long n,
-                             uint16_t* lat, int* overflow, cudaStream_t s) {
-  if (!ensure_H(c, (size_t)n)) return cudaErrorMemoryAllocation;
-  EpBiasGeluH ep{c->w[1], c->H, n};
-  cudaError_t e = gemm::launch<256, true, EpBiasGeluH, true>(
-      n, kNHid, kNIn, gemm::Mat{X, n, kNIn}, gemm::Mat{c->W1t, kNHid, kNIn}, ep, c->err, s,
-      c->max_ctas, bmax);
-  if (e != cudaSuccess) return e;
-  const int nl = c->n_lat;
-  EpLatent e2{c->w[3], lat, nl, n, overflow};
-  const gemm::Mat a2{c->H, n, kNHid}, b2{c->W2t, nl, kNHid};
-  if (nl == 64) return gemm::launch<64, true>(n, nl, kNHid, a2, b2, e2, c->err, s, c->max_ctas);
-  return gemm::launch<32, true>(n, nl, kNHid, a2, b2, e2, c->err, s, c->max_ctas);
+  return codec_encode_vectors(c, c->X, nb, lat, overflow, s);
 }
 
 
@@ -406,13 +406,13 @@ cudaError_t codec_encode_vectors(Codec* c, const uint16_t* vec, long long n, uin
   if (!ensure_H(c, (size_t)n)) return cudaErrorMemoryAllocation;
   EpBiasGeluH ep{c->w[1], c->H, n};
   cudaError_t e = gemm::launch<256, true>(n, kNHid, kNIn, gemm::Mat{vec, n, kNIn},
-                                          gemm::Mat{c->W1t, kNHid, kNIn}, ep, c->err, s, c->max_ctas);
+                                          gemm::Mat{c->W1t, kNHid, kNIn}, ep, c->err, s, c->max_ctas, c->max_stages);
   if (e != cudaSuccess) return e;
   const int nl = c->n_lat;
   EpLatent e2{c->w[3], lat, nl, n, overflow};
   const gemm::Mat a2{c->H, n, kNHid}, b2{c->W2t, nl, kNHid};
-  if (nl == 64) return gemm::launch<64, true>(n, nl, kNHid, a2, b2, e2, c->err, s, c->max_ctas);
-  return gemm::launch<32, true>(n, nl, kNHid, a2, b2, e2, c->err, s, c->max_ctas);
+  if (nl == 64) return gemm::launch<64, true>(n, nl, kNHid, a2, b2, e2, c->err, s, c->max_ctas, c->max_stages);
+  return gemm::launch<32, true>(n, nl, kNHid, a2, b2, e2, c->err, s, c->max_ctas, c->max_stages);
 }
 
 static cudaError_t decode_hidden(Codec* c, const uint16_t* lat, long long nb, cudaStream_t s) {
@@ -420,7 +420,7 @@ static cudaError_t decode_hidden(Codec* c, const uint16_t* lat, long long nb, cu
   const int nl = c->n_lat;
   EpBiasGeluH ep{c->w[5], c->H, nb};
   return gemm::launch<256, false>(nb, kNHid, nl, gemm::Mat{lat, nb, nl},
-                                  gemm::Mat{c->W3t, kNHid, nl}, ep, c->err, s, c->max_ctas);
+                                  gemm::Mat{c->W3t, kNHid, nl}, ep, c->err, s, c->max_ctas, c->max_stages);
 }
 
 cudaError_t codec_decode_grid_e(Codec* c, const uint16_t* lat, int nx, int ny, int nz,
@@ -431,7 +431,7 @@ cudaError_t codec_decode_grid_e(Codec* c, const uint16_t* lat, int nx, int ny, i
   if (e != cudaSuccess) return e;
   EpDecGrid ep{c->w[7], bmax, e_out, nx, ny, nz, NBx, NBy, nb};
   return gemm::launch<256, true>(nb, 512, kNHid, gemm::Mat{c->H, nb, kNHid},
-                                 gemm::Mat{c->W4e, 512, kNHid}, ep, c->err, s, c->max_ctas);
+                                 gemm::Mat{c->W4e, 512, kNHid}, ep, c->err, s, c->max_ctas, c->max_stages);
 }
 
 cudaError_t codec_decode_vectors(Codec* c, const uint16_t* lat, long long nvec, float* out,
@@ -440,7 +440,7 @@ cudaError_t codec_decode_vectors(Codec* c, const uint16_t* lat, long long nvec, 
   if (e != cudaSuccess) return e;
   EpVec ep{c->w[7], out, kNIn, nvec};
   return gemm::launch<256, true>(nvec, kNIn, kNHid, gemm::Mat{c->H, nvec, kNHid},
-                                 gemm::Mat{c->W4t, kNIn, kNHid}, ep, c->err, s, c->max_ctas);
+                                 gemm::Mat{c->W4t, kNIn, kNHid}, ep, c->err, s, c->max_ctas, c->max_stages);
 }
 
 cudaError_t snapshot_pack(const float* const f[4], int nx, int ny, int nz, unsigned* bmax,

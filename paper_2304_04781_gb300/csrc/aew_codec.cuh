@@ -26,15 +26,11 @@ cudaError_t codec_get_weights(const Codec* c, float* const w[8]);
 // Rebuild the tensor-core operand copies of the weights from the FP32 masters.
 cudaError_t codec_refresh(Codec* c, cudaStream_t s);
 
-// Encode one grid state: raw BF16 block vectors plus per-block, per-field maxima of |f|
-// (bmax, float bits [nblocks][4], written), then the encoder with the power-of-two
-// per-block normalisation applied to its input.  latents FP16 [nblocks][n_lat].
+// Encode one grid state: BF16 block vectors plus per-block, per-field maxima of |f|
+// (bmax, float bits [nblocks][4], written), normalised by the power-of-two block scales,
+// then the encoder.  latents FP16 [nblocks][n_lat].
 cudaError_t codec_encode_grid(Codec* c, const float* const f[4], int nx, int ny, int nz,
                               unsigned* bmax, uint16_t* lat, int* overflow, cudaStream_t s);
-
-// Encoder on raw BF16 block vectors X [n][2048] with block maxima bmax [n][4].
-cudaError_t codec_encode_raw(Codec* c, const uint16_t* X, const unsigned* bmax, long long n,
-                             uint16_t* lat, int* overflow, cudaStream_t s);
 
 // Encode already normalised BF16 block vectors [n][2048] into FP16 latents [n][n_lat].
 cudaError_t codec_encode_vectors(Codec* c, const uint16_t* vec, long long n, uint16_t* lat,
@@ -58,6 +54,8 @@ cudaError_t snapshot_pack(const float* const f[4], int nx, int ny, int nz, unsig
 // Device error flag of the codec kernels (set by a bounded wait that gave up); read and
 // clear it (synchronises the stream).  Returns true if it was set.
 bool codec_take_error(Codec* c, cudaStream_t s);
+// the device error flag the codec kernels and the stencil steps set on a timed-out wait
+int* codec_err_flag(Codec* c);
 
 // One training step (MSE + LAMB); loss (device float) written if loss_dev != null.
 cudaError_t codec_train_step(Codec* c, const uint16_t* batch, int B, float lr, float* loss_dev,

@@ -28,6 +28,7 @@ struct Codec {
   float* sc_tmp = nullptr;
   int* err = nullptr;
   int max_ctas = 0;          // CTA cap of the codec GEMMs (0: one per SM)
+  int max_stages = 0;        // stage cap of the codec GEMMs (0: as many as fit)
   size_t bytes = 0;
   // training state (allocated by the training unit)
   void* train = nullptr;

@@ -24,6 +24,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <cstdint>
 
@@ -39,18 +40,16 @@ constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kTmaWarp = 8;
 constexpr int kMmaWarp = 9;
 constexpr int kThreads = 320;
-constexpr int kXfWarp0 = 10;                 // warps 10-13: A-operand scaling (SCALE only)
-constexpr int kThreadsScaled = 448;
 constexpr uint64_t kWaitNs = 200000000ull;   // 200 ms (a healthy wait takes microseconds)
 constexpr int kSmemBudget = 200 * 1024;
 
-template <int BN, bool SCALE = false>
+template <int BN>
 __host__ __device__ constexpr int stage_bytes() {
-  return kBM * kBK * 2 * (SCALE ? 2 : 1) + BN * kBK * 2;
+  return kBM * kBK * 2 + BN * kBK * 2;   // [A][B]
 }
-template <int BN, bool SCALE = false>
+template <int BN>
 __host__ __device__ constexpr int max_stages() {
-  return kSmemBudget / stage_bytes<BN, SCALE>() > 8 ? 8 : kSmemBudget / stage_bytes<BN, SCALE>();
+  return kSmemBudget / stage_bytes<BN>() > 8 ? 8 : kSmemBudget / stage_bytes<BN>();
 }
 inline size_t smem_bytes_for(int stage_b, int ns) { return (size_t)ns * stage_b + 256 + 1024; }
 
@@ -61,6 +60,8 @@ inline size_t smem_bytes_for(int stage_b, int ns) { return (size_t)ns * stage_b 
 // (64 K x box_rows) with 128-byte swizzle, or (8 K x box_rows) unswizzled.
 CUresult make_tmap(CUtensorMap* map, const void* base, bool fp16, long long rows, int K,
                    long long ld, int box_rows, bool swizzle128);
+// the driver's cuTensorMapEncodeTiled (looked up once; null if unavailable)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
                                             uint32_t mbar) {
@@ -127,28 +128,23 @@ __device__ __forceinline__ float gelu_prime_f(float a) {
 // ---------------------------------------------------------------------------------
 // The kernel (persistent: each CTA walks tiles blockIdx.x, +gridDim.x, ...)
 // ---------------------------------------------------------------------------------
-// SCALE: the A operand of row r, K chunk c (64 values of field f = c & 3) is multiplied
-// by 2^-e, e the binary exponent of ascale[r][f] (a float stored as bits; 0 -> row of
-// zeros), by four extra warps between the TMA landing and the MMA (exact for powers
-// of two).
-template <int BN, bool BF16, bool SW, bool SCALE, class EP>
-__global__ void __launch_bounds__(SCALE ? kThreadsScaled : kThreads, 1)
+template <int BN, bool BF16, bool SW, class EP>
+__global__ void __launch_bounds__(kThreads, 1)
     gemm_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
-                int M, int N, int K, int ns, const unsigned* ascale, EP ep, int* err) {
+                int M, int N, int K, int ns, EP ep, int* err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   constexpr int A_BYTES = kBM * kBK * 2;
   constexpr int B_BYTES = BN * kBK * 2;
-  constexpr int STAGE = stage_bytes<BN, SCALE>();         // [A (TMA)][B][A scaled]
+  constexpr int STAGE = stage_bytes<BN>();                // [A][B]
   constexpr uint32_t TCOLS = 2 * BN < 32 ? 32 : 2 * BN;   // two accumulators
   constexpr uint32_t IDESC = tc::idesc_f16(kBM, BN, BF16);
   static_assert(BN % 32 == 0 && BN <= 256, "BN");
 
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + ns * STAGE);
   uint64_t* empty = full + ns;
-  uint64_t* ready = empty + ns;    // SCALE: scaled A operand of the stage written
-  uint64_t* accf = ready + ns;     // accumulator a ready for the epilogue
+  uint64_t* accf = empty + ns;     // accumulator a ready for the epilogue
   uint64_t* acce = accf + 2;       // accumulator a drained by the epilogue
   uint32_t* tslot = reinterpret_cast<uint32_t*>(acce + 2);
   int* abort_flag = reinterpret_cast<int*>(tslot + 1);
@@ -170,7 +166,6 @@ __global__ void __launch_bounds__(SCALE ? kThreadsScaled : kThreads, 1)
     for (int s = 0; s < ns; ++s) {
       tc::mbar_init(tc::smem_u32(&full[s]), 1);
       tc::mbar_init(tc::smem_u32(&empty[s]), 1);
-      tc::mbar_init(tc::smem_u32(&ready[s]), 128);
     }
     for (int a = 0; a < 2; ++a) {
       tc::mbar_init(tc::smem_u32(&accf[a]), 1);
@@ -229,14 +224,14 @@ __global__ void __launch_bounds__(SCALE ? kThreadsScaled : kThreads, 1)
         bool ok = true;
         for (int c = 0; c < nK; ++c, ++it) {
           const int s = it % ns;
-          if (!tc::mbar_wait(tc::smem_u32(SCALE ? &ready[s] : &full[s]), (it / ns) & 1, kWaitNs)) {
+          if (!tc::mbar_wait(tc::smem_u32(&full[s]), (it / ns) & 1, kWaitNs)) {
             atomicExch(abort_flag, 1);
             ok = false;
             break;
           }
           tc::fence_after_sync();
           const uint32_t st0 = tc::smem_u32(smem + s * STAGE);
-          const uint32_t a0 = SCALE ? st0 + A_BYTES + B_BYTES : st0, b0 = st0 + A_BYTES;
+          const uint32_t a0 = st0, b0 = st0 + A_BYTES;
 #pragma unroll
           for (int kk = 0; kk < kBK / 16; ++kk) {
             uint64_t ad, bd;
@@ -256,44 +251,6 @@ __global__ void __launch_bounds__(SCALE ? kThreadsScaled : kThreads, 1)
       }
     }
     __syncwarp();
-  } else if (SCALE && warp >= kXfWarp0) {
-    // ------------------------------------------------------------- A-operand scaling
-    const int t = tid - kXfWarp0 * 32;          // 0..127
-    const int piece = t & 7;                    // 16-byte piece of a 128-byte row
-    int it = 0;
-    for (int tt = blockIdx.x; tt < T; tt += gridDim.x) {
-      const int m0 = (tt / tn) * kBM;
-      for (int c = 0; c < nK; ++c, ++it) {
-        const int s = it % ns;
-        if (!tc::mbar_wait(tc::smem_u32(&full[s]), (it / ns) & 1, kWaitNs)) {
-          atomicExch(abort_flag, 1);
-          tt = T;
-          break;
-        }
-        const uint8_t* src = smem + s * STAGE;
-        uint8_t* dst = smem + s * STAGE + A_BYTES + B_BYTES;
-        const int f = c & 3;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int r = (t >> 3) + 16 * q;
-          float sc = 0.f;
-          if (m0 + r < M) {
-            sc = block_inv_scale(__uint_as_float(__ldg(ascale + (size_t)(m0 + r) * 4 + f)));
-          }
-          uint4 v = *reinterpret_cast<const uint4*>(src + r * 128 + piece * 16);
-          uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const float lo = __uint_as_float(w[j] << 16) * sc;
-            const float hi = __uint_as_float(w[j] & 0xffff0000u) * sc;
-            w[j] = pack_bf16(lo, hi);
-          }
-          *reinterpret_cast<uint4*>(dst + r * 128 + piece * 16) = make_uint4(w[0], w[1], w[2], w[3]);
-        }
-        tc::fence_proxy_async();
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&ready[s])) : "memory");
-      }
-    }
   } else {
     // ------------------------------------------------------------- epilogue warps
     const int q = warp & 3, hh = (warp >> 2) & 1;
@@ -338,22 +295,23 @@ struct Mat {
 #define AEW_GEMM_SWIZZLE 1
 #endif
 
-template <int BN, bool BF16, class EP, bool SCALE = false>
+template <int BN, bool BF16, class EP>
 cudaError_t launch(long long M, int N, int K, const Mat& A, const Mat& B, const EP& ep, int* err,
-                   cudaStream_t s, int max_ctas = 0, const unsigned* ascale = nullptr) {
+                   cudaStream_t s, int max_ctas = 0, int max_ns = 0) {
   constexpr bool SW = AEW_GEMM_SWIZZLE != 0;
-  auto kern = gemm_kernel<BN, BF16, SW, SCALE, EP>;
+  auto kern = gemm_kernel<BN, BF16, SW, EP>;
   const int nK = (K + kBK - 1) / kBK;
-  int ns = max_stages<BN, SCALE>();
+  int ns = max_stages<BN>();
   if (ns > nK + 2) ns = nK + 2;   // a few chunks of the next tile may be in flight
+  if (max_ns > 0 && ns > max_ns) ns = max_ns;   // fewer stages: room for a co-resident CTA
   if (ns < 2) ns = 2;
-  const size_t smem = smem_bytes_for(stage_bytes<BN, SCALE>(), ns);
+  const size_t smem = smem_bytes_for(stage_bytes<BN>(), ns);
   static int sms = 0;
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(
         kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-        (int)smem_bytes_for(stage_bytes<BN, SCALE>(), max_stages<BN, SCALE>()));
+        (int)smem_bytes_for(stage_bytes<BN>(), max_stages<BN>()));
     if (e != cudaSuccess) return e;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -367,7 +325,7 @@ cudaError_t launch(long long M, int N, int K, const Mat& A, const Mat& B, const 
   const long long tiles = ((M + kBM - 1) / kBM) * (long long)((N + BN - 1) / BN);
   const int cap = (max_ctas > 0 && max_ctas < sms) ? max_ctas : sms;
   const int grid = (int)(tiles < cap ? tiles : cap);
-  kern<<<grid, SCALE ? kThreadsScaled : kThreads, smem, s>>>(ta, tb, (int)M, N, K, ns, ascale, ep, err);
+  kern<<<grid, kThreads, smem, s>>>(ta, tb, (int)M, N, K, ns, ep, err);
   return cudaGetLastError();
 }
 

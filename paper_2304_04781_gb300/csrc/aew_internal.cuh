@@ -37,11 +37,13 @@ struct FwdStep {
   int krec;          // receiver node plane (-1: none)
   const int* rec_map;  // [ny][nx] receiver index or -1
   float* d_out;        // receiver record row [nrec][3] (or null)
-  // Optional packing of the INPUT state n into BF16 block vectors [nblocks][2048]
-  // (order z*256 + f*64 + y*8 + x, not yet normalised) and the per-block, per-field
-  // maxima of |f| (float bits, atomicMax into bmax[nblocks][4], zeroed beforehand).
+  // Optional packing of the INPUT state n into normalised BF16 block vectors
+  // [nblocks][2048] (order z*256 + f*64 + y*8 + x; every field of every block divided by
+  // its power-of-two scale) and the per-block, per-field maxima of |f| (float bits,
+  // bmax[nblocks][4]).  Needs nx, ny, nz multiples of 8.
   uint16_t* xpack;
   unsigned int* bmax;
+  int* err;            // sticky device error flag (set on a timed-out wait)
 };
 
 // ------------------------------------------------------------------------------
@@ -71,12 +73,16 @@ struct AdjStep {
   int krec;
   const int* rec_map;
   const float* resid;  // residual row r^{n+1} [nrec][3] (or null)
+  int* err;            // sticky device error flag (set on a timed-out wait)
 };
 
 enum { kAccFirst = 1, kAccLast = 2 };
 
+// TMA-staged steps (aew_stencil.cu); every field pointer must be 16-byte aligned
 cudaError_t launch_fwd_step(const FwdStep& a, bool incremental, cudaStream_t s);
 cudaError_t launch_adj_step(const AdjStep& a, cudaStream_t s);
+// one bounded wait that nothing completes: sets *err after wait_ns (failure-path test)
+cudaError_t launch_wait_probe(int* err, unsigned long long wait_ns, cudaStream_t s);
 int default_kc(int nx, int ny, int nz, bool adjoint);
 
 // ------------------------------------------------------------------------------

@@ -1,36 +1,98 @@
 // Leapfrog stencil kernels for the velocity-strain acoustic system (Sec. 2, Eq. (1),
-// rho = 1) and its discrete adjoint.
+// rho = 1) and its discrete adjoint, with every input plane staged in shared memory by
+// the Tensor Memory Accelerator.
 //
-// Layout: every field is an FP32 [nz][ny][nx] array (x fastest).  Each CTA owns a
-// 128 (x) x TY (y) column of nodes and marches through a chunk of kc z-planes
-// ("2.5-D" blocking).  A thread owns 4 consecutive x nodes, loaded and stored as one
-// 128-bit float4 (every row access of a warp is one contiguous 512-byte segment).
-// Neighbours along x come from the adjacent lane by warp shuffle, neighbours along y
-// from a shared-memory copy of the plane (with one halo row on each side and one halo
-// column for the warp edges), neighbours along z stay in registers from the previous
-// plane.  The next plane's inputs are loaded before the current plane is computed.
+// Tiling.  Each CTA owns a 128 (x) x TY (y) column of nodes and marches through a chunk
+// of kc z-planes.  One thread computes 4 consecutive x nodes (float4 accesses; a warp
+// covers one 512-byte row segment).  For every plane the CTA needs, one elected thread
+// issues one cp.async.bulk.tensor.3d per input field into a ring of S shared-memory
+// stages; completion is counted in bytes on the stage's mbarrier.  The boxes carry the
+// halos the update needs (zero-filled by the TMA outside the grid):
+//   forward   e, m (and dm, e^n for the incremental step)  136 x (TY+2)  x-1..x+128, y-1..y+TY
+//             vx                                           136 x TY      x-1 face
+//             vy                                           128 x (TY+1)  y-1 face
+//             vz                                           128 x TY
+//   adjoint   mu                                           136 x (TY+2)
+//             lam_x / lam_y / lam_z                        as vx / vy / vz
+//             m, e^n, FP32 window accumulator              128 x TY
+// The plane below the chunk (for the z-face under its first plane) and the plane above
+// it (for the z-faces of its last plane) are staged with only the fields they feed.
+// With the next planes in flight, the SM's threads only wait when HBM falls behind.
 //
-// One fused pass per time step: each thread computes the new face velocities of its
-// own nodes, takes the low-side faces from its x/y neighbours' results (recomputing
-// them only at CTA edges, with the identical expression, so results are bitwise
-// independent of the tiling), and then updates the strain of its nodes.  Algorithmic
-// HBM traffic of the forward step: 5 fields read + 4 written = 36 bytes per node.
+// Faces shared with a neighbouring thread are recomputed with the identical expression
+// instead of exchanged (x neighbours still come by warp shuffle), so the results are
+// bitwise independent of the tiling.  Per plane a CTA synchronises once, after which
+// the freed stage is refilled.  Every wait is bounded (200 ms); a timed-out wait sets
+// the sticky error flag, and a kernel that finds the flag set returns at once.
+//
+// Algorithmic HBM traffic per node: forward 36 B (5 fields read, 4 written),
+// incremental forward 44 B, adjoint 48 B + 16 B / W (FP64 flush every W steps).
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
 #include <cstdlib>
+#include <cstring>
 
+#include "aew_gemm.cuh"
 #include "aew_internal.cuh"
+#include "aew_tc.cuh"
 
 namespace aew {
 namespace {
 
-constexpr int TY = 8;            // rows (warps) per CTA
+constexpr int TY = 8;                 // rows (warps) per CTA
 constexpr int NTHR = 32 * TY;
-constexpr int W4 = kTXW / 4;     // float4 per CTA row
+constexpr int kHX = 4;                // x halo width (one float4)
+constexpr int kWE = kTXW + 2 * kHX;   // 136: row width of boxes with an x halo
+constexpr int kW4E = kWE / 4;         // 34 float4 per halo row
+constexpr int kW4 = kTXW / 4;         // 32 float4 per plain row
+constexpr uint64_t kWaitNs = 200000000ull;
+constexpr int kMaxStages = 4;
+// PACK: one plane of the CTA's 16 blocks, 4 fields x 8 rows x 8 BF16 each; then the
+// layer's block maxima per row [TY][16][4] and inverse scales [16][4]
+constexpr int kPackTile = (kTXW / 8) * 512;
+constexpr int kPackExtra = 2 * kPackTile + (TY * 16 * 4 + 16 * 4) * 4;
 
-__device__ __forceinline__ float4 ld4(const float* p, size_t i) {
-  return __ldg(reinterpret_cast<const float4*>(p + i));
+// bytes one box delivers (the mbarrier transaction count) ...
+constexpr int kTxXY = kWE * (TY + 2) * 4;   // x halo both sides, y halo both sides
+constexpr int kTxX = kWE * TY * 4;          // x halo only
+constexpr int kTxYm = kTXW * (TY + 1) * 4;  // one row below
+constexpr int kTxO = kTXW * TY * 4;         // own nodes only
+// ... and the shared-memory room it takes (128-byte aligned destinations)
+constexpr int al128(int b) { return (b + 127) & ~127; }
+constexpr int kBoxXY = al128(kTxXY);
+constexpr int kBoxX = al128(kTxX);
+constexpr int kBoxYm = al128(kTxYm);
+constexpr int kBoxO = al128(kTxO);
+
+// stage layouts (byte offsets)
+struct FwdLayout {
+  static constexpr int E = 0, M = kBoxXY, VX = 2 * kBoxXY, VY = VX + kBoxX, VZ = VY + kBoxYm;
+  static constexpr int DM = VZ + kBoxO, EF = DM + kBoxXY;
+  __host__ __device__ static constexpr int bytes(bool incr) { return incr ? EF + kBoxXY : VZ + kBoxO; }
+};
+struct AdjLayout {
+  static constexpr int MU = 0, LX = kBoxXY, LY = LX + kBoxX, LZ = LY + kBoxYm, M = LZ + kBoxO;
+  static constexpr int EN = M + kBoxO, W = EN + kBoxO, BYTES = W + kBoxO;
+};
+
+struct FwdMaps {
+  CUtensorMap e, m, vx, vy, vz, dm, ef;
+};
+struct AdjMaps {
+  CUtensorMap mu, lx, ly, lz, m, en, w;
+};
+
+__device__ __forceinline__ void tma3(uint32_t dst, const CUtensorMap* map, int x, int y, int z,
+                                     uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(mbar)
+      : "memory");
 }
+
 __device__ __forceinline__ void st4(float* p, size_t i, float4 v) {
   *reinterpret_cast<float4*>(p + i) = v;
 }
@@ -38,30 +100,19 @@ __device__ __forceinline__ float& comp(float4& v, int c) {
   return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
 }
 __device__ __forceinline__ float4 z4() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+__device__ __forceinline__ float4 mul4(float4 a, float4 b) {
+  return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w);
+}
+__device__ __forceinline__ float4 fma4(float4 a, float4 b, float4 c) {
+  return make_float4(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y), fmaf(a.z, b.z, c.z),
+                     fmaf(a.w, b.w, c.w));
+}
+__device__ __forceinline__ float hmax4(float4 a) {
+  return fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w)));
+}
 __device__ __forceinline__ uint32_t pack2bf(float a, float b) {
   __nv_bfloat162 t = __floats2bfloat162_rn(a, b);
   return *reinterpret_cast<uint32_t*>(&t);
-}
-
-// m e (+ dm ef) for one float4 of nodes whose strain e4 is already loaded
-template <bool INCR>
-__device__ __forceinline__ float4 me_of(const FwdStep& a, size_t i, float4 e4) {
-  float4 m4 = ld4(a.m, i);
-  float4 r = make_float4(m4.x * e4.x, m4.y * e4.y, m4.z * e4.z, m4.w * e4.w);
-  if (INCR) {
-    float4 d = ld4(a.dm, i), f = ld4(a.ef, i);
-    r.x = fmaf(d.x, f.x, r.x);
-    r.y = fmaf(d.y, f.y, r.y);
-    r.z = fmaf(d.z, f.z, r.z);
-    r.w = fmaf(d.w, f.w, r.w);
-  }
-  return r;
-}
-template <bool INCR>
-__device__ __forceinline__ float me_one(const FwdStep& a, size_t i) {
-  float r = __ldg(a.m + i) * __ldg(a.e + i);
-  if (INCR) r = fmaf(__ldg(a.dm + i), __ldg(a.ef + i), r);
-  return r;
 }
 // face update v' = v + dth (hi - lo)
 __device__ __forceinline__ float fupd(float dth, float hi, float lo, float v) {
@@ -71,26 +122,96 @@ __device__ __forceinline__ float4 fupd4(float dth, float4 hi, float4 lo, float4 
   return make_float4(fupd(dth, hi.x, lo.x, v.x), fupd(dth, hi.y, lo.y, v.y),
                      fupd(dth, hi.z, lo.z, v.z), fupd(dth, hi.w, lo.w, v.w));
 }
-__device__ __forceinline__ float4 amax4(float4 a) {
-  return make_float4(fabsf(a.x), fabsf(a.y), fabsf(a.z), fabsf(a.w));
+// lam' = (lam + inj) + dth (mu - mu_hi)
+__device__ __forceinline__ float lupd(float dth, float mu_hi, float mu, float l) {
+  return fmaf(dth, mu - mu_hi, l);
 }
-__device__ __forceinline__ float hmax4(float4 a) {
-  return fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w)));
+__device__ __forceinline__ float4 lupd4(float dth, float4 hi, float4 lo, float4 l) {
+  return make_float4(lupd(dth, hi.x, lo.x, l.x), lupd(dth, hi.y, lo.y, l.y),
+                     lupd(dth, hi.z, lo.z, l.z), lupd(dth, hi.w, lo.w, l.w));
 }
+
+__device__ __forceinline__ bool sticky_error(const int* err) {
+  return err && *reinterpret_cast<const volatile int*>(err) != 0;
+}
+
+// Ring bookkeeping shared by both kernels: the CTA stages planes p0 = kbeg - 1 .. pn =
+// kend in order; plane p lives in stage (p - p0) % S and completes phase
+// ((p - p0) / S) & 1 of that stage's barrier.
+struct Ring {
+  uint8_t* base;
+  uint32_t bar0;   // shared address of barrier 0 (8 bytes each)
+  int stage_bytes, S, p0;
+  __device__ int slot(int p) const { return (p - p0) % S; }
+  __device__ uint32_t parity(int p) const { return ((p - p0) / S) & 1; }
+  __device__ uint8_t* at(int p) const { return base + (size_t)slot(p) * stage_bytes; }
+  __device__ uint32_t sat(int p) const { return tc::smem_u32(at(p)); }
+  __device__ uint32_t bar(int p) const { return bar0 + 8u * slot(p); }
+  __device__ bool wait(int p) const { return tc::mbar_wait(bar(p), parity(p), kWaitNs); }
+};
 
 // ---------------------------------------------------------------------------------
 // Forward-type step
 // ---------------------------------------------------------------------------------
-template <bool INCR, bool PACK>
-__global__ void __launch_bounds__(NTHR, 3) fwd_step_kernel(const FwdStep a) {
-  __shared__ float4 sme[2][TY + 2][W4 + 2];
-  __shared__ float4 svy[TY][W4];
+// fields staged per plane: full planes carry everything, the plane below the chunk
+// e, m (dm, e^n) and vz, the plane above it e, m (dm, e^n); planes outside the grid
+// only complete their barrier phase
+template <bool INCR>
+__device__ void fwd_issue(const FwdMaps& mp, const Ring& r, int p, int kbeg, int kend, int nz,
+                          int x0, int y0) {
+  const uint32_t bar = r.bar(p), d = r.sat(p);
+  uint32_t bytes = 0;
+  const bool inside = p >= 0 && p < nz;
+  const bool full = p >= kbeg && p < kend;
+  const bool below = p == kbeg - 1;
+  if (inside) bytes = (INCR ? 4 : 2) * kTxXY + (full ? kTxX + kTxYm + kTxO : 0) +
+                      (below ? kTxO : 0);
+  gemm::mbar_expect_tx(bar, bytes);
+  if (!inside) return;
+  tma3(d + FwdLayout::E, &mp.e, x0 - kHX, y0 - 1, p, bar);
+  tma3(d + FwdLayout::M, &mp.m, x0 - kHX, y0 - 1, p, bar);
+  if (INCR) {
+    tma3(d + FwdLayout::DM, &mp.dm, x0 - kHX, y0 - 1, p, bar);
+    tma3(d + FwdLayout::EF, &mp.ef, x0 - kHX, y0 - 1, p, bar);
+  }
+  if (full) {
+    tma3(d + FwdLayout::VX, &mp.vx, x0 - kHX, y0, p, bar);
+    tma3(d + FwdLayout::VY, &mp.vy, x0, y0 - 1, p, bar);
+  }
+  if (full || below) tma3(d + FwdLayout::VZ, &mp.vz, x0, y0, p, bar);
+}
 
-  const int lane = threadIdx.x, ty = threadIdx.y;
+// m e (+ dm e^n) of float4 number q of a halo box in stage s
+template <bool INCR>
+__device__ __forceinline__ float4 me_at(const uint8_t* s, int q) {
+  float4 r = mul4(reinterpret_cast<const float4*>(s + FwdLayout::M)[q],
+                  reinterpret_cast<const float4*>(s + FwdLayout::E)[q]);
+  if (INCR)
+    r = fma4(reinterpret_cast<const float4*>(s + FwdLayout::DM)[q],
+             reinterpret_cast<const float4*>(s + FwdLayout::EF)[q], r);
+  return r;
+}
+template <bool INCR>
+__device__ __forceinline__ float me_sc(const uint8_t* s, int f) {
+  float r = reinterpret_cast<const float*>(s + FwdLayout::M)[f] *
+            reinterpret_cast<const float*>(s + FwdLayout::E)[f];
+  if (INCR)
+    r = fmaf(reinterpret_cast<const float*>(s + FwdLayout::DM)[f],
+             reinterpret_cast<const float*>(s + FwdLayout::EF)[f], r);
+  return r;
+}
+
+template <bool INCR, bool PACK>
+__global__ void __launch_bounds__(NTHR, (INCR || PACK) ? 2 : 3)
+    fwd_tma_kernel(const __grid_constant__ FwdMaps mp, const FwdStep a, int S) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t bars[kMaxStages];
+  if (sticky_error(a.err)) return;
+
+  const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + lane;
   const int nx = a.nx, ny = a.ny, nz = a.nz;
-  const int x0 = blockIdx.x * kTXW;
-  const int i0 = x0 + 4 * lane;
-  const int y = blockIdx.y * TY + ty;
+  const int x0 = blockIdx.x * kTXW, y0 = blockIdx.y * TY;
+  const int i0 = x0 + 4 * lane, y = y0 + ty;
   const int kbeg = blockIdx.z * a.kc;
   const int kend = min(kbeg + a.kc, nz);
   const bool act = (i0 < nx) && (y < ny);
@@ -98,120 +219,108 @@ __global__ void __launch_bounds__(NTHR, 3) fwd_step_kernel(const FwdStep a) {
   const size_t row = (size_t)y * nx + i0;
   const float dth = a.dth;
 
-  float4 e_c = z4(), me_c = z4(), e_n = z4(), me_n = z4();
-  float4 vx_c = z4(), vy_c = z4(), vz_c = z4(), vzl = z4();
-  if (act) {
-    const size_t i = (size_t)kbeg * P + row;
-    e_c = ld4(a.e, i);
-    me_c = me_of<INCR>(a, i, e_c);
-    if (kbeg + 1 < nz) {
-      e_n = ld4(a.e, i + P);
-      me_n = me_of<INCR>(a, i + P, e_n);
-    }
-    vx_c = ld4(a.vx, i);
-    vy_c = ld4(a.vy, i);
-    vz_c = ld4(a.vz, i);
-    if (kbeg >= 1) {  // z-face below the chunk, recomputed exactly as its owner does
-      const float4 e_m = ld4(a.e, i - P);
-      const float4 me_m = me_of<INCR>(a, i - P, e_m);
-      vzl = fupd4(dth, me_c, me_m, ld4(a.vz, i - P));
-      if (kbeg - 1 == a.sk && y == a.sj) {
-        const int d = a.si - i0;
-        if (d >= 0 && d < 4) comp(vzl, d) += a.dts;
-      }
+  Ring r;
+  r.base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) &
+                                      ~static_cast<uintptr_t>(127));
+  r.bar0 = tc::smem_u32(&bars[0]);
+  r.stage_bytes = FwdLayout::bytes(INCR);
+  r.S = S;
+  r.p0 = kbeg - 1;
+  const int pn = kend;
+  int next = r.p0;   // next plane to issue (thread 0)
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) tc::mbar_init(r.bar0 + 8u * s, 1);
+    tc::mbar_fence_init();
+    tc::fence_proxy_async();
+    for (; next <= pn && next < r.p0 + S; ++next)
+      fwd_issue<INCR>(mp, r, next, kbeg, kend, nz, x0, y0);
+  }
+  __syncthreads();
+
+  // indices (float4 units) of this thread's nodes in the boxes
+  const int qE = (ty + 1) * kW4E + 1 + lane;   // halo boxes, own row
+  const int qX = ty * kW4E + 1 + lane;         // vx box
+  const int qY = (ty + 1) * kW4 + lane;        // vy box, own row
+  const int qO = ty * kW4 + lane;              // own-only boxes
+
+  bool failed = false;
+  float4 vzl = z4();
+  // z-face below the chunk, recomputed exactly as its owner computes it
+  if (!r.wait(r.p0)) failed = true;
+  if (!r.wait(kbeg)) failed = true;
+  failed = __syncthreads_or(failed);   // every thread takes the same path from here
+  if (kbeg >= 1 && !failed) {
+    const uint8_t* sb = r.at(r.p0);
+    const uint8_t* sc = r.at(kbeg);
+    vzl = fupd4(dth, me_at<INCR>(sc, qE), me_at<INCR>(sb, qE),
+                reinterpret_cast<const float4*>(sb + FwdLayout::VZ)[qO]);
+    if (kbeg - 1 == a.sk && y == a.sj) {
+      const int d = a.si - i0;
+      if (d >= 0 && d < 4) comp(vzl, d) += a.dts;
     }
   }
-  // block-vector packing of the input state: raw BF16 values and the running maxima
-  // of |f| over the planes of the current 8-plane block layer
+
   float pm[4] = {0.f, 0.f, 0.f, 0.f};
   const int NBx = nx >> 3, NBy = ny >> 3;
-
-  for (int k = kbeg; k < kend; ++k) {
-    const int b = k & 1;
+  uint8_t* pk = r.base + (size_t)S * r.stage_bytes;   // PACK: two staging tiles
+  int k = kbeg;
+  for (; k < kend && !failed; ++k) {
+    if (!r.wait(k) || !r.wait(k + 1)) failed = true;
+    const uint8_t* sc = r.at(k);
+    const uint8_t* sn = r.at(k + 1);
     const size_t i = (size_t)k * P + row;
-    if (PACK) {
-      const size_t blk = ((size_t)(k >> 3) * NBy + (y >> 3)) * NBx + (i0 >> 3);
+
+    const float4 e_c = reinterpret_cast<const float4*>(sc + FwdLayout::E)[qE];
+    const float4 me_c = me_at<INCR>(sc, qE);
+    const float4 me_yp = me_at<INCR>(sc, qE + kW4E);
+    const float4 me_ym = me_at<INCR>(sc, qE - kW4E);
+    const float4 me_n = me_at<INCR>(sn, qE);
+    const float4 vx_c = reinterpret_cast<const float4*>(sc + FwdLayout::VX)[qX];
+    const float4 vy_c = reinterpret_cast<const float4*>(sc + FwdLayout::VY)[qY];
+    const float4 vy_m = reinterpret_cast<const float4*>(sc + FwdLayout::VY)[qY - kW4];
+    const float4 vz_c = reinterpret_cast<const float4*>(sc + FwdLayout::VZ)[qO];
+
+    if (PACK) {   // BF16 block vectors of the input state and block maxima
       if (act) {
-        uint16_t* dst = a.xpack + blk * 2048 + (k & 7) * 256 + (y & 7) * 8 + (i0 & 7);
+        // this plane's piece of block (lane / 2): [field][y][x] in the staging tile
+        uint8_t* dst = pk + (k & 1) * kPackTile + (lane >> 1) * 512 + ty * 16 + (lane & 1) * 8;
         const float4 fv[4] = {e_c, vx_c, vy_c, vz_c};
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
-          *reinterpret_cast<uint2*>(dst + f * 64) =
+          *reinterpret_cast<uint2*>(dst + f * 128) =
               make_uint2(pack2bf(fv[f].x, fv[f].y), pack2bf(fv[f].z, fv[f].w));
           pm[f] = fmaxf(pm[f], hmax4(fv[f]));
         }
       }
-      if ((k & 7) == 7 || k == kend - 1) {   // block layer complete within this CTA
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-          const float v = fmaxf(pm[f], __shfl_xor_sync(0xffffffffu, pm[f], 1));
-          if (act && (lane & 1) == 0 && v > 0.f) atomicMax(a.bmax + blk * 4 + f, __float_as_uint(v));
-          pm[f] = 0.f;
-        }
-      }
     }
-    // inputs of the next plane, in flight while this plane is computed
-    float4 vx_x = z4(), vy_x = z4(), vz_x = z4(), e_x = z4(), me_x = z4();
-    if (act && k + 1 < kend) {
-      vx_x = ld4(a.vx, i + P);
-      vy_x = ld4(a.vy, i + P);
-      vz_x = ld4(a.vz, i + P);
-      if (k + 2 < nz) {
-        e_x = ld4(a.e, i + 2 * P);
-        me_x = me_of<INCR>(a, i + 2 * P, e_x);
-      }
-    }
-    // stage m e of this plane for the y neighbours and the warp-edge x neighbours
-    sme[b][ty + 1][lane + 1] = me_c;
-    if (ty == 0) {
-      float4 h = z4();
-      if (i0 < nx && y >= 1 && y <= ny) h = me_of<INCR>(a, i - nx, ld4(a.e, i - nx));
-      sme[b][0][lane + 1] = h;
-    }
-    if (ty == TY - 1) {
-      float4 h = z4();
-      if (i0 < nx && y + 1 < ny) h = me_of<INCR>(a, i + nx, ld4(a.e, i + nx));
-      sme[b][TY + 1][lane + 1] = h;
-    }
-    if (lane == 0) sme[b][ty + 1][0].w = (y < ny && x0 >= 1) ? me_one<INCR>(a, i - 1) : 0.f;
-    if (lane == 31) {
-      const size_t ih = (size_t)k * P + (size_t)y * nx + x0 + kTXW;
-      sme[b][ty + 1][W4 + 1].x = (y < ny && x0 + kTXW < nx) ? me_one<INCR>(a, ih) : 0.f;
-    }
-    __syncthreads();
 
     // x-faces of the own nodes; the face x+3 -> x+4 takes m e from the next lane
     float mx1 = __shfl_down_sync(0xffffffffu, me_c.x, 1);
-    if (lane == 31) mx1 = sme[b][ty + 1][W4 + 1].x;
+    if (lane == 31) mx1 = me_sc<INCR>(sc, (ty + 1) * kWE + kHX + kTXW);
     float4 vx1;
     vx1.x = fupd(dth, me_c.y, me_c.x, vx_c.x);
     vx1.y = fupd(dth, me_c.z, me_c.y, vx_c.y);
     vx1.z = fupd(dth, me_c.w, me_c.z, vx_c.z);
     vx1.w = fupd(dth, mx1, me_c.w, vx_c.w);
-    if (i0 + 4 == nx) vx1.w = 0.f;  // unused last face
+    if (i0 + 4 == nx) vx1.w = 0.f;   // unused last face
     float vxl = __shfl_up_sync(0xffffffffu, vx1.w, 1);
     if (lane == 0) {
       vxl = 0.f;
-      if (act && i0 >= 1) vxl = fupd(dth, me_c.x, sme[b][ty + 1][0].w, __ldg(a.vx + i - 1));
+      if (i0 >= 1)
+        vxl = fupd(dth, me_c.x, me_sc<INCR>(sc, (ty + 1) * kWE + kHX - 1),
+                   reinterpret_cast<const float*>(sc + FwdLayout::VX)[ty * kWE + kHX - 1]);
     }
-    // y-faces
-    float4 vy1 = fupd4(dth, sme[b][ty + 2][lane + 1], me_c, vy_c);
+    // y-faces: own, and the one below recomputed as the row below computes it
+    float4 vy1 = fupd4(dth, me_yp, me_c, vy_c);
     if (y == ny - 1) vy1 = z4();
-    svy[ty][lane] = vy1;
+    float4 vyl = z4();
+    if (y >= 1) vyl = fupd4(dth, me_c, me_ym, vy_m);
     // z-faces
     float4 vz1 = fupd4(dth, me_n, me_c, vz_c);
     if (k == nz - 1) vz1 = z4();
     if (k == a.sk && y == a.sj) {
       const int d = a.si - i0;
       if (d >= 0 && d < 4) comp(vz1, d) += a.dts;
-    }
-    __syncthreads();
-    float4 vyl;
-    if (ty > 0) {
-      vyl = svy[ty - 1][lane];
-    } else {
-      vyl = z4();
-      if (act && y >= 1) vyl = fupd4(dth, me_c, sme[b][0][lane + 1], ld4(a.vy, i - nx));
     }
     // strain update on interior nodes
     float4 e1;
@@ -225,14 +334,14 @@ __global__ void __launch_bounds__(NTHR, 3) fwd_step_kernel(const FwdStep a) {
       if (i0 == 0) e1.x = 0.f;
       if (i0 + 4 == nx) e1.w = 0.f;
     }
-    if (act) {
+    if (act && !failed) {
       st4(a.e1, i, e1);
       st4(a.vx1, i, vx1);
       st4(a.vy1, i, vy1);
       st4(a.vz1, i, vz1);
       if (k == a.krec && a.d_out) {
-        const int4 r = __ldg(reinterpret_cast<const int4*>(a.rec_map + (size_t)y * nx + i0));
-        const int rr[4] = {r.x, r.y, r.z, r.w};
+        const int4 rm = __ldg(reinterpret_cast<const int4*>(a.rec_map + (size_t)y * nx + i0));
+        const int rr[4] = {rm.x, rm.y, rm.z, rm.w};
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           if (rr[c] >= 0) {
@@ -244,30 +353,122 @@ __global__ void __launch_bounds__(NTHR, 3) fwd_step_kernel(const FwdStep a) {
       }
     }
     vzl = vz1;
-    e_c = e_n;
-    me_c = me_n;
-    e_n = e_x;
-    me_n = me_x;
-    vx_c = vx_x;
-    vy_c = vy_x;
-    vz_c = vz_x;
+    // every thread is done with plane k: refill its stage
+    failed = __syncthreads_or(failed);
+    if (tid == 0 && !failed)
+      for (; next <= pn && next <= k + S; ++next)
+        fwd_issue<INCR>(mp, r, next, kbeg, kend, nz, x0, y0);
+    if (PACK && !failed) {
+      // plane k of the CTA's 16 blocks: one coalesced 512-byte row per block (the tile
+      // is rewritten two planes later, after the next barrier)
+      const uint8_t* src = pk + (k & 1) * kPackTile;
+      for (int j = ty; j < kTXW / 8; j += TY) {
+        const int bx = (x0 >> 3) + j;
+        if (bx < NBx) {
+          const size_t blk = ((size_t)(k >> 3) * NBy + (y0 >> 3)) * NBx + bx;
+          uint8_t* dst = reinterpret_cast<uint8_t*>(a.xpack) + blk * 4096 + (k & 7) * 512;
+          reinterpret_cast<uint4*>(dst)[lane] = reinterpret_cast<const uint4*>(src + j * 512)[lane];
+        }
+      }
+      if ((k & 7) == 7) {
+        // Layer complete: the CTA holds its 16 blocks whole (8 rows, 8 planes).  Their
+        // maxima per field: lane pairs by shuffle, the 8 rows through shared memory.
+        float* red = reinterpret_cast<float*>(pk + 2 * kPackTile);   // [TY][16][4]
+        float* isc = red + TY * 16 * 4;                              // [16][4]
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          const float v = fmaxf(pm[f], __shfl_xor_sync(0xffffffffu, pm[f], 1));
+          if ((lane & 1) == 0) red[(ty * 16 + (lane >> 1)) * 4 + f] = v;
+          pm[f] = 0.f;
+        }
+        __syncthreads();
+        const size_t blk0 = ((size_t)(k >> 3) * NBy + (y0 >> 3)) * NBx + (x0 >> 3);
+        if (tid < 64) {
+          const int j = tid >> 2, f = tid & 3;
+          float mx = 0.f;
+#pragma unroll
+          for (int w = 0; w < TY; ++w) mx = fmaxf(mx, red[(w * 16 + j) * 4 + f]);
+          if ((x0 >> 3) + j < NBx) a.bmax[(blk0 + j) * 4 + f] = __float_as_uint(mx);
+          isc[j * 4 + f] = gemm::block_inv_scale(mx);
+        }
+        __syncthreads();   // the table, and every thread's raw rows of the layer, are visible
+        // normalise the layer's block vectors in place, 16 bytes per thread and block
+        // (exact: every scale is a power of two); the rows are still in L2.  Eight
+        // blocks' loads are in flight at a time.
+        const int f = (tid >> 3) & 3;   // element tid * 8 lies in field (k >> 6) & 3
+        const int nbl = min(kTXW / 8, NBx - (x0 >> 3));
+        uint4* p0 = reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(a.xpack) + blk0 * 4096) + tid;
+#pragma unroll
+        for (int j0 = 0; j0 < kTXW / 8; j0 += 8) {
+          uint4 v[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (j0 + j < nbl) v[j] = __ldcg(p0 + (size_t)(j0 + j) * 256);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            if (j0 + j < nbl) {
+              const float sc = isc[(j0 + j) * 4 + f];
+              uint32_t w[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
+#pragma unroll
+              for (int q = 0; q < 4; ++q)
+                w[q] = pack2bf(__uint_as_float(w[q] << 16) * sc,
+                               __uint_as_float(w[q] & 0xffff0000u) * sc);
+              p0[(size_t)(j0 + j) * 256] = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+          }
+        }
+      }
+    }
   }
-
+  if (failed) {
+    if (tid == 0) {
+      atomicExch(a.err, 1);
+      // let the copies still in flight land before the shared memory is released
+      for (int p = max(r.p0, next - S); p < next; ++p) r.wait(p);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------------
 // Adjoint step
 // ---------------------------------------------------------------------------------
+struct AdjFlags {
+  bool en, w;   // e^n present; FP32 window accumulator read
+};
+
+__device__ void adj_issue(const AdjMaps& mp, const Ring& r, int p, int kbeg, int kend, int nz,
+                          int x0, int y0, AdjFlags f) {
+  const uint32_t bar = r.bar(p), d = r.sat(p);
+  uint32_t bytes = 0;
+  const bool inside = p >= 0 && p < nz;
+  const bool full = p >= kbeg && p < kend;
+  const bool below = p == kbeg - 1;
+  if (inside)
+    bytes = kTxXY + (full ? kTxX + kTxYm + kTxO * (2 + (f.en ? 1 : 0) + (f.w ? 1 : 0)) : 0) +
+            (below ? kTxO : 0);
+  gemm::mbar_expect_tx(bar, bytes);
+  if (!inside) return;
+  tma3(d + AdjLayout::MU, &mp.mu, x0 - kHX, y0 - 1, p, bar);
+  if (full) {
+    tma3(d + AdjLayout::LX, &mp.lx, x0 - kHX, y0, p, bar);
+    tma3(d + AdjLayout::LY, &mp.ly, x0, y0 - 1, p, bar);
+    tma3(d + AdjLayout::M, &mp.m, x0, y0, p, bar);
+    if (f.en) tma3(d + AdjLayout::EN, &mp.en, x0, y0, p, bar);
+    if (f.w) tma3(d + AdjLayout::W, &mp.w, x0, y0, p, bar);
+  }
+  if (full || below) tma3(d + AdjLayout::LZ, &mp.lz, x0, y0, p, bar);
+}
+
 __device__ __forceinline__ float inj_one(const AdjStep& a, int comp3, int x, int y, int k) {
   if (k != a.krec || a.resid == nullptr) return 0.f;
-  const int r = __ldg(a.rec_map + (size_t)y * a.nx + x);
-  return r >= 0 ? __ldg(a.resid + 3 * r + comp3) : 0.f;
+  const int q = __ldg(a.rec_map + (size_t)y * a.nx + x);
+  return q >= 0 ? __ldg(a.resid + 3 * q + comp3) : 0.f;
 }
 // add B^T r to the three face fields of a float4 of nodes on the receiver plane
 __device__ __forceinline__ void inj4(const AdjStep& a, int y, int i0, float4& lx, float4& ly,
                                      float4& lz) {
-  const int4 r = __ldg(reinterpret_cast<const int4*>(a.rec_map + (size_t)y * a.nx + i0));
-  const int rr[4] = {r.x, r.y, r.z, r.w};
+  const int4 q = __ldg(reinterpret_cast<const int4*>(a.rec_map + (size_t)y * a.nx + i0));
+  const int rr[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     if (rr[c] >= 0) {
@@ -277,24 +478,17 @@ __device__ __forceinline__ void inj4(const AdjStep& a, int y, int i0, float4& lx
     }
   }
 }
-// lam' = (lam + inj) + dth (mu - mu_hi)
-__device__ __forceinline__ float lupd(float dth, float mu_hi, float mu, float l) {
-  return fmaf(dth, mu - mu_hi, l);
-}
-__device__ __forceinline__ float4 lupd4(float dth, float4 hi, float4 lo, float4 l) {
-  return make_float4(lupd(dth, hi.x, lo.x, l.x), lupd(dth, hi.y, lo.y, l.y),
-                     lupd(dth, hi.z, lo.z, l.z), lupd(dth, hi.w, lo.w, l.w));
-}
 
-__global__ void __launch_bounds__(NTHR, 3) adj_step_kernel(const AdjStep a) {
-  __shared__ float4 smu[2][TY + 2][W4 + 2];
-  __shared__ float4 sly[TY][W4];
+__global__ void __launch_bounds__(NTHR, 2)
+    adj_tma_kernel(const __grid_constant__ AdjMaps mp, const AdjStep a, int S) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t bars[kMaxStages];
+  if (sticky_error(a.err)) return;
 
-  const int lane = threadIdx.x, ty = threadIdx.y;
+  const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + lane;
   const int nx = a.nx, ny = a.ny, nz = a.nz;
-  const int x0 = blockIdx.x * kTXW;
-  const int i0 = x0 + 4 * lane;
-  const int y = blockIdx.y * TY + ty;
+  const int x0 = blockIdx.x * kTXW, y0 = blockIdx.y * TY;
+  const int i0 = x0 + 4 * lane, y = y0 + ty;
   const int kbeg = blockIdx.z * a.kc;
   const int kend = min(kbeg + a.kc, nz);
   const bool act = (i0 < nx) && (y < ny);
@@ -302,61 +496,80 @@ __global__ void __launch_bounds__(NTHR, 3) adj_step_kernel(const AdjStep a) {
   const size_t row = (size_t)y * nx + i0;
   const float dth = a.dth;
   const bool has_r = a.resid != nullptr && a.krec >= 0;
-
   const int mode = a.acc_mode;
-  const bool need_acc32 = !(mode & kAccFirst);
-  float4 mu_c = z4(), mu_n = z4(), lx_c = z4(), ly_c = z4(), lz_c = z4(), lzl = z4();
-  float4 m_c = z4(), en_c = z4(), w_c = z4();
-  if (act) {
-    const size_t i = (size_t)kbeg * P + row;
-    m_c = ld4(a.m, i);
-    if (a.en) en_c = ld4(a.en, i);
-    if (need_acc32) w_c = ld4(a.acc32, i);
-    mu_c = ld4(a.mu, i);
-    if (kbeg + 1 < nz) mu_n = ld4(a.mu, i + P);
-    lx_c = ld4(a.lx, i);
-    ly_c = ld4(a.ly, i);
-    lz_c = ld4(a.lz, i);
-    if (kbeg >= 1) {
-      float4 lzm = ld4(a.lz, i - P);
-      if (has_r && kbeg - 1 == a.krec) {
-        float4 dx = z4(), dy = z4();
-        inj4(a, y, i0, dx, dy, lzm);
-      }
-      lzl = lupd4(dth, mu_c, ld4(a.mu, i - P), lzm);
+  const AdjFlags fl{a.en != nullptr, !(mode & kAccFirst)};
+
+  Ring r;
+  r.base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) &
+                                      ~static_cast<uintptr_t>(127));
+  r.bar0 = tc::smem_u32(&bars[0]);
+  r.stage_bytes = AdjLayout::BYTES;
+  r.S = S;
+  r.p0 = kbeg - 1;
+  const int pn = kend;
+  int next = r.p0;
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) tc::mbar_init(r.bar0 + 8u * s, 1);
+    tc::mbar_fence_init();
+    tc::fence_proxy_async();
+    for (; next <= pn && next < r.p0 + S; ++next) adj_issue(mp, r, next, kbeg, kend, nz, x0, y0, fl);
+  }
+  __syncthreads();
+
+  const int qE = (ty + 1) * kW4E + 1 + lane;
+  const int qX = ty * kW4E + 1 + lane;
+  const int qY = (ty + 1) * kW4 + lane;
+  const int qO = ty * kW4 + lane;
+
+  bool failed = false;
+  float4 lzl = z4();
+  if (!r.wait(r.p0)) failed = true;
+  if (!r.wait(kbeg)) failed = true;
+  failed = __syncthreads_or(failed);
+  if (kbeg >= 1 && !failed) {
+    const uint8_t* sb = r.at(r.p0);
+    const uint8_t* sc = r.at(kbeg);
+    float4 lzm = reinterpret_cast<const float4*>(sb + AdjLayout::LZ)[qO];
+    if (has_r && kbeg - 1 == a.krec && act) {
+      float4 dx = z4(), dy = z4();
+      inj4(a, y, i0, dx, dy, lzm);
     }
+    lzl = lupd4(dth, reinterpret_cast<const float4*>(sc + AdjLayout::MU)[qE],
+                reinterpret_cast<const float4*>(sb + AdjLayout::MU)[qE], lzm);
   }
 
-  for (int k = kbeg; k < kend; ++k) {
-    const int b = k & 1;
+  int k = kbeg;
+  for (; k < kend && !failed; ++k) {
     const size_t i = (size_t)k * P + row;
-    float4 lx_x = z4(), ly_x = z4(), lz_x = z4(), mu_x = z4();
-    float4 m_x = z4(), en_x = z4(), w_x = z4();
-    if (act && k + 1 < kend) {
-      lx_x = ld4(a.lx, i + P);
-      ly_x = ld4(a.ly, i + P);
-      lz_x = ld4(a.lz, i + P);
-      m_x = ld4(a.m, i + P);
-      if (a.en) en_x = ld4(a.en, i + P);
-      if (need_acc32) w_x = ld4(a.acc32, i + P);
-      if (k + 2 < nz) mu_x = ld4(a.mu, i + 2 * P);
+    // the FP64 accumulator of a window's last step: in flight while the planes land
+    double2 a64lo = make_double2(0.0, 0.0), a64hi = a64lo;
+    if ((mode & kAccLast) && act) {
+      const double2* p64 = reinterpret_cast<const double2*>(a.acc64 + i);
+      a64lo = p64[0];
+      a64hi = p64[1];
     }
-    const float4 m4 = m_c, en4 = en_c;
+    if (!r.wait(k) || !r.wait(k + 1)) failed = true;
+    const uint8_t* sc = r.at(k);
+    const uint8_t* sn = r.at(k + 1);
+    const float4* MU = reinterpret_cast<const float4*>(sc + AdjLayout::MU);
+    const float4 mu_c = MU[qE];
+    const float4 mu_yp = MU[qE + kW4E];
+    const float4 mu_ym = MU[qE - kW4E];
+    const float4 mu_n = reinterpret_cast<const float4*>(sn + AdjLayout::MU)[qE];
+    float4 lx_c = reinterpret_cast<const float4*>(sc + AdjLayout::LX)[qX];
+    float4 ly_c = reinterpret_cast<const float4*>(sc + AdjLayout::LY)[qY];
+    float4 ly_m = reinterpret_cast<const float4*>(sc + AdjLayout::LY)[qY - kW4];
+    float4 lz_c = reinterpret_cast<const float4*>(sc + AdjLayout::LZ)[qO];
+    const float4 m4 = reinterpret_cast<const float4*>(sc + AdjLayout::M)[qO];
+    const float4 en4 = fl.en ? reinterpret_cast<const float4*>(sc + AdjLayout::EN)[qO] : z4();
+    const float4 w_c = fl.w ? reinterpret_cast<const float4*>(sc + AdjLayout::W)[qO] : z4();
+
     const bool rplane = has_r && k == a.krec;
     if (rplane && act) inj4(a, y, i0, lx_c, ly_c, lz_c);
 
-    smu[b][ty + 1][lane + 1] = mu_c;
-    if (ty == 0) smu[b][0][lane + 1] = (i0 < nx && y >= 1 && y <= ny) ? ld4(a.mu, i - nx) : z4();
-    if (ty == TY - 1) smu[b][TY + 1][lane + 1] = (i0 < nx && y + 1 < ny) ? ld4(a.mu, i + nx) : z4();
-    if (lane == 0) smu[b][ty + 1][0].w = (y < ny && x0 >= 1) ? __ldg(a.mu + i - 1) : 0.f;
-    if (lane == 31) {
-      const size_t ih = (size_t)k * P + (size_t)y * nx + x0 + kTXW;
-      smu[b][ty + 1][W4 + 1].x = (y < ny && x0 + kTXW < nx) ? __ldg(a.mu + ih) : 0.f;
-    }
-    __syncthreads();
-
     float mx1 = __shfl_down_sync(0xffffffffu, mu_c.x, 1);
-    if (lane == 31) mx1 = smu[b][ty + 1][W4 + 1].x;
+    if (lane == 31)
+      mx1 = reinterpret_cast<const float*>(sc + AdjLayout::MU)[(ty + 1) * kWE + kHX + kTXW];
     float4 lx1;
     lx1.x = lupd(dth, mu_c.y, mu_c.x, lx_c.x);
     lx1.y = lupd(dth, mu_c.z, mu_c.y, lx_c.y);
@@ -367,33 +580,26 @@ __global__ void __launch_bounds__(NTHR, 3) adj_step_kernel(const AdjStep a) {
     if (lane == 0) {
       lxl = 0.f;
       if (act && i0 >= 1) {
-        float l = __ldg(a.lx + i - 1);
+        float l = reinterpret_cast<const float*>(sc + AdjLayout::LX)[ty * kWE + kHX - 1];
         if (rplane) l += inj_one(a, 0, i0 - 1, y, k);
-        lxl = lupd(dth, mu_c.x, smu[b][ty + 1][0].w, l);
+        lxl = lupd(dth, mu_c.x,
+                   reinterpret_cast<const float*>(sc + AdjLayout::MU)[(ty + 1) * kWE + kHX - 1], l);
       }
     }
-    float4 ly1 = lupd4(dth, smu[b][ty + 2][lane + 1], mu_c, ly_c);
+    float4 ly1 = lupd4(dth, mu_yp, mu_c, ly_c);
     if (y == ny - 1) ly1 = z4();
-    sly[ty][lane] = ly1;
+    float4 lyl = z4();
+    if (act && y >= 1) {
+      if (rplane) {
+        ly_m.x += inj_one(a, 1, i0 + 0, y - 1, k);
+        ly_m.y += inj_one(a, 1, i0 + 1, y - 1, k);
+        ly_m.z += inj_one(a, 1, i0 + 2, y - 1, k);
+        ly_m.w += inj_one(a, 1, i0 + 3, y - 1, k);
+      }
+      lyl = lupd4(dth, mu_c, mu_ym, ly_m);
+    }
     float4 lz1 = lupd4(dth, mu_n, mu_c, lz_c);
     if (k == nz - 1) lz1 = z4();
-    __syncthreads();
-    float4 lyl;
-    if (ty > 0) {
-      lyl = sly[ty - 1][lane];
-    } else {
-      lyl = z4();
-      if (act && y >= 1) {
-        float4 l = ld4(a.ly, i - nx);
-        if (rplane) {
-          l.x += inj_one(a, 1, i0 + 0, y - 1, k);
-          l.y += inj_one(a, 1, i0 + 1, y - 1, k);
-          l.z += inj_one(a, 1, i0 + 2, y - 1, k);
-          l.w += inj_one(a, 1, i0 + 3, y - 1, k);
-        }
-        lyl = lupd4(dth, mu_c, smu[b][0][lane + 1], l);
-      }
-    }
     // dt q = dt G^T lam' = -dt/h (div lam') on interior nodes
     float4 dq;
     dq.x = -dth * (((lx1.x - lxl) + (ly1.x - lyl.x)) + (lz1.x - lzl.x));
@@ -406,53 +612,111 @@ __global__ void __launch_bounds__(NTHR, 3) adj_step_kernel(const AdjStep a) {
       if (i0 == 0) dq.x = 0.f;
       if (i0 + 4 == nx) dq.w = 0.f;
     }
-    float4 mu1 = make_float4(fmaf(m4.x, dq.x, mu_c.x), fmaf(m4.y, dq.y, mu_c.y),
-                             fmaf(m4.z, dq.z, mu_c.z), fmaf(m4.w, dq.w, mu_c.w));
-    if (act) {
+    const float4 mu1 = fma4(m4, dq, mu_c);
+    if (act && !failed) {
       st4(a.mu1, i, mu1);
       st4(a.lx1, i, lx1);
       st4(a.ly1, i, ly1);
       st4(a.lz1, i, lz1);
       // dJ/dm += dt e^n q
-      const float4 g = make_float4(en4.x * dq.x, en4.y * dq.y, en4.z * dq.z, en4.w * dq.w);
+      const float4 g = mul4(en4, dq);
       if (mode & kAccLast) {
         float4 s = g;
-        if (need_acc32) {
-          const float4 w = w_c;
-          s = make_float4(w.x + g.x, w.y + g.y, w.z + g.z, w.w + g.w);
-        }
-        double2* p = reinterpret_cast<double2*>(a.acc64 + i);
-        double2 lo = p[0], hi = p[1];
-        lo.x += (double)s.x;
-        lo.y += (double)s.y;
-        hi.x += (double)s.z;
-        hi.y += (double)s.w;
-        p[0] = lo;
-        p[1] = hi;
+        if (fl.w) s = make_float4(w_c.x + g.x, w_c.y + g.y, w_c.z + g.z, w_c.w + g.w);
+        a64lo.x += (double)s.x;
+        a64lo.y += (double)s.y;
+        a64hi.x += (double)s.z;
+        a64hi.y += (double)s.w;
+        double2* p64 = reinterpret_cast<double2*>(a.acc64 + i);
+        p64[0] = a64lo;
+        p64[1] = a64hi;
       } else if (mode & kAccFirst) {
         st4(a.acc32, i, g);
       } else {
-        const float4 w = w_c;
-        st4(a.acc32, i, make_float4(w.x + g.x, w.y + g.y, w.z + g.z, w.w + g.w));
+        st4(a.acc32, i, make_float4(w_c.x + g.x, w_c.y + g.y, w_c.z + g.z, w_c.w + g.w));
       }
     }
     lzl = lz1;
-    m_c = m_x;
-    en_c = en_x;
-    w_c = w_x;
-    mu_c = mu_n;
-    mu_n = mu_x;
-    lx_c = lx_x;
-    ly_c = ly_x;
-    lz_c = lz_x;
+    failed = __syncthreads_or(failed);
+    if (tid == 0 && !failed)
+      for (; next <= pn && next <= k + S; ++next) adj_issue(mp, r, next, kbeg, kend, nz, x0, y0, fl);
   }
+  if (failed) {
+    if (tid == 0) {
+      atomicExch(a.err, 1);
+      for (int p = max(r.p0, next - S); p < next; ++p) r.wait(p);
+    }
+  }
+}
+
+// Failure-path probe: one thread waits, with the given bound, on an mbarrier that
+// nothing arrives at, and records the time-out exactly as the stencil and codec kernels
+// record theirs.
+__global__ void wait_probe_kernel(int* err, uint64_t ns) {
+  __shared__ __align__(8) uint64_t bar;
+  const uint32_t b = tc::smem_u32(&bar);
+  tc::mbar_init(b, 1);
+  tc::mbar_fence_init();
+  if (!tc::mbar_wait(b, 0, ns)) atomicExch(err, 1);
+  // complete the phase so the barrier is not left pending when the CTA exits
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b) : "memory");
+}
+
+// ---------------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------------
+// 3-D tensor map of an FP32 field [nz][ny][nx] with a (bx, by, 1) box; zero fill
+// outside the grid
+bool field_map(CUtensorMap* map, const float* base, int nx, int ny, int nz, int bx, int by) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = gemm::tensor_map_encoder();
+  if (!enc || !base || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4};
+  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box,
+             es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// At least 3 stages: the first plane of a chunk needs the planes below and above it
+// resident at once.
+int stages_for(bool adjoint) {
+  int s = 3;
+  if (const char* env = getenv(adjoint ? "AEW_STENCIL_STAGES_ADJ" : "AEW_STENCIL_STAGES_FWD")) {
+    const int v = atoi(env);   // tuning override
+    if (v >= 3 && v <= kMaxStages) s = v;
+  }
+  return s;
+}
+
+dim3 grid_of(int nx, int ny, int nz, int kc) {
+  return dim3((nx + kTXW - 1) / kTXW, (ny + TY - 1) / TY, (nz + kc - 1) / kc);
+}
+
+template <bool INCR, bool PACK>
+cudaError_t launch_fwd(const FwdMaps& mp, const FwdStep& a, cudaStream_t s) {
+  const int S = stages_for(false);
+  const int extra = (PACK ? kPackExtra : 0) + 128;
+  const size_t smem = (size_t)S * FwdLayout::bytes(INCR) + extra;
+  static bool attr = false;   // per instantiation
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(fwd_tma_kernel<INCR, PACK>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(kMaxStages * FwdLayout::bytes(INCR) + extra));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  fwd_tma_kernel<INCR, PACK><<<grid_of(a.nx, a.ny, a.nz, a.kc), dim3(32, TY), smem, s>>>(mp, a, S);
+  return cudaGetLastError();
 }
 
 }  // namespace
 
 int default_kc(int nx, int ny, int nz, bool adjoint) {
   // z planes per CTA: short chunks give many CTAs (several waves, good balance) at the
-  // cost of re-reading one plane per chunk; 8 measured best at 256^3 on GB300.
+  // cost of staging one plane below and one above each chunk; 8 measured best at 256^3
+  // on GB300 (the packing forward step rounds it up to whole 8-plane block layers).
   (void)nx;
   (void)ny;
   int kc = nz < 8 ? nz : 8;
@@ -463,25 +727,60 @@ int default_kc(int nx, int ny, int nz, bool adjoint) {
   return kc < 1 ? 1 : kc;
 }
 
-static dim3 grid_of(int nx, int ny, int nz, int kc) {
-  return dim3((nx + kTXW - 1) / kTXW, (ny + TY - 1) / TY, (nz + kc - 1) / kc);
+cudaError_t launch_fwd_step(const FwdStep& a, bool incremental, cudaStream_t s) {
+  if (!a.err) return cudaErrorInvalidValue;
+  FwdMaps mp;
+  memset(&mp, 0, sizeof(mp));
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  bool ok = field_map(&mp.e, a.e, nx, ny, nz, kWE, TY + 2) &&
+            field_map(&mp.m, a.m, nx, ny, nz, kWE, TY + 2) &&
+            field_map(&mp.vx, a.vx, nx, ny, nz, kWE, TY) &&
+            field_map(&mp.vy, a.vy, nx, ny, nz, kTXW, TY + 1) &&
+            field_map(&mp.vz, a.vz, nx, ny, nz, kTXW, TY);
+  if (ok && incremental)
+    ok = field_map(&mp.dm, a.dm, nx, ny, nz, kWE, TY + 2) &&
+         field_map(&mp.ef, a.ef, nx, ny, nz, kWE, TY + 2);
+  if (!ok) return cudaErrorInvalidValue;
+  if (incremental) return launch_fwd<true, false>(mp, a, s);
+  if (a.xpack) {
+    // packing normalises whole 8-plane block layers inside one CTA
+    if (nx % 8 || ny % 8 || nz % 8) return cudaErrorInvalidValue;
+    FwdStep b = a;
+    b.kc = (a.kc + 7) / 8 * 8;
+    return launch_fwd<false, true>(mp, b, s);
+  }
+  return launch_fwd<false, false>(mp, a, s);
 }
 
-cudaError_t launch_fwd_step(const FwdStep& a, bool incremental, cudaStream_t s) {
-  const dim3 grid = grid_of(a.nx, a.ny, a.nz, a.kc), block(32, TY);
-  if (incremental) {
-    fwd_step_kernel<true, false><<<grid, block, 0, s>>>(a);
-  } else if (a.xpack) {
-    fwd_step_kernel<false, true><<<grid, block, 0, s>>>(a);
-  } else {
-    fwd_step_kernel<false, false><<<grid, block, 0, s>>>(a);
-  }
+cudaError_t launch_wait_probe(int* err, unsigned long long wait_ns, cudaStream_t s) {
+  if (!err) return cudaErrorInvalidValue;
+  wait_probe_kernel<<<1, 1, 0, s>>>(err, wait_ns);
   return cudaGetLastError();
 }
 
 cudaError_t launch_adj_step(const AdjStep& a, cudaStream_t s) {
-  const dim3 grid = grid_of(a.nx, a.ny, a.nz, a.kc), block(32, TY);
-  adj_step_kernel<<<grid, block, 0, s>>>(a);
+  if (!a.err) return cudaErrorInvalidValue;
+  AdjMaps mp;
+  memset(&mp, 0, sizeof(mp));
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  bool ok = field_map(&mp.mu, a.mu, nx, ny, nz, kWE, TY + 2) &&
+            field_map(&mp.lx, a.lx, nx, ny, nz, kWE, TY) &&
+            field_map(&mp.ly, a.ly, nx, ny, nz, kTXW, TY + 1) &&
+            field_map(&mp.lz, a.lz, nx, ny, nz, kTXW, TY) &&
+            field_map(&mp.m, a.m, nx, ny, nz, kTXW, TY);
+  if (ok && a.en) ok = field_map(&mp.en, a.en, nx, ny, nz, kTXW, TY);
+  if (ok && !(a.acc_mode & kAccFirst)) ok = field_map(&mp.w, a.acc32, nx, ny, nz, kTXW, TY);
+  if (!ok) return cudaErrorInvalidValue;
+  const int S = stages_for(true);
+  const size_t smem = (size_t)S * AdjLayout::BYTES + 128;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(adj_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(kMaxStages * AdjLayout::BYTES + 128));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  adj_tma_kernel<<<grid_of(nx, ny, nz, a.kc), dim3(32, TY), smem, s>>>(mp, a, S);
   return cudaGetLastError();
 }
 

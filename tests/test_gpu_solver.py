@@ -215,8 +215,12 @@ def test_config2_full_vs_revolve_and_fd():
         fd = (8 * (J(cc + eps * dc) - J(cc - eps * dc)) - (J(cc + 2 * eps * dc) - J(cc - 2 * eps * dc))) / (12 * eps)
         rows.append((fd, aewave.dot(gf, dc)))
     print("config2 FD (fd, adjoint):", rows)
+    # The FD error is absolute (FP32 rounding of the misfit), about the same in every
+    # direction; a direction nearly orthogonal to the gradient (derivative ~1e-3 of the
+    # others) is held to a floor of 1e-4 of the largest directional derivative.
+    floor = 1e-4 * max(abs(ad) for _, ad in rows)
     for k, (fd, ad) in enumerate(rows):
-        assert abs(fd - ad) <= 1e-2 * abs(ad), (k, fd, ad)
+        assert abs(fd - ad) <= 1e-2 * abs(ad) + floor, (k, fd, ad)
 
 
 def test_error_paths():
@@ -241,3 +245,22 @@ def test_error_paths():
     # the handle stays usable after errors
     d = s.forward(cuda(c))
     assert torch.isfinite(d).all()
+
+
+def test_timed_out_wait_is_reported_and_the_handle_recovers():
+    """A bounded device wait that runs out (nothing completes its barrier) sets the sticky
+    flag: later kernels of the handle return at once, the next check reports
+    AEW_E_TIMEOUT, and after that the handle computes normally again."""
+    from paper_2304_04781_gb300 import aewave
+    prob, c, _ = setup((16, 16, 16), 20, 16)
+    s = solver(prob)
+    d_ok = s.forward(cuda(c))
+    s.test_wait_timeout(1_000_000)                 # 1 ms
+    d_skip = s.forward(cuda(c))                    # stencil kernels see the flag
+    assert not torch.equal(d_skip, d_ok)           # rows 1..nt were never written
+    with pytest.raises(aewave.AewError) as ei:
+        s.sync_check()
+    assert ei.value.code == -11
+    s.sync_check()                                 # cleared
+    d = s.forward(cuda(c))
+    assert torch.equal(d, d_ok)

@@ -180,3 +180,21 @@ def test_emulated_codec_close_to_exact_and_rounded():
     assert np.linalg.norm(out_e - out_x) / np.linalg.norm(out_x) < 2e-2
     cols = C.field_columns(0)
     np.testing.assert_allclose(C.decode(Wt, z_emul, cols=cols), out_x[:, cols], rtol=1e-12, atol=1e-12)
+
+
+def test_training_schedule_follows_table_2():
+    """The training driver's defaults and the oracle's schedule are the values Table 2
+    prints (fixture tests/golden/table2_training.json)."""
+    import inspect
+    import json
+    import os
+    from paper_2304_04781_gb300 import train
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "table2_training.json")))
+    sig = inspect.signature(train.train).parameters
+    assert sig["epochs"].default == g["epochs"]
+    assert sig["batch"].default == g["batch_size"]
+    assert sig["lr0"].default == g["initial_learning_rate"]
+    assert sig["halve_every"].default == g["learning_rate_decay_every_epochs"]
+    lr0, k = g["initial_learning_rate"], g["learning_rate_decay_every_epochs"]
+    for ep in range(g["epochs"]):
+        assert C.lr_schedule(ep, lr0) == pytest.approx(lr0 * g["learning_rate_decay_factor"] ** (ep // k), rel=0, abs=0)
