@@ -62,6 +62,7 @@ struct aew_handle {
   // AE mode: side stream running the codec GEMMs concurrently with the stencil steps,
   // double-buffered packed inputs and decoded strains, and the events ordering them
   cudaStream_t side = nullptr;
+  int overlap_ctas = 0;   // CTA cap of the codec GEMMs that run beside a stencil step
   cudaEvent_t ev_a[2] = {}, ev_b[2] = {}, ev_sync = nullptr, ev_sync2 = nullptr;
   uint16_t* xpk[2] = {};
   float* edb[2] = {};
@@ -287,7 +288,8 @@ float* drow(aew_handle* h, float* d, int n) {
 int encode_packed(aew_handle* h, int n, cudaStream_t s) {
   const size_t nb = nblocks_of(h);
   cudaError_t e = aew::codec_encode_vectors(h->codec, h->xpk[n & 1], (long long)nb,
-                                            h->lat + (size_t)n * nb * h->cfg.n_lat, h->ovf, s);
+                                            h->lat + (size_t)n * nb * h->cfg.n_lat, h->ovf, s,
+                                            h->overlap_ctas);
   if (e != cudaSuccess) return cuda_fail(h, e, "codec_encode_vectors");
   h->stats.kernel_launches += 2;
   return AEW_OK;
@@ -298,7 +300,7 @@ int decode_e(aew_handle* h, int n, float* buf, cudaStream_t s) {
   const size_t nb = nblocks_of(h);
   cudaError_t e = aew::codec_decode_grid_e(h->codec, h->lat + (size_t)n * nb * h->cfg.n_lat,
                                            h->cfg.nx, h->cfg.ny, h->cfg.nz,
-                                           h->bmx + (size_t)n * nb * 4, buf, s);
+                                           h->bmx + (size_t)n * nb * 4, buf, s, h->overlap_ctas);
   if (e != cudaSuccess) return cuda_fail(h, e, "codec_decode_grid_e");
   h->stats.kernel_launches += 2;
   return AEW_OK;
@@ -582,10 +584,15 @@ int aew_create(const aew_config* cfg, aew_handle** out) {
          dalloc(h, &h->ovf, 1) && dalloc(h, &h->xpk[0], nb * aew::kNIn) &&
          dalloc(h, &h->xpk[1], nb * aew::kNIn) && dalloc(h, &h->edb[0], C) &&
          dalloc(h, &h->edb[1], C);
-    int prio = 0, lo = 0, hi = 0;
-    if (const char* env = getenv("AEW_SIDE_PRIORITY"))   // tuning override: codec stream first
-      if (atoi(env) != 0 && cudaDeviceGetStreamPriorityRange(&lo, &hi) == cudaSuccess) prio = hi;
-    ok = ok && cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, prio) == cudaSuccess;
+    // The codec GEMMs run on a high-priority side stream with half the SMs, so their
+    // CTAs are placed first and the concurrent stencil step keeps the other half
+    // (measured best at 256^3 among caps of 76-152 CTAs and 2-4 GEMM stages).
+    int lo = 0, hi = 0, sms = 0;
+    if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess) hi = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    h->overlap_ctas = sms > 1 ? sms / 2 : 0;
+    if (const char* env = getenv("AEW_GEMM_CTAS_OVERLAP")) h->overlap_ctas = atoi(env);   // tuning override
+    ok = ok && cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, hi) == cudaSuccess;
     for (int i = 0; ok && i < 2; ++i)
       ok = cudaEventCreateWithFlags(&h->ev_a[i], cudaEventDisableTiming) == cudaSuccess &&
            cudaEventCreateWithFlags(&h->ev_b[i], cudaEventDisableTiming) == cudaSuccess;

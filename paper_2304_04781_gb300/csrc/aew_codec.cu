@@ -401,42 +401,48 @@ cudaError_t codec_encode_grid(Codec* c, const float* const f[4], int nx, int ny,
 }
 
 
+static int ctas_of(const Codec* c, int ctas) { return ctas > 0 ? ctas : c->max_ctas; }
+
 cudaError_t codec_encode_vectors(Codec* c, const uint16_t* vec, long long n, uint16_t* lat,
-                                 int* overflow, cudaStream_t s) {
+                                 int* overflow, cudaStream_t s, int ctas) {
   if (!ensure_H(c, (size_t)n)) return cudaErrorMemoryAllocation;
+  const int g = ctas_of(c, ctas);
   EpBiasGeluH ep{c->w[1], c->H, n};
   cudaError_t e = gemm::launch<256, true>(n, kNHid, kNIn, gemm::Mat{vec, n, kNIn},
-                                          gemm::Mat{c->W1t, kNHid, kNIn}, ep, c->err, s, c->max_ctas, c->max_stages);
+                                          gemm::Mat{c->W1t, kNHid, kNIn}, ep, c->err, s, g, c->max_stages);
   if (e != cudaSuccess) return e;
   const int nl = c->n_lat;
   EpLatent e2{c->w[3], lat, nl, n, overflow};
   const gemm::Mat a2{c->H, n, kNHid}, b2{c->W2t, nl, kNHid};
-  if (nl == 64) return gemm::launch<64, true>(n, nl, kNHid, a2, b2, e2, c->err, s, c->max_ctas, c->max_stages);
-  return gemm::launch<32, true>(n, nl, kNHid, a2, b2, e2, c->err, s, c->max_ctas, c->max_stages);
+  if (nl == 64) return gemm::launch<64, true>(n, nl, kNHid, a2, b2, e2, c->err, s, g, c->max_stages);
+  return gemm::launch<32, true>(n, nl, kNHid, a2, b2, e2, c->err, s, g, c->max_stages);
 }
 
-static cudaError_t decode_hidden(Codec* c, const uint16_t* lat, long long nb, cudaStream_t s) {
+static cudaError_t decode_hidden(Codec* c, const uint16_t* lat, long long nb, cudaStream_t s,
+                                 int ctas) {
   if (!ensure_H(c, (size_t)nb)) return cudaErrorMemoryAllocation;
   const int nl = c->n_lat;
   EpBiasGeluH ep{c->w[5], c->H, nb};
   return gemm::launch<256, false>(nb, kNHid, nl, gemm::Mat{lat, nb, nl},
-                                  gemm::Mat{c->W3t, kNHid, nl}, ep, c->err, s, c->max_ctas, c->max_stages);
+                                  gemm::Mat{c->W3t, kNHid, nl}, ep, c->err, s, ctas_of(c, ctas),
+                                  c->max_stages);
 }
 
 cudaError_t codec_decode_grid_e(Codec* c, const uint16_t* lat, int nx, int ny, int nz,
-                                const unsigned* bmax, float* e_out, cudaStream_t s) {
+                                const unsigned* bmax, float* e_out, cudaStream_t s, int ctas) {
   const int NBx = nx / 8, NBy = ny / 8, NBz = nz / 8;
   const long long nb = (long long)NBx * NBy * NBz;
-  cudaError_t e = decode_hidden(c, lat, nb, s);
+  cudaError_t e = decode_hidden(c, lat, nb, s, ctas);
   if (e != cudaSuccess) return e;
   EpDecGrid ep{c->w[7], bmax, e_out, nx, ny, nz, NBx, NBy, nb};
   return gemm::launch<256, true>(nb, 512, kNHid, gemm::Mat{c->H, nb, kNHid},
-                                 gemm::Mat{c->W4e, 512, kNHid}, ep, c->err, s, c->max_ctas, c->max_stages);
+                                 gemm::Mat{c->W4e, 512, kNHid}, ep, c->err, s, ctas_of(c, ctas),
+                                 c->max_stages);
 }
 
 cudaError_t codec_decode_vectors(Codec* c, const uint16_t* lat, long long nvec, float* out,
                                  cudaStream_t s) {
-  cudaError_t e = decode_hidden(c, lat, nvec, s);
+  cudaError_t e = decode_hidden(c, lat, nvec, s, 0);
   if (e != cudaSuccess) return e;
   EpVec ep{c->w[7], out, kNIn, nvec};
   return gemm::launch<256, true>(nvec, kNIn, kNHid, gemm::Mat{c->H, nvec, kNHid},

@@ -33,13 +33,15 @@ cudaError_t codec_encode_grid(Codec* c, const float* const f[4], int nx, int ny,
                               unsigned* bmax, uint16_t* lat, int* overflow, cudaStream_t s);
 
 // Encode already normalised BF16 block vectors [n][2048] into FP16 latents [n][n_lat].
+// ctas > 0 caps the GEMMs' persistent CTAs (room for a concurrent stencil step)
 cudaError_t codec_encode_vectors(Codec* c, const uint16_t* vec, long long n, uint16_t* lat,
-                                 int* overflow, cudaStream_t s);
+                                 int* overflow, cudaStream_t s, int ctas = 0);
 
 // Decode the strain part of latents into the grid: e = s_b * dec_e(z) with the block's
 // power-of-two scale s_b from bmax[b][0]; 0 on boundary nodes.
 cudaError_t codec_decode_grid_e(Codec* c, const uint16_t* lat, int nx, int ny, int nz,
-                                const unsigned* bmax, float* e_out, cudaStream_t s);
+                                const unsigned* bmax, float* e_out, cudaStream_t s,
+                                int ctas = 0);
 
 // Decode latents to normalised vectors FP32 [nvec][2048].
 cudaError_t codec_decode_vectors(Codec* c, const uint16_t* lat, long long nvec, float* out,

@@ -5,18 +5,18 @@
 // bias / activation / store).
 //
 // Persistent CTAs (one per SM) walk 128 x BN output tiles; K runs in chunks of 64
-// through a ring of `ns` shared-memory stages.  Ten warps:
-//   warp 8, one lane  TMA producer: per chunk one cp.async.bulk.tensor per operand
+// through a ring of `ns` shared-memory stages.  Eighteen warps:
+//   warp 16, one lane TMA producer: per chunk one cp.async.bulk.tensor per operand
 //                      (128-byte-swizzled tile; or, with SW = false, eight 16-byte-wide
 //                      boxes into the unswizzled canonical layout), completion counted
 //                      in bytes on the stage's `full` mbarrier;
-//   warp 9            TMEM allocation (two BN-column accumulators) and, on one lane,
+//   warp 17           TMEM allocation (two BN-column accumulators) and, on one lane,
 //                      the MMA issuer: 4 x tcgen05.mma (K = 16) per chunk,
 //                      tcgen05.commit to the stage's `empty` mbarrier, and per tile to
 //                      the accumulator's `accf` mbarrier;
-//   warps 0-7         epilogue (two warps per TMEM lane quarter, one column half each),
-//                      which drains accumulator a while the MMAs fill the other one,
-//                      then arrives on `acce[a]`.
+//   warps 0-15        epilogue (four warps per TMEM lane quarter, each taking every
+//                      fourth 32-column group), which drains accumulator a while the
+//                      MMAs fill the other one, then arrives on `acce[a]`.
 // Every wait is bounded in time; on timeout the kernel records an error and returns.
 #pragma once
 
@@ -35,11 +35,11 @@ namespace gemm {
 
 constexpr int kBM = 128;
 constexpr int kBK = 64;
-constexpr int kEpiWarps = 8;                 // warps 0-7: epilogue
+constexpr int kEpiWarps = 16;                // warps 0-15: epilogue
 constexpr int kEpiThreads = kEpiWarps * 32;
-constexpr int kTmaWarp = 8;
-constexpr int kMmaWarp = 9;
-constexpr int kThreads = 320;
+constexpr int kTmaWarp = 16;
+constexpr int kMmaWarp = 17;
+constexpr int kThreads = 576;
 constexpr uint64_t kWaitNs = 200000000ull;   // 200 ms (a healthy wait takes microseconds)
 constexpr int kSmemBudget = 200 * 1024;
 
@@ -253,8 +253,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncwarp();
   } else {
     // ------------------------------------------------------------- epilogue warps
-    const int q = warp & 3, hh = (warp >> 2) & 1;
-    constexpr int CW = BN >= 64 ? BN / 2 : BN;   // columns per warp
+    // a warp reaches only its TMEM lane quarter (warp % 4); column groups g = cg, cg+4..
+    const int q = warp & 3, cg = warp >> 2;
+    constexpr int G = BN / 32;                   // 32-column groups per tile
     int tl = 0;
     for (int t = blockIdx.x; t < T; t += gridDim.x, ++tl) {
       const int a = tl & 1;
@@ -266,14 +267,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       const int m0 = (t / tn) * kBM, n0 = (t % tn) * BN;
       const long long row = (long long)m0 + q * 32 + lane;
-      if (BN >= 64 || hh == 0) {
 #pragma unroll 1
-        for (int cc = 0; cc < CW; cc += 32) {
-          const int col = (BN >= 64 ? hh * CW : 0) + cc;
-          float v[32];
-          tc::tmem_ld32(tmem + (uint32_t)(a * BN) + ((uint32_t)(q * 32) << 16) + (uint32_t)col, v);
-          ep(row, n0 + col, v);
-        }
+      for (int g = cg; g < G; g += kEpiWarps / 4) {
+        const int col = g * 32;
+        float v[32];
+        tc::tmem_ld32(tmem + (uint32_t)(a * BN) + ((uint32_t)(q * 32) << 16) + (uint32_t)col, v);
+        ep(row, n0 + col, v);
       }
       tc::fence_before_sync();
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&acce[a])) : "memory");
