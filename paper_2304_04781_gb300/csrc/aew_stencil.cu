@@ -49,9 +49,12 @@ constexpr int kW4E = kWE / 4;         // 34 float4 per halo row
 constexpr int kW4 = kTXW / 4;         // 32 float4 per plain row
 constexpr uint64_t kWaitNs = 200000000ull;
 constexpr int kMaxStages = 4;
-// PACK: one plane of the CTA's 16 blocks, 4 fields x 8 rows x 8 BF16 each; then the
-// layer's block maxima per row [TY][16][4] and inverse scales [16][4]
-constexpr int kPackTile = (kTXW / 8) * 512;
+// PACK: one plane of the CTA's 16 blocks, 4 fields x 8 rows x 8 BF16 each (a 512-byte
+// row per block, rows 528 bytes apart so that the 16 lane pairs of a warp, one per
+// block, write distinct banks); then the layer's block maxima per row [TY][16][4] and
+// inverse scales [16][4]
+constexpr int kPackRow = 512 + 16;
+constexpr int kPackTile = (kTXW / 8) * kPackRow;
 constexpr int kPackExtra = 2 * kPackTile + (TY * 16 * 4 + 16 * 4) * 4;
 
 // bytes one box delivers (the mbarrier transaction count) ...
@@ -283,7 +286,7 @@ __global__ void __launch_bounds__(NTHR, (INCR || PACK) ? 2 : 3)
     if (PACK) {   // BF16 block vectors of the input state and block maxima
       if (act) {
         // this plane's piece of block (lane / 2): [field][y][x] in the staging tile
-        uint8_t* dst = pk + (k & 1) * kPackTile + (lane >> 1) * 512 + ty * 16 + (lane & 1) * 8;
+        uint8_t* dst = pk + (k & 1) * kPackTile + (lane >> 1) * kPackRow + ty * 16 + (lane & 1) * 8;
         const float4 fv[4] = {e_c, vx_c, vy_c, vz_c};
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
@@ -367,7 +370,7 @@ __global__ void __launch_bounds__(NTHR, (INCR || PACK) ? 2 : 3)
         if (bx < NBx) {
           const size_t blk = ((size_t)(k >> 3) * NBy + (y0 >> 3)) * NBx + bx;
           uint8_t* dst = reinterpret_cast<uint8_t*>(a.xpack) + blk * 4096 + (k & 7) * 512;
-          reinterpret_cast<uint4*>(dst)[lane] = reinterpret_cast<const uint4*>(src + j * 512)[lane];
+          reinterpret_cast<uint4*>(dst)[lane] = reinterpret_cast<const uint4*>(src + j * kPackRow)[lane];
         }
       }
       if ((k & 7) == 7) {
