@@ -730,6 +730,18 @@ int default_kc(int nx, int ny, int nz, bool adjoint) {
   return kc < 1 ? 1 : kc;
 }
 
+// z planes per CTA of the packing step: whole 8-plane layers.  Two layers per CTA let it
+// normalise the first while the second one's planes are already in flight (measured at
+// 256^3: 16 planes 1.3% faster than 8 per AE gradient step, 24 and 32 slower).
+static int pack_kc(int kc) {
+  static const int v = [] {
+    const char* env = getenv("AEW_STENCIL_KC_PACK");   // tuning override
+    return env ? atoi(env) : 16;
+  }();
+  (void)kc;
+  return v > 0 ? v : 16;
+}
+
 cudaError_t launch_fwd_step(const FwdStep& a, bool incremental, cudaStream_t s) {
   if (!a.err) return cudaErrorInvalidValue;
   FwdMaps mp;
@@ -749,7 +761,7 @@ cudaError_t launch_fwd_step(const FwdStep& a, bool incremental, cudaStream_t s) 
     // packing normalises whole 8-plane block layers inside one CTA
     if (nx % 8 || ny % 8 || nz % 8) return cudaErrorInvalidValue;
     FwdStep b = a;
-    b.kc = (a.kc + 7) / 8 * 8;
+    b.kc = (pack_kc(a.kc) + 7) / 8 * 8;
     return launch_fwd<false, true>(mp, b, s);
   }
   return launch_fwd<false, false>(mp, a, s);
