@@ -31,6 +31,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "gradients/hour at 256^3x2000 steps: AE vs checkpointing; stencil HBM GB/s"
+# DRAM bytes (read + write) of one forward-step launch at 256^3, from an ncu capture of
+# the current kernel (dram__bytes_read.sum + dram__bytes_write.sum); None once the
+# kernel changes until it is captured again
+FWD_TRAFFIC_256 = 586.34e6
 SHAPE = (256, 256, 256)
 NT = 2000
 NREC = 128
@@ -343,7 +347,8 @@ def run_ours(args):
             "config": dict(workload(shape, nt), codec_weights="trained" if trained else "random-init"),
             "roofline": {"kernel": "forward leapfrog step", "bound": "hbm", "achieved": stencil_gbs,
                          "peak": peak, "unit": "GB/s", "frac": stencil_gbs / peak,
-                         "peak_kind": f"{peak_kind} copy bandwidth", "traffic": None,
+                         "peak_kind": f"{peak_kind} copy bandwidth",
+                         "traffic": FWD_TRAFFIC_256 if tuple(shape) == SHAPE else None,
                          "bytes_per_launch": bytes_step},
             "stencil": {"cell_updates_per_s": C / step_s, "gbs": stencil_gbs,
                         "frac_of_8tbs": stencil_gbs / 8000.0},
@@ -449,6 +454,7 @@ def run_accuracy(args):
     # (|<J dc, r>| is then small against |J dc| |r|: the cancellation is reported) and
     # for the smooth residual r = J dc2 of a second direction
     d = ref.forward(c)
+    ref.gradient(c, d_obs)      # a forward history at c for the Jacobian-vector products
     Jdc = ref.jvp(dirs[0])
     dc2 = torch.from_numpy(inputs.direction(shape, H, seed=99).astype(np.float32)).cuda()
     Jdc2 = ref.jvp(dc2)
