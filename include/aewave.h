@@ -225,7 +225,8 @@ int aew_jvp(aew_handle* h, const float* dc_dev, float* dd_dev, void* stream);
 /* Algorithm 1 (data generation): run the forward solve for c_dev and pack every
  * `every`-th state n (n = every, 2*every, ... < nt) into BF16 block vectors, each
  * field of each block divided by its power-of-two scale (see aew_codec_encode).
- * out_dev: device BF16 (uint16 bit patterns) [max_vectors][2048]; *n_written receives
+ * out_dev: device BF16 (uint16 bit patterns) [max_vectors][2048], 16-byte aligned
+ * (AEW_E_ARG otherwise); the forward step that reads a state packs it; *n_written receives
  * the number of vectors written (whole states only, at most max_vectors).
  * block_max_dev (may be NULL): device FP32 [max_vectors][4] receiving the block maxima
  * of each written vector.  The history storage of the handle is not touched. */

@@ -123,12 +123,14 @@ size_t nblocks_of(const aew_handle* h) {
 // ---------------------------------------------------------------------------------
 // Single steps
 // ---------------------------------------------------------------------------------
+// xpack / bmax: pack the input state n into normalised BF16 block vectors and store
+// its block maxima (AE forward and Algorithm 1 snapshots)
 int fwd_step(aew_handle* h, int n, float* const in[4], float* const out[4], const float* wav,
-             float* d_row, cudaStream_t s, uint16_t* xpack = nullptr) {
+             float* d_row, cudaStream_t s, uint16_t* xpack = nullptr, unsigned* bmax = nullptr) {
   aew::FwdStep a{};
-  if (xpack) {  // pack the input state n (AE forward, n >= 1) and its block maxima
+  if (xpack) {
     a.xpack = xpack;
-    a.bmax = h->bmx + (size_t)n * nblocks_of(h) * 4;
+    a.bmax = bmax;
   }
   a.m = h->m;
   a.e = in[0];
@@ -481,7 +483,7 @@ int gradient_ae(aew_handle* h, const float* d_obs, const float* wav, cudaStream_
   for (int n = 0; n < nt; ++n) {
     if (n >= 3) AEW_CK(cudaStreamWaitEvent(s, h->ev_b[n & 1], 0));
     rc = fwd_step(h, n, h->st[cur], h->st[cur ^ 1], wav, drow(h, h->d, n + 1), s,
-                  n >= 1 ? h->xpk[n & 1] : nullptr);
+                  n >= 1 ? h->xpk[n & 1] : nullptr, h->bmx + (size_t)n * nblocks_of(h) * 4);
     if (rc) return rc;
     cur ^= 1;
     if (n >= 1) {
@@ -1022,6 +1024,8 @@ int aew_snapshots(aew_handle* h, const float* c_dev, int every, uint16_t* out_de
   if (!h) return AEW_E_ARG;
   if (!out_dev || !n_written || every < 1 || max_vectors < 0)
     return fail(h, AEW_E_ARG, "bad argument");
+  if (reinterpret_cast<uintptr_t>(out_dev) & 15)
+    return fail(h, AEW_E_ARG, "out_dev must be 16-byte aligned");
   if (h->cfg.nx % 8 || h->cfg.ny % 8 || h->cfg.nz % 8)
     return fail(h, AEW_E_CONFIG, "snapshots need nx, ny, nz multiples of 8");
   h->err.clear();
@@ -1030,26 +1034,25 @@ int aew_snapshots(aew_handle* h, const float* c_dev, int every, uint16_t* out_de
   if (rc) return rc;
   h->have_grad = false;
   const size_t nb = nblocks_of(h);
-  if (!h->bm_tmp && !dalloc(h, &h->bm_tmp, nb * 4)) return fail(h, AEW_E_NOMEM, "workspace");
-  if (!h->raw_tmp && !dalloc(h, &h->raw_tmp, nb * aew::kNIn))
+  if (!block_max_dev && !h->bm_tmp && !dalloc(h, &h->bm_tmp, nb * 4))
     return fail(h, AEW_E_NOMEM, "workspace");
   if ((rc = zero_state(h, h->st[0], s))) return rc;
   int cur = 0;
   long long written = 0;
-  for (int n = 0; n + 1 < h->cfg.nt; ++n) {
-    if ((rc = fwd_step(h, n, h->st[cur], h->st[cur ^ 1], h->wav.data(), nullptr, s))) return rc;
+  // state n (1 <= n < nt, n % every == 0) is packed by the forward step that reads it:
+  // step n, or one extra step past the end for the state nt - 1
+  for (int n = 0; n < h->cfg.nt; ++n) {
+    const bool pack = n >= 1 && n % every == 0 && written + (long long)nb <= max_vectors;
+    if (n + 1 == h->cfg.nt && !pack) break;
+    uint16_t* xp = pack ? out_dev + (size_t)written * aew::kNIn : nullptr;
+    unsigned* bm = pack ? (block_max_dev ? reinterpret_cast<unsigned*>(block_max_dev) +
+                                               (size_t)written * 4
+                                         : h->bm_tmp)
+                        : nullptr;
+    if ((rc = fwd_step(h, n, h->st[cur], h->st[cur ^ 1], h->wav.data(), nullptr, s, xp, bm)))
+      return rc;
     cur ^= 1;
-    const int step = n + 1;
-    if (step % every == 0 && written + (long long)nb <= max_vectors) {
-      const float* f[4] = {h->st[cur][0], h->st[cur][1], h->st[cur][2], h->st[cur][3]};
-      AEW_CK(aew::snapshot_pack(f, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->bm_tmp, h->raw_tmp,
-                                out_dev + (size_t)written * aew::kNIn, s));
-      if (block_max_dev)
-        AEW_CK(cudaMemcpyAsync(block_max_dev + (size_t)written * 4, h->bm_tmp,
-                               nb * 4 * sizeof(float), cudaMemcpyDeviceToDevice, s));
-      h->stats.kernel_launches += 2;
-      written += (long long)nb;
-    }
+    if (pack) written += (long long)nb;
   }
   AEW_CK(cudaStreamSynchronize(s));
   *n_written = written;

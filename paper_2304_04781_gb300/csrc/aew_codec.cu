@@ -24,6 +24,7 @@
 
 #include "aew_codec.cuh"
 #include "aew_codec_state.cuh"
+#include "aew_dec.cuh"
 #include "aew_gemm.cuh"
 
 namespace aew {
@@ -428,10 +429,52 @@ static cudaError_t decode_hidden(Codec* c, const uint16_t* lat, long long nb, cu
                                   c->max_stages);
 }
 
+static bool use_two_gemm_decode() {
+  static const bool v = [] {
+    const char* env = getenv("AEW_DEC_FUSED");   // A/B switch to the two-GEMM decode
+    return env && atoi(env) == 0;
+  }();
+  return v;
+}
+
+// strain decode in one kernel: layer 1, GELU, layer 2 with H kept in shared memory
+static cudaError_t decode_e_fused(Codec* c, const uint16_t* lat, long long nb, const EpDecGrid& ep,
+                                  cudaStream_t s, int ctas) {
+  static bool attr = false;
+  static int sms = 0;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(dec::dec2_kernel<EpDecGrid>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)dec::kSmem);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    attr = true;
+  }
+  const int nl = c->n_lat;
+  CUtensorMap tz, tw3, tw4;
+  if (gemm::make_tmap(&tz, lat, true, nb, nl, nl, dec::kRows, true) != CUDA_SUCCESS ||
+      gemm::make_tmap(&tw3, c->W3t, true, kNHid, nl, nl, 256, true) != CUDA_SUCCESS ||
+      gemm::make_tmap(&tw4, c->W4e, false, 512, kNHid, kNHid, 256, true) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  const long long tiles = (nb + dec::kRows - 1) / dec::kRows;
+  const int g = ctas_of(c, ctas);
+  const int cap = (g > 0 && g < sms) ? g : sms;
+  const int grid = (int)(tiles < cap ? tiles : cap);
+  dec::dec2_kernel<EpDecGrid><<<grid, dec::kThreads, dec::kSmem, s>>>(tz, tw3, tw4, (int)nb,
+                                                                      c->w[5], ep, c->err);
+  return cudaGetLastError();
+}
+
 cudaError_t codec_decode_grid_e(Codec* c, const uint16_t* lat, int nx, int ny, int nz,
                                 const unsigned* bmax, float* e_out, cudaStream_t s, int ctas) {
   const int NBx = nx / 8, NBy = ny / 8, NBz = nz / 8;
   const long long nb = (long long)NBx * NBy * NBz;
+  if (!use_two_gemm_decode()) {
+    EpDecGrid ep{c->w[7], bmax, e_out, nx, ny, nz, NBx, NBy, nb};
+    return decode_e_fused(c, lat, nb, ep, s, ctas);
+  }
   cudaError_t e = decode_hidden(c, lat, nb, s, ctas);
   if (e != cudaSuccess) return e;
   EpDecGrid ep{c->w[7], bmax, e_out, nx, ny, nz, NBx, NBy, nb};

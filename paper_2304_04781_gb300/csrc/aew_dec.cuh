@@ -1,0 +1,252 @@
+// Fused strain decoder (the adjoint's decode, Sec. 3.3 layers of Eq. (5)):
+//   H = GELU(Z W3 + b3)         Z: FP16 latents [M][n_lat], W3t FP16 [512][n_lat]
+//   E = H W4e^T (+ b4, x s_b)   W4e: the 512 strain rows of W4, BF16 [512][512]
+// for tiles of 128 blocks, with H kept in shared memory between the two products
+// instead of a round trip through HBM.
+//
+// Persistent CTAs (one per SM) walk the 128-block tiles.  Eighteen warps:
+//   warp 16, one lane TMA producer.  Per tile: the latent tile (128 x 64, zero-filled
+//                      past n_lat) and all of W3t (512 x 64) into the H buffer, which
+//                      is free once the previous tile's second-layer MMAs have read it;
+//                      then the 16 chunks of W4e (two output halves x 8 K chunks of
+//                      256 x 64) through a 3-stage ring.
+//   warp 17           TMEM (512 columns) and, on one lane, the MMA issuer: layer 1 as
+//                      two N = 256 MMAs per K step into columns 0-511 (FP16 x FP16),
+//                      then, once the epilogue has written H, layer 2 for output half h
+//                      into columns 256h..256h+255 (BF16 x BF16).
+//   warps 0-15        epilogue.  E1: layer-1 accumulator + b3, GELU, BF16, written into
+//                      the H buffer in the 128-byte-swizzled K-major layout the MMA
+//                      reads (8 K chunks of 128 rows x 128 bytes).  E2: layer-2
+//                      accumulator through the grid-scatter epilogue.
+// H buffer, TMEM and ring are each reused tile after tile; mbarriers order every reuse,
+// and every wait is bounded (a timed-out wait aborts the CTA and sets the error flag).
+#pragma once
+
+#include "aew_gemm.cuh"
+
+namespace aew {
+namespace dec {
+
+constexpr int kRows = 128;                  // blocks per tile
+constexpr int kHid = 512;
+constexpr int kChunk = 16384;               // 128 rows x 64 x 2 bytes
+constexpr int kHBytes = 8 * kChunk;         // H: 8 K chunks
+constexpr int kW3Off = kChunk;              // W3t (512 x 64) behind the latent tile
+constexpr int kRing = 3;
+constexpr int kStage = 256 * 64 * 2;        // one W4e chunk: 256 output rows x 64 K
+constexpr int kF1Bytes = kChunk + kHid * 64 * 2;
+constexpr size_t kSmem = (size_t)kHBytes + (size_t)kRing * kStage + 256 + 1024;
+constexpr int kThreads = 576;
+constexpr int kEpi = 16;                    // epilogue warps
+constexpr int kTmaWarp = 16, kMmaWarp = 17;
+
+// byte offset of element k (0..63) of row r (0..127) in a 128-byte-swizzled K chunk
+__device__ __forceinline__ uint32_t sw128_off(int r, int k) {
+  const int ch = k >> 3;
+  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((ch ^ (r & 7)) << 4) + ((k & 7) << 1));
+}
+
+template <class EP>
+__global__ void __launch_bounds__(kThreads, 1)
+    dec2_kernel(const __grid_constant__ CUtensorMap tz, const __grid_constant__ CUtensorMap tw3,
+                const __grid_constant__ CUtensorMap tw4, int M, const float* __restrict__ b3,
+                EP ep, int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint8_t* hb = smem;                       // H buffer (and layer-1 operands)
+  uint8_t* ring = smem + kHBytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(ring + kRing * kStage);
+  uint64_t* empty = full + kRing;
+  uint64_t* f1 = empty + kRing;             // layer-1 operands landed
+  uint64_t* acc1 = f1 + 1;                  // layer-1 accumulator complete
+  uint64_t* hready = acc1 + 1;              // H written by the epilogue
+  uint64_t* hfree = hready + 1;             // layer-2 MMAs done reading H
+  uint64_t* acc2 = hfree + 1;               // [2] output half complete
+  uint64_t* tfree = acc2 + 2;               // layer-2 accumulator drained
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(tfree + 1);
+  int* abort_flag = reinterpret_cast<int*>(tslot + 1);
+
+  if (*reinterpret_cast<volatile int*>(err) != 0) return;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int T = (M + kRows - 1) / kRows;
+  constexpr uint32_t ID1 = tc::idesc_f16(kRows, 256, false);   // FP16 x FP16
+  constexpr uint32_t ID2 = tc::idesc_f16(kRows, 256, true);    // BF16 x BF16
+  constexpr uint64_t W = gemm::kWaitNs;
+
+  if (warp == kMmaWarp) {
+    tc::tmem_alloc(tc::smem_u32(tslot), 512);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    gemm::prefetch_tmap(&tz);
+    gemm::prefetch_tmap(&tw3);
+    gemm::prefetch_tmap(&tw4);
+    for (int s = 0; s < kRing; ++s) {
+      tc::mbar_init(tc::smem_u32(&full[s]), 1);
+      tc::mbar_init(tc::smem_u32(&empty[s]), 1);
+    }
+    tc::mbar_init(tc::smem_u32(f1), 1);
+    tc::mbar_init(tc::smem_u32(acc1), 1);
+    tc::mbar_init(tc::smem_u32(hready), kEpi * 32);
+    tc::mbar_init(tc::smem_u32(hfree), 1);
+    tc::mbar_init(tc::smem_u32(&acc2[0]), 1);
+    tc::mbar_init(tc::smem_u32(&acc2[1]), 1);
+    tc::mbar_init(tc::smem_u32(tfree), kEpi * 32);
+    *abort_flag = 0;
+    tc::mbar_fence_init();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tslot;
+
+  if (warp == kTmaWarp) {
+    if (lane == 0) {
+      // ------------------------------------------------------------- TMA producer
+      int it = 0, tl = 0;
+      for (int t = blockIdx.x; t < T; t += gridDim.x, ++tl) {
+        const int m0 = t * kRows;
+        if (tl >= 1 && !tc::mbar_wait(tc::smem_u32(hfree), (tl - 1) & 1, W)) {
+          atomicExch(abort_flag, 1);
+          break;
+        }
+        const uint32_t fb = tc::smem_u32(f1), h0 = tc::smem_u32(hb);
+        gemm::mbar_expect_tx(fb, kF1Bytes);
+        gemm::tma_load_2d(h0, &tz, 0, m0, fb);
+        gemm::tma_load_2d(h0 + kW3Off, &tw3, 0, 0, fb);
+        gemm::tma_load_2d(h0 + kW3Off + 256 * 128, &tw3, 0, 256, fb);
+        bool ok = true;
+        for (int h = 0; h < 2 && ok; ++h)
+          for (int kk = 0; kk < 8; ++kk, ++it) {
+            const int s = it % kRing;
+            if (it >= kRing &&
+                !tc::mbar_wait(tc::smem_u32(&empty[s]), ((it / kRing) - 1) & 1, W)) {
+              atomicExch(abort_flag, 1);
+              ok = false;
+              break;
+            }
+            const uint32_t b = tc::smem_u32(&full[s]);
+            gemm::mbar_expect_tx(b, kStage);
+            gemm::tma_load_2d(tc::smem_u32(ring + s * kStage), &tw4, kk * 64, h * 256, b);
+          }
+        if (!ok) break;
+      }
+    }
+    __syncwarp();
+  } else if (warp == kMmaWarp) {
+    if (lane == 0) {
+      // ------------------------------------------------------------- MMA issuer
+      int it = 0, tl = 0;
+      const uint32_t h0 = tc::smem_u32(hb);
+      for (int t = blockIdx.x; t < T; t += gridDim.x, ++tl) {
+        const uint32_t ph = tl & 1;
+        bool ok = (tl == 0 || tc::mbar_wait(tc::smem_u32(tfree), (tl - 1) & 1, W)) &&
+                  tc::mbar_wait(tc::smem_u32(f1), ph, W);
+        if (!ok) {
+          atomicExch(abort_flag, 1);
+          break;
+        }
+        tc::fence_after_sync();
+        // layer 1: K = 64 in four steps of 16, outputs 0-255 and 256-511
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const uint64_t ad = gemm::sdesc_sw128(h0 + k * 32);
+          tc::mma_f16(tmem, ad, gemm::sdesc_sw128(h0 + kW3Off + k * 32), ID1, k > 0 ? 1u : 0u);
+          tc::mma_f16(tmem + 256, ad, gemm::sdesc_sw128(h0 + kW3Off + 256 * 128 + k * 32), ID1,
+                      k > 0 ? 1u : 0u);
+        }
+        tc::mma_commit(tc::smem_u32(acc1));
+        if (!tc::mbar_wait(tc::smem_u32(hready), ph, W)) {
+          atomicExch(abort_flag, 1);
+          break;
+        }
+        tc::fence_after_sync();
+        // layer 2: A = H from shared memory, B = W4e chunks from the ring
+        for (int h = 0; h < 2 && ok; ++h) {
+          for (int kk = 0; kk < 8; ++kk, ++it) {
+            const int s = it % kRing;
+            if (!tc::mbar_wait(tc::smem_u32(&full[s]), (it / kRing) & 1, W)) {
+              atomicExch(abort_flag, 1);
+              ok = false;
+              break;
+            }
+            tc::fence_after_sync();
+            const uint32_t a0 = h0 + kk * kChunk, b0 = tc::smem_u32(ring + s * kStage);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+              tc::mma_f16(tmem + (uint32_t)(h * 256), gemm::sdesc_sw128(a0 + k * 32),
+                          gemm::sdesc_sw128(b0 + k * 32), ID2, (kk > 0 || k > 0) ? 1u : 0u);
+            tc::mma_commit(tc::smem_u32(&empty[s]));
+          }
+          if (ok) tc::mma_commit(tc::smem_u32(&acc2[h]));
+        }
+        if (!ok) break;
+        tc::mma_commit(tc::smem_u32(hfree));
+      }
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------- epilogue warps
+    const int q = warp & 3, cg = warp >> 2;   // TMEM lane quarter; column groups cg, cg+4, ..
+    const int r = q * 32 + lane;              // row of the tile
+    int tl = 0;
+    for (int t = blockIdx.x; t < T; t += gridDim.x, ++tl) {
+      const uint32_t ph = tl & 1;
+      bool ok = tc::mbar_wait(tc::smem_u32(acc1), ph, W);
+      tc::fence_after_sync();
+      if (!ok || *reinterpret_cast<volatile int*>(abort_flag)) {
+        if (lane == 0) atomicExch(err, 1);
+        break;
+      }
+      // E1: H = bf16(gelu(acc + b3)), 32 columns at a time
+#pragma unroll 1
+      for (int g = cg; g < kHid / 32; g += kEpi / 4) {
+        float v[32];
+        tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(g * 32), v);
+        uint32_t pk[16];
+#pragma unroll
+        for (int j = 0; j < 32; j += 2)
+          pk[j / 2] = gemm::pack_bf16(gemm::gelu_f(v[j] + __ldg(b3 + g * 32 + j)),
+                                      gemm::gelu_f(v[j + 1] + __ldg(b3 + g * 32 + j + 1)));
+        uint8_t* chunk = hb + (g >> 1) * kChunk;
+        const int k0 = (g & 1) * 32;          // column within the 64-wide K chunk
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          *reinterpret_cast<uint4*>(chunk + sw128_off(r, k0 + 8 * c)) =
+              make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]);
+      }
+      tc::fence_proxy_async();                // H visible to the tensor core
+      tc::fence_before_sync();
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(hready)) : "memory");
+      // E2: output halves through the grid epilogue
+      const long long row = (long long)t * kRows + r;
+      for (int h = 0; h < 2 && ok; ++h) {
+        ok = tc::mbar_wait(tc::smem_u32(&acc2[h]), ph, W);
+        tc::fence_after_sync();
+        if (!ok || *reinterpret_cast<volatile int*>(abort_flag)) {
+          ok = false;
+          break;
+        }
+#pragma unroll 1
+        for (int g = cg; g < 8; g += kEpi / 4) {
+          float v[32];
+          tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * 256 + g * 32), v);
+          ep(row, h * 256 + g * 32, v);
+        }
+      }
+      if (!ok) {
+        if (lane == 0) atomicExch(err, 1);
+        break;
+      }
+      tc::fence_before_sync();
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(tfree)) : "memory");
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == kMmaWarp) tc::tmem_dealloc(tmem, 512);
+}
+
+}  // namespace dec
+}  // namespace aew
