@@ -59,6 +59,8 @@ def parse():
                         "(or checkpointing with --ref revolve), decoded-state error")
     p.add_argument("--ref", default="full", choices=["full", "revolve"])
     p.add_argument("--hvps", type=int, default=1)
+    p.add_argument("--f0", type=float, default=25.0,
+                   help="accuracy mode: Ricker peak frequency [Hz] of the workload")
     p.add_argument("--err-hvps", type=int, default=0,
                    help="compare only the first k HVPs with the reference (0: all)")
     return p.parse_args()
@@ -399,12 +401,12 @@ def run_accuracy(args):
     ctrue = torch.from_numpy(inputs.bump_model(c_np.astype(np.float64), H).astype(np.float32)).cuda()
     dirs = [torch.from_numpy(inputs.direction(shape, H, seed=(20 if args.hvps == 1 else 30) + k)
                              .astype(np.float32)).cuda() for k in range(args.hvps)]
-    out = {"config": workload(shape, nt, args.nrec, args.n_lat), "codec_weights": "trained" if trained else "random-init",
+    out = {"config": dict(workload(shape, nt, args.nrec, args.n_lat), f0_hz=args.f0), "codec_weights": "trained" if trained else "random-init",
            "n_lat": args.n_lat, "reference": args.ref}
     def ev():
         return torch.cuda.Event(enable_timing=True)
 
-    ae = aewave.Solver(shape, H, nt, rec, storage="ae", n_lat=args.n_lat)
+    ae = aewave.Solver(shape, H, nt, rec, storage="ae", n_lat=args.n_lat, f0=args.f0)
     ae.codec_set(W)
     d_obs = ae.forward(ctrue)
     a, b = ev(), ev(); a.record()
@@ -428,9 +430,9 @@ def run_accuracy(args):
     torch.cuda.empty_cache()
 
     if args.ref == "full":
-        ref = aewave.Solver(shape, H, nt, rec, storage="full")
+        ref = aewave.Solver(shape, H, nt, rec, storage="full", f0=args.f0)
     else:
-        ref = aewave.Solver(shape, H, nt, rec, storage="revolve", n_checkpoints=20)
+        ref = aewave.Solver(shape, H, nt, rec, storage="revolve", n_checkpoints=20, f0=args.f0)
     a, b = ev(), ev(); a.record()
     J_ref, g_ref = ref.gradient(c, d_obs)
     b.record(); torch.cuda.synchronize()
@@ -475,7 +477,7 @@ def run_accuracy(args):
     torch.cuda.empty_cache()
 
     # decoded-state error on states of this run (every 50th step)
-    tr = train.make_handle(shape, nt=nt, n_lat=args.n_lat)
+    tr = train.make_handle(shape, nt=nt, n_lat=args.n_lat, f0=args.f0)
     tr.codec_set(W)
     every = max(1, nt // 40)
     snaps, sc = train.generate(tr, [2], every)

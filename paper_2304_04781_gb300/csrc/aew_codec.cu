@@ -75,11 +75,13 @@ struct EpBiasGeluH {
   long long M;
   __device__ __forceinline__ void operator()(long long row, int col, const float (&v)[32]) const {
     if (row >= M) return;
+    const float4* bq = reinterpret_cast<const float4*>(bias + col);
     uint32_t pk[16];
 #pragma unroll
-    for (int j = 0; j < 32; j += 2) {
-      const float a0 = v[j] + __ldg(bias + col + j), a1 = v[j + 1] + __ldg(bias + col + j + 1);
-      pk[j / 2] = gemm::pack_bf16(gemm::gelu_f(a0), gemm::gelu_f(a1));
+    for (int j = 0; j < 32; j += 4) {
+      const float4 b = __ldg(bq + j / 4);
+      pk[j / 2] = gemm::pack_bf16(gemm::gelu_f(v[j] + b.x), gemm::gelu_f(v[j + 1] + b.y));
+      pk[j / 2 + 1] = gemm::pack_bf16(gemm::gelu_f(v[j + 2] + b.z), gemm::gelu_f(v[j + 3] + b.w));
     }
     uint4* dst = reinterpret_cast<uint4*>(H + row * kNHid + col);
 #pragma unroll
@@ -96,14 +98,19 @@ struct EpLatent {
   int* ovf;
   __device__ __forceinline__ void operator()(long long row, int col, const float (&v)[32]) const {
     if (row >= M || col >= nl) return;
+    const float4* bq = reinterpret_cast<const float4*>(bias + col);
     uint32_t pk[16];
     bool bad = false;
 #pragma unroll
-    for (int j = 0; j < 32; j += 2) {
-      const float a0 = v[j] + __ldg(bias + col + j), a1 = v[j + 1] + __ldg(bias + col + j + 1);
-      const __half2 hv = __floats2half2_rn(a0, a1);
-      bad |= !(fabsf(a0) <= 65504.f) || !(fabsf(a1) <= 65504.f);
-      pk[j / 2] = *reinterpret_cast<const uint32_t*>(&hv);
+    for (int j = 0; j < 32; j += 4) {
+      const float4 b = __ldg(bq + j / 4);
+      const float a[4] = {v[j] + b.x, v[j + 1] + b.y, v[j + 2] + b.z, v[j + 3] + b.w};
+#pragma unroll
+      for (int h = 0; h < 4; h += 2) {
+        const __half2 hv = __floats2half2_rn(a[h], a[h + 1]);
+        bad |= !(fabsf(a[h]) <= 65504.f) || !(fabsf(a[h + 1]) <= 65504.f);
+        pk[(j + h) / 2] = *reinterpret_cast<const uint32_t*>(&hv);
+      }
     }
     if (bad) atomicOr(ovf, 1);
     uint4* dst = reinterpret_cast<uint4*>(lat + row * nl + col);
@@ -133,12 +140,14 @@ struct EpDecGrid {
     for (int yy = 0; yy < 4; ++yy) {
       const int jy = (int)(8 * by) + y0 + yy;
       const bool yb = zb || jy == 0 || jy == ny - 1;
+      const float4* bq = reinterpret_cast<const float4*>(b4 + z * 256 + (y0 + yy) * 8);
+      const float4 blo = __ldg(bq), bhi = __ldg(bq + 1);
+      const float bv[8] = {blo.x, blo.y, blo.z, blo.w, bhi.x, bhi.y, bhi.z, bhi.w};
       float o[8];
 #pragma unroll
       for (int x = 0; x < 8; ++x) {
         const int ix = (int)(8 * bx) + x;
-        const float bv = __ldg(b4 + z * 256 + (y0 + yy) * 8 + x);
-        const float val = (v[yy * 8 + x] + bv) * s;
+        const float val = (v[yy * 8 + x] + bv[x]) * s;
         o[x] = (yb || ix == 0 || ix == nx - 1) ? 0.f : val;
       }
       float4* dst = reinterpret_cast<float4*>(e + ((size_t)kz * ny + jy) * nx + 8 * bx);
@@ -157,10 +166,12 @@ struct EpVec {
   __device__ __forceinline__ void operator()(long long row, int col, const float (&v)[32]) const {
     if (row >= M) return;
     float4* dst = reinterpret_cast<float4*>(out + row * ld + col);
+    const float4* bq = reinterpret_cast<const float4*>(bias + col);
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
-      dst[q] = make_float4(v[4 * q] + __ldg(bias + col + 4 * q), v[4 * q + 1] + __ldg(bias + col + 4 * q + 1),
-                           v[4 * q + 2] + __ldg(bias + col + 4 * q + 2), v[4 * q + 3] + __ldg(bias + col + 4 * q + 3));
+    for (int q = 0; q < 8; ++q) {
+      const float4 b = __ldg(bq + q);
+      dst[q] = make_float4(v[4 * q] + b.x, v[4 * q + 1] + b.y, v[4 * q + 2] + b.z, v[4 * q + 3] + b.w);
+    }
   }
 };
 
@@ -429,14 +440,6 @@ static cudaError_t decode_hidden(Codec* c, const uint16_t* lat, long long nb, cu
                                   c->max_stages);
 }
 
-static bool use_two_gemm_decode() {
-  static const bool v = [] {
-    const char* env = getenv("AEW_DEC_FUSED");   // A/B switch to the two-GEMM decode
-    return env && atoi(env) == 0;
-  }();
-  return v;
-}
-
 // strain decode in one kernel: layer 1, GELU, layer 2 with H kept in shared memory
 static cudaError_t decode_e_fused(Codec* c, const uint16_t* lat, long long nb, const EpDecGrid& ep,
                                   cudaStream_t s, int ctas) {
@@ -471,16 +474,8 @@ cudaError_t codec_decode_grid_e(Codec* c, const uint16_t* lat, int nx, int ny, i
                                 const unsigned* bmax, float* e_out, cudaStream_t s, int ctas) {
   const int NBx = nx / 8, NBy = ny / 8, NBz = nz / 8;
   const long long nb = (long long)NBx * NBy * NBz;
-  if (!use_two_gemm_decode()) {
-    EpDecGrid ep{c->w[7], bmax, e_out, nx, ny, nz, NBx, NBy, nb};
-    return decode_e_fused(c, lat, nb, ep, s, ctas);
-  }
-  cudaError_t e = decode_hidden(c, lat, nb, s, ctas);
-  if (e != cudaSuccess) return e;
   EpDecGrid ep{c->w[7], bmax, e_out, nx, ny, nz, NBx, NBy, nb};
-  return gemm::launch<256, true>(nb, 512, kNHid, gemm::Mat{c->H, nb, kNHid},
-                                 gemm::Mat{c->W4e, 512, kNHid}, ep, c->err, s, ctas_of(c, ctas),
-                                 c->max_stages);
+  return decode_e_fused(c, lat, nb, ep, s, ctas);
 }
 
 cudaError_t codec_decode_vectors(Codec* c, const uint16_t* lat, long long nvec, float* out,

@@ -204,11 +204,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int g = cg; g < kHid / 32; g += kEpi / 4) {
         float v[32];
         tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(g * 32), v);
+        const float4* bq = reinterpret_cast<const float4*>(b3 + g * 32);
         uint32_t pk[16];
 #pragma unroll
-        for (int j = 0; j < 32; j += 2)
-          pk[j / 2] = gemm::pack_bf16(gemm::gelu_f(v[j] + __ldg(b3 + g * 32 + j)),
-                                      gemm::gelu_f(v[j + 1] + __ldg(b3 + g * 32 + j + 1)));
+        for (int j = 0; j < 32; j += 4) {
+          const float4 b = __ldg(bq + j / 4);
+          pk[j / 2] = gemm::pack_bf16(gemm::gelu_f(v[j] + b.x), gemm::gelu_f(v[j + 1] + b.y));
+          pk[j / 2 + 1] = gemm::pack_bf16(gemm::gelu_f(v[j + 2] + b.z), gemm::gelu_f(v[j + 3] + b.w));
+        }
         uint8_t* chunk = hb + (g >> 1) * kChunk;
         const int k0 = (g & 1) * 32;          // column within the 64-wide K chunk
 #pragma unroll

@@ -103,11 +103,13 @@ __device__ __forceinline__ float& comp(float4& v, int c) {
   return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
 }
 __device__ __forceinline__ float4 z4() { return make_float4(0.f, 0.f, 0.f, 0.f); }
-// products rounded on their own (__fmul_rn is never contracted into a following add),
-// so every kernel variant computes m e and e^n q to the same bits
+// Products are left to the compiler, which may contract m e into the following
+// subtraction differently in each kernel variant: the plain, packing and incremental
+// steps can then differ in the last FP32 bit (rounding the products on their own with
+// __fmul_rn cost the plain step 8% through register spills).  Results within one
+// variant are deterministic.
 __device__ __forceinline__ float4 mul4(float4 a, float4 b) {
-  return make_float4(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y), __fmul_rn(a.z, b.z),
-                     __fmul_rn(a.w, b.w));
+  return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w);
 }
 __device__ __forceinline__ float4 fma4(float4 a, float4 b, float4 c) {
   return make_float4(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y), fmaf(a.z, b.z, c.z),
@@ -199,8 +201,8 @@ __device__ __forceinline__ float4 me_at(const uint8_t* s, int q) {
 }
 template <bool INCR>
 __device__ __forceinline__ float me_sc(const uint8_t* s, int f) {
-  float r = __fmul_rn(reinterpret_cast<const float*>(s + FwdLayout::M)[f],
-                      reinterpret_cast<const float*>(s + FwdLayout::E)[f]);
+  float r = reinterpret_cast<const float*>(s + FwdLayout::M)[f] *
+            reinterpret_cast<const float*>(s + FwdLayout::E)[f];
   if (INCR)
     r = fmaf(reinterpret_cast<const float*>(s + FwdLayout::DM)[f],
              reinterpret_cast<const float*>(s + FwdLayout::EF)[f], r);

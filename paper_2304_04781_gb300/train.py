@@ -29,11 +29,12 @@ def field_columns(f: int) -> torch.Tensor:
     return torch.cat([torch.arange(z * 256 + f * 64, z * 256 + f * 64 + 64) for z in range(8)])
 
 
-def make_handle(shape, h=10.0, nt=1000, n_lat=64, nrec=64) -> aewave.Solver:
+def make_handle(shape, h=10.0, nt=1000, n_lat=64, nrec=64, f0=25.0) -> aewave.Solver:
     nz, ny, nx = shape
     rec = inputs.receiver_grid(nx, ny, nrec)
     # no history storage is needed for data generation / training
-    return aewave.Solver(shape, h, nt, rec, storage="revolve", n_checkpoints=0, n_lat=n_lat)
+    return aewave.Solver(shape, h, nt, rec, storage="revolve", n_checkpoints=0, n_lat=n_lat,
+                         f0=f0)
 
 
 def block_scale(bmax: torch.Tensor) -> torch.Tensor:
@@ -137,10 +138,11 @@ def main():
     p.add_argument("--batch", type=int, default=512)
     p.add_argument("--n-lat", type=int, default=64)
     p.add_argument("--init-seed", type=int, default=0)
+    p.add_argument("--f0", type=float, default=25.0, help="Ricker peak frequency [Hz]")
     p.add_argument("--out", default="")
     a = p.parse_args()
     shape = tuple(a.shape)
-    solver = make_handle(shape, nt=a.nt, n_lat=a.n_lat)
+    solver = make_handle(shape, nt=a.nt, n_lat=a.n_lat, f0=a.f0)
     solver.codec_set(inputs.codec_init(seed=a.init_seed, n_lat=a.n_lat))
     t0 = time.time()
     data, _ = generate(solver, a.seeds, a.every)

@@ -82,11 +82,14 @@ def test_decode_matches_oracle(n_lat):
     assert np.all(e[0] == 0) and np.all(e[:, :, -1] == 0)
 
 
-def test_snapshots_bitwise_match_packing():
+def test_snapshots_match_packing():
     """Algorithm 1: every 10th state cut into blocks, each field of each block divided by
-    its power-of-two scale.  The BF16 codes are compared bit for bit with the same
-    packing of the same FP32 states done on the host (BF16 rounding, then the exact
-    power-of-two scaling)."""
+    its power-of-two scale, packed by the forward step that reads the state.  The
+    reference is the host packing (BF16 rounding, then the exact power-of-two scaling)
+    of the same states advanced by the plain step.  The two step variants may contract
+    m e differently, so their FP32 states can differ in the last bit: the block maxima
+    must agree to a few FP32 ulps and the BF16 codes bit for bit except, rarely, one
+    BF16 ulp where such a difference crosses a rounding boundary."""
     shape = (32, 32, 32)
     prob, c, _ = setup(shape, 41, 16)
     s = solver(prob, storage="ae")
@@ -104,10 +107,14 @@ def test_snapshots_bitwise_match_packing():
         Xb = torch.from_numpy(X.astype(np.float32)).to(torch.bfloat16).double().numpy()
         Y = C.normalise(Xb, sc)                      # exact: scales are powers of two
         want = torch.from_numpy(Y).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
-        np.testing.assert_array_equal(got[64 * q: 64 * (q + 1)], want)
+        g = got[64 * q: 64 * (q + 1)]
+        assert np.mean(g == want) > 0.999
+        gv = torch.from_numpy(g.view(np.int16)).view(torch.bfloat16).double().numpy()
+        wv = torch.from_numpy(want.view(np.int16)).view(torch.bfloat16).double().numpy()
+        assert np.all(np.abs(gv - wv) <= 2.0 ** -7 * np.maximum(np.abs(gv), np.abs(wv)))
         Xa = np.abs(X)
         bm_ref = np.stack([Xa[:, C.field_columns(f)].max(1) for f in range(4)], 1)
-        np.testing.assert_array_equal(host(bm[64 * q: 64 * (q + 1)]), bm_ref)
+        np.testing.assert_allclose(host(bm[64 * q: 64 * (q + 1)]), bm_ref, rtol=1e-6, atol=0)
 
 
 def test_training_steps_match_oracle():
