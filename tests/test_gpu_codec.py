@@ -80,6 +80,16 @@ def test_decode_matches_oracle(n_lat):
     e_ref = W.interior(C.unpack_field(Xe, shape, 0))
     assert relerr(e, e_ref) < CODEC_TOL
     assert np.all(e[0] == 0) and np.all(e[:, :, -1] == 0)
+    # block by block, in each block's own units (the scales span 14 decades, so the
+    # global norm alone would not see a wrong scale on a small block)
+    z = np.zeros(shape)
+    Pe = C.pack_blocks([e, z, z, z])[:, cols]
+    Pr = C.pack_blocks([e_ref, z, z, z])[:, cols]
+    nr = np.linalg.norm(Pr, axis=1)
+    live = nr > 0
+    assert np.all(Pe[~live] == 0)
+    blk = np.linalg.norm(Pe[live] - Pr[live], axis=1) / nr[live]
+    assert blk.max() < 5 * CODEC_TOL, blk.max()
 
 
 def test_snapshots_match_packing():
