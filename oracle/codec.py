@@ -211,8 +211,12 @@ def compressed_e_history(W: dict, states, emulate: bool = False):
 PARAMS = ("W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4")
 
 
-def loss_and_grad(W: dict, Y: np.ndarray, emulate: bool = False, act: str = "gelu"):
+def loss_and_grad(W: dict, Y: np.ndarray, emulate: bool = False, act: str = "gelu",
+                  weights: np.ndarray = None):
     """Mean squared error (1/(B*2048)) sum (decode(encode(Y)) - Y)^2 and its gradient.
+
+    weights [B][4] (optional): every squared error of vector v in field f's columns is
+    multiplied by weights[v][f] (None: all ones, the plain mean squared error of Table 2).
 
     The FP16 latent rounding (emulate) is treated as identity in the derivative
     (straight-through).  With emulate, GEMM operands are rounded as on the GPU:
@@ -237,9 +241,14 @@ def loss_and_grad(W: dict, Y: np.ndarray, emulate: bool = False, act: str = "gel
     h3 = rb(sig(a3))
     a4 = h3 @ rb(P["W4"]) + P["b4"]
     diff = a4 - Y
-    loss = float(np.mean(diff * diff))
+    if weights is None:
+        wfull = np.ones_like(diff)
+    else:
+        fcol = (np.arange(Y.shape[1]) >> 6) & 3          # field of each column
+        wfull = np.asarray(weights, np.float64)[:, fcol]
+    loss = float(np.mean(wfull * diff * diff))
     g = {}
-    d4 = 2.0 * diff / diff.size
+    d4 = 2.0 * wfull * diff / diff.size
     g["W4"] = h3.T @ rb(d4)
     g["b4"] = d4.sum(0)
     dh3 = rb(d4) @ rb(P["W4"]).T

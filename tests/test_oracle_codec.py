@@ -198,3 +198,29 @@ def test_training_schedule_follows_table_2():
     lr0, k = g["initial_learning_rate"], g["learning_rate_decay_every_epochs"]
     for ep in range(g["epochs"]):
         assert C.lr_schedule(ep, lr0) == pytest.approx(lr0 * g["learning_rate_decay_factor"] ** (ep // k), rel=0, abs=0)
+
+
+def test_weighted_training_gradient_matches_finite_differences():
+    """The per-vector, per-field weighted loss: its back-propagated gradient against
+    central differences, and all-one weights reproduce the plain mean squared error."""
+    rng = np.random.default_rng(14)
+    d = 2048
+    Wt = {"W1": rng.uniform(-.05, .05, (d, 8)), "b1": rng.uniform(-.1, .1, 8),
+          "W2": rng.uniform(-.5, .5, (8, 4)), "b2": rng.uniform(-.1, .1, 4),
+          "W3": rng.uniform(-.5, .5, (4, 8)), "b3": rng.uniform(-.1, .1, 8),
+          "W4": rng.uniform(-.5, .5, (8, d)), "b4": rng.uniform(-.1, .1, d)}
+    Y = rng.uniform(-1, 1, (6, d))
+    w = rng.uniform(0, 3, (6, 4))
+    w[:, 1:] *= rng.integers(0, 2, (6, 3))          # some fields switched off
+    L1, g1 = C.loss_and_grad(Wt, Y)
+    L0, g0 = C.loss_and_grad(Wt, Y, weights=np.ones((6, 4)))
+    assert L0 == L1 and all(np.array_equal(g0[k], g1[k]) for k in g1)
+    _, g = C.loss_and_grad(Wt, Y, weights=w)
+    eps = 1e-4   # the loss is O(1): a smaller step drowns the derivative in rounding
+    for name in C.PARAMS:
+        flat = Wt[name].ravel()
+        for idx in rng.choice(flat.size, size=min(4, flat.size), replace=False):
+            Wp = {k: v.copy() for k, v in Wt.items()}; Wm = {k: v.copy() for k, v in Wt.items()}
+            Wp[name].ravel()[idx] += eps; Wm[name].ravel()[idx] -= eps
+            fd = (C.loss_and_grad(Wp, Y, weights=w)[0] - C.loss_and_grad(Wm, Y, weights=w)[0]) / (2 * eps)
+            assert fd == pytest.approx(g[name].ravel()[idx], rel=1e-5, abs=1e-10), (name, idx)
