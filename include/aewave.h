@@ -235,12 +235,14 @@ int aew_snapshots(aew_handle* h, const float* c_dev, int every, uint16_t* out_de
                   void* stream);
 
 /* One training step of the codec on a minibatch: batch_dev = BF16 [batch][2048]
- * normalised vectors; loss = mean squared reconstruction error (Sec. 3.3); LAMB
- * update (You et al. 2019; beta1 0.9, beta2 0.999, eps 1e-6, no weight decay) of the
- * FP32 master weights with learning rate lr.  loss_host (may be NULL) receives the
- * loss before the update (this synchronises the stream). */
-int aew_codec_train_step(aew_handle* h, const uint16_t* batch_dev, int batch, float lr,
-                         float* loss_host, void* stream);
+ * normalised vectors (batch a multiple of 8); loss = mean squared reconstruction error
+ * (Sec. 3.3), each squared error of vector v in field f's columns multiplied by
+ * weights_dev[v][f] (device FP32 [batch][4]; NULL = all ones, the plain error of
+ * Table 2); LAMB update (You et al. 2019; beta1 0.9, beta2 0.999, eps 1e-6, no weight
+ * decay) of the FP32 master weights with learning rate lr.  loss_host (may be NULL)
+ * receives the loss before the update (this synchronises the stream). */
+int aew_codec_train_step(aew_handle* h, const uint16_t* batch_dev, const float* weights_dev,
+                         int batch, float lr, float* loss_host, void* stream);
 
 /* ---------------------------------------------------------------------------------
  * Checks and host logic

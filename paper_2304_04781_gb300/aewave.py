@@ -76,8 +76,8 @@ _SIGS = [
     ("aew_jvp", c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     ("aew_snapshots", c_int, [c_void_p, c_void_p, c_int, c_void_p, c_longlong, c_void_p,
                               POINTER(c_longlong), c_void_p]),
-    ("aew_codec_train_step", c_int, [c_void_p, c_void_p, c_int, c_float, POINTER(c_float),
-                                     c_void_p]),
+    ("aew_codec_train_step", c_int, [c_void_p, c_void_p, c_void_p, c_int, c_float,
+                                     POINTER(c_float), c_void_p]),
     ("aew_dot", c_int, [c_void_p, c_void_p, c_size_t, POINTER(c_double), c_void_p]),
     ("aew_dot_noalloc", c_int, [c_void_p, c_void_p, c_size_t, c_void_p, c_void_p]),
     ("aew_revolve_plan", c_int, [c_int, c_int, c_void_p, c_void_p, c_longlong,
@@ -337,10 +337,15 @@ class Solver:
             return out[: n.value], bm[: n.value]
         return out[: n.value]
 
-    def train_step(self, batch: torch.Tensor, lr: float, want_loss: bool = True) -> Optional[float]:
+    def train_step(self, batch: torch.Tensor, lr: float, want_loss: bool = True,
+                   weights: Optional[torch.Tensor] = None) -> Optional[float]:
+        """One LAMB step on a BF16 minibatch [B][2048]; weights (FP32 [B][4], optional)
+        weigh each vector's fields in the squared error."""
         loss = c_float(0.0)
-        self._check(lib().aew_codec_train_step(self._h, _ptr(batch), batch.shape[0], c_float(lr),
-                                               byref(loss) if want_loss else None, _stream()))
+        w = None if weights is None else weights.contiguous().float()
+        self._check(lib().aew_codec_train_step(self._h, _ptr(batch), _ptr(w), batch.shape[0],
+                                               c_float(lr), byref(loss) if want_loss else None,
+                                               _stream()))
         return loss.value if want_loss else None
 
 

@@ -1059,15 +1059,16 @@ int aew_snapshots(aew_handle* h, const float* c_dev, int every, uint16_t* out_de
   return AEW_OK;
 }
 
-int aew_codec_train_step(aew_handle* h, const uint16_t* batch_dev, int batch, float lr,
-                         float* loss_host, void* stream) {
+int aew_codec_train_step(aew_handle* h, const uint16_t* batch_dev, const float* weights_dev,
+                         int batch, float lr, float* loss_host, void* stream) {
   if (!h) return AEW_E_ARG;
   if (!batch_dev || batch < 1) return fail(h, AEW_E_ARG, "bad batch");
   if (!aew::codec_ready(h->codec)) return fail(h, AEW_E_NOCODEC, "codec weights not set");
   h->err.clear();
   cudaStream_t s = S(stream);
   float* loss_dev = h->scale_tmp;
-  cudaError_t e = aew::codec_train_step(h->codec, batch_dev, batch, lr, loss_dev, s, &h->err);
+  cudaError_t e =
+      aew::codec_train_step(h->codec, batch_dev, weights_dev, batch, lr, loss_dev, s, &h->err);
   if (e != cudaSuccess) return cuda_fail(h, e, "codec_train_step");
   if (loss_host && aew::codec_take_error(h->codec, s))
     return fail(h, AEW_E_TIMEOUT, "a codec kernel gave up waiting (bounded mbarrier wait)");

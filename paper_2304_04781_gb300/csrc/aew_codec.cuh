@@ -60,7 +60,8 @@ bool codec_take_error(Codec* c, cudaStream_t s);
 int* codec_err_flag(Codec* c);
 
 // One training step (MSE + LAMB); loss (device float) written if loss_dev != null.
-cudaError_t codec_train_step(Codec* c, const uint16_t* batch, int B, float lr, float* loss_dev,
-                             cudaStream_t s, std::string* err);
+// weights: FP32 [B][4] per vector and field (null: the plain mean squared error)
+cudaError_t codec_train_step(Codec* c, const uint16_t* batch, const float* weights, int B,
+                             float lr, float* loss_dev, cudaStream_t s, std::string* err);
 
 }  // namespace aew

@@ -149,6 +149,7 @@ struct EpFwdLatent {
 struct EpMse {
   const float* bias;
   const uint16_t* Y;
+  const float* w;    // [M][4] weight of each vector's fields (null: all ones)
   float* d4;
   uint16_t* d4b;
   uint16_t* d4T;
@@ -157,6 +158,8 @@ struct EpMse {
   long long M;
   __device__ __forceinline__ void operator()(long long row, int col, const float (&v)[32]) const {
     if (row >= M) return;
+    // the 32 columns lie in one field's 64-column group: one weight
+    const float wf = w ? __ldg(w + row * 4 + ((col >> 6) & 3)) : 1.f;
     double acc = 0.0;
     uint32_t pk[16];
     float dd[32];
@@ -164,8 +167,8 @@ struct EpMse {
     for (int j = 0; j < 32; ++j) {
       const float a = v[j] + __ldg(bias + col + j);
       const float diff = a - gemm::bf16_val(__ldg(Y + row * kNIn + col + j));
-      acc += (double)diff * (double)diff;
-      dd[j] = scale * diff;
+      acc += (double)wf * (double)diff * (double)diff;
+      dd[j] = scale * wf * diff;
       d4T[(size_t)(col + j) * M + row] = gemm::bf16_bits(dd[j]);
     }
 #pragma unroll
@@ -315,8 +318,8 @@ void train_state_free(void* t) {
 }
 size_t train_state_bytes(const void* t) { return t ? static_cast<const TrainState*>(t)->bytes : 0; }
 
-cudaError_t codec_train_step(Codec* c, const uint16_t* Y, int B, float lr, float* loss_dev,
-                             cudaStream_t st, std::string* err) {
+cudaError_t codec_train_step(Codec* c, const uint16_t* Y, const float* wts, int B, float lr,
+                             float* loss_dev, cudaStream_t st, std::string* err) {
   if (B % 8 != 0) {
     if (err) *err = "batch must be a multiple of 8";
     return cudaErrorInvalidValue;
@@ -355,7 +358,7 @@ cudaError_t codec_train_step(Codec* c, const uint16_t* Y, int B, float lr, float
   TCK((gemm::launch<256, false>(Bm, H, nl, ld(s->z16, nl, Bm, nl), ld(c->W3t, nl, H, nl),
                                 EpFwdGelu{c->w[5], s->a3, s->h3, s->h3T, H, Bm}, e, st)));
   TCK((gemm::launch<256, true>(Bm, I, H, ld(s->h3, H, Bm, H), ld(c->W4t, H, I, H),
-                               EpMse{c->w[7], Y, s->d4, s->d4b, s->d4T, s->red,
+                               EpMse{c->w[7], Y, wts, s->d4, s->d4b, s->d4T, s->red,
                                      2.0f / (float)((double)B * I), Bm},
                                e, st)));
   // ---- backward

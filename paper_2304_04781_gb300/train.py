@@ -66,10 +66,35 @@ def generate(solver: aewave.Solver, seeds, every: int = 10, h: float = 10.0,
     return data, bmax
 
 
+LOSSES = ("state", "strain", "strain-amplitude", "strain-energy")
+
+
+def loss_weights(bmax: torch.Tensor, kind: str):
+    """Per-vector, per-field weights [N][4] of the squared error (None for "state").
+
+    state             every field of every vector alike (Table 2's plain error)
+    strain            the strain outputs only (the adjoint decodes nothing else)
+    strain-amplitude  strain only, each vector weighted by its block scale s_e
+    strain-energy     strain only, weighted by s_e^2: the physical squared error
+    Amplitude weights are divided by their mean over the data set."""
+    if kind == "state":
+        return None
+    w = torch.zeros(bmax.shape, device=bmax.device, dtype=torch.float32)
+    if kind == "strain":
+        w[:, 0] = 1.0
+        return w
+    se = block_scale(bmax[:, 0].contiguous()).double()
+    a = se if kind == "strain-amplitude" else se * se
+    w[:, 0] = (a / a.mean()).float()
+    return w
+
+
 def train(solver: aewave.Solver, data: torch.Tensor, epochs: int = 20, batch: int = 512,
-          lr0: float = 1e-3, halve_every: int = 5, seed: int = 0, log_every: int = 0):
-    """Train the handle's codec in place on `data`; returns per-epoch mean losses (over
-    about 16 sampled minibatches per epoch, each loss taken before its update)."""
+          lr0: float = 1e-3, halve_every: int = 5, seed: int = 0, log_every: int = 0,
+          weights: torch.Tensor = None):
+    """Train the handle's codec in place on `data` (weights: optional [N][4], see
+    loss_weights); returns per-epoch mean losses (over about 16 sampled minibatches per
+    epoch, each loss taken before its update)."""
     g = torch.Generator(device="cuda")
     g.manual_seed(seed)
     N = data.shape[0]
@@ -84,7 +109,9 @@ def train(solver: aewave.Solver, data: torch.Tensor, epochs: int = 20, batch: in
         for i in range(nb):
             idx = perm[i * batch:(i + 1) * batch]
             mb = data.index_select(0, idx)
-            loss = solver.train_step(mb, lr, want_loss=(i % every == 0) or i == nb - 1)
+            wb = None if weights is None else weights.index_select(0, idx)
+            loss = solver.train_step(mb, lr, want_loss=(i % every == 0) or i == nb - 1,
+                                     weights=wb)
             if loss is not None:
                 tot += loss
                 cnt += 1
@@ -139,24 +166,27 @@ def main():
     p.add_argument("--n-lat", type=int, default=64)
     p.add_argument("--init-seed", type=int, default=0)
     p.add_argument("--f0", type=float, default=25.0, help="Ricker peak frequency [Hz]")
+    p.add_argument("--loss", default="state", choices=LOSSES,
+                   help="weights of the squared error (see loss_weights)")
     p.add_argument("--out", default="")
     a = p.parse_args()
     shape = tuple(a.shape)
     solver = make_handle(shape, nt=a.nt, n_lat=a.n_lat, f0=a.f0)
     solver.codec_set(inputs.codec_init(seed=a.init_seed, n_lat=a.n_lat))
     t0 = time.time()
-    data, _ = generate(solver, a.seeds, a.every)
+    data, bmax = generate(solver, a.seeds, a.every)
     nvec = data.shape[0]
+    weights = loss_weights(bmax, a.loss)
     torch.cuda.synchronize()
     t1 = time.time()
-    hist = train(solver, data, a.epochs, a.batch)
+    hist = train(solver, data, a.epochs, a.batch, weights=weights)
     torch.cuda.synchronize()
     t2 = time.time()
     del data
     hold, hsc = generate(solver, [a.holdout], a.every)
     err = decoded_error(solver, hold, hsc)
     W = solver.codec_get()
-    res = {"vectors": int(nvec), "gen_s": t1 - t0, "train_s": t2 - t1, "epochs": a.epochs,
+    res = {"vectors": int(nvec), "loss_kind": a.loss, "gen_s": t1 - t0, "train_s": t2 - t1, "epochs": a.epochs,
            "loss": hist, "holdout_decoded_error": err, "weights_finite": weights_finite(W)}
     print(json.dumps(res))
     if a.out:

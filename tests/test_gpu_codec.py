@@ -127,8 +127,10 @@ def test_snapshots_match_packing():
         np.testing.assert_allclose(host(bm[64 * q: 64 * (q + 1)]), bm_ref, rtol=1e-6, atol=0)
 
 
-def test_training_steps_match_oracle():
-    """10 LAMB steps on one batch of 256 snapshot-like vectors (lr 1e-3)."""
+@pytest.mark.parametrize("weighted", [False, True])
+def test_training_steps_match_oracle(weighted):
+    """10 LAMB steps on one batch of 256 snapshot-like vectors (lr 1e-3), with the plain
+    mean squared error and with per-vector, per-field weights (some fields off)."""
     shape = (32, 32, 32)
     prob, _, _ = setup(shape, 4, 16)
     s = solver(prob, storage="ae")
@@ -140,16 +142,24 @@ def test_training_steps_match_oracle():
     Y = np.concatenate([Y, rng.uniform(-1, 1, (128, 2048)) * 0.3])
     Y = C.round_bf16(Y)
     batch = torch.from_numpy(Y.astype(np.float32)).to(torch.bfloat16).cuda()
+    w = None
+    if weighted:
+        w = rng.uniform(0.1, 3.0, (256, 4)).astype(np.float32)
+        w[::2, 1:] = 0.0                          # strain only for every other vector
+    wdev = None if w is None else torch.from_numpy(w).cuda()
     Wo = {k: v.astype(np.float64) for k, v in Wt.items()}
     opt = C.Lamb(Wo)
     for it in range(10):
-        loss = s.train_step(batch, 1e-3)
-        L_ref, g = C.loss_and_grad(Wo, Y, emulate=True)
+        loss = s.train_step(batch, 1e-3, weights=wdev)
+        L_ref, g = C.loss_and_grad(Wo, Y, emulate=True, weights=w)
         Wo = opt.step(Wo, g, 1e-3)
         assert abs(loss - L_ref) <= 1e-3 * L_ref, (it, loss, L_ref)
     Wg = s.codec_get()
+    # weights concentrate the gradient on fewer vectors, so less of the BF16 rounding of
+    # the back-propagated errors averages out in the bias sums
+    tol = 2e-3 if weighted else 1e-3
     for k in C.PARAMS:
-        assert relerr(Wg[k], Wo[k]) < 1e-3, k
+        assert relerr(Wg[k], Wo[k]) < tol, k
         moved = relerr(Wo[k], Wt[k])
         if np.linalg.norm(Wt[k]) > 0:
             assert moved > 1e-3, k   # the parameters did change
