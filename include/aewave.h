@@ -228,8 +228,10 @@ int aew_jvp(aew_handle* h, const float* dc_dev, float* dd_dev, void* stream);
  * out_dev: device BF16 (uint16 bit patterns) [max_vectors][2048], 16-byte aligned
  * (AEW_E_ARG otherwise); the forward step that reads a state packs it; *n_written receives
  * the number of vectors written (whole states only, at most max_vectors).
- * block_max_dev (may be NULL): device FP32 [max_vectors][4] receiving the block maxima
- * of each written vector.  The history storage of the handle is not touched. */
+ * block_max_dev (may be NULL): device FP32 [max_vectors][4], 16-byte aligned
+ * (AEW_E_ARG otherwise), receiving the block maxima of each written vector (the forward
+ * step that writes a state stores them).  The history storage of the handle is not
+ * touched. */
 int aew_snapshots(aew_handle* h, const float* c_dev, int every, uint16_t* out_dev,
                   long long max_vectors, float* block_max_dev, long long* n_written,
                   void* stream);

@@ -57,7 +57,7 @@ struct aew_handle {
   double* part = nullptr;
   aew::FieldCheck* chk = nullptr;
   float* scale_tmp = nullptr;
-  unsigned* bm_tmp = nullptr;    // block maxima of a standalone encode / a snapshot
+  unsigned* bm_tmp = nullptr;    // block maxima of a standalone encode / a snapshot (2 slices)
   uint16_t* raw_tmp = nullptr;   // raw BF16 block vectors of a snapshot
   // AE mode: side stream running the codec GEMMs concurrently with the stencil steps,
   // double-buffered packed inputs and decoded strains, and the events ordering them
@@ -123,15 +123,18 @@ size_t nblocks_of(const aew_handle* h) {
 // ---------------------------------------------------------------------------------
 // Single steps
 // ---------------------------------------------------------------------------------
-// xpack / bmax: pack the input state n into normalised BF16 block vectors and store
-// its block maxima (AE forward and Algorithm 1 snapshots)
+// xpack / bmax_in: pack the input state n into normalised BF16 block vectors, by the
+// block maxima that the step producing state n stored in bmax_in; bmax_out: store the
+// block maxima of the output state n + 1 (AE forward and Algorithm 1 snapshots)
 int fwd_step(aew_handle* h, int n, float* const in[4], float* const out[4], const float* wav,
-             float* d_row, cudaStream_t s, uint16_t* xpack = nullptr, unsigned* bmax = nullptr) {
+             float* d_row, cudaStream_t s, uint16_t* xpack = nullptr,
+             const unsigned* bmax_in = nullptr, unsigned* bmax_out = nullptr) {
   aew::FwdStep a{};
   if (xpack) {
     a.xpack = xpack;
-    a.bmax = bmax;
+    a.bmax_in = bmax_in;
   }
+  a.bmax_out = bmax_out;
   a.m = h->m;
   a.e = in[0];
   a.vx = in[1];
@@ -482,8 +485,12 @@ int gradient_ae(aew_handle* h, const float* d_obs, const float* wav, cudaStream_
   int cur = 0;
   for (int n = 0; n < nt; ++n) {
     if (n >= 3) AEW_CK(cudaStreamWaitEvent(s, h->ev_b[n & 1], 0));
+    // step n packs state n by the maxima step n - 1 stored, and stores those of state
+    // n + 1 (states 1 .. nt - 1 are encoded)
+    const size_t nb4 = nblocks_of(h) * 4;
     rc = fwd_step(h, n, h->st[cur], h->st[cur ^ 1], wav, drow(h, h->d, n + 1), s,
-                  n >= 1 ? h->xpk[n & 1] : nullptr, h->bmx + (size_t)n * nblocks_of(h) * 4);
+                  n >= 1 ? h->xpk[n & 1] : nullptr, h->bmx + n * nb4,
+                  n + 1 < nt ? h->bmx + (n + 1) * nb4 : nullptr);
     if (rc) return rc;
     cur ^= 1;
     if (n >= 1) {
@@ -947,7 +954,7 @@ int aew_codec_encode(aew_handle* h, const float* const fields_dev[4], uint16_t* 
   h->err.clear();
   cudaStream_t s = S(stream);
   const size_t nb = nblocks_of(h);
-  if (!h->bm_tmp && !dalloc(h, &h->bm_tmp, nb * 4)) return fail(h, AEW_E_NOMEM, "workspace");
+  if (!h->bm_tmp && !dalloc(h, &h->bm_tmp, 2 * nb * 4)) return fail(h, AEW_E_NOMEM, "workspace");
   int* ovf = reinterpret_cast<int*>(h->scale_tmp + 4);
   AEW_CK(cudaMemsetAsync(ovf, 0, sizeof(int), s));
   const float* f[4] = {fields_dev[0], fields_dev[1], fields_dev[2], fields_dev[3]};
@@ -1026,6 +1033,8 @@ int aew_snapshots(aew_handle* h, const float* c_dev, int every, uint16_t* out_de
     return fail(h, AEW_E_ARG, "bad argument");
   if (reinterpret_cast<uintptr_t>(out_dev) & 15)
     return fail(h, AEW_E_ARG, "out_dev must be 16-byte aligned");
+  if (reinterpret_cast<uintptr_t>(block_max_dev) & 15)
+    return fail(h, AEW_E_ARG, "block_max_dev must be 16-byte aligned");
   if (h->cfg.nx % 8 || h->cfg.ny % 8 || h->cfg.nz % 8)
     return fail(h, AEW_E_CONFIG, "snapshots need nx, ny, nz multiples of 8");
   h->err.clear();
@@ -1034,25 +1043,36 @@ int aew_snapshots(aew_handle* h, const float* c_dev, int every, uint16_t* out_de
   if (rc) return rc;
   h->have_grad = false;
   const size_t nb = nblocks_of(h);
-  if (!block_max_dev && !h->bm_tmp && !dalloc(h, &h->bm_tmp, nb * 4))
+  // without block_max_dev the maxima go to two alternating scratch slices (a step reads
+  // one state's and writes the next one's)
+  if (!block_max_dev && !h->bm_tmp && !dalloc(h, &h->bm_tmp, 2 * nb * 4))
     return fail(h, AEW_E_NOMEM, "workspace");
   if ((rc = zero_state(h, h->st[0], s))) return rc;
   int cur = 0;
   long long written = 0;
+  const int nt = h->cfg.nt;
   // state n (1 <= n < nt, n % every == 0) is packed by the forward step that reads it:
-  // step n, or one extra step past the end for the state nt - 1
-  for (int n = 0; n < h->cfg.nt; ++n) {
-    const bool pack = n >= 1 && n % every == 0 && written + (long long)nb <= max_vectors;
-    if (n + 1 == h->cfg.nt && !pack) break;
+  // step n, or one extra step past the end for the state nt - 1; its maxima come from
+  // step n - 1, which wrote the state
+  auto packs = [&](int n, long long w) {
+    return n >= 1 && n < nt && n % every == 0 && w + (long long)nb <= max_vectors;
+  };
+  auto bm_at = [&](long long w) {
+    return block_max_dev ? reinterpret_cast<unsigned*>(block_max_dev) + (size_t)w * 4
+                         : h->bm_tmp + ((size_t)(w / (long long)nb) & 1) * nb * 4;
+  };
+  for (int n = 0; n < nt; ++n) {
+    const bool pack = packs(n, written);
+    if (n + 1 == nt && !pack) break;
+    const long long wnext = written + (pack ? (long long)nb : 0);
     uint16_t* xp = pack ? out_dev + (size_t)written * aew::kNIn : nullptr;
-    unsigned* bm = pack ? (block_max_dev ? reinterpret_cast<unsigned*>(block_max_dev) +
-                                               (size_t)written * 4
-                                         : h->bm_tmp)
-                        : nullptr;
-    if ((rc = fwd_step(h, n, h->st[cur], h->st[cur ^ 1], h->wav.data(), nullptr, s, xp, bm)))
+    const unsigned* bin = pack ? bm_at(written) : nullptr;
+    unsigned* bout = packs(n + 1, wnext) ? bm_at(wnext) : nullptr;
+    if ((rc = fwd_step(h, n, h->st[cur], h->st[cur ^ 1], h->wav.data(), nullptr, s, xp, bin,
+                       bout)))
       return rc;
     cur ^= 1;
-    if (pack) written += (long long)nb;
+    written = wnext;
   }
   AEW_CK(cudaStreamSynchronize(s));
   *n_written = written;

@@ -39,10 +39,14 @@ struct FwdStep {
   float* d_out;        // receiver record row [nrec][3] (or null)
   // Optional packing of the INPUT state n into normalised BF16 block vectors
   // [nblocks][2048] (order z*256 + f*64 + y*8 + x; every field of every block divided by
-  // its power-of-two scale) and the per-block, per-field maxima of |f| (float bits,
-  // bmax[nblocks][4]).  Needs nx, ny, nz multiples of 8.
+  // its power-of-two scale), with the per-block, per-field maxima of |f| of that state
+  // (float bits, bmax_in[nblocks][4]) as the step that produced it stored them.
   uint16_t* xpack;
-  unsigned int* bmax;
+  const unsigned int* bmax_in;
+  // Optional: the per-block, per-field maxima of |f| of the OUTPUT state n + 1 (float
+  // bits, bmax_out[nblocks][4], every entry written).  Must not alias bmax_in.
+  unsigned int* bmax_out;
+  // Both options need nx, ny, nz multiples of 8.
   int* err;            // sticky device error flag (set on a timed-out wait)
 };
 

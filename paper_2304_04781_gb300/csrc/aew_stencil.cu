@@ -51,11 +51,12 @@ constexpr uint64_t kWaitNs = 200000000ull;
 constexpr int kMaxStages = 4;
 // PACK: one plane of the CTA's 16 blocks, 4 fields x 8 rows x 8 BF16 each (a 512-byte
 // row per block, rows 528 bytes apart so that the 16 lane pairs of a warp, one per
-// block, write distinct banks); then the layer's block maxima per row [TY][16][4] and
-// inverse scales [16][4]
+// block, write distinct banks), double-buffered.  MAXO: the block maxima of the output
+// per warp row, [TY][16][4] floats.
 constexpr int kPackRow = 512 + 16;
 constexpr int kPackTile = (kTXW / 8) * kPackRow;
-constexpr int kPackExtra = 2 * kPackTile + (TY * 16 * 4 + 16 * 4) * 4;
+constexpr int kPackExtra = 2 * kPackTile;
+constexpr int kMaxoExtra = TY * 16 * 4 * 4;
 
 // bytes one box delivers (the mbarrier transaction count) ...
 constexpr int kTxXY = kWE * (TY + 2) * 4;   // x halo both sides, y halo both sides
@@ -209,7 +210,11 @@ __device__ __forceinline__ float me_sc(const uint8_t* s, int f) {
   return r;
 }
 
-template <bool INCR, bool PACK>
+// PACK: the input state's block vectors, normalised by the maxima in a.bmax_in (known
+// before the step: the step that wrote the state stored them), go out in one pass.
+// MAXO: the maxima of the output state, reduced inside the CTA (which owns whole
+// blocks: 128 x 8 nodes per plane, chunks of whole 8-plane layers) and stored whole.
+template <bool INCR, bool PACK, bool MAXO>
 __global__ void __launch_bounds__(NTHR, (INCR || PACK) ? 2 : 3)
     fwd_tma_kernel(const __grid_constant__ FwdMaps mp, const FwdStep a, int S) {
   extern __shared__ uint8_t smem_raw[];
@@ -268,11 +273,29 @@ __global__ void __launch_bounds__(NTHR, (INCR || PACK) ? 2 : 3)
     }
   }
 
-  float pm[4] = {0.f, 0.f, 0.f, 0.f};
   const int NBx = nx >> 3, NBy = ny >> 3;
-  uint8_t* pk = r.base + (size_t)S * r.stage_bytes;   // PACK: two staging tiles
+  uint8_t* pk = r.base + (size_t)S * r.stage_bytes;              // PACK: staging tiles
+  float* red = reinterpret_cast<float*>(pk + (PACK ? kPackExtra : 0));   // MAXO
+  float pm[4] = {0.f, 0.f, 0.f, 0.f};   // MAXO: this thread's output maxima
+  // PACK: inverse scales of this lane's block in the current layer, and the maxima of
+  // the next layer, loaded one layer ahead (lane / 2 is the block: 8 nodes = 2 lanes)
+  float isc[4] = {0.f, 0.f, 0.f, 0.f};
+  uint4 mnext = make_uint4(0u, 0u, 0u, 0u);
+  const unsigned* bml = nullptr;
+  if (PACK) {
+    bml = a.bmax_in + (((size_t)(y0 >> 3) * NBx + (i0 >> 3)) << 2);
+    if (act) mnext = __ldg(reinterpret_cast<const uint4*>(bml + (size_t)(kbeg >> 3) * NBy * NBx * 4));
+  }
   int k = kbeg;
   for (; k < kend && !failed; ++k) {
+    if (PACK && (k & 7) == 0) {
+      isc[0] = gemm::block_inv_scale(__uint_as_float(mnext.x));
+      isc[1] = gemm::block_inv_scale(__uint_as_float(mnext.y));
+      isc[2] = gemm::block_inv_scale(__uint_as_float(mnext.z));
+      isc[3] = gemm::block_inv_scale(__uint_as_float(mnext.w));
+      if (act && k + 8 < kend)
+        mnext = __ldg(reinterpret_cast<const uint4*>(bml + (size_t)((k >> 3) + 1) * NBy * NBx * 4));
+    }
     if (!r.wait(k) || !r.wait(k + 1)) failed = true;
     const uint8_t* sc = r.at(k);
     const uint8_t* sn = r.at(k + 1);
@@ -288,17 +311,17 @@ __global__ void __launch_bounds__(NTHR, (INCR || PACK) ? 2 : 3)
     const float4 vy_m = reinterpret_cast<const float4*>(sc + FwdLayout::VY)[qY - kW4];
     const float4 vz_c = reinterpret_cast<const float4*>(sc + FwdLayout::VZ)[qO];
 
-    if (PACK) {   // BF16 block vectors of the input state and block maxima
+    if (PACK) {   // normalised BF16 block vectors of the input state
       if (act) {
-        // this plane's piece of block (lane / 2): [field][y][x] in the staging tile
+        // this plane's piece of block (lane / 2): [field][y][x] in the staging tile.
+        // x / s is exact in FP32 (s a power of two), so one rounding to BF16.
         uint8_t* dst = pk + (k & 1) * kPackTile + (lane >> 1) * kPackRow + ty * 16 + (lane & 1) * 8;
         const float4 fv[4] = {e_c, vx_c, vy_c, vz_c};
 #pragma unroll
-        for (int f = 0; f < 4; ++f) {
+        for (int f = 0; f < 4; ++f)
           *reinterpret_cast<uint2*>(dst + f * 128) =
-              make_uint2(pack2bf(fv[f].x, fv[f].y), pack2bf(fv[f].z, fv[f].w));
-          pm[f] = fmaxf(pm[f], hmax4(fv[f]));
-        }
+              make_uint2(pack2bf(fv[f].x * isc[f], fv[f].y * isc[f]),
+                         pack2bf(fv[f].z * isc[f], fv[f].w * isc[f]));
       }
     }
 
@@ -361,11 +384,37 @@ __global__ void __launch_bounds__(NTHR, (INCR || PACK) ? 2 : 3)
       }
     }
     vzl = vz1;
+    if (MAXO) {
+      if (act) {
+        pm[0] = fmaxf(pm[0], hmax4(e1));
+        pm[1] = fmaxf(pm[1], hmax4(vx1));
+        pm[2] = fmaxf(pm[2], hmax4(vy1));
+        pm[3] = fmaxf(pm[3], hmax4(vz1));
+      }
+      if ((k & 7) == 7) {   // layer complete: this row's maxima of its 16 blocks
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          const float v = fmaxf(pm[f], __shfl_xor_sync(0xffffffffu, pm[f], 1));
+          if ((lane & 1) == 0) red[(ty * 16 + (lane >> 1)) * 4 + f] = v;
+          pm[f] = 0.f;
+        }
+      }
+    }
     // every thread is done with plane k: refill its stage
     failed = __syncthreads_or(failed);
     if (tid == 0 && !failed)
       for (; next <= pn && next <= k + S; ++next)
         fwd_issue<INCR>(mp, r, next, kbeg, kend, nz, x0, y0);
+    if (MAXO && (k & 7) == 7 && !failed && tid < 64) {
+      // the rows' tables are visible after the barrier; they are rewritten eight
+      // planes (and barriers) later
+      const int j = tid >> 2, f = tid & 3;
+      float mx = 0.f;
+#pragma unroll
+      for (int w = 0; w < TY; ++w) mx = fmaxf(mx, red[(w * 16 + j) * 4 + f]);
+      const size_t blk0 = ((size_t)(k >> 3) * NBy + (y0 >> 3)) * NBx + (x0 >> 3);
+      if ((x0 >> 3) + j < NBx) a.bmax_out[(blk0 + j) * 4 + f] = __float_as_uint(mx);
+    }
     if (PACK && !failed) {
       // plane k of the CTA's 16 blocks: one coalesced 512-byte row per block (the tile
       // is rewritten two planes later, after the next barrier)
@@ -376,54 +425,6 @@ __global__ void __launch_bounds__(NTHR, (INCR || PACK) ? 2 : 3)
           const size_t blk = ((size_t)(k >> 3) * NBy + (y0 >> 3)) * NBx + bx;
           uint8_t* dst = reinterpret_cast<uint8_t*>(a.xpack) + blk * 4096 + (k & 7) * 512;
           reinterpret_cast<uint4*>(dst)[lane] = reinterpret_cast<const uint4*>(src + j * kPackRow)[lane];
-        }
-      }
-      if ((k & 7) == 7) {
-        // Layer complete: the CTA holds its 16 blocks whole (8 rows, 8 planes).  Their
-        // maxima per field: lane pairs by shuffle, the 8 rows through shared memory.
-        float* red = reinterpret_cast<float*>(pk + 2 * kPackTile);   // [TY][16][4]
-        float* isc = red + TY * 16 * 4;                              // [16][4]
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-          const float v = fmaxf(pm[f], __shfl_xor_sync(0xffffffffu, pm[f], 1));
-          if ((lane & 1) == 0) red[(ty * 16 + (lane >> 1)) * 4 + f] = v;
-          pm[f] = 0.f;
-        }
-        __syncthreads();
-        const size_t blk0 = ((size_t)(k >> 3) * NBy + (y0 >> 3)) * NBx + (x0 >> 3);
-        if (tid < 64) {
-          const int j = tid >> 2, f = tid & 3;
-          float mx = 0.f;
-#pragma unroll
-          for (int w = 0; w < TY; ++w) mx = fmaxf(mx, red[(w * 16 + j) * 4 + f]);
-          if ((x0 >> 3) + j < NBx) a.bmax[(blk0 + j) * 4 + f] = __float_as_uint(mx);
-          isc[j * 4 + f] = gemm::block_inv_scale(mx);
-        }
-        __syncthreads();   // the table, and every thread's raw rows of the layer, are visible
-        // normalise the layer's block vectors in place, 16 bytes per thread and block
-        // (exact: every scale is a power of two); the rows are still in L2.  Eight
-        // blocks' loads are in flight at a time.
-        const int f = (tid >> 3) & 3;   // element tid * 8 lies in field (k >> 6) & 3
-        const int nbl = min(kTXW / 8, NBx - (x0 >> 3));
-        uint4* p0 = reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(a.xpack) + blk0 * 4096) + tid;
-#pragma unroll
-        for (int j0 = 0; j0 < kTXW / 8; j0 += 8) {
-          uint4 v[8];
-#pragma unroll
-          for (int j = 0; j < 8; ++j)
-            if (j0 + j < nbl) v[j] = __ldcg(p0 + (size_t)(j0 + j) * 256);
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            if (j0 + j < nbl) {
-              const float sc = isc[(j0 + j) * 4 + f];
-              uint32_t w[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
-#pragma unroll
-              for (int q = 0; q < 4; ++q)
-                w[q] = pack2bf(__uint_as_float(w[q] << 16) * sc,
-                               __uint_as_float(w[q] & 0xffff0000u) * sc);
-              p0[(size_t)(j0 + j) * 256] = make_uint4(w[0], w[1], w[2], w[3]);
-            }
-          }
         }
       }
     }
@@ -702,20 +703,21 @@ dim3 grid_of(int nx, int ny, int nz, int kc) {
   return dim3((nx + kTXW - 1) / kTXW, (ny + TY - 1) / TY, (nz + kc - 1) / kc);
 }
 
-template <bool INCR, bool PACK>
+template <bool INCR, bool PACK, bool MAXO>
 cudaError_t launch_fwd(const FwdMaps& mp, const FwdStep& a, cudaStream_t s) {
   const int S = stages_for(false);
-  const int extra = (PACK ? kPackExtra : 0) + 128;
+  const int extra = (PACK ? kPackExtra : 0) + (MAXO ? kMaxoExtra : 0) + 128;
   const size_t smem = (size_t)S * FwdLayout::bytes(INCR) + extra;
   static bool attr = false;   // per instantiation
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(fwd_tma_kernel<INCR, PACK>,
+    cudaError_t e = cudaFuncSetAttribute(fwd_tma_kernel<INCR, PACK, MAXO>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(kMaxStages * FwdLayout::bytes(INCR) + extra));
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  fwd_tma_kernel<INCR, PACK><<<grid_of(a.nx, a.ny, a.nz, a.kc), dim3(32, TY), smem, s>>>(mp, a, S);
+  fwd_tma_kernel<INCR, PACK, MAXO>
+      <<<grid_of(a.nx, a.ny, a.nz, a.kc), dim3(32, TY), smem, s>>>(mp, a, S);
   return cudaGetLastError();
 }
 
@@ -735,15 +737,12 @@ int default_kc(int nx, int ny, int nz, bool adjoint) {
   return kc < 1 ? 1 : kc;
 }
 
-// z planes per CTA of the packing step: whole 8-plane layers.  Two layers per CTA let it
-// normalise the first while the second one's planes are already in flight (measured at
-// 256^3: 16 planes 1.3% faster than 8 per AE gradient step, 24 and 32 slower).
-static int pack_kc(int kc) {
+// z planes per CTA of the packing step (whole 8-plane layers; default 16)
+static int pack_kc() {
   static const int v = [] {
     const char* env = getenv("AEW_STENCIL_KC_PACK");   // tuning override
     return env ? atoi(env) : 16;
   }();
-  (void)kc;
   return v > 0 ? v : 16;
 }
 
@@ -761,15 +760,18 @@ cudaError_t launch_fwd_step(const FwdStep& a, bool incremental, cudaStream_t s) 
     ok = field_map(&mp.dm, a.dm, nx, ny, nz, kWE, TY + 2) &&
          field_map(&mp.ef, a.ef, nx, ny, nz, kWE, TY + 2);
   if (!ok) return cudaErrorInvalidValue;
-  if (incremental) return launch_fwd<true, false>(mp, a, s);
-  if (a.xpack) {
-    // packing normalises whole 8-plane block layers inside one CTA
+  if (incremental) return launch_fwd<true, false, false>(mp, a, s);
+  if (a.xpack || a.bmax_out) {
+    // block maxima and packing work on whole 8 x 8 x 8 blocks inside one CTA
     if (nx % 8 || ny % 8 || nz % 8) return cudaErrorInvalidValue;
+    if (a.xpack && !a.bmax_in) return cudaErrorInvalidValue;
     FwdStep b = a;
-    b.kc = (pack_kc(a.kc) + 7) / 8 * 8;
-    return launch_fwd<false, true>(mp, b, s);
+    b.kc = ((a.xpack ? pack_kc() : a.kc) + 7) / 8 * 8;
+    if (!a.xpack) return launch_fwd<false, false, true>(mp, b, s);
+    if (!a.bmax_out) return launch_fwd<false, true, false>(mp, b, s);
+    return launch_fwd<false, true, true>(mp, b, s);
   }
-  return launch_fwd<false, false>(mp, a, s);
+  return launch_fwd<false, false, false>(mp, a, s);
 }
 
 cudaError_t launch_wait_probe(int* err, unsigned long long wait_ns, cudaStream_t s) {
