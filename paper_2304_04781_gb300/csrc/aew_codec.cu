@@ -121,36 +121,66 @@ struct EpLatent {
 
 // strain part of the decoder output, scattered to the grid:
 // column n = z*64 + y*8 + x of block row -> node (8bz+z, 8by+y, 8bx+x);
-// e = (acc + b4[z*256 + y*8 + x]) * s_b (power-of-two block scale), 0 on boundary nodes
+// e = (acc + b4[z*256 + y*8 + x]) * s_b (power-of-two block scale), 0 on boundary nodes.
+// The row's block coordinates and scale are found once per row (Row), then each
+// 32-column group is stored through it.
 struct EpDecGrid {
   const float* b4;
   const unsigned* bmax;   // [nblocks][4] maxima of |f| (float bits); field 0 = strain
   float* e;
   int nx, ny, nz, NBx, NBy;
-  long long M;
-  __device__ __forceinline__ void operator()(long long row, int col, const float (&v)[32]) const {
-    if (row >= M) return;
-    const float s = gemm::block_scale(__uint_as_float(__ldg(bmax + row * 4)));
-    const long long bx = row % NBx, t = row / NBx;
-    const long long by = t % NBy, bz = t / NBy;
+  long long M;            // number of blocks (< 2^31, checked by the launcher)
+  struct Row {
+    float* base;          // node (8bz, 8by, 8bx)
+    float s;
+    int kz0, jy0;         // 8bz, 8by
+    bool live, xlo, xhi;  // row in range; block on the x = 0 / x = nx - 1 face
+  };
+  __device__ __forceinline__ Row row(long long rw) const {
+    Row c;
+    c.live = rw < M;
+    if (!c.live) return c;
+    const int r = (int)rw;
+    const int bx = r % NBx, t = r / NBx;
+    const int by = t % NBy, bz = t / NBy;
+    c.s = gemm::block_scale(__uint_as_float(__ldg(bmax + (size_t)r * 4)));
+    c.kz0 = 8 * bz;
+    c.jy0 = 8 * by;
+    c.base = e + ((size_t)c.kz0 * ny + c.jy0) * nx + 8 * bx;
+    c.xlo = bx == 0;
+    c.xhi = bx == NBx - 1;
+    return c;
+  }
+  // b4 of a 32-column group (4 rows of 8 nodes): b4[z*256 + y*8 + x], 32 consecutive
+  // floats from z*256 + y0*8
+  struct Bias {
+    float4 q[8];
+  };
+  __device__ __forceinline__ void bias(int col, Bias& bb) const {
+    const float4* bq = reinterpret_cast<const float4*>(b4 + (col >> 6) * 256 + (col & 63));
+#pragma unroll
+    for (int j = 0; j < 8; ++j) bb.q[j] = __ldg(bq + j);
+  }
+  __device__ __forceinline__ void operator()(const Row& c, int col, const Bias& bb,
+                                             const float (&v)[32]) const {
+    if (!c.live) return;
     const int z = col >> 6, y0 = (col & 63) >> 3;
-    const int kz = (int)(8 * bz) + z;
+    const int kz = c.kz0 + z;
     const bool zb = (kz == 0 || kz == nz - 1);
+    float* pz = c.base + (size_t)z * ny * nx;
 #pragma unroll
     for (int yy = 0; yy < 4; ++yy) {
-      const int jy = (int)(8 * by) + y0 + yy;
+      const int jy = c.jy0 + y0 + yy;
       const bool yb = zb || jy == 0 || jy == ny - 1;
-      const float4* bq = reinterpret_cast<const float4*>(b4 + z * 256 + (y0 + yy) * 8);
-      const float4 blo = __ldg(bq), bhi = __ldg(bq + 1);
+      const float4 blo = bb.q[2 * yy], bhi = bb.q[2 * yy + 1];
       const float bv[8] = {blo.x, blo.y, blo.z, blo.w, bhi.x, bhi.y, bhi.z, bhi.w};
       float o[8];
 #pragma unroll
       for (int x = 0; x < 8; ++x) {
-        const int ix = (int)(8 * bx) + x;
-        const float val = (v[yy * 8 + x] + bv[x]) * s;
-        o[x] = (yb || ix == 0 || ix == nx - 1) ? 0.f : val;
+        const float val = (v[yy * 8 + x] + bv[x]) * c.s;
+        o[x] = (yb || (x == 0 && c.xlo) || (x == 7 && c.xhi)) ? 0.f : val;
       }
-      float4* dst = reinterpret_cast<float4*>(e + ((size_t)kz * ny + jy) * nx + 8 * bx);
+      float4* dst = reinterpret_cast<float4*>(pz + (size_t)(y0 + yy) * nx);
       dst[0] = make_float4(o[0], o[1], o[2], o[3]);
       dst[1] = make_float4(o[4], o[5], o[6], o[7]);
     }
@@ -461,6 +491,7 @@ static cudaError_t decode_e_fused(Codec* c, const uint16_t* lat, long long nb, c
       gemm::make_tmap(&tw3, c->W3t, true, kNHid, nl, nl, 256, true) != CUDA_SUCCESS ||
       gemm::make_tmap(&tw4, c->W4e, false, 512, kNHid, kNHid, 256, true) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
+  if (nb >= (1LL << 31)) return cudaErrorInvalidValue;
   const long long tiles = (nb + dec::kRows - 1) / dec::kRows;
   const int g = ctas_of(c, ctas);
   const int cap = (g > 0 && g < sms) ? g : sms;

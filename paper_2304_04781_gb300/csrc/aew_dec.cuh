@@ -202,13 +202,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       // E1: H = bf16(gelu(acc + b3)), 32 columns at a time
 #pragma unroll 1
       for (int g = cg; g < kHid / 32; g += kEpi / 4) {
+        // the bias loads go out ahead of the TMEM load, so that the two latencies overlap
+        float4 bq[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) bq[j] = __ldg(reinterpret_cast<const float4*>(b3 + g * 32) + j);
         float v[32];
         tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(g * 32), v);
-        const float4* bq = reinterpret_cast<const float4*>(b3 + g * 32);
         uint32_t pk[16];
 #pragma unroll
         for (int j = 0; j < 32; j += 4) {
-          const float4 b = __ldg(bq + j / 4);
+          const float4 b = bq[j / 4];
           pk[j / 2] = gemm::pack_bf16(gemm::gelu_f(v[j] + b.x), gemm::gelu_f(v[j + 1] + b.y));
           pk[j / 2 + 1] = gemm::pack_bf16(gemm::gelu_f(v[j + 2] + b.z), gemm::gelu_f(v[j + 3] + b.w));
         }
@@ -223,7 +226,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc::fence_before_sync();
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(hready)) : "memory");
       // E2: output halves through the grid epilogue
-      const long long row = (long long)t * kRows + r;
+      const typename EP::Row rc = ep.row((long long)t * kRows + r);
       for (int h = 0; h < 2 && ok; ++h) {
         ok = tc::mbar_wait(tc::smem_u32(&acc2[h]), ph, W);
         tc::fence_after_sync();
@@ -233,9 +236,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
 #pragma unroll 1
         for (int g = cg; g < 8; g += kEpi / 4) {
+          typename EP::Bias bb;
+          ep.bias(h * 256 + g * 32, bb);   // ahead of the TMEM load, as in E1
           float v[32];
           tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * 256 + g * 32), v);
-          ep(row, h * 256 + g * 32, v);
+          ep(rc, h * 256 + g * 32, bb, v);
         }
       }
       if (!ok) {
