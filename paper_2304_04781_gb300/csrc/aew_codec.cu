@@ -25,6 +25,7 @@
 #include "aew_codec.cuh"
 #include "aew_codec_state.cuh"
 #include "aew_dec.cuh"
+#include "aew_gemm2.cuh"
 #include "aew_gemm.cuh"
 
 namespace aew {
@@ -363,6 +364,7 @@ Codec* codec_new(int n_lat) {
   cudaMemset(c->err, 0, sizeof(int));
   if (const char* env = getenv("AEW_GEMM_CTAS")) c->max_ctas = atoi(env);   // tuning override
   if (const char* env = getenv("AEW_GEMM_STAGES")) c->max_stages = atoi(env);   // tuning override
+  if (const char* env = getenv("AEW_GEMM_PAIR")) c->pair_gemm = atoi(env) != 0;  // tuning override
   c->bytes += ((size_t)2 * kNIn * kNHid + 2 * nl * kNHid) * 2;
   return c;
 }
@@ -450,8 +452,10 @@ cudaError_t codec_encode_vectors(Codec* c, const uint16_t* vec, long long n, uin
   if (!ensure_H(c, (size_t)n)) return cudaErrorMemoryAllocation;
   const int g = ctas_of(c, ctas);
   EpBiasGeluH ep{c->w[1], c->H, n};
-  cudaError_t e = gemm::launch<256, true>(n, kNHid, kNIn, gemm::Mat{vec, n, kNIn},
-                                          gemm::Mat{c->W1t, kNHid, kNIn}, ep, c->err, s, g, c->max_stages);
+  const gemm::Mat a1{vec, n, kNIn}, b1{c->W1t, kNHid, kNIn};
+  cudaError_t e = c->pair_gemm && c->max_stages == 0
+                      ? gemm2::launch<true>(n, kNHid, kNIn, a1, b1, ep, c->err, s, g)
+                      : gemm::launch<256, true>(n, kNHid, kNIn, a1, b1, ep, c->err, s, g, c->max_stages);
   if (e != cudaSuccess) return e;
   const int nl = c->n_lat;
   EpLatent e2{c->w[3], lat, nl, n, overflow};

@@ -29,6 +29,7 @@ struct Codec {
   int* err = nullptr;
   int max_ctas = 0;          // CTA cap of the codec GEMMs (0: one per SM)
   int max_stages = 0;        // stage cap of the codec GEMMs (0: as many as fit)
+  bool pair_gemm = true;     // encoder layer 1 on SM pairs (cta_group::2)
   size_t bytes = 0;
   // training state (allocated by the training unit)
   void* train = nullptr;
