@@ -34,7 +34,7 @@ METRIC = "gradients/hour at 256^3x2000 steps: AE vs checkpointing; stencil HBM G
 # DRAM bytes (read + write) of one forward-step launch at 256^3, from an ncu capture of
 # the current kernel (dram__bytes_read.sum + dram__bytes_write.sum); None once the
 # kernel changes until it is captured again
-FWD_TRAFFIC_256 = 586.34e6
+FWD_TRAFFIC_256 = 586.19e6
 SHAPE = (256, 256, 256)
 NT = 2000
 NREC = 128

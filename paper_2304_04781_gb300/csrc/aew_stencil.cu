@@ -116,6 +116,17 @@ __device__ __forceinline__ float4 fma4(float4 a, float4 b, float4 c) {
   return make_float4(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y), fmaf(a.z, b.z, c.z),
                      fmaf(a.w, b.w, c.w));
 }
+// 1 / s for a block maximum m >= 0 given as float bits, equal to
+// gemm::block_inv_scale(m) (s = 2^max(e, -100), m = f 2^e with f in [0.5, 1); 0 for
+// m = 0) but from the exponent field: e = biased - 126 for normal m, and subnormal m
+// falls under the clamp.  Maxima of 2^126 and above take the library path.
+__device__ __forceinline__ float inv_scale_bits(uint32_t mb) {
+  const int eb = (int)(mb >> 23);
+  if (mb == 0u) return 0.f;
+  if (eb >= 253) return gemm::block_inv_scale(__uint_as_float(mb));
+  const int e = max(eb - 126, gemm::kExpMin);
+  return __uint_as_float((uint32_t)(127 - e) << 23);
+}
 __device__ __forceinline__ float hmax4(float4 a) {
   return fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w)));
 }
@@ -286,13 +297,21 @@ __global__ void __launch_bounds__(NTHR, (INCR || PACK) ? 2 : 3)
     bml = a.bmax_in + (((size_t)(y0 >> 3) * NBx + (i0 >> 3)) << 2);
     if (act) mnext = __ldg(reinterpret_cast<const uint4*>(bml + (size_t)(kbeg >> 3) * NBy * NBx * 4));
   }
+  // PACK copy-out: this warp writes the plane rows of blocks ty and ty + 8 of the CTA,
+  // 16 bytes per lane; their addresses at plane kbeg, advanced by whole layers below
+  const bool cp0 = (x0 >> 3) + ty < NBx, cp1 = (x0 >> 3) + ty + 8 < NBx;
+  const size_t layer_bytes = (size_t)NBy * NBx * 4096;
+  uint8_t* cpd = nullptr;
+  if (PACK)
+    cpd = reinterpret_cast<uint8_t*>(a.xpack) +
+          (((size_t)(kbeg >> 3) * NBy + (y0 >> 3)) * NBx + (x0 >> 3) + ty) * 4096 + lane * 16;
   int k = kbeg;
   for (; k < kend && !failed; ++k) {
     if (PACK && (k & 7) == 0) {
-      isc[0] = gemm::block_inv_scale(__uint_as_float(mnext.x));
-      isc[1] = gemm::block_inv_scale(__uint_as_float(mnext.y));
-      isc[2] = gemm::block_inv_scale(__uint_as_float(mnext.z));
-      isc[3] = gemm::block_inv_scale(__uint_as_float(mnext.w));
+      isc[0] = inv_scale_bits(mnext.x);
+      isc[1] = inv_scale_bits(mnext.y);
+      isc[2] = inv_scale_bits(mnext.z);
+      isc[3] = inv_scale_bits(mnext.w);
       if (act && k + 8 < kend)
         mnext = __ldg(reinterpret_cast<const uint4*>(bml + (size_t)((k >> 3) + 1) * NBy * NBx * 4));
     }
@@ -418,15 +437,13 @@ __global__ void __launch_bounds__(NTHR, (INCR || PACK) ? 2 : 3)
     if (PACK && !failed) {
       // plane k of the CTA's 16 blocks: one coalesced 512-byte row per block (the tile
       // is rewritten two planes later, after the next barrier)
-      const uint8_t* src = pk + (k & 1) * kPackTile;
-      for (int j = ty; j < kTXW / 8; j += TY) {
-        const int bx = (x0 >> 3) + j;
-        if (bx < NBx) {
-          const size_t blk = ((size_t)(k >> 3) * NBy + (y0 >> 3)) * NBx + bx;
-          uint8_t* dst = reinterpret_cast<uint8_t*>(a.xpack) + blk * 4096 + (k & 7) * 512;
-          reinterpret_cast<uint4*>(dst)[lane] = reinterpret_cast<const uint4*>(src + j * kPackRow)[lane];
-        }
-      }
+      static_assert(kTXW / 8 == 2 * TY, "two block rows per warp");
+      const uint8_t* src = pk + (k & 1) * kPackTile + ty * kPackRow + lane * 16;
+      uint8_t* dst = cpd + (size_t)((k - kbeg) >> 3) * layer_bytes + (k & 7) * 512;
+      if (cp0) *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(src);
+      if (cp1)
+        *reinterpret_cast<uint4*>(dst + 8 * 4096) =
+            *reinterpret_cast<const uint4*>(src + 8 * kPackRow);
     }
   }
   if (failed) {
