@@ -54,6 +54,30 @@ def test_encode_matches_oracle(shape, n_lat):
     np.testing.assert_array_equal(host(bm), bm_ref)
 
 
+@pytest.mark.parametrize("n", [64, 210, 700])
+def test_pair_gemm_matches_single_sm_gemm(n, monkeypatch):
+    """The encoder's wide layer on SM pairs (cta_group::2: M = 256 MMAs reading both
+    CTAs' shared memories, rows 128-255 accumulated in the odd CTA's TMEM) gives the
+    latents of the single-SM kernel bit for bit: every output is the same K-ordered FP32
+    sum of the same BF16 products.  Ragged row counts leave the odd CTA's rows wholly
+    (64) or partly (210, 700) past the end."""
+    prob, _, _ = setup((32, 32, 32), 4, 16)
+    Wt = inputs.codec_init(seed=3, n_lat=64)
+    rng = np.random.default_rng(n)
+    vec = torch.from_numpy(rng.uniform(-1.0, 1.0, (n, 2048)).astype(np.float32))
+    vec = vec.to(torch.bfloat16).cuda()
+    lat = {}
+    for pair in ("1", "0"):
+        monkeypatch.setenv("AEW_GEMM_PAIR", pair)   # read when the handle's codec is made
+        s = solver(prob, storage="ae")
+        s.codec_set(Wt)
+        lat[pair] = s.codec_encode_vectors(vec).view(torch.int16).cpu()
+        s.close()
+    assert torch.equal(lat["1"], lat["0"])
+    Z = C.encode(Wt, vec.double().cpu().numpy(), emulate=True)
+    assert relerr(lat["1"].view(torch.float16).double().numpy(), Z) < CODEC_TOL
+
+
 @pytest.mark.parametrize("n_lat", [64, 32])
 def test_decode_matches_oracle(n_lat):
     shape = (40, 48, 56)
@@ -95,8 +119,9 @@ def test_decode_matches_oracle(n_lat):
 def test_snapshots_match_packing():
     """Algorithm 1: every 10th state cut into blocks, each field of each block divided by
     its power-of-two scale, packed by the forward step that reads the state.  The
-    reference is the host packing (BF16 rounding, then the exact power-of-two scaling)
-    of the same states advanced by the plain step.  The two step variants may contract
+    reference is the host packing (BF16 rounding, then the exact power-of-two scaling,
+    which gives the same codes as the kernel's scaling then rounding) of the same states
+    advanced by the plain step.  The two step variants may contract
     m e differently, so their FP32 states can differ in the last bit: the block maxima
     must agree to a few FP32 ulps and the BF16 codes bit for bit except, rarely, one
     BF16 ulp where such a difference crosses a rounding boundary."""
