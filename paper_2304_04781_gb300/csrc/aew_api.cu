@@ -56,9 +56,8 @@ struct aew_handle {
   int* rec_map = nullptr;
   double* part = nullptr;
   aew::FieldCheck* chk = nullptr;
-  float* scale_tmp = nullptr;
+  float* scratch8 = nullptr;     // 8 words: training loss, encode overflow flag
   unsigned* bm_tmp = nullptr;    // block maxima of a standalone encode / a snapshot (2 slices)
-  uint16_t* raw_tmp = nullptr;   // raw BF16 block vectors of a snapshot
   // AE mode: side stream running the codec GEMMs concurrently with the stencil steps,
   // double-buffered packed inputs and decoded strains, and the events ordering them
   cudaStream_t side = nullptr;
@@ -578,7 +577,7 @@ int aew_create(const aew_config* cfg, aew_handle** out) {
             dalloc(h, &h->dd, (nt + 1) * h->nrow) &&
             dalloc(h, &h->rec_map, (size_t)c.nx * c.ny) &&
             dalloc(h, &h->part, aew::kRedBlocks + 8) && dalloc(h, &h->chk, 1) &&
-            dalloc(h, &h->scale_tmp, 8);
+            dalloc(h, &h->scratch8, 8);
   for (int b = 0; ok && b < 2; ++b)
     for (int i = 0; ok && i < 4; ++i) ok = dalloc(h, &h->st[b][i], C) && dalloc(h, &h->ad[b][i], C);
   if (ok && c.storage == AEW_FULL) ok = dalloc(h, &h->estore, nt * C);
@@ -955,7 +954,7 @@ int aew_codec_encode(aew_handle* h, const float* const fields_dev[4], uint16_t* 
   cudaStream_t s = S(stream);
   const size_t nb = nblocks_of(h);
   if (!h->bm_tmp && !dalloc(h, &h->bm_tmp, 2 * nb * 4)) return fail(h, AEW_E_NOMEM, "workspace");
-  int* ovf = reinterpret_cast<int*>(h->scale_tmp + 4);
+  int* ovf = reinterpret_cast<int*>(h->scratch8 + 4);
   AEW_CK(cudaMemsetAsync(ovf, 0, sizeof(int), s));
   const float* f[4] = {fields_dev[0], fields_dev[1], fields_dev[2], fields_dev[3]};
   cudaError_t e = aew::codec_encode_grid(h->codec, f, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->bm_tmp,
@@ -1012,7 +1011,7 @@ int aew_codec_encode_vectors(aew_handle* h, const uint16_t* vectors_dev, long lo
   h->err.clear();
   if (n == 0) return AEW_OK;
   cudaStream_t s = S(stream);
-  int* ovf = reinterpret_cast<int*>(h->scale_tmp + 4);
+  int* ovf = reinterpret_cast<int*>(h->scratch8 + 4);
   AEW_CK(cudaMemsetAsync(ovf, 0, sizeof(int), s));
   cudaError_t e = aew::codec_encode_vectors(h->codec, vectors_dev, n, latents_dev, ovf, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "codec_encode_vectors");
@@ -1086,7 +1085,7 @@ int aew_codec_train_step(aew_handle* h, const uint16_t* batch_dev, const float* 
   if (!aew::codec_ready(h->codec)) return fail(h, AEW_E_NOCODEC, "codec weights not set");
   h->err.clear();
   cudaStream_t s = S(stream);
-  float* loss_dev = h->scale_tmp;
+  float* loss_dev = h->scratch8;
   cudaError_t e =
       aew::codec_train_step(h->codec, batch_dev, weights_dev, batch, lr, loss_dev, s, &h->err);
   if (e != cudaSuccess) return cuda_fail(h, e, "codec_train_step");
