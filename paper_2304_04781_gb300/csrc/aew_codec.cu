@@ -477,18 +477,10 @@ static cudaError_t decode_hidden(Codec* c, const uint16_t* lat, long long nb, cu
 // strain decode in one kernel: layer 1, GELU, layer 2 with H kept in shared memory
 static cudaError_t decode_e_fused(Codec* c, const uint16_t* lat, long long nb, const EpDecGrid& ep,
                                   cudaStream_t s, int ctas) {
-  static bool attr = false;
-  static int sms = 0;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(dec::dec2_kernel<EpDecGrid>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)dec::kSmem);
-    if (e != cudaSuccess) return e;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    attr = true;
-  }
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      dec::dec2_kernel<EpDecGrid>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dec::kSmem);
+  if (attr != cudaSuccess) return attr;
+  const int sms = gemm::sm_count();
   const int nl = c->n_lat;
   CUtensorMap tz, tw3, tw4;
   if (gemm::make_tmap(&tz, lat, true, nb, nl, nl, dec::kRows, true) != CUDA_SUCCESS ||

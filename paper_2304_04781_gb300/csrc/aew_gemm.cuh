@@ -283,6 +283,17 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == kMmaWarp) tc::tmem_dealloc(tmem, TCOLS);
 }
 
+// SM count of the current device, found once (thread-safe static initialisation).
+inline int sm_count() {
+  static const int n = [] {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+  }();
+  return n;
+}
+
 // Operand description for launch(): row-major [rows][K] 16-bit matrix, row stride ld.
 struct Mat {
   const void* p;
@@ -305,18 +316,12 @@ cudaError_t launch(long long M, int N, int K, const Mat& A, const Mat& B, const 
   if (max_ns > 0 && ns > max_ns) ns = max_ns;   // fewer stages: room for a co-resident CTA
   if (ns < 2) ns = 2;
   const size_t smem = smem_bytes_for(stage_bytes<BN>(), ns);
-  static int sms = 0;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(
-        kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-        (int)smem_bytes_for(stage_bytes<BN>(), max_stages<BN>()));
-    if (e != cudaSuccess) return e;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    configured = true;
-  }
+  // once per instantiation (thread-safe static initialisation)
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      (int)smem_bytes_for(stage_bytes<BN>(), max_stages<BN>()));
+  if (attr != cudaSuccess) return attr;
+  const int sms = sm_count();
   CUtensorMap ta, tb;
   if (make_tmap(&ta, A.p, !BF16, A.rows, K, A.ld, kBM, SW) != CUDA_SUCCESS ||
       make_tmap(&tb, B.p, !BF16, B.rows, K, B.ld, BN, SW) != CUDA_SUCCESS)

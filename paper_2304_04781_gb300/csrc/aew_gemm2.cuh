@@ -270,16 +270,11 @@ template <bool BF16, class EP>
 cudaError_t launch(long long M, int N, int K, const gemm::Mat& A, const gemm::Mat& B, const EP& ep,
                    int* err, cudaStream_t s, int max_ctas = 0) {
   auto kern = gemm2_kernel<BF16, EP>;
-  static int sms = 0;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
-    if (e != cudaSuccess) return e;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    configured = true;
-  }
+  // once per instantiation (thread-safe static initialisation)
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+  if (attr != cudaSuccess) return attr;
+  const int sms = gemm::sm_count();
   CUtensorMap ta, tb;
   if (gemm::make_tmap(&ta, A.p, !BF16, A.rows, K, A.ld, kBM, true) != CUDA_SUCCESS ||
       gemm::make_tmap(&tb, B.p, !BF16, B.rows, K, B.ld, kBN / 2, true) != CUDA_SUCCESS)

@@ -725,14 +725,11 @@ cudaError_t launch_fwd(const FwdMaps& mp, const FwdStep& a, cudaStream_t s) {
   const int S = stages_for(false);
   const int extra = (PACK ? kPackExtra : 0) + (MAXO ? kMaxoExtra : 0) + 128;
   const size_t smem = (size_t)S * FwdLayout::bytes(INCR) + extra;
-  static bool attr = false;   // per instantiation
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(fwd_tma_kernel<INCR, PACK, MAXO>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(kMaxStages * FwdLayout::bytes(INCR) + extra));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  // once per instantiation (thread-safe static initialisation)
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      fwd_tma_kernel<INCR, PACK, MAXO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      (int)(kMaxStages * FwdLayout::bytes(INCR) + extra));
+  if (attr != cudaSuccess) return attr;
   fwd_tma_kernel<INCR, PACK, MAXO>
       <<<grid_of(a.nx, a.ny, a.nz, a.kc), dim3(32, TY), smem, s>>>(mp, a, S);
   return cudaGetLastError();
@@ -812,13 +809,10 @@ cudaError_t launch_adj_step(const AdjStep& a, cudaStream_t s) {
   if (!ok) return cudaErrorInvalidValue;
   const int S = stages_for(true);
   const size_t smem = (size_t)S * AdjLayout::BYTES + 128;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(adj_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(kMaxStages * AdjLayout::BYTES + 128));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      adj_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      (int)(kMaxStages * AdjLayout::BYTES + 128));
+  if (attr != cudaSuccess) return attr;
   adj_tma_kernel<<<grid_of(nx, ny, nz, a.kc), dim3(32, TY), smem, s>>>(mp, a, S);
   return cudaGetLastError();
 }
