@@ -196,6 +196,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
           tma_load_2d_pair(sa + kABytes, &tb, c * kBK, n0, fb);
         }
       }
+      // the MMAs' last arrivals on this CTA's stage barriers land before the teardown
+      for (int j = it > kStages ? it - kStages : 0; j < it && ok; ++j)
+        ok = wait_cl(tc::smem_u32(&empty[j % kStages]), (j / kStages) & 1, W);
+      if (!ok) atomicExch(err, 1);
     }
     __syncwarp();
   } else if (warp == kMmaWarp) {
