@@ -132,6 +132,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         if (!ok) break;
       }
+      // the MMAs' last arrivals (ring stages, H released) land before the teardown
+      bool ok = !*reinterpret_cast<volatile int*>(abort_flag);
+      for (int j = it > kRing ? it - kRing : 0; j < it && ok; ++j)
+        ok = tc::mbar_wait(tc::smem_u32(&empty[j % kRing]), (j / kRing) & 1, W);
+      if (ok && tl > 0) ok = tc::mbar_wait(tc::smem_u32(hfree), (tl - 1) & 1, W);
+      if (!ok) atomicExch(err, 1);
     }
     __syncwarp();
   } else if (warp == kMmaWarp) {

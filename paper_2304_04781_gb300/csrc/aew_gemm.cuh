@@ -183,13 +183,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       // ----------------------------------------------------------- TMA producer
       int it = 0;
-      for (int t = blockIdx.x; t < T; t += gridDim.x) {
+      bool ok = true;
+      for (int t = blockIdx.x; t < T && ok; t += gridDim.x) {
         const int m0 = (t / tn) * kBM, n0 = (t % tn) * BN;
         for (int c = 0; c < nK; ++c, ++it) {
           const int s = it % ns;
           if (it >= ns && !tc::mbar_wait(tc::smem_u32(&empty[s]), ((it / ns) - 1) & 1, kWaitNs)) {
             atomicExch(abort_flag, 1);
-            t = T;
+            ok = false;
             break;
           }
           const uint32_t fb = tc::smem_u32(&full[s]);
@@ -207,6 +208,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       }
+      // the MMAs' last arrivals on the stage barriers land before the teardown
+      for (int j = it > ns ? it - ns : 0; j < it && ok; ++j)
+        ok = tc::mbar_wait(tc::smem_u32(&empty[j % ns]), (j / ns) & 1, kWaitNs);
+      if (!ok) atomicExch(err, 1);
     }
     __syncwarp();
   } else if (warp == kMmaWarp) {
