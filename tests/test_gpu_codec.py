@@ -152,6 +152,24 @@ def test_snapshots_match_packing():
         np.testing.assert_allclose(host(bm[64 * q: 64 * (q + 1)]), bm_ref, rtol=1e-6, atol=0)
 
 
+@pytest.mark.parametrize("every", [1, 3])
+def test_snapshots_without_caller_maxima_match_with_them(every):
+    """Without a block-maxima buffer the steps hand the maxima on through two alternating
+    scratch slices (a step reads one state's and writes the next one's); the packed
+    vectors must equal those written when the caller keeps the maxima, including every
+    = 1, where each step both reads and writes maxima, and a budget that stops mid-run."""
+    shape = (24, 32, 40)
+    prob, c, _ = setup(shape, 14, 16)
+    s = solver(prob, storage="ae")
+    nb = s.nblocks
+    budget = 5 * nb if every == 1 else 4 * nb
+    with_bm, bm = s.snapshots(cuda(c), every=every, max_vectors=budget, with_scales=True)
+    without = s.snapshots(cuda(c), every=every, max_vectors=budget)
+    assert with_bm.shape == without.shape and with_bm.shape[0] in (budget, 4 * nb)
+    assert torch.equal(with_bm.view(torch.int16), without.view(torch.int16))
+    assert torch.all(bm >= 0) and torch.any(bm > 0)
+
+
 @pytest.mark.parametrize("weighted", [False, True])
 def test_training_steps_match_oracle(weighted):
     """10 LAMB steps on one batch of 256 snapshot-like vectors (lr 1e-3), with the plain
