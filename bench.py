@@ -307,6 +307,7 @@ def run_ours(args):
     bytes_step = 36.0 * C
     stencil_gbs = bytes_step / step_s / 1e9
     peak, peak_kind = load_peaks()
+    latent_bytes = int(ae.stats()["latent_bytes"])
     del ae
     torch.cuda.empty_cache()
 
@@ -332,6 +333,43 @@ def run_ours(args):
     rev_hvp_ms = r0.elapsed_time(r1) / args.revolve_runs
     rev_hvp_fwd = rev.stats()["hvp_forward_steps"]
     del rev
+    torch.cuda.empty_cache()
+
+    def time_gradient(solver):
+        solver.gradient(c, d_obs, g)
+        torch.cuda.synchronize()
+        t0_, t1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0_.record(stream)
+        for _ in range(args.revolve_runs):
+            solver.gradient(c, d_obs, g)
+        t1_.record(stream)
+        torch.cuda.synchronize()
+        return t0_.elapsed_time(t1_) / args.revolve_runs
+
+    # ---- checkpointing with as many state slots as the latent store's bytes (4 FP32
+    # fields per slot), and full storage of e^n where it fits: references, not the headline
+    slots_eq = max(1, latent_bytes // (16 * C))
+    req = aewave.Solver(shape, H, nt, rec, storage="revolve", n_checkpoints=slots_eq)
+    req_ms = time_gradient(req)
+    req_fwd = req.stats()["forward_steps"]
+    del req
+    torch.cuda.empty_cache()
+    full = None
+    hist = nt * C * 4
+    if torch.cuda.mem_get_info()[0] > hist + 16 * C * 8:
+        try:
+            fs = aewave.Solver(shape, H, nt, rec, storage="full")
+        except aewave.AewError as err:
+            full = {"unavailable": str(err)}
+        else:
+            full_ms = time_gradient(fs)
+            full = {"ms_per_gradient": full_ms, "gradients_per_hour": 3600e3 / full_ms,
+                    "history_bytes": hist,
+                    "note": "e^n of every step kept in HBM (no recomputation, no compression)"}
+            del fs
+            torch.cuda.empty_cache()
+    else:
+        full = {"unavailable": f"e^n history of {hist / 1e9:.1f} GB does not fit beside the rest"}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -357,6 +395,10 @@ def run_ours(args):
             "revolve": {"gradients_per_hour": 3600e3 / rev_ms, "ms_per_gradient": rev_ms,
                         "forward_steps": rev_fwd, "slots": 20},
             "speedup_vs_revolve": rev_ms / ms_max,
+            "revolve_equal_memory": {"slots": slots_eq, "ms_per_gradient": req_ms,
+                                     "gradients_per_hour": 3600e3 / req_ms, "forward_steps": req_fwd,
+                                     "latent_bytes": latent_bytes},
+            "full_storage": full,
             "hvp": {"ae_ms": ae_hvp_ms, "revolve_ms": rev_hvp_ms, "speedup_vs_revolve": rev_hvp_ms / ae_hvp_ms,
                     "ae_hvps_per_hour": 3600e3 / ae_hvp_ms, "revolve_forward_steps": rev_hvp_fwd,
                     "note": "Gauss-Newton HVP reusing the gradient's latents (AE) vs recomputing "
