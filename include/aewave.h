@@ -254,6 +254,15 @@ int aew_codec_train_step(aew_handle* h, const uint16_t* batch_dev, const float* 
  * (for the adjoint-identity and finite-difference checks).  Synchronises `stream`. */
 int aew_dot(const float* a_dev, const float* b_dev, size_t n, double* out_host, void* stream);
 
+/* Test hook for the codec's activation (Sec. 3.3 layers; GELU, reading R5):
+ * y_dev[i] = GELU(x_dev[i]) = x Phi(x) as the encoder and decoder kernels evaluate it
+ * (Phi through Abramowitz & Stegun eq. 7.1.28, |error| <= 3e-7, within 1e-6 in FP32),
+ * dy_dev[i] = GELU'(x_dev[i]) = Phi(x) + x phi(x) as the training kernels evaluate it
+ * (erff).  Device FP32 arrays of n elements, caller-owned;
+ * asynchronous on `stream`.  AEW_E_ARG for n < 0 or NULL pointers with n > 0, AEW_E_CUDA
+ * if the launch fails. */
+int aew_test_gelu(const float* x_dev, float* y_dev, float* dy_dev, long long n, void* stream);
+
 /* aew_dot without any device allocation, for callers that cannot allocate device
  * memory (an application whose allocations all go through its own pool, or a hook that
  * must not change the device memory footprint).  No counterpart in the paper: it is a

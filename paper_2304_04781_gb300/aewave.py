@@ -80,6 +80,7 @@ _SIGS = [
                                      POINTER(c_float), c_void_p]),
     ("aew_dot", c_int, [c_void_p, c_void_p, c_size_t, POINTER(c_double), c_void_p]),
     ("aew_dot_noalloc", c_int, [c_void_p, c_void_p, c_size_t, c_void_p, c_void_p]),
+    ("aew_test_gelu", c_int, [c_void_p, c_void_p, c_void_p, c_longlong, c_void_p]),
     ("aew_revolve_plan", c_int, [c_int, c_int, c_void_p, c_void_p, c_longlong,
                                  POINTER(c_longlong), POINTER(c_longlong)]),
 ]
@@ -138,6 +139,18 @@ def dot(a: torch.Tensor, b: torch.Tensor) -> float:
     if rc != 0:
         raise AewError(rc, "aew_dot failed")
     return out.value
+
+
+def activation_probe(x: torch.Tensor):
+    """(GELU(x) as the encoder/decoder kernels compute it, GELU'(x) as the training
+    kernels compute it) for a CUDA FP32 tensor."""
+    assert x.dtype == torch.float32 and x.is_cuda
+    x = x.contiguous()
+    y, dy = torch.empty_like(x), torch.empty_like(x)
+    rc = lib().aew_test_gelu(_ptr(x), _ptr(y), _ptr(dy), x.numel(), _stream())
+    if rc != 0:
+        raise AewError(rc, "aew_test_gelu failed")
+    return y, dy
 
 
 def dot_noalloc(a: torch.Tensor, b: torch.Tensor, out: torch.Tensor) -> None:

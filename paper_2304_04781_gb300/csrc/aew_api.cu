@@ -886,6 +886,13 @@ int aew_hessvec(aew_handle* h, const float* dc_dev, float* hdc_dev, void* stream
   return AEW_OK;
 }
 
+int aew_test_gelu(const float* x_dev, float* y_dev, float* dy_dev, long long n, void* stream) {
+  if (n < 0 || (n > 0 && (!x_dev || !y_dev || !dy_dev))) return AEW_E_ARG;
+  return aew::launch_activation_probe(x_dev, y_dev, dy_dev, n, S(stream)) == cudaSuccess
+             ? AEW_OK
+             : AEW_E_CUDA;
+}
+
 int aew_dot(const float* a_dev, const float* b_dev, size_t n, double* out_host, void* stream) {
   if (!a_dev || !b_dev || !out_host) return AEW_E_ARG;
   cudaStream_t s = S(stream);

@@ -81,8 +81,8 @@ struct EpBiasGeluH {
 #pragma unroll
     for (int j = 0; j < 32; j += 4) {
       const float4 b = __ldg(bq + j / 4);
-      pk[j / 2] = gemm::pack_bf16(gemm::gelu_f(v[j] + b.x), gemm::gelu_f(v[j + 1] + b.y));
-      pk[j / 2 + 1] = gemm::pack_bf16(gemm::gelu_f(v[j + 2] + b.z), gemm::gelu_f(v[j + 3] + b.w));
+      pk[j / 2] = gemm::pack_bf16(gemm::gelu_fast(v[j] + b.x), gemm::gelu_fast(v[j + 1] + b.y));
+      pk[j / 2 + 1] = gemm::pack_bf16(gemm::gelu_fast(v[j + 2] + b.z), gemm::gelu_fast(v[j + 3] + b.w));
     }
     uint4* dst = reinterpret_cast<uint4*>(H + row * kNHid + col);
 #pragma unroll
@@ -336,6 +336,26 @@ CUresult make_tmap(CUtensorMap* map, const void* base, bool fp16, long long rows
 }
 
 }  // namespace gemm
+
+// the inference epilogues' GELU and the training kernels' GELU derivative, element by
+// element (test hook)
+__global__ void activation_probe_kernel(const float* __restrict__ x, float* __restrict__ y,
+                                        float* __restrict__ dy, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float v = x[i];
+    y[i] = gemm::gelu_fast(v);
+    dy[i] = gemm::gelu_prime_f(v);
+  }
+}
+cudaError_t launch_activation_probe(const float* x, float* y, float* dy, long long n,
+                                    cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const long long want = (n + 255) / 256;
+  const int grid = (int)(want < 152 * 8 ? want : 152 * 8);
+  activation_probe_kernel<<<grid, 256, 0, s>>>(x, y, dy, n);
+  return cudaGetLastError();
+}
 
 Codec* codec_new(int n_lat) {
   Codec* c = new Codec();

@@ -21,6 +21,10 @@ bool codec_ready(const Codec* c);
 
 // w[8] = W1, b1, W2, b2, W3, b3, W4, b4 (host FP32, row-major, layer y -> y W + b)
 cudaError_t codec_set_weights(Codec* c, const float* const w[8]);
+// y = GELU(x) as the inference epilogues evaluate it, dy = GELU'(x) as the training
+// kernels evaluate it (test hook)
+cudaError_t launch_activation_probe(const float* x, float* y, float* dy, long long n,
+                                    cudaStream_t s);
 cudaError_t codec_get_weights(const Codec* c, float* const w[8]);
 
 // Rebuild the tensor-core operand copies of the weights from the FP32 masters.

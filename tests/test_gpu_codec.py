@@ -54,6 +54,31 @@ def test_encode_matches_oracle(shape, n_lat):
     np.testing.assert_array_equal(host(bm), bm_ref)
 
 
+def test_activation_meets_its_error_bound():
+    """GELU as the encoder and decoder kernels evaluate it (Phi from Abramowitz & Stegun
+    eq. 7.1.28, |erf error| <= 3e-7, one approximate reciprocal) and the derivative the
+    training kernels use (erff), against the exact FP64 functions over the range the
+    hidden layers see and beyond.  In FP32 the 16th power multiplies the rounding of its
+    base by 16, so |dPhi| <= 1e-6 (about 1e-3 of the BF16 rounding the activations take
+    next) and |dGELU| <= 1e-6 |x| + one FP32 rounding of the product; both tails go to 0
+    and x, and 0 maps to 0."""
+    from scipy.special import erf
+    from paper_2304_04781_gb300 import aewave
+    x = np.concatenate([np.linspace(-12.0, 12.0, 480001), [0.0, -0.0, 1e-30, -1e-30, 40.0, -40.0,
+                                                          1e6, -1e6]]).astype(np.float32)
+    y, dy = aewave.activation_probe(torch.from_numpy(x).cuda())
+    y, dy = host(y), host(dy)
+    xd = x.astype(np.float64)
+    phi = 0.5 * (1.0 + erf(xd / np.sqrt(2.0)))
+    g = xd * phi
+    assert np.all(np.abs(y - g) <= 1e-6 * np.abs(xd) + 2.0 ** -23 * np.abs(g) + 1e-37)
+    gp = phi + xd * np.exp(-0.5 * xd * xd) / np.sqrt(2.0 * np.pi)
+    assert np.all(np.abs(dy - gp) <= 1e-6 + 2.0 ** -20 * np.abs(xd * (gp - phi)))
+    assert np.all(y[x == 0] == 0.0)
+    # x = 40, -40, 1e6, -1e6: the upper tail gives x itself, the lower tail 0
+    assert y[-4] == 40.0 and y[-3] == 0.0 and y[-2] == 1e6 and y[-1] == 0.0
+
+
 @pytest.mark.parametrize("n", [64, 210, 700])
 def test_pair_gemm_matches_single_sm_gemm(n, monkeypatch):
     """The encoder's wide layer on SM pairs (cta_group::2: M = 256 MMAs reading both
