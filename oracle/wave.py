@@ -29,7 +29,7 @@ The incremental forward / incremental adjoint problems of Sec. 4 give the
 Gauss-Newton Hessian-vector product H dc = J_F^T J_F dc.
 
 The autoencoder variant (Sec. 3) replaces the stored forward strain e^n in the
-adjoint and incremental problems by its decoded approximation; the drivers accept an
+adjoint and incremental problems by its decoded approximation; the solve functions accept an
 ``e_of`` callback that supplies e^n for step n, so the same code runs full storage
 and compressed storage.
 """

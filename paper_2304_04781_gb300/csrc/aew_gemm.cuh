@@ -60,7 +60,7 @@ inline size_t smem_bytes_for(int stage_b, int ns) { return (size_t)ns * stage_b 
 // (64 K x box_rows) with 128-byte swizzle, or (8 K x box_rows) unswizzled.
 CUresult make_tmap(CUtensorMap* map, const void* base, bool fp16, long long rows, int K,
                    long long ld, int box_rows, bool swizzle128);
-// the driver's cuTensorMapEncodeTiled (looked up once; null if unavailable)
+// cuTensorMapEncodeTiled of the CUDA driver API (looked up once; null if unavailable)
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
