@@ -32,3 +32,24 @@ def test_reference_arm_prints_the_contract_line():
     assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
     assert line["config"]["grid"] == [16, 16, 16] and line["config"]["nt"] == 8
+
+
+def test_clock_summary_reads_nvidia_smi_rows():
+    """The sampler's summary: median SM clock under load, the maximum clock, and every
+    throttle reason seen Active in any sample; malformed or unavailable rows are skipped
+    (nvidia-smi prints "[N/A]" or "Not Active" in these columns)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    s = bench.ClockSampler(0)
+    s.rows = [
+        ["0", "2070", "2070", "900.1", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"],
+        ["0", "2055", "2070", "1390.0", "0x4", "Not Active", "Not Active", "Not Active", "Active"],
+        ["0", "[N/A]", "2070", "1390.0", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"],
+        ["0", "1980", "2070", "1400.2", "0x20", "Not Active", "Not Active", "Active", "Not Active"],
+        ["garbage"],
+    ]
+    out = s.summary()
+    assert out["samples"] == 3 and out["sm_mhz"] == 2055.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap", "sw_thermal_slowdown"]
+    s.rows = []
+    assert s.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
