@@ -101,6 +101,14 @@ def normalise(X: np.ndarray, s: np.ndarray) -> np.ndarray:
     return np.where(s > 0, X / np.where(s > 0, s, 1.0), 0.0)
 
 
+def encoder_inputs(X: np.ndarray, s: np.ndarray, emulate: bool = False) -> np.ndarray:
+    """The encoder's input vectors.  Exact mode: x / s_v.  Emulated mode: as on the GPU,
+    each state is stored in BF16 when it is written, before the window's scale is known,
+    and divided by the power of two afterwards (exact), i.e. bf16(x) / s_v; this equals
+    bf16(x / s_v) except for values below BF16's normal range (|x| < 2^-126)."""
+    return normalise(C.round_bf16(X) if emulate else X, s)
+
+
 def window_vectors(e_hist, shape, tb: int):
     """Raw vectors of window tb from the strain history e_hist[n], n = 0..nt-1."""
     nt = len(e_hist)
@@ -123,8 +131,7 @@ def roundtrip_window(W: dict, e_hist, shape, tb: int, emulate: bool = False) -> 
     there; the stored forward strain is 0 there too)."""
     X = window_vectors(e_hist, shape, tb)
     s = vector_scales(X)
-    Y = normalise(X, s)
-    Z = C.encode(W, Y, emulate)
+    Z = C.encode(W, encoder_inputs(X, s, emulate), emulate)
     Xh = C.decode(W, Z, emulate) * s[:, None]
     E = unpack(Xh, shape)
     return np.stack([interior(E[t]) for t in range(TSTEPS)])

@@ -67,6 +67,18 @@ def test_vector_scales_bracket_the_vector_max_by_brute_force():
     assert np.abs(Y).max() < 1.0 and not Y[7].any()
 
 
+def test_emulated_encoder_inputs_round_when_written_then_scale_exactly():
+    rng = np.random.default_rng(21)
+    X = rng.standard_normal((6, 2048)) * 10.0 ** rng.uniform(-20, 5, (6, 1))
+    X[5, :100] = 1e-40                      # below BF16's normal range
+    s = CT.vector_scales(X)
+    Y = CT.encoder_inputs(X, s, emulate=True)
+    np.testing.assert_array_equal(Y, C.round_bf16(X) / s[:, None])
+    # for normal values it is the same as normalising first and rounding once
+    np.testing.assert_array_equal(Y[:5], C.round_bf16(X[:5] / s[:5, None]))
+    np.testing.assert_array_equal(CT.encoder_inputs(X, s), X / s[:, None])
+
+
 def test_pca_codec_reproduces_data_in_a_k_dimensional_affine_subspace():
     rng = np.random.default_rng(2)
     k = 12
