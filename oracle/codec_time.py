@@ -138,15 +138,19 @@ def roundtrip_window(W: dict, e_hist, shape, tb: int, emulate: bool = False) -> 
 
 
 def compressed_e_history(W: dict, e_hist, emulate: bool = False):
-    """Decoded strain history e-hat^n, n = 0..nt-1 (window by window)."""
+    """Decoded strain history e-hat^n, n = 0..nt-1 (window by window).  The initial state
+    e^0 is the zero initial condition of Eq. (2): it is known exactly and is not taken
+    from the codec (window 0's scale is set by its later states, so decoding would turn
+    the exact zero into small nonzero values)."""
     nt = len(e_hist)
     shape = np.asarray(e_hist[0]).shape
     out = []
     for tb in range(n_windows(nt)):
         E = roundtrip_window(W, e_hist, shape, tb, emulate)
         for t in range(TSTEPS):
-            if TSTEPS * tb + t < nt:
-                out.append(E[t])
+            n = TSTEPS * tb + t
+            if n < nt:
+                out.append(np.zeros(shape) if n == 0 else E[t])
     return out
 
 

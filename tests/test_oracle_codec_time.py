@@ -155,6 +155,22 @@ def test_compressed_history_and_gradient_with_a_code_exact_on_its_data():
     assert np.sqrt(num / den) < 2e-2
 
 
+def test_compressed_history_keeps_the_exact_zero_initial_state():
+    """e^0 = 0 (Eq. (2)) is not decoded: with a code that is not exact, window 0 decodes
+    its slot 0 to nonzero values, but the history's first entry stays exactly 0."""
+    prob, c = _small_problem(nt=40)
+    _, states = W.forward_states(prob, c)
+    e_hist = [st[0] for st in states]
+    Y = []
+    for tb in range(3):      # later windows have nonzero first slots
+        X = CT.window_vectors(e_hist, prob.shape, tb)
+        Y.append(CT.normalise(X, CT.vector_scales(X)))
+    Wt = CT.pca_codec(np.concatenate(Y), 4)       # far from exact
+    assert np.abs(CT.roundtrip_window(Wt, e_hist, prob.shape, 0)[0]).max() > 0
+    eh = CT.compressed_e_history(Wt, e_hist)
+    assert not eh[0].any() and eh[1].any()
+
+
 def test_compressed_history_zeroes_boundary_nodes():
     shape = (8, 8, 8)
     rng = np.random.default_rng(6)
