@@ -1,12 +1,16 @@
 """Benchmark: autoencoder-compressed adjoint gradients per hour at 256^3 x 2000 steps
-(128 receivers, codec 2048 -> 512 -> 64, FP16 latents held in HBM), against binomial
-recompute-checkpointing on the same GPU, plus the forward stencil's HBM bandwidth.
+(128 receivers, FP16 latents held in HBM), against binomial recompute-checkpointing and
+full storage on the same GPU, with the accuracy of the compressed gradient and GN-HVP
+and the hot-path kernels' rooflines.
 
-One step = one gradient of the misfit (forward solve with per-step encoding into the
-latent store, residual and misfit, adjoint solve with per-step decoding and FP64
-gradient accumulation).  Inputs: synthetic Gaussian-random-field velocity model, data
-from a +5% bump model; the working set (~1 GB of fields per step) is far larger than
-L2, so no explicit flush is needed.
+One step = one gradient of the misfit (forward solve with the history compressed into
+the latent store, residual and misfit, adjoint solve decoding it, FP64 gradient
+accumulation).  The default codec compresses in time (Sec. 3.2): the strain of each
+2x8x8-node block over 16 steps, 2048 -> 1024 (GELU) -> 512 FP16 latents, 16.8 GB at
+256^3 x 2000 (--codec space: the 8x8x8-node, 4-field codec 2048 -> 512 -> 64).
+Inputs: synthetic Gaussian-random-field velocity model, data from a +5% bump model;
+the working set (~1 GB of fields per step) is far larger than L2, so no explicit flush
+is needed.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -52,8 +56,11 @@ def parse():
     p.add_argument("--shape", type=int, nargs=3, default=list(SHAPE))
     p.add_argument("--nt", type=int, default=NT)
     p.add_argument("--nrec", type=int, default=NREC)
-    p.add_argument("--n-lat", type=int, default=64)
+    p.add_argument("--codec", default="time", choices=["time", "space"])
+    p.add_argument("--n-lat", type=int, default=0, help="latent width (default 512 time, 64 space)")
     p.add_argument("--weights", default="")
+    p.add_argument("--no-accuracy", action="store_true",
+                   help="skip the accuracy block of the timed run (errors against full storage)")
     p.add_argument("--accuracy", action="store_true",
                    help="instead of timing: AE gradient / GN-HVP errors against full storage "
                         "(or checkpointing with --ref revolve), decoded-state error")
@@ -66,14 +73,28 @@ def parse():
     return p.parse_args()
 
 
-def workload(shape, nt, nrec=NREC, n_lat=64):
+def codec_desc(codec: str, n_lat: int):
+    if codec == "time":
+        return (f"compression in time: strain of 2x8x8-node blocks x 16 steps = 2048 -> "
+                f"{2 * n_lat} (GELU) -> {n_lat} FP16 latents", f"2048-{2 * n_lat}(GELU)-{n_lat}")
+    return (f"compression in space: 8^3-node blocks x 4 fields = 2048 -> 512 (GELU) -> {n_lat} "
+            f"FP16 latents", f"2048-512(GELU)-{n_lat}")
+
+
+def workload(shape, nt, nrec=NREC, n_lat=512, codec="time"):
+    desc, arch = codec_desc(codec, n_lat)
     return {
         "workload": f"{shape[2]}x{shape[1]}x{shape[0]} grid, {nt} steps, {nrec} receivers; "
-                    f"AE storage (8^3-node blocks x 4 fields = 2048 -> 512 -> {n_lat}, FP16 latents)",
-        "grid": list(shape), "nt": nt, "receivers": nrec, "codec": f"2048-512(GELU)-{n_lat}, bf16 x bf16 -> f32",
+                    f"AE storage ({desc})",
+        "grid": list(shape), "nt": nt, "receivers": nrec,
+        "codec": f"{arch}, bf16 x bf16 -> f32", "codec_kind": codec,
         "l2": "inputs larger than L2 (per-step working set ~1 GB)",
         "storage": "AE latents in HBM; baseline binomial checkpointing with 20 state slots",
     }
+
+
+def nlat_of(args):
+    return args.n_lat or (512 if args.codec == "time" else 64)
 
 
 # --------------------------------------------------------------------------- distributed
@@ -138,18 +159,20 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
+        """Median SM clock, the largest maximum clock reported, and the throttle reasons
+        seen Active; a row counts only if every column it is read for parses."""
+        sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in self.rows:
             try:
-                sm.append(float(r[1]))
-                mx = float(r[2])
-                for k, nm in enumerate(names):
-                    if r[5 + k].lower().startswith("active"):
-                        reasons.add(nm)
+                clk, cmax = float(r[1]), float(r[2])
+                act = [r[5 + k].lower().startswith("active") for k in range(len(names))]
             except Exception:
                 continue
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+            sm.append(clk)
+            mx.append(cmax)
+            reasons.update(nm for nm, a in zip(names, act) if a)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
@@ -208,12 +231,32 @@ def run_reference(args):
 
 # --------------------------------------------------------------------------- GPU arm
 def load_peaks():
+    """(HBM copy GB/s, BF16 TFLOP/s burst, sustained, kind) from MEASURED_PEAKS.json."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             p = json.load(f)
-        return float(p["hbm_gbs"]), "measured"
+        return (float(p["hbm_gbs"]), float(p["bf16_tflops"]), float(p["bf16_tflops_sustained"]),
+                "measured")
     except Exception:
-        return 6800.0, "fallback"
+        return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+# algorithmic bytes per node of the stencil kernels (FP32 fields; W = 8 steps per FP64
+# flush of the gradient accumulator)
+BYTES_PER_NODE = {
+    "forward": 36.0,        # read e, m, vx, vy, vz; write e, vx, vy, vz
+    "forward_pack": 38.0,   # + the output strain as BF16 into its window slot
+    "adjoint": 50.0,        # read mu, lam (3), m, e^n, FP32 window acc; write mu, lam, acc;
+                            # + 16 B FP64 read-modify-write / 8
+    "incremental": 44.0,    # forward + dm, e^n
+}
+
+
+def codec_flops_per_window(nvec: int, n_lat: int, n_hid: int) -> dict:
+    """Dense flops of one window's encoder (2048 -> n_hid -> n_lat) and decoder."""
+    enc = 2.0 * nvec * (2048 * n_hid + n_hid * n_lat)
+    dec = 2.0 * nvec * (n_lat * n_hid + n_hid * 2048)
+    return {"encode_window": enc, "decode_window": dec}
 
 
 def run_ours(args):
@@ -227,15 +270,18 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     shape, nt = tuple(args.shape), args.nt
     nz, ny, nx = shape
+    n_lat = nlat_of(args)
     rec = inputs.receiver_grid(nx, ny, NREC)
     C = nx * ny * nz
     seed = 2 + rank
     c_np = inputs.velocity_model(shape, H, seed=seed).astype(np.float32)
     ctrue = inputs.bump_model(c_np.astype(np.float64), H).astype(np.float32)
     c = torch.from_numpy(c_np).cuda()
-    Wt, trained = load_weights(args.weights or default_weights(64), 64)
+    wpath = args.weights or default_weights(args.codec, n_lat)
+    Wt, trained = load_weights(wpath, args.codec, n_lat)
+    hbm_peak, tf_peak, tf_sust, peak_kind = load_peaks()
 
-    ae = aewave.Solver(shape, H, nt, rec, storage="ae")
+    ae = aewave.Solver(shape, H, nt, rec, storage="ae", codec=args.codec, n_lat=n_lat)
     ae.codec_set(Wt)
     d_obs = ae.forward(torch.from_numpy(ctrue).cuda())
     g = torch.empty_like(c)
@@ -260,6 +306,7 @@ def run_ours(args):
     launches = ae.stats()["kernel_launches"] - l0
     ms_max = reduce_max(ms, world, torch.device("cuda", local))
     value = world * 3600e3 / ms_max
+    g_ae = g.clone()
 
     # ---- Gauss-Newton Hessian-vector products reusing this gradient's latents
     dc = torch.from_numpy(inputs.direction(shape, H, seed=20).astype(np.float32)).cuda()
@@ -273,6 +320,7 @@ def run_ours(args):
     h1.record(stream)
     torch.cuda.synchronize()
     ae_hvp_ms = h0.elapsed_time(h1) / args.steps
+    hv_ae = hv.clone()
 
     # ---- end to end through the public API with host buffers
     c_host = torch.from_numpy(c_np).pin_memory()
@@ -292,22 +340,38 @@ def run_ours(args):
     e2e_s = reduce_max(e2e_s, world, torch.device("cuda", local))
     h2d = c_host.numel() * 4 + d_host.numel() * 4
     d2h = g_host.numel() * 4 + 8
-
-    # ---- forward stencil kernel alone (nt back-to-back launches)
-    aefwd = ae
-    aefwd.forward(c)
-    torch.cuda.synchronize()
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
-    aefwd.forward(c)
-    f1.record(stream)
-    torch.cuda.synchronize()
-    fwd_ms = f0.elapsed_time(f1)
-    step_s = fwd_ms / 1e3 / nt
-    bytes_step = 36.0 * C
-    stencil_gbs = bytes_step / step_s / 1e9
-    peak, peak_kind = load_peaks()
     latent_bytes = int(ae.stats()["latent_bytes"])
+
+    # ---- decoded-state error of this run's windows / states (the codec as trained)
+    decoded = None
+    if not args.no_accuracy:
+        every = 8 if args.codec == "time" else max(1, nt // 40)
+        k = ae.nvec * ((nt // aewave.WINDOW - 1) // every + 1) if args.codec == "time" \
+            else ae.nblocks * ((nt - 1) // every)
+        vec, mx = ae.snapshots(c, every, k, with_scales=True)
+        decoded = ae.codec_eval(vec, mx)
+        decoded["sample"] = (f"every {every}th {'16-step window' if args.codec == 'time' else 'state'} "
+                             f"of this run, all vectors")
+        del vec, mx
+        torch.cuda.empty_cache()
+
+    # ---- the hot-path kernels alone (CUDA events around back-to-back launches)
+    nprof = min(nt, 200)
+    kernels = {}
+    kinds = ["forward", "adjoint", "incremental"] + (["forward_pack"] if args.codec == "time" else [])
+    for kind in kinds:
+        kms = ae.profile(c, kind, nprof)
+        b = BYTES_PER_NODE[kind] * C
+        kernels[kind] = {"ms_per_launch": kms, "bytes_per_launch": b, "bytes_per_node": BYTES_PER_NODE[kind],
+                         "achieved_gbs": b / kms / 1e6, "frac_of_hbm": b / kms / 1e6 / hbm_peak}
+    if args.codec == "time":
+        fl = codec_flops_per_window(ae.nvec, n_lat, ae.n_hid)
+        for kind in ("encode_window", "decode_window"):
+            kms = ae.profile(c, kind, 8)
+            kernels[kind] = {"ms_per_launch": kms, "flops_per_launch": fl[kind],
+                             "achieved_tflops": fl[kind] / kms / 1e9,
+                             "frac_of_bf16_burst": fl[kind] / kms / 1e9 / tf_peak,
+                             "note": "both layers of one window (two tcgen05 GEMMs) on all SMs"}
     del ae
     torch.cuda.empty_cache()
 
@@ -323,6 +387,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     rev_ms = r0.elapsed_time(r1) / args.revolve_runs
     rev_fwd = rev.stats()["forward_steps"]
+    g_exact = g.clone()        # checkpointing recomputes the exact states (= full storage)
     rev.hessvec(dc, hv)
     torch.cuda.synchronize()
     r0.record(stream)
@@ -332,6 +397,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     rev_hvp_ms = r0.elapsed_time(r1) / args.revolve_runs
     rev_hvp_fwd = rev.stats()["hvp_forward_steps"]
+    hv_exact = hv.clone()
     del rev
     torch.cuda.empty_cache()
 
@@ -366,10 +432,25 @@ def run_ours(args):
             full = {"ms_per_gradient": full_ms, "gradients_per_hour": 3600e3 / full_ms,
                     "history_bytes": hist,
                     "note": "e^n of every step kept in HBM (no recomputation, no compression)"}
+            g_exact = g.clone()
+            fs.hessvec(dc, hv)
+            hv_exact = hv.clone()
             del fs
             torch.cuda.empty_cache()
     else:
         full = {"unavailable": f"e^n history of {hist / 1e9:.1f} GB does not fit beside the rest"}
+
+    rel = lambda x, y: float(torch.linalg.vector_norm((x - y).double()) / torch.linalg.vector_norm(y.double()))
+    accuracy = {
+        "gradient_rel_err": rel(g_ae, g_exact), "hvp_rel_err": rel(hv_ae, hv_exact),
+        "reference": "full storage of e^n" if "ms_per_gradient" in (full or {}) else
+                     "20-slot checkpointing (bitwise equal to full storage)",
+        "decoded_strain_rel_err": None if decoded is None else
+            {"normalised": decoded["normalised"]["e"], "physical": decoded["physical"]["e"],
+             "vectors": decoded["vectors"], "sample": decoded["sample"]},
+        "codec_weights": os.path.relpath(wpath, ROOT) if trained else "random-init",
+        "target": "<= 1e-2 relative to the full-storage gradient / HVP",
+    }
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -379,19 +460,26 @@ def run_ours(args):
                          f"({secs:.1f} s), scaled to {nt} steps"}
 
     if rank == 0:
+        dom = kernels["adjoint"]
         line = {
             "metric": METRIC, "value": value, "unit": "gradients/hour", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 stencil, bf16 codec", "data": "synthetic (GRF velocity, bump-model observations)",
-            "config": dict(workload(shape, nt), codec_weights="trained" if trained else "random-init"),
-            "roofline": {"kernel": "forward leapfrog step", "bound": "hbm", "achieved": stencil_gbs,
-                         "peak": peak, "unit": "GB/s", "frac": stencil_gbs / peak,
-                         "peak_kind": f"{peak_kind} copy bandwidth",
-                         "traffic": FWD_TRAFFIC_256 if tuple(shape) == SHAPE else None,
-                         "bytes_per_launch": bytes_step},
-            "stencil": {"cell_updates_per_s": C / step_s, "gbs": stencil_gbs,
-                        "frac_of_8tbs": stencil_gbs / 8000.0},
+            "config": dict(workload(shape, nt, NREC, n_lat, args.codec),
+                           codec_weights="trained" if trained else "random-init"),
+            "accuracy": accuracy,
+            "roofline": {"kernel": "adjoint step (adj_tma_kernel), the longest per-step kernel "
+                                   "of the AE gradient", "bound": "hbm",
+                         "achieved": dom["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
+                         "frac": dom["achieved_gbs"] / hbm_peak,
+                         "peak_kind": f"{peak_kind} copy bandwidth (burst: kernel timed alone)",
+                         "traffic": None, "bytes_per_launch": dom["bytes_per_launch"],
+                         "timing": f"CUDA events around {nprof} back-to-back launches"},
+            "kernels": kernels,
+            "stencil": {"cell_updates_per_s": C / (kernels["forward"]["ms_per_launch"] / 1e3),
+                        "gbs": kernels["forward"]["achieved_gbs"],
+                        "frac_of_8tbs": kernels["forward"]["achieved_gbs"] / 8000.0},
             "revolve": {"gradients_per_hour": 3600e3 / rev_ms, "ms_per_gradient": rev_ms,
                         "forward_steps": rev_fwd, "slots": 20},
             "speedup_vs_revolve": rev_ms / ms_max,
@@ -415,13 +503,15 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def default_weights(n_lat: int) -> str:
-    return os.path.join(ROOT, "paper_2304_04781_gb300", "weights", f"codec_{n_lat}.npz")
+def default_weights(codec: str, n_lat: int) -> str:
+    name = f"codec_time_{n_lat}.npz" if codec == "time" else f"codec_{n_lat}.npz"
+    return os.path.join(ROOT, "paper_2304_04781_gb300", "weights", name)
 
 
-def load_weights(path: str, n_lat: int):
+def load_weights(path: str, codec: str, n_lat: int):
+    """(weights, trained): the file's weights, or Glorot-uniform ones if it is missing."""
     from paper_2304_04781_gb300 import inputs
-    W = inputs.codec_init(seed=0, n_lat=n_lat)
+    W = inputs.codec_init(seed=0, n_hid=2 * n_lat if codec == "time" else 512, n_lat=n_lat)
     if path and os.path.exists(path):
         z = np.load(path)
         return {k: z[k] for k in W}, True
@@ -433,22 +523,24 @@ def run_accuracy(args):
     the same GPU, decoded-state error, adjoint identity and checkpointing equality at the
     full size.  Prints one JSON line."""
     import torch
-    from paper_2304_04781_gb300 import aewave, inputs, train
+    from paper_2304_04781_gb300 import aewave, inputs
     shape, nt = tuple(args.shape), args.nt
     nz, ny, nx = shape
+    n_lat = nlat_of(args)
     rec = inputs.receiver_grid(nx, ny, args.nrec)
-    W, trained = load_weights(args.weights or default_weights(args.n_lat), args.n_lat)
+    W, trained = load_weights(args.weights or default_weights(args.codec, n_lat), args.codec, n_lat)
     c_np = inputs.velocity_model(shape, H, seed=2).astype(np.float32)
     c = torch.from_numpy(c_np).cuda()
     ctrue = torch.from_numpy(inputs.bump_model(c_np.astype(np.float64), H).astype(np.float32)).cuda()
     dirs = [torch.from_numpy(inputs.direction(shape, H, seed=(20 if args.hvps == 1 else 30) + k)
                              .astype(np.float32)).cuda() for k in range(args.hvps)]
-    out = {"config": dict(workload(shape, nt, args.nrec, args.n_lat), f0_hz=args.f0), "codec_weights": "trained" if trained else "random-init",
-           "n_lat": args.n_lat, "reference": args.ref}
+    out = {"config": dict(workload(shape, nt, args.nrec, n_lat, args.codec), f0_hz=args.f0),
+           "codec_weights": "trained" if trained else "random-init", "n_lat": n_lat,
+           "reference": args.ref}
     def ev():
         return torch.cuda.Event(enable_timing=True)
 
-    ae = aewave.Solver(shape, H, nt, rec, storage="ae", n_lat=args.n_lat, f0=args.f0)
+    ae = aewave.Solver(shape, H, nt, rec, storage="ae", codec=args.codec, n_lat=n_lat, f0=args.f0)
     ae.codec_set(W)
     d_obs = ae.forward(ctrue)
     a, b = ev(), ev(); a.record()
@@ -518,13 +610,14 @@ def run_accuracy(args):
     del ref
     torch.cuda.empty_cache()
 
-    # decoded-state error on states of this run (every 50th step)
-    tr = train.make_handle(shape, nt=nt, n_lat=args.n_lat, f0=args.f0)
+    # decoded-state error on this run's states (every 8th window / every nt/40-th state)
+    from paper_2304_04781_gb300 import train
+    tr = train.make_handle(shape, args.codec, n_lat, nt=nt, f0=args.f0)
     tr.codec_set(W)
-    every = max(1, nt // 40)
-    snaps, sc = train.generate(tr, [2], every)
-    out["decoded_state_error"] = train.decoded_error(tr, snaps, sc)
-    out["decoded_state_sample"] = f"states n = {every}, {2 * every}, ... of this run, all blocks"
+    every = 8 if args.codec == "time" else max(1, nt // 40)
+    snaps, mx = train.generate(tr, [2], every)
+    out["decoded_state_error"] = tr.codec_eval(snaps, mx)
+    out["decoded_state_sample"] = f"every {every}th {'window' if args.codec == 'time' else 'state'} of this run"
     print(json.dumps(out))
 
 

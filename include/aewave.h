@@ -10,8 +10,10 @@
  *   hessvec  : dc -> J_F^T J_F dc                      (incremental forward + incremental
  *                                                       adjoint, Sec. 4)
  * with the forward history kept in one of three ways: full storage, binomial
- * recompute-checkpointing, or per-block autoencoder latents (compression in space,
- * Sec. 3.1; architecture and training of Sec. 3.3; data generation of Algorithm 1).
+ * recompute-checkpointing, or autoencoder latents -- of every state's 8x8x8-node
+ * blocks (compression in space, Sec. 3.1) or of the strain of 2x8x8-node blocks over
+ * 16 consecutive steps (compression in time, Sec. 3.2); architecture and training of
+ * Sec. 3.3, data generation of Algorithm 1.
  *
  * Discretisation (the same in every mode): nodes [k][j][i] = (z, y, x), row-major with
  * x fastest, spacing h, rho = 1, m = c^2.  e lives on nodes and is 0 on boundary
@@ -56,7 +58,13 @@ typedef struct aew_handle aew_handle;
 enum {
   AEW_FULL = 0,     /* every strain e^n kept in HBM (FP32, nt * nx*ny*nz floats)       */
   AEW_REVOLVE = 1,  /* binomial recompute-checkpointing with n_checkpoints state slots  */
-  AEW_AE = 2        /* every state encoded to FP16 latents by the per-block codec       */
+  AEW_AE = 2        /* the history encoded to FP16 latents by the autoencoder codec     */
+};
+
+/* Codec kind of AEW_AE storage. */
+enum {
+  AEW_CODEC_SPACE = 0,  /* per state: 8x8x8-node blocks x 4 fields (e, vx, vy, vz)        */
+  AEW_CODEC_TIME = 1    /* per 16-step window: the strain of 2x8x8-node blocks            */
 };
 
 /* Error codes. */
@@ -76,8 +84,10 @@ enum {
 };
 
 typedef struct {
-  int nx, ny, nz;         /* nodes per axis, each >= 4 and a multiple of 4
-                             (a multiple of 8 for AEW_AE: 8x8x8-node codec blocks)   */
+  int nx, ny, nz;         /* nodes per axis, each >= 4 and a multiple of 4; for
+                             AEW_AE with the space codec multiples of 8 (8x8x8-node
+                             blocks), with the time codec nx, ny multiples of 8 and
+                             nz even (2x8x8-node blocks)                              */
   double h;               /* grid spacing [m]                                         */
   double cfl;             /* dt = cfl * h / cmax                                      */
   double cmax;            /* wave speed used for dt [m/s]                             */
@@ -92,7 +102,10 @@ typedef struct {
   int n_checkpoints;      /* AEW_REVOLVE: number of state slots (>= 0)                */
   int accum_window;       /* steps summed in FP32 before each FP64 flush of the
                              gradient accumulator (>= 1; 8 is a good default)         */
-  int n_lat;              /* codec latent width: 64 (32x compression) or 32 (64x)     */
+  int n_lat;              /* codec latent width: space codec 64 (32x compression of
+                             the 4-field state) or 32 (64x); time codec 512 (4x of the
+                             strain values, 32x of the FP32 state's bytes) or 256     */
+  int codec;              /* AEW_CODEC_SPACE (0) or AEW_CODEC_TIME (1)                */
 } aew_config;
 
 typedef struct {
@@ -105,7 +118,34 @@ typedef struct {
   double last_misfit;           /* J of the last gradient                            */
   int latent_overflow;          /* 1 if a latent overflowed FP16 in the last encode  */
   long long kernel_launches;    /* kernels launched by this handle since creation    */
+  double decoded_err_normalised; /* strain rel-L2 error of decode(encode(y)) in
+                                    normalised units, from the last aew_codec_eval    */
+  double decoded_err_physical;  /* the same in physical units (x = y s)              */
+  double last_gradient_ms;      /* device time of the last aew_gradient (0 until it
+                                   has finished on its stream)                       */
+  double last_hessvec_ms;       /* device time of the last aew_hessvec (likewise)    */
 } aew_stats_t;
+
+/* Loss of the codec training: Table 2's mean squared reconstruction error, or a
+ * weighted variant (each squared error of vector v in field f times w[v][f]). */
+enum {
+  AEW_LOSS_STATE = 0,             /* every output alike (Table 2)                          */
+  AEW_LOSS_STRAIN = 1,            /* strain outputs only (the adjoint reads nothing else)  */
+  AEW_LOSS_STRAIN_AMPLITUDE = 2,  /* strain only, each vector weighted by its strain scale
+                                     s, divided by the data set's mean of s              */
+  AEW_LOSS_STRAIN_ENERGY = 3      /* strain only, weighted by s^2 / mean(s^2): the
+                                     squared error in physical units                     */
+};
+
+typedef struct {
+  int epochs;               /* passes over the data (Table 2: 20; 0 = none)             */
+  int batch;                /* minibatch size (Table 2: 512), a multiple of 8, <= n     */
+  double lr0;               /* initial learning rate (Table 2: 1e-3)                    */
+  int halve_every;          /* lr = lr0 * 0.5^(epoch / halve_every) (Table 2: 5;
+                               <= 0: constant)                                          */
+  int loss;                 /* AEW_LOSS_*                                               */
+  unsigned long long seed;  /* seed of the per-epoch shuffles                           */
+} aew_train_cfg;
 
 /* ---------------------------------------------------------------------------------
  * Handle lifetime
@@ -127,19 +167,25 @@ const char* aew_last_error(const aew_handle* h);
 int aew_stats(const aew_handle* h, aew_stats_t* out);
 
 /* ---------------------------------------------------------------------------------
- * Codec: the per-block autoencoder of Sec. 3.1 / Sec. 3.3 (dense layers sigma(yW+b),
- * Eq. (5)).  Encoder 2048 -> 512 (GELU) -> n_lat; decoder n_lat -> 512 (GELU) -> 2048.
- * Block vector order: k = z*256 + f*64 + y*8 + x, f = 0:e, 1:vx, 2:vy, 3:vz (x, y, z
- * node offsets inside the 8x8x8 block); block b = (bz*NBy + by)*NBx + bx.
- * Normalisation: each field of each block is divided by its power-of-two scale
- * (aew_codec_encode), so encoder inputs lie in (-1, 1) whatever the amplitude.
+ * Codec: the autoencoder of Sec. 3.1-3.3 (dense layers sigma(yW+b), Eq. (5)).
+ * Encoder 2048 -> n_hid (GELU) -> n_lat; decoder n_lat -> n_hid (GELU) -> 2048, with
+ * n_hid = 512 for the space codec and n_hid = 2 n_lat for the time codec.
+ * Space codec, block vector order: k = z*256 + f*64 + y*8 + x, f = 0:e, 1:vx, 2:vy,
+ * 3:vz (x, y, z node offsets inside the 8x8x8 block); block b = (bz*NBy + by)*NBx + bx.
+ * Each field of each block is divided by its power-of-two scale (aew_codec_encode).
+ * Time codec, window vector order: k = t*128 + z*64 + y*8 + x (t the step inside the
+ * 16-step window of states e^{16w} .. e^{16w+15}; z, y, x the node offsets inside the
+ * 2x8x8 block); vector v = (bz*NBy + by)*NBx + bx with NBz = nz/2, NBy = ny/8,
+ * NBx = nx/8; states past nt - 1 are 0.  The whole vector is divided by its
+ * power-of-two scale s = 2^max(e, -100), m 2^e (m in [0.5, 1)) its largest |e|.
+ * Either way encoder inputs lie in (-1, 1) whatever the amplitude.
  * Precision: BF16 operands (FP16 for the decoder's first layer, whose input is the
  * FP16 latent) with FP32 accumulation on tcgen05 tensor cores; FP32 biases and GELU.
  * ------------------------------------------------------------------------------- */
 
 /* Set the codec weights from host FP32 arrays, row-major, layer y -> y W + b:
- * W1 [2048][512], b1 [512], W2 [512][n_lat], b2 [n_lat],
- * W3 [n_lat][512], b3 [512], W4 [512][2048], b4 [2048].  Copied; not retained. */
+ * W1 [2048][n_hid], b1 [n_hid], W2 [n_hid][n_lat], b2 [n_lat],
+ * W3 [n_lat][n_hid], b3 [n_hid], W4 [n_hid][2048], b4 [2048].  Copied; not retained. */
 int aew_codec_set(aew_handle* h, const float* W1_host, const float* b1_host,
                   const float* W2_host, const float* b2_host,
                   const float* W3_host, const float* b3_host,
@@ -151,7 +197,8 @@ int aew_codec_get(const aew_handle* h, float* W1_host, float* b1_host,
                   float* W3_host, float* b3_host,
                   float* W4_host, float* b4_host);
 
-/* Encode one state.  fields_dev = {e, vx, vy, vz} device [nz][ny][nx];
+/* Space codec only (AEW_E_CONFIG otherwise).  Encode one state.
+ * fields_dev = {e, vx, vy, vz} device [nz][ny][nx];
  * latents_dev: device FP16 [nblocks][n_lat] (written).  Each field of each block is
  * normalised by its own power-of-two scale s = 2^e, where max |f| over the block is
  * m 2^e with m in [0.5, 1) (the per-vector normalisation of Sec. 3.3); block_max_dev
@@ -171,12 +218,28 @@ int aew_codec_encode_vectors(aew_handle* h, const uint16_t* vectors_dev, long lo
 int aew_codec_decode(aew_handle* h, const uint16_t* latents_dev, long long n, float* out_dev,
                      void* stream);
 
-/* Decode latents to the strain field only: e_dev[nz][ny][nx] = s_b * (decoded strain
+/* Space codec only (AEW_E_CONFIG otherwise).
+ * Decode latents to the strain field only: e_dev[nz][ny][nx] = s_b * (decoded strain
  * part) with the block's power-of-two scale from block_max_dev (device FP32
  * [nblocks][4], as written by aew_codec_encode; field 0 is used), boundary nodes 0
  * (the boundary condition of Sec. 2). */
 int aew_codec_decode_e(aew_handle* h, const uint16_t* latents_dev, const float* block_max_dev,
                        float* e_dev, void* stream);
+
+/* Time codec only (AEW_E_CONFIG otherwise).  Encode one window of nsteps (1..16)
+ * strain fields e_dev[nsteps][nz][ny][nx] (device, contiguous, 16-byte aligned; the
+ * window's later states are taken as 0) into latents_dev, device FP16 [nvec][n_lat]
+ * (nvec = (nz/2)(ny/8)(nx/8)).  vmax_dev (may be NULL): device FP32 [nvec] receiving
+ * each vector's largest |e|, from which its scale follows.  Synchronises the stream;
+ * AEW_E_OVERFLOW if a latent overflowed FP16. */
+int aew_codec_encode_window(aew_handle* h, const float* e_dev, int nsteps, uint16_t* latents_dev,
+                            float* vmax_dev, void* stream);
+
+/* Time codec only.  Decode one window: e_dev[16][nz][ny][nx] (device, written, 16-byte
+ * aligned) = s_v * (decoded value) with each vector's scale from vmax_dev (device FP32
+ * [nvec], as aew_codec_encode_window writes it), 0 on boundary nodes (Sec. 2). */
+int aew_codec_decode_window(aew_handle* h, const uint16_t* latents_dev, const float* vmax_dev,
+                            float* e_dev, void* stream);
 
 /* ---------------------------------------------------------------------------------
  * Solves
@@ -225,6 +288,10 @@ int aew_jvp(aew_handle* h, const float* dc_dev, float* dd_dev, void* stream);
 /* Algorithm 1 (data generation): run the forward solve for c_dev and pack every
  * `every`-th state n (n = every, 2*every, ... < nt) into BF16 block vectors, each
  * field of each block divided by its power-of-two scale (see aew_codec_encode).
+ * With the time codec the unit is the window instead: every `every`-th complete
+ * window w (w = 0, every, 2*every, ...; 16 w + 15 <= nt - 1) is packed into normalised
+ * window vectors, and block_max_dev is then FP32 [max_vectors] (each vector's largest
+ * |e|).
  * out_dev: device BF16 (uint16 bit patterns) [max_vectors][2048], 16-byte aligned
  * (AEW_E_ARG otherwise); the forward step that reads a state packs it; *n_written receives
  * the number of vectors written (whole states only, at most max_vectors).
@@ -236,6 +303,27 @@ int aew_snapshots(aew_handle* h, const float* c_dev, int every, uint16_t* out_de
                   long long max_vectors, float* block_max_dev, long long* n_written,
                   void* stream);
 
+/* Train the codec (Sec. 3.3, Table 2) on n normalised vectors vectors_dev (device BF16
+ * [n][2048], 16-byte aligned, as aew_snapshots writes them), entirely on the device:
+ * each epoch a fresh seeded shuffle (a Feistel bijection of [0, n), cycle-walked;
+ * seed and epoch as key), floor(n / batch) minibatches gathered from it, one
+ * aew_codec_train_step-like LAMB step each at lr = lr0 * 0.5^(epoch / halve_every).
+ * maxima_dev: the vectors' maxima from aew_snapshots (device FP32 [n][4] for the space
+ * codec, [n] for the time codec), read for the amplitude-weighted losses, whose
+ * weights are computed on the device (NULL allowed for AEW_LOSS_STATE / _STRAIN).
+ * epoch_loss_host (may be NULL): host FP64 [epochs], each epoch's mean minibatch loss
+ * (each taken before its update).  Synchronous. */
+int aew_codec_train(aew_handle* h, const uint16_t* vectors_dev, const float* maxima_dev,
+                    long long n, const aew_train_cfg* cfg, double* epoch_loss_host, void* stream);
+
+/* Decoded error of the codec on n normalised vectors (BF16 [n][2048]) with their maxima
+ * (as for aew_codec_train): err_host[10] (host FP64) = rel-L2 of decode(encode(y)) - y
+ * in normalised units for the fields e, vx, vy, vz and over all values, then the same
+ * in physical units (x = y s); with the time codec every value is strain (err_host[0]
+ * = err_host[4]).  The strain errors are also kept in aew_stats.  Synchronous. */
+int aew_codec_eval(aew_handle* h, const uint16_t* vectors_dev, const float* maxima_dev,
+                   long long n, double* err_host, void* stream);
+
 /* One training step of the codec on a minibatch: batch_dev = BF16 [batch][2048]
  * normalised vectors (batch a multiple of 8); loss = mean squared reconstruction error
  * (Sec. 3.3), each squared error of vector v in field f's columns multiplied by
@@ -246,9 +334,51 @@ int aew_snapshots(aew_handle* h, const float* c_dev, int every, uint16_t* out_de
 int aew_codec_train_step(aew_handle* h, const uint16_t* batch_dev, const float* weights_dev,
                          int batch, float lr, float* loss_host, void* stream);
 
+/* Initialise the codec as the optimal rank-n_lat affine code of a data set (Sec. 1: a
+ * linear autoencoder learns the principal subspace of its data), written into the GELU
+ * layers of Eq. (5) through GELU(a) - GELU(-a) = a: hidden units j and n_lat + j carry
+ * +a_j and -a_j of a = (y - mu) V (V the n_lat leading eigenvectors of the weighted
+ * covariance, mu the weighted mean), the latent is GELU(a+) - GELU(a-) = a, and the
+ * decoder returns mu + z V^T the same way (needs n_hid >= 2 n_lat; further hidden units
+ * get zero weights).  Training steps may refine it from there.
+ * vectors_dev: device BF16 [n][2048] normalised vectors (as aew_snapshots writes them),
+ * 16-byte aligned; loss: the squared error the code minimises, AEW_LOSS_STATE (every
+ * vector alike) or, with the time codec, AEW_LOSS_STRAIN (the same),
+ * AEW_LOSS_STRAIN_AMPLITUDE (vector v weighted by its scale s_v) or
+ * AEW_LOSS_STRAIN_ENERGY (by s_v^2: the error in physical units), the weights computed
+ * on the device from maxima_dev (device FP32 [n], the vectors' maxima from
+ * aew_snapshots; may be NULL for the unweighted losses); eigvals_host (may be NULL):
+ * host FP64 [2048] receiving the covariance's eigenvalues in descending order (the
+ * tail sum past n_lat is the code's weighted mean squared error per unit weight).
+ * The second moments are tcgen05 GEMMs on the device (FP64 sums); the 2048 x 2048
+ * eigenproblem is solved on the host (Householder + implicit QL).  Synchronous; resets
+ * the training state.  AEW_E_NOMEM if the 34 MB moment buffer and 128 MB work buffer
+ * cannot be allocated. */
+int aew_codec_init_pca(aew_handle* h, const uint16_t* vectors_dev, const float* maxima_dev,
+                       long long n, int loss, double* eigvals_host, void* stream);
+
 /* ---------------------------------------------------------------------------------
  * Checks and host logic
  * ------------------------------------------------------------------------------- */
+
+/* Measurement hook: nsteps launches of one kernel of the hot path, back to back on the
+ * handle's own buffers (whatever they hold; the work does not depend on the values),
+ * with m = c_dev^2 (device [nz][ny][nx]), timed with CUDA events on `stream`; *ms_host
+ * receives the mean device time per launch.  kind: 0 forward step, 1 forward step that
+ * also packs its output strain into a time-codec window, 2 adjoint step reading a
+ * strain field (with the FP64 flush every accum_window steps), 3 incremental forward
+ * step, 4 encoder of one window (both layers), 5 decoder of one window (both layers,
+ * scattered to 16 strain slices).  Kinds 1, 4 and 5 need AE storage with the time codec
+ * (AEW_E_CONFIG otherwise), 4 and 5 codec weights.  Overwrites the handle's stored
+ * history (a later aew_hessvec needs a new aew_gradient).  Synchronises the stream. */
+int aew_profile_steps(aew_handle* h, const float* c_dev, int kind, int nsteps, double* ms_host,
+                      void* stream);
+
+/* Host only (no device work): all eigenpairs of the symmetric n x n FP64 matrix A_host
+ * (row-major), the solver aew_codec_init_pca uses: eigenvalues w_host[n] in descending
+ * order, eigenvectors as the columns of V_host (row-major n x n).  AEW_E_ARG for bad
+ * arguments or if the QL iteration does not converge. */
+int aew_sym_eig(int n, const double* A_host, double* w_host, double* V_host);
 
 /* FP64 inner product sum a[i] b[i] of two device FP32 arrays of n elements
  * (for the adjoint-identity and finite-difference checks).  Synchronises `stream`. */

@@ -19,6 +19,9 @@ from . import build as _build
 
 AEW_FULL, AEW_REVOLVE, AEW_AE = 0, 1, 2
 STORAGE = {"full": AEW_FULL, "revolve": AEW_REVOLVE, "ae": AEW_AE}
+AEW_CODEC_SPACE, AEW_CODEC_TIME = 0, 1
+CODEC = {"space": AEW_CODEC_SPACE, "time": AEW_CODEC_TIME}
+WINDOW = 16   # steps per window of the time codec
 
 _ERRORS = {
     -1: "AEW_E_CONFIG", -2: "AEW_E_CFL", -3: "AEW_E_NONFINITE", -4: "AEW_E_NOCODEC",
@@ -40,6 +43,7 @@ class aew_config(ctypes.Structure):
         ("nt", c_int), ("src", c_int * 3), ("f0", c_double), ("t0", c_double),
         ("nrec", c_int), ("rec_ijk", POINTER(c_int)),
         ("storage", c_int), ("n_checkpoints", c_int), ("accum_window", c_int), ("n_lat", c_int),
+        ("codec", c_int),
     ]
 
 
@@ -48,8 +52,20 @@ class aew_stats_t(ctypes.Structure):
         ("device_bytes", c_size_t), ("latent_bytes", c_size_t), ("history_bytes", c_size_t),
         ("forward_steps", c_longlong), ("adjoint_steps", c_longlong),
         ("hvp_forward_steps", c_longlong), ("last_misfit", c_double), ("latent_overflow", c_int),
-        ("kernel_launches", c_longlong),
+        ("kernel_launches", c_longlong), ("decoded_err_normalised", c_double),
+        ("decoded_err_physical", c_double), ("last_gradient_ms", c_double),
+        ("last_hessvec_ms", c_double),
     ]
+
+
+class aew_train_cfg(ctypes.Structure):
+    _fields_ = [
+        ("epochs", c_int), ("batch", c_int), ("lr0", c_double), ("halve_every", c_int),
+        ("loss", c_int), ("seed", ctypes.c_ulonglong),
+    ]
+
+
+LOSSES = {"state": 0, "strain": 1, "strain-amplitude": 2, "strain-energy": 3}
 
 
 _LIB = None
@@ -66,6 +82,8 @@ _SIGS = [
     ("aew_codec_encode_vectors", c_int, [c_void_p, c_void_p, c_longlong, c_void_p, c_void_p]),
     ("aew_codec_decode", c_int, [c_void_p, c_void_p, c_longlong, c_void_p, c_void_p]),
     ("aew_codec_decode_e", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("aew_codec_encode_window", c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    ("aew_codec_decode_window", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("aew_sync_check", c_int, [c_void_p, c_void_p]),
     ("aew_test_wait_timeout", c_int, [c_void_p, ctypes.c_ulonglong, c_void_p]),
     ("aew_forward", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
@@ -83,6 +101,13 @@ _SIGS = [
     ("aew_test_gelu", c_int, [c_void_p, c_void_p, c_void_p, c_longlong, c_void_p]),
     ("aew_revolve_plan", c_int, [c_int, c_int, c_void_p, c_void_p, c_longlong,
                                  POINTER(c_longlong), POINTER(c_longlong)]),
+    ("aew_codec_init_pca", c_int, [c_void_p, c_void_p, c_void_p, c_longlong, c_int, c_void_p,
+                                   c_void_p]),
+    ("aew_codec_train", c_int, [c_void_p, c_void_p, c_void_p, c_longlong, POINTER(aew_train_cfg),
+                                c_void_p, c_void_p]),
+    ("aew_codec_eval", c_int, [c_void_p, c_void_p, c_void_p, c_longlong, c_void_p, c_void_p]),
+    ("aew_sym_eig", c_int, [c_int, c_void_p, c_void_p, c_void_p]),
+    ("aew_profile_steps", c_int, [c_void_p, c_void_p, c_int, c_int, POINTER(c_double), c_void_p]),
 ]
 
 
@@ -178,13 +203,26 @@ def revolve_plan(nt: int, s: int):
     return [(names[ops[i]], args[i]) for i in range(n.value)], f.value
 
 
+def sym_eig(A: np.ndarray):
+    """Host eigensolver of the library (aew_sym_eig): (eigenvalues descending,
+    eigenvectors as columns) of a symmetric FP64 matrix."""
+    A = np.ascontiguousarray(np.asarray(A, dtype=np.float64))
+    n = A.shape[0]
+    w = np.empty(n)
+    V = np.empty((n, n))
+    rc = lib().aew_sym_eig(n, A.ctypes.data, w.ctypes.data, V.ctypes.data)
+    if rc != 0:
+        raise AewError(rc, "aew_sym_eig failed")
+    return w, V
+
+
 class Solver:
     """Owns one aew_handle: grid, time stepping, receivers and history storage."""
 
     def __init__(self, shape, h: float, nt: int, rec, storage: str = "full",
-                 n_checkpoints: int = 20, accum_window: int = 8, n_lat: int = 64,
+                 n_checkpoints: int = 20, accum_window: int = 8, n_lat: Optional[int] = None,
                  cfl: float = 0.5, cmax: float = 3000.0, src=None, f0: float = 25.0,
-                 t0: Optional[float] = None):
+                 t0: Optional[float] = None, codec: str = "space"):
         nz, ny, nx = shape
         self.shape = (nz, ny, nx)
         self.nt = nt
@@ -204,8 +242,13 @@ class Solver:
         cfg.storage = STORAGE[storage]
         cfg.n_checkpoints = n_checkpoints
         cfg.accum_window = accum_window
+        if n_lat is None:
+            n_lat = 512 if codec == "time" else 64
         cfg.n_lat = n_lat
+        cfg.codec = CODEC[codec]
         self.n_lat = n_lat
+        self.codec = codec
+        self.n_hid = 2 * n_lat if codec == "time" else 512
         self.dt = cfl * h / cmax
         self._h = c_void_p()
         L = lib()
@@ -233,6 +276,12 @@ class Solver:
     def nblocks(self) -> int:
         nz, ny, nx = self.shape
         return (nz // 8) * (ny // 8) * (nx // 8)
+
+    @property
+    def nvec(self) -> int:
+        """Vectors per window of the time codec (2 x 8 x 8-node blocks)."""
+        nz, ny, nx = self.shape
+        return (nz // 2) * (ny // 8) * (nx // 8)
 
     def _drec(self) -> torch.Tensor:
         return torch.empty((self.nt + 1, self.nrec, 3), device="cuda", dtype=torch.float32)
@@ -285,6 +334,16 @@ class Solver:
         """Enqueue a kernel whose bounded wait runs out (failure-path test hook)."""
         self._check(lib().aew_test_wait_timeout(self._h, int(wait_ns), _stream()))
 
+    PROFILE_KINDS = {"forward": 0, "forward_pack": 1, "adjoint": 2, "incremental": 3,
+                     "encode_window": 4, "decode_window": 5}
+
+    def profile(self, c: torch.Tensor, kind: str, nsteps: int) -> float:
+        """aew_profile_steps: mean device ms per launch of one hot-path kernel."""
+        ms = c_double(0.0)
+        self._check(lib().aew_profile_steps(self._h, _ptr(c), self.PROFILE_KINDS[kind], nsteps,
+                                            byref(ms), _stream()))
+        return ms.value
+
     def stats(self) -> dict:
         s = aew_stats_t()
         self._check(lib().aew_stats(self._h, byref(s)))
@@ -297,9 +356,9 @@ class Solver:
         self._check(lib().aew_codec_set(self._h, *[a.ctypes.data for a in arrs]))
 
     def codec_get(self) -> dict:
-        nl = self.n_lat
-        shapes = {"W1": (2048, 512), "b1": (512,), "W2": (512, nl), "b2": (nl,),
-                  "W3": (nl, 512), "b3": (512,), "W4": (512, 2048), "b4": (2048,)}
+        nl, nh = self.n_lat, self.n_hid
+        shapes = {"W1": (2048, nh), "b1": (nh,), "W2": (nh, nl), "b2": (nl,),
+                  "W3": (nl, nh), "b3": (nh,), "W4": (nh, 2048), "b4": (2048,)}
         out = {k: np.empty(v, np.float32) for k, v in shapes.items()}
         self._check(lib().aew_codec_get(self._h, *[out[k].ctypes.data for k in shapes]))
         return out
@@ -335,20 +394,76 @@ class Solver:
                                              _ptr(e), _stream()))
         return e
 
+    def codec_encode_window(self, e: torch.Tensor):
+        """Time codec: encode one window of strain fields e [nsteps <= 16][nz][ny][nx]
+        (CUDA FP32): returns (FP16 latents [nvec][n_lat], FP32 vector maxima [nvec])."""
+        e = e.contiguous()
+        lat = torch.empty((self.nvec, self.n_lat), device="cuda", dtype=torch.float16)
+        vmax = torch.empty((self.nvec,), device="cuda", dtype=torch.float32)
+        self._check(lib().aew_codec_encode_window(self._h, _ptr(e), e.shape[0], _ptr(lat),
+                                                  _ptr(vmax), _stream()))
+        return lat, vmax
+
+    def codec_decode_window(self, lat: torch.Tensor, vmax: torch.Tensor) -> torch.Tensor:
+        """Time codec: the 16 decoded strain fields [16][nz][ny][nx] of one window."""
+        e = torch.empty((WINDOW,) + self.shape, device="cuda", dtype=torch.float32)
+        self._check(lib().aew_codec_decode_window(self._h, _ptr(lat), _ptr(vmax.contiguous()),
+                                                  _ptr(e), _stream()))
+        return e
+
     def snapshots(self, c: torch.Tensor, every: int, max_vectors: int,
                   out: Optional[torch.Tensor] = None, with_scales: bool = False):
-        """Algorithm 1: normalised BF16 block vectors of every `every`-th state.
+        """Algorithm 1: normalised BF16 vectors of every `every`-th state (space codec)
+        or window (time codec).
 
-        Returns the [n][2048] bfloat16 tensor (and the [n][4] block maxima)."""
+        Returns the [n][2048] bfloat16 tensor (and the maxima that fix the scales:
+        [n][4] block maxima, or [n] vector maxima with the time codec)."""
         if out is None:
             out = torch.empty((max_vectors, 2048), device="cuda", dtype=torch.bfloat16)
-        bm = torch.zeros((max_vectors, 4), device="cuda") if with_scales else None
+        mshape = (max_vectors,) if self.codec == "time" else (max_vectors, 4)
+        bm = torch.zeros(mshape, device="cuda") if with_scales else None
         n = c_longlong(0)
         self._check(lib().aew_snapshots(self._h, _ptr(c), every, _ptr(out), max_vectors, _ptr(bm),
                                         byref(n), _stream()))
         if with_scales:
             return out[: n.value], bm[: n.value]
         return out[: n.value]
+
+    def codec_init_pca(self, vectors: torch.Tensor, maxima: Optional[torch.Tensor] = None,
+                       loss: str = "state"):
+        """aew_codec_init_pca: set the codec to the optimal rank-n_lat code of the BF16
+        vectors [n][2048] under `loss` (weights from the vectors' maxima on the device);
+        returns the covariance's eigenvalues (descending, FP64 numpy array of 2048)."""
+        assert vectors.dtype == torch.bfloat16 and vectors.shape[-1] == 2048
+        ev = np.empty(2048)
+        m = None if maxima is None else maxima.contiguous().float()
+        self._check(lib().aew_codec_init_pca(self._h, _ptr(vectors.contiguous()), _ptr(m),
+                                             vectors.shape[0], LOSSES[loss], ev.ctypes.data,
+                                             _stream()))
+        return ev
+
+    def codec_train(self, vectors: torch.Tensor, maxima: Optional[torch.Tensor] = None,
+                    epochs: int = 20, batch: int = 512, lr0: float = 1e-3, halve_every: int = 5,
+                    loss: str = "state", seed: int = 0):
+        """aew_codec_train: Table 2's epochs on the device; returns each epoch's mean loss."""
+        cfg = aew_train_cfg()
+        cfg.epochs, cfg.batch, cfg.lr0, cfg.halve_every = epochs, batch, lr0, halve_every
+        cfg.loss, cfg.seed = LOSSES[loss], seed
+        out = np.zeros(max(epochs, 1))
+        m = None if maxima is None else maxima.contiguous().float()
+        self._check(lib().aew_codec_train(self._h, _ptr(vectors.contiguous()), _ptr(m),
+                                          vectors.shape[0], byref(cfg), out.ctypes.data, _stream()))
+        return out[:epochs].tolist()
+
+    def codec_eval(self, vectors: torch.Tensor, maxima: torch.Tensor) -> dict:
+        """aew_codec_eval: decoded rel-L2 errors, normalised and physical units."""
+        out = np.zeros(10)
+        self._check(lib().aew_codec_eval(self._h, _ptr(vectors.contiguous()),
+                                         _ptr(maxima.contiguous().float()), vectors.shape[0],
+                                         out.ctypes.data, _stream()))
+        names = ["e", "vx", "vy", "vz", "all"]
+        return {"normalised": dict(zip(names, out[:5].tolist())),
+                "physical": dict(zip(names, out[5:].tolist())), "vectors": int(vectors.shape[0])}
 
     def train_step(self, batch: torch.Tensor, lr: float, want_loss: bool = True,
                    weights: Optional[torch.Tensor] = None) -> Optional[float]:

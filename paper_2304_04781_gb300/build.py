@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libaewave.so")
 OBJ = os.path.join(HERE, "_build")
 SOURCES = ["aew_api.cu", "aew_stencil.cu", "aew_reduce.cu", "aew_codec.cu", "aew_train.cu",
-           "aew_revolve.cpp", "aew_noalloc.cu"]
+           "aew_revolve.cpp", "aew_pca.cpp", "aew_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]
@@ -61,7 +61,7 @@ def build(force: bool = False, verbose: bool = False, extra=(), out: str = LIB,
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(lambda s: _compile(s, list(extra), objdir), SOURCES))
     tmp = out + ".tmp"
-    cmd = [nvcc(), *ARCH, "-shared", "-Xcompiler", "-fPIC", *objs, "-o", tmp]
+    cmd = [nvcc(), *ARCH, "-shared", "-Xcompiler", "-fPIC", *objs, "-lpthread", "-o", tmp]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

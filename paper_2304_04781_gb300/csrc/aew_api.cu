@@ -19,6 +19,7 @@
 #include "../../include/aewave.h"
 #include "aew_codec.cuh"
 #include "aew_internal.cuh"
+#include "aew_pca.h"
 #include "aew_revolve.h"
 
 using aew::Codec;
@@ -65,6 +66,18 @@ struct aew_handle {
   cudaEvent_t ev_a[2] = {}, ev_b[2] = {}, ev_sync = nullptr, ev_sync2 = nullptr;
   uint16_t* xpk[2] = {};
   float* edb[2] = {};
+  // AE mode with the time codec: per window and vector the max |e| (float bits)
+  // [nwin][nvec], raw BF16 window vectors being filled / encoded, decoded windows of
+  // 16 strain slices, and a window workspace of the standalone codec calls
+  bool tcodec = false;
+  unsigned* vmx = nullptr;
+  uint16_t* xt[2] = {};
+  float* edt[2] = {};
+  uint16_t* wk_raw = nullptr;
+  unsigned* wk_vmax = nullptr;
+  // device timing of the last gradient and hessvec (read lazily by aew_stats)
+  cudaEvent_t tg[2] = {}, th[2] = {};
+  bool tg_set = false, th_set = false;
   std::vector<float> wav;
   bool have_grad = false;
   Codec* codec = nullptr;
@@ -119,16 +132,28 @@ size_t nblocks_of(const aew_handle* h) {
   return (size_t)(h->cfg.nx / 8) * (h->cfg.ny / 8) * (h->cfg.nz / 8);
 }
 
+// time codec: vectors per window (2 x 8 x 8-node blocks) and windows covering e^0..e^{nt-1}
+size_t nvec_of(const aew_handle* h) {
+  return (size_t)(h->cfg.nx / 8) * (h->cfg.ny / 8) * (h->cfg.nz / 2);
+}
+int nwin_of(const aew_handle* h) { return (h->cfg.nt + aew::kTSteps - 1) / aew::kTSteps; }
+
 // ---------------------------------------------------------------------------------
 // Single steps
 // ---------------------------------------------------------------------------------
 // xpack / bmax_in: pack the input state n into normalised BF16 block vectors, by the
 // block maxima that the step producing state n stored in bmax_in; bmax_out: store the
 // block maxima of the output state n + 1 (AE forward and Algorithm 1 snapshots)
+// tpack / tslot / vmax (time codec): store the output strain e^{n+1} as raw BF16 in slot
+// tslot of the window buffer and fold its per-vector maxima into vmax
 int fwd_step(aew_handle* h, int n, float* const in[4], float* const out[4], const float* wav,
              float* d_row, cudaStream_t s, uint16_t* xpack = nullptr,
-             const unsigned* bmax_in = nullptr, unsigned* bmax_out = nullptr) {
+             const unsigned* bmax_in = nullptr, unsigned* bmax_out = nullptr,
+             uint16_t* tpack = nullptr, int tslot = 0, unsigned* vmax = nullptr) {
   aew::FwdStep a{};
+  a.tpack = tpack;
+  a.tslot = tslot;
+  a.vmax = vmax;
   if (xpack) {
     a.xpack = xpack;
     a.bmax_in = bmax_in;
@@ -507,6 +532,170 @@ int gradient_ae(aew_handle* h, const float* d_obs, const float* wav, cudaStream_
   return AEW_OK;
 }
 
+// ---------------------------------------------------------------------------------
+// Compression in time: windows of 16 strain states per 2 x 8 x 8-node block
+// ---------------------------------------------------------------------------------
+// encoder of window tb (raw vectors in xt[tb % 2], maxima vmx[tb]) into its latents
+int encode_window(aew_handle* h, int tb, cudaStream_t s) {
+  const size_t nv = nvec_of(h);
+  cudaError_t e = aew::codec_encode_window(h->codec, h->xt[tb & 1], h->vmx + (size_t)tb * nv,
+                                           (long long)nv, h->lat + (size_t)tb * nv * h->cfg.n_lat,
+                                           h->ovf, s, h->overlap_ctas);
+  if (e != cudaSuccess) return cuda_fail(h, e, "codec_encode_window");
+  h->stats.kernel_launches += 2;
+  return AEW_OK;
+}
+
+// decoder of window tb into its 16 strain slices edt[tb % 2]
+int decode_window(aew_handle* h, int tb, cudaStream_t s) {
+  const size_t nv = nvec_of(h);
+  cudaError_t e = aew::codec_decode_window(h->codec, h->lat + (size_t)tb * nv * h->cfg.n_lat,
+                                           h->vmx + (size_t)tb * nv, h->cfg.nx, h->cfg.ny,
+                                           h->cfg.nz, h->edt[tb & 1], s, h->overlap_ctas);
+  if (e != cudaSuccess) return cuda_fail(h, e, "codec_decode_window");
+  h->stats.kernel_launches += 2;
+  return AEW_OK;
+}
+
+// decoded strain e^n (n >= 1) of the window being read
+const float* window_e(aew_handle* h, int n) {
+  return n >= 1 ? h->edt[(n / aew::kTSteps) & 1] + (size_t)(n % aew::kTSteps) * h->C : nullptr;
+}
+
+// Adjoint sweep with the time codec: entering window tb (in reverse), the decoder of
+// window tb - 1 runs on the side stream into the buffer window tb + 1 used, while the
+// adjoint steps of window tb run on s.  ev_b[w % 2]: window w decoded; ev_a[w % 2]:
+// window w's adjoint steps done.
+int time_adjoint_sweep(aew_handle* h, const float* resid, cudaStream_t s) {
+  const int nt = h->cfg.nt, W = nwin_of(h), T = aew::kTSteps;
+  int rc;
+  if ((rc = begin_adjoint(h, s))) return rc;
+  if ((rc = join(h, s, h->side, h->ev_sync))) return rc;
+  if ((rc = decode_window(h, W - 1, h->side))) return rc;
+  AEW_CK(cudaEventRecord(h->ev_b[(W - 1) & 1], h->side));
+  int acur = 0;
+  for (int n = nt - 1; n >= 0; --n) {
+    const int tb = n / T;
+    if (n == nt - 1 || n % T == T - 1) {
+      if (tb >= 1) {
+        if (tb + 1 <= W - 1) AEW_CK(cudaStreamWaitEvent(h->side, h->ev_a[(tb + 1) & 1], 0));
+        if ((rc = decode_window(h, tb - 1, h->side))) return rc;
+        AEW_CK(cudaEventRecord(h->ev_b[(tb - 1) & 1], h->side));
+      }
+      AEW_CK(cudaStreamWaitEvent(s, h->ev_b[tb & 1], 0));
+    }
+    if ((rc = adj_step(h, n, acur, resid, window_e(h, n), s))) return rc;
+    acur ^= 1;
+    if (n % T == 0) AEW_CK(cudaEventRecord(h->ev_a[tb & 1], s));
+  }
+  return join(h, h->side, s, h->ev_sync2);
+}
+
+// AE gradient with the time codec: the step that writes state m = n + 1 stores it in
+// slot m % 16 of window m / 16 (buffer xt[(m / 16) % 2]) with the vectors' maxima; a
+// complete window is encoded on the side stream while the next window's steps run on
+// s.  ev_a[w % 2]: window w complete; ev_b[w % 2]: window w encoded (its buffer is free
+// for window w + 2).
+int gradient_ae_time(aew_handle* h, const float* d_obs, const float* wav, cudaStream_t s) {
+  const int nt = h->cfg.nt, W = nwin_of(h), T = aew::kTSteps;
+  const size_t nv = nvec_of(h), wbytes = nv * aew::kNIn * sizeof(uint16_t);
+  int rc;
+  if ((rc = zero_state(h, h->st[0], s))) return rc;
+  AEW_CK(cudaMemsetAsync(h->vmx, 0, (size_t)W * nv * sizeof(unsigned), s));
+  AEW_CK(cudaMemsetAsync(h->xt[0], 0, wbytes, s));   // slot 0 of window 0 is e^0 = 0
+  AEW_CK(cudaMemsetAsync(h->ovf, 0, sizeof(int), s));
+  AEW_CK(cudaMemsetAsync(h->d, 0, h->nrow * sizeof(float), s));
+  if ((rc = join(h, s, h->side, h->ev_sync))) return rc;
+  auto window_done = [&](int tb) -> int {
+    AEW_CK(cudaEventRecord(h->ev_a[tb & 1], s));
+    AEW_CK(cudaStreamWaitEvent(h->side, h->ev_a[tb & 1], 0));
+    int r = encode_window(h, tb, h->side);
+    if (r) return r;
+    AEW_CK(cudaEventRecord(h->ev_b[tb & 1], h->side));
+    return AEW_OK;
+  };
+  if (nt == 1 && (rc = window_done(0))) return rc;
+  int cur = 0;
+  for (int n = 0; n < nt; ++n) {
+    const int m = n + 1;
+    uint16_t* tp = nullptr;
+    unsigned* vm = nullptr;
+    const int tb = m / T, slot = m % T;
+    if (m <= nt - 1) {
+      if (slot == 0) {
+        if (tb >= 2) AEW_CK(cudaStreamWaitEvent(s, h->ev_b[tb & 1], 0));
+        if (T * tb + T > nt) AEW_CK(cudaMemsetAsync(h->xt[tb & 1], 0, wbytes, s));   // tail 0
+      }
+      tp = h->xt[tb & 1];
+      vm = h->vmx + (size_t)tb * nv;
+    }
+    rc = fwd_step(h, n, h->st[cur], h->st[cur ^ 1], wav, drow(h, h->d, n + 1), s, nullptr,
+                  nullptr, nullptr, tp, slot, vm);
+    if (rc) return rc;
+    cur ^= 1;
+    if (m <= nt - 1 && (slot == T - 1 || m == nt - 1) && (rc = window_done(tb))) return rc;
+  }
+  if ((rc = join(h, h->side, s, h->ev_sync2))) return rc;
+  if ((rc = residual_and_misfit(h, d_obs, s))) return rc;
+  if ((rc = time_adjoint_sweep(h, h->R, s))) return rc;
+  h->stats.forward_steps = nt;
+  h->stats.adjoint_steps = nt;
+  return AEW_OK;
+}
+
+// Algorithm 1 with the time codec: the complete windows tb = 0, every, 2 every, ... are
+// packed by the forward steps that write their states (raw BF16 plus per-vector
+// maxima), then normalised in place once their last state is in.
+int snapshots_time(aew_handle* h, int every, uint16_t* out, long long max_vectors,
+                   float* vmax_dev, long long* n_written, cudaStream_t s) {
+  const int nt = h->cfg.nt, T = aew::kTSteps, W = nwin_of(h);
+  const size_t nv = nvec_of(h);
+  if (!vmax_dev && !h->wk_vmax && !dalloc(h, &h->wk_vmax, nv))
+    return fail(h, AEW_E_NOMEM, "workspace");
+  std::vector<long long> at((size_t)W, -1);
+  long long w = 0;
+  int last = -1;
+  for (int tb = 0; tb < W; ++tb)
+    if (tb % every == 0 && T * tb + T - 1 <= nt - 1 && w + (long long)nv <= max_vectors) {
+      at[tb] = w;
+      w += (long long)nv;
+      last = tb;
+    }
+  *n_written = 0;
+  if (last < 0) return AEW_OK;
+  auto vm = [&](int tb) {
+    return vmax_dev ? reinterpret_cast<unsigned*>(vmax_dev) + at[tb] : h->wk_vmax;
+  };
+  int rc;
+  if ((rc = zero_state(h, h->st[0], s))) return rc;
+  if (at[0] >= 0) {   // slot 0 of window 0 is e^0 = 0, written by no step
+    AEW_CK(cudaMemsetAsync(out + (size_t)at[0] * aew::kNIn, 0, nv * aew::kNIn * sizeof(uint16_t), s));
+    AEW_CK(cudaMemsetAsync(vm(0), 0, nv * sizeof(unsigned), s));
+  }
+  int cur = 0;
+  for (int n = 0; n < T * last + T - 1; ++n) {
+    const int m = n + 1, tb = m / T, slot = m % T;
+    uint16_t* tp = nullptr;
+    unsigned* vq = nullptr;
+    if (at[tb] >= 0) {
+      tp = out + (size_t)at[tb] * aew::kNIn;
+      vq = vm(tb);
+      if (slot == 0) AEW_CK(cudaMemsetAsync(vq, 0, nv * sizeof(unsigned), s));
+    }
+    if ((rc = fwd_step(h, n, h->st[cur], h->st[cur ^ 1], h->wav.data(), nullptr, s, nullptr,
+                       nullptr, nullptr, tp, slot, vq)))
+      return rc;
+    cur ^= 1;
+    if (tp && slot == T - 1) {
+      AEW_CK(aew::window_normalise(tp, vq, (long long)nv, tp, s));
+      ++h->stats.kernel_launches;
+    }
+  }
+  AEW_CK(cudaStreamSynchronize(s));
+  *n_written = w;
+  return AEW_OK;
+}
+
 }  // namespace
 
 // =================================================================================
@@ -540,9 +729,16 @@ int aew_create(const aew_config* cfg, aew_handle** out) {
     return bad("storage must be AEW_FULL, AEW_REVOLVE or AEW_AE");
   if (c.storage == AEW_REVOLVE && c.n_checkpoints < 0) return bad("n_checkpoints must be >= 0");
   if (c.accum_window < 1) return bad("accum_window must be >= 1");
-  if (c.storage == AEW_AE && (c.nx % 8 || c.ny % 8 || c.nz % 8))
+  if (c.storage == AEW_AE && c.codec == AEW_CODEC_SPACE && (c.nx % 8 || c.ny % 8 || c.nz % 8))
     return bad("AE storage needs nx, ny, nz multiples of 8");
-  if (c.n_lat != 64 && c.n_lat != 32) return bad("n_lat must be 64 or 32");
+  if (c.codec != AEW_CODEC_SPACE && c.codec != AEW_CODEC_TIME)
+    return bad("codec must be AEW_CODEC_SPACE or AEW_CODEC_TIME");
+  if (c.codec == AEW_CODEC_SPACE && c.n_lat != 64 && c.n_lat != 32)
+    return bad("n_lat must be 64 or 32 for the space codec");
+  if (c.codec == AEW_CODEC_TIME && c.n_lat != 512 && c.n_lat != 256)
+    return bad("n_lat must be 512 or 256 for the time codec");
+  if (c.storage == AEW_AE && c.codec == AEW_CODEC_TIME && (c.nx % 8 || c.ny % 8 || c.nz % 2))
+    return bad("AE storage with the time codec needs nx, ny multiples of 8 and nz even");
 
   aew_handle* h = new aew_handle();
   h->cfg = c;
@@ -586,12 +782,22 @@ int aew_create(const aew_config* cfg, aew_handle** out) {
   for (int i = 0; ok && c.storage == AEW_REVOLVE && i < 4; ++i) {
     ok = dalloc(h, &h->zst[i], C) && cudaMemset(h->zst[i], 0, C * sizeof(float)) == cudaSuccess;
   }
-  if (ok && c.storage == AEW_AE) {
+  h->tcodec = c.codec == AEW_CODEC_TIME;
+  if (ok && c.storage == AEW_AE && !h->tcodec) {
     const size_t nb = (size_t)(c.nx / 8) * (c.ny / 8) * (c.nz / 8);
     ok = dalloc(h, &h->lat, nt * nb * c.n_lat) && dalloc(h, &h->bmx, nt * nb * 4) &&
          dalloc(h, &h->ovf, 1) && dalloc(h, &h->xpk[0], nb * aew::kNIn) &&
          dalloc(h, &h->xpk[1], nb * aew::kNIn) && dalloc(h, &h->edb[0], C) &&
          dalloc(h, &h->edb[1], C);
+  }
+  if (ok && c.storage == AEW_AE && h->tcodec) {
+    const size_t nv = nvec_of(h), W = (size_t)nwin_of(h);
+    ok = dalloc(h, &h->lat, W * nv * c.n_lat) && dalloc(h, &h->vmx, W * nv) &&
+         dalloc(h, &h->ovf, 1) && dalloc(h, &h->xt[0], nv * aew::kNIn) &&
+         dalloc(h, &h->xt[1], nv * aew::kNIn) && dalloc(h, &h->edt[0], aew::kTSteps * C) &&
+         dalloc(h, &h->edt[1], aew::kTSteps * C);
+  }
+  if (ok && c.storage == AEW_AE) {
     // The codec GEMMs run on a high-priority side stream with half the SMs, so their
     // CTAs are placed first and the concurrent stencil step keeps the other half
     // (measured best at 256^3 among caps of 76-152 CTAs and 2-4 GEMM stages).
@@ -620,15 +826,23 @@ int aew_create(const aew_config* cfg, aew_handle** out) {
     aew_destroy(h);
     return AEW_E_CUDA;
   }
-  h->codec = aew::codec_new(c.n_lat);
+  h->codec = aew::codec_new(c.n_lat, h->tcodec);
   if (!h->codec) {
     g_create_err = "codec allocation failed";
     aew_destroy(h);
     return AEW_E_NOMEM;
   }
+  for (int i = 0; i < 2; ++i)
+    if (cudaEventCreate(&h->tg[i]) != cudaSuccess || cudaEventCreate(&h->th[i]) != cudaSuccess) {
+      g_create_err = "event creation failed";
+      aew_destroy(h);
+      return AEW_E_CUDA;
+    }
   h->stats.device_bytes = h->bytes + aew::codec_device_bytes(h->codec);
   h->stats.latent_bytes =
-      c.storage == AEW_AE ? nt * (size_t)(c.nx / 8) * (c.ny / 8) * (c.nz / 8) * c.n_lat * 2 : 0;
+      c.storage != AEW_AE ? 0
+      : h->tcodec         ? (size_t)nwin_of(h) * nvec_of(h) * c.n_lat * 2
+                          : nt * (size_t)(c.nx / 8) * (c.ny / 8) * (c.nz / 8) * c.n_lat * 2;
   h->stats.history_bytes = c.storage == AEW_FULL      ? nt * C * 4
                            : c.storage == AEW_REVOLVE ? (size_t)c.n_checkpoints * 4 * C * 4
                                                       : h->stats.latent_bytes;
@@ -642,6 +856,10 @@ void aew_destroy(aew_handle* h) {
   for (int i = 0; i < 2; ++i) {
     if (h->ev_a[i]) cudaEventDestroy(h->ev_a[i]);
     if (h->ev_b[i]) cudaEventDestroy(h->ev_b[i]);
+  }
+  for (int i = 0; i < 2; ++i) {
+    if (h->tg[i]) cudaEventDestroy(h->tg[i]);
+    if (h->th[i]) cudaEventDestroy(h->th[i]);
   }
   if (h->ev_sync) cudaEventDestroy(h->ev_sync);
   if (h->ev_sync2) cudaEventDestroy(h->ev_sync2);
@@ -658,6 +876,14 @@ const char* aew_last_error(const aew_handle* h) {
 int aew_stats(const aew_handle* h, aew_stats_t* out) {
   if (!h || !out) return AEW_E_ARG;
   *out = h->stats;
+  float ms = 0.f;
+  if (h->tg_set && cudaEventQuery(h->tg[1]) == cudaSuccess &&
+      cudaEventElapsedTime(&ms, h->tg[0], h->tg[1]) == cudaSuccess)
+    out->last_gradient_ms = ms;
+  if (h->th_set && cudaEventQuery(h->th[1]) == cudaSuccess &&
+      cudaEventElapsedTime(&ms, h->th[0], h->th[1]) == cudaSuccess)
+    out->last_hessvec_ms = ms;
+  cudaGetLastError();   // a query of an unfinished event is not an error of the handle
   return AEW_OK;
 }
 
@@ -742,6 +968,8 @@ int aew_gradient(aew_handle* h, const float* c_dev, const float* d_obs_dev, floa
     return fail(h, AEW_E_NOCODEC, "AE storage needs codec weights (aew_codec_set)");
   int rc = prepare_c(h, c_dev, s);
   if (rc) return rc;
+  h->tg_set = false;
+  AEW_CK(cudaEventRecord(h->tg[0], s));
   const float* wav = h->wav.data();
   if (h->cfg.storage == AEW_FULL) {
     rc = gradient_full(h, d_obs_dev, wav, s);
@@ -750,6 +978,8 @@ int aew_gradient(aew_handle* h, const float* c_dev, const float* d_obs_dev, floa
     rc = run_revolve(h, d_obs_dev, nullptr, wav, true, s, &fwd);
     h->stats.forward_steps = fwd;
     h->stats.adjoint_steps = h->cfg.nt;
+  } else if (h->tcodec) {
+    rc = gradient_ae_time(h, d_obs_dev, wav, s);
   } else {
     rc = gradient_ae(h, d_obs_dev, wav, s);
   }
@@ -758,6 +988,8 @@ int aew_gradient(aew_handle* h, const float* c_dev, const float* d_obs_dev, floa
     return fail(h, AEW_E_TIMEOUT, "a kernel gave up waiting (bounded mbarrier wait)");
   AEW_CK(aew::launch_finalize_grad(h->c, h->acc64, g_dev, h->C, s));
   ++h->stats.kernel_launches;
+  AEW_CK(cudaEventRecord(h->tg[1], s));
+  h->tg_set = true;
   if (misfit_host || h->cfg.storage == AEW_AE) {
     double J = 0.0;
     int ovf = 0;
@@ -785,6 +1017,31 @@ static int incremental_forward(aew_handle* h, float* dd_out, cudaStream_t s, lon
   *fwd = 0;
   if (h->cfg.storage == AEW_REVOLVE && (rc = zero_state(h, h->st[0], s))) return rc;
   const bool ae = h->cfg.storage == AEW_AE;
+  if (ae && h->tcodec) {
+    // decoder of window tb + 1 on the side stream while window tb's steps run on s;
+    // ev_b[w % 2]: window w decoded, ev_a[w % 2]: window w's incremental steps done
+    const int W = nwin_of(h), T = aew::kTSteps;
+    if ((rc = join(h, s, h->side, h->ev_sync))) return rc;
+    if ((rc = decode_window(h, 0, h->side))) return rc;
+    AEW_CK(cudaEventRecord(h->ev_b[0], h->side));
+    for (int n = 0; n < nt; ++n) {
+      const int tb = n / T;
+      if (n % T == 0) {
+        if (tb + 1 <= W - 1) {
+          if (tb >= 1) AEW_CK(cudaStreamWaitEvent(h->side, h->ev_a[(tb + 1) & 1], 0));
+          if ((rc = decode_window(h, tb + 1, h->side))) return rc;
+          AEW_CK(cudaEventRecord(h->ev_b[(tb + 1) & 1], h->side));
+        }
+        AEW_CK(cudaStreamWaitEvent(s, h->ev_b[tb & 1], 0));
+      }
+      if ((rc = incr_step(h, h->ad[cur], h->ad[cur ^ 1], window_e(h, n), drow(h, dd_out, n + 1), s)))
+        return rc;
+      if (n % T == T - 1 || n == nt - 1) AEW_CK(cudaEventRecord(h->ev_a[tb & 1], s));
+      cur ^= 1;
+      ++*fwd;
+    }
+    return join(h, h->side, s, h->ev_sync2);
+  }
   if (ae) {
     // decode of step n+1 on the side stream while incremental step n runs on s;
     // edb[m % 2] is next read by incremental step m, previously by step m - 2
@@ -859,6 +1116,8 @@ int aew_hessvec(aew_handle* h, const float* dc_dev, float* hdc_dev, void* stream
   cudaStream_t s = S(stream);
   int rc = prepare_dc(h, dc_dev, s);
   if (rc) return rc;
+  h->th_set = false;
+  AEW_CK(cudaEventRecord(h->th[0], s));
   long long fwd = 0;
   if ((rc = incremental_forward(h, h->dd, s, &fwd))) return rc;
   // incremental adjoint: the adjoint solve with residual dd (row 0 unused)
@@ -868,7 +1127,8 @@ int aew_hessvec(aew_handle* h, const float* dc_dev, float* hdc_dev, void* stream
     if ((rc = run_revolve(h, nullptr, h->dd, h->wav.data(), false, s, &f2))) return rc;
     fwd += f2;
   } else if (h->cfg.storage == AEW_AE) {
-    if ((rc = ae_adjoint_sweep(h, h->dd, s))) return rc;
+    if ((rc = h->tcodec ? time_adjoint_sweep(h, h->dd, s) : ae_adjoint_sweep(h, h->dd, s)))
+      return rc;
   } else {
     if ((rc = begin_adjoint(h, s))) return rc;
     int acur = 0;
@@ -883,6 +1143,8 @@ int aew_hessvec(aew_handle* h, const float* dc_dev, float* hdc_dev, void* stream
     return fail(h, AEW_E_TIMEOUT, "a kernel gave up waiting (bounded mbarrier wait)");
   AEW_CK(aew::launch_finalize_grad(h->c, h->acc64, hdc_dev, h->C, s));
   ++h->stats.kernel_launches;
+  AEW_CK(cudaEventRecord(h->th[1], s));
+  h->th_set = true;
   return AEW_OK;
 }
 
@@ -953,6 +1215,7 @@ int aew_codec_get(const aew_handle* h, float* W1, float* b1, float* W2, float* b
 int aew_codec_encode(aew_handle* h, const float* const fields_dev[4], uint16_t* latents_dev,
                      float* block_max_dev, void* stream) {
   if (!h) return AEW_E_ARG;
+  if (h->tcodec) return fail(h, AEW_E_CONFIG, "aew_codec_encode needs the space codec");
   if (!fields_dev || !latents_dev) return fail(h, AEW_E_ARG, "NULL argument");
   if (h->cfg.nx % 8 || h->cfg.ny % 8 || h->cfg.nz % 8)
     return fail(h, AEW_E_CONFIG, "codec needs nx, ny, nz multiples of 8");
@@ -996,6 +1259,7 @@ int aew_codec_decode(aew_handle* h, const uint16_t* latents_dev, long long n, fl
 int aew_codec_decode_e(aew_handle* h, const uint16_t* latents_dev, const float* block_max_dev,
                        float* e_dev, void* stream) {
   if (!h) return AEW_E_ARG;
+  if (h->tcodec) return fail(h, AEW_E_CONFIG, "aew_codec_decode_e needs the space codec");
   if (!latents_dev || !block_max_dev || !e_dev) return fail(h, AEW_E_ARG, "NULL argument");
   if (h->cfg.nx % 8 || h->cfg.ny % 8 || h->cfg.nz % 8)
     return fail(h, AEW_E_CONFIG, "codec needs nx, ny, nz multiples of 8");
@@ -1031,6 +1295,187 @@ int aew_codec_encode_vectors(aew_handle* h, const uint16_t* vectors_dev, long lo
   return AEW_OK;
 }
 
+int aew_codec_encode_window(aew_handle* h, const float* e_dev, int nsteps, uint16_t* latents_dev,
+                            float* vmax_dev, void* stream) {
+  if (!h) return AEW_E_ARG;
+  if (!h->tcodec) return fail(h, AEW_E_CONFIG, "aew_codec_encode_window needs the time codec");
+  if (!e_dev || !latents_dev || nsteps < 1 || nsteps > aew::kTSteps)
+    return fail(h, AEW_E_ARG, "bad argument");
+  if (reinterpret_cast<uintptr_t>(e_dev) & 15) return fail(h, AEW_E_ARG, "e_dev must be 16-byte aligned");
+  if (h->cfg.nx % 8 || h->cfg.ny % 8 || h->cfg.nz % 2)
+    return fail(h, AEW_E_CONFIG, "the time codec needs nx, ny multiples of 8 and nz even");
+  if (!aew::codec_ready(h->codec)) return fail(h, AEW_E_NOCODEC, "codec weights not set");
+  h->err.clear();
+  cudaStream_t s = S(stream);
+  const size_t nv = nvec_of(h);
+  if ((!h->wk_raw && !dalloc(h, &h->wk_raw, nv * aew::kNIn)) ||
+      (!h->wk_vmax && !dalloc(h, &h->wk_vmax, nv)))
+    return fail(h, AEW_E_NOMEM, "workspace");
+  int* ovf = reinterpret_cast<int*>(h->scratch8 + 4);
+  AEW_CK(cudaMemsetAsync(ovf, 0, sizeof(int), s));
+  AEW_CK(aew::window_pack(e_dev, nsteps, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->wk_raw, h->wk_vmax, s));
+  cudaError_t e = aew::codec_encode_window(h->codec, h->wk_raw, h->wk_vmax, (long long)nv,
+                                           latents_dev, ovf, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "codec_encode_window");
+  h->stats.kernel_launches += 3;
+  if (vmax_dev)
+    AEW_CK(cudaMemcpyAsync(vmax_dev, h->wk_vmax, nv * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  if (aew::codec_take_error(h->codec, s))
+    return fail(h, AEW_E_TIMEOUT, "a codec kernel gave up waiting (bounded mbarrier wait)");
+  int o = 0;
+  AEW_CK(cudaMemcpyAsync(&o, ovf, sizeof(int), cudaMemcpyDeviceToHost, s));
+  AEW_CK(cudaStreamSynchronize(s));
+  if (o) return fail(h, AEW_E_OVERFLOW, "a latent overflowed FP16");
+  return AEW_OK;
+}
+
+int aew_codec_decode_window(aew_handle* h, const uint16_t* latents_dev, const float* vmax_dev,
+                            float* e_dev, void* stream) {
+  if (!h) return AEW_E_ARG;
+  if (!h->tcodec) return fail(h, AEW_E_CONFIG, "aew_codec_decode_window needs the time codec");
+  if (!latents_dev || !vmax_dev || !e_dev) return fail(h, AEW_E_ARG, "NULL argument");
+  if (reinterpret_cast<uintptr_t>(e_dev) & 15) return fail(h, AEW_E_ARG, "e_dev must be 16-byte aligned");
+  if (h->cfg.nx % 8 || h->cfg.ny % 8 || h->cfg.nz % 2)
+    return fail(h, AEW_E_CONFIG, "the time codec needs nx, ny multiples of 8 and nz even");
+  if (!aew::codec_ready(h->codec)) return fail(h, AEW_E_NOCODEC, "codec weights not set");
+  h->err.clear();
+  cudaStream_t s = S(stream);
+  cudaError_t e = aew::codec_decode_window(h->codec, latents_dev,
+                                           reinterpret_cast<const unsigned*>(vmax_dev), h->cfg.nx,
+                                           h->cfg.ny, h->cfg.nz, e_dev, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "codec_decode_window");
+  h->stats.kernel_launches += 2;
+  if (aew::codec_take_error(h->codec, s))
+    return fail(h, AEW_E_TIMEOUT, "a codec kernel gave up waiting (bounded mbarrier wait)");
+  return AEW_OK;
+}
+
+int aew_codec_init_pca(aew_handle* h, const uint16_t* vectors_dev, const float* maxima_dev,
+                       long long n, int loss, double* eigvals_host, void* stream) {
+  if (!h) return AEW_E_ARG;
+  if (!vectors_dev || n < 1) return fail(h, AEW_E_ARG, "bad argument");
+  if (reinterpret_cast<uintptr_t>(vectors_dev) & 15)
+    return fail(h, AEW_E_ARG, "vectors_dev must be 16-byte aligned");
+  const bool weighted = loss == AEW_LOSS_STRAIN_AMPLITUDE || loss == AEW_LOSS_STRAIN_ENERGY;
+  if (loss != AEW_LOSS_STATE && !(h->tcodec && (loss == AEW_LOSS_STRAIN || weighted)))
+    return fail(h, AEW_E_ARG, "PCA weights: AEW_LOSS_STATE, or a strain loss with the time codec");
+  if (weighted && !maxima_dev) return fail(h, AEW_E_ARG, "weighted PCA needs the vectors' maxima");
+  const int k = h->cfg.n_lat, nh = aew::codec_nhid(h->codec), I = aew::kNIn;
+  if (2 * k > nh) return fail(h, AEW_E_CONFIG, "the hidden layer must hold 2 n_lat units");
+  h->err.clear();
+  cudaStream_t s = S(stream);
+  double* G = nullptr;
+  double* sm = nullptr;
+  float* wv = nullptr;
+  if (cudaMalloc(&G, (size_t)I * I * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&sm, (I + 1) * sizeof(double)) != cudaSuccess ||
+      (weighted && cudaMalloc(&wv, (size_t)n * sizeof(float)) != cudaSuccess)) {
+    cudaGetLastError();
+    cudaFree(G);
+    cudaFree(sm);
+    cudaFree(wv);
+    return fail(h, AEW_E_NOMEM, "moment buffers");
+  }
+  std::vector<double> Gh((size_t)I * I), sh(I + 1);
+  cudaError_t e = cudaSuccess;
+  if (weighted)   // w_v = s_v (amplitude) or s_v^2 (energy): the scales are powers of two
+    e = aew::vector_weights(maxima_dev, n, loss == AEW_LOSS_STRAIN_AMPLITUDE ? 1 : 2, wv, s);
+  if (e == cudaSuccess) e = aew::codec_moments(h->codec, vectors_dev, n, wv, G, sm, s);
+  cudaFree(wv);
+  if (e == cudaSuccess) e = cudaMemcpy(Gh.data(), G, Gh.size() * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(sh.data(), sm, sh.size() * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(G);
+  cudaFree(sm);
+  h->stats.kernel_launches += 2 + 2 * ((n + 32767) / 32768);
+  if (e != cudaSuccess) return cuda_fail(h, e, "codec_moments");
+  if (aew::codec_take_error(h->codec, s))
+    return fail(h, AEW_E_TIMEOUT, "a codec kernel gave up waiting (bounded mbarrier wait)");
+  const double sw = sh[I];
+  if (!(sw > 0)) return fail(h, AEW_E_ARG, "the weights sum to zero");
+  // weighted covariance (G / sw - mu mu^T), its eigenvectors, the rank-k pair code
+  std::vector<double> mu(I), C((size_t)I * I), w(I), V((size_t)I * I);
+  for (int i = 0; i < I; ++i) mu[i] = sh[i] / sw;
+  for (int i = 0; i < I; ++i)
+    for (int j = 0; j < I; ++j) C[(size_t)i * I + j] = Gh[(size_t)i * I + j] / sw - mu[i] * mu[j];
+  if (!aew::sym_eig(I, C.data(), w.data(), V.data()))
+    return fail(h, AEW_E_CUDA, "the symmetric eigensolver did not converge");
+  const size_t szs[8] = {(size_t)I * nh, (size_t)nh, (size_t)nh * k, (size_t)k,
+                         (size_t)k * nh, (size_t)nh, (size_t)nh * I, (size_t)I};
+  std::vector<std::vector<float>> W(8);
+  for (int i = 0; i < 8; ++i) W[i].resize(szs[i]);
+  aew::pca_pair_weights(I, nh, k, mu.data(), V.data(), W[0].data(), W[1].data(), W[2].data(),
+                        W[3].data(), W[4].data(), W[5].data(), W[6].data(), W[7].data());
+  const float* wp[8];
+  for (int i = 0; i < 8; ++i) wp[i] = W[i].data();
+  e = aew::codec_set_weights(h->codec, wp);
+  if (e != cudaSuccess) return cuda_fail(h, e, "codec_set_weights");
+  aew::codec_reset_training(h->codec);
+  if (eigvals_host) std::memcpy(eigvals_host, w.data(), I * sizeof(double));
+  return AEW_OK;
+}
+
+int aew_profile_steps(aew_handle* h, const float* c_dev, int kind, int nsteps, double* ms_host,
+                      void* stream) {
+  if (!h) return AEW_E_ARG;
+  if (kind < 0 || kind > 5 || nsteps < 1 || !ms_host) return fail(h, AEW_E_ARG, "bad argument");
+  const bool tw = h->cfg.storage == AEW_AE && h->tcodec;
+  if ((kind == 1 || kind >= 4) && !tw)
+    return fail(h, AEW_E_CONFIG, "this kernel needs AE storage with the time codec");
+  if (kind >= 4 && !aew::codec_ready(h->codec)) return fail(h, AEW_E_NOCODEC, "codec weights not set");
+  h->err.clear();
+  cudaStream_t s = S(stream);
+  int rc = prepare_c(h, c_dev, s);
+  if (rc) return rc;
+  h->have_grad = false;
+  const int nt = h->cfg.nt, T = aew::kTSteps;
+  cudaEvent_t e0, e1;
+  AEW_CK(cudaEventCreate(&e0));
+  AEW_CK(cudaEventCreate(&e1));
+  AEW_CK(cudaEventRecord(e0, s));
+  int cur = 0;
+  for (int k = 0; k < nsteps && rc == AEW_OK; ++k) {
+    const int n = k % nt;
+    switch (kind) {
+      case 0:
+        rc = fwd_step(h, n, h->st[cur], h->st[cur ^ 1], h->wav.data(), nullptr, s);
+        break;
+      case 1:
+        rc = fwd_step(h, n, h->st[cur], h->st[cur ^ 1], h->wav.data(), nullptr, s, nullptr,
+                      nullptr, nullptr, h->xt[0], (n + 1) % T, h->vmx);
+        break;
+      case 2:
+        rc = adj_step(h, nt - 1 - n, cur, h->R, h->st[0][0], s);
+        break;
+      case 3:
+        rc = incr_step(h, h->ad[cur], h->ad[cur ^ 1], h->st[0][0], nullptr, s);
+        break;
+      case 4:
+        rc = encode_window(h, 0, s);
+        break;
+      case 5:
+        rc = decode_window(h, 0, s);
+        break;
+    }
+    cur ^= 1;
+  }
+  AEW_CK(cudaEventRecord(e1, s));
+  AEW_CK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  if (aew::codec_take_error(h->codec, s))
+    return fail(h, AEW_E_TIMEOUT, "a kernel gave up waiting (bounded mbarrier wait)");
+  *ms_host = ms / nsteps;
+  return AEW_OK;
+}
+
+int aew_sym_eig(int n, const double* A_host, double* w_host, double* V_host) {
+  if (n < 1 || !A_host || !w_host || !V_host) return AEW_E_ARG;
+  return aew::sym_eig(n, A_host, w_host, V_host) ? AEW_OK : AEW_E_ARG;
+}
+
 int aew_snapshots(aew_handle* h, const float* c_dev, int every, uint16_t* out_dev,
                   long long max_vectors, float* block_max_dev, long long* n_written,
                   void* stream) {
@@ -1041,10 +1486,18 @@ int aew_snapshots(aew_handle* h, const float* c_dev, int every, uint16_t* out_de
     return fail(h, AEW_E_ARG, "out_dev must be 16-byte aligned");
   if (reinterpret_cast<uintptr_t>(block_max_dev) & 15)
     return fail(h, AEW_E_ARG, "block_max_dev must be 16-byte aligned");
-  if (h->cfg.nx % 8 || h->cfg.ny % 8 || h->cfg.nz % 8)
-    return fail(h, AEW_E_CONFIG, "snapshots need nx, ny, nz multiples of 8");
   h->err.clear();
   cudaStream_t s = S(stream);
+  if (h->tcodec) {
+    if (h->cfg.nx % 8 || h->cfg.ny % 8 || h->cfg.nz % 2)
+      return fail(h, AEW_E_CONFIG, "time-codec snapshots need nx, ny multiples of 8 and nz even");
+    int rc = prepare_c(h, c_dev, s);
+    if (rc) return rc;
+    h->have_grad = false;
+    return snapshots_time(h, every, out_dev, max_vectors, block_max_dev, n_written, s);
+  }
+  if (h->cfg.nx % 8 || h->cfg.ny % 8 || h->cfg.nz % 8)
+    return fail(h, AEW_E_CONFIG, "snapshots need nx, ny, nz multiples of 8");
   int rc = prepare_c(h, c_dev, s);
   if (rc) return rc;
   h->have_grad = false;
@@ -1082,6 +1535,45 @@ int aew_snapshots(aew_handle* h, const float* c_dev, int every, uint16_t* out_de
   }
   AEW_CK(cudaStreamSynchronize(s));
   *n_written = written;
+  return AEW_OK;
+}
+
+int aew_codec_train(aew_handle* h, const uint16_t* vectors_dev, const float* maxima_dev,
+                    long long n, const aew_train_cfg* cfg, double* epoch_loss_host, void* stream) {
+  if (!h) return AEW_E_ARG;
+  if (!vectors_dev || !cfg || n < 1) return fail(h, AEW_E_ARG, "bad argument");
+  if (cfg->loss < AEW_LOSS_STATE || cfg->loss > AEW_LOSS_STRAIN_ENERGY)
+    return fail(h, AEW_E_ARG, "unknown loss");
+  if (!aew::codec_ready(h->codec)) return fail(h, AEW_E_NOCODEC, "codec weights not set");
+  if (reinterpret_cast<uintptr_t>(vectors_dev) & 15)
+    return fail(h, AEW_E_ARG, "vectors_dev must be 16-byte aligned");
+  h->err.clear();
+  cudaStream_t s = S(stream);
+  aew::TrainCfg tc{cfg->epochs, cfg->batch, cfg->halve_every, cfg->loss, cfg->lr0, cfg->seed};
+  cudaError_t e = aew::codec_train(h->codec, vectors_dev, maxima_dev, n, tc, epoch_loss_host, s,
+                                   &h->err);
+  if (e == cudaErrorInvalidValue && !h->err.empty()) return AEW_E_ARG;
+  if (e != cudaSuccess) return cuda_fail(h, e, "codec_train");
+  h->stats.kernel_launches += (long long)cfg->epochs * (n / (cfg->batch > 0 ? cfg->batch : 1)) * 30;
+  if (aew::codec_take_error(h->codec, s))
+    return fail(h, AEW_E_TIMEOUT, "a codec kernel gave up waiting (bounded mbarrier wait)");
+  return AEW_OK;
+}
+
+int aew_codec_eval(aew_handle* h, const uint16_t* vectors_dev, const float* maxima_dev,
+                   long long n, double* err_host, void* stream) {
+  if (!h) return AEW_E_ARG;
+  if (!vectors_dev || !maxima_dev || !err_host || n < 1) return fail(h, AEW_E_ARG, "bad argument");
+  if (!aew::codec_ready(h->codec)) return fail(h, AEW_E_NOCODEC, "codec weights not set");
+  h->err.clear();
+  cudaStream_t s = S(stream);
+  cudaError_t e = aew::codec_eval(h->codec, vectors_dev, maxima_dev, n, err_host, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "codec_eval");
+  h->stats.kernel_launches += 3 * ((n + 16383) / 16384) + 2;
+  if (aew::codec_take_error(h->codec, s))
+    return fail(h, AEW_E_TIMEOUT, "a codec kernel gave up waiting (bounded mbarrier wait)");
+  h->stats.decoded_err_normalised = err_host[0];
+  h->stats.decoded_err_physical = err_host[5];
   return AEW_OK;
 }
 

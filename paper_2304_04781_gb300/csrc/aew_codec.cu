@@ -17,6 +17,8 @@
 #include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -69,11 +71,12 @@ cudaError_t transpose16(const float* src, int rows, int cols, uint16_t* dst, boo
 // ---------------------------------------------------------------------------------
 // Epilogues
 // ---------------------------------------------------------------------------------
-// H[row][col..] = bf16(gelu(acc + bias))
+// H[row][col..] = bf16(gelu(acc + bias)), row stride ld
 struct EpBiasGeluH {
   const float* bias;
   uint16_t* H;
   long long M;
+  int ld;
   __device__ __forceinline__ void operator()(long long row, int col, const float (&v)[32]) const {
     if (row >= M) return;
     const float4* bq = reinterpret_cast<const float4*>(bias + col);
@@ -84,9 +87,80 @@ struct EpBiasGeluH {
       pk[j / 2] = gemm::pack_bf16(gemm::gelu_fast(v[j] + b.x), gemm::gelu_fast(v[j + 1] + b.y));
       pk[j / 2 + 1] = gemm::pack_bf16(gemm::gelu_fast(v[j + 2] + b.z), gemm::gelu_fast(v[j + 3] + b.w));
     }
-    uint4* dst = reinterpret_cast<uint4*>(H + row * kNHid + col);
+    uint4* dst = reinterpret_cast<uint4*>(H + row * ld + col);
 #pragma unroll
     for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+  }
+};
+
+// Encoder layer 1 of the time codec on raw (unnormalised) BF16 window vectors:
+// H[row][col..] = bf16(gelu(acc / s_row + bias)), s_row the vector's power-of-two scale
+// from its max |e| (vmax, float bits).  Dividing the FP32 sum by a power of two equals
+// summing the normalised products (the scale commutes with every rounding involved).
+struct EpScaleGeluH {
+  const float* bias;
+  const unsigned* vmax;
+  uint16_t* H;
+  long long M;
+  int ld;
+  __device__ __forceinline__ void operator()(long long row, int col, const float (&v)[32]) const {
+    if (row >= M) return;
+    const float is = gemm::block_inv_scale(__uint_as_float(__ldg(vmax + row)));
+    const float4* bq = reinterpret_cast<const float4*>(bias + col);
+    uint32_t pk[16];
+#pragma unroll
+    for (int j = 0; j < 32; j += 4) {
+      const float4 b = __ldg(bq + j / 4);
+      pk[j / 2] = gemm::pack_bf16(gemm::gelu_fast(fmaf(v[j], is, b.x)),
+                                  gemm::gelu_fast(fmaf(v[j + 1], is, b.y)));
+      pk[j / 2 + 1] = gemm::pack_bf16(gemm::gelu_fast(fmaf(v[j + 2], is, b.z)),
+                                      gemm::gelu_fast(fmaf(v[j + 3], is, b.w)));
+    }
+    uint4* dst = reinterpret_cast<uint4*>(H + row * ld + col);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+  }
+};
+
+// Decoder layer 2 of the time codec, scattered to the window's strain slices:
+// column n = t*128 + z*64 + y*8 + x of vector row (bz, by, bx) -> slice t, node
+// (2bz + z, 8by + y, 8bx + x); e = (acc + b4[n]) * s_row, 0 on boundary nodes.
+// A 32-column group is 4 rows of 8 nodes: two float4 stores per row.
+struct EpDecWindow {
+  const float* b4;
+  const unsigned* vmax;
+  float* e;               // slice 0 of [16][nz][ny][nx]
+  int nx, ny, nz, NBx, NBy;
+  long long M;            // vectors (< 2^31)
+  size_t slice;           // nx ny nz
+  __device__ __forceinline__ void operator()(long long rw, int col, const float (&v)[32]) const {
+    if (rw >= M) return;
+    const int r = (int)rw;
+    const int bx = r % NBx, q = r / NBx;
+    const int by = q % NBy, bz = q / NBy;
+    const float sc = gemm::block_scale(__uint_as_float(__ldg(vmax + r)));
+    const int t = col >> 7, z = (col >> 6) & 1, y0 = (col & 63) >> 3;
+    const int kz = 2 * bz + z;
+    const bool zb = kz == 0 || kz == nz - 1;
+    const bool xlo = bx == 0, xhi = bx == NBx - 1;
+    float* base = e + (size_t)t * slice + ((size_t)kz * ny + 8 * by + y0) * nx + 8 * bx;
+    const float4* bq = reinterpret_cast<const float4*>(b4 + col);
+#pragma unroll
+    for (int yy = 0; yy < 4; ++yy) {
+      const int jy = 8 * by + y0 + yy;
+      const bool yb = zb || jy == 0 || jy == ny - 1;
+      const float4 blo = __ldg(bq + 2 * yy), bhi = __ldg(bq + 2 * yy + 1);
+      const float bv[8] = {blo.x, blo.y, blo.z, blo.w, bhi.x, bhi.y, bhi.z, bhi.w};
+      float o[8];
+#pragma unroll
+      for (int x = 0; x < 8; ++x) {
+        const float val = (v[yy * 8 + x] + bv[x]) * sc;
+        o[x] = (yb || (x == 0 && xlo) || (x == 7 && xhi)) ? 0.f : val;
+      }
+      float4* dst = reinterpret_cast<float4*>(base + (size_t)yy * nx);
+      dst[0] = make_float4(o[0], o[1], o[2], o[3]);
+      dst[1] = make_float4(o[4], o[5], o[6], o[7]);
+    }
   }
 };
 
@@ -225,7 +299,7 @@ bool ensure_H(Codec* c, size_t rows) {
   if (c->H) cudaFree(c->H);
   c->H = nullptr;
   c->H_rows = 0;
-  if (cudaMalloc(&c->H, rows * kNHid * sizeof(uint16_t)) != cudaSuccess) {
+  if (cudaMalloc(&c->H, rows * (size_t)c->n_hid * sizeof(uint16_t)) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
@@ -290,6 +364,182 @@ __global__ void normalise_kernel(const uint16_t* raw, const unsigned* __restrict
     *reinterpret_cast<uint4*>(out + b * kNIn + k) = make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
+
+// Strain fields e[t][nz][ny][nx] (t < nsteps; later slots 0) -> raw BF16 window
+// vectors [nvec][2048], k = t*128 + z*64 + y*8 + x, and max |e| per vector (atomicMax;
+// vmax zeroed by the caller).  One thread per float4 of a grid row; the two threads of
+// an 8-node row combine their maxima by shuffle.
+__global__ void window_pack_kernel(const float* __restrict__ e, int nsteps, int nx, int ny,
+                                   int nz, uint16_t* __restrict__ raw, unsigned* vmax) {
+  const int xq_n = nx >> 2;
+  const long long total = (long long)kTSteps * nz * ny * xq_n;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long iters = (total + stride - 1) / stride;
+  const int NBx = nx >> 3, NBy = ny >> 3;
+  for (long long q = 0; q < iters; ++q) {
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x + q * stride;
+    const bool live = t0 < total;
+    const int xq = live ? (int)(t0 % xq_n) : 0;
+    long long r = live ? t0 / xq_n : 0;
+    const int y = (int)(r % ny);
+    r /= ny;
+    const int z = (int)(r % nz);
+    const int t = (int)(r / nz);
+    const long long v = ((long long)(z >> 1) * NBy + (y >> 3)) * NBx + (xq >> 1);
+    float m = 0.f;
+    if (live) {
+      float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (t < nsteps)
+        a = *reinterpret_cast<const float4*>(e + (((size_t)t * nz + z) * ny + y) * nx + 4 * (size_t)xq);
+      *reinterpret_cast<uint2*>(raw + v * kNIn + t * 128 + (z & 1) * 64 + (y & 7) * 8 + 4 * (xq & 1)) =
+          make_uint2(gemm::pack_bf16(a.x, a.y), gemm::pack_bf16(a.z, a.w));
+      m = fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w)));
+    }
+    // xq and xq ^ 1 are adjacent lanes (xq_n is even) and share vector v
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+    if (live && (xq & 1) == 0 && m > 0.f) atomicMax(vmax + v, __float_as_uint(m));
+  }
+}
+
+// y = x * 2^-e per vector (exact), from raw BF16 window vectors and their maxima; out
+// may be raw itself (each thread rewrites only the 16 bytes it read)
+__global__ void window_normalise_kernel(const uint16_t* raw, const unsigned* __restrict__ vmax,
+                                        long long n, uint16_t* out) {
+  const long long total = n * (kNIn / 8);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long b = t / (kNIn / 8);
+    const int k = (int)(t % (kNIn / 8)) * 8;
+    const float sc = gemm::block_inv_scale(__uint_as_float(vmax[b]));
+    uint4 v = *reinterpret_cast<const uint4*>(raw + b * kNIn + k);
+    uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      w[j] = gemm::pack_bf16(__uint_as_float(w[j] << 16) * sc, __uint_as_float(w[j] & 0xffff0000u) * sc);
+    *reinterpret_cast<uint4*>(out + b * kNIn + k) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+// Moments of the PCA initialisation.  YT[i][v] = bf16(sqrt(w[n0 + v]) Y[n0 + v][i]) for
+// v < nc, 0 for nc <= v < ncp (32 x 32 tiles through shared memory).
+__global__ void moment_transpose_kernel(const uint16_t* __restrict__ Y, long long n0, int nc,
+                                        int ncp, const float* __restrict__ w,
+                                        uint16_t* __restrict__ YT, int ldT) {
+  __shared__ uint16_t tile[32][34];
+  const int i0 = blockIdx.x * 32, v0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int v = v0 + r, i = i0 + threadIdx.x;
+    uint16_t b = 0;
+    if (v < nc) {
+      const uint16_t y = Y[(size_t)(n0 + v) * kNIn + i];
+      b = w ? gemm::bf16_bits(gemm::bf16_val(y) * sqrtf(w[n0 + v])) : y;
+    }
+    tile[r][threadIdx.x] = b;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int i = i0 + r, v = v0 + threadIdx.x;
+    if (v < ncp) YT[(size_t)i * ldT + v] = tile[threadIdx.x][r];
+  }
+}
+
+// per-block partial sums part[b][0..2047] = sum_v w_v y_v, part[b][2048] = sum_v w_v over
+// the vectors v = b, b + gridDim.x, ...; thread t owns columns 8t .. 8t + 7
+__global__ void moment_sum_kernel(const uint16_t* __restrict__ Y, long long n,
+                                  const float* __restrict__ w, double* __restrict__ part) {
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  double sw = 0.0;
+  for (long long v = blockIdx.x; v < n; v += gridDim.x) {
+    const double wv = w ? (double)w[v] : 1.0;
+    const uint4 q = *reinterpret_cast<const uint4*>(Y + (size_t)v * kNIn + 8 * threadIdx.x);
+    const uint32_t u[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      acc[2 * j] += wv * (double)__uint_as_float(u[j] << 16);
+      acc[2 * j + 1] += wv * (double)__uint_as_float(u[j] & 0xffff0000u);
+    }
+    sw += wv;
+  }
+  double* out = part + (size_t)blockIdx.x * (kNIn + 1);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) out[8 * threadIdx.x + j] = acc[j];
+  if (threadIdx.x == 0) out[kNIn] = sw;
+}
+
+// s64[i] = sum over blocks of part[b][i], in block order (deterministic)
+__global__ void moment_reduce_kernel(const double* __restrict__ part, int nblk,
+                                     double* __restrict__ s64) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > kNIn) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += part[(size_t)b * (kNIn + 1) + i];
+  s64[i] = s;
+}
+
+// Decoded-error sums of a chunk of vectors: acc[f] += sum (yh - y)^2, acc[4 + f] +=
+// sum y^2, acc[8 + f] and acc[12 + f] the same times s^2 (physical units), per field f
+// (time codec: every column is field 0).  One warp per vector, grid-stride; one set of
+// atomics per block.
+__global__ void eval_err_kernel(const uint16_t* __restrict__ Y, const float* __restrict__ Yh,
+                                const float* __restrict__ mx, int time, int nc,
+                                double* __restrict__ acc) {
+  __shared__ double sh[8][16];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double a[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) a[j] = 0.0;
+  for (int v = blockIdx.x * 8 + wid; v < nc; v += gridDim.x * 8) {
+    float sc[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+      sc[f] = gemm::block_scale(time ? mx[v] : mx[(size_t)v * 4 + f]);
+    for (int k = lane; k < kNIn; k += 32) {
+      const int f = time ? 0 : ((k >> 6) & 3);
+      const double y = (double)gemm::bf16_val(Y[(size_t)v * kNIn + k]);
+      const double d = (double)Yh[(size_t)v * kNIn + k] - y;
+      const double s2 = (double)sc[f] * (double)sc[f];
+#pragma unroll
+      for (int g = 0; g < 4; ++g)
+        if (g == f) {
+          a[g] += d * d;
+          a[4 + g] += y * y;
+          a[8 + g] += d * d * s2;
+          a[12 + g] += y * y * s2;
+        }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 16; ++j)
+    for (int o = 16; o > 0; o >>= 1) a[j] += __shfl_xor_sync(0xffffffffu, a[j], o);
+  if (lane == 0)
+    for (int j = 0; j < 16; ++j) sh[wid][j] = a[j];
+  __syncthreads();
+  if (threadIdx.x < 16) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += sh[w][threadIdx.x];
+    atomicAdd(acc + threadIdx.x, t);
+  }
+}
+
+__global__ void vector_weights_kernel(const float* __restrict__ mx, long long n, int pw,
+                                      float* __restrict__ w) {
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+       v += (long long)gridDim.x * blockDim.x) {
+    const float sc = gemm::block_scale(mx[v]);
+    w[v] = pw == 1 ? sc : sc * sc;
+  }
+}
+
+// G64[row][col..] += acc (one tile owns each element: no atomics)
+struct EpGramAcc {
+  double* G;
+  __device__ __forceinline__ void operator()(long long row, int col, const float (&v)[32]) const {
+    if (row >= kNIn) return;
+    double* g = G + row * kNIn + col;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) g[j] += (double)v[j];
+  }
+};
 
 // strain rows of W4t (vector index z*256 + j, j < 64) packed as W4e [512][512]
 __global__ void strain_rows_kernel(const uint16_t* __restrict__ W4t, uint16_t* __restrict__ W4e) {
@@ -357,23 +607,24 @@ cudaError_t launch_activation_probe(const float* x, float* y, float* dy, long lo
   return cudaGetLastError();
 }
 
-Codec* codec_new(int n_lat) {
+Codec* codec_new(int n_lat, bool time) {
   Codec* c = new Codec();
   c->n_lat = n_lat;
-  const size_t nl = (size_t)n_lat;
-  const size_t sz[8] = {(size_t)kNIn * kNHid, kNHid, kNHid * nl, nl, nl * kNHid, kNHid,
-                        (size_t)kNHid * kNIn, kNIn};
+  c->time = time;
+  c->n_hid = time ? 2 * n_lat : kNHid;
+  const size_t nl = (size_t)n_lat, nh = (size_t)c->n_hid;
+  const size_t sz[8] = {(size_t)kNIn * nh, nh, nh * nl, nl, nl * nh, nh, nh * kNIn, kNIn};
   bool ok = true;
   for (int i = 0; i < 8 && ok; ++i) {
     c->wn[i] = sz[i];
     ok = cudaMalloc(&c->w[i], sz[i] * sizeof(float)) == cudaSuccess;
     c->bytes += sz[i] * sizeof(float);
   }
-  ok = ok && cudaMalloc(&c->W1t, (size_t)kNIn * kNHid * 2) == cudaSuccess &&
-       cudaMalloc(&c->W2t, nl * kNHid * 2) == cudaSuccess &&
-       cudaMalloc(&c->W3t, nl * kNHid * 2) == cudaSuccess &&
-       cudaMalloc(&c->W4t, (size_t)kNIn * kNHid * 2) == cudaSuccess &&
-       cudaMalloc(&c->W4e, (size_t)512 * kNHid * 2) == cudaSuccess &&
+  ok = ok && cudaMalloc(&c->W1t, (size_t)kNIn * nh * 2) == cudaSuccess &&
+       cudaMalloc(&c->W2t, nl * nh * 2) == cudaSuccess &&
+       cudaMalloc(&c->W3t, nl * nh * 2) == cudaSuccess &&
+       cudaMalloc(&c->W4t, (size_t)kNIn * nh * 2) == cudaSuccess &&
+       (time || cudaMalloc(&c->W4e, (size_t)512 * kNHid * 2) == cudaSuccess) &&
        cudaMalloc(&c->err, sizeof(int)) == cudaSuccess &&
        cudaMalloc(&c->sc_tmp, 4 * sizeof(float)) == cudaSuccess;
   if (!ok) {
@@ -385,7 +636,7 @@ Codec* codec_new(int n_lat) {
   if (const char* env = getenv("AEW_GEMM_CTAS")) c->max_ctas = atoi(env);   // tuning override
   if (const char* env = getenv("AEW_GEMM_STAGES")) c->max_stages = atoi(env);   // tuning override
   if (const char* env = getenv("AEW_GEMM_PAIR")) c->pair_gemm = atoi(env) != 0;  // tuning override
-  c->bytes += ((size_t)2 * kNIn * kNHid + 2 * nl * kNHid) * 2;
+  c->bytes += ((size_t)2 * kNIn * nh + 2 * nl * nh + (time ? 0 : (size_t)512 * kNHid)) * 2;
   return c;
 }
 
@@ -406,6 +657,11 @@ void codec_free(Codec* c) {
 }
 
 int codec_nlat(const Codec* c) { return c->n_lat; }
+int codec_nhid(const Codec* c) { return c->n_hid; }
+void codec_reset_training(Codec* c) {
+  if (c->train) train_state_free(c->train);
+  c->train = nullptr;
+}
 
 int* codec_err_flag(Codec* c) { return c->err; }
 
@@ -418,19 +674,20 @@ bool codec_take_error(Codec* c, cudaStream_t s) {
   return v != 0;
 }
 size_t codec_device_bytes(const Codec* c) {
-  return c->bytes + c->H_rows * kNHid * 2 + c->X_rows * kNIn * 2 +
+  return c->bytes + c->H_rows * (size_t)c->n_hid * 2 + c->X_rows * kNIn * 2 +
          (c->train ? train_state_bytes(c->train) : 0);
 }
 bool codec_ready(const Codec* c) { return c && c->ready; }
 
 // refresh the tensor-core operand copies from the FP32 masters
 cudaError_t codec_refresh(Codec* c, cudaStream_t s) {
-  const int nl = c->n_lat;
+  const int nl = c->n_lat, nh = c->n_hid;
   cudaError_t e;
-  if ((e = transpose16(c->w[0], kNIn, kNHid, c->W1t, false, s)) != cudaSuccess) return e;
-  if ((e = transpose16(c->w[2], kNHid, nl, c->W2t, false, s)) != cudaSuccess) return e;
-  if ((e = transpose16(c->w[4], nl, kNHid, c->W3t, true, s)) != cudaSuccess) return e;
-  if ((e = transpose16(c->w[6], kNHid, kNIn, c->W4t, false, s)) != cudaSuccess) return e;
+  if ((e = transpose16(c->w[0], kNIn, nh, c->W1t, false, s)) != cudaSuccess) return e;
+  if ((e = transpose16(c->w[2], nh, nl, c->W2t, false, s)) != cudaSuccess) return e;
+  if ((e = transpose16(c->w[4], nl, nh, c->W3t, true, s)) != cudaSuccess) return e;
+  if ((e = transpose16(c->w[6], nh, kNIn, c->W4t, false, s)) != cudaSuccess) return e;
+  if (c->time) return cudaSuccess;
   strain_rows_kernel<<<512, 128, 0, s>>>(c->W4t, c->W4e);
   return cudaGetLastError();
 }
@@ -467,30 +724,38 @@ cudaError_t codec_encode_grid(Codec* c, const float* const f[4], int nx, int ny,
 
 static int ctas_of(const Codec* c, int ctas) { return ctas > 0 ? ctas : c->max_ctas; }
 
+// encoder layer 2: latents = fp16(H W2 + b2) from the hidden activations in c->H
+static cudaError_t encode_layer2(Codec* c, long long n, uint16_t* lat, int* overflow,
+                                 cudaStream_t s, int g) {
+  const int nl = c->n_lat, nh = c->n_hid;
+  EpLatent e2{c->w[3], lat, nl, n, overflow};
+  const gemm::Mat a2{c->H, n, nh}, b2{c->W2t, nl, nh};
+  if (nl == 64) return gemm::launch<64, true>(n, nl, nh, a2, b2, e2, c->err, s, g, c->max_stages);
+  if (nl == 32) return gemm::launch<32, true>(n, nl, nh, a2, b2, e2, c->err, s, g, c->max_stages);
+  return gemm::launch<256, true>(n, nl, nh, a2, b2, e2, c->err, s, g, c->max_stages);
+}
+
 cudaError_t codec_encode_vectors(Codec* c, const uint16_t* vec, long long n, uint16_t* lat,
                                  int* overflow, cudaStream_t s, int ctas) {
   if (!ensure_H(c, (size_t)n)) return cudaErrorMemoryAllocation;
   const int g = ctas_of(c, ctas);
-  EpBiasGeluH ep{c->w[1], c->H, n};
-  const gemm::Mat a1{vec, n, kNIn}, b1{c->W1t, kNHid, kNIn};
+  const int nh = c->n_hid;
+  EpBiasGeluH ep{c->w[1], c->H, n, nh};
+  const gemm::Mat a1{vec, n, kNIn}, b1{c->W1t, nh, kNIn};
   cudaError_t e = c->pair_gemm && c->max_stages == 0
-                      ? gemm2::launch<true>(n, kNHid, kNIn, a1, b1, ep, c->err, s, g)
-                      : gemm::launch<256, true>(n, kNHid, kNIn, a1, b1, ep, c->err, s, g, c->max_stages);
+                      ? gemm2::launch<true>(n, nh, kNIn, a1, b1, ep, c->err, s, g)
+                      : gemm::launch<256, true>(n, nh, kNIn, a1, b1, ep, c->err, s, g, c->max_stages);
   if (e != cudaSuccess) return e;
-  const int nl = c->n_lat;
-  EpLatent e2{c->w[3], lat, nl, n, overflow};
-  const gemm::Mat a2{c->H, n, kNHid}, b2{c->W2t, nl, kNHid};
-  if (nl == 64) return gemm::launch<64, true>(n, nl, kNHid, a2, b2, e2, c->err, s, g, c->max_stages);
-  return gemm::launch<32, true>(n, nl, kNHid, a2, b2, e2, c->err, s, g, c->max_stages);
+  return encode_layer2(c, n, lat, overflow, s, g);
 }
 
 static cudaError_t decode_hidden(Codec* c, const uint16_t* lat, long long nb, cudaStream_t s,
                                  int ctas) {
   if (!ensure_H(c, (size_t)nb)) return cudaErrorMemoryAllocation;
-  const int nl = c->n_lat;
-  EpBiasGeluH ep{c->w[5], c->H, nb};
-  return gemm::launch<256, false>(nb, kNHid, nl, gemm::Mat{lat, nb, nl},
-                                  gemm::Mat{c->W3t, kNHid, nl}, ep, c->err, s, ctas_of(c, ctas),
+  const int nl = c->n_lat, nh = c->n_hid;
+  EpBiasGeluH ep{c->w[5], c->H, nb, nh};
+  return gemm::launch<256, false>(nb, nh, nl, gemm::Mat{lat, nb, nl},
+                                  gemm::Mat{c->W3t, nh, nl}, ep, c->err, s, ctas_of(c, ctas),
                                   c->max_stages);
 }
 
@@ -529,9 +794,151 @@ cudaError_t codec_decode_vectors(Codec* c, const uint16_t* lat, long long nvec, 
                                  cudaStream_t s) {
   cudaError_t e = decode_hidden(c, lat, nvec, s, 0);
   if (e != cudaSuccess) return e;
+  const int nh = c->n_hid;
   EpVec ep{c->w[7], out, kNIn, nvec};
-  return gemm::launch<256, true>(nvec, kNIn, kNHid, gemm::Mat{c->H, nvec, kNHid},
-                                 gemm::Mat{c->W4t, kNIn, kNHid}, ep, c->err, s, c->max_ctas, c->max_stages);
+  return gemm::launch<256, true>(nvec, kNIn, nh, gemm::Mat{c->H, nvec, nh},
+                                 gemm::Mat{c->W4t, kNIn, nh}, ep, c->err, s, c->max_ctas, c->max_stages);
+}
+
+// ---------------------------------------------------------------------------------
+// Compression in time
+// ---------------------------------------------------------------------------------
+cudaError_t codec_encode_window(Codec* c, const uint16_t* raw, const unsigned* vmax,
+                                long long nvec, uint16_t* lat, int* overflow, cudaStream_t s,
+                                int ctas) {
+  if (!ensure_H(c, (size_t)nvec)) return cudaErrorMemoryAllocation;
+  const int g = ctas_of(c, ctas);
+  const int nh = c->n_hid;
+  EpScaleGeluH ep{c->w[1], vmax, c->H, nvec, nh};
+  const gemm::Mat a1{raw, nvec, kNIn}, b1{c->W1t, nh, kNIn};
+  cudaError_t e = c->pair_gemm && c->max_stages == 0
+                      ? gemm2::launch<true>(nvec, nh, kNIn, a1, b1, ep, c->err, s, g)
+                      : gemm::launch<256, true>(nvec, nh, kNIn, a1, b1, ep, c->err, s, g, c->max_stages);
+  if (e != cudaSuccess) return e;
+  return encode_layer2(c, nvec, lat, overflow, s, g);
+}
+
+cudaError_t codec_decode_window(Codec* c, const uint16_t* lat, const unsigned* vmax, int nx,
+                                int ny, int nz, float* e_out, cudaStream_t s, int ctas) {
+  const int NBx = nx / 8, NBy = ny / 8, NBz = nz / 2;
+  const long long nvec = (long long)NBx * NBy * NBz;
+  if (nvec >= (1LL << 31)) return cudaErrorInvalidValue;
+  cudaError_t e = decode_hidden(c, lat, nvec, s, ctas);
+  if (e != cudaSuccess) return e;
+  const int nh = c->n_hid;
+  EpDecWindow ep{c->w[7], vmax, e_out, nx, ny, nz, NBx, NBy, nvec, (size_t)nx * ny * nz};
+  return gemm::launch<256, true>(nvec, kNIn, nh, gemm::Mat{c->H, nvec, nh},
+                                 gemm::Mat{c->W4t, kNIn, nh}, ep, c->err, s, ctas_of(c, ctas),
+                                 c->max_stages);
+}
+
+cudaError_t window_pack(const float* e, int nsteps, int nx, int ny, int nz, uint16_t* raw,
+                        unsigned* vmax, cudaStream_t s) {
+  const long long nvec = (long long)(nx / 8) * (ny / 8) * (nz / 2);
+  cudaError_t err = cudaMemsetAsync(vmax, 0, (size_t)nvec * sizeof(unsigned), s);
+  if (err != cudaSuccess) return err;
+  const long long total = (long long)kTSteps * nz * ny * (nx / 4);
+  long long blocks = (total + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  window_pack_kernel<<<(unsigned)blocks, 256, 0, s>>>(e, nsteps, nx, ny, nz, raw, vmax);
+  return cudaGetLastError();
+}
+
+cudaError_t codec_moments(Codec* c, const uint16_t* Y, long long n, const float* w, double* G64,
+                          double* s64, cudaStream_t s) {
+  constexpr int kChunk = 32768;   // vectors per GEMM (K); 128 MB of transposed BF16
+  constexpr int kPartBlocks = 1024;
+  uint16_t* YT = nullptr;
+  double* part = nullptr;
+  cudaError_t e = cudaMalloc(&YT, (size_t)kNIn * kChunk * sizeof(uint16_t));
+  if (e == cudaSuccess) e = cudaMalloc(&part, (size_t)kPartBlocks * (kNIn + 1) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemsetAsync(G64, 0, (size_t)kNIn * kNIn * sizeof(double), s);
+  if (e == cudaSuccess && n > 0) {
+    moment_sum_kernel<<<kPartBlocks, kNIn / 8, 0, s>>>(Y, n, w, part);
+    e = cudaGetLastError();
+  } else if (e == cudaSuccess) {
+    e = cudaMemsetAsync(part, 0, (size_t)kPartBlocks * (kNIn + 1) * sizeof(double), s);
+  }
+  if (e == cudaSuccess) {
+    moment_reduce_kernel<<<(kNIn + 1 + 255) / 256, 256, 0, s>>>(part, kPartBlocks, s64);
+    e = cudaGetLastError();
+  }
+  for (long long n0 = 0; e == cudaSuccess && n0 < n; n0 += kChunk) {
+    const int nc = (int)std::min<long long>(kChunk, n - n0);
+    const int ncp = (nc + 63) / 64 * 64;
+    dim3 grid(kNIn / 32, ncp / 32), block(32, 8);
+    moment_transpose_kernel<<<grid, block, 0, s>>>(Y, n0, nc, ncp, w, YT, kChunk);
+    e = cudaGetLastError();
+    if (e == cudaSuccess)
+      e = gemm::launch<256, true>(kNIn, kNIn, ncp, gemm::Mat{YT, kNIn, kChunk},
+                                  gemm::Mat{YT, kNIn, kChunk}, EpGramAcc{G64}, c->err, s);
+  }
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = e2;
+  cudaFree(YT);
+  cudaFree(part);
+  return e;
+}
+
+cudaError_t vector_weights(const float* mx, long long n, int pw, float* w, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  vector_weights_kernel<<<152 * 8, 256, 0, s>>>(mx, n, pw, w);
+  return cudaGetLastError();
+}
+
+cudaError_t codec_eval(Codec* c, const uint16_t* Y, const float* maxima, long long n,
+                       double* out, cudaStream_t s) {
+  constexpr int kChunk = 16384;
+  uint16_t* lat = nullptr;
+  float* dec = nullptr;
+  double* acc = nullptr;
+  int* ovf = nullptr;
+  cudaError_t e = cudaMalloc(&lat, (size_t)kChunk * c->n_lat * sizeof(uint16_t));
+  if (e == cudaSuccess) e = cudaMalloc(&dec, (size_t)kChunk * kNIn * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&acc, 16 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&ovf, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, 16 * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ovf, 0, sizeof(int), s);
+  for (long long n0 = 0; e == cudaSuccess && n0 < n; n0 += kChunk) {
+    const int nc = (int)std::min<long long>(kChunk, n - n0);
+    e = codec_encode_vectors(c, Y + (size_t)n0 * kNIn, nc, lat, ovf, s);
+    if (e == cudaSuccess) e = codec_decode_vectors(c, lat, nc, dec, s);
+    if (e == cudaSuccess) {
+      eval_err_kernel<<<1024, 256, 0, s>>>(Y + (size_t)n0 * kNIn, dec,
+                                           maxima + (size_t)n0 * (c->time ? 1 : 4), c->time ? 1 : 0,
+                                           nc, acc);
+      e = cudaGetLastError();
+    }
+  }
+  double h[16] = {};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, s);
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = e2;
+  cudaFree(lat);
+  cudaFree(dec);
+  cudaFree(acc);
+  cudaFree(ovf);
+  if (e != cudaSuccess) return e;
+  auto rel = [](double num, double den) { return den > 0 ? std::sqrt(num / den) : 0.0; };
+  double nd = 0, nn = 0, pd = 0, pn = 0;
+  for (int f = 0; f < 4; ++f) {
+    out[f] = rel(h[f], h[4 + f]);
+    out[5 + f] = rel(h[8 + f], h[12 + f]);
+    nd += h[f];
+    nn += h[4 + f];
+    pd += h[8 + f];
+    pn += h[12 + f];
+  }
+  out[4] = rel(nd, nn);
+  out[9] = rel(pd, pn);
+  return cudaSuccess;
+}
+
+cudaError_t window_normalise(const uint16_t* raw, const unsigned* vmax, long long nvec,
+                             uint16_t* out, cudaStream_t s) {
+  if (nvec <= 0) return cudaSuccess;
+  window_normalise_kernel<<<152 * 8, 256, 0, s>>>(raw, vmax, nvec, out);
+  return cudaGetLastError();
 }
 
 cudaError_t snapshot_pack(const float* const f[4], int nx, int ny, int nz, unsigned* bmax,

@@ -8,19 +8,21 @@ namespace aew {
 
 struct Codec {
   int n_lat = 64;
+  int n_hid = 512;           // hidden width: 512 (space codec) or 2 n_lat (time codec)
+  bool time = false;         // compression in time (16-step strain windows)
   bool ready = false;
-  // FP32 master weights: W1 [2048][512], b1, W2 [512][nl], b2, W3 [nl][512], b3,
-  // W4 [512][2048], b4
+  // FP32 master weights: W1 [2048][nh], b1, W2 [nh][nl], b2, W3 [nl][nh], b3,
+  // W4 [nh][2048], b4
   float* w[8] = {};
   size_t wn[8] = {};
-  // operand copies (K-major rows): W1t [512][2048] bf16, W2t [nl][512] bf16,
-  // W3t [512][nl] fp16, W4t [2048][512] bf16
+  // operand copies (K-major rows): W1t [nh][2048] bf16, W2t [nl][nh] bf16,
+  // W3t [nh][nl] fp16, W4t [2048][nh] bf16
   uint16_t* W1t = nullptr;
   uint16_t* W2t = nullptr;
   uint16_t* W3t = nullptr;
   uint16_t* W4t = nullptr;
-  uint16_t* W4e = nullptr;   // the 512 strain rows of W4t, [512][512]
-  // workspace: hidden activations H [rows][512] bf16, packed inputs X [rows][2048] bf16
+  uint16_t* W4e = nullptr;   // space codec: the 512 strain rows of W4t, [512][512]
+  // workspace: hidden activations H [rows][nh] bf16, packed inputs X [rows][2048] bf16
   uint16_t* H = nullptr;
   size_t H_rows = 0;
   uint16_t* X = nullptr;

@@ -47,6 +47,14 @@ struct FwdStep {
   // bits, bmax_out[nblocks][4], every entry written).  Must not alias bmax_in.
   unsigned int* bmax_out;
   // Both options need nx, ny, nz multiples of 8.
+  // Optional (compression in time): the OUTPUT strain e^{n+1} as raw BF16 into slot
+  // tslot of a window of strain vectors tpack[nvec][2048] (2 x 8 x 8-node blocks,
+  // order t*128 + z*64 + y*8 + x, vector (bz*NBy + by)*NBx + bx), and the largest
+  // |e^{n+1}| of each vector folded into vmax[nvec] (float bits, atomicMax).  Needs nx,
+  // ny multiples of 8 and nz even.
+  uint16_t* tpack;
+  unsigned* vmax;
+  int tslot;
   int* err;            // sticky device error flag (set on a timed-out wait)
 };
 

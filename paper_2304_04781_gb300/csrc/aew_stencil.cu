@@ -225,7 +225,7 @@ __device__ __forceinline__ float me_sc(const uint8_t* s, int f) {
 // before the step: the step that wrote the state stored them), go out in one pass.
 // MAXO: the maxima of the output state, reduced inside the CTA (which owns whole
 // blocks: 128 x 8 nodes per plane, chunks of whole 8-plane layers) and stored whole.
-template <bool INCR, bool PACK, bool MAXO>
+template <bool INCR, bool PACK, bool MAXO, bool TPACK>
 __global__ void __launch_bounds__(NTHR, (INCR || PACK) ? 2 : 3)
     fwd_tma_kernel(const __grid_constant__ FwdMaps mp, const FwdStep a, int S) {
   extern __shared__ uint8_t smem_raw[];
@@ -288,6 +288,7 @@ __global__ void __launch_bounds__(NTHR, (INCR || PACK) ? 2 : 3)
   uint8_t* pk = r.base + (size_t)S * r.stage_bytes;              // PACK: staging tiles
   float* red = reinterpret_cast<float*>(pk + (PACK ? kPackExtra : 0));   // MAXO
   float pm[4] = {0.f, 0.f, 0.f, 0.f};   // MAXO: this thread's output maxima
+  float tm = 0.f;                       // TPACK: this thread's max |e^{n+1}| in the z pair
   // PACK: inverse scales of this lane's block in the current layer, and the maxima of
   // the next layer, loaded one layer ahead (lane / 2 is the block: 8 nodes = 2 lanes)
   float isc[4] = {0.f, 0.f, 0.f, 0.f};
@@ -403,6 +404,21 @@ __global__ void __launch_bounds__(NTHR, (INCR || PACK) ? 2 : 3)
       }
     }
     vzl = vz1;
+    if (TPACK) {
+      // raw BF16 strain into its window slot: this lane pair holds one 8-node row of
+      // vector (z pair k/2, y block, x block i0/8)
+      if (act && !failed) {
+        const size_t v = ((size_t)(k >> 1) * NBy + (y0 >> 3)) * NBx + (i0 >> 3);
+        *reinterpret_cast<uint2*>(a.tpack + v * 2048 + a.tslot * 128 + (k & 1) * 64 + ty * 8 +
+                                  (i0 & 7)) = make_uint2(pack2bf(e1.x, e1.y), pack2bf(e1.z, e1.w));
+        tm = fmaxf(tm, hmax4(e1));
+      }
+      if (k & 1) {   // z pair complete: this row's maxima of its 16 vectors
+        const float v = fmaxf(tm, __shfl_xor_sync(0xffffffffu, tm, 1));
+        if ((lane & 1) == 0) red[ty * 16 + (lane >> 1)] = v;
+        tm = 0.f;
+      }
+    }
     if (MAXO) {
       if (act) {
         pm[0] = fmaxf(pm[0], hmax4(e1));
@@ -433,6 +449,14 @@ __global__ void __launch_bounds__(NTHR, (INCR || PACK) ? 2 : 3)
       for (int w = 0; w < TY; ++w) mx = fmaxf(mx, red[(w * 16 + j) * 4 + f]);
       const size_t blk0 = ((size_t)(k >> 3) * NBy + (y0 >> 3)) * NBx + (x0 >> 3);
       if ((x0 >> 3) + j < NBx) a.bmax_out[(blk0 + j) * 4 + f] = __float_as_uint(mx);
+    }
+    if (TPACK && (k & 1) && !failed && tid < 16) {
+      // the rows' maxima are visible after the barrier; rewritten two planes later
+      float mx = 0.f;
+#pragma unroll
+      for (int w = 0; w < TY; ++w) mx = fmaxf(mx, red[w * 16 + tid]);
+      const size_t v = ((size_t)(k >> 1) * NBy + (y0 >> 3)) * NBx + (x0 >> 3) + tid;
+      if ((x0 >> 3) + tid < NBx && mx > 0.f) atomicMax(a.vmax + v, __float_as_uint(mx));
     }
     if (PACK && !failed) {
       // plane k of the CTA's 16 blocks: one coalesced 512-byte row per block (the tile
@@ -720,17 +744,17 @@ dim3 grid_of(int nx, int ny, int nz, int kc) {
   return dim3((nx + kTXW - 1) / kTXW, (ny + TY - 1) / TY, (nz + kc - 1) / kc);
 }
 
-template <bool INCR, bool PACK, bool MAXO>
+template <bool INCR, bool PACK, bool MAXO, bool TPACK = false>
 cudaError_t launch_fwd(const FwdMaps& mp, const FwdStep& a, cudaStream_t s) {
   const int S = stages_for(false);
-  const int extra = (PACK ? kPackExtra : 0) + (MAXO ? kMaxoExtra : 0) + 128;
+  const int extra = (PACK ? kPackExtra : 0) + ((MAXO || TPACK) ? kMaxoExtra : 0) + 128;
   const size_t smem = (size_t)S * FwdLayout::bytes(INCR) + extra;
   // once per instantiation (thread-safe static initialisation)
   static const cudaError_t attr = cudaFuncSetAttribute(
-      fwd_tma_kernel<INCR, PACK, MAXO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      fwd_tma_kernel<INCR, PACK, MAXO, TPACK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
       (int)(kMaxStages * FwdLayout::bytes(INCR) + extra));
   if (attr != cudaSuccess) return attr;
-  fwd_tma_kernel<INCR, PACK, MAXO>
+  fwd_tma_kernel<INCR, PACK, MAXO, TPACK>
       <<<grid_of(a.nx, a.ny, a.nz, a.kc), dim3(32, TY), smem, s>>>(mp, a, S);
   return cudaGetLastError();
 }
@@ -775,6 +799,15 @@ cudaError_t launch_fwd_step(const FwdStep& a, bool incremental, cudaStream_t s) 
          field_map(&mp.ef, a.ef, nx, ny, nz, kWE, TY + 2);
   if (!ok) return cudaErrorInvalidValue;
   if (incremental) return launch_fwd<true, false, false>(mp, a, s);
+  if (a.tpack) {
+    // window packing works on 2 x 8 x 8-node blocks: whole z pairs inside one CTA
+    if (nx % 8 || ny % 8 || nz % 2 || !a.vmax || a.xpack || a.bmax_out || a.tslot < 0 ||
+        a.tslot >= 16)
+      return cudaErrorInvalidValue;
+    FwdStep b = a;
+    b.kc = (a.kc + 1) / 2 * 2;
+    return launch_fwd<false, false, false, true>(mp, b, s);
+  }
   if (a.xpack || a.bmax_out) {
     // block maxima and packing work on whole 8 x 8 x 8 blocks inside one CTA
     if (nx % 8 || ny % 8 || nz % 8) return cudaErrorInvalidValue;

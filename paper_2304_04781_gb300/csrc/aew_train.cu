@@ -59,7 +59,7 @@ TrainState* train_new(Codec* c, int B) {
   TrainState* s = new TrainState();
   s->B = B;
   s->nl = c->n_lat;
-  const size_t b = (size_t)B, nl = (size_t)c->n_lat, H = kNHid, I = kNIn;
+  const size_t b = (size_t)B, nl = (size_t)c->n_lat, H = (size_t)c->n_hid, I = kNIn;
   bool ok = talloc(s, &s->a1, b * H) && talloc(s, &s->a3, b * H) && talloc(s, &s->d1, b * H) &&
             talloc(s, &s->d2, b * nl) && talloc(s, &s->d3, b * H) && talloc(s, &s->d4, b * I) &&
             talloc(s, &s->h1, b * H) && talloc(s, &s->h1T, b * H) && talloc(s, &s->z16, b * nl) &&
@@ -254,7 +254,101 @@ __global__ void to_bf16_kernel(const float* __restrict__ w, size_t n, uint16_t* 
     o[i] = gemm::bf16_bits(w[i]);
 }
 
-__global__ void loss_kernel(const double* red, double inv_n, float* out) { out[0] = (float)(red[0] * inv_n); }
+__global__ void loss_kernel(const double* red, double inv_n, float* out, double* acc) {
+  const double l = red[0] * inv_n;
+  if (out) out[0] = (float)l;
+  if (acc) acc[0] += l;
+}
+
+// ---------------------------------------------------------------------------------
+// Epoch driver pieces: seeded shuffle, minibatch gather, loss weights
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+  // SplitMix64 finaliser (Steele, Lea and Flood, "Fast splittable pseudorandom number
+  // generators", OOPSLA 2014)
+  x += 0x9e3779b97f4a7c15ull;
+  x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+  x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+  return x ^ (x >> 31);
+}
+// A seeded bijection of [0, n): a balanced four-round Feistel network on 2 hb bits
+// (2^(2 hb) >= n), walked until it lands inside [0, n) (a bijection on the larger
+// domain restricted by cycle walking stays a bijection).
+__device__ __forceinline__ long long shuffle_index(long long i, long long n, int hb, uint64_t key) {
+  const uint64_t mask = (1ull << hb) - 1;
+  uint64_t x = (uint64_t)i;
+  do {
+    uint64_t L = x >> hb, R = x & mask;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const uint64_t F = mix64(key ^ (R * 0x100000001b3ull) ^ ((uint64_t)r << 56)) & mask;
+      const uint64_t nL = R;
+      R = L ^ F;
+      L = nL;
+    }
+    x = (L << hb) | R;
+  } while (x >= (uint64_t)n);
+  return (long long)x;
+}
+
+// minibatch b of an epoch: rows i0 .. i0 + B of the shuffled order, one warp per row
+__global__ void gather_kernel(const uint16_t* __restrict__ Y, const float* __restrict__ wts,
+                              long long n, int hb, uint64_t key, long long i0, int B,
+                              uint16_t* __restrict__ out, float* __restrict__ wout) {
+  const int lane = threadIdx.x & 31;
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < B;
+       r += (gridDim.x * blockDim.x) >> 5) {
+    const long long src = shuffle_index(i0 + r, n, hb, key);
+    const uint4* a = reinterpret_cast<const uint4*>(Y + (size_t)src * kNIn);
+    uint4* o = reinterpret_cast<uint4*>(out + (size_t)r * kNIn);
+#pragma unroll
+    for (int q = 0; q < kNIn / 8 / 32; ++q) o[q * 32 + lane] = a[q * 32 + lane];
+    if (wts && lane < 4) wout[(size_t)r * 4 + lane] = wts[(size_t)src * 4 + lane];
+  }
+}
+
+// a_v of the loss weights from the data set's maxima (space codec: block maxima [n][4],
+// strain in column 0; time codec: vector maxima [n]): the power-of-two scale s (pw = 1)
+// or s^2 (pw = 2); per-block FP64 partial sums for the mean
+__global__ void weight_terms_kernel(const float* __restrict__ mx, int stride, long long n, int pw,
+                                    double* __restrict__ a, double* __restrict__ part) {
+  __shared__ double sh[256];
+  double sum = 0.0;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+       v += (long long)gridDim.x * blockDim.x) {
+    const double sc = (double)gemm::block_scale(mx[(size_t)v * stride]);
+    const double t = pw == 1 ? sc : sc * sc;
+    a[v] = t;
+    sum += t;
+  }
+  sh[threadIdx.x] = sum;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+// w[v][f] = a_v / mean(a) for the fields f < nf (the others 0)
+__global__ void weight_write_kernel(const double* __restrict__ a, const double* __restrict__ part,
+                                    int nblk, long long n, int nf, float* __restrict__ w) {
+  double tot = 0.0;
+  for (int b = 0; b < nblk; ++b) tot += part[b];
+  const double inv = tot > 0 ? (double)n / tot : 0.0;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+       v += (long long)gridDim.x * blockDim.x) {
+    const float x = (float)(a[v] * inv);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) w[(size_t)v * 4 + f] = f < nf ? x : 0.f;
+  }
+}
+
+// strain columns only (space codec): w[v] = (1, 0, 0, 0)
+__global__ void weight_strain_kernel(long long n, float* __restrict__ w) {
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+       v += (long long)gridDim.x * blockDim.x)
+    reinterpret_cast<float4*>(w)[v] = make_float4(1.f, 0.f, 0.f, 0.f);
+}
 
 // LAMB pass 1: moments, u (written over g), partial norms |w|^2 and |u|^2
 __global__ void lamb1_kernel(const float* __restrict__ w, float* __restrict__ g, float* __restrict__ m,
@@ -308,6 +402,15 @@ gemm::Mat ld(const uint16_t* p, long long ldim, long long rows, int K) {
     if (_e != cudaSuccess) return _e;       \
   } while (0)
 
+// a GEMM whose N is the latent width (32, 64, 256 or 512): the narrowest fitting tile
+template <bool BF16, class EP>
+cudaError_t launch_nl(long long M, int N, int K, const gemm::Mat& A, const gemm::Mat& B,
+                      const EP& ep, int* err, cudaStream_t st) {
+  if (N <= 32) return gemm::launch<32, BF16>(M, N, K, A, B, ep, err, st);
+  if (N <= 64) return gemm::launch<64, BF16>(M, N, K, A, B, ep, err, st);
+  return gemm::launch<256, BF16>(M, N, K, A, B, ep, err, st);
+}
+
 }  // namespace
 
 void train_state_free(void* t) {
@@ -319,7 +422,7 @@ void train_state_free(void* t) {
 size_t train_state_bytes(const void* t) { return t ? static_cast<const TrainState*>(t)->bytes : 0; }
 
 cudaError_t codec_train_step(Codec* c, const uint16_t* Y, const float* wts, int B, float lr,
-                             float* loss_dev, cudaStream_t st, std::string* err) {
+                             float* loss_dev, cudaStream_t st, std::string* err, double* loss_acc) {
   if (B % 8 != 0) {
     if (err) *err = "batch must be a multiple of 8";
     return cudaErrorInvalidValue;
@@ -334,7 +437,7 @@ cudaError_t codec_train_step(Codec* c, const uint16_t* Y, const float* wts, int 
   }
   const int nl = c->n_lat;
   const long long Bm = B;
-  const int H = kNHid, I = kNIn;
+  const int H = c->n_hid, I = kNIn;
   int* e = c->err;
   TCK(cudaMemsetAsync(s->red, 0, 32 * sizeof(double), st));
   // backward weight copies of the current masters
@@ -349,12 +452,8 @@ cudaError_t codec_train_step(Codec* c, const uint16_t* Y, const float* wts, int 
   // ---- forward
   TCK((gemm::launch<256, true>(Bm, H, I, ld(Y, I, Bm, I), ld(c->W1t, I, H, I),
                                EpFwdGelu{c->w[1], s->a1, s->h1, s->h1T, H, Bm}, e, st)));
-  if (nl == 64)
-    TCK((gemm::launch<64, true>(Bm, nl, H, ld(s->h1, H, Bm, H), ld(c->W2t, H, nl, H),
-                                EpFwdLatent{c->w[3], s->z16, s->zbT, nl, Bm}, e, st)));
-  else
-    TCK((gemm::launch<32, true>(Bm, nl, H, ld(s->h1, H, Bm, H), ld(c->W2t, H, nl, H),
-                                EpFwdLatent{c->w[3], s->z16, s->zbT, nl, Bm}, e, st)));
+  TCK((launch_nl<true>(Bm, nl, H, ld(s->h1, H, Bm, H), ld(c->W2t, H, nl, H),
+                       EpFwdLatent{c->w[3], s->z16, s->zbT, nl, Bm}, e, st)));
   TCK((gemm::launch<256, false>(Bm, H, nl, ld(s->z16, nl, Bm, nl), ld(c->W3t, nl, H, nl),
                                 EpFwdGelu{c->w[5], s->a3, s->h3, s->h3T, H, Bm}, e, st)));
   TCK((gemm::launch<256, true>(Bm, I, H, ld(s->h3, H, Bm, H), ld(c->W4t, H, I, H),
@@ -368,18 +467,10 @@ cudaError_t codec_train_step(Codec* c, const uint16_t* Y, const float* wts, int 
                                EpBack{s->a3, s->d3, s->d3b, s->d3T, H, Bm}, e, st)));
   TCK((gemm::launch<256, true>((long long)nl, H, B, ld(s->zbT, B, nl, B), ld(s->d3T, B, H, B),
                                EpStore{s->g[4], H, nl}, e, st)));
-  if (nl == 64)
-    TCK((gemm::launch<64, true>(Bm, nl, H, ld(s->d3b, H, Bm, H), ld(s->W3b, H, nl, H),
-                                EpBack{nullptr, s->d2, s->d2b, s->d2T, nl, Bm}, e, st)));
-  else
-    TCK((gemm::launch<32, true>(Bm, nl, H, ld(s->d3b, H, Bm, H), ld(s->W3b, H, nl, H),
-                                EpBack{nullptr, s->d2, s->d2b, s->d2T, nl, Bm}, e, st)));
-  if (nl == 64)
-    TCK((gemm::launch<64, true>((long long)H, nl, B, ld(s->h1T, B, H, B), ld(s->d2T, B, nl, B),
-                                EpStore{s->g[2], nl, H}, e, st)));
-  else
-    TCK((gemm::launch<32, true>((long long)H, nl, B, ld(s->h1T, B, H, B), ld(s->d2T, B, nl, B),
-                                EpStore{s->g[2], nl, H}, e, st)));
+  TCK((launch_nl<true>(Bm, nl, H, ld(s->d3b, H, Bm, H), ld(s->W3b, H, nl, H),
+                       EpBack{nullptr, s->d2, s->d2b, s->d2T, nl, Bm}, e, st)));
+  TCK((launch_nl<true>((long long)H, nl, B, ld(s->h1T, B, H, B), ld(s->d2T, B, nl, B),
+                       EpStore{s->g[2], nl, H}, e, st)));
   TCK((gemm::launch<256, true>(Bm, H, nl, ld(s->d2b, nl, Bm, nl), ld(s->W2b, nl, H, nl),
                                EpBack{s->a1, s->d1, nullptr, s->d1T, H, Bm}, e, st)));
   TCK((gemm::launch<256, true>((long long)I, H, B, ld(s->YT, B, I, B), ld(s->d1T, B, H, B),
@@ -389,8 +480,8 @@ cudaError_t codec_train_step(Codec* c, const uint16_t* Y, const float* wts, int 
   TCK((colsum_kernel<<<(nl + 255) / 256, 256, 0, st>>>(s->d2, B, nl, s->g[3]), cudaGetLastError()));
   TCK((colsum_kernel<<<(H + 255) / 256, 256, 0, st>>>(s->d3, B, H, s->g[5]), cudaGetLastError()));
   TCK((colsum_kernel<<<(I + 255) / 256, 256, 0, st>>>(s->d4, B, I, s->g[7]), cudaGetLastError()));
-  if (loss_dev) {
-    loss_kernel<<<1, 1, 0, st>>>(s->red, 1.0 / ((double)B * I), loss_dev);
+  if (loss_dev || loss_acc) {
+    loss_kernel<<<1, 1, 0, st>>>(s->red, 1.0 / ((double)B * I), loss_dev, loss_acc);
     TCK(cudaGetLastError());
   }
   // ---- LAMB
@@ -406,6 +497,79 @@ cudaError_t codec_train_step(Codec* c, const uint16_t* Y, const float* wts, int 
     TCK(cudaGetLastError());
   }
   return codec_refresh(c, st);
+}
+
+cudaError_t codec_train(Codec* c, const uint16_t* Y, const float* maxima, long long n,
+                        const TrainCfg& cfg, double* epoch_loss, cudaStream_t st,
+                        std::string* err) {
+  const int B = cfg.batch;
+  if (B < 8 || B % 8 != 0 || n < B || cfg.epochs < 0) {
+    if (err) *err = "batch must be a multiple of 8 and at most the number of vectors";
+    return cudaErrorInvalidValue;
+  }
+  if (cfg.loss != kLossState && cfg.loss != kLossStrain && !maxima) {
+    if (err) *err = "amplitude-weighted losses need the vectors' maxima";
+    return cudaErrorInvalidValue;
+  }
+  // loss weights [n][4] (none for the plain error, or the strain columns of the time codec)
+  const bool need_w = !(cfg.loss == kLossState || (cfg.loss == kLossStrain && c->time));
+  float* W = nullptr;
+  double* a = nullptr;
+  double* part = nullptr;
+  uint16_t* mb = nullptr;
+  float* mw = nullptr;
+  double* lacc = nullptr;
+  constexpr int kWB = 512;
+  cudaError_t e = cudaMalloc(&mb, (size_t)B * kNIn * sizeof(uint16_t));
+  if (e == cudaSuccess) e = cudaMalloc(&lacc, sizeof(double));
+  if (e == cudaSuccess && need_w) {
+    e = cudaMalloc(&W, (size_t)n * 4 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&mw, (size_t)B * 4 * sizeof(float));
+    if (e == cudaSuccess && cfg.loss == kLossStrain) {
+      weight_strain_kernel<<<nblk((size_t)n), 256, 0, st>>>(n, W);
+      e = cudaGetLastError();
+    } else if (e == cudaSuccess) {
+      e = cudaMalloc(&a, (size_t)n * sizeof(double));
+      if (e == cudaSuccess) e = cudaMalloc(&part, kWB * sizeof(double));
+      const int pw = cfg.loss == kLossStrainAmplitude ? 1 : 2;
+      if (e == cudaSuccess) {
+        weight_terms_kernel<<<kWB, 256, 0, st>>>(maxima, c->time ? 1 : 4, n, pw, a, part);
+        e = cudaGetLastError();
+      }
+      if (e == cudaSuccess) {
+        weight_write_kernel<<<nblk((size_t)n), 256, 0, st>>>(a, part, kWB, n, c->time ? 4 : 1, W);
+        e = cudaGetLastError();
+      }
+    }
+  }
+  int hb = 1;
+  while ((1ll << (2 * hb)) < n) ++hb;
+  const long long nb = n / B;
+  for (int ep = 0; ep < cfg.epochs && e == cudaSuccess; ++ep) {
+    const float lr = (float)(cfg.lr0 * std::pow(0.5, ep / (cfg.halve_every > 0 ? cfg.halve_every : 1 << 30)));
+    const uint64_t key = cfg.seed * 0x9e3779b97f4a7c15ull + (uint64_t)ep * 0xd1b54a32d192ed03ull + 1;
+    e = cudaMemsetAsync(lacc, 0, sizeof(double), st);
+    for (long long b = 0; b < nb && e == cudaSuccess; ++b) {
+      gather_kernel<<<(B + 7) / 8, 256, 0, st>>>(Y, W, n, hb, key, b * B, B, mb, mw);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = codec_train_step(c, mb, W ? mw : nullptr, B, lr, nullptr, st, err, lacc);
+    }
+    if (e == cudaSuccess && epoch_loss) {
+      double l = 0.0;
+      e = cudaMemcpyAsync(&l, lacc, sizeof(double), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      epoch_loss[ep] = nb > 0 ? l / (double)nb : 0.0;
+    }
+  }
+  cudaError_t e2 = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = e2;
+  cudaFree(mb);
+  cudaFree(mw);
+  cudaFree(W);
+  cudaFree(a);
+  cudaFree(part);
+  cudaFree(lacc);
+  return e;
 }
 
 }  // namespace aew

@@ -52,6 +52,10 @@ def _cfg(**kw):
     (dict(accum_window=0), "accum_window"),
     (dict(storage=2, nx=20), "multiples of 8"),
     (dict(n_lat=48), "n_lat"),
+    (dict(codec=2), "codec"),
+    (dict(codec=1, n_lat=64), "n_lat"),
+    (dict(codec=1, storage=2, n_lat=512, nx=20), "multiples of 8"),
+    (dict(codec=1, storage=2, n_lat=512, nz=12, ny=20), "multiples of 8"),
 ])
 def test_create_rejects_bad_configs(kw, frag):
     L = aewave.lib()
@@ -86,3 +90,24 @@ def test_revolve_plan_matches_brute_force_small():
         for s in range(0, 4):
             _, fwd = aewave.revolve_plan(nt, s)
             assert fwd == R.brute_force(nt, s) + 1
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 64, 257])
+def test_host_eigensolver_matches_the_definition(n):
+    """aew_sym_eig (the PCA initialisation's solver) on random symmetric matrices, one
+    with clustered eigenvalues: A V = V diag(w), V orthonormal, w descending and equal to
+    numpy's eigenvalues."""
+    import numpy as np
+    rng = np.random.default_rng(n)
+    B = rng.standard_normal((n, n))
+    A = B + B.T
+    if n == 257:   # repeated eigenvalues in clusters of 8
+        Q, _ = np.linalg.qr(B)
+        lam = np.repeat(np.linspace(3.0, -1.0, 33), 8)[:n]
+        A = (Q * lam) @ Q.T
+    w, V = aewave.sym_eig(A)
+    scale = max(1.0, float(np.abs(w).max()))
+    assert np.all(np.diff(w) <= 1e-12 * scale)
+    np.testing.assert_allclose(w, np.sort(np.linalg.eigvalsh(A))[::-1], atol=1e-12 * scale)
+    assert np.abs(A @ V - V * w).max() < 1e-12 * scale
+    assert np.abs(V.T @ V - np.eye(n)).max() < 1e-12

@@ -253,12 +253,17 @@ def test_ae_gradient_matches_oracle_ae_gradient(ae_case):
     ehat = C.compressed_e_history(Wt, states, emulate=True)
     J_ref, g_ref, _ = W.gradient(prob, c, d_obs, e_of=lambda n: ehat[n])
     assert abs(J - J_ref) / J_ref < 1e-4
-    assert relerr(host(g), g_ref) < 1e-2
+    eg = relerr(host(g), g_ref)
     # the HVP reuses the stored latents
     dc = inputs.direction(prob.shape, prob.h, seed=20).astype(np.float32).astype(np.float64)
     H = host(s.hessvec(cuda(dc)))
     H_ref = W.hessvec_gn(prob, c, dc, lambda n: ehat[n])
-    assert relerr(H, H_ref) < 1e-2
+    eh = relerr(H, H_ref)
+    print(f"AE parity (random codec, 32^3): gradient {eg:.2e}, HVP {eh:.2e}")
+    # random weights decode noise, whose GN-HVP (applied twice) cancels more than the
+    # gradient: measured 3.6e-4 / 1.4e-3; the trained codec's parity is held to 1e-3
+    # for both below
+    assert eg < 1e-3 and eh < 2e-3
     st = s.stats()
     assert st["latent_bytes"] == prob.nt * 64 * 64 * 2
 
@@ -273,4 +278,33 @@ def test_roundtrip_of_one_state_matches_oracle(ae_case):
     e_ref = C.roundtrip_e(Wt, states[n], emulate=True)
     lat, bm = s.codec_encode([cuda(a) for a in states[n]])
     e = host(s.codec_decode_e(lat, bm))
-    assert relerr(e, e_ref) < 1e-2
+    er = relerr(e, e_ref)
+    print(f"one-state roundtrip parity: {er:.2e}")
+    assert er < 2 * CODEC_TOL
+
+
+def test_trained_codec_gradient_and_hvp_match_oracle():
+    """The committed trained codec (weights/codec_64.npz, 8 draws at 128^3 x 1000) in the
+    compressed gradient and GN-HVP at 64^3 x 160 steps, against the oracle with the same
+    weights: trained activations exercise other BF16 ranges than random weights."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.dirname(__file__)), "paper_2304_04781_gb300",
+                        "weights", "codec_64.npz")
+    z = np.load(path)
+    Wt = {k: z[k] for k in C.PARAMS}
+    prob, c, _ = setup((64, 64, 64), 160, 16, seed=3)
+    ctrue = inputs.bump_model(c, prob.h).astype(np.float32).astype(np.float64)
+    d_obs, _, _ = W.forward(prob, ctrue)
+    s = solver(prob, storage="ae")
+    s.codec_set(Wt)
+    J, g = s.gradient(cuda(c), cuda(d_obs))
+    _, states = W.forward_states(prob, c)
+    ehat = C.compressed_e_history(Wt, states, emulate=True)
+    J_ref, g_ref, _ = W.gradient(prob, c, d_obs, e_of=lambda n: ehat[n])
+    dc = inputs.direction(prob.shape, prob.h, seed=21).astype(np.float32).astype(np.float64)
+    H = host(s.hessvec(cuda(dc)))
+    H_ref = W.hessvec_gn(prob, c, dc, lambda n: ehat[n])
+    eg, eh = relerr(host(g), g_ref), relerr(H, H_ref)
+    print(f"AE parity (trained codec, 64^3): gradient {eg:.2e}, HVP {eh:.2e}")
+    assert abs(J - J_ref) / J_ref < 1e-4
+    assert eg < 1e-3 and eh < 1e-3

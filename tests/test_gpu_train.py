@@ -1,0 +1,150 @@
+"""GPU checks of the codec's training calls behind the C-ABI against the FP64 oracle:
+aew_codec_train (epochs on the device: seeded shuffle, minibatch gather, Table 2's
+learning-rate halving, loss weights computed from the vectors' maxima), the PCA
+initialisation aew_codec_init_pca (device moments, host eigensolver, GELU pair code)
+against the oracle's optimal rank-k code, and aew_codec_eval's decoded errors."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import codec as C
+from oracle import codec_time as CT
+from oracle import wave as W
+from paper_2304_04781_gb300 import inputs
+
+from .helpers import relerr, setup, solver
+
+pytestmark = pytest.mark.gpu
+
+
+def _p2(m):
+    """power-of-two scales of maxima (the scale definition of Sec. 3.3's normalisation
+    as the oracle states it: 2^max(e, -100), m = f 2^e, f in [1/2, 1))"""
+    _, e = np.frexp(m)
+    return np.where(m > 0, np.ldexp(1.0, np.maximum(e, -100)), 0.0)
+
+
+def _data(n, seed):
+    rng = np.random.default_rng(seed)
+    Y = C.round_bf16(rng.uniform(-1, 1, (n, 2048)) * rng.uniform(0.05, 1.0, (n, 1)))
+    return Y
+
+
+@pytest.mark.parametrize("codec", ["space", "time"])
+def test_training_epochs_follow_table_2_and_the_weights(codec):
+    """3 epochs of one minibatch each (batch = n: the shuffle only reorders rows) with
+    the learning rate halved every epoch and the strain-energy weights: the same as 3
+    oracle LAMB steps with lr 1e-3, 5e-4, 2.5e-4 and w = s^2 / mean(s^2) on the strain."""
+    prob, _, _ = setup((32, 32, 32), 4, 16)
+    nl = 512 if codec == "time" else 64
+    s = solver(prob, storage="full", codec=codec, n_lat=nl)
+    Wt = inputs.codec_init(seed=5, n_hid=s.n_hid, n_lat=nl)
+    s.codec_set(Wt)
+    n = 256
+    Y = _data(n, 6)
+    rng = np.random.default_rng(7)
+    # maxima over a few powers of two (and some zeros): every vector keeps some weight,
+    # so the LAMB steps (sign-like at first) see well-determined gradients everywhere
+    if codec == "time":
+        mx = (rng.uniform(0.5, 1.0, n) * 2.0 ** rng.integers(-4, 4, n)).astype(np.float32)
+        mx[:3] = 0.0
+        a = _p2(mx.astype(np.float64)) ** 2
+        w = np.repeat((a / a.mean())[:, None], 4, axis=1)
+    else:
+        mx = (rng.uniform(0.5, 1.0, (n, 4)) * 2.0 ** rng.integers(-4, 4, (n, 4))).astype(np.float32)
+        a = _p2(mx[:, 0].astype(np.float64)) ** 2
+        w = np.zeros((n, 4))
+        w[:, 0] = a / a.mean()
+    w = w.astype(np.float32).astype(np.float64)
+    ydev = torch.from_numpy(Y.astype(np.float32)).to(torch.bfloat16).cuda()
+    losses = s.codec_train(ydev, torch.from_numpy(mx).cuda(), epochs=3, batch=n, lr0=1e-3,
+                           halve_every=1, loss="strain-energy", seed=3)
+    Wo = {k: v.astype(np.float64) for k, v in Wt.items()}
+    opt = C.Lamb(Wo)
+    for ep, lr in enumerate((1e-3, 5e-4, 2.5e-4)):
+        L, g = C.loss_and_grad(Wo, Y, emulate=True, weights=w)
+        assert abs(losses[ep] - L) <= 2e-3 * L, (ep, losses[ep], L)
+        Wo = opt.step(Wo, g, lr)
+    Wg = s.codec_get()
+    for k in C.PARAMS:
+        assert relerr(Wg[k], Wo[k]) < 2e-3, k
+
+
+def test_epoch_visits_every_vector_once():
+    """With lr0 = 0 nothing moves, and an epoch's mean minibatch loss is the data set's
+    loss exactly when the shuffled minibatches partition the data (a seeded bijection):
+    one vector with a hundredfold error makes any repeat or omission visible."""
+    prob, _, _ = setup((32, 32, 32), 4, 16)
+    s = solver(prob, storage="full")
+    Wt = inputs.codec_init(seed=8)
+    s.codec_set(Wt)
+    n = 1000
+    Y = _data(n, 9)
+    Y[123] = C.round_bf16(np.full(2048, 0.999) * np.sign(np.arange(2048) % 2 - 0.5))
+    ydev = torch.from_numpy(Y.astype(np.float32)).to(torch.bfloat16).cuda()
+    for seed in (0, 1, 2):
+        losses = s.codec_train(ydev, None, epochs=2, batch=40, lr0=0.0, loss="state", seed=seed)
+        L, _ = C.loss_and_grad({k: v.astype(np.float64) for k, v in Wt.items()}, Y, emulate=True)
+        for l in losses:
+            assert abs(l - L) <= 1e-3 * L, (seed, l, L)
+    Wg = s.codec_get()
+    for k in C.PARAMS:
+        np.testing.assert_array_equal(Wg[k], Wt[k])
+
+
+@pytest.fixture(scope="module")
+def windows():
+    """normalised BF16 window vectors of an oracle run and their maxima"""
+    prob, c, _ = setup((32, 32, 32), 128, 16, seed=4)
+    _, states = W.forward_states(prob, c)
+    e_hist = [st[0] for st in states]
+    X = np.concatenate([CT.window_vectors(e_hist, prob.shape, tb) for tb in range(8)])
+    X = X[np.abs(X).max(1) > 0]
+    X32 = X.astype(np.float32).astype(np.float64)
+    mx = np.abs(X32).max(1)
+    Y = C.round_bf16(CT.normalise(X32, CT.vector_scales(X32)))
+    return prob, Y, mx
+
+
+@pytest.mark.parametrize("loss", ["state", "strain-energy"])
+def test_pca_initialisation_matches_the_optimal_code(windows, loss):
+    prob, Y, mx = windows
+    s = solver(prob, storage="full", codec="time")
+    ydev = torch.from_numpy(Y.astype(np.float32)).to(torch.bfloat16).cuda()
+    ev = s.codec_init_pca(ydev, torch.from_numpy(mx.astype(np.float32)).cuda(), loss)
+    wts = _p2(mx) ** 2 if loss == "strain-energy" else None
+    ref = CT.pca_codec(Y, 512, wts)
+    Wg = {k: v.astype(np.float64) for k, v in s.codec_get().items()}
+    R = C.decode(Wg, C.encode(Wg, Y))
+    R_ref = C.decode(ref, C.encode(ref, Y))
+    assert relerr(R, R_ref) < 1e-3
+    # eigenvalues of the weighted covariance, descending
+    w = np.ones(Y.shape[0]) if wts is None else wts
+    mu = (w[:, None] * Y).sum(0) / w.sum()
+    lam = np.sort(np.linalg.eigvalsh(((Y - mu) * w[:, None]).T @ (Y - mu) / w.sum()))[::-1]
+    top = lam[:600]
+    assert relerr(ev[:600], top) < 1e-4
+    assert np.all(np.diff(ev) <= 1e-9 * ev[0])
+    # the code's weighted error is the eigenvalue tail (Eckart-Young)
+    err = float((w[:, None] * (R - Y) ** 2).sum() / w.sum())
+    assert err == pytest.approx(lam[512:].sum(), rel=2e-2)
+
+
+def test_decoded_error_evaluation_matches_oracle(windows):
+    prob, Y, mx = windows
+    s = solver(prob, storage="full", codec="time")
+    ydev = torch.from_numpy(Y.astype(np.float32)).to(torch.bfloat16).cuda()
+    mdev = torch.from_numpy(mx.astype(np.float32)).cuda()
+    s.codec_init_pca(ydev, mdev, "state")
+    out = s.codec_eval(ydev, mdev)
+    Wg = {k: v.astype(np.float64) for k, v in s.codec_get().items()}
+    R = C.decode(Wg, C.encode(Wg, Y, emulate=True), emulate=True)
+    sc = _p2(mx)[:, None]
+    e_norm = np.linalg.norm(R - Y) / np.linalg.norm(Y)
+    e_phys = np.linalg.norm((R - Y) * sc) / np.linalg.norm(Y * sc)
+    assert out["normalised"]["e"] == pytest.approx(e_norm, rel=5e-2)
+    assert out["physical"]["e"] == pytest.approx(e_phys, rel=5e-2)
+    assert out["normalised"]["all"] == out["normalised"]["e"]
+    st = s.stats()
+    assert st["decoded_err_normalised"] == out["normalised"]["e"]
+    assert st["decoded_err_physical"] == out["physical"]["e"]

@@ -183,14 +183,15 @@ def test_emulated_codec_close_to_exact_and_rounded():
 
 
 def test_training_schedule_follows_table_2():
-    """The training driver's defaults and the oracle's schedule are the values Table 2
-    prints (fixture tests/golden/table2_training.json)."""
+    """The training call's defaults (aew_codec_train through the binding) and the
+    oracle's schedule are the values Table 2 prints (fixture
+    tests/golden/table2_training.json)."""
     import inspect
     import json
     import os
-    from paper_2304_04781_gb300 import train
+    from paper_2304_04781_gb300 import aewave
     g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "table2_training.json")))
-    sig = inspect.signature(train.train).parameters
+    sig = inspect.signature(aewave.Solver.codec_train).parameters
     assert sig["epochs"].default == g["epochs"]
     assert sig["batch"].default == g["batch_size"]
     assert sig["lr0"].default == g["initial_learning_rate"]
@@ -224,31 +225,3 @@ def test_weighted_training_gradient_matches_finite_differences():
             Wp[name].ravel()[idx] += eps; Wm[name].ravel()[idx] -= eps
             fd = (C.loss_and_grad(Wp, Y, weights=w)[0] - C.loss_and_grad(Wm, Y, weights=w)[0]) / (2 * eps)
             assert fd == pytest.approx(g[name].ravel()[idx], rel=1e-5, abs=1e-10), (name, idx)
-
-
-def test_training_loss_weights_follow_the_block_scales():
-    """train.py's per-vector, per-field weights (R23): the strain field only, weighted by
-    the block's power-of-two strain scale s_e (or s_e^2) over its data-set mean, with the
-    scales of the oracle's definition (block_scales) for the same maxima; the plain
-    "state" objective has no weights."""
-    import torch
-    from paper_2304_04781_gb300 import train
-    rng = np.random.default_rng(21)
-    bm = rng.uniform(0.5, 1.0, (300, 4)) * 10.0 ** rng.integers(-40, 3, (300, 4))
-    bm[:5, 0] = 0.0                                  # zero blocks weigh nothing
-    bm[5, 0] = 1e-35                                 # below the 2^-100 clamp
-    bm32 = bm.astype(np.float32)
-    t = torch.from_numpy(bm32)
-    assert train.loss_weights(t, "state") is None
-    w = train.loss_weights(t, "strain").numpy()
-    assert np.all(w[:, 0] == 1.0) and np.all(w[:, 1:] == 0.0)
-    # the oracle's scales of each block's strain maximum, one block at a time
-    s_ref = np.array([C.block_scales([np.full((8, 8, 8), m)] + [np.zeros((8, 8, 8))] * 3)[0, 0]
-                      for m in bm32[:, 0].astype(np.float64)])
-    for kind, p in (("strain-amplitude", 1), ("strain-energy", 2)):
-        w = train.loss_weights(t, kind).numpy().astype(np.float64)
-        a = s_ref ** p
-        want = (a / a.mean()).astype(np.float32).astype(np.float64)   # weights are FP32
-        np.testing.assert_allclose(w[:, 0], want, rtol=1e-6, atol=1.5e-45)
-        assert np.all(w[:, 1:] == 0.0) and np.all(w[:5, 0] == 0.0)
-        assert abs(w[:, 0].mean() - 1.0) < 1e-6
