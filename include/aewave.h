@@ -401,7 +401,8 @@ int aew_test_gelu(const float* x_dev, float* y_dev, float* dy_dev, long long n, 
  * n must be at most 2^32 (AEW_E_ARG otherwise, before any device work).
  * out_dev: device FP64 scalar receiving sum a[i] b[i] (written on `stream`; the call
  * does not synchronise).  The first call on a device looks up the array's device
- * address, so it must not be made during stream capture.  All calls share the array:
+ * address (again after the device's context is created anew, e.g. by cudaDeviceReset),
+ * so it must not be made during stream capture.  All calls share the array:
  * calls that overlap on the GPU race and must be serialised by the caller.  Returns
  * AEW_E_ARG for NULL pointers, AEW_E_CUDA if a launch fails. */
 int aew_dot_noalloc(const float* a_dev, const float* b_dev, size_t n, double* out_dev,

@@ -724,12 +724,17 @@ cudaError_t codec_encode_grid(Codec* c, const float* const f[4], int nx, int ny,
 
 static int ctas_of(const Codec* c, int ctas) { return ctas > 0 ? ctas : c->max_ctas; }
 
+// the time codec's products are all wide (N >= 512, hundreds of thousands of rows): they
+// run on SM pairs, whose 256 x 256 tiles pull a third fewer operand bytes per SM
+static bool pair_wide(const Codec* c) { return c->time && c->pair_gemm && c->max_stages == 0; }
+
 // encoder layer 2: latents = fp16(H W2 + b2) from the hidden activations in c->H
 static cudaError_t encode_layer2(Codec* c, long long n, uint16_t* lat, int* overflow,
                                  cudaStream_t s, int g) {
   const int nl = c->n_lat, nh = c->n_hid;
   EpLatent e2{c->w[3], lat, nl, n, overflow};
   const gemm::Mat a2{c->H, n, nh}, b2{c->W2t, nl, nh};
+  if (pair_wide(c)) return gemm2::launch<true>(n, nl, nh, a2, b2, e2, c->err, s, g);
   if (nl == 64) return gemm::launch<64, true>(n, nl, nh, a2, b2, e2, c->err, s, g, c->max_stages);
   if (nl == 32) return gemm::launch<32, true>(n, nl, nh, a2, b2, e2, c->err, s, g, c->max_stages);
   return gemm::launch<256, true>(n, nl, nh, a2, b2, e2, c->err, s, g, c->max_stages);
@@ -754,6 +759,9 @@ static cudaError_t decode_hidden(Codec* c, const uint16_t* lat, long long nb, cu
   if (!ensure_H(c, (size_t)nb)) return cudaErrorMemoryAllocation;
   const int nl = c->n_lat, nh = c->n_hid;
   EpBiasGeluH ep{c->w[5], c->H, nb, nh};
+  if (pair_wide(c))
+    return gemm2::launch<false>(nb, nh, nl, gemm::Mat{lat, nb, nl}, gemm::Mat{c->W3t, nh, nl}, ep,
+                                c->err, s, ctas_of(c, ctas));
   return gemm::launch<256, false>(nb, nh, nl, gemm::Mat{lat, nb, nl},
                                   gemm::Mat{c->W3t, nh, nl}, ep, c->err, s, ctas_of(c, ctas),
                                   c->max_stages);
@@ -827,6 +835,9 @@ cudaError_t codec_decode_window(Codec* c, const uint16_t* lat, const unsigned* v
   if (e != cudaSuccess) return e;
   const int nh = c->n_hid;
   EpDecWindow ep{c->w[7], vmax, e_out, nx, ny, nz, NBx, NBy, nvec, (size_t)nx * ny * nz};
+  if (pair_wide(c))
+    return gemm2::launch<true>(nvec, kNIn, nh, gemm::Mat{c->H, nvec, nh},
+                               gemm::Mat{c->W4t, kNIn, nh}, ep, c->err, s, ctas_of(c, ctas));
   return gemm::launch<256, true>(nvec, kNIn, nh, gemm::Mat{c->H, nvec, nh},
                                  gemm::Mat{c->W4t, kNIn, nh}, ep, c->err, s, ctas_of(c, ctas),
                                  c->max_stages);

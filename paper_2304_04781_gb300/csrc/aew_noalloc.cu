@@ -15,8 +15,11 @@
 //
 // The host cannot use the array's name as a device address: at the first call on each
 // device (with that device current) the library looks up its address with
-// cudaGetSymbolAddress and caches it.  That first call must therefore not happen while
-// a stream is being captured.
+// cudaGetSymbolAddress and caches it, keyed by the device's current context (its
+// process-unique ID), so that a context created anew -- after cudaDeviceReset, say --
+// gets its own lookup instead of a stale address.  That first call on a device (and on
+// each new context) must therefore not happen while a stream is being captured.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -35,6 +38,7 @@ static __device__ __align__(256) double g_dot_partials[kMaxPartials];
 
 std::mutex g_mu;
 double* g_addr[kMaxDevices] = {};
+unsigned long long g_ctx[kMaxDevices] = {};   // ID of the context g_addr belongs to
 
 __global__ void dot_chunks_kernel(const float* __restrict__ a, const float* __restrict__ b,
                                   size_t n, double* part) {
@@ -67,18 +71,49 @@ __global__ void dot_sum_kernel(const double* part, int nblk, double* out_dev) {
   }
 }
 
-// device address of the scratch array on the current device (looked up once)
+// ID of the calling thread's current context (0 if none is current or the driver
+// entry points are unavailable), through the driver entry points the runtime exposes
+unsigned long long current_context_id() {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && f && q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && f && q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+    cudaGetLastError();
+  });
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx ||
+      get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
+
+// device address of the scratch array on the current device, looked up once per device
+// and context (the lookup makes the device's primary context current if none was)
 double* scratch_on_current_device() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
+  const unsigned long long id = current_context_id();
+  if (!g_addr[dev] || id == 0 || id != g_ctx[dev]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_dot_partials) != cudaSuccess) {
       cudaGetLastError();
       return nullptr;
     }
     g_addr[dev] = static_cast<double*>(p);
+    g_ctx[dev] = current_context_id();
   }
   return g_addr[dev];
 }
