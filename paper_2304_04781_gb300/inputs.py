@@ -30,6 +30,7 @@ __all__ = [
     "bump_model",
     "direction",
     "receiver_grid",
+    "source_grid",
     "codec_init",
     "random_latents",
     "smooth_state",
@@ -110,6 +111,22 @@ def receiver_grid(nx: int, ny: int, nrec: int) -> np.ndarray:
             j = int(np.floor((q + 0.5) * ny / ry + 0.5))
             out[r] = (min(max(i, 1), nx - 2), min(max(j, 1), ny - 2), 1)
             r += 1
+    return out
+
+
+def source_grid(nx: int, ny: int, nz: int, nshots: int):
+    """Source nodes (i, j, k) of nshots shots: a regular grid over the horizontal plane
+    at mid-depth k = nz // 2 (one shot: the centre node).  Returns a list of tuples."""
+    ry = int(np.floor(np.sqrt(nshots)))
+    while nshots % ry:
+        ry -= 1
+    rx = nshots // ry
+    out = []
+    for q in range(ry):
+        for p in range(rx):
+            i = int(np.floor((p + 0.5) * nx / rx))
+            j = int(np.floor((q + 0.5) * ny / ry))
+            out.append((min(max(i, 1), nx - 2), min(max(j, 1), ny - 2), nz // 2))
     return out
 
 
