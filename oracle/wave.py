@@ -26,7 +26,9 @@ explicit transposes G^T and D^T (not with the identity D = -G^T, so that the
 adjoint-identity test checks the transposes). dJ/dc = 2 c (dJ/dm).
 
 The incremental forward / incremental adjoint problems of Sec. 4 give the
-Gauss-Newton Hessian-vector product H dc = J_F^T J_F dc.
+Gauss-Newton Hessian-vector product H dc = J_F^T J_F dc, and with the second-order
+terms (the first-order adjoint times the incremental strain, and its source in the
+second-order adjoint) the full Newton Hessian-vector product.
 
 The autoencoder variant (Sec. 3) replaces the stored forward strain e^n in the
 adjoint and incremental problems by its decoded approximation; the solve functions accept an
@@ -297,6 +299,85 @@ def hessvec_gn(p: Problem, c: np.ndarray, dc: np.ndarray,
     """Gauss-Newton Hessian-vector product J_F^T J_F dc (incremental fwd + adjoint)."""
     dd = incremental_forward(p, c, dc, e_of)
     return jacobian_transpose(p, c, dd, e_of)
+
+
+def incremental_forward_states(p: Problem, c: np.ndarray, dc: np.ndarray,
+                               e_of: Callable[[int], np.ndarray]):
+    """The incremental forward solve of incremental_forward, also returning the
+    incremental strain history de^n, n = 0..nt-1 (de^0 = 0)."""
+    dt, h = p.dt, p.h
+    m = c.astype(np.float64) ** 2
+    dm = 2.0 * c * dc
+    de = np.zeros(p.shape); dvx = np.zeros(p.shape); dvy = np.zeros(p.shape); dvz = np.zeros(p.shape)
+    dd = np.zeros((p.nt + 1, p.nrec, 3))
+    hist = []
+    for n in range(p.nt):
+        hist.append(de)
+        gx, gy, gz = grad_op(m * de + dm * e_of(n), h)
+        dvx = dvx + dt * gx
+        dvy = dvy + dt * gy
+        dvz = dvz + dt * gz
+        de = interior(de + dt * div_op(dvx, dvy, dvz, h))
+        dd[n + 1] = _sample(p, dvx, dvy, dvz)
+    return dd, hist
+
+
+def hessvec_full(p: Problem, c: np.ndarray, d_obs: np.ndarray, dc: np.ndarray,
+                 e_of: Callable[[int], np.ndarray],
+                 de_of: Optional[Callable[[int], np.ndarray]] = None) -> np.ndarray:
+    """Full Newton Hessian-vector product H dc of J(c) = 1/2 |F(c) - d_obs|^2 (Sec. 4's
+    incremental forward and incremental adjoint problems with the second-order terms).
+
+    Differentiating the gradient dJ/dm = sum_n dt e^n q^n (q^n = G^T lam^{n+1}, see
+    adjoint) in the direction dm gives
+        H_m dm = sum_n dt (de^n q^n + e^n dq^n),
+    de^n the incremental forward strain and dq^n = G^T dlam^{n+1} from the second-order
+    adjoint: the adjoint recursion driven by the residual B dv (dv the incremental
+    forward velocity) plus the derivative of its own m-dependence, a source dt dm q^n
+    in the mu update:
+        dlam += B^T (B dv^{n+1});  dlam += dt D^T dmu;  dq = G^T dlam;
+        dmu = interior(dmu + dt m dq + dt dm q).
+    In c (m = c^2, dm = 2 c dc): H dc = 2 c H_m(2 c dc) + 2 dc (dJ/dm).
+    Only the terms in q distinguish it from the Gauss-Newton product; at zero residual
+    q = 0 and the two coincide.
+
+    e_of(n) supplies the forward strain e^n; de_of(n) the incremental strain used in the
+    de^n q^n term (None: the exact one from this incremental forward solve); the
+    residual comes from an exact forward solve."""
+    dt, h = p.dt, p.h
+    m = c.astype(np.float64) ** 2
+    dm = 2.0 * c * dc
+    d, _, _ = forward(p, c)
+    r = d - d_obs
+    dd, de_hist = incremental_forward_states(p, c, dc, e_of)
+    if de_of is None:
+        de_of = lambda n: de_hist[n]
+    lx = np.zeros(p.shape); ly = np.zeros(p.shape); lz = np.zeros(p.shape); mu = np.zeros(p.shape)
+    hx = np.zeros(p.shape); hy = np.zeros(p.shape); hz = np.zeros(p.shape); hmu = np.zeros(p.shape)
+    gm = np.zeros(p.shape)      # dJ/dm
+    Hm = np.zeros(p.shape)      # H_m dm
+    ri, rj, rk = p.rec[:, 0], p.rec[:, 1], p.rec[:, 2]
+    for n in range(p.nt - 1, -1, -1):
+        # first-order adjoint (as in adjoint)
+        np.add.at(lx, (rk, rj, ri), r[n + 1][:, 0])
+        np.add.at(ly, (rk, rj, ri), r[n + 1][:, 1])
+        np.add.at(lz, (rk, rj, ri), r[n + 1][:, 2])
+        ax, ay, az = div_op_T(mu, h)
+        lx = lx + dt * ax; ly = ly + dt * ay; lz = lz + dt * az
+        q = grad_op_T(lx, ly, lz, h)
+        # second-order adjoint
+        np.add.at(hx, (rk, rj, ri), dd[n + 1][:, 0])
+        np.add.at(hy, (rk, rj, ri), dd[n + 1][:, 1])
+        np.add.at(hz, (rk, rj, ri), dd[n + 1][:, 2])
+        bx, by, bz = div_op_T(hmu, h)
+        hx = hx + dt * bx; hy = hy + dt * by; hz = hz + dt * bz
+        hq = grad_op_T(hx, hy, hz, h)
+        e_n = e_of(n)
+        gm += dt * e_n * q
+        Hm += dt * (de_of(n) * q + e_n * hq)
+        hmu = interior(hmu + dt * m * hq + dt * dm * q)
+        mu = interior(mu + dt * m * q)
+    return 2.0 * c * Hm + 2.0 * dc * gm
 
 
 def forward_states(p: Problem, c: np.ndarray, wavelet=None):

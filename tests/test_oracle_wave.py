@@ -254,3 +254,62 @@ def test_wrong_adjoint_is_caught():
     JTr = W.jacobian_transpose(prob, c, r, bad)
     lhs, rhs = float(np.sum(Jdc[1:] * r[1:])), float(np.sum(dc * JTr))
     assert abs(lhs - rhs) > 1e-6 * abs(lhs)
+
+
+# ---------------------------------------------------------------------------- full Newton
+def test_full_hessian_equals_gradient_derivative_at_nonzero_residual():
+    """The full Newton HVP is the derivative of the gradient: at a nonzero residual (data
+    from the bump model) the central difference of the gradient reproduces H dc to
+    O(eps^2), while the Gauss-Newton product does not."""
+    prob = _problem(n=16, nt=120)
+    c = inputs.velocity_model(prob.shape, prob.h, seed=0)
+    d_obs, _, _ = W.forward(prob, inputs.bump_model(c, prob.h, amp=0.2))
+    _, states = W.forward_states(prob, c)
+    e_of = lambda n: states[n][0]
+    dc = inputs.direction(prob.shape, prob.h, seed=31)
+    H = W.hessvec_full(prob, c, d_obs, dc, e_of)
+    # the difference errs by ~0.18 (eps/|c|)^2 relative (measured: 1.8e-6 at 1e-4 and
+    # 1.8e-8 at 1e-5, an exact eps^2 scaling), far above FP64 round-off at 1e-5
+    eps = 1e-5 * np.abs(c).max()
+    _, gp, _ = W.gradient(prob, c + eps * dc, d_obs)
+    _, gm, _ = W.gradient(prob, c - eps * dc, d_obs)
+    fd = (gp - gm) / (2 * eps)
+    err = np.linalg.norm(fd - H) / np.linalg.norm(H)
+    assert err < 1e-7, err
+    Hgn = W.hessvec_gn(prob, c, dc, e_of)
+    assert np.linalg.norm(fd - Hgn) / np.linalg.norm(fd) > 1e-3    # the residual terms matter
+
+
+def test_full_hessian_is_symmetric_and_reduces_to_gauss_newton_at_zero_residual():
+    prob = _problem(n=16, nt=80)
+    c = inputs.velocity_model(prob.shape, prob.h, seed=1)
+    _, states = W.forward_states(prob, c)
+    e_of = lambda n: states[n][0]
+    dc1 = inputs.direction(prob.shape, prob.h, seed=40)
+    dc2 = inputs.direction(prob.shape, prob.h, seed=41)
+    d_obs, _, _ = W.forward(prob, inputs.bump_model(c, prob.h, amp=0.2))
+    H1 = W.hessvec_full(prob, c, d_obs, dc1, e_of)
+    H2 = W.hessvec_full(prob, c, d_obs, dc2, e_of)
+    a, b = float(np.sum(dc2 * H1)), float(np.sum(dc1 * H2))
+    assert abs(a - b) <= 1e-10 * max(abs(a), abs(b))
+    d0, _, _ = W.forward(prob, c)                     # zero residual
+    Hf = W.hessvec_full(prob, c, d0, dc1, e_of)
+    Hg = W.hessvec_gn(prob, c, dc1, e_of)
+    np.testing.assert_allclose(Hf, Hg, rtol=0, atol=1e-12 * np.abs(Hg).max())
+
+
+def test_incremental_strain_history_matches_the_jacobian_product():
+    prob = _problem(n=12, nt=50)
+    c = inputs.velocity_model(prob.shape, prob.h, seed=2)
+    _, states = W.forward_states(prob, c)
+    dc = inputs.direction(prob.shape, prob.h, seed=42)
+    dd, hist = W.incremental_forward_states(prob, c, dc, lambda n: states[n][0])
+    np.testing.assert_array_equal(dd, W.incremental_forward(prob, c, dc, lambda n: states[n][0]))
+    assert len(hist) == prob.nt and not hist[0].any()
+    # de^n is the derivative of e^n: central difference of two forward solves
+    eps = 1e-5 * np.abs(c).max()
+    _, sp = W.forward_states(prob, c + eps * dc)
+    _, sm = W.forward_states(prob, c - eps * dc)
+    n = 40
+    fd = (sp[n][0] - sm[n][0]) / (2 * eps)
+    assert np.linalg.norm(fd - hist[n]) <= 1e-6 * np.linalg.norm(hist[n])
