@@ -71,6 +71,12 @@ def parse():
                    help="accuracy mode: Ricker peak frequency [Hz] of the workload")
     p.add_argument("--err-hvps", type=int, default=0,
                    help="compare only the first k HVPs with the reference (0: all)")
+    p.add_argument("--kernel", default="",
+                   choices=["", "forward", "forward_pack", "adjoint", "incremental",
+                            "encode_window", "decode_window"],
+                   help="instead of the benchmark: time one hot-path kernel alone "
+                        "(aew_profile_steps) on an AE handle of --shape, for profiling")
+    p.add_argument("--launches", type=int, default=16)
     return p.parse_args()
 
 
@@ -331,6 +337,20 @@ def run_ours(args):
     ae_hvp_ms = h0.elapsed_time(h1) / args.steps
     hv_ae = hv.clone()
 
+    # ---- full Newton HVPs (second-order terms; the incremental strain compressed too)
+    hvf_ae, ae_hvpf_ms = None, None
+    if args.codec == "time":
+        hvf = torch.empty_like(c)
+        multishot.multishot_hessvec(lambda: ae.hessvec_full(dc, hvf))
+        torch.cuda.synchronize()
+        h0.record(stream)
+        for _ in range(max(1, args.steps // 2)):
+            multishot.multishot_hessvec(lambda: ae.hessvec_full(dc, hvf))
+        h1.record(stream)
+        torch.cuda.synchronize()
+        ae_hvpf_ms = h0.elapsed_time(h1) / max(1, args.steps // 2)
+        hvf_ae = hvf.clone()
+
     # ---- end to end through the public API with host buffers
     c_host = torch.from_numpy(c_np).pin_memory()
     d_host = d_obs.cpu().pin_memory()
@@ -435,6 +455,7 @@ def run_ours(args):
     del req
     torch.cuda.empty_cache()
     full = None
+    hvf_exact = "full storage unavailable"
     hist = nt * C * 4
     if torch.cuda.mem_get_info()[0] > hist + 16 * C * 8:
         try:
@@ -449,6 +470,12 @@ def run_ours(args):
             g_exact = g.clone()
             hv_shots(fs)
             hv_exact = hv.clone()
+            if hvf_ae is not None:
+                try:      # needs a second e^n-sized history (the incremental strain)
+                    multishot.multishot_hessvec(lambda: fs.hessvec_full(dc, hv))
+                    hvf_exact = hv.clone()
+                except aewave.AewError as err:
+                    hvf_exact = str(err)
             del fs
             torch.cuda.empty_cache()
     else:
@@ -465,6 +492,9 @@ def run_ours(args):
         "codec_weights": os.path.relpath(wpath, ROOT) if trained else "random-init",
         "target": "<= 1e-2 relative to the full-storage gradient / HVP",
     }
+    if hvf_ae is not None:
+        accuracy["hvp_full_newton_rel_err"] = (rel(hvf_ae, hvf_exact) if torch.is_tensor(hvf_exact)
+                                              else f"no full-storage reference: {hvf_exact}")
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -508,6 +538,10 @@ def run_ours(args):
                     "ae_hvps_per_hour": 3600e3 / ae_hvp_ms, "revolve_forward_steps": rev_hvp_fwd,
                     "note": "Gauss-Newton HVP reusing the gradient's latents (AE) vs recomputing "
                             "states from 20 checkpoint slots"},
+            "hvp_full_newton": None if ae_hvpf_ms is None else
+                {"ae_ms": ae_hvpf_ms, "ae_hvps_per_hour": 3600e3 / ae_hvpf_ms,
+                 "note": "full Newton HVP: incremental forward with its strain compressed by the "
+                         "time codec, then first- and second-order adjoints in lockstep"},
             "e2e": {"value": world * 3600.0 / e2e_s, "unit": "gradients/hour",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
@@ -638,9 +672,30 @@ def run_accuracy(args):
     print(json.dumps(out))
 
 
+def run_kernel(args):
+    """One hot-path kernel alone: 2 warm-up launches, then --launches timed ones (CUDA
+    events on the launching stream); prints one JSON line."""
+    import torch
+    from paper_2304_04781_gb300 import aewave, inputs
+    shape, nt = tuple(args.shape), args.nt
+    nz, ny, nx = shape
+    n_lat = nlat_of(args)
+    W, trained = load_weights(args.weights or default_weights(args.codec, n_lat), args.codec, n_lat)
+    s = aewave.Solver(shape, H, nt, inputs.receiver_grid(nx, ny, args.nrec), storage="ae",
+                      codec=args.codec, n_lat=n_lat)
+    s.codec_set(W)
+    c = torch.from_numpy(inputs.velocity_model(shape, H, seed=2).astype(np.float32)).cuda()
+    s.profile(c, args.kernel, 2)
+    ms = s.profile(c, args.kernel, args.launches)
+    print(json.dumps({"kernel": args.kernel, "shape": list(shape), "ms_per_launch": ms,
+                      "launches": args.launches, "codec_weights": "trained" if trained else "random-init"}))
+
+
 def main():
     args = parse()
-    if args.accuracy:
+    if args.kernel:
+        run_kernel(args)
+    elif args.accuracy:
         run_accuracy(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -281,6 +281,25 @@ int aew_gradient(aew_handle* h, const float* c_dev, const float* d_obs_dev,
  * incremental adjoint with residual B dv).  AEW_E_NOGRADIENT if no gradient ran. */
 int aew_hessvec(aew_handle* h, const float* dc_dev, float* hdc_dev, void* stream);
 
+/* Full Newton Hessian-vector product at the c of the last aew_gradient (Sec. 4's
+ * incremental forward and incremental adjoint problems with the second-order terms):
+ *   hdc_dev = H dc = 2 c H_m(2 c dc) + 2 dc dJ/dm,
+ *   H_m dm = sum_n dt (de^n q^n + e^n dq^n),
+ * de^n the incremental forward strain, q^n = G^T lam^{n+1} the first-order adjoint of
+ * the last gradient's residual, dq^n the second-order adjoint: the adjoint recursion
+ * driven by the residual B dv plus the source dt dm q^n in its mu update.  The
+ * incremental forward keeps its strain history (FP32 with full storage; compressed by
+ * the time codec into a second latent store with AE storage), then the two adjoints run
+ * backward in lockstep (two adjoint steps per time step).  Needs full storage or AE
+ * storage with the time codec (AEW_E_CONFIG otherwise) and a prior aew_gradient
+ * (AEW_E_NOGRADIENT).  The first call allocates the extra buffers -- with full storage a
+ * second nt * nx*ny*nz FP32 history, with the time codec a second latent store and two
+ * decoded windows, and in both cases the second adjoint's states and accumulators --
+ * and returns AEW_E_NOMEM if they do not fit.  At zero residual the result equals
+ * aew_hessvec's.  With the time codec the call synchronises the stream (latent
+ * overflow check). */
+int aew_hessvec_full(aew_handle* h, const float* dc_dev, float* hdc_dev, void* stream);
+
 /* Jacobian-vector product dd_dev = J_F dc_dev [nt+1][nrec][3] (incremental forward
  * alone) at the c of the last aew_gradient. */
 int aew_jvp(aew_handle* h, const float* dc_dev, float* dd_dev, void* stream);

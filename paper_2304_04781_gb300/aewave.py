@@ -91,6 +91,7 @@ _SIGS = [
                               c_void_p, c_void_p]),
     ("aew_gradient", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_double), c_void_p]),
     ("aew_hessvec", c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("aew_hessvec_full", c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     ("aew_jvp", c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     ("aew_snapshots", c_int, [c_void_p, c_void_p, c_int, c_void_p, c_longlong, c_void_p,
                               POINTER(c_longlong), c_void_p]),
@@ -318,6 +319,14 @@ class Solver:
         if out is None:
             out = torch.empty_like(dc)
         self._check(lib().aew_hessvec(self._h, _ptr(dc), _ptr(out), _stream()))
+        return out
+
+    def hessvec_full(self, dc: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Full Newton Hessian-vector product (second-order terms included) at the c of
+        the last gradient."""
+        if out is None:
+            out = torch.empty_like(dc)
+        self._check(lib().aew_hessvec_full(self._h, _ptr(dc), _ptr(out), _stream()))
         return out
 
     def jvp(self, dc: torch.Tensor) -> torch.Tensor:

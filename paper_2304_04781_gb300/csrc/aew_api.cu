@@ -75,6 +75,20 @@ struct aew_handle {
   float* edt[2] = {};
   uint16_t* wk_raw = nullptr;
   unsigned* wk_vmax = nullptr;
+  // full Newton HVP: the last gradient (FP32, for its 2 dc dJ/dm term), the second-order
+  // adjoint's states and accumulators, the first-order adjoint's dt q, and the
+  // incremental strain history (FP32 for full storage; latents of the time codec)
+  float* gc = nullptr;
+  bool nw_ready = false;
+  float* ad2[2][4] = {};
+  float* acc32b = nullptr;
+  double* acc64b = nullptr;
+  float* qbuf = nullptr;
+  float* desto = nullptr;
+  uint16_t* lat2 = nullptr;
+  unsigned* vmx2 = nullptr;
+  float* edt2[2] = {};
+  cudaEvent_t ev_c[2] = {}, ev_d[2] = {};
   // device timing of the last gradient and hessvec (read lazily by aew_stats)
   cudaEvent_t tg[2] = {}, th[2] = {};
   bool tg_set = false, th_set = false;
@@ -187,8 +201,12 @@ int fwd_step(aew_handle* h, int n, float* const in[4], float* const out[4], cons
 }
 
 int incr_step(aew_handle* h, float* const in[4], float* const out[4], const float* en,
-              float* d_row, cudaStream_t s) {
+              float* d_row, cudaStream_t s, uint16_t* tpack = nullptr, int tslot = 0,
+              unsigned* vmax = nullptr) {
   aew::FwdStep a{};
+  a.tpack = tpack;
+  a.tslot = tslot;
+  a.vmax = vmax;
   a.m = h->m;
   a.e = in[0];
   a.vx = in[1];
@@ -218,22 +236,27 @@ int incr_step(aew_handle* h, float* const in[4], float* const out[4], const floa
   return AEW_OK;
 }
 
-// reverse step n: (lam, mu) in ad[cur] -> ad[cur ^ 1]
-int adj_step(aew_handle* h, int n, int cur, const float* resid, const float* en,
-             cudaStream_t s) {
+// reverse step n on explicit buffers: (mu, lam) in `in` -> `out`, accumulating
+// e^n dt q into (acc32, acc64); qout / qin + dm2: the full Newton HVP's coupling
+int adj_step_x(aew_handle* h, int n, float* const in[4], float* const out[4],
+               const float* resid, const float* en, float* acc32, double* acc64, float* qout,
+               const float* qin, const float* dm2, cudaStream_t s) {
   aew::AdjStep a{};
   a.m = h->m;
-  a.mu = h->ad[cur][0];
-  a.lx = h->ad[cur][1];
-  a.ly = h->ad[cur][2];
-  a.lz = h->ad[cur][3];
-  a.mu1 = h->ad[cur ^ 1][0];
-  a.lx1 = h->ad[cur ^ 1][1];
-  a.ly1 = h->ad[cur ^ 1][2];
-  a.lz1 = h->ad[cur ^ 1][3];
+  a.mu = in[0];
+  a.lx = in[1];
+  a.ly = in[2];
+  a.lz = in[3];
+  a.mu1 = out[0];
+  a.lx1 = out[1];
+  a.ly1 = out[2];
+  a.lz1 = out[3];
   a.en = en;
-  a.acc32 = h->acc32;
-  a.acc64 = h->acc64;
+  a.acc32 = acc32;
+  a.acc64 = acc64;
+  a.qout = qout;
+  a.qin = qin;
+  a.dm2 = dm2;
   const int W = h->cfg.accum_window;
   const int w = (h->cfg.nt - 1 - n) % W;
   a.acc_mode = (w == 0 ? aew::kAccFirst : 0) | ((w == W - 1 || n == 0) ? aew::kAccLast : 0);
@@ -249,6 +272,13 @@ int adj_step(aew_handle* h, int n, int cur, const float* resid, const float* en,
   AEW_CK(aew::launch_adj_step(a, s));
   ++h->stats.kernel_launches;
   return AEW_OK;
+}
+
+// reverse step n: (lam, mu) in ad[cur] -> ad[cur ^ 1]
+int adj_step(aew_handle* h, int n, int cur, const float* resid, const float* en,
+             cudaStream_t s) {
+  return adj_step_x(h, n, h->ad[cur], h->ad[cur ^ 1], resid, en, h->acc32, h->acc64, nullptr,
+                    nullptr, nullptr, s);
 }
 
 int zero_state(aew_handle* h, float* const f[4], cudaStream_t s) {
@@ -643,6 +673,176 @@ int gradient_ae_time(aew_handle* h, const float* d_obs, const float* wav, cudaSt
   return AEW_OK;
 }
 
+// ---------------------------------------------------------------------------------
+// Full Newton HVP
+// ---------------------------------------------------------------------------------
+// buffers of the second-order adjoint and the incremental strain history (first call)
+int ensure_newton(aew_handle* h) {
+  if (h->nw_ready) return AEW_OK;
+  const size_t C = h->C, nt = (size_t)h->cfg.nt;
+  bool ok = dalloc(h, &h->acc32b, C) && dalloc(h, &h->acc64b, C) && dalloc(h, &h->qbuf, C);
+  for (int b = 0; ok && b < 2; ++b)
+    for (int i = 0; ok && i < 4; ++i) ok = dalloc(h, &h->ad2[b][i], C);
+  if (ok && h->cfg.storage == AEW_FULL) ok = dalloc(h, &h->desto, nt * C);
+  if (ok && h->cfg.storage == AEW_AE) {
+    const size_t nv = nvec_of(h), W = (size_t)nwin_of(h);
+    ok = dalloc(h, &h->lat2, W * nv * h->cfg.n_lat) && dalloc(h, &h->vmx2, W * nv) &&
+         dalloc(h, &h->edt2[0], aew::kTSteps * C) && dalloc(h, &h->edt2[1], aew::kTSteps * C);
+    for (int i = 0; ok && i < 2; ++i)
+      ok = cudaEventCreateWithFlags(&h->ev_c[i], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&h->ev_d[i], cudaEventDisableTiming) == cudaSuccess;
+  }
+  if (!ok) {
+    cudaGetLastError();
+    return fail(h, AEW_E_NOMEM, "device allocation failed for the full Newton HVP buffers");
+  }
+  h->stats.device_bytes = h->bytes + aew::codec_device_bytes(h->codec);
+  h->nw_ready = true;
+  return AEW_OK;
+}
+
+// incremental forward keeping the incremental strain history: full storage writes it to
+// desto; the time codec packs it into windows (xt) and encodes them (lat2, vmx2) on the
+// side stream, while the forward strain's windows are decoded ahead as in
+// incremental_forward.  ev_a/ev_b: e windows read / decoded; ev_c/ev_d: de windows
+// complete / encoded.
+int newton_incremental_forward(aew_handle* h, cudaStream_t s) {
+  const int nt = h->cfg.nt;
+  int rc;
+  if ((rc = zero_state(h, h->ad[0], s))) return rc;
+  if (h->nrow) AEW_CK(cudaMemsetAsync(h->dd, 0, h->nrow * sizeof(float), s));
+  int cur = 0;
+  if (h->cfg.storage == AEW_FULL) {
+    AEW_CK(cudaMemsetAsync(h->desto, 0, h->C * sizeof(float), s));
+    for (int n = 0; n < nt; ++n) {
+      float* in[4] = {h->desto + (size_t)n * h->C, h->ad[cur][1], h->ad[cur][2], h->ad[cur][3]};
+      float* eo = n + 1 < nt ? h->desto + (size_t)(n + 1) * h->C : h->ad[cur ^ 1][0];
+      float* out[4] = {eo, h->ad[cur ^ 1][1], h->ad[cur ^ 1][2], h->ad[cur ^ 1][3]};
+      const float* en = n > 0 ? h->estore + (size_t)n * h->C : nullptr;
+      if ((rc = incr_step(h, in, out, en, drow(h, h->dd, n + 1), s))) return rc;
+      cur ^= 1;
+    }
+    return AEW_OK;
+  }
+  const int W = nwin_of(h), T = aew::kTSteps;
+  const size_t nv = nvec_of(h), wbytes = nv * aew::kNIn * sizeof(uint16_t);
+  AEW_CK(cudaMemsetAsync(h->ovf, 0, sizeof(int), s));
+  AEW_CK(cudaMemsetAsync(h->vmx2, 0, (size_t)W * nv * sizeof(unsigned), s));
+  AEW_CK(cudaMemsetAsync(h->xt[0], 0, wbytes, s));   // de^0 = 0
+  if ((rc = join(h, s, h->side, h->ev_sync))) return rc;
+  auto encode_de = [&](int tb) -> int {
+    AEW_CK(cudaEventRecord(h->ev_c[tb & 1], s));
+    AEW_CK(cudaStreamWaitEvent(h->side, h->ev_c[tb & 1], 0));
+    cudaError_t e = aew::codec_encode_window(h->codec, h->xt[tb & 1], h->vmx2 + (size_t)tb * nv,
+                                             (long long)nv, h->lat2 + (size_t)tb * nv * h->cfg.n_lat,
+                                             h->ovf, h->side, h->overlap_ctas);
+    if (e != cudaSuccess) return cuda_fail(h, e, "codec_encode_window");
+    h->stats.kernel_launches += 2;
+    AEW_CK(cudaEventRecord(h->ev_d[tb & 1], h->side));
+    return AEW_OK;
+  };
+  if ((rc = decode_window(h, 0, h->side))) return rc;
+  AEW_CK(cudaEventRecord(h->ev_b[0], h->side));
+  if (nt == 1 && (rc = encode_de(0))) return rc;
+  for (int n = 0; n < nt; ++n) {
+    const int tb = n / T;
+    if (n % T == 0) {
+      if (tb + 1 <= W - 1) {
+        if (tb >= 1) AEW_CK(cudaStreamWaitEvent(h->side, h->ev_a[(tb + 1) & 1], 0));
+        if ((rc = decode_window(h, tb + 1, h->side))) return rc;
+        AEW_CK(cudaEventRecord(h->ev_b[(tb + 1) & 1], h->side));
+      }
+      AEW_CK(cudaStreamWaitEvent(s, h->ev_b[tb & 1], 0));
+    }
+    const int m = n + 1, to = m / T, slot = m % T;
+    uint16_t* tp = nullptr;
+    unsigned* vm = nullptr;
+    if (m <= nt - 1) {
+      if (slot == 0) {
+        if (to >= 2) AEW_CK(cudaStreamWaitEvent(s, h->ev_d[to & 1], 0));
+        if (T * to + T > nt) AEW_CK(cudaMemsetAsync(h->xt[to & 1], 0, wbytes, s));
+      }
+      tp = h->xt[to & 1];
+      vm = h->vmx2 + (size_t)to * nv;
+    }
+    if ((rc = incr_step(h, h->ad[cur], h->ad[cur ^ 1], window_e(h, n), drow(h, h->dd, n + 1), s,
+                        tp, slot, vm)))
+      return rc;
+    cur ^= 1;
+    if (n % T == T - 1 || n == nt - 1) AEW_CK(cudaEventRecord(h->ev_a[tb & 1], s));
+    if (m <= nt - 1 && (slot == T - 1 || m == nt - 1) && (rc = encode_de(to))) return rc;
+  }
+  return join(h, h->side, s, h->ev_sync2);
+}
+
+// decoder of the incremental strain's window tb into edt2[tb % 2]
+int decode_de_window(aew_handle* h, int tb, cudaStream_t s) {
+  const size_t nv = nvec_of(h);
+  cudaError_t e = aew::codec_decode_window(h->codec, h->lat2 + (size_t)tb * nv * h->cfg.n_lat,
+                                           h->vmx2 + (size_t)tb * nv, h->cfg.nx, h->cfg.ny,
+                                           h->cfg.nz, h->edt2[tb & 1], s, h->overlap_ctas);
+  if (e != cudaSuccess) return cuda_fail(h, e, "codec_decode_window");
+  h->stats.kernel_launches += 2;
+  return AEW_OK;
+}
+
+// the two adjoints in lockstep, n = nt-1 .. 0: first order (ad, residual R, accumulating
+// de^n dt q into acc32/acc64, writing dt q), second order (ad2, residual B dv = dd,
+// accumulating e^n dt dq into acc32b/acc64b, with the dm dt q source)
+int newton_adjoint_sweep(aew_handle* h, cudaStream_t s) {
+  const int nt = h->cfg.nt, T = aew::kTSteps;
+  int rc;
+  for (int i = 0; i < 4; ++i) {
+    AEW_CK(cudaMemsetAsync(h->ad[0][i], 0, h->C * sizeof(float), s));
+    AEW_CK(cudaMemsetAsync(h->ad2[0][i], 0, h->C * sizeof(float), s));
+  }
+  AEW_CK(cudaMemsetAsync(h->acc64, 0, h->C * sizeof(double), s));
+  AEW_CK(cudaMemsetAsync(h->acc64b, 0, h->C * sizeof(double), s));
+  const bool ae = h->cfg.storage == AEW_AE;
+  const int W = nwin_of(h);
+  auto decode_both = [&](int tb) -> int {
+    int r = decode_window(h, tb, h->side);
+    if (!r) r = decode_de_window(h, tb, h->side);
+    return r;
+  };
+  if (ae) {
+    if ((rc = join(h, s, h->side, h->ev_sync))) return rc;
+    if ((rc = decode_both(W - 1))) return rc;
+    AEW_CK(cudaEventRecord(h->ev_b[(W - 1) & 1], h->side));
+  }
+  int cur = 0;
+  for (int n = nt - 1; n >= 0; --n) {
+    const float* en = nullptr;
+    const float* den = nullptr;
+    if (ae) {
+      const int tb = n / T;
+      if (n == nt - 1 || n % T == T - 1) {
+        if (tb >= 1) {
+          if (tb + 1 <= W - 1) AEW_CK(cudaStreamWaitEvent(h->side, h->ev_a[(tb + 1) & 1], 0));
+          if ((rc = decode_both(tb - 1))) return rc;
+          AEW_CK(cudaEventRecord(h->ev_b[(tb - 1) & 1], h->side));
+        }
+        AEW_CK(cudaStreamWaitEvent(s, h->ev_b[tb & 1], 0));
+      }
+      en = window_e(h, n);
+      den = n >= 1 ? h->edt2[tb & 1] + (size_t)(n % T) * h->C : nullptr;
+    } else if (n > 0) {
+      en = h->estore + (size_t)n * h->C;
+      den = h->desto + (size_t)n * h->C;
+    }
+    if ((rc = adj_step_x(h, n, h->ad[cur], h->ad[cur ^ 1], h->R, den, h->acc32, h->acc64,
+                         h->qbuf, nullptr, nullptr, s)))
+      return rc;
+    if ((rc = adj_step_x(h, n, h->ad2[cur], h->ad2[cur ^ 1], h->dd, en, h->acc32b, h->acc64b,
+                         nullptr, h->qbuf, h->dm, s)))
+      return rc;
+    cur ^= 1;
+    if (ae && n % T == 0) AEW_CK(cudaEventRecord(h->ev_a[(n / T) & 1], s));
+  }
+  if (ae) return join(h, h->side, s, h->ev_sync2);
+  return AEW_OK;
+}
+
 // Algorithm 1 with the time codec: the complete windows tb = 0, every, 2 every, ... are
 // packed by the forward steps that write their states (raw BF16 plus per-vector
 // maxima), then normalised in place once their last state is in.
@@ -777,6 +977,8 @@ int aew_create(const aew_config* cfg, aew_handle** out) {
   for (int b = 0; ok && b < 2; ++b)
     for (int i = 0; ok && i < 4; ++i) ok = dalloc(h, &h->st[b][i], C) && dalloc(h, &h->ad[b][i], C);
   if (ok && c.storage == AEW_FULL) ok = dalloc(h, &h->estore, nt * C);
+  if (ok && (c.storage == AEW_FULL || (c.storage == AEW_AE && c.codec == AEW_CODEC_TIME)))
+    ok = dalloc(h, &h->gc, C);
   if (ok && c.storage == AEW_REVOLVE && c.n_checkpoints > 0)
     ok = dalloc(h, &h->ckpt, (size_t)c.n_checkpoints * 4 * C);
   for (int i = 0; ok && c.storage == AEW_REVOLVE && i < 4; ++i) {
@@ -860,6 +1062,8 @@ void aew_destroy(aew_handle* h) {
   for (int i = 0; i < 2; ++i) {
     if (h->tg[i]) cudaEventDestroy(h->tg[i]);
     if (h->th[i]) cudaEventDestroy(h->th[i]);
+    if (h->ev_c[i]) cudaEventDestroy(h->ev_c[i]);
+    if (h->ev_d[i]) cudaEventDestroy(h->ev_d[i]);
   }
   if (h->ev_sync) cudaEventDestroy(h->ev_sync);
   if (h->ev_sync2) cudaEventDestroy(h->ev_sync2);
@@ -988,6 +1192,7 @@ int aew_gradient(aew_handle* h, const float* c_dev, const float* d_obs_dev, floa
     return fail(h, AEW_E_TIMEOUT, "a kernel gave up waiting (bounded mbarrier wait)");
   AEW_CK(aew::launch_finalize_grad(h->c, h->acc64, g_dev, h->C, s));
   ++h->stats.kernel_launches;
+  if (h->gc) AEW_CK(cudaMemcpyAsync(h->gc, g_dev, h->C * sizeof(float), cudaMemcpyDeviceToDevice, s));
   AEW_CK(cudaEventRecord(h->tg[1], s));
   h->tg_set = true;
   if (misfit_host || h->cfg.storage == AEW_AE) {
@@ -1145,6 +1350,36 @@ int aew_hessvec(aew_handle* h, const float* dc_dev, float* hdc_dev, void* stream
   ++h->stats.kernel_launches;
   AEW_CK(cudaEventRecord(h->th[1], s));
   h->th_set = true;
+  return AEW_OK;
+}
+
+int aew_hessvec_full(aew_handle* h, const float* dc_dev, float* hdc_dev, void* stream) {
+  if (!h) return AEW_E_ARG;
+  if (!hdc_dev) return fail(h, AEW_E_ARG, "hdc is NULL");
+  if (!h->gc)
+    return fail(h, AEW_E_CONFIG, "the full Newton HVP needs full storage or the time codec");
+  h->err.clear();
+  cudaStream_t s = S(stream);
+  int rc = prepare_dc(h, dc_dev, s);
+  if (rc) return rc;
+  if ((rc = ensure_newton(h))) return rc;
+  h->th_set = false;
+  AEW_CK(cudaEventRecord(h->th[0], s));
+  if ((rc = newton_incremental_forward(h, s))) return rc;
+  if ((rc = newton_adjoint_sweep(h, s))) return rc;
+  h->stats.hvp_forward_steps = h->cfg.nt;
+  if (aew::codec_take_error(h->codec, s))
+    return fail(h, AEW_E_TIMEOUT, "a kernel gave up waiting (bounded mbarrier wait)");
+  AEW_CK(aew::launch_finalize_hvp_full(h->c, dc_dev, h->acc64, h->acc64b, h->gc, hdc_dev, h->C, s));
+  ++h->stats.kernel_launches;
+  AEW_CK(cudaEventRecord(h->th[1], s));
+  h->th_set = true;
+  if (h->cfg.storage == AEW_AE) {
+    int ovf = 0;
+    AEW_CK(cudaMemcpyAsync(&ovf, h->ovf, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AEW_CK(cudaStreamSynchronize(s));
+    if (ovf) return fail(h, AEW_E_OVERFLOW, "a latent overflowed FP16 during encoding");
+  }
   return AEW_OK;
 }
 

@@ -85,6 +85,12 @@ struct AdjStep {
   int krec;
   const int* rec_map;
   const float* resid;  // residual row r^{n+1} [nrec][3] (or null)
+  // Full Newton HVP (both optional): qout receives this step's dt q (0 on boundary
+  // nodes); with qin and dm2 the mu update gains the second-order adjoint's source:
+  //   mu' = interior ? mu + m dtq + dm2 qin : 0   (qin = the first-order adjoint's dt q)
+  float* qout;
+  const float* qin;
+  const float* dm2;
   int* err;            // sticky device error flag (set on a timed-out wait)
 };
 
@@ -122,6 +128,11 @@ cudaError_t launch_sum_partials(const double* part, int nblk, double scale, doub
 // g = 2 c acc64 (FP32 output)
 cudaError_t launch_finalize_grad(const float* c, const double* acc64, float* g, size_t n,
                                  cudaStream_t s);
+// out = 2 c (a + b) + (dc / c) g  (full Newton HVP from its two accumulators and the
+// gradient g of the same c)
+cudaError_t launch_finalize_hvp_full(const float* c, const float* dc, const double* a,
+                                     const double* b, const float* g, float* out, size_t n,
+                                     cudaStream_t s);
 constexpr int kRedBlocks = 1024;
 
 }  // namespace aew

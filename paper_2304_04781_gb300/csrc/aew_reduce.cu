@@ -113,6 +113,19 @@ __global__ void finalize_grad_kernel(const float* __restrict__ c, const double* 
     g[i] = (float)(2.0 * (double)c[i] * acc[i]);
 }
 
+// full Newton HVP in c: H dc = 2 c (accA + accB) + (dc / c) g, with g = 2 c dJ/dm the
+// gradient of the same c (so (dc / c) g = 2 dc dJ/dm)
+__global__ void finalize_hvp_full_kernel(const float* __restrict__ c, const float* __restrict__ dc,
+                                         const double* __restrict__ a, const double* __restrict__ b,
+                                         const float* __restrict__ g, float* __restrict__ out,
+                                         size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const double ci = (double)c[i];
+    out[i] = (float)(2.0 * ci * (a[i] + b[i]) + (double)dc[i] / ci * (double)g[i]);
+  }
+}
+
 int grid_for(size_t n) {
   size_t b = (n + RT - 1) / RT;
   if (b > 152 * 8) b = 152 * 8;
@@ -148,6 +161,12 @@ cudaError_t launch_sum_partials(const double* part, int nblk, double scale, doub
 cudaError_t launch_finalize_grad(const float* c, const double* acc64, float* g, size_t n,
                                  cudaStream_t s) {
   finalize_grad_kernel<<<grid_for(n), RT, 0, s>>>(c, acc64, g, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_finalize_hvp_full(const float* c, const float* dc, const double* a,
+                                     const double* b, const float* g, float* out, size_t n,
+                                     cudaStream_t s) {
+  finalize_hvp_full_kernel<<<grid_for(n), RT, 0, s>>>(c, dc, a, b, g, out, n);
   return cudaGetLastError();
 }
 

@@ -529,6 +529,9 @@ __device__ __forceinline__ void inj4(const AdjStep& a, int y, int i0, float4& lx
   }
 }
 
+// V bit 0: write dt q to a.qout; bit 1: add a.dm2 * a.qin to the mu update (full Newton
+// HVP: the first-order adjoint writes its dt q, the second-order adjoint reads it)
+template <int V>
 __global__ void __launch_bounds__(NTHR, 2)
     adj_tma_kernel(const __grid_constant__ AdjMaps mp, const AdjStep a, int S) {
   extern __shared__ uint8_t smem_raw[];
@@ -598,6 +601,10 @@ __global__ void __launch_bounds__(NTHR, 2)
       a64lo = p64[0];
       a64hi = p64[1];
     }
+    // second-order source dm2 * qin of the own nodes, in flight while the planes land
+    float4 src2 = z4();
+    if ((V & 2) && act) src2 = mul4(__ldg(reinterpret_cast<const float4*>(a.dm2 + i)),
+                                     __ldg(reinterpret_cast<const float4*>(a.qin + i)));
     if (!r.wait(k) || !r.wait(k + 1)) failed = true;
     const uint8_t* sc = r.at(k);
     const uint8_t* sn = r.at(k + 1);
@@ -662,8 +669,12 @@ __global__ void __launch_bounds__(NTHR, 2)
       if (i0 == 0) dq.x = 0.f;
       if (i0 + 4 == nx) dq.w = 0.f;
     }
-    const float4 mu1 = fma4(m4, dq, mu_c);
+    // boundary nodes: mu_c, dq and (written as 0 there) qin are all 0
+    const float4 mu1 = (V & 2) ? fma4(m4, dq, make_float4(mu_c.x + src2.x, mu_c.y + src2.y,
+                                                         mu_c.z + src2.z, mu_c.w + src2.w))
+                               : fma4(m4, dq, mu_c);
     if (act && !failed) {
+      if (V & 1) st4(a.qout, i, dq);
       st4(a.mu1, i, mu1);
       st4(a.lx1, i, lx1);
       st4(a.ly1, i, ly1);
@@ -759,6 +770,19 @@ cudaError_t launch_fwd(const FwdMaps& mp, const FwdStep& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <int V>
+cudaError_t launch_adj(const AdjMaps& mp, const AdjStep& a, cudaStream_t s) {
+  const int S = stages_for(true);
+  const size_t smem = (size_t)S * AdjLayout::BYTES + 128;
+  // once per instantiation (thread-safe static initialisation)
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      adj_tma_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      (int)(kMaxStages * AdjLayout::BYTES + 128));
+  if (attr != cudaSuccess) return attr;
+  adj_tma_kernel<V><<<grid_of(a.nx, a.ny, a.nz, a.kc), dim3(32, TY), smem, s>>>(mp, a, S);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 int default_kc(int nx, int ny, int nz, bool adjoint) {
@@ -798,6 +822,13 @@ cudaError_t launch_fwd_step(const FwdStep& a, bool incremental, cudaStream_t s) 
     ok = field_map(&mp.dm, a.dm, nx, ny, nz, kWE, TY + 2) &&
          field_map(&mp.ef, a.ef, nx, ny, nz, kWE, TY + 2);
   if (!ok) return cudaErrorInvalidValue;
+  if (incremental && a.tpack) {
+    if (nx % 8 || ny % 8 || nz % 2 || !a.vmax || a.tslot < 0 || a.tslot >= 16)
+      return cudaErrorInvalidValue;
+    FwdStep b = a;
+    b.kc = (a.kc + 1) / 2 * 2;
+    return launch_fwd<true, false, false, true>(mp, b, s);
+  }
   if (incremental) return launch_fwd<true, false, false>(mp, a, s);
   if (a.tpack) {
     // window packing works on 2 x 8 x 8-node blocks: whole z pairs inside one CTA
@@ -840,14 +871,14 @@ cudaError_t launch_adj_step(const AdjStep& a, cudaStream_t s) {
   if (ok && a.en) ok = field_map(&mp.en, a.en, nx, ny, nz, kTXW, TY);
   if (ok && !(a.acc_mode & kAccFirst)) ok = field_map(&mp.w, a.acc32, nx, ny, nz, kTXW, TY);
   if (!ok) return cudaErrorInvalidValue;
-  const int S = stages_for(true);
-  const size_t smem = (size_t)S * AdjLayout::BYTES + 128;
-  static const cudaError_t attr = cudaFuncSetAttribute(
-      adj_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-      (int)(kMaxStages * AdjLayout::BYTES + 128));
-  if (attr != cudaSuccess) return attr;
-  adj_tma_kernel<<<grid_of(nx, ny, nz, a.kc), dim3(32, TY), smem, s>>>(mp, a, S);
-  return cudaGetLastError();
+  if ((a.qin != nullptr) != (a.dm2 != nullptr)) return cudaErrorInvalidValue;
+  const int V = (a.qout ? 1 : 0) | (a.qin ? 2 : 0);
+  switch (V) {
+    case 0: return launch_adj<0>(mp, a, s);
+    case 1: return launch_adj<1>(mp, a, s);
+    case 2: return launch_adj<2>(mp, a, s);
+    default: return launch_adj<3>(mp, a, s);
+  }
 }
 
 }  // namespace aew
