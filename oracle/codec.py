@@ -84,6 +84,21 @@ def gelu_prime(x):
     return 0.5 * (1.0 + erf(x / math.sqrt(2.0))) + x * np.exp(-0.5 * x * x) / math.sqrt(2.0 * math.pi)
 
 
+def elu(x):
+    """ELU of Sec. 3.3: e^y - 1 for y < 0, y otherwise."""
+    x = np.asarray(x, dtype=np.float64)
+    return np.where(x < 0, np.expm1(np.minimum(x, 0.0)), x)
+
+
+def elu_prime(x):
+    x = np.asarray(x, dtype=np.float64)
+    return np.where(x < 0, np.exp(np.minimum(x, 0.0)), 1.0)
+
+
+ACTIVATIONS = {"gelu": (gelu, gelu_prime), "elu": (elu, elu_prime),
+               "linear": (lambda a: a, lambda a: np.ones_like(a))}
+
+
 # --------------------------------------------------------------------------------------
 # Block packing (Sec. 3.1 "compression data structure")
 # --------------------------------------------------------------------------------------
@@ -150,14 +165,16 @@ def normalise(X: np.ndarray, s) -> np.ndarray:
 # --------------------------------------------------------------------------------------
 # Encoder / decoder
 # --------------------------------------------------------------------------------------
-def encode(W: dict, Y: np.ndarray, emulate: bool = False) -> np.ndarray:
-    """Normalised vectors Y [B][2048] -> latents [B][n_lat] (FP16-rounded if emulate)."""
+def encode(W: dict, Y: np.ndarray, emulate: bool = False, act: str = "gelu") -> np.ndarray:
+    """Normalised vectors Y [B][2048] -> latents [B][n_lat] (FP16-rounded if emulate);
+    act: the hidden layer's activation (GELU, or the paper's ELU)."""
+    sig = ACTIVATIONS[act][0]
     W1, b1, W2, b2 = (np.asarray(W[k], np.float64) for k in ("W1", "b1", "W2", "b2"))
     if emulate:
         Y = round_bf16(Y)
         W1, W2 = round_bf16(W1), round_bf16(W2)
         b1, b2 = round_fp32(b1), round_fp32(b2)
-    h = gelu(Y @ W1 + b1)
+    h = sig(Y @ W1 + b1)
     if emulate:
         h = round_bf16(h)
     z = h @ W2 + b2
@@ -166,8 +183,10 @@ def encode(W: dict, Y: np.ndarray, emulate: bool = False) -> np.ndarray:
     return z
 
 
-def decode(W: dict, Z: np.ndarray, emulate: bool = False, cols=None) -> np.ndarray:
+def decode(W: dict, Z: np.ndarray, emulate: bool = False, cols=None,
+           act: str = "gelu") -> np.ndarray:
     """Latents Z [B][n_lat] -> normalised reconstruction [B][2048] (or [B][len(cols)])."""
+    sig = ACTIVATIONS[act][0]
     W3, b3, W4, b4 = (np.asarray(W[k], np.float64) for k in ("W3", "b3", "W4", "b4"))
     if cols is not None:
         W4, b4 = W4[:, cols], b4[cols]
@@ -176,7 +195,7 @@ def decode(W: dict, Z: np.ndarray, emulate: bool = False, cols=None) -> np.ndarr
         W3 = round_fp16(W3)
         W4 = round_bf16(W4)
         b3, b4 = round_fp32(b3), round_fp32(b4)
-    h = gelu(Z @ W3 + b3)
+    h = sig(Z @ W3 + b3)
     if emulate:
         h = round_bf16(h)
     return h @ W4 + b4
@@ -222,12 +241,9 @@ def loss_and_grad(W: dict, Y: np.ndarray, emulate: bool = False, act: str = "gel
     (straight-through).  With emulate, GEMM operands are rounded as on the GPU:
     BF16 for all products except the decoder's first-layer forward product (FP16).
     act="linear" drops both activations (the linear autoencoder of Sec. 1, which
-    learns the PCA subspace).
+    learns the PCA subspace); act="elu" takes the paper's ELU (Sec. 3.3).
     """
-    if act == "linear":
-        sig, sig_p = (lambda a: a), (lambda a: np.ones_like(a))
-    else:
-        sig, sig_p = gelu, gelu_prime
+    sig, sig_p = ACTIVATIONS[act]
     P = {k: np.asarray(W[k], np.float64) for k in PARAMS}
     rb = round_bf16 if emulate else (lambda a: a)
     rh = round_fp16 if emulate else (lambda a: a)

@@ -109,6 +109,22 @@ def encoder_inputs(X: np.ndarray, s: np.ndarray, emulate: bool = False) -> np.nd
     return normalise(C.round_bf16(X) if emulate else X, s)
 
 
+BETA = 1e-7    # the paper's lower bound of the min-max range (Sec. 3.3)
+
+
+def minmax_scales(X: np.ndarray, beta: float = BETA):
+    """The paper's per-vector normalisation (Sec. 3.3): offset min(y_true) and range
+    r = max(max(y_true) - min(y_true), beta), both kept in FP64."""
+    mn = X.min(axis=1)
+    r = np.maximum(X.max(axis=1) - mn, beta)
+    return mn, r
+
+
+def minmax_normalise(X: np.ndarray, mn: np.ndarray, r: np.ndarray) -> np.ndarray:
+    """y = (y_true - min) / r, in [0, 1]."""
+    return (X - mn[:, None]) / r[:, None]
+
+
 def window_vectors(e_hist, shape, tb: int):
     """Raw vectors of window tb from the strain history e_hist[n], n = 0..nt-1."""
     nt = len(e_hist)
@@ -125,19 +141,36 @@ def interior(f: np.ndarray) -> np.ndarray:
     return out
 
 
-def roundtrip_window(W: dict, e_hist, shape, tb: int, emulate: bool = False) -> np.ndarray:
+def roundtrip_window(W: dict, e_hist, shape, tb: int, emulate: bool = False,
+                     norm: str = "pow2", act: str = "gelu", beta: float = BETA) -> np.ndarray:
     """Encode and decode window tb: the decoded strain [16][nz][ny][nx] in physical
-    units (x s_v), 0 on boundary nodes (the boundary condition of Sec. 2 fixes e = 0
-    there; the stored forward strain is 0 there too)."""
+    units, 0 on boundary nodes (the boundary condition of Sec. 2 fixes e = 0 there; the
+    stored forward strain is 0 there too).
+
+    norm="pow2": each vector divided by its power-of-two scale s_v, decoded values
+    times s_v.  norm="minmax": the paper's min-max normalisation (Sec. 3.3), inputs
+    (bf16(x) - min) / r in emulated mode (the state is stored in BF16 when written, the
+    FP32 normalisation follows once the window is complete, one more rounding to BF16),
+    decoded values y r + min in FP64.  act: GELU or the paper's ELU."""
     X = window_vectors(e_hist, shape, tb)
-    s = vector_scales(X)
-    Z = C.encode(W, encoder_inputs(X, s, emulate), emulate)
-    Xh = C.decode(W, Z, emulate) * s[:, None]
+    if norm == "minmax":
+        Xs = C.round_bf16(X) if emulate else X
+        mn, r = minmax_scales(Xs, beta)
+        Y = minmax_normalise(Xs, mn, r)
+        if emulate:
+            Y = C.round_bf16(C.round_fp32(Y))
+        Z = C.encode(W, Y, emulate, act)
+        Xh = C.decode(W, Z, emulate, act=act) * r[:, None] + mn[:, None]
+    else:
+        s = vector_scales(X)
+        Z = C.encode(W, encoder_inputs(X, s, emulate), emulate, act)
+        Xh = C.decode(W, Z, emulate, act=act) * s[:, None]
     E = unpack(Xh, shape)
     return np.stack([interior(E[t]) for t in range(TSTEPS)])
 
 
-def compressed_e_history(W: dict, e_hist, emulate: bool = False):
+def compressed_e_history(W: dict, e_hist, emulate: bool = False, norm: str = "pow2",
+                         act: str = "gelu", beta: float = BETA):
     """Decoded strain history e-hat^n, n = 0..nt-1 (window by window).  The initial state
     e^0 is the zero initial condition of Eq. (2): it is known exactly and is not taken
     from the codec (window 0's scale is set by its later states, so decoding would turn
@@ -146,7 +179,7 @@ def compressed_e_history(W: dict, e_hist, emulate: bool = False):
     shape = np.asarray(e_hist[0]).shape
     out = []
     for tb in range(n_windows(nt)):
-        E = roundtrip_window(W, e_hist, shape, tb, emulate)
+        E = roundtrip_window(W, e_hist, shape, tb, emulate, norm, act, beta)
         for t in range(TSTEPS):
             n = TSTEPS * tb + t
             if n < nt:

@@ -253,3 +253,77 @@ def test_roundtrip_e_unpacks_scales_and_zeroes_the_boundary():
     inner[1:-1, 1:-1, 1:-1] = state[0][1:-1, 1:-1, 1:-1]
     np.testing.assert_allclose(e, inner, rtol=1e-9, atol=1e-9)
     assert not e[0].any() and not e[:, -1].any() and not e[:, :, 0].any()
+
+
+# --------------------------------------------------------------------------------------
+# The paper's normalisation and activation (Sec. 3.3): min-max to [0, 1], ELU
+# --------------------------------------------------------------------------------------
+def test_elu_is_continuous_with_unit_slope_at_zero_and_tends_to_minus_one():
+    x = np.linspace(-30, 30, 60001)
+    y, dy = C.elu(x), C.elu_prime(x)
+    assert np.all(y[x >= 0] == x[x >= 0])
+    assert np.all(np.diff(y) >= 0)                      # increasing (flat in FP64 below -37)
+    assert np.all(np.diff(y[x > -20]) > 0)
+    assert abs(C.elu(-1e-12) + 1e-12) < 1e-20 and C.elu_prime(-1e-12) == pytest.approx(1.0)
+    assert C.elu(-40.0) == pytest.approx(-1.0, abs=1e-15)
+    h = 1e-6
+    mid = x[(np.abs(x) > 1e-3)]
+    fd = (C.elu(mid + h) - C.elu(mid - h)) / (2 * h)
+    np.testing.assert_allclose(C.elu_prime(mid), fd, rtol=1e-7, atol=1e-9)
+
+
+def test_elu_training_gradient_matches_finite_differences():
+    rng = np.random.default_rng(31)
+    d = 2048
+    Wt = {"W1": rng.uniform(-.05, .05, (d, 8)), "b1": rng.uniform(-.5, .5, 8),
+          "W2": rng.uniform(-.5, .5, (8, 4)), "b2": rng.uniform(-.1, .1, 4),
+          "W3": rng.uniform(-.5, .5, (4, 8)), "b3": rng.uniform(-.5, .5, 8),
+          "W4": rng.uniform(-.5, .5, (8, d)), "b4": rng.uniform(-.1, .1, d)}
+    Y = rng.uniform(0, 1, (6, d))
+    L, g = C.loss_and_grad(Wt, Y, act="elu")
+    assert L == pytest.approx(float(np.mean((C.decode(Wt, C.encode(Wt, Y, act="elu"), act="elu") - Y) ** 2)),
+                              rel=1e-12)
+    eps = 1e-4
+    for name in C.PARAMS:
+        flat = Wt[name].ravel()
+        for idx in rng.choice(flat.size, size=min(3, flat.size), replace=False):
+            Wp = {k: v.copy() for k, v in Wt.items()}; Wm = {k: v.copy() for k, v in Wt.items()}
+            Wp[name].ravel()[idx] += eps; Wm[name].ravel()[idx] -= eps
+            fd = (C.loss_and_grad(Wp, Y, act="elu")[0] - C.loss_and_grad(Wm, Y, act="elu")[0]) / (2 * eps)
+            assert fd == pytest.approx(g[name].ravel()[idx], rel=1e-5, abs=1e-10), (name, idx)
+
+
+def test_minmax_normalisation_spans_zero_to_one_and_inverts_exactly():
+    rng = np.random.default_rng(32)
+    X = rng.standard_normal((40, 2048)) * 10.0 ** rng.uniform(-12, 2, (40, 1)) + rng.uniform(-1, 1, (40, 1))
+    X[5] = 0.25                                          # constant vector
+    X[6] = 3e-9 * rng.standard_normal(2048)              # range below beta
+    mn, r = CT.minmax_scales(X)
+    Y = CT.minmax_normalise(X, mn, r)
+    big = np.ptp(X, axis=1) > CT.BETA
+    assert np.all(Y >= 0) and np.all(Y[big].max(1) == pytest.approx(1.0)) and np.all(Y.min(1) == 0.0)
+    assert r[5] == CT.BETA and not Y[5].any()
+    assert r[6] == CT.BETA                               # small range: the floor is the range
+    assert Y[6].max() == pytest.approx(np.ptp(X[6]) / CT.BETA) and Y[6].max() < 1.0
+    np.testing.assert_allclose(Y * r[:, None] + mn[:, None], X, rtol=1e-15, atol=1e-15 * np.abs(X).max())
+
+
+def test_minmax_history_with_a_code_exact_on_its_data():
+    prob, c = _small_problem(nt=40)
+    _, states = W.forward_states(prob, c)
+    e_hist = [st[0] for st in states]
+    Ys = []
+    for tb in range(CT.n_windows(prob.nt)):
+        X = CT.window_vectors(e_hist, prob.shape, tb)
+        mn, r = CT.minmax_scales(X, beta=1e-30)
+        Ys.append(CT.minmax_normalise(X, mn, r))
+    Y = np.concatenate(Ys)
+    Wt = CT.pca_codec(Y, Y.shape[0])
+    eh = CT.compressed_e_history(Wt, e_hist, norm="minmax", beta=1e-30)
+    emax = max(float(np.abs(e).max()) for e in e_hist)
+    for n in range(prob.nt):
+        np.testing.assert_allclose(eh[n], e_hist[n], rtol=0, atol=1e-8 * emax)
+    # with the paper's absolute beta = 1e-7 these states (|e| ~ 1e-7 and below) are
+    # mostly squeezed under the floor of the range: the vectors are not scaled to [0, 1]
+    mn, r = CT.minmax_scales(CT.window_vectors(e_hist, prob.shape, 1))
+    assert np.mean(r == CT.BETA) > 0.5
