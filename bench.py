@@ -62,6 +62,11 @@ def parse():
     p.add_argument("--weights", default="")
     p.add_argument("--no-accuracy", action="store_true",
                    help="skip the accuracy block of the timed run (errors against full storage)")
+    p.add_argument("--norm", default="pow2", choices=["pow2", "minmax"],
+                   help="time codec normalisation (accuracy / kernel modes): power of two, or "
+                        "the paper's min-max")
+    p.add_argument("--act", default="gelu", choices=["gelu", "elu"])
+    p.add_argument("--beta", type=float, default=0.0, help="min-max range floor (0: 1e-7)")
     p.add_argument("--accuracy", action="store_true",
                    help="instead of timing: AE gradient / GN-HVP errors against full storage "
                         "(or checkpointing with --ref revolve), decoded-state error")
@@ -585,13 +590,15 @@ def run_accuracy(args):
     ctrue = torch.from_numpy(inputs.bump_model(c_np.astype(np.float64), H).astype(np.float32)).cuda()
     dirs = [torch.from_numpy(inputs.direction(shape, H, seed=(20 if args.hvps == 1 else 30) + k)
                              .astype(np.float32)).cuda() for k in range(args.hvps)]
-    out = {"config": dict(workload(shape, nt, args.nrec, n_lat, args.codec), f0_hz=args.f0),
+    out = {"config": dict(workload(shape, nt, args.nrec, n_lat, args.codec), f0_hz=args.f0,
+                          norm=args.norm, act=args.act, beta=args.beta),
            "codec_weights": "trained" if trained else "random-init", "n_lat": n_lat,
            "reference": args.ref}
     def ev():
         return torch.cuda.Event(enable_timing=True)
 
-    ae = aewave.Solver(shape, H, nt, rec, storage="ae", codec=args.codec, n_lat=n_lat, f0=args.f0)
+    ae = aewave.Solver(shape, H, nt, rec, storage="ae", codec=args.codec, n_lat=n_lat, f0=args.f0,
+                       norm=args.norm, act=args.act, beta=args.beta)
     ae.codec_set(W)
     d_obs = ae.forward(ctrue)
     a, b = ev(), ev(); a.record()
@@ -663,7 +670,8 @@ def run_accuracy(args):
 
     # decoded-state error on this run's states (every 8th window / every nt/40-th state)
     from paper_2304_04781_gb300 import train
-    tr = train.make_handle(shape, args.codec, n_lat, nt=nt, f0=args.f0)
+    tr = train.make_handle(shape, args.codec, n_lat, nt=nt, f0=args.f0, norm=args.norm,
+                           act=args.act, beta=args.beta)
     tr.codec_set(W)
     every = 8 if args.codec == "time" else max(1, nt // 40)
     snaps, mx = train.generate(tr, [2], every)
@@ -682,7 +690,7 @@ def run_kernel(args):
     n_lat = nlat_of(args)
     W, trained = load_weights(args.weights or default_weights(args.codec, n_lat), args.codec, n_lat)
     s = aewave.Solver(shape, H, nt, inputs.receiver_grid(nx, ny, args.nrec), storage="ae",
-                      codec=args.codec, n_lat=n_lat)
+                      codec=args.codec, n_lat=n_lat, norm=args.norm, act=args.act, beta=args.beta)
     s.codec_set(W)
     c = torch.from_numpy(inputs.velocity_model(shape, H, seed=2).astype(np.float32)).cuda()
     s.profile(c, args.kernel, 2)

@@ -67,6 +67,18 @@ enum {
   AEW_CODEC_TIME = 1    /* per 16-step window: the strain of 2x8x8-node blocks            */
 };
 
+/* Normalisation and activation of the time codec: the default power-of-two vector
+ * scale with GELU, or the paper's per-vector min-max normalisation to [0, 1] (offset and
+ * range kept in FP64, the range floored at beta; Sec. 3.3) and its ELU. */
+enum {
+  AEW_NORM_POW2 = 0,
+  AEW_NORM_MINMAX = 1
+};
+enum {
+  AEW_ACT_GELU = 0,
+  AEW_ACT_ELU = 1    /* e^a - 1 below 0, a above */
+};
+
 /* Error codes. */
 enum {
   AEW_OK = 0,
@@ -106,6 +118,9 @@ typedef struct {
                              the 4-field state) or 32 (64x); time codec 512 (4x of the
                              strain values, 32x of the FP32 state's bytes) or 256     */
   int codec;              /* AEW_CODEC_SPACE (0) or AEW_CODEC_TIME (1)                */
+  int norm;               /* time codec: AEW_NORM_POW2 (0) or AEW_NORM_MINMAX (1)     */
+  int act;                /* time codec: AEW_ACT_GELU (0) or AEW_ACT_ELU (1)          */
+  double beta;            /* AEW_NORM_MINMAX: floor of the range (0 = the paper's 1e-7)*/
 } aew_config;
 
 typedef struct {
@@ -229,16 +244,18 @@ int aew_codec_decode_e(aew_handle* h, const uint16_t* latents_dev, const float* 
 /* Time codec only (AEW_E_CONFIG otherwise).  Encode one window of nsteps (1..16)
  * strain fields e_dev[nsteps][nz][ny][nx] (device, contiguous, 16-byte aligned; the
  * window's later states are taken as 0) into latents_dev, device FP16 [nvec][n_lat]
- * (nvec = (nz/2)(ny/8)(nx/8)).  vmax_dev (may be NULL): device FP32 [nvec] receiving
- * each vector's largest |e|, from which its scale follows.  Synchronises the stream;
- * AEW_E_OVERFLOW if a latent overflowed FP16. */
+ * (nvec = (nz/2)(ny/8)(nx/8)).  scale_dev (may be NULL) receives what fixes each
+ * vector's scale: with AEW_NORM_POW2 device FP32 [nvec], each vector's largest |e|;
+ * with AEW_NORM_MINMAX device FP64 [2][nvec], the offsets (minima) then the ranges.
+ * Synchronises the stream; AEW_E_OVERFLOW if a latent overflowed FP16. */
 int aew_codec_encode_window(aew_handle* h, const float* e_dev, int nsteps, uint16_t* latents_dev,
-                            float* vmax_dev, void* stream);
+                            void* scale_dev, void* stream);
 
 /* Time codec only.  Decode one window: e_dev[16][nz][ny][nx] (device, written, 16-byte
- * aligned) = s_v * (decoded value) with each vector's scale from vmax_dev (device FP32
- * [nvec], as aew_codec_encode_window writes it), 0 on boundary nodes (Sec. 2). */
-int aew_codec_decode_window(aew_handle* h, const uint16_t* latents_dev, const float* vmax_dev,
+ * aligned) = s_v * (decoded value) (AEW_NORM_MINMAX: decoded value * range + offset)
+ * with each vector's scale_dev as aew_codec_encode_window writes it, 0 on boundary
+ * nodes (Sec. 2). */
+int aew_codec_decode_window(aew_handle* h, const uint16_t* latents_dev, const void* scale_dev,
                             float* e_dev, void* stream);
 
 /* ---------------------------------------------------------------------------------
@@ -310,7 +327,7 @@ int aew_jvp(aew_handle* h, const float* dc_dev, float* dd_dev, void* stream);
  * With the time codec the unit is the window instead: every `every`-th complete
  * window w (w = 0, every, 2*every, ...; 16 w + 15 <= nt - 1) is packed into normalised
  * window vectors, and block_max_dev is then FP32 [max_vectors] (each vector's largest
- * |e|).
+ * |e|), or with AEW_NORM_MINMAX FP32 [max_vectors][2] (each vector's offset and range).
  * out_dev: device BF16 (uint16 bit patterns) [max_vectors][2048], 16-byte aligned
  * (AEW_E_ARG otherwise); the forward step that reads a state packs it; *n_written receives
  * the number of vectors written (whole states only, at most max_vectors).
@@ -329,7 +346,8 @@ int aew_snapshots(aew_handle* h, const float* c_dev, int every, uint16_t* out_de
  * aew_codec_train_step-like LAMB step each at lr = lr0 * 0.5^(epoch / halve_every).
  * maxima_dev: the vectors' maxima from aew_snapshots (device FP32 [n][4] for the space
  * codec, [n] for the time codec), read for the amplitude-weighted losses, whose
- * weights are computed on the device (NULL allowed for AEW_LOSS_STATE / _STRAIN).
+ * weights are computed on the device (NULL allowed for AEW_LOSS_STATE / _STRAIN; with
+ * AEW_NORM_MINMAX only those two are accepted).
  * epoch_loss_host (may be NULL): host FP64 [epochs], each epoch's mean minibatch loss
  * (each taken before its update).  Synchronous. */
 int aew_codec_train(aew_handle* h, const uint16_t* vectors_dev, const float* maxima_dev,
@@ -338,8 +356,9 @@ int aew_codec_train(aew_handle* h, const uint16_t* vectors_dev, const float* max
 /* Decoded error of the codec on n normalised vectors (BF16 [n][2048]) with their maxima
  * (as for aew_codec_train): err_host[10] (host FP64) = rel-L2 of decode(encode(y)) - y
  * in normalised units for the fields e, vx, vy, vz and over all values, then the same
- * in physical units (x = y s); with the time codec every value is strain (err_host[0]
- * = err_host[4]).  The strain errors are also kept in aew_stats.  Synchronous. */
+ * in physical units (x = y s; AEW_NORM_MINMAX: maxima_dev FP32 [n][2] offsets and
+ * ranges, x = y r + offset); with the time codec every value is strain (err_host[0] =
+ * err_host[4]).  The strain errors are also kept in aew_stats.  Synchronous. */
 int aew_codec_eval(aew_handle* h, const uint16_t* vectors_dev, const float* maxima_dev,
                    long long n, double* err_host, void* stream);
 

@@ -43,7 +43,7 @@ class aew_config(ctypes.Structure):
         ("nt", c_int), ("src", c_int * 3), ("f0", c_double), ("t0", c_double),
         ("nrec", c_int), ("rec_ijk", POINTER(c_int)),
         ("storage", c_int), ("n_checkpoints", c_int), ("accum_window", c_int), ("n_lat", c_int),
-        ("codec", c_int),
+        ("codec", c_int), ("norm", c_int), ("act", c_int), ("beta", c_double),
     ]
 
 
@@ -223,7 +223,8 @@ class Solver:
     def __init__(self, shape, h: float, nt: int, rec, storage: str = "full",
                  n_checkpoints: int = 20, accum_window: int = 8, n_lat: Optional[int] = None,
                  cfl: float = 0.5, cmax: float = 3000.0, src=None, f0: float = 25.0,
-                 t0: Optional[float] = None, codec: str = "space"):
+                 t0: Optional[float] = None, codec: str = "space", norm: str = "pow2",
+                 act: str = "gelu", beta: float = 0.0):
         nz, ny, nx = shape
         self.shape = (nz, ny, nx)
         self.nt = nt
@@ -247,6 +248,10 @@ class Solver:
             n_lat = 512 if codec == "time" else 64
         cfg.n_lat = n_lat
         cfg.codec = CODEC[codec]
+        cfg.norm = {"pow2": 0, "minmax": 1}[norm]
+        cfg.act = {"gelu": 0, "elu": 1}[act]
+        cfg.beta = beta
+        self.norm = norm
         self.n_lat = n_lat
         self.codec = codec
         self.n_hid = 2 * n_lat if codec == "time" else 512
@@ -405,10 +410,14 @@ class Solver:
 
     def codec_encode_window(self, e: torch.Tensor):
         """Time codec: encode one window of strain fields e [nsteps <= 16][nz][ny][nx]
-        (CUDA FP32): returns (FP16 latents [nvec][n_lat], FP32 vector maxima [nvec])."""
+        (CUDA FP32): returns (FP16 latents [nvec][n_lat], the scales: FP32 vector maxima
+        [nvec], or with min-max normalisation FP64 [2][nvec] offsets and ranges)."""
         e = e.contiguous()
         lat = torch.empty((self.nvec, self.n_lat), device="cuda", dtype=torch.float16)
-        vmax = torch.empty((self.nvec,), device="cuda", dtype=torch.float32)
+        if self.norm == "minmax":      # offsets then ranges, FP64
+            vmax = torch.empty((2, self.nvec), device="cuda", dtype=torch.float64)
+        else:
+            vmax = torch.empty((self.nvec,), device="cuda", dtype=torch.float32)
         self._check(lib().aew_codec_encode_window(self._h, _ptr(e), e.shape[0], _ptr(lat),
                                                   _ptr(vmax), _stream()))
         return lat, vmax
@@ -429,7 +438,8 @@ class Solver:
         [n][4] block maxima, or [n] vector maxima with the time codec)."""
         if out is None:
             out = torch.empty((max_vectors, 2048), device="cuda", dtype=torch.bfloat16)
-        mshape = (max_vectors,) if self.codec == "time" else (max_vectors, 4)
+        mshape = ((max_vectors, 2) if self.norm == "minmax" else (max_vectors,)) \
+            if self.codec == "time" else (max_vectors, 4)
         bm = torch.zeros(mshape, device="cuda") if with_scales else None
         n = c_longlong(0)
         self._check(lib().aew_snapshots(self._h, _ptr(c), every, _ptr(out), max_vectors, _ptr(bm),

@@ -75,6 +75,13 @@ struct aew_handle {
   float* edt[2] = {};
   uint16_t* wk_raw = nullptr;
   unsigned* wk_vmax = nullptr;
+  // min-max normalisation (time codec): each window vector's offset and range (FP64
+  // [nwin][nvec]) of the forward strain and (full Newton HVP) the incremental strain
+  double* wmn = nullptr;
+  double* wr = nullptr;
+  double* wmn2 = nullptr;
+  double* wr2 = nullptr;
+  double* wk_mr = nullptr;   // standalone window calls: [2][nvec]
   // full Newton HVP: the last gradient (FP32, for its 2 dc dJ/dm term), the second-order
   // adjoint's states and accumulators, the first-order adjoint's dt q, and the
   // incremental strain history (FP32 for full storage; latents of the time codec)
@@ -568,9 +575,12 @@ int gradient_ae(aew_handle* h, const float* d_obs, const float* wav, cudaStream_
 // encoder of window tb (raw vectors in xt[tb % 2], maxima vmx[tb]) into its latents
 int encode_window(aew_handle* h, int tb, cudaStream_t s) {
   const size_t nv = nvec_of(h);
+  const bool mm = aew::codec_minmax(h->codec);
   cudaError_t e = aew::codec_encode_window(h->codec, h->xt[tb & 1], h->vmx + (size_t)tb * nv,
                                            (long long)nv, h->lat + (size_t)tb * nv * h->cfg.n_lat,
-                                           h->ovf, s, h->overlap_ctas);
+                                           h->ovf, s, h->overlap_ctas,
+                                           mm ? h->wmn + (size_t)tb * nv : nullptr,
+                                           mm ? h->wr + (size_t)tb * nv : nullptr);
   if (e != cudaSuccess) return cuda_fail(h, e, "codec_encode_window");
   h->stats.kernel_launches += 2;
   return AEW_OK;
@@ -579,9 +589,12 @@ int encode_window(aew_handle* h, int tb, cudaStream_t s) {
 // decoder of window tb into its 16 strain slices edt[tb % 2]
 int decode_window(aew_handle* h, int tb, cudaStream_t s) {
   const size_t nv = nvec_of(h);
+  const bool mm = aew::codec_minmax(h->codec);
   cudaError_t e = aew::codec_decode_window(h->codec, h->lat + (size_t)tb * nv * h->cfg.n_lat,
                                            h->vmx + (size_t)tb * nv, h->cfg.nx, h->cfg.ny,
-                                           h->cfg.nz, h->edt[tb & 1], s, h->overlap_ctas);
+                                           h->cfg.nz, h->edt[tb & 1], s, h->overlap_ctas,
+                                           mm ? h->wmn + (size_t)tb * nv : nullptr,
+                                           mm ? h->wr + (size_t)tb * nv : nullptr);
   if (e != cudaSuccess) return cuda_fail(h, e, "codec_decode_window");
   h->stats.kernel_launches += 2;
   return AEW_OK;
@@ -688,6 +701,8 @@ int ensure_newton(aew_handle* h) {
     const size_t nv = nvec_of(h), W = (size_t)nwin_of(h);
     ok = dalloc(h, &h->lat2, W * nv * h->cfg.n_lat) && dalloc(h, &h->vmx2, W * nv) &&
          dalloc(h, &h->edt2[0], aew::kTSteps * C) && dalloc(h, &h->edt2[1], aew::kTSteps * C);
+    if (ok && aew::codec_minmax(h->codec))
+      ok = dalloc(h, &h->wmn2, W * nv) && dalloc(h, &h->wr2, W * nv);
     for (int i = 0; ok && i < 2; ++i)
       ok = cudaEventCreateWithFlags(&h->ev_c[i], cudaEventDisableTiming) == cudaSuccess &&
            cudaEventCreateWithFlags(&h->ev_d[i], cudaEventDisableTiming) == cudaSuccess;
@@ -733,9 +748,12 @@ int newton_incremental_forward(aew_handle* h, cudaStream_t s) {
   auto encode_de = [&](int tb) -> int {
     AEW_CK(cudaEventRecord(h->ev_c[tb & 1], s));
     AEW_CK(cudaStreamWaitEvent(h->side, h->ev_c[tb & 1], 0));
+    const bool mm = aew::codec_minmax(h->codec);
     cudaError_t e = aew::codec_encode_window(h->codec, h->xt[tb & 1], h->vmx2 + (size_t)tb * nv,
                                              (long long)nv, h->lat2 + (size_t)tb * nv * h->cfg.n_lat,
-                                             h->ovf, h->side, h->overlap_ctas);
+                                             h->ovf, h->side, h->overlap_ctas,
+                                             mm ? h->wmn2 + (size_t)tb * nv : nullptr,
+                                             mm ? h->wr2 + (size_t)tb * nv : nullptr);
     if (e != cudaSuccess) return cuda_fail(h, e, "codec_encode_window");
     h->stats.kernel_launches += 2;
     AEW_CK(cudaEventRecord(h->ev_d[tb & 1], h->side));
@@ -778,9 +796,12 @@ int newton_incremental_forward(aew_handle* h, cudaStream_t s) {
 // decoder of the incremental strain's window tb into edt2[tb % 2]
 int decode_de_window(aew_handle* h, int tb, cudaStream_t s) {
   const size_t nv = nvec_of(h);
+  const bool mm = aew::codec_minmax(h->codec);
   cudaError_t e = aew::codec_decode_window(h->codec, h->lat2 + (size_t)tb * nv * h->cfg.n_lat,
                                            h->vmx2 + (size_t)tb * nv, h->cfg.nx, h->cfg.ny,
-                                           h->cfg.nz, h->edt2[tb & 1], s, h->overlap_ctas);
+                                           h->cfg.nz, h->edt2[tb & 1], s, h->overlap_ctas,
+                                           mm ? h->wmn2 + (size_t)tb * nv : nullptr,
+                                           mm ? h->wr2 + (size_t)tb * nv : nullptr);
   if (e != cudaSuccess) return cuda_fail(h, e, "codec_decode_window");
   h->stats.kernel_launches += 2;
   return AEW_OK;
@@ -863,8 +884,12 @@ int snapshots_time(aew_handle* h, int every, uint16_t* out, long long max_vector
     }
   *n_written = 0;
   if (last < 0) return AEW_OK;
+  // the steps' vector maxima: into the caller's buffer (power-of-two scales), or scratch
+  // (min-max: the caller's buffer receives offsets and ranges instead)
+  const bool mm = aew::codec_minmax(h->codec);
+  if (mm && !h->wk_vmax && !dalloc(h, &h->wk_vmax, nv)) return fail(h, AEW_E_NOMEM, "workspace");
   auto vm = [&](int tb) {
-    return vmax_dev ? reinterpret_cast<unsigned*>(vmax_dev) + at[tb] : h->wk_vmax;
+    return vmax_dev && !mm ? reinterpret_cast<unsigned*>(vmax_dev) + at[tb] : h->wk_vmax;
   };
   int rc;
   if ((rc = zero_state(h, h->st[0], s))) return rc;
@@ -887,7 +912,11 @@ int snapshots_time(aew_handle* h, int every, uint16_t* out, long long max_vector
       return rc;
     cur ^= 1;
     if (tp && slot == T - 1) {
-      AEW_CK(aew::window_normalise(tp, vq, (long long)nv, tp, s));
+      if (aew::codec_minmax(h->codec))   // offsets and ranges out as FP32 pairs
+        AEW_CK(aew::window_minmax(tp, (long long)nv, aew::codec_beta(h->codec), tp, nullptr, nullptr, s,
+                                  vmax_dev ? vmax_dev + 2 * (size_t)at[tb] : nullptr));
+      else
+        AEW_CK(aew::window_normalise(tp, vq, (long long)nv, tp, s));
       ++h->stats.kernel_launches;
     }
   }
@@ -939,6 +968,12 @@ int aew_create(const aew_config* cfg, aew_handle** out) {
     return bad("n_lat must be 512 or 256 for the time codec");
   if (c.storage == AEW_AE && c.codec == AEW_CODEC_TIME && (c.nx % 8 || c.ny % 8 || c.nz % 2))
     return bad("AE storage with the time codec needs nx, ny multiples of 8 and nz even");
+  if ((c.norm != AEW_NORM_POW2 && c.norm != AEW_NORM_MINMAX) ||
+      (c.act != AEW_ACT_GELU && c.act != AEW_ACT_ELU))
+    return bad("norm must be AEW_NORM_POW2 or AEW_NORM_MINMAX, act AEW_ACT_GELU or AEW_ACT_ELU");
+  if ((c.norm != AEW_NORM_POW2 || c.act != AEW_ACT_GELU) && c.codec != AEW_CODEC_TIME)
+    return bad("min-max normalisation and ELU are variants of the time codec");
+  if (!(c.beta >= 0.0)) return bad("beta must be >= 0 (0: the default 1e-7)");
 
   aew_handle* h = new aew_handle();
   h->cfg = c;
@@ -992,6 +1027,10 @@ int aew_create(const aew_config* cfg, aew_handle** out) {
          dalloc(h, &h->xpk[1], nb * aew::kNIn) && dalloc(h, &h->edb[0], C) &&
          dalloc(h, &h->edb[1], C);
   }
+  if (ok && c.storage == AEW_AE && h->tcodec && c.norm == AEW_NORM_MINMAX) {
+    const size_t nv = nvec_of(h), W = (size_t)nwin_of(h);
+    ok = dalloc(h, &h->wmn, W * nv) && dalloc(h, &h->wr, W * nv);
+  }
   if (ok && c.storage == AEW_AE && h->tcodec) {
     const size_t nv = nvec_of(h), W = (size_t)nwin_of(h);
     ok = dalloc(h, &h->lat, W * nv * c.n_lat) && dalloc(h, &h->vmx, W * nv) &&
@@ -1034,6 +1073,7 @@ int aew_create(const aew_config* cfg, aew_handle** out) {
     aew_destroy(h);
     return AEW_E_NOMEM;
   }
+  aew::codec_set_variant(h->codec, c.norm, c.act, c.beta > 0.0 ? c.beta : 1e-7);
   for (int i = 0; i < 2; ++i)
     if (cudaEventCreate(&h->tg[i]) != cudaSuccess || cudaEventCreate(&h->th[i]) != cudaSuccess) {
       g_create_err = "event creation failed";
@@ -1531,7 +1571,7 @@ int aew_codec_encode_vectors(aew_handle* h, const uint16_t* vectors_dev, long lo
 }
 
 int aew_codec_encode_window(aew_handle* h, const float* e_dev, int nsteps, uint16_t* latents_dev,
-                            float* vmax_dev, void* stream) {
+                            void* scale_dev, void* stream) {
   if (!h) return AEW_E_ARG;
   if (!h->tcodec) return fail(h, AEW_E_CONFIG, "aew_codec_encode_window needs the time codec");
   if (!e_dev || !latents_dev || nsteps < 1 || nsteps > aew::kTSteps)
@@ -1543,18 +1583,23 @@ int aew_codec_encode_window(aew_handle* h, const float* e_dev, int nsteps, uint1
   h->err.clear();
   cudaStream_t s = S(stream);
   const size_t nv = nvec_of(h);
+  const bool mm = aew::codec_minmax(h->codec);
   if ((!h->wk_raw && !dalloc(h, &h->wk_raw, nv * aew::kNIn)) ||
-      (!h->wk_vmax && !dalloc(h, &h->wk_vmax, nv)))
+      (!h->wk_vmax && !dalloc(h, &h->wk_vmax, nv)) ||
+      (mm && !h->wk_mr && !dalloc(h, &h->wk_mr, 2 * nv)))
     return fail(h, AEW_E_NOMEM, "workspace");
   int* ovf = reinterpret_cast<int*>(h->scratch8 + 4);
   AEW_CK(cudaMemsetAsync(ovf, 0, sizeof(int), s));
   AEW_CK(aew::window_pack(e_dev, nsteps, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->wk_raw, h->wk_vmax, s));
   cudaError_t e = aew::codec_encode_window(h->codec, h->wk_raw, h->wk_vmax, (long long)nv,
-                                           latents_dev, ovf, s);
+                                           latents_dev, ovf, s, 0, mm ? h->wk_mr : nullptr,
+                                           mm ? h->wk_mr + nv : nullptr);
   if (e != cudaSuccess) return cuda_fail(h, e, "codec_encode_window");
-  h->stats.kernel_launches += 3;
-  if (vmax_dev)
-    AEW_CK(cudaMemcpyAsync(vmax_dev, h->wk_vmax, nv * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  h->stats.kernel_launches += mm ? 4 : 3;
+  if (scale_dev)
+    AEW_CK(cudaMemcpyAsync(scale_dev, mm ? static_cast<const void*>(h->wk_mr) : h->wk_vmax,
+                           mm ? 2 * nv * sizeof(double) : nv * sizeof(float),
+                           cudaMemcpyDeviceToDevice, s));
   if (aew::codec_take_error(h->codec, s))
     return fail(h, AEW_E_TIMEOUT, "a codec kernel gave up waiting (bounded mbarrier wait)");
   int o = 0;
@@ -1564,20 +1609,24 @@ int aew_codec_encode_window(aew_handle* h, const float* e_dev, int nsteps, uint1
   return AEW_OK;
 }
 
-int aew_codec_decode_window(aew_handle* h, const uint16_t* latents_dev, const float* vmax_dev,
+int aew_codec_decode_window(aew_handle* h, const uint16_t* latents_dev, const void* scale_dev,
                             float* e_dev, void* stream) {
   if (!h) return AEW_E_ARG;
   if (!h->tcodec) return fail(h, AEW_E_CONFIG, "aew_codec_decode_window needs the time codec");
-  if (!latents_dev || !vmax_dev || !e_dev) return fail(h, AEW_E_ARG, "NULL argument");
+  if (!latents_dev || !scale_dev || !e_dev) return fail(h, AEW_E_ARG, "NULL argument");
   if (reinterpret_cast<uintptr_t>(e_dev) & 15) return fail(h, AEW_E_ARG, "e_dev must be 16-byte aligned");
   if (h->cfg.nx % 8 || h->cfg.ny % 8 || h->cfg.nz % 2)
     return fail(h, AEW_E_CONFIG, "the time codec needs nx, ny multiples of 8 and nz even");
   if (!aew::codec_ready(h->codec)) return fail(h, AEW_E_NOCODEC, "codec weights not set");
   h->err.clear();
   cudaStream_t s = S(stream);
+  const bool mm = aew::codec_minmax(h->codec);
+  const size_t nv = nvec_of(h);
+  const double* mr = static_cast<const double*>(scale_dev);
   cudaError_t e = aew::codec_decode_window(h->codec, latents_dev,
-                                           reinterpret_cast<const unsigned*>(vmax_dev), h->cfg.nx,
-                                           h->cfg.ny, h->cfg.nz, e_dev, s);
+                                           static_cast<const unsigned*>(scale_dev), h->cfg.nx,
+                                           h->cfg.ny, h->cfg.nz, e_dev, s, 0, mm ? mr : nullptr,
+                                           mm ? mr + nv : nullptr);
   if (e != cudaSuccess) return cuda_fail(h, e, "codec_decode_window");
   h->stats.kernel_launches += 2;
   if (aew::codec_take_error(h->codec, s))
@@ -1597,6 +1646,10 @@ int aew_codec_init_pca(aew_handle* h, const uint16_t* vectors_dev, const float* 
   if (weighted && !maxima_dev) return fail(h, AEW_E_ARG, "weighted PCA needs the vectors' maxima");
   const int k = h->cfg.n_lat, nh = aew::codec_nhid(h->codec), I = aew::kNIn;
   if (2 * k > nh) return fail(h, AEW_E_CONFIG, "the hidden layer must hold 2 n_lat units");
+  if (h->cfg.act != AEW_ACT_GELU)
+    return fail(h, AEW_E_CONFIG, "the PCA code passes GELU(a) - GELU(-a) = a: GELU only");
+  if (aew::codec_minmax(h->codec) && weighted)
+    return fail(h, AEW_E_ARG, "min-max normalisation: unweighted PCA only");
   h->err.clear();
   cudaStream_t s = S(stream);
   double* G = nullptr;

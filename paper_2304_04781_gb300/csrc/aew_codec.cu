@@ -71,8 +71,17 @@ cudaError_t transpose16(const float* src, int rows, int cols, uint16_t* dst, boo
 // ---------------------------------------------------------------------------------
 // Epilogues
 // ---------------------------------------------------------------------------------
-// H[row][col..] = bf16(gelu(acc + bias)), row stride ld
-struct EpBiasGeluH {
+// hidden-layer activation of the inference epilogues: GELU (ACT 0) or the paper's ELU
+// (ACT 1: e^a - 1 below 0, a above)
+template <int ACT>
+__device__ __forceinline__ float act_fwd(float a) {
+  if (ACT == 1) return a > 0.f ? a : expm1f(a);
+  return gemm::gelu_fast(a);
+}
+
+// H[row][col..] = bf16(act(acc + bias)), row stride ld
+template <int ACT>
+struct EpBiasAct {
   const float* bias;
   uint16_t* H;
   long long M;
@@ -84,8 +93,8 @@ struct EpBiasGeluH {
 #pragma unroll
     for (int j = 0; j < 32; j += 4) {
       const float4 b = __ldg(bq + j / 4);
-      pk[j / 2] = gemm::pack_bf16(gemm::gelu_fast(v[j] + b.x), gemm::gelu_fast(v[j + 1] + b.y));
-      pk[j / 2 + 1] = gemm::pack_bf16(gemm::gelu_fast(v[j + 2] + b.z), gemm::gelu_fast(v[j + 3] + b.w));
+      pk[j / 2] = gemm::pack_bf16(act_fwd<ACT>(v[j] + b.x), act_fwd<ACT>(v[j + 1] + b.y));
+      pk[j / 2 + 1] = gemm::pack_bf16(act_fwd<ACT>(v[j + 2] + b.z), act_fwd<ACT>(v[j + 3] + b.w));
     }
     uint4* dst = reinterpret_cast<uint4*>(H + row * ld + col);
 #pragma unroll
@@ -93,11 +102,14 @@ struct EpBiasGeluH {
   }
 };
 
+using EpBiasGeluH = EpBiasAct<0>;
+
 // Encoder layer 1 of the time codec on raw (unnormalised) BF16 window vectors:
-// H[row][col..] = bf16(gelu(acc / s_row + bias)), s_row the vector's power-of-two scale
+// H[row][col..] = bf16(act(acc / s_row + bias)), s_row the vector's power-of-two scale
 // from its max |e| (vmax, float bits).  Dividing the FP32 sum by a power of two equals
 // summing the normalised products (the scale commutes with every rounding involved).
-struct EpScaleGeluH {
+template <int ACT>
+struct EpScaleAct {
   const float* bias;
   const unsigned* vmax;
   uint16_t* H;
@@ -111,10 +123,10 @@ struct EpScaleGeluH {
 #pragma unroll
     for (int j = 0; j < 32; j += 4) {
       const float4 b = __ldg(bq + j / 4);
-      pk[j / 2] = gemm::pack_bf16(gemm::gelu_fast(fmaf(v[j], is, b.x)),
-                                  gemm::gelu_fast(fmaf(v[j + 1], is, b.y)));
-      pk[j / 2 + 1] = gemm::pack_bf16(gemm::gelu_fast(fmaf(v[j + 2], is, b.z)),
-                                      gemm::gelu_fast(fmaf(v[j + 3], is, b.w)));
+      pk[j / 2] = gemm::pack_bf16(act_fwd<ACT>(fmaf(v[j], is, b.x)),
+                                  act_fwd<ACT>(fmaf(v[j + 1], is, b.y)));
+      pk[j / 2 + 1] = gemm::pack_bf16(act_fwd<ACT>(fmaf(v[j + 2], is, b.z)),
+                                      act_fwd<ACT>(fmaf(v[j + 3], is, b.w)));
     }
     uint4* dst = reinterpret_cast<uint4*>(H + row * ld + col);
 #pragma unroll
@@ -133,12 +145,15 @@ struct EpDecWindow {
   int nx, ny, nz, NBx, NBy;
   long long M;            // vectors (< 2^31)
   size_t slice;           // nx ny nz
+  const double* mn;       // min-max normalisation (else null): offset and range
+  const double* rr;
   __device__ __forceinline__ void operator()(long long rw, int col, const float (&v)[32]) const {
     if (rw >= M) return;
     const int r = (int)rw;
     const int bx = r % NBx, q = r / NBx;
     const int by = q % NBy, bz = q / NBy;
-    const float sc = gemm::block_scale(__uint_as_float(__ldg(vmax + r)));
+    const float sc = rr ? (float)__ldg(rr + r) : gemm::block_scale(__uint_as_float(__ldg(vmax + r)));
+    const float off = rr ? (float)__ldg(mn + r) : 0.f;
     const int t = col >> 7, z = (col >> 6) & 1, y0 = (col & 63) >> 3;
     const int kz = 2 * bz + z;
     const bool zb = kz == 0 || kz == nz - 1;
@@ -154,7 +169,7 @@ struct EpDecWindow {
       float o[8];
 #pragma unroll
       for (int x = 0; x < 8; ++x) {
-        const float val = (v[yy * 8 + x] + bv[x]) * sc;
+        const float val = fmaf(v[yy * 8 + x] + bv[x], sc, off);
         o[x] = (yb || (x == 0 && xlo) || (x == 7 && xhi)) ? 0.f : val;
       }
       float4* dst = reinterpret_cast<float4*>(base + (size_t)yy * nx);
@@ -489,22 +504,26 @@ __global__ void eval_err_kernel(const uint16_t* __restrict__ Y, const float* __r
 #pragma unroll
   for (int j = 0; j < 16; ++j) a[j] = 0.0;
   for (int v = blockIdx.x * 8 + wid; v < nc; v += gridDim.x * 8) {
+    // time == 2 (min-max): mx is [n][2] = (offset, range), x = y r + offset
     float sc[4];
+    const float off = time == 2 ? mx[2 * (size_t)v] : 0.f;
 #pragma unroll
     for (int f = 0; f < 4; ++f)
-      sc[f] = gemm::block_scale(time ? mx[v] : mx[(size_t)v * 4 + f]);
+      sc[f] = time == 2 ? mx[2 * (size_t)v + 1]
+                        : gemm::block_scale(time ? mx[v] : mx[(size_t)v * 4 + f]);
     for (int k = lane; k < kNIn; k += 32) {
       const int f = time ? 0 : ((k >> 6) & 3);
       const double y = (double)gemm::bf16_val(Y[(size_t)v * kNIn + k]);
       const double d = (double)Yh[(size_t)v * kNIn + k] - y;
       const double s2 = (double)sc[f] * (double)sc[f];
+      const double x = y * (double)sc[f] + (double)off;
 #pragma unroll
       for (int g = 0; g < 4; ++g)
         if (g == f) {
           a[g] += d * d;
           a[4 + g] += y * y;
           a[8 + g] += d * d * s2;
-          a[12 + g] += y * y * s2;
+          a[12 + g] += x * x;
         }
     }
   }
@@ -518,6 +537,54 @@ __global__ void eval_err_kernel(const uint16_t* __restrict__ Y, const float* __r
     double t = 0.0;
     for (int w = 0; w < 8; ++w) t += sh[w][threadIdx.x];
     atomicAdd(acc + threadIdx.x, t);
+  }
+}
+
+// The paper's min-max normalisation of raw BF16 window vectors, one warp per vector:
+// min and max of its 2048 values, r = max(max - min, beta), y = (x - min) / r in FP32,
+// one rounding to BF16 (in place allowed: each lane rewrites what it read); the offset
+// and range are kept in FP64.
+__global__ void window_minmax_kernel(const uint16_t* raw, long long nvec, double beta,
+                                     uint16_t* out, double* __restrict__ mn,
+                                     double* __restrict__ rr, float2* __restrict__ pair32) {
+  const int lane = threadIdx.x & 31;
+  for (long long v = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; v < nvec;
+       v += ((long long)gridDim.x * blockDim.x) >> 5) {
+    const uint4* src = reinterpret_cast<const uint4*>(raw + (size_t)v * kNIn);
+    uint4 q[8];
+    float lo = INFINITY, hi = -INFINITY;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      q[k] = src[k * 32 + lane];
+      const uint32_t w[4] = {q[k].x, q[k].y, q[k].z, q[k].w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float a = __uint_as_float(w[j] << 16), b = __uint_as_float(w[j] & 0xffff0000u);
+        lo = fminf(lo, fminf(a, b));
+        hi = fmaxf(hi, fmaxf(a, b));
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    const double r = fmax((double)hi - (double)lo, beta);
+    const float fl = lo, ir = (float)(1.0 / r);
+    uint4* dst = reinterpret_cast<uint4*>(out + (size_t)v * kNIn);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      uint32_t w[4] = {q[k].x, q[k].y, q[k].z, q[k].w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        w[j] = gemm::pack_bf16((__uint_as_float(w[j] << 16) - fl) * ir,
+                               (__uint_as_float(w[j] & 0xffff0000u) - fl) * ir);
+      dst[k * 32 + lane] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    if (lane == 0) {
+      if (mn) mn[v] = (double)lo;
+      if (rr) rr[v] = r;
+      if (pair32) pair32[v] = make_float2(lo, (float)r);
+    }
   }
 }
 
@@ -740,31 +807,45 @@ static cudaError_t encode_layer2(Codec* c, long long n, uint16_t* lat, int* over
   return gemm::launch<256, true>(n, nl, nh, a2, b2, e2, c->err, s, g, c->max_stages);
 }
 
+// encoder layer 1 on normalised vectors with epilogue EP (bias + activation)
+template <class EP>
+static cudaError_t encode_layer1(Codec* c, const uint16_t* vec, long long n, const EP& ep,
+                                 cudaStream_t s, int g) {
+  const int nh = c->n_hid;
+  const gemm::Mat a1{vec, n, kNIn}, b1{c->W1t, nh, kNIn};
+  return c->pair_gemm && c->max_stages == 0
+             ? gemm2::launch<true>(n, nh, kNIn, a1, b1, ep, c->err, s, g)
+             : gemm::launch<256, true>(n, nh, kNIn, a1, b1, ep, c->err, s, g, c->max_stages);
+}
+
 cudaError_t codec_encode_vectors(Codec* c, const uint16_t* vec, long long n, uint16_t* lat,
                                  int* overflow, cudaStream_t s, int ctas) {
   if (!ensure_H(c, (size_t)n)) return cudaErrorMemoryAllocation;
   const int g = ctas_of(c, ctas);
   const int nh = c->n_hid;
-  EpBiasGeluH ep{c->w[1], c->H, n, nh};
-  const gemm::Mat a1{vec, n, kNIn}, b1{c->W1t, nh, kNIn};
-  cudaError_t e = c->pair_gemm && c->max_stages == 0
-                      ? gemm2::launch<true>(n, nh, kNIn, a1, b1, ep, c->err, s, g)
-                      : gemm::launch<256, true>(n, nh, kNIn, a1, b1, ep, c->err, s, g, c->max_stages);
+  cudaError_t e = c->act == 1 ? encode_layer1(c, vec, n, EpBiasAct<1>{c->w[1], c->H, n, nh}, s, g)
+                              : encode_layer1(c, vec, n, EpBiasAct<0>{c->w[1], c->H, n, nh}, s, g);
   if (e != cudaSuccess) return e;
   return encode_layer2(c, n, lat, overflow, s, g);
 }
 
-static cudaError_t decode_hidden(Codec* c, const uint16_t* lat, long long nb, cudaStream_t s,
-                                 int ctas) {
-  if (!ensure_H(c, (size_t)nb)) return cudaErrorMemoryAllocation;
+template <int ACT>
+static cudaError_t decode_hidden_t(Codec* c, const uint16_t* lat, long long nb, cudaStream_t s,
+                                   int ctas) {
   const int nl = c->n_lat, nh = c->n_hid;
-  EpBiasGeluH ep{c->w[5], c->H, nb, nh};
+  EpBiasAct<ACT> ep{c->w[5], c->H, nb, nh};
   if (pair_wide(c))
     return gemm2::launch<false>(nb, nh, nl, gemm::Mat{lat, nb, nl}, gemm::Mat{c->W3t, nh, nl}, ep,
                                 c->err, s, ctas_of(c, ctas));
   return gemm::launch<256, false>(nb, nh, nl, gemm::Mat{lat, nb, nl},
                                   gemm::Mat{c->W3t, nh, nl}, ep, c->err, s, ctas_of(c, ctas),
                                   c->max_stages);
+}
+
+static cudaError_t decode_hidden(Codec* c, const uint16_t* lat, long long nb, cudaStream_t s,
+                                 int ctas) {
+  if (!ensure_H(c, (size_t)nb)) return cudaErrorMemoryAllocation;
+  return c->act == 1 ? decode_hidden_t<1>(c, lat, nb, s, ctas) : decode_hidden_t<0>(c, lat, nb, s, ctas);
 }
 
 // strain decode in one kernel: layer 1, GELU, layer 2 with H kept in shared memory
@@ -811,30 +892,38 @@ cudaError_t codec_decode_vectors(Codec* c, const uint16_t* lat, long long nvec, 
 // ---------------------------------------------------------------------------------
 // Compression in time
 // ---------------------------------------------------------------------------------
-cudaError_t codec_encode_window(Codec* c, const uint16_t* raw, const unsigned* vmax,
+cudaError_t codec_encode_window(Codec* c, uint16_t* raw, const unsigned* vmax,
                                 long long nvec, uint16_t* lat, int* overflow, cudaStream_t s,
-                                int ctas) {
+                                int ctas, double* mn, double* rr) {
   if (!ensure_H(c, (size_t)nvec)) return cudaErrorMemoryAllocation;
   const int g = ctas_of(c, ctas);
   const int nh = c->n_hid;
-  EpScaleGeluH ep{c->w[1], vmax, c->H, nvec, nh};
-  const gemm::Mat a1{raw, nvec, kNIn}, b1{c->W1t, nh, kNIn};
-  cudaError_t e = c->pair_gemm && c->max_stages == 0
-                      ? gemm2::launch<true>(nvec, nh, kNIn, a1, b1, ep, c->err, s, g)
-                      : gemm::launch<256, true>(nvec, nh, kNIn, a1, b1, ep, c->err, s, g, c->max_stages);
+  cudaError_t e;
+  if (c->norm == 1) {   // the paper's min-max normalisation, then the plain layer 1
+    if (!mn || !rr) return cudaErrorInvalidValue;
+    if ((e = window_minmax(raw, nvec, c->beta, raw, mn, rr, s)) != cudaSuccess) return e;
+    e = c->act == 1 ? encode_layer1(c, raw, nvec, EpBiasAct<1>{c->w[1], c->H, nvec, nh}, s, g)
+                    : encode_layer1(c, raw, nvec, EpBiasAct<0>{c->w[1], c->H, nvec, nh}, s, g);
+  } else {
+    e = c->act == 1 ? encode_layer1(c, raw, nvec, EpScaleAct<1>{c->w[1], vmax, c->H, nvec, nh}, s, g)
+                    : encode_layer1(c, raw, nvec, EpScaleAct<0>{c->w[1], vmax, c->H, nvec, nh}, s, g);
+  }
   if (e != cudaSuccess) return e;
   return encode_layer2(c, nvec, lat, overflow, s, g);
 }
 
 cudaError_t codec_decode_window(Codec* c, const uint16_t* lat, const unsigned* vmax, int nx,
-                                int ny, int nz, float* e_out, cudaStream_t s, int ctas) {
+                                int ny, int nz, float* e_out, cudaStream_t s, int ctas,
+                                const double* mn, const double* rr) {
+  if (c->norm == 1 && (!mn || !rr)) return cudaErrorInvalidValue;
   const int NBx = nx / 8, NBy = ny / 8, NBz = nz / 2;
   const long long nvec = (long long)NBx * NBy * NBz;
   if (nvec >= (1LL << 31)) return cudaErrorInvalidValue;
   cudaError_t e = decode_hidden(c, lat, nvec, s, ctas);
   if (e != cudaSuccess) return e;
   const int nh = c->n_hid;
-  EpDecWindow ep{c->w[7], vmax, e_out, nx, ny, nz, NBx, NBy, nvec, (size_t)nx * ny * nz};
+  EpDecWindow ep{c->w[7], vmax, e_out, nx, ny, nz, NBx, NBy, nvec, (size_t)nx * ny * nz,
+                 c->norm == 1 ? mn : nullptr, c->norm == 1 ? rr : nullptr};
   if (pair_wide(c))
     return gemm2::launch<true>(nvec, kNIn, nh, gemm::Mat{c->H, nvec, nh},
                                gemm::Mat{c->W4t, kNIn, nh}, ep, c->err, s, ctas_of(c, ctas));
@@ -916,8 +1005,8 @@ cudaError_t codec_eval(Codec* c, const uint16_t* Y, const float* maxima, long lo
     if (e == cudaSuccess) e = codec_decode_vectors(c, lat, nc, dec, s);
     if (e == cudaSuccess) {
       eval_err_kernel<<<1024, 256, 0, s>>>(Y + (size_t)n0 * kNIn, dec,
-                                           maxima + (size_t)n0 * (c->time ? 1 : 4), c->time ? 1 : 0,
-                                           nc, acc);
+                                           maxima + (size_t)n0 * (c->time ? (c->norm == 1 ? 2 : 1) : 4),
+                                           c->time ? (c->norm == 1 ? 2 : 1) : 0, nc, acc);
       e = cudaGetLastError();
     }
   }
@@ -944,6 +1033,24 @@ cudaError_t codec_eval(Codec* c, const uint16_t* Y, const float* maxima, long lo
   out[9] = rel(pd, pn);
   return cudaSuccess;
 }
+
+cudaError_t window_minmax(const uint16_t* raw, long long nvec, double beta, uint16_t* out,
+                          double* mn, double* rr, cudaStream_t s, float* pair32) {
+  if (nvec <= 0) return cudaSuccess;
+  long long blocks = (nvec * 32 + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  window_minmax_kernel<<<(unsigned)blocks, 256, 0, s>>>(raw, nvec, beta, out, mn, rr,
+                                                        reinterpret_cast<float2*>(pair32));
+  return cudaGetLastError();
+}
+
+void codec_set_variant(Codec* c, int norm, int act, double beta) {
+  c->norm = norm;
+  c->act = act;
+  c->beta = beta;
+}
+bool codec_minmax(const Codec* c) { return c->norm == 1; }
+double codec_beta(const Codec* c) { return c->beta; }
 
 cudaError_t window_normalise(const uint16_t* raw, const unsigned* vmax, long long nvec,
                              uint16_t* out, cudaStream_t s) {

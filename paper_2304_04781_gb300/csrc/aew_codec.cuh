@@ -16,6 +16,11 @@ constexpr int kTSteps = 16;  // steps per window of the time codec
 
 // space codec: n_hid = 512, n_lat 32 or 64; time codec: n_hid = 2 n_lat, n_lat 256 or 512
 Codec* codec_new(int n_lat, bool time);
+// time codec: normalisation (0 power of two, 1 min-max with floor beta), activation
+// (0 GELU, 1 ELU)
+void codec_set_variant(Codec* c, int norm, int act, double beta);
+bool codec_minmax(const Codec* c);
+double codec_beta(const Codec* c);
 void codec_free(Codec* c);
 int codec_nlat(const Codec* c);
 int codec_nhid(const Codec* c);
@@ -60,13 +65,20 @@ cudaError_t codec_decode_vectors(Codec* c, const uint16_t* lat, long long nvec, 
 // Encode one window: raw BF16 strain vectors [nvec][2048] (as the forward step packs
 // them) and each vector's max |e| (vmax, float bits [nvec]); the layer-1 epilogue
 // divides by the vector's power-of-two scale.  latents FP16 [nvec][n_lat].
-cudaError_t codec_encode_window(Codec* c, const uint16_t* raw, const unsigned* vmax,
+// With min-max normalisation (codec_minmax) the window is normalised in place first and
+// each vector's offset and range are written to mn / rr (FP64 [nvec]; vmax unused).
+cudaError_t codec_encode_window(Codec* c, uint16_t* raw, const unsigned* vmax,
                                 long long nvec, uint16_t* lat, int* overflow, cudaStream_t s,
-                                int ctas = 0);
+                                int ctas = 0, double* mn = nullptr, double* rr = nullptr);
 // Decode one window into 16 strain slices e_out[t][nz][ny][nx] (slice stride nx ny nz):
-// e = s_v * decoded value, 0 on boundary nodes.
+// e = s_v * decoded value (min-max: decoded value * rr + mn), 0 on boundary nodes.
 cudaError_t codec_decode_window(Codec* c, const uint16_t* lat, const unsigned* vmax, int nx,
-                                int ny, int nz, float* e_out, cudaStream_t s, int ctas = 0);
+                                int ny, int nz, float* e_out, cudaStream_t s, int ctas = 0,
+                                const double* mn = nullptr, const double* rr = nullptr);
+// The paper's min-max normalisation of raw BF16 window vectors (in place allowed):
+// y = (x - min) / r, r = max(max - min, beta); offsets and ranges to mn / rr (FP64).
+cudaError_t window_minmax(const uint16_t* raw, long long nvec, double beta, uint16_t* out,
+                          double* mn, double* rr, cudaStream_t s, float* pair32 = nullptr);
 // Pack nsteps (<= 16) strain fields e[t][nz][ny][nx] into raw BF16 window vectors
 // [nvec][2048] (missing steps 0) and fold max |e| per vector into vmax (zeroed here).
 cudaError_t window_pack(const float* e, int nsteps, int nx, int ny, int nz, uint16_t* raw,
@@ -119,7 +131,8 @@ cudaError_t codec_train(Codec* c, const uint16_t* Y, const float* maxima, long l
 // Decoded error of n normalised vectors: out[0..4] rel-L2 of decode(encode(y)) - y in
 // normalised units per field (e, vx, vy, vz) and overall, out[5..9] the same in physical
 // units (x = y s with the vectors' scales from their maxima; time codec: every column is
-// strain, out[0] = out[4]).  maxima: [n][4] block maxima or [n] vector maxima.
+// strain, out[0] = out[4]).  maxima: [n][4] block maxima or [n] vector maxima; with
+// min-max normalisation [n][2] (offset, range), x = y r + offset.
 cudaError_t codec_eval(Codec* c, const uint16_t* Y, const float* maxima, long long n,
                        double* out, cudaStream_t s);
 

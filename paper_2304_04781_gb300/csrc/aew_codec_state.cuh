@@ -10,6 +10,11 @@ struct Codec {
   int n_lat = 64;
   int n_hid = 512;           // hidden width: 512 (space codec) or 2 n_lat (time codec)
   bool time = false;         // compression in time (16-step strain windows)
+  // time codec only: normalisation (0: power-of-two scale, 1: the paper's min-max to
+  // [0, 1] with the range floored at beta) and hidden activation (0: GELU, 1: ELU)
+  int norm = 0;
+  int act = 0;
+  double beta = 1e-7;
   bool ready = false;
   // FP32 master weights: W1 [2048][nh], b1, W2 [nh][nl], b2, W3 [nl][nh], b3,
   // W4 [nh][2048], b4

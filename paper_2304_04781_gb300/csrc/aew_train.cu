@@ -93,7 +93,16 @@ __device__ __forceinline__ void store_row16(uint16_t* dst, const uint32_t (&pk)[
   for (int q = 0; q < 4; ++q) d[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
 }
 
-// a = acc + bias -> pre (FP32), h = bf16(gelu(a)) row-major and transposed
+// the training kernels' activation and its derivative: GELU by erff (act 0) or ELU
+// (act 1: e^a - 1 below 0, a above; derivative e^a below 0, 1 above)
+__device__ __forceinline__ float act_f(int act, float a) {
+  return act == 1 ? (a > 0.f ? a : expm1f(a)) : gemm::gelu_f(a);
+}
+__device__ __forceinline__ float act_prime_f(int act, float a) {
+  return act == 1 ? (a > 0.f ? 1.f : expf(a)) : gemm::gelu_prime_f(a);
+}
+
+// a = acc + bias -> pre (FP32), h = bf16(act(a)) row-major and transposed
 struct EpFwdGelu {
   const float* bias;
   float* pre;
@@ -101,6 +110,7 @@ struct EpFwdGelu {
   uint16_t* hT;
   int N;
   long long M;
+  int act;
   __device__ __forceinline__ void operator()(long long row, int col, const float (&v)[32]) const {
     if (row >= M) return;
     uint32_t pk[16];
@@ -111,8 +121,8 @@ struct EpFwdGelu {
 #pragma unroll
       for (int q = 0; q < 4; ++q) a[q] = v[j + q] + __ldg(bias + col + j + q);
       pd[j / 4] = make_float4(a[0], a[1], a[2], a[3]);
-      const float g0 = gemm::gelu_f(a[0]), g1 = gemm::gelu_f(a[1]);
-      const float g2 = gemm::gelu_f(a[2]), g3 = gemm::gelu_f(a[3]);
+      const float g0 = act_f(act, a[0]), g1 = act_f(act, a[1]);
+      const float g2 = act_f(act, a[2]), g3 = act_f(act, a[3]);
       pk[j / 2] = gemm::pack_bf16(g0, g1);
       pk[j / 2 + 1] = gemm::pack_bf16(g2, g3);
       hT[(size_t)(col + j + 0) * M + row] = gemm::bf16_bits(g0);
@@ -190,12 +200,13 @@ struct EpBack {
   uint16_t* dT;
   int N;
   long long M;
+  int act;
   __device__ __forceinline__ void operator()(long long row, int col, const float (&v)[32]) const {
     if (row >= M || col >= N) return;
     float dd[32];
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
-      dd[j] = pre ? v[j] * gemm::gelu_prime_f(pre[row * N + col + j]) : v[j];
+      dd[j] = pre ? v[j] * act_prime_f(act, pre[row * N + col + j]) : v[j];
       dT[(size_t)(col + j) * M + row] = gemm::bf16_bits(dd[j]);
     }
     float4* pd = reinterpret_cast<float4*>(d + row * N + col);
@@ -451,11 +462,11 @@ cudaError_t codec_train_step(Codec* c, const uint16_t* Y, const float* wts, int 
   }
   // ---- forward
   TCK((gemm::launch<256, true>(Bm, H, I, ld(Y, I, Bm, I), ld(c->W1t, I, H, I),
-                               EpFwdGelu{c->w[1], s->a1, s->h1, s->h1T, H, Bm}, e, st)));
+                               EpFwdGelu{c->w[1], s->a1, s->h1, s->h1T, H, Bm, c->act}, e, st)));
   TCK((launch_nl<true>(Bm, nl, H, ld(s->h1, H, Bm, H), ld(c->W2t, H, nl, H),
                        EpFwdLatent{c->w[3], s->z16, s->zbT, nl, Bm}, e, st)));
   TCK((gemm::launch<256, false>(Bm, H, nl, ld(s->z16, nl, Bm, nl), ld(c->W3t, nl, H, nl),
-                                EpFwdGelu{c->w[5], s->a3, s->h3, s->h3T, H, Bm}, e, st)));
+                                EpFwdGelu{c->w[5], s->a3, s->h3, s->h3T, H, Bm, c->act}, e, st)));
   TCK((gemm::launch<256, true>(Bm, I, H, ld(s->h3, H, Bm, H), ld(c->W4t, H, I, H),
                                EpMse{c->w[7], Y, wts, s->d4, s->d4b, s->d4T, s->red,
                                      2.0f / (float)((double)B * I), Bm},
@@ -464,15 +475,15 @@ cudaError_t codec_train_step(Codec* c, const uint16_t* Y, const float* wts, int 
   TCK((gemm::launch<256, true>((long long)H, I, B, ld(s->h3T, B, H, B), ld(s->d4T, B, I, B),
                                EpStore{s->g[6], I, H}, e, st)));
   TCK((gemm::launch<256, true>(Bm, H, I, ld(s->d4b, I, Bm, I), ld(s->W4b, I, H, I),
-                               EpBack{s->a3, s->d3, s->d3b, s->d3T, H, Bm}, e, st)));
+                               EpBack{s->a3, s->d3, s->d3b, s->d3T, H, Bm, c->act}, e, st)));
   TCK((gemm::launch<256, true>((long long)nl, H, B, ld(s->zbT, B, nl, B), ld(s->d3T, B, H, B),
                                EpStore{s->g[4], H, nl}, e, st)));
   TCK((launch_nl<true>(Bm, nl, H, ld(s->d3b, H, Bm, H), ld(s->W3b, H, nl, H),
-                       EpBack{nullptr, s->d2, s->d2b, s->d2T, nl, Bm}, e, st)));
+                       EpBack{nullptr, s->d2, s->d2b, s->d2T, nl, Bm, c->act}, e, st)));
   TCK((launch_nl<true>((long long)H, nl, B, ld(s->h1T, B, H, B), ld(s->d2T, B, nl, B),
                        EpStore{s->g[2], nl, H}, e, st)));
   TCK((gemm::launch<256, true>(Bm, H, nl, ld(s->d2b, nl, Bm, nl), ld(s->W2b, nl, H, nl),
-                               EpBack{s->a1, s->d1, nullptr, s->d1T, H, Bm}, e, st)));
+                               EpBack{s->a1, s->d1, nullptr, s->d1T, H, Bm, c->act}, e, st)));
   TCK((gemm::launch<256, true>((long long)I, H, B, ld(s->YT, B, I, B), ld(s->d1T, B, H, B),
                                EpStore{s->g[0], H, I}, e, st)));
   // bias gradients
@@ -509,6 +520,10 @@ cudaError_t codec_train(Codec* c, const uint16_t* Y, const float* maxima, long l
   }
   if (cfg.loss != kLossState && cfg.loss != kLossStrain && !maxima) {
     if (err) *err = "amplitude-weighted losses need the vectors' maxima";
+    return cudaErrorInvalidValue;
+  }
+  if (cfg.loss != kLossState && cfg.loss != kLossStrain && c->norm == 1) {
+    if (err) *err = "min-max normalisation trains with the plain losses only";
     return cudaErrorInvalidValue;
   }
   // loss weights [n][4] (none for the plain error, or the strain columns of the time codec)

@@ -33,12 +33,12 @@ LOSSES = tuple(aewave.LOSSES)
 
 
 def make_handle(shape, codec="space", n_lat=None, h=10.0, nt=1000, nrec=64,
-                f0=25.0) -> aewave.Solver:
+                f0=25.0, norm="pow2", act="gelu", beta=0.0) -> aewave.Solver:
     nz, ny, nx = shape
     rec = inputs.receiver_grid(nx, ny, nrec)
     # no history storage is needed for data generation / training
     return aewave.Solver(shape, h, nt, rec, storage="revolve", n_checkpoints=0, n_lat=n_lat,
-                         f0=f0, codec=codec)
+                         f0=f0, codec=codec, norm=norm, act=act, beta=beta)
 
 
 def per_draw(solver: aewave.Solver, every: int) -> int:
@@ -52,12 +52,16 @@ def per_draw(solver: aewave.Solver, every: int) -> int:
 def generate(solver: aewave.Solver, seeds, every: int, h: float = 10.0,
              drop_zero: bool = True):
     """Algorithm 1 over several prior draws.  Returns (BF16 [N][2048] normalised vectors,
-    FP32 maxima: [N][4] block maxima (space codec) or [N] vector maxima (time codec)).
-    Vectors that are still entirely at rest (maxima 0) encode and decode to zero
-    whatever the weights, and are dropped."""
+    FP32 maxima: [N][4] block maxima (space codec), [N] vector maxima (time codec), or
+    [N][2] offsets and ranges (min-max normalisation)).  With the power-of-two scales,
+    vectors that are still entirely at rest (maxima 0) encode and decode to zero whatever
+    the weights, and are dropped."""
     k = per_draw(solver, every)
     data = torch.empty((k * len(seeds), 2048), device="cuda", dtype=torch.bfloat16)
-    mshape = (k * len(seeds),) if solver.codec == "time" else (k * len(seeds), 4)
+    if solver.codec == "time":
+        mshape = (k * len(seeds), 2) if solver.norm == "minmax" else (k * len(seeds),)
+    else:
+        mshape = (k * len(seeds), 4)
     maxima = torch.empty(mshape, device="cuda")
     n = 0
     for s in seeds:
@@ -66,7 +70,7 @@ def generate(solver: aewave.Solver, seeds, every: int, h: float = 10.0,
         maxima[n:n + v.shape[0]] = m
         n += v.shape[0]
     data, maxima = data[:n], maxima[:n]
-    if drop_zero:
+    if drop_zero and solver.norm != "minmax":
         live = maxima if maxima.dim() == 1 else maxima.amax(dim=1)
         keep = torch.nonzero(live > 0).squeeze(1)
         data, maxima = data.index_select(0, keep), maxima.index_select(0, keep)
@@ -101,18 +105,24 @@ def main():
     p.add_argument("--seed", type=int, default=0, help="shuffle seed")
     p.add_argument("--f0", type=float, default=25.0, help="Ricker peak frequency [Hz]")
     p.add_argument("--loss", default="state", choices=LOSSES)
+    p.add_argument("--norm", default="pow2", choices=("pow2", "minmax"),
+                   help="time codec: power-of-two vector scales, or the paper's min-max")
+    p.add_argument("--act", default="gelu", choices=("gelu", "elu"))
+    p.add_argument("--beta", type=float, default=0.0, help="min-max range floor (0: 1e-7)")
     p.add_argument("--out", default="")
     a = p.parse_args()
     shape = tuple(a.shape)
     n_lat = a.n_lat or (512 if a.codec == "time" else 64)
     every = a.every or (1 if a.codec == "time" else 10)
-    solver = make_handle(shape, a.codec, n_lat, nt=a.nt, f0=a.f0)
+    solver = make_handle(shape, a.codec, n_lat, nt=a.nt, f0=a.f0, norm=a.norm, act=a.act,
+                         beta=a.beta)
     solver.codec_set(inputs.codec_init(seed=a.init_seed, n_hid=solver.n_hid, n_lat=n_lat))
     t0 = time.time()
     data, maxima = generate(solver, a.seeds, every)
     torch.cuda.synchronize()
     t1 = time.time()
-    res = {"codec": a.codec, "n_lat": n_lat, "n_hid": solver.n_hid, "vectors": int(data.shape[0]),
+    res = {"codec": a.codec, "norm": a.norm, "act": a.act, "beta": a.beta,
+           "n_lat": n_lat, "n_hid": solver.n_hid, "vectors": int(data.shape[0]),
            "loss_kind": a.loss, "init": a.init, "f0_hz": a.f0, "every": every,
            "train_shape": list(shape), "train_nt": a.nt, "seeds": list(a.seeds)}
     if a.init == "pca":
