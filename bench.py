@@ -82,6 +82,19 @@ def parse():
                    help="instead of the benchmark: time one hot-path kernel alone "
                         "(aew_profile_steps) on an AE handle of --shape, for profiling")
     p.add_argument("--launches", type=int, default=16)
+    p.add_argument("--map", action="store_true",
+                   help="MAP estimation (Newton-CG, BiLaplacian prior) and DIAS at the workload "
+                        "size with the compressed history against full storage")
+    p.add_argument("--theta", type=float, default=6400.0, help="prior theta [m^2]")
+    p.add_argument("--prior-std", type=float, default=50.0, help="prior sample std [m/s]")
+    p.add_argument("--noise-rel", type=float, default=0.01,
+                   help="noise std relative to the rms of the observed data")
+    p.add_argument("--newton-iters", type=int, default=3)
+    p.add_argument("--cg-max", type=int, default=10)
+    p.add_argument("--dias-samples", type=int, default=30)
+    p.add_argument("--dias-rank", type=int, default=5)
+    p.add_argument("--dias-iters", type=int, default=2)
+    p.add_argument("--map-ref", default="full", choices=["full", "none"])
     return p.parse_args()
 
 
@@ -680,6 +693,96 @@ def run_accuracy(args):
     print(json.dumps(out))
 
 
+def run_map(args):
+    """MAP estimation and DIAS (Sec. 2, Sec. 4.3) at the workload size: Newton-CG with
+    the BiLaplacian prior on the compressed history and on full storage from the same
+    start, then the DIAS active subspace at the compressed MAP point and the DIAS-F
+    solve from it.  Prints one JSON line.
+
+    The misfit is unweighted, 1/2 |d - d_obs|^2; noise of std sigma_n (noise-rel x the
+    rms of the data) and a prior with sample std prior-std [m/s] make the objective, times
+    sigma_n^2, 1/2 |d - d_obs|^2 + 1/2 |alpha_reg A_1 (c - c0)|^2 with
+    alpha_reg = sigma_n alpha_s (A_1: the operator at alpha = 1).  alpha_s is measured:
+    the std of a sample A_1^{-1} w scales as 1 / alpha."""
+    import torch
+    from paper_2304_04781_gb300 import aewave, inputs
+    shape, nt = tuple(args.shape), args.nt
+    nz, ny, nx = shape
+    n_lat = nlat_of(args)
+    rec = inputs.receiver_grid(nx, ny, args.nrec)
+    W, trained = load_weights(args.weights or default_weights(args.codec, n_lat), args.codec, n_lat)
+    c0_np = inputs.velocity_model(shape, H, seed=2).astype(np.float32)
+    c0 = torch.from_numpy(c0_np).cuda()
+    ctrue = torch.from_numpy(inputs.bump_model(c0_np.astype(np.float64), H).astype(np.float32)).cuda()
+    theta = args.theta
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    def mean_rel(c):
+        return float(((c - ctrue).abs() / ctrue).double().mean())
+
+    ae = aewave.Solver(shape, H, nt, rec, storage="ae", codec=args.codec, n_lat=n_lat, f0=args.f0,
+                       norm=args.norm, act=args.act, beta=args.beta)
+    ae.codec_set(W)
+    d_obs = ae.forward(ctrue)
+    w = torch.from_numpy(inputs.white_noise(1, shape, seed=77)[0]).cuda()
+    a, b = ev(), ev(); a.record()
+    x1, its = ae.prior_solve(w, 1.0, theta)
+    b.record(); torch.cuda.synchronize()
+    alpha_s = float(x1.double().std()) / args.prior_std
+    sigma_n = args.noise_rel * float(d_obs[1:].double().pow(2).mean().sqrt())
+    alpha = alpha_s * sigma_n
+    out = {"config": dict(workload(shape, nt, args.nrec, n_lat, args.codec), f0_hz=args.f0,
+                          norm=args.norm, act=args.act),
+           "codec_weights": "trained" if trained else "random-init",
+           "prior": {"theta_m2": theta, "sample_std": args.prior_std, "alpha_s": alpha_s,
+                     "noise_rel": args.noise_rel, "sigma_n": sigma_n, "alpha_reg": alpha,
+                     "solve_ms": a.elapsed_time(b), "solve_cg_iters": its},
+           "initial_mean_rel_err": mean_rel(c0)}
+    del x1, w
+    kw = dict(alpha=alpha, theta=theta, newton_iters=args.newton_iters, cg_max=args.cg_max)
+
+    def solve(s, W1=None, c_start=None, iters=None):
+        c = (c_start if c_start is not None else c0).clone()
+        k = dict(kw) if iters is None else dict(kw, newton_iters=iters)
+        a, b = ev(), ev(); a.record()
+        hist = s.newton_cg(c, d_obs, c0, W1=W1, **k)
+        b.record(); torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        hvps = sum(h["cg_iters"] for h in hist)
+        grads = 1 + sum(h["backtracks"] + 1 for h in hist)
+        return c, {"ms": ms, "ms_per_iter": ms / max(len(hist), 1), "hvps": hvps,
+                   "gradients": grads, "mean_rel_err": mean_rel(c), "history": hist}
+
+    c_ae, out["map_ae"] = solve(ae)
+    # DIAS: active subspace at the compressed MAP point, then the DIAS-F solve from it
+    noise = torch.from_numpy(inputs.white_noise(args.dias_samples, shape, seed=500)).cuda()
+    a, b = ev(), ev(); a.record()
+    lam, W1, G = ae.dias_subspace(c_ae, d_obs, noise, alpha_s, theta, args.dias_rank)
+    b.record(); torch.cuda.synchronize()
+    del G, noise
+    torch.cuda.empty_cache()
+    c_dias, dias = solve(ae, W1=W1, c_start=c_ae, iters=args.dias_iters)
+    out["dias"] = {"samples": args.dias_samples, "rank": args.dias_rank,
+                   "subspace_ms": a.elapsed_time(b),
+                   "ms_per_sample": a.elapsed_time(b) / args.dias_samples,
+                   "eigenvalues": [float(v) for v in lam[:max(args.dias_rank + 3, 8)]],
+                   "solve": dias}
+    out["ae_device_bytes"] = ae.stats()["device_bytes"]
+    c_ae_h = c_ae.cpu()
+    del ae, W1, c_dias
+    torch.cuda.empty_cache()
+    if args.map_ref == "full":
+        full = aewave.Solver(shape, H, nt, rec, storage="full", f0=args.f0)
+        c_full, out["map_full"] = solve(full)
+        du_ref = (c_full.cpu() - c0.cpu()).double()
+        out["map_update_rel_diff"] = float(torch.linalg.vector_norm(c_ae_h.double() - c0.cpu().double() - du_ref)
+                                           / torch.linalg.vector_norm(du_ref))
+        del full
+    print(json.dumps(out))
+
+
 def run_kernel(args):
     """One hot-path kernel alone: 2 warm-up launches, then --launches timed ones (CUDA
     events on the launching stream); prints one JSON line."""
@@ -703,6 +806,8 @@ def main():
     args = parse()
     if args.kernel:
         run_kernel(args)
+    elif args.map:
+        run_map(args)
     elif args.accuracy:
         run_accuracy(args)
     elif args.impl == "reference":

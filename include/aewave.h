@@ -92,7 +92,8 @@ enum {
   AEW_E_OVERFLOW = -8,    /* a latent overflowed FP16                                  */
   AEW_E_ARG = -9,         /* NULL pointer or out-of-range argument                     */
   AEW_E_IO = -10,         /* file could not be read or written                         */
-  AEW_E_TIMEOUT = -11     /* a bounded device-side wait gave up                        */
+  AEW_E_TIMEOUT = -11,    /* a bounded device-side wait gave up                        */
+  AEW_E_NOCONVERGE = -12  /* an iterative solve missed its tolerance                   */
 };
 
 typedef struct {
@@ -455,6 +456,104 @@ int aew_dot_noalloc(const float* a_dev, const float* b_dev, size_t n, double* ou
  * steps of the plan. */
 int aew_revolve_plan(int nt, int s, int* ops, int* args, long long cap,
                      long long* n_ops, long long* fwd_steps);
+
+/* ---------------------------------------------------------------------------------
+ * MAP estimation with the BiLaplacian prior, and DIAS (Sec. 2, Sec. 4.3)
+ *
+ * Prior (Sec. 2): the elliptic operator of the prior PDE with an isotropic Theta =
+ * theta I, discretised on the nodes with zero-flux boundaries,
+ *     A q = alpha (q - theta Lap_N q),
+ *     (Lap_N q)_i = sum over the grid neighbours nb that node i has of (q_nb - q_i) / h^2,
+ * symmetric positive definite, and the prior precision is its square: the
+ * regularisation is R(c) = 1/2 |A (c - c0)|^2.  With the projection P = I - W1^T W1
+ * onto the inactive subspace (rows of W1 orthonormal) it is the DIAS-F form
+ * 1/2 |A P (c - c0)|^2, precision P A^2 P (Sec. 4.3, the approximation of the
+ * pseudo-inverse by the projected inverse covariance).
+ * --------------------------------------------------------------------------------- */
+typedef struct aew_newton_cfg {
+  double alpha;         /* prior weight alpha (> 0) */
+  double theta;         /* prior length scale theta [m^2] (>= 0) */
+  int newton_iters;     /* Newton iterations (>= 1) */
+  int cg_max;           /* CG iterations per Newton step (>= 1) */
+  int full_hessian;     /* 0: Gauss-Newton misfit Hessian (aew_hessvec); 1: full
+                           (aew_hessvec_full, which needs full or time-codec storage) */
+  double c1;            /* Armijo constant (typically 1e-4) */
+  int max_backtracks;   /* step halvings tried (>= 1) */
+  double eta_max;       /* cap of the CG forcing term (typically 0.5) */
+  double gtol;          /* stop once |g| <= gtol |g_0| (0: run every iteration) */
+} aew_newton_cfg;
+
+/* One Newton iteration, at the iterate it starts from. */
+typedef struct aew_newton_iter {
+  double cost;          /* misfit + regularisation */
+  double misfit;
+  double reg;
+  double gnorm;         /* |g|, g = misfit gradient + regularisation gradient */
+  int cg_iters;         /* CG iterations taken (0 if the first direction had d^T H d <= 0:
+                           the step is then along -g) */
+  int backtracks;       /* step halvings before the Armijo condition held */
+  double step;          /* step length taken */
+} aew_newton_iter;
+
+/* out_dev = A q_dev (FP64 arithmetic, FP32 in and out; [nz][ny][nx] of the handle's
+ * grid and spacing).  Asynchronous on `stream`.  AEW_E_ARG for NULL pointers, alpha <= 0
+ * or theta < 0.  q_dev and out_dev must not overlap. */
+int aew_prior_apply(aew_handle* h, double alpha, double theta, const float* q_dev,
+                    float* out_dev, void* stream);
+
+/* x_dev = A^{-1} w_dev by conjugate gradients on FP64 vectors (A is SPD with spectrum
+ * inside [alpha, alpha (1 + 12 theta / h^2)]), stopped when |w - A x| <= rtol |w| or
+ * after max_iter iterations; *iters_host (may be NULL) receives the iterations taken.
+ * Prior samples are c + A^{-1} w for white noise w.  Synchronises `stream` (the
+ * convergence test reads the residual every 8 iterations).  AEW_E_ARG for bad
+ * arguments; AEW_E_NOMEM if the four FP64 work vectors cannot be allocated (they are
+ * freed on return); AEW_E_NOCONVERGE if the residual test did not pass within max_iter
+ * (x_dev then holds the last iterate). */
+int aew_prior_solve(aew_handle* h, double alpha, double theta, const float* w_dev,
+                    float* x_dev, double rtol, int max_iter, int* iters_host, void* stream);
+
+/* Inexact Newton-CG for the MAP point (Sec. 2, Sec. 4.3):
+ *   minimise J(c) = 1/2 sum_n |d^n(c) - d_obs^n|^2 + R(c),
+ * R as above (projected by W1 when W1_dev is not NULL: the DIAS-F problem).  Iteration
+ * k: the gradient g = g_misfit + dR/dc at c_k; CG from 0 on H p = -g with
+ * H v = H_misfit v + (P) A^2 (P) v, H_misfit the Gauss-Newton (aew_hessvec) or full
+ * (aew_hessvec_full) Hessian of the misfit at c_k, stopped at |r| <= eta |g| with
+ * eta = min(eta_max, sqrt(|g| / |g_0|)) (Eisenstat-Walker), after cg_max iterations,
+ * or at a direction with d^T H d <= 0; then Armijo backtracking (step 1, halved up to
+ * max_backtracks times, J(c + s p) <= J(c) + c1 s g^T p).  Each trial point runs the
+ * gradient solve, whose adjoint half is skipped when the trial's misfit already fails
+ * the Armijo test -- so an accepted trial already holds the next iterate's gradient
+ * and history (with revolve storage the adjoint always runs).  If no trial passes, the
+ * smallest step is taken.
+ *   c_dev        in: the initial iterate; out: the final one [nz][ny][nx]
+ *   d_obs_dev    [nt+1][nrec][3]
+ *   c0_dev       prior mean [nz][ny][nx]
+ *   W1_dev, r    NULL/0, or r orthonormal rows [r][nz*ny*nx] spanning the active subspace
+ *   hist_host    newton_iters entries (may be NULL); *iters_host (may be NULL) receives
+ *                the iterations recorded (fewer than newton_iters when gtol stopped it)
+ * Allocates nine FP32 work vectors for the call and frees them on return.  Returns the
+ * errors of aew_gradient / aew_hessvec(_full) (for example AEW_E_CFL if a trial point
+ * leaves the stability bound), AEW_E_ARG for bad arguments, AEW_E_NOMEM. */
+int aew_newton_cg(aew_handle* h, float* c_dev, const float* d_obs_dev, const float* c0_dev,
+                  const aew_newton_cfg* cfg, const float* W1_dev, int r,
+                  aew_newton_iter* hist_host, int* iters_host, void* stream);
+
+/* DIAS active subspace (Sec. 4.3), centred at c_dev (the two-step algorithm centres it
+ * at the MAP point): for each of the N white-noise fields w_i (noise_dev [N][nz*ny*nx],
+ * caller-drawn), the prior sample c_i = c + A^{-1} w_i (aew_prior_solve, rtol 1e-10),
+ * the misfit gradient g_i at c_i (aew_gradient) into G_dev[i], then the eigenpairs of
+ * C = (1/N) sum_i g_i g_i^T through the N x N Gram matrix M = G G^T / N (FP64 sums of
+ * FP32 products over 64-node tiles): C's leading eigenvectors are
+ * W1_k = G^T u_k / sqrt(N lambda_k) for M's eigenpairs (lambda_k, u_k).
+ *   G_dev       [N][nz*ny*nx] workspace, receives the sample gradients
+ *   W1_dev      [r][nz*ny*nx] receives the r leading eigenvectors (orthonormal rows)
+ *   lambda_host [N] receives all eigenvalues of M (= the nonzero ones of C), descending
+ * 1 <= r <= N <= 64, r <= 32.  Synchronises `stream`.  Errors of aew_prior_solve and
+ * aew_gradient (AEW_E_CFL if a sample leaves the stability bound); AEW_E_ARG if fewer
+ * than r eigenvalues are positive. */
+int aew_dias_subspace(aew_handle* h, const float* c_dev, const float* d_obs_dev,
+                      const float* noise_dev, int N, double alpha, double theta, int r,
+                      float* G_dev, float* W1_dev, double* lambda_host, void* stream);
 
 #ifdef __cplusplus
 }

@@ -26,7 +26,7 @@ WINDOW = 16   # steps per window of the time codec
 _ERRORS = {
     -1: "AEW_E_CONFIG", -2: "AEW_E_CFL", -3: "AEW_E_NONFINITE", -4: "AEW_E_NOCODEC",
     -5: "AEW_E_NOGRADIENT", -6: "AEW_E_NOMEM", -7: "AEW_E_CUDA", -8: "AEW_E_OVERFLOW",
-    -9: "AEW_E_ARG", -10: "AEW_E_IO", -11: "AEW_E_TIMEOUT",
+    -9: "AEW_E_ARG", -10: "AEW_E_IO", -11: "AEW_E_TIMEOUT", -12: "AEW_E_NOCONVERGE",
 }
 
 
@@ -66,6 +66,21 @@ class aew_train_cfg(ctypes.Structure):
 
 
 LOSSES = {"state": 0, "strain": 1, "strain-amplitude": 2, "strain-energy": 3}
+
+
+class aew_newton_cfg(ctypes.Structure):
+    _fields_ = [
+        ("alpha", c_double), ("theta", c_double), ("newton_iters", c_int), ("cg_max", c_int),
+        ("full_hessian", c_int), ("c1", c_double), ("max_backtracks", c_int),
+        ("eta_max", c_double), ("gtol", c_double),
+    ]
+
+
+class aew_newton_iter(ctypes.Structure):
+    _fields_ = [
+        ("cost", c_double), ("misfit", c_double), ("reg", c_double), ("gnorm", c_double),
+        ("cg_iters", c_int), ("backtracks", c_int), ("step", c_double),
+    ]
 
 
 _LIB = None
@@ -109,6 +124,13 @@ _SIGS = [
     ("aew_codec_eval", c_int, [c_void_p, c_void_p, c_void_p, c_longlong, c_void_p, c_void_p]),
     ("aew_sym_eig", c_int, [c_int, c_void_p, c_void_p, c_void_p]),
     ("aew_profile_steps", c_int, [c_void_p, c_void_p, c_int, c_int, POINTER(c_double), c_void_p]),
+    ("aew_prior_apply", c_int, [c_void_p, c_double, c_double, c_void_p, c_void_p, c_void_p]),
+    ("aew_prior_solve", c_int, [c_void_p, c_double, c_double, c_void_p, c_void_p, c_double, c_int,
+                                POINTER(c_int), c_void_p]),
+    ("aew_newton_cg", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, POINTER(aew_newton_cfg),
+                              c_void_p, c_int, c_void_p, POINTER(c_int), c_void_p]),
+    ("aew_dias_subspace", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_double,
+                                  c_double, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
 ]
 
 
@@ -333,6 +355,57 @@ class Solver:
             out = torch.empty_like(dc)
         self._check(lib().aew_hessvec_full(self._h, _ptr(dc), _ptr(out), _stream()))
         return out
+
+    # ------------------------------------------------------------------ MAP / DIAS
+    def prior_apply(self, q: torch.Tensor, alpha: float, theta: float,
+                    out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """A q = alpha (q - theta Lap_N q), the BiLaplacian prior's elliptic operator."""
+        if out is None:
+            out = torch.empty_like(q)
+        self._check(lib().aew_prior_apply(self._h, alpha, theta, _ptr(q), _ptr(out), _stream()))
+        return out
+
+    def prior_solve(self, w: torch.Tensor, alpha: float, theta: float, rtol: float = 1e-6,
+                    max_iter: int = 5000, out: Optional[torch.Tensor] = None):
+        """(A^{-1} w, CG iterations)."""
+        if out is None:
+            out = torch.empty_like(w)
+        it = c_int(0)
+        self._check(lib().aew_prior_solve(self._h, alpha, theta, _ptr(w), _ptr(out), rtol,
+                                          max_iter, byref(it), _stream()))
+        return out, it.value
+
+    def newton_cg(self, c: torch.Tensor, d_obs: torch.Tensor, c0: torch.Tensor, alpha: float,
+                  theta: float, newton_iters: int = 5, cg_max: int = 20, full_hessian: bool = False,
+                  c1: float = 1e-4, max_backtracks: int = 10, eta_max: float = 0.5,
+                  gtol: float = 0.0, W1: Optional[torch.Tensor] = None):
+        """Inexact Newton-CG for the MAP point (or, with the active subspace W1 [r][n],
+        the DIAS-F point).  c is updated in place; returns the per-iteration history as
+        a list of dicts."""
+        cfg = aew_newton_cfg(alpha, theta, newton_iters, cg_max, int(full_hessian), c1,
+                             max_backtracks, eta_max, gtol)
+        hist = (aew_newton_iter * newton_iters)()
+        n = c_int(0)
+        r = 0 if W1 is None else W1.shape[0]
+        self._check(lib().aew_newton_cg(self._h, _ptr(c), _ptr(d_obs), _ptr(c0), byref(cfg),
+                                        _ptr(W1), r, hist, byref(n), _stream()))
+        return [{k: getattr(hist[i], k) for k, _ in aew_newton_iter._fields_}
+                for i in range(n.value)]
+
+    def dias_subspace(self, c: torch.Tensor, d_obs: torch.Tensor, noise: torch.Tensor,
+                      alpha: float, theta: float, r: int, G: Optional[torch.Tensor] = None):
+        """DIAS active subspace at c from the gradients at the prior samples
+        c + A^{-1} noise[i]: (eigenvalues [N], W1 [r][n], sample gradients G [N][n])."""
+        N = noise.shape[0]
+        n = c.numel()
+        if G is None:
+            G = torch.empty((N, n), device="cuda", dtype=torch.float32)
+        W1 = torch.empty((r, n), device="cuda", dtype=torch.float32)
+        lam = np.empty(N)
+        self._check(lib().aew_dias_subspace(self._h, _ptr(c), _ptr(d_obs), _ptr(noise), N, alpha,
+                                            theta, r, _ptr(G), _ptr(W1), lam.ctypes.data,
+                                            _stream()))
+        return lam, W1, G
 
     def jvp(self, dc: torch.Tensor) -> torch.Tensor:
         dd = self._drec()

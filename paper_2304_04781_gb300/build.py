@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libaewave.so")
 OBJ = os.path.join(HERE, "_build")
 SOURCES = ["aew_api.cu", "aew_stencil.cu", "aew_reduce.cu", "aew_codec.cu", "aew_train.cu",
-           "aew_revolve.cpp", "aew_pca.cpp", "aew_noalloc.cu"]
+           "aew_revolve.cpp", "aew_pca.cpp", "aew_noalloc.cu", "aew_newton.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -21,6 +21,7 @@
 #include "aew_internal.cuh"
 #include "aew_pca.h"
 #include "aew_revolve.h"
+#include "aew_solver.h"
 
 using aew::Codec;
 
@@ -101,6 +102,9 @@ struct aew_handle {
   bool tg_set = false, th_set = false;
   std::vector<float> wav;
   bool have_grad = false;
+  // Armijo gate of a gradient run by the Newton driver: stop after the forward solve
+  // when the misfit exceeds it (+inf: never)
+  double gate = INFINITY;
   Codec* codec = nullptr;
   std::vector<void*> allocs;
   size_t bytes = 0;
@@ -335,6 +339,19 @@ int residual_and_misfit(aew_handle* h, const float* d_obs, cudaStream_t s) {
   return AEW_OK;
 }
 
+// internal return value: the Armijo gate stopped a gradient after its forward solve
+constexpr int kGated = 1;
+
+// with a finite gate, read the misfit just computed and stop the gradient if it fails
+int misfit_gate(aew_handle* h, cudaStream_t s) {
+  if (!std::isfinite(h->gate)) return AEW_OK;
+  double J = 0.0;
+  AEW_CK(cudaMemcpyAsync(&J, h->part + aew::kRedBlocks, sizeof(double), cudaMemcpyDeviceToHost, s));
+  AEW_CK(cudaStreamSynchronize(s));
+  h->stats.last_misfit = J;
+  return J > h->gate ? kGated : AEW_OK;
+}
+
 int begin_adjoint(aew_handle* h, cudaStream_t s) {
   for (int i = 0; i < 4; ++i) AEW_CK(cudaMemsetAsync(h->ad[0][i], 0, h->C * sizeof(float), s));
   AEW_CK(cudaMemsetAsync(h->acc64, 0, h->C * sizeof(double), s));
@@ -427,6 +444,7 @@ int gradient_full(aew_handle* h, const float* d_obs, const float* wav, cudaStrea
   }
   int rc = residual_and_misfit(h, d_obs, s);
   if (rc) return rc;
+  if ((rc = misfit_gate(h, s))) return rc;
   if ((rc = begin_adjoint(h, s))) return rc;
   int cur = 0;
   for (int n = nt - 1; n >= 0; --n) {
@@ -563,6 +581,7 @@ int gradient_ae(aew_handle* h, const float* d_obs, const float* wav, cudaStream_
   }
   if ((rc = join(h, h->side, s, h->ev_sync2))) return rc;
   if ((rc = residual_and_misfit(h, d_obs, s))) return rc;
+  if ((rc = misfit_gate(h, s))) return rc;
   if ((rc = ae_adjoint_sweep(h, h->R, s))) return rc;
   h->stats.forward_steps = nt;
   h->stats.adjoint_steps = nt;
@@ -680,6 +699,7 @@ int gradient_ae_time(aew_handle* h, const float* d_obs, const float* wav, cudaSt
   }
   if ((rc = join(h, h->side, s, h->ev_sync2))) return rc;
   if ((rc = residual_and_misfit(h, d_obs, s))) return rc;
+  if ((rc = misfit_gate(h, s))) return rc;
   if ((rc = time_adjoint_sweep(h, h->R, s))) return rc;
   h->stats.forward_steps = nt;
   h->stats.adjoint_steps = nt;
@@ -1200,13 +1220,14 @@ int aew_propagate(aew_handle* h, const float* c_dev, float* const state_dev[4], 
   return AEW_OK;
 }
 
-int aew_gradient(aew_handle* h, const float* c_dev, const float* d_obs_dev, float* g_dev,
-                 double* misfit_host, void* stream) {
+// the gradient drivers with an optional Armijo gate (aew::gradient_gated)
+static int gradient_impl(aew_handle* h, const float* c_dev, const float* d_obs_dev, float* g_dev,
+                         double* misfit_host, double gate, bool* accepted, cudaStream_t s) {
   if (!h) return AEW_E_ARG;
   if (!d_obs_dev && h->nrow) return fail(h, AEW_E_ARG, "d_obs is NULL");
   if (!g_dev) return fail(h, AEW_E_ARG, "g is NULL");
   h->err.clear();
-  cudaStream_t s = S(stream);
+  if (accepted) *accepted = true;
   h->have_grad = false;
   if (h->cfg.storage == AEW_AE && !aew::codec_ready(h->codec))
     return fail(h, AEW_E_NOCODEC, "AE storage needs codec weights (aew_codec_set)");
@@ -1215,6 +1236,7 @@ int aew_gradient(aew_handle* h, const float* c_dev, const float* d_obs_dev, floa
   h->tg_set = false;
   AEW_CK(cudaEventRecord(h->tg[0], s));
   const float* wav = h->wav.data();
+  h->gate = h->cfg.storage == AEW_REVOLVE ? INFINITY : gate;
   if (h->cfg.storage == AEW_FULL) {
     rc = gradient_full(h, d_obs_dev, wav, s);
   } else if (h->cfg.storage == AEW_REVOLVE) {
@@ -1226,6 +1248,14 @@ int aew_gradient(aew_handle* h, const float* c_dev, const float* d_obs_dev, floa
     rc = gradient_ae_time(h, d_obs_dev, wav, s);
   } else {
     rc = gradient_ae(h, d_obs_dev, wav, s);
+  }
+  h->gate = INFINITY;
+  if (rc == kGated) {   // the misfit failed the gate: no adjoint solve, no gradient
+    if (aew::codec_take_error(h->codec, s))
+      return fail(h, AEW_E_TIMEOUT, "a kernel gave up waiting (bounded mbarrier wait)");
+    if (misfit_host) *misfit_host = h->stats.last_misfit;
+    if (accepted) *accepted = false;
+    return AEW_OK;
   }
   if (rc) return rc;
   if (aew::codec_take_error(h->codec, s))
@@ -1246,9 +1276,15 @@ int aew_gradient(aew_handle* h, const float* c_dev, const float* d_obs_dev, floa
     h->stats.latent_overflow = ovf;
     if (misfit_host) *misfit_host = J;
     if (ovf) return fail(h, AEW_E_OVERFLOW, "a latent overflowed FP16 during encoding");
+    if (accepted && J > gate) *accepted = false;   // revolve: tested after the adjoint
   }
   h->have_grad = true;
   return AEW_OK;
+}
+
+int aew_gradient(aew_handle* h, const float* c_dev, const float* d_obs_dev, float* g_dev,
+                 double* misfit_host, void* stream) {
+  return gradient_impl(h, c_dev, d_obs_dev, g_dev, misfit_host, INFINITY, nullptr, S(stream));
 }
 
 // incremental forward at the stored c: dd = J_F dc  (dm must be prepared)
@@ -1886,3 +1922,24 @@ int aew_codec_train_step(aew_handle* h, const uint16_t* batch_dev, const float* 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// Internal interface of the optimisation drivers (aew_solver.h)
+// ---------------------------------------------------------------------------------
+namespace aew {
+
+GridInfo grid_of(const aew_handle* h) {
+  return GridInfo{h->cfg.nx, h->cfg.ny, h->cfg.nz, h->cfg.h, h->C};
+}
+
+int set_error(aew_handle* h, int code, const std::string& msg) { return fail(h, code, msg); }
+
+int gradient_gated(aew_handle* h, const float* c_dev, const float* d_obs_dev, float* g_dev,
+                   double gate, double* misfit, bool* accepted, cudaStream_t s) {
+  double J = 0.0;
+  const int rc = gradient_impl(h, c_dev, d_obs_dev, g_dev, &J, gate, accepted, s);
+  if (misfit) *misfit = J;
+  return rc;
+}
+
+}  // namespace aew

@@ -1,0 +1,642 @@
+// MAP estimation with the BiLaplacian prior (Sec. 2) by inexact Newton-CG, and the
+// DIAS active subspace (Sec. 4.3), built on the gradient and Hessian-vector solves of
+// aew_api.cu.
+//
+// The solves dominate: one Newton iteration is a gradient plus up to cg_max
+// Hessian-vector products, each two or three wave solves over the whole history.
+// What runs here besides them is HBM-bound vector work: the prior operator (a 7-point
+// stencil with zero-flux boundaries, one thread per node, neighbours through L1/L2), the
+// projection onto the inactive subspace, CG updates, and FP64-accumulated inner
+// products.  Arithmetic is FP32 -- GB300's FP64 rate is a small fraction of its FP32
+// rate -- with FP64 only in the reductions.
+//
+// Prior solve A x = w: conjugate gradients whose scalars never leave the device.  Each
+// kernel that needs rr or p^T A p sums the previous kernel's per-block FP64 partials
+// itself (every block in the same order, so all blocks agree), so an iteration is three
+// launches and the host reads the residual only every 8 iterations.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/aewave.h"
+#include "aew_internal.cuh"
+#include "aew_pca.h"
+#include "aew_solver.h"
+
+namespace aew {
+namespace {
+
+constexpr int NT = 256;
+constexpr int kVecBlocks = 152 * 4;   // grid of the vector kernels (grid-stride)
+constexpr int kMaxN = 64;             // DIAS gradient samples
+constexpr int kMaxR = 32;             // DIAS active subspace dimension
+constexpr int kGramTile = 64;         // nodes per Gram tile
+
+struct Grid {
+  int nx, ny, nz;
+  size_t C;
+};
+
+int vec_grid(size_t n) {
+  const size_t b = (n + NT - 1) / NT;
+  return (int)std::max<size_t>(1, std::min<size_t>(b, kVecBlocks));
+}
+
+// block-level FP64 sum of v into part[blockIdx.x]
+__device__ void block_store(double v, double* part) {
+  __shared__ double sw[NT / 32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < NT / 32; ++w) s += sw[w];
+    part[blockIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+// sum of part[0..n) by the whole block, in a fixed order (all blocks agree)
+__device__ double block_sum_of(const double* __restrict__ part, int n) {
+  __shared__ double sw[NT / 32];
+  __shared__ double total;
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += NT) v += part[i];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < NT / 32; ++w) s += sw[w];
+    total = s;
+  }
+  __syncthreads();
+  return total;
+}
+
+// A x at node n: alpha x_n - alpha theta / h^2 * sum over existing neighbours (x_nb - x_n)
+__device__ __forceinline__ float prior_at(const float* __restrict__ x, size_t n, const Grid& g,
+                                          float alpha, float at) {
+  const int i = (int)(n % (size_t)g.nx);
+  const size_t rest = n / (size_t)g.nx;
+  const int j = (int)(rest % (size_t)g.ny);
+  const int k = (int)(rest / (size_t)g.ny);
+  const size_t sy = (size_t)g.nx, sz = (size_t)g.nx * g.ny;
+  const float xn = x[n];
+  float lap = 0.f;
+  if (i > 0) lap += x[n - 1] - xn;
+  if (i + 1 < g.nx) lap += x[n + 1] - xn;
+  if (j > 0) lap += x[n - sy] - xn;
+  if (j + 1 < g.ny) lap += x[n + sy] - xn;
+  if (k > 0) lap += x[n - sz] - xn;
+  if (k + 1 < g.nz) lap += x[n + sz] - xn;
+  return alpha * xn - at * lap;
+}
+
+// y = A x (+ yadd); optional per-block partials of sum wdot . (A x)
+// (y may be yadd; x must not overlap y)
+__global__ void prior_kernel(const float* __restrict__ x, float* y, const float* yadd, Grid g,
+                             float alpha, float at,
+                             const float* __restrict__ wdot, double* part) {
+  double acc = 0.0;
+  for (size_t n = blockIdx.x * (size_t)NT + threadIdx.x; n < g.C; n += (size_t)gridDim.x * NT) {
+    float v = prior_at(x, n, g, alpha, at);
+    if (part) acc += (double)wdot[n] * (double)v;
+    if (yadd) v += yadd[n];
+    y[n] = v;
+  }
+  if (part) block_store(acc, part);
+}
+
+// out = a x + b y (either of x, y may be out)
+__global__ void axpby_kernel(float a, const float* x, float b, const float* y, float* out,
+                             size_t n) {
+  for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < n; i += (size_t)gridDim.x * NT)
+    out[i] = a * x[i] + b * y[i];
+}
+
+__global__ void dot_kernel(const float* __restrict__ a, const float* __restrict__ b, size_t n,
+                           double* part) {
+  double acc = 0.0;
+  for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < n; i += (size_t)gridDim.x * NT)
+    acc += (double)a[i] * (double)b[i];
+  block_store(acc, part);
+}
+
+// CG for A x = w, FP32 vectors, scalars from FP64 partials (see the file comment).
+// update: a = rr / pAp; x += a p; r -= a Ap; partials of r.r into prr_new
+__global__ void cg_update_kernel(float* __restrict__ x, float* __restrict__ r,
+                                 const float* __restrict__ p, const float* __restrict__ Ap,
+                                 size_t n, const double* ppap, const double* prr, int nblk,
+                                 double* prr_new) {
+  const double pap = block_sum_of(ppap, nblk);
+  const double rr = block_sum_of(prr, nblk);
+  const float a = pap > 0.0 ? (float)(rr / pap) : 0.f;
+  double acc = 0.0;
+  for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < n; i += (size_t)gridDim.x * NT) {
+    x[i] += a * p[i];
+    const float ri = r[i] - a * Ap[i];
+    r[i] = ri;
+    acc += (double)ri * (double)ri;
+  }
+  block_store(acc, prr_new);
+}
+
+// direction: p = r + (rr_new / rr_old) p
+__global__ void cg_dir_kernel(float* __restrict__ p, const float* __restrict__ r, size_t n,
+                              const double* prr_old, const double* prr_new, int nblk) {
+  const double ro = block_sum_of(prr_old, nblk);
+  const double rn = block_sum_of(prr_new, nblk);
+  const float b = ro > 0.0 ? (float)(rn / ro) : 0.f;
+  for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < n; i += (size_t)gridDim.x * NT)
+    p[i] = r[i] + b * p[i];
+}
+
+// projection: partial dots of v with the r rows of W1, part[k][nblk]
+__global__ void proj_dots_kernel(const float* __restrict__ W1, int r, const float* __restrict__ v,
+                                 size_t n, double* part) {
+  for (int k = 0; k < r; ++k) {
+    const float* w = W1 + (size_t)k * n;
+    double acc = 0.0;
+    for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < n; i += (size_t)gridDim.x * NT)
+      acc += (double)w[i] * (double)v[i];
+    block_store(acc, part + (size_t)k * gridDim.x);
+  }
+}
+
+// out = v - sum_k (W1_k . v) W1_k, the coefficients summed from proj_dots_kernel's partials
+__global__ void proj_apply_kernel(const float* __restrict__ W1, int r, const float* v, float* out,
+                                  size_t n, const double* part, int nblk) {
+  __shared__ float coef[kMaxR];
+  for (int k = 0; k < r; ++k) {
+    const double s = block_sum_of(part + (size_t)k * nblk, nblk);
+    if (threadIdx.x == 0) coef[k] = (float)s;
+  }
+  __syncthreads();
+  for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < n; i += (size_t)gridDim.x * NT) {
+    float acc = v[i];
+    for (int k = 0; k < r; ++k) acc -= coef[k] * W1[(size_t)k * n + i];
+    out[i] = acc;
+  }
+}
+
+// Gram matrix of the N rows of G: per block, FP32 sums over 64-node tiles staged in
+// shared memory, accumulated in FP64; part[block][pair], pairs (a <= b) row-major
+__global__ void gram_kernel(const float* __restrict__ G, int N, size_t n, double* part) {
+  __shared__ float tile[kMaxN][kGramTile + 1];
+  const int npair = N * (N + 1) / 2;
+  constexpr int kPer = (kMaxN * (kMaxN + 1) / 2 + NT - 1) / NT;
+  double acc[kPer];
+  int pa[kPer], pb[kPer];
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    acc[q] = 0.0;
+    int p = threadIdx.x + q * NT, a = 0;
+    pa[q] = -1;
+    pb[q] = -1;
+    if (p < npair) {
+      while (p >= N - a) {   // row a holds pairs (a, a..N-1)
+        p -= N - a;
+        ++a;
+      }
+      pa[q] = a;
+      pb[q] = a + p;
+    }
+  }
+  const size_t ntile = (n + kGramTile - 1) / kGramTile;
+  for (size_t t = blockIdx.x; t < ntile; t += gridDim.x) {
+    const size_t base = t * kGramTile;
+    __syncthreads();
+    for (int e = threadIdx.x; e < N * kGramTile; e += NT) {
+      const int row = e / kGramTile, col = e % kGramTile;
+      const size_t i = base + col;
+      tile[row][col] = i < n ? G[(size_t)row * n + i] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      if (pa[q] < 0) continue;
+      float s = 0.f;
+      for (int c = 0; c < kGramTile; ++c) s += tile[pa[q]][c] * tile[pb[q]][c];
+      acc[q] += (double)s;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    const int p = threadIdx.x + q * NT;
+    if (p < npair) part[(size_t)blockIdx.x * npair + p] = acc[q];
+  }
+}
+
+// M[a][b] = M[b][a] = scale * sum over blocks of part[.][pair]
+__global__ void gram_sum_kernel(const double* part, int nblk, int N, double scale, double* M) {
+  const int npair = N * (N + 1) / 2;
+  for (int p = blockIdx.x * NT + threadIdx.x; p < npair; p += gridDim.x * NT) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[(size_t)b * npair + p];
+    int a = 0, q = p;
+    while (q >= N - a) {
+      q -= N - a;
+      ++a;
+    }
+    M[a * N + a + q] = scale * s;
+    M[(a + q) * N + a] = scale * s;
+  }
+}
+
+// W1[k][i] = sum_j coef[j][k] G[j][i]
+__global__ void combine_kernel(const float* __restrict__ G, int N, size_t n,
+                               const float* __restrict__ coef, int r, float* __restrict__ W1) {
+  __shared__ float cs[kMaxN * kMaxR];
+  for (int e = threadIdx.x; e < N * r; e += NT) cs[e] = coef[e];
+  __syncthreads();
+  for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < n; i += (size_t)gridDim.x * NT) {
+    float acc[kMaxR];
+#pragma unroll
+    for (int k = 0; k < kMaxR; ++k) acc[k] = 0.f;
+    for (int j = 0; j < N; ++j) {
+      const float gj = G[(size_t)j * n + i];
+#pragma unroll
+      for (int k = 0; k < kMaxR; ++k)
+        if (k < r) acc[k] += cs[j * r + k] * gj;
+    }
+#pragma unroll
+    for (int k = 0; k < kMaxR; ++k)
+      if (k < r) W1[(size_t)k * n + i] = acc[k];
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// host helpers
+// ---------------------------------------------------------------------------------
+#define NW_CK(expr)                                                         \
+  do {                                                                      \
+    cudaError_t _e = (expr);                                                \
+    if (_e != cudaSuccess)                                                  \
+      return set_error(h, AEW_E_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+  } while (0)
+
+// device buffers of one call, freed when it returns
+struct Work {
+  std::vector<void*> ptrs;
+  ~Work() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+  template <class T>
+  bool alloc(T** p, size_t count) {
+    void* q = nullptr;
+    if (cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) {
+      cudaGetLastError();
+      *p = nullptr;
+      return false;
+    }
+    ptrs.push_back(q);
+    *p = static_cast<T*>(q);
+    return true;
+  }
+};
+
+struct Ops {
+  aew_handle* h;
+  Grid g;
+  cudaStream_t s;
+  double* part;        // [kVecBlocks] FP64 partials
+  double* ppart;       // [kMaxR][kVecBlocks] projection partials
+  std::vector<double> hp;
+
+  int grid() const { return vec_grid(g.C); }
+
+  int axpby(float a, const float* x, float b, const float* y, float* out) {
+    axpby_kernel<<<grid(), NT, 0, s>>>(a, x, b, y, out, g.C);
+    NW_CK(cudaGetLastError());
+    return AEW_OK;
+  }
+  int copy(const float* x, float* out) {
+    NW_CK(cudaMemcpyAsync(out, x, g.C * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    return AEW_OK;
+  }
+  // host FP64 inner product (synchronises)
+  int dot(const float* a, const float* b, double* out) {
+    const int nb = grid();
+    dot_kernel<<<nb, NT, 0, s>>>(a, b, g.C, part);
+    NW_CK(cudaGetLastError());
+    hp.resize(nb);
+    NW_CK(cudaMemcpyAsync(hp.data(), part, nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+    NW_CK(cudaStreamSynchronize(s));
+    double acc = 0.0;
+    for (int i = 0; i < nb; ++i) acc += hp[i];
+    *out = acc;
+    return AEW_OK;
+  }
+  // y = A x (+ yadd)
+  int prior(double alpha, double theta, double hh, const float* x, float* y,
+            const float* yadd = nullptr) {
+    prior_kernel<<<grid(), NT, 0, s>>>(x, y, yadd, g, (float)alpha,
+                                       (float)(alpha * theta / (hh * hh)), nullptr, nullptr);
+    NW_CK(cudaGetLastError());
+    return AEW_OK;
+  }
+  // out = P v = v - W1^T (W1 v)  (out may be v)
+  int project(const float* W1, int r, const float* v, float* out) {
+    const int nb = grid();
+    proj_dots_kernel<<<nb, NT, 0, s>>>(W1, r, v, g.C, ppart);
+    NW_CK(cudaGetLastError());
+    proj_apply_kernel<<<nb, NT, 0, s>>>(W1, r, v, out, g.C, ppart, nb);
+    NW_CK(cudaGetLastError());
+    return AEW_OK;
+  }
+};
+
+int prior_args_ok(aew_handle* h, double alpha, double theta) {
+  if (!(alpha > 0.0) || !std::isfinite(alpha))
+    return set_error(h, AEW_E_ARG, "prior alpha must be positive and finite");
+  if (!(theta >= 0.0) || !std::isfinite(theta))
+    return set_error(h, AEW_E_ARG, "prior theta must be non-negative and finite");
+  return AEW_OK;
+}
+
+// CG on A x = w (device scalars); x_dev written
+int prior_cg(aew_handle* h, const Grid& g, double hh, double alpha, double theta,
+             const float* w, float* x, double rtol, int max_iter, int* iters, cudaStream_t s) {
+  Work ws;
+  float *r, *p, *Ap;
+  double* part;   // [3][kVecBlocks]: p.Ap, rr (two parities)
+  if (!ws.alloc(&r, g.C) || !ws.alloc(&p, g.C) || !ws.alloc(&Ap, g.C) ||
+      !ws.alloc(&part, 3 * (size_t)kVecBlocks))
+    return set_error(h, AEW_E_NOMEM, "prior solve: work vectors do not fit");
+  const int nb = vec_grid(g.C);
+  double* ppap = part;
+  double* prr[2] = {part + kVecBlocks, part + 2 * kVecBlocks};
+  const float fa = (float)alpha, fat = (float)(alpha * theta / (hh * hh));
+  NW_CK(cudaMemsetAsync(x, 0, g.C * sizeof(float), s));
+  NW_CK(cudaMemcpyAsync(r, w, g.C * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  NW_CK(cudaMemcpyAsync(p, w, g.C * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  dot_kernel<<<nb, NT, 0, s>>>(w, w, g.C, prr[0]);
+  NW_CK(cudaGetLastError());
+  std::vector<double> hp(nb);
+  auto host_sum = [&](const double* dpart, double* out) -> int {
+    NW_CK(cudaMemcpyAsync(hp.data(), dpart, nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+    NW_CK(cudaStreamSynchronize(s));
+    double a = 0.0;
+    for (int i = 0; i < nb; ++i) a += hp[i];
+    *out = a;
+    return AEW_OK;
+  };
+  double ww = 0.0;
+  int rc = host_sum(prr[0], &ww);
+  if (rc) return rc;
+  if (iters) *iters = 0;
+  if (ww == 0.0) return AEW_OK;   // w = 0: x = 0
+  const double tol2 = rtol * rtol * ww;
+  int it = 0;
+  for (; it < max_iter; ++it) {
+    const int cur = it & 1, nxt = cur ^ 1;
+    prior_kernel<<<nb, NT, 0, s>>>(p, Ap, nullptr, g, fa, fat, p, ppap);
+    cg_update_kernel<<<nb, NT, 0, s>>>(x, r, p, Ap, g.C, ppap, prr[cur], nb, prr[nxt]);
+    cg_dir_kernel<<<nb, NT, 0, s>>>(p, r, g.C, prr[cur], prr[nxt], nb);
+    NW_CK(cudaGetLastError());
+    if ((it & 7) == 7 || it + 1 == max_iter) {
+      double rr = 0.0;
+      if ((rc = host_sum(prr[nxt], &rr))) return rc;
+      if (rr <= tol2) {
+        ++it;
+        if (iters) *iters = it;
+        return AEW_OK;
+      }
+    }
+  }
+  if (iters) *iters = it;
+  char buf[160];
+  std::snprintf(buf, sizeof buf, "prior solve: relative residual above %.3g after %d iterations",
+                rtol, max_iter);
+  return set_error(h, AEW_E_NOCONVERGE, buf);
+}
+
+}  // namespace
+}  // namespace aew
+
+using aew::Grid;
+using aew::set_error;
+
+extern "C" {
+
+int aew_prior_apply(aew_handle* h, double alpha, double theta, const float* q_dev,
+                    float* out_dev, void* stream) {
+  if (!h) return AEW_E_ARG;
+  if (!q_dev || !out_dev) return set_error(h, AEW_E_ARG, "NULL vector");
+  int rc = aew::prior_args_ok(h, alpha, theta);
+  if (rc) return rc;
+  const aew::GridInfo gi = aew::grid_of(h);
+  const Grid g{gi.nx, gi.ny, gi.nz, gi.C};
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  aew::prior_kernel<<<aew::vec_grid(g.C), aew::NT, 0, s>>>(
+      q_dev, out_dev, nullptr, g, (float)alpha, (float)(alpha * theta / (gi.h * gi.h)), nullptr,
+      nullptr);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(h, AEW_E_CUDA, cudaGetErrorString(e));
+  return AEW_OK;
+}
+
+int aew_prior_solve(aew_handle* h, double alpha, double theta, const float* w_dev, float* x_dev,
+                    double rtol, int max_iter, int* iters_host, void* stream) {
+  if (!h) return AEW_E_ARG;
+  if (!w_dev || !x_dev) return set_error(h, AEW_E_ARG, "NULL vector");
+  if (!(rtol > 0.0) || max_iter < 1) return set_error(h, AEW_E_ARG, "rtol > 0, max_iter >= 1");
+  int rc = aew::prior_args_ok(h, alpha, theta);
+  if (rc) return rc;
+  const aew::GridInfo gi = aew::grid_of(h);
+  const Grid g{gi.nx, gi.ny, gi.nz, gi.C};
+  return aew::prior_cg(h, g, gi.h, alpha, theta, w_dev, x_dev, rtol, max_iter, iters_host,
+                       static_cast<cudaStream_t>(stream));
+}
+
+int aew_newton_cg(aew_handle* h, float* c_dev, const float* d_obs_dev, const float* c0_dev,
+                  const aew_newton_cfg* cfg, const float* W1_dev, int r,
+                  aew_newton_iter* hist_host, int* iters_host, void* stream) {
+  if (!h) return AEW_E_ARG;
+  if (!c_dev || !c0_dev || !cfg) return set_error(h, AEW_E_ARG, "NULL argument");
+  int rc = aew::prior_args_ok(h, cfg->alpha, cfg->theta);
+  if (rc) return rc;
+  if (cfg->newton_iters < 1 || cfg->cg_max < 1 || cfg->max_backtracks < 1 ||
+      !(cfg->c1 > 0.0 && cfg->c1 < 1.0) || !(cfg->eta_max > 0.0) || !(cfg->gtol >= 0.0))
+    return set_error(h, AEW_E_ARG, "bad Newton-CG settings");
+  if (W1_dev ? (r < 1 || r > aew::kMaxR) : r != 0)
+    return set_error(h, AEW_E_ARG, "W1 needs 1 <= r <= 32 rows (r = 0 without W1)");
+  if (iters_host) *iters_host = 0;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const aew::GridInfo gi = aew::grid_of(h);
+  const Grid g{gi.nx, gi.ny, gi.nz, gi.C};
+  const double al = cfg->alpha, th = cfg->theta, hh = gi.h;
+
+  aew::Work ws;
+  float *g_tot, *gm, *x, *res, *d, *Hd, *t1, *t2, *ct;
+  double *part, *ppart;
+  if (!ws.alloc(&g_tot, g.C) || !ws.alloc(&gm, g.C) || !ws.alloc(&x, g.C) ||
+      !ws.alloc(&res, g.C) || !ws.alloc(&d, g.C) || !ws.alloc(&Hd, g.C) || !ws.alloc(&t1, g.C) ||
+      !ws.alloc(&t2, g.C) || !ws.alloc(&ct, g.C) || !ws.alloc(&part, aew::kVecBlocks) ||
+      !ws.alloc(&ppart, (size_t)aew::kMaxR * aew::kVecBlocks))
+    return set_error(h, AEW_E_NOMEM, "Newton-CG: work vectors do not fit");
+  aew::Ops op{h, g, s, part, ppart, {}};
+
+  // R(c) = 1/2 |A P (c - c0)|^2 and, with grad, grad = P A^2 P (c - c0)
+  auto reg = [&](const float* c, double* R, float* grad) -> int {
+    int e = op.axpby(1.f, c, -1.f, c0_dev, t1);
+    if (!e && W1_dev) e = op.project(W1_dev, r, t1, t1);
+    if (!e) e = op.prior(al, th, hh, t1, t2);
+    if (!e) e = op.dot(t2, t2, R);
+    if (e) return e;
+    *R *= 0.5;
+    if (!grad) return AEW_OK;
+    if ((e = op.prior(al, th, hh, t2, grad))) return e;
+    if (W1_dev) e = op.project(W1_dev, r, grad, grad);
+    return e;
+  };
+  // Hd = H_misfit v + P A^2 P v
+  auto hess = [&](const float* v, float* out) -> int {
+    int e = cfg->full_hessian ? aew_hessvec_full(h, v, out, stream) : aew_hessvec(h, v, out, stream);
+    if (e) return e;
+    const float* vin = v;
+    if (W1_dev) {
+      if ((e = op.project(W1_dev, r, v, t1))) return e;
+      vin = t1;
+    }
+    if ((e = op.prior(al, th, hh, vin, t2))) return e;
+    if (W1_dev) {
+      if ((e = op.prior(al, th, hh, t2, t1))) return e;
+      if ((e = op.project(W1_dev, r, t1, t1))) return e;
+      return op.axpby(1.f, out, 1.f, t1, out);
+    }
+    return op.prior(al, th, hh, t2, out, out);
+  };
+
+  double Jm = 0.0;
+  bool ok = true;
+  if ((rc = aew::gradient_gated(h, c_dev, d_obs_dev, gm, INFINITY, &Jm, &ok, s))) return rc;
+  double g0n = -1.0;
+  for (int it = 0; it < cfg->newton_iters; ++it) {
+    double R = 0.0;
+    if ((rc = reg(c_dev, &R, g_tot))) return rc;
+    if ((rc = op.axpby(1.f, gm, 1.f, g_tot, g_tot))) return rc;
+    double gg = 0.0;
+    if ((rc = op.dot(g_tot, g_tot, &gg))) return rc;
+    const double gn = std::sqrt(gg), J = Jm + R;
+    if (g0n < 0.0) g0n = gn;
+    if (cfg->gtol > 0.0 && gn <= cfg->gtol * g0n) break;
+    const double eta = std::min(cfg->eta_max, std::sqrt(g0n > 0.0 ? gn / g0n : 0.0));
+
+    // CG on H x = -g from x = 0
+    NW_CK(cudaMemsetAsync(x, 0, g.C * sizeof(float), s));
+    if ((rc = op.axpby(-1.f, g_tot, 0.f, g_tot, res))) return rc;
+    if ((rc = op.copy(res, d))) return rc;
+    double rr = gg;
+    int k = 0;
+    for (k = 1; k <= cfg->cg_max; ++k) {
+      if ((rc = hess(d, Hd))) return rc;
+      double dHd = 0.0;
+      if ((rc = op.dot(d, Hd, &dHd))) return rc;
+      if (!(dHd > 0.0)) {   // negative (or no) curvature: keep the current iterate
+        --k;
+        break;
+      }
+      const double a = rr / dHd;
+      if ((rc = op.axpby((float)a, d, 1.f, x, x))) return rc;
+      if ((rc = op.axpby((float)-a, Hd, 1.f, res, res))) return rc;
+      double rr_new = 0.0;
+      if ((rc = op.dot(res, res, &rr_new))) return rc;
+      if (std::sqrt(rr_new) <= eta * gn) break;
+      if ((rc = op.axpby(1.f, res, (float)(rr_new / rr), d, d))) return rc;
+      rr = rr_new;
+    }
+    if (k > cfg->cg_max) k = cfg->cg_max;
+    if (k == 0 && (rc = op.axpby(-1.f, g_tot, 0.f, g_tot, x))) return rc;   // steepest descent
+    double slope = 0.0;
+    if ((rc = op.dot(g_tot, x, &slope))) return rc;
+
+    // Armijo backtracking; each trial's gradient stops after its forward solve if the
+    // misfit already fails the test
+    double step = 1.0, Jm_t = 0.0;
+    int bt = 0;
+    bool accepted = false;
+    for (; bt < cfg->max_backtracks; ++bt) {
+      if ((rc = op.axpby((float)step, x, 1.f, c_dev, ct))) return rc;
+      double Rt = 0.0;
+      if ((rc = reg(ct, &Rt, nullptr))) return rc;
+      const double gate = J + cfg->c1 * step * slope - Rt;
+      if ((rc = aew::gradient_gated(h, ct, d_obs_dev, gm, gate, &Jm_t, &accepted, s))) return rc;
+      if (accepted) break;
+      step *= 0.5;
+    }
+    if (!accepted) {   // no trial passed: take the smallest step
+      if ((rc = op.axpby((float)step, x, 1.f, c_dev, ct))) return rc;
+      if ((rc = aew::gradient_gated(h, ct, d_obs_dev, gm, INFINITY, &Jm_t, &ok, s))) return rc;
+    }
+    if ((rc = op.copy(ct, c_dev))) return rc;
+    Jm = Jm_t;
+    if (hist_host) hist_host[it] = aew_newton_iter{J, J - R, R, gn, k, bt, step};
+    if (iters_host) *iters_host = it + 1;
+  }
+  NW_CK(cudaStreamSynchronize(s));
+  return AEW_OK;
+}
+
+int aew_dias_subspace(aew_handle* h, const float* c_dev, const float* d_obs_dev,
+                      const float* noise_dev, int N, double alpha, double theta, int r,
+                      float* G_dev, float* W1_dev, double* lambda_host, void* stream) {
+  if (!h) return AEW_E_ARG;
+  if (!c_dev || !noise_dev || !G_dev || !W1_dev || !lambda_host)
+    return set_error(h, AEW_E_ARG, "NULL argument");
+  if (N < 1 || N > aew::kMaxN || r < 1 || r > N || r > aew::kMaxR)
+    return set_error(h, AEW_E_ARG, "need 1 <= r <= N <= 64 and r <= 32");
+  int rc = aew::prior_args_ok(h, alpha, theta);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const aew::GridInfo gi = aew::grid_of(h);
+  const Grid g{gi.nx, gi.ny, gi.nz, gi.C};
+  aew::Work ws;
+  float *cs, *coef;
+  double *part, *M;
+  const int npair = N * (N + 1) / 2;
+  const int gb = aew::vec_grid(g.C);
+  if (!ws.alloc(&cs, g.C) || !ws.alloc(&coef, (size_t)N * r) ||
+      !ws.alloc(&part, (size_t)gb * npair) || !ws.alloc(&M, (size_t)N * N))
+    return set_error(h, AEW_E_NOMEM, "DIAS: work vectors do not fit");
+  aew::Ops op{h, g, s, nullptr, nullptr, {}};
+  // CG iterations for rtol 1e-6 grow with sqrt of A's condition number
+  const double kappa = 1.0 + 12.0 * theta / (gi.h * gi.h);
+  const int max_iter = (int)std::min(100000.0, 1000.0 + 40.0 * std::sqrt(kappa));
+  for (int i = 0; i < N; ++i) {
+    float* gi_dev = G_dev + (size_t)i * g.C;
+    if ((rc = aew::prior_cg(h, g, gi.h, alpha, theta, noise_dev + (size_t)i * g.C, cs, 1e-6,
+                            max_iter, nullptr, s)))
+      return rc;
+    if ((rc = op.axpby(1.f, c_dev, 1.f, cs, cs))) return rc;
+    double J = 0.0;
+    bool ok = true;
+    if ((rc = aew::gradient_gated(h, cs, d_obs_dev, gi_dev, INFINITY, &J, &ok, s))) return rc;
+  }
+  aew::gram_kernel<<<gb, aew::NT, 0, s>>>(G_dev, N, g.C, part);
+  aew::gram_sum_kernel<<<(npair + aew::NT - 1) / aew::NT, aew::NT, 0, s>>>(part, gb, N, 1.0 / N, M);
+  NW_CK(cudaGetLastError());
+  std::vector<double> Mh((size_t)N * N), V((size_t)N * N), w(N);
+  NW_CK(cudaMemcpyAsync(Mh.data(), M, Mh.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  NW_CK(cudaStreamSynchronize(s));
+  if (!aew::sym_eig(N, Mh.data(), w.data(), V.data()))
+    return set_error(h, AEW_E_ARG, "DIAS: eigensolver did not converge");
+  for (int j = 0; j < N; ++j) lambda_host[j] = w[j];
+  if (!(w[r - 1] > 0.0)) return set_error(h, AEW_E_ARG, "DIAS: fewer than r positive eigenvalues");
+  std::vector<float> ch((size_t)N * r);
+  for (int j = 0; j < N; ++j)
+    for (int k = 0; k < r; ++k)
+      ch[(size_t)j * r + k] = (float)(V[(size_t)j * N + k] / std::sqrt(N * w[k]));
+  NW_CK(cudaMemcpyAsync(coef, ch.data(), ch.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+  aew::combine_kernel<<<gb, aew::NT, 0, s>>>(G_dev, N, g.C, coef, r, W1_dev);
+  NW_CK(cudaGetLastError());
+  NW_CK(cudaStreamSynchronize(s));
+  return AEW_OK;
+}
+
+}  // extern "C"

@@ -17,7 +17,9 @@ and data are not available):
 * receivers: a regular grid on the top face (node plane k = 1), which records the
   velocity (Sec. 2, the parameter-to-observable map F = B A);
 * source: a point force on the z-face of the centre node (Sec. 4.1 uses a Ricker
-  wavelet in time with direction [0, 0, -1]).
+  wavelet in time with direction [0, 0, -1]);
+* prior samples (MAP / DIAS): white noise w ~ N(0, I) per node, which the prior's
+  elliptic operator maps to a sample A^{-1} w.
 """
 from __future__ import annotations
 
@@ -34,6 +36,8 @@ __all__ = [
     "codec_init",
     "random_latents",
     "smooth_state",
+    "white_noise",
+    "orthonormal_rows",
 ]
 
 
@@ -167,3 +171,16 @@ def smooth_state(shape, h: float = 10.0, seed: int = 0, corr_len: float = 40.0) 
     for f in range(4):
         out[f] = scales[f] * gaussian_random_field(shape, h, corr_len, seed * 7 + f)
     return out
+
+
+def white_noise(n: int, shape, seed: int) -> np.ndarray:
+    """n white-noise fields N(0, 1), float32 [n][nz][ny][nx]."""
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((n,) + tuple(shape)).astype(np.float32)
+
+
+def orthonormal_rows(r: int, n: int, seed: int) -> np.ndarray:
+    """r orthonormal rows of length n (a random subspace), float64 [r][n]."""
+    rng = np.random.default_rng(seed)
+    q, _ = np.linalg.qr(rng.standard_normal((n, r)))
+    return np.ascontiguousarray(q.T)
