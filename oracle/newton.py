@@ -17,8 +17,10 @@ samples q0 + A^{-1} w, w white noise) are exact here.
 MAP (Sec. 2): minimise J(q) = misfit(q) + R(q) by inexact Newton-CG: each Newton step
 solves (H_misfit + A^2) p = -g by conjugate gradients, stopped at a relative residual
 eta = min(eta_max, sqrt(|g| / |g_0|)) (Eisenstat-Walker, eta_max = 0.5), then an Armijo backtracking line
-search (c1 = 1e-4, step halved).  H_misfit is the Gauss-Newton Hessian (or the full
-one).
+search (c1 = 1e-4, step halved).  A trial point outside the wave solver's stability
+bound (c dt / h > 1/sqrt(3), or c <= 0 anywhere) fails the test like a cost increase.  If
+no trial passes, the step is not taken and the iteration stops.  H_misfit is the
+Gauss-Newton Hessian (or the full one).
 
 DIAS-F (Sec. 4.3): the active subspace of C = (1/N) sum_i grad f(q_i) grad f(q_i)^T
 over N gradient samples at q_i = q_MAP + A^{-1} w_i (the two-step algorithm: centred at
@@ -112,6 +114,12 @@ class NewtonCfg:
     eta_max: float = 0.5           # cap of the Eisenstat-Walker forcing term
 
 
+def stable(p: W.Problem, q) -> bool:
+    """q is a wave speed the leapfrog scheme can run: positive, and max q dt / h within
+    the 3-D stability bound 1/sqrt(3)."""
+    return bool(np.all(q > 0) and q.max() * p.dt / p.h <= 1.0 / np.sqrt(3.0))
+
+
 def cost(p: W.Problem, q, d_obs, q0, cfg: NewtonCfg, proj=None) -> float:
     d, _, _ = W.forward(p, q)
     return W.misfit(d, d_obs) + regularisation(q, q0, p.h, cfg.alpha, cfg.theta, proj)
@@ -119,7 +127,8 @@ def cost(p: W.Problem, q, d_obs, q0, cfg: NewtonCfg, proj=None) -> float:
 
 def newton_cg(p: W.Problem, q: np.ndarray, d_obs, q0, cfg: NewtonCfg, proj=None):
     """Inexact Newton-CG (see the module docstring); returns (q, history) with one entry
-    (cost, |g|, cg iterations, step length) per Newton iteration."""
+    (cost, |g|, cg iterations, step length) per Newton iteration (step 0: the line search
+    found no acceptable step and the iteration stopped)."""
     q = np.array(q, dtype=np.float64)
     hist = []
     g0n = None
@@ -163,10 +172,16 @@ def newton_cg(p: W.Problem, q: np.ndarray, d_obs, q0, cfg: NewtonCfg, proj=None)
         # Armijo backtracking
         slope = float(np.sum(g * x))
         step = 1.0
+        accepted = False
         for _ in range(cfg.max_backtracks):
-            if cost(p, q + step * x, d_obs, q0, cfg, proj) <= J + cfg.c1 * step * slope:
+            qt = q + step * x
+            if stable(p, qt) and cost(p, qt, d_obs, q0, cfg, proj) <= J + cfg.c1 * step * slope:
+                accepted = True
                 break
             step *= 0.5
+        if not accepted:        # no sufficient decrease along x: stop where we are
+            hist.append((J, gn, k, 0.0))
+            break
         q = q + step * x
         hist.append((J, gn, k, step))
     return q, hist

@@ -122,3 +122,23 @@ def test_active_subspace_matches_a_dense_eigendecomposition():
     np.testing.assert_allclose(lam, ev[::-1][:4], rtol=1e-10)
     np.testing.assert_allclose(W1 @ W1.T, np.eye(4), atol=1e-10)
     np.testing.assert_allclose(W1.T @ W1, V[:, ::-1][:, :4] @ V[:, ::-1][:, :4].T, atol=1e-10)
+
+
+def test_stability_bound_and_a_failed_line_search():
+    prob, d_obs, q0 = _map_problem()
+    bound = (1.0 / np.sqrt(3.0)) * prob.h / prob.dt
+    q = np.full(prob.shape, 2000.0)
+    assert NW.stable(prob, q)
+    q[3, 4, 5] = bound
+    assert NW.stable(prob, q)
+    q[3, 4, 5] = bound * (1 + 1e-12)
+    assert not NW.stable(prob, q)
+    q[3, 4, 5] = 0.0
+    assert not NW.stable(prob, q)
+    # c1 near 1 asks for the linear model's whole decrease, which a Newton step on a
+    # curved cost does not give: no trial passes, nothing moves, the iteration stops
+    cfg = NW.NewtonCfg(alpha=1e-10, theta=6400.0, newton_iters=3, cg_max=5, c1=0.999999,
+                       max_backtracks=1)
+    q, hist = NW.newton_cg(prob, q0, d_obs, q0, cfg)
+    assert len(hist) == 1 and hist[0][3] == 0.0
+    np.testing.assert_array_equal(q, q0)
