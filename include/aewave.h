@@ -523,8 +523,9 @@ int aew_prior_solve(aew_handle* h, double alpha, double theta, const float* w_de
  * max_backtracks times, J(c + s p) <= J(c) + c1 s g^T p).  Each trial point runs the
  * gradient solve, whose adjoint half is skipped when the trial's misfit already fails
  * the Armijo test -- so an accepted trial already holds the next iterate's gradient
- * and history (with revolve storage the adjoint always runs).  If no trial passes, the
- * smallest step is taken.
+ * and history (with revolve storage the adjoint always runs).  A trial outside the
+ * stability bound (max c dt / h > 1/sqrt(3)) or with c <= 0 fails the test.  If no
+ * trial passes, c stays, the iteration is recorded with step 0 and the call returns.
  *   c_dev        in: the initial iterate; out: the final one [nz][ny][nx]
  *   d_obs_dev    [nt+1][nrec][3]
  *   c0_dev       prior mean [nz][ny][nx]
@@ -532,8 +533,8 @@ int aew_prior_solve(aew_handle* h, double alpha, double theta, const float* w_de
  *   hist_host    newton_iters entries (may be NULL); *iters_host (may be NULL) receives
  *                the iterations recorded (fewer than newton_iters when gtol stopped it)
  * Allocates nine FP32 work vectors for the call and frees them on return.  Returns the
- * errors of aew_gradient / aew_hessvec(_full) (for example AEW_E_CFL if a trial point
- * leaves the stability bound), AEW_E_ARG for bad arguments, AEW_E_NOMEM. */
+ * errors of aew_gradient / aew_hessvec(_full) (AEW_E_CFL if the initial c leaves the
+ * stability bound), AEW_E_ARG for bad arguments, AEW_E_NOMEM. */
 int aew_newton_cg(aew_handle* h, float* c_dev, const float* d_obs_dev, const float* c0_dev,
                   const aew_newton_cfg* cfg, const float* W1_dev, int r,
                   aew_newton_iter* hist_host, int* iters_host, void* stream);

@@ -557,7 +557,8 @@ int aew_newton_cg(aew_handle* h, float* c_dev, const float* d_obs_dev, const flo
     if ((rc = op.dot(g_tot, x, &slope))) return rc;
 
     // Armijo backtracking; each trial's gradient stops after its forward solve if the
-    // misfit already fails the test
+    // misfit already fails the test.  A trial outside the stability bound (or with
+    // c <= 0) fails like a cost increase.
     double step = 1.0, Jm_t = 0.0;
     int bt = 0;
     bool accepted = false;
@@ -566,19 +567,26 @@ int aew_newton_cg(aew_handle* h, float* c_dev, const float* d_obs_dev, const flo
       double Rt = 0.0;
       if ((rc = reg(ct, &Rt, nullptr))) return rc;
       const double gate = J + cfg->c1 * step * slope - Rt;
-      if ((rc = aew::gradient_gated(h, ct, d_obs_dev, gm, gate, &Jm_t, &accepted, s))) return rc;
+      rc = aew::gradient_gated(h, ct, d_obs_dev, gm, gate, &Jm_t, &accepted, s);
+      if (rc == AEW_E_CFL || rc == AEW_E_CONFIG) {
+        accepted = false;
+        rc = AEW_OK;
+      }
+      if (rc) return rc;
       if (accepted) break;
       step *= 0.5;
     }
-    if (!accepted) {   // no trial passed: take the smallest step
-      if ((rc = op.axpby((float)step, x, 1.f, c_dev, ct))) return rc;
-      if ((rc = aew::gradient_gated(h, ct, d_obs_dev, gm, INFINITY, &Jm_t, &ok, s))) return rc;
+    if (!accepted) {   // no sufficient decrease along x: stop at the current iterate
+      if (hist_host) hist_host[it] = aew_newton_iter{J, J - R, R, gn, k, bt, 0.0};
+      if (iters_host) *iters_host = it + 1;
+      break;
     }
     if ((rc = op.copy(ct, c_dev))) return rc;
     Jm = Jm_t;
     if (hist_host) hist_host[it] = aew_newton_iter{J, J - R, R, gn, k, bt, step};
     if (iters_host) *iters_host = it + 1;
   }
+  aew::set_error(h, AEW_OK, "");
   NW_CK(cudaStreamSynchronize(s));
   return AEW_OK;
 }
