@@ -57,6 +57,7 @@ class Problem:
     cfl: float = 0.5
     cmax: float = 3000.0    # dt = cfl h / cmax
     src: tuple = None       # source node (i, j, k); force on its z-face
+    src_sigma: float = 0.0  # Gaussian smoothing of the source in space [m] (0: point)
     f0: float = 25.0        # Ricker peak frequency [Hz]
     t0: Optional[float] = None   # Ricker centre time, default 1/f0
     rec: np.ndarray = field(default=None)   # int [nrec][3] of (i, j, k)
@@ -159,6 +160,22 @@ def _sample(p: Problem, vx, vy, vz) -> np.ndarray:
     return np.stack([vx[k, j, i], vy[k, j, i], vz[k, j, i]], axis=1)
 
 
+def source_weights(p: Problem):
+    """The source's spatial weights on the z-faces (Sec. 4.1's box problem smooths the
+    source by a narrow Gaussian in space).  Returns (R, w): the faces (i + a, j + b,
+    k + c + 1/2) for |a|, |b|, |c| <= R around the source face (i, j, k + 1/2) get
+    w[c + R][b + R][a + R] proportional to exp(-r^2 / (2 sigma^2)), r the distance
+    between the face centres, normalised to sum 1 (so that sigma -> 0 is the point
+    source); R = ceil(3 sigma / h).  A point source is R = 0, w = [[[1]]]."""
+    if p.src_sigma <= 0.0:
+        return 0, np.ones((1, 1, 1))
+    R = int(math.ceil(3.0 * p.src_sigma / p.h))
+    o = np.arange(-R, R + 1) * p.h
+    r2 = o[:, None, None] ** 2 + o[None, :, None] ** 2 + o[None, None, :] ** 2
+    w = np.exp(-r2 / (2.0 * p.src_sigma ** 2))
+    return R, w / w.sum()
+
+
 def forward_step(p: Problem, m, e, vx, vy, vz, s_n: float):
     """One leapfrog step (see module docstring); returns the new (e, vx, vy, vz)."""
     dt, h = p.dt, p.h
@@ -167,7 +184,8 @@ def forward_step(p: Problem, m, e, vx, vy, vz, s_n: float):
     vy = vy + dt * gy
     vz = vz + dt * gz
     i, j, k = p.src
-    vz[k, j, i] += dt * s_n
+    R, w = source_weights(p)
+    vz[k - R:k + R + 1, j - R:j + R + 1, i - R:i + R + 1] += dt * s_n * w
     e = interior(e + dt * div_op(vx, vy, vz, h))
     return e, vx, vy, vz
 
@@ -231,6 +249,7 @@ def adjoint(p: Problem, c: np.ndarray, e_of: Callable[[int], np.ndarray],
     sgrad = np.zeros(p.nt)
     ri, rj, rk = p.rec[:, 0], p.rec[:, 1], p.rec[:, 2]
     si, sj, sk = p.src
+    R, w_src = source_weights(p)
     for n in range(p.nt - 1, -1, -1):
         r = resid[n + 1]
         np.add.at(lx, (rk, rj, ri), r[:, 0])
@@ -243,7 +262,8 @@ def adjoint(p: Problem, c: np.ndarray, e_of: Callable[[int], np.ndarray],
         q = grad_op_T(lx, ly, lz, h)
         mbar += dt * e_of(n) * q
         mu = interior(mu + dt * m * q)
-        sgrad[n] = dt * lz[sk, sj, si]
+        sgrad[n] = dt * float(np.sum(w_src * lz[sk - R:sk + R + 1, sj - R:sj + R + 1,
+                                                 si - R:si + R + 1]))
     if want_source_grad:
         return mbar, sgrad
     return mbar

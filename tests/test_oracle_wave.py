@@ -313,3 +313,61 @@ def test_incremental_strain_history_matches_the_jacobian_product():
     n = 40
     fd = (sp[n][0] - sm[n][0]) / (2 * eps)
     assert np.linalg.norm(fd - hist[n]) <= 1e-6 * np.linalg.norm(hist[n])
+
+
+# ------------------------------------------------------------------ smoothed source
+def test_source_weights_are_a_normalised_symmetric_gaussian():
+    prob = _problem(n=16, nt=4)
+    prob.src_sigma = 20.0
+    R, w = W.source_weights(prob)
+    assert R == 6 and w.shape == (13, 13, 13)
+    assert abs(w.sum() - 1.0) < 1e-14
+    np.testing.assert_allclose(w, w[::-1], atol=0)
+    np.testing.assert_allclose(w, w.transpose(2, 1, 0), atol=1e-18)
+    # the ratio of neighbouring weights along an axis is exp(-(2a + 1) h^2 / (2 sigma^2))
+    a = 2
+    ratio = w[R, R, R + a + 1] / w[R, R, R + a]
+    assert ratio == pytest.approx(np.exp(-(2 * a + 1) * prob.h ** 2 / (2 * 20.0 ** 2)), rel=1e-12)
+
+
+def test_smoothed_source_is_the_weighted_sum_of_point_sources():
+    # the wave equation is linear in the source: a source spread over the 125 faces of a
+    # two-face box gives the weighted sum of 125 point-source solves, face by face
+    prob = _problem(n=16, nt=30)
+    prob.src_sigma = 4.0
+    c = inputs.velocity_model(prob.shape, prob.h, seed=0)
+    R, w = W.source_weights(prob)
+    assert R == 2
+    d_s, (e_s, *_), _ = W.forward(prob, c)
+    i, j, k = prob.src
+    d_sum = np.zeros_like(d_s)
+    e_sum = np.zeros(prob.shape)
+    for cz in range(-R, R + 1):
+        for by in range(-R, R + 1):
+            for ax in range(-R, R + 1):
+                q = W.Problem(shape=prob.shape, h=prob.h, nt=prob.nt, rec=prob.rec,
+                              src=(i + ax, j + by, k + cz))
+                d_p, (e_p, *_), _ = W.forward(q, c)
+                d_sum += w[cz + R, by + R, ax + R] * d_p
+                e_sum += w[cz + R, by + R, ax + R] * e_p
+    np.testing.assert_allclose(d_s, d_sum, rtol=0, atol=1e-12 * np.abs(d_s).max())
+    np.testing.assert_allclose(e_s, e_sum, rtol=0, atol=1e-12 * np.abs(e_s).max())
+
+
+def test_smoothed_source_adjoint_identity_and_point_limit():
+    prob = _problem(n=16, nt=60)
+    prob.src_sigma = 15.0
+    c = inputs.velocity_model(prob.shape, prob.h, seed=0)
+    rng = np.random.default_rng(2)
+    w = rng.standard_normal(prob.nt)
+    r = rng.standard_normal((prob.nt + 1, prob.nrec, 3)); r[0] = 0
+    d, _, states = W.forward(prob, c, wavelet=w, keep_states=True)
+    _, sgrad = W.adjoint(prob, c, lambda n: states[n][0], r, want_source_grad=True)
+    lhs = float(np.sum(d[1:] * r[1:]))
+    assert abs(lhs - float(np.dot(w, sgrad))) <= 1e-12 * abs(lhs)
+    # a very narrow Gaussian is the point source
+    prob.src_sigma = 1.0
+    d1, _, _ = W.forward(prob, c)
+    prob.src_sigma = 0.0
+    d0, _, _ = W.forward(prob, c)
+    np.testing.assert_allclose(d1, d0, rtol=0, atol=1e-14 * np.abs(d0).max())
