@@ -35,37 +35,43 @@ namespace aew {
 
 namespace {
 
-__global__ void transpose_to16_kernel(const float* __restrict__ src, int rows, int cols,
-                                      uint16_t* __restrict__ dst, int fp16) {
-  // dst[c][r] = round(src[r][c])
+// the four weight transposes of codec_refresh in one launch: a block takes one 32 x 32
+// tile of one matrix (tile prefix per matrix)
+struct Transposes {
+  const float* src[4];
+  uint16_t* dst[4];
+  int rows[4], cols[4], fp16[4];
+  int tiles[5];
+};
+__global__ void transpose_multi_kernel(Transposes t) {
   __shared__ float tile[32][33];
-  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  int m = 0;
+  while (m < 3 && (int)blockIdx.x >= t.tiles[m + 1]) ++m;
+  const int rows = t.rows[m], cols = t.cols[m];
+  const int tx = (cols + 31) / 32;
+  const int b = blockIdx.x - t.tiles[m];
+  const int c0 = (b % tx) * 32, r0 = (b / tx) * 32;
+  const float* src = t.src[m];
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
     const int r = r0 + i, c = c0 + threadIdx.x;
     tile[i][threadIdx.x] = (r < rows && c < cols) ? src[(size_t)r * cols + c] : 0.f;
   }
   __syncthreads();
+  uint16_t* dst = t.dst[m];
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
     const int c = c0 + i, r = r0 + threadIdx.x;
     if (c < cols && r < rows) {
       const float v = tile[threadIdx.x][i];
-      uint16_t b;
-      if (fp16) {
+      uint16_t bits;
+      if (t.fp16[m]) {
         __half hv = __float2half_rn(v);
-        b = *reinterpret_cast<uint16_t*>(&hv);
+        bits = *reinterpret_cast<uint16_t*>(&hv);
       } else {
-        b = gemm::bf16_bits(v);
+        bits = gemm::bf16_bits(v);
       }
-      dst[(size_t)c * rows + r] = b;
+      dst[(size_t)c * rows + r] = bits;
     }
   }
-}
-
-cudaError_t transpose16(const float* src, int rows, int cols, uint16_t* dst, bool fp16,
-                        cudaStream_t s) {
-  dim3 grid((cols + 31) / 32, (rows + 31) / 32), block(32, 8);
-  transpose_to16_kernel<<<grid, block, 0, s>>>(src, rows, cols, dst, fp16 ? 1 : 0);
-  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------------
@@ -750,10 +756,12 @@ bool codec_ready(const Codec* c) { return c && c->ready; }
 cudaError_t codec_refresh(Codec* c, cudaStream_t s) {
   const int nl = c->n_lat, nh = c->n_hid;
   cudaError_t e;
-  if ((e = transpose16(c->w[0], kNIn, nh, c->W1t, false, s)) != cudaSuccess) return e;
-  if ((e = transpose16(c->w[2], nh, nl, c->W2t, false, s)) != cudaSuccess) return e;
-  if ((e = transpose16(c->w[4], nl, nh, c->W3t, true, s)) != cudaSuccess) return e;
-  if ((e = transpose16(c->w[6], nh, kNIn, c->W4t, false, s)) != cudaSuccess) return e;
+  Transposes t{{c->w[0], c->w[2], c->w[4], c->w[6]}, {c->W1t, c->W2t, c->W3t, c->W4t},
+               {kNIn, nh, nl, nh}, {nh, nl, nh, kNIn}, {0, 0, 1, 0}, {0, 0, 0, 0, 0}};
+  for (int m = 0; m < 4; ++m)
+    t.tiles[m + 1] = t.tiles[m] + ((t.rows[m] + 31) / 32) * ((t.cols[m] + 31) / 32);
+  transpose_multi_kernel<<<t.tiles[4], dim3(32, 8), 0, s>>>(t);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (c->time) return cudaSuccess;
   strain_rows_kernel<<<512, 128, 0, s>>>(c->W4t, c->W4e);
   return cudaGetLastError();

@@ -11,7 +11,9 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <string>
 
 #include "aew_codec.cuh"
@@ -166,28 +168,33 @@ struct EpMse {
   double* loss;
   float scale;
   long long M;
+  // called by all 32 lanes of a warp together (rows m0 + 32 q + lane): the loss is
+  // reduced across the warp before its one atomic
   __device__ __forceinline__ void operator()(long long row, int col, const float (&v)[32]) const {
-    if (row >= M) return;
-    // the 32 columns lie in one field's 64-column group: one weight
-    const float wf = w ? __ldg(w + row * 4 + ((col >> 6) & 3)) : 1.f;
     double acc = 0.0;
-    uint32_t pk[16];
-    float dd[32];
+    if (row < M) {
+      // the 32 columns lie in one field's 64-column group: one weight
+      const float wf = w ? __ldg(w + row * 4 + ((col >> 6) & 3)) : 1.f;
+      uint32_t pk[16];
+      float dd[32];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      const float a = v[j] + __ldg(bias + col + j);
-      const float diff = a - gemm::bf16_val(__ldg(Y + row * kNIn + col + j));
-      acc += (double)wf * (double)diff * (double)diff;
-      dd[j] = scale * wf * diff;
-      d4T[(size_t)(col + j) * M + row] = gemm::bf16_bits(dd[j]);
+      for (int j = 0; j < 32; ++j) {
+        const float a = v[j] + __ldg(bias + col + j);
+        const float diff = a - gemm::bf16_val(__ldg(Y + row * kNIn + col + j));
+        acc += (double)wf * (double)diff * (double)diff;
+        dd[j] = scale * wf * diff;
+        d4T[(size_t)(col + j) * M + row] = gemm::bf16_bits(dd[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < 32; j += 2) pk[j / 2] = gemm::pack_bf16(dd[j], dd[j + 1]);
+      float4* pd = reinterpret_cast<float4*>(d4 + row * kNIn + col);
+#pragma unroll
+      for (int j = 0; j < 32; j += 4) pd[j / 4] = make_float4(dd[j], dd[j + 1], dd[j + 2], dd[j + 3]);
+      store_row16(d4b + row * kNIn + col, pk);
     }
 #pragma unroll
-    for (int j = 0; j < 32; j += 2) pk[j / 2] = gemm::pack_bf16(dd[j], dd[j + 1]);
-    float4* pd = reinterpret_cast<float4*>(d4 + row * kNIn + col);
-#pragma unroll
-    for (int j = 0; j < 32; j += 4) pd[j / 4] = make_float4(dd[j], dd[j + 1], dd[j + 2], dd[j + 3]);
-    store_row16(d4b + row * kNIn + col, pk);
-    atomicAdd(loss, acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc);
   }
 };
 
@@ -252,15 +259,45 @@ __global__ void transpose16_kernel(const uint16_t* __restrict__ src, int rows, i
   }
 }
 
-__global__ void colsum_kernel(const float* __restrict__ d, int rows, int cols, float* __restrict__ out) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= cols) return;
-  double s = 0.0;
-  for (int r = 0; r < rows; ++r) s += d[(size_t)r * cols + c];
-  out[c] = (float)s;
+// bias gradients: the column sums of up to four [rows][cols] FP32 matrices in one
+// launch.  A block takes 32 columns of one matrix: lane = column (coalesced rows), the 8
+// warps split the rows, FP64 partials combined in a fixed order.
+struct ColSums {
+  const float* d[4];
+  float* out[4];
+  int cols[4];
+  int tiles[5];   // prefix of 32-column tiles per matrix
+  int n;
+};
+__global__ void colsum_multi_kernel(ColSums cs, int rows) {
+  __shared__ double part[8][33];
+  int m = 0;
+  while (m + 1 < cs.n && (int)blockIdx.x >= cs.tiles[m + 1]) ++m;
+  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+  const int c = (blockIdx.x - cs.tiles[m]) * 32 + lane;
+  const int cols = cs.cols[m];
+  double acc = 0.0;
+  if (c < cols)
+    for (int r = wq; r < rows; r += 8) acc += cs.d[m][(size_t)r * cols + c];
+  part[wq][lane] = acc;
+  __syncthreads();
+  if (wq == 0 && c < cols) {
+    double t = 0.0;
+    for (int q = 0; q < 8; ++q) t += part[q][lane];
+    cs.out[m][c] = (float)t;
+  }
 }
 
-__global__ void to_bf16_kernel(const float* __restrict__ w, size_t n, uint16_t* __restrict__ o) {
+// BF16 copies of up to three FP32 tensors in one launch (blockIdx.y = tensor)
+struct ToBf16 {
+  const float* w[3];
+  uint16_t* o[3];
+  size_t n[3];
+};
+__global__ void to_bf16_multi_kernel(ToBf16 t) {
+  const float* w = t.w[blockIdx.y];
+  uint16_t* o = t.o[blockIdx.y];
+  const size_t n = t.n[blockIdx.y];
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     o[i] = gemm::bf16_bits(w[i]);
 }
@@ -361,39 +398,95 @@ __global__ void weight_strain_kernel(long long n, float* __restrict__ w) {
     reinterpret_cast<float4*>(w)[v] = make_float4(1.f, 0.f, 0.f, 0.f);
 }
 
-// LAMB pass 1: moments, u (written over g), partial norms |w|^2 and |u|^2
-__global__ void lamb1_kernel(const float* __restrict__ w, float* __restrict__ g, float* __restrict__ m,
-                             float* __restrict__ v, size_t n, float b1, float b2, float c1, float c2,
-                             float eps, double* norms) {
-  double sw = 0.0, su = 0.0;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const float gi = g[i];
-    const float mi = b1 * m[i] + (1.f - b1) * gi;
-    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    const float u = (mi / c1) / (sqrtf(vi / c2) + eps);
-    g[i] = u;
-    sw += (double)w[i] * (double)w[i];
-    su += (double)u * (double)u;
-  }
+// LAMB over all eight parameter tensors in two launches.  Blocks are dealt to the
+// tensors in proportion to their sizes (prefix blk[]); a block reduces its norms in
+// shared memory and adds them with one FP64 atomic per tensor and norm.
+struct LambArgs {
+  float* w[8];
+  float* g[8];
+  float* m[8];
+  float* v[8];
+  size_t n[8];
+  int blk[9];
+};
+__device__ __forceinline__ int lamb_tensor(const LambArgs& a) {
+  int t = 0;
+  while (t < 7 && (int)blockIdx.x >= a.blk[t + 1]) ++t;
+  return t;
+}
+__device__ __forceinline__ void block_add2(double x, double y, double* dst) {
+  __shared__ double sx[8], sy[8];
+#pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    sw += __shfl_xor_sync(0xffffffffu, sw, o);
-    su += __shfl_xor_sync(0xffffffffu, su, o);
+    x += __shfl_xor_sync(0xffffffffu, x, o);
+    y += __shfl_xor_sync(0xffffffffu, y, o);
   }
   if ((threadIdx.x & 31) == 0) {
-    atomicAdd(norms, sw);
-    atomicAdd(norms + 1, su);
+    sx[threadIdx.x >> 5] = x;
+    sy[threadIdx.x >> 5] = y;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+      a += sx[q];
+      b += sy[q];
+    }
+    atomicAdd(dst, a);
+    atomicAdd(dst + 1, b);
   }
 }
 
-// LAMB pass 2: w -= lr * (|w| / |u|) * u
-__global__ void lamb2_kernel(float* __restrict__ w, const float* __restrict__ u, size_t n, float lr,
-                             const double* norms) {
-  const double wn = sqrt(norms[0]), un = sqrt(norms[1]);
+// pass 1: moments, u (written over g), norms |w|^2 and |u|^2 into norms[2 t], [2 t + 1]
+__global__ void lamb1_multi_kernel(LambArgs a, float b1, float b2, float c1, float c2, float eps,
+                                   double* norms) {
+  const int t = lamb_tensor(a);
+  const size_t n4 = a.n[t] / 4;
+  const int nb = a.blk[t + 1] - a.blk[t];
+  float4* w = reinterpret_cast<float4*>(a.w[t]);
+  float4* g = reinterpret_cast<float4*>(a.g[t]);
+  float4* m = reinterpret_cast<float4*>(a.m[t]);
+  float4* v = reinterpret_cast<float4*>(a.v[t]);
+  double sw = 0.0, su = 0.0;
+  for (size_t i = (size_t)(blockIdx.x - a.blk[t]) * blockDim.x + threadIdx.x; i < n4;
+       i += (size_t)nb * blockDim.x) {
+    const float4 gi = g[i], mi0 = m[i], vi0 = v[i], wi = w[i];
+    float gg[4] = {gi.x, gi.y, gi.z, gi.w}, mm[4] = {mi0.x, mi0.y, mi0.z, mi0.w};
+    float vv[4] = {vi0.x, vi0.y, vi0.z, vi0.w}, ww[4] = {wi.x, wi.y, wi.z, wi.w}, uu[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      mm[q] = b1 * mm[q] + (1.f - b1) * gg[q];
+      vv[q] = b2 * vv[q] + (1.f - b2) * gg[q] * gg[q];
+      uu[q] = (mm[q] / c1) / (sqrtf(vv[q] / c2) + eps);
+      sw += (double)ww[q] * (double)ww[q];
+      su += (double)uu[q] * (double)uu[q];
+    }
+    m[i] = make_float4(mm[0], mm[1], mm[2], mm[3]);
+    v[i] = make_float4(vv[0], vv[1], vv[2], vv[3]);
+    g[i] = make_float4(uu[0], uu[1], uu[2], uu[3]);
+  }
+  block_add2(sw, su, norms + 2 * t);
+}
+
+// pass 2: w -= lr * (|w| / |u|) * u
+__global__ void lamb2_multi_kernel(LambArgs a, float lr, const double* norms) {
+  const int t = lamb_tensor(a);
+  const size_t n4 = a.n[t] / 4;
+  const int nb = a.blk[t + 1] - a.blk[t];
+  const double wn = sqrt(norms[2 * t]), un = sqrt(norms[2 * t + 1]);
   const float r = (wn > 0.0 && un > 0.0) ? (float)(wn / un) : 1.f;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    w[i] -= lr * r * u[i];
+  float4* w = reinterpret_cast<float4*>(a.w[t]);
+  const float4* u = reinterpret_cast<const float4*>(a.g[t]);
+  for (size_t i = (size_t)(blockIdx.x - a.blk[t]) * blockDim.x + threadIdx.x; i < n4;
+       i += (size_t)nb * blockDim.x) {
+    float4 x = w[i];
+    const float4 y = u[i];
+    x.x -= lr * r * y.x;
+    x.y -= lr * r * y.y;
+    x.z -= lr * r * y.z;
+    x.w -= lr * r * y.w;
+    w[i] = x;
+  }
 }
 
 int nblk(size_t n) {
@@ -419,6 +512,30 @@ cudaError_t launch_nl(long long M, int N, int K, const gemm::Mat& A, const gemm:
                       const EP& ep, int* err, cudaStream_t st) {
   if (N <= 32) return gemm::launch<32, BF16>(M, N, K, A, B, ep, err, st);
   if (N <= 64) return gemm::launch<64, BF16>(M, N, K, A, B, ep, err, st);
+  return gemm::launch<256, BF16>(M, N, K, A, B, ep, err, st);
+}
+
+// a training GEMM (M rows of the batch or of a weight): the widest tile that still gives
+// every SM a tile, since one batch's products are too small to fill the GPU with
+// 128 x 256 tiles (AEW_TRAIN_BN = 64, 128 or 256 forces a width: tuning override)
+template <bool BF16, class EP>
+cudaError_t launch_t(long long M, int N, int K, const gemm::Mat& A, const gemm::Mat& B,
+                     const EP& ep, int* err, cudaStream_t st) {
+  static const int forced = [] {
+    const char* env = getenv("AEW_TRAIN_BN");   // tuning override
+    return env ? atoi(env) : 0;
+  }();
+  const long long mt = (M + 127) / 128;
+  const int sms = gemm::sm_count();
+  int bn = forced;
+  if (bn != 64 && bn != 128 && bn != 256) {
+    if (N < 128 || mt * ((N + 255) / 256) >= sms) bn = 256;
+    else if (mt * ((N + 127) / 128) >= sms || N < 256) bn = 128;
+    else bn = 64;
+  }
+  if (N <= 64) return launch_nl<BF16>(M, N, K, A, B, ep, err, st);
+  if (bn == 64) return gemm::launch<64, BF16>(M, N, K, A, B, ep, err, st);
+  if (bn == 128) return gemm::launch<128, BF16>(M, N, K, A, B, ep, err, st);
   return gemm::launch<256, BF16>(M, N, K, A, B, ep, err, st);
 }
 
@@ -452,45 +569,51 @@ cudaError_t codec_train_step(Codec* c, const uint16_t* Y, const float* wts, int 
   int* e = c->err;
   TCK(cudaMemsetAsync(s->red, 0, 32 * sizeof(double), st));
   // backward weight copies of the current masters
-  TCK((to_bf16_kernel<<<nblk((size_t)H * I), 256, 0, st>>>(c->w[6], (size_t)H * I, s->W4b), cudaGetLastError()));
-  TCK((to_bf16_kernel<<<nblk((size_t)nl * H), 256, 0, st>>>(c->w[4], (size_t)nl * H, s->W3b), cudaGetLastError()));
-  TCK((to_bf16_kernel<<<nblk((size_t)H * nl), 256, 0, st>>>(c->w[2], (size_t)H * nl, s->W2b), cudaGetLastError()));
+  {
+    const ToBf16 tb{{c->w[6], c->w[4], c->w[2]}, {s->W4b, s->W3b, s->W2b},
+                    {(size_t)H * I, (size_t)nl * H, (size_t)H * nl}};
+    to_bf16_multi_kernel<<<dim3(nblk((size_t)H * I), 3), 256, 0, st>>>(tb);
+    TCK(cudaGetLastError());
+  }
   {
     dim3 grid((I + 31) / 32, (B + 31) / 32), block(32, 8);
     transpose16_kernel<<<grid, block, 0, st>>>(Y, B, I, s->YT);
     TCK(cudaGetLastError());
   }
   // ---- forward
-  TCK((gemm::launch<256, true>(Bm, H, I, ld(Y, I, Bm, I), ld(c->W1t, I, H, I),
+  TCK((launch_t<true>(Bm, H, I, ld(Y, I, Bm, I), ld(c->W1t, I, H, I),
                                EpFwdGelu{c->w[1], s->a1, s->h1, s->h1T, H, Bm, c->act}, e, st)));
-  TCK((launch_nl<true>(Bm, nl, H, ld(s->h1, H, Bm, H), ld(c->W2t, H, nl, H),
+  TCK((launch_t<true>(Bm, nl, H, ld(s->h1, H, Bm, H), ld(c->W2t, H, nl, H),
                        EpFwdLatent{c->w[3], s->z16, s->zbT, nl, Bm}, e, st)));
-  TCK((gemm::launch<256, false>(Bm, H, nl, ld(s->z16, nl, Bm, nl), ld(c->W3t, nl, H, nl),
+  TCK((launch_t<false>(Bm, H, nl, ld(s->z16, nl, Bm, nl), ld(c->W3t, nl, H, nl),
                                 EpFwdGelu{c->w[5], s->a3, s->h3, s->h3T, H, Bm, c->act}, e, st)));
-  TCK((gemm::launch<256, true>(Bm, I, H, ld(s->h3, H, Bm, H), ld(c->W4t, H, I, H),
+  TCK((launch_t<true>(Bm, I, H, ld(s->h3, H, Bm, H), ld(c->W4t, H, I, H),
                                EpMse{c->w[7], Y, wts, s->d4, s->d4b, s->d4T, s->red,
                                      2.0f / (float)((double)B * I), Bm},
                                e, st)));
   // ---- backward
-  TCK((gemm::launch<256, true>((long long)H, I, B, ld(s->h3T, B, H, B), ld(s->d4T, B, I, B),
+  TCK((launch_t<true>((long long)H, I, B, ld(s->h3T, B, H, B), ld(s->d4T, B, I, B),
                                EpStore{s->g[6], I, H}, e, st)));
-  TCK((gemm::launch<256, true>(Bm, H, I, ld(s->d4b, I, Bm, I), ld(s->W4b, I, H, I),
+  TCK((launch_t<true>(Bm, H, I, ld(s->d4b, I, Bm, I), ld(s->W4b, I, H, I),
                                EpBack{s->a3, s->d3, s->d3b, s->d3T, H, Bm, c->act}, e, st)));
-  TCK((gemm::launch<256, true>((long long)nl, H, B, ld(s->zbT, B, nl, B), ld(s->d3T, B, H, B),
+  TCK((launch_t<true>((long long)nl, H, B, ld(s->zbT, B, nl, B), ld(s->d3T, B, H, B),
                                EpStore{s->g[4], H, nl}, e, st)));
-  TCK((launch_nl<true>(Bm, nl, H, ld(s->d3b, H, Bm, H), ld(s->W3b, H, nl, H),
+  TCK((launch_t<true>(Bm, nl, H, ld(s->d3b, H, Bm, H), ld(s->W3b, H, nl, H),
                        EpBack{nullptr, s->d2, s->d2b, s->d2T, nl, Bm, c->act}, e, st)));
-  TCK((launch_nl<true>((long long)H, nl, B, ld(s->h1T, B, H, B), ld(s->d2T, B, nl, B),
+  TCK((launch_t<true>((long long)H, nl, B, ld(s->h1T, B, H, B), ld(s->d2T, B, nl, B),
                        EpStore{s->g[2], nl, H}, e, st)));
-  TCK((gemm::launch<256, true>(Bm, H, nl, ld(s->d2b, nl, Bm, nl), ld(s->W2b, nl, H, nl),
+  TCK((launch_t<true>(Bm, H, nl, ld(s->d2b, nl, Bm, nl), ld(s->W2b, nl, H, nl),
                                EpBack{s->a1, s->d1, nullptr, s->d1T, H, Bm, c->act}, e, st)));
-  TCK((gemm::launch<256, true>((long long)I, H, B, ld(s->YT, B, I, B), ld(s->d1T, B, H, B),
+  TCK((launch_t<true>((long long)I, H, B, ld(s->YT, B, I, B), ld(s->d1T, B, H, B),
                                EpStore{s->g[0], H, I}, e, st)));
   // bias gradients
-  TCK((colsum_kernel<<<(H + 255) / 256, 256, 0, st>>>(s->d1, B, H, s->g[1]), cudaGetLastError()));
-  TCK((colsum_kernel<<<(nl + 255) / 256, 256, 0, st>>>(s->d2, B, nl, s->g[3]), cudaGetLastError()));
-  TCK((colsum_kernel<<<(H + 255) / 256, 256, 0, st>>>(s->d3, B, H, s->g[5]), cudaGetLastError()));
-  TCK((colsum_kernel<<<(I + 255) / 256, 256, 0, st>>>(s->d4, B, I, s->g[7]), cudaGetLastError()));
+  {
+    ColSums cs{{s->d1, s->d2, s->d3, s->d4}, {s->g[1], s->g[3], s->g[5], s->g[7]}, {H, nl, H, I},
+               {0, 0, 0, 0, 0}, 4};
+    for (int q = 0; q < 4; ++q) cs.tiles[q + 1] = cs.tiles[q] + (cs.cols[q] + 31) / 32;
+    colsum_multi_kernel<<<cs.tiles[4], 256, 0, st>>>(cs, B);
+    TCK(cudaGetLastError());
+  }
   if (loss_dev || loss_acc) {
     loss_kernel<<<1, 1, 0, st>>>(s->red, 1.0 / ((double)B * I), loss_dev, loss_acc);
     TCK(cudaGetLastError());
@@ -499,14 +622,27 @@ cudaError_t codec_train_step(Codec* c, const uint16_t* Y, const float* wts, int 
   s->t += 1;
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-6f;
   const float c1 = (float)(1.0 - std::pow(0.9, s->t)), c2 = (float)(1.0 - std::pow(0.999, s->t));
+  LambArgs la{};
+  size_t total = 0;
   for (int i = 0; i < 8; ++i) {
-    const size_t n = c->wn[i];
-    lamb1_kernel<<<nblk(n), 256, 0, st>>>(c->w[i], s->g[i], s->m[i], s->v[i], n, b1, b2, c1, c2, eps,
-                                          s->red + 1 + 2 * i);
-    TCK(cudaGetLastError());
-    lamb2_kernel<<<nblk(n), 256, 0, st>>>(c->w[i], s->g[i], n, lr, s->red + 1 + 2 * i);
-    TCK(cudaGetLastError());
+    la.w[i] = c->w[i];
+    la.g[i] = s->g[i];
+    la.m[i] = s->m[i];
+    la.v[i] = s->v[i];
+    la.n[i] = c->wn[i];
+    if (c->wn[i] % 4) return cudaErrorInvalidValue;   // float4 passes
+    total += c->wn[i];
   }
+  constexpr int kLambBlocks = 152 * 4;
+  la.blk[0] = 0;
+  for (int i = 0; i < 8; ++i) {
+    const int b = (int)std::max<size_t>(1, (size_t)((double)kLambBlocks * c->wn[i] / total + 0.5));
+    la.blk[i + 1] = la.blk[i] + b;
+  }
+  lamb1_multi_kernel<<<la.blk[8], 256, 0, st>>>(la, b1, b2, c1, c2, eps, s->red + 1);
+  TCK(cudaGetLastError());
+  lamb2_multi_kernel<<<la.blk[8], 256, 0, st>>>(la, lr, s->red + 1);
+  TCK(cudaGetLastError());
   return codec_refresh(c, st);
 }
 
