@@ -95,8 +95,10 @@ def parse():
     p.add_argument("--dias-rank", type=int, default=5)
     p.add_argument("--dias-iters", type=int, default=2)
     p.add_argument("--map-ref", default="full", choices=["full", "none"])
-    p.add_argument("--map-cmax", type=float, default=4000.0,
+    p.add_argument("--map-cmax", type=float, default=3000.0,
                    help="MAP / DIAS: the speed that sets dt (stability bound 1.155 x this)")
+    p.add_argument("--src-sigma", type=float, default=50.0,
+                   help="MAP / DIAS: source smoothing in space [m] (Sec. 4.1's box problem: 50 m)")
     p.add_argument("--train-step", action="store_true",
                    help="time codec training steps (Table 2's batch) alone")
     p.add_argument("--batch", type=int, default=512)
@@ -708,12 +710,11 @@ def run_map(args):
     rms of the data) and a prior with sample std prior-std [m/s] make the objective, times
     sigma_n^2, 1/2 |d - d_obs|^2 + 1/2 |alpha_reg A_1 (c - c0)|^2 with
     alpha_reg = sigma_n alpha_s (A_1: the operator at alpha = 1).  alpha_s is measured:
-    the std of a sample A_1^{-1} w scales as 1 / alpha.  dt is set by --map-cmax
-    (4000 m/s): the point source makes the misfit's sensitivity singular at the source
-    node, Newton steps grow the speed there, and Newton trial points and prior samples
-    around the MAP point need room below the stability bound.  Errors against the true
-    model are reported over all nodes (the paper's average relative error), inside the
-    bump and outside it."""
+    the std of a sample A_1^{-1} w scales as 1 / alpha.  The source is smoothed by a
+    Gaussian of --src-sigma (50 m, as in Sec. 4.1's box problem): a point source makes
+    the misfit's sensitivity singular at its node, where Newton steps then grow the
+    speed up to the stability bound.  Errors against the true model are reported over
+    all nodes (the paper's average relative error), inside the bump and outside it."""
     import torch
     from paper_2304_04781_gb300 import aewave, inputs
     shape, nt = tuple(args.shape), args.nt
@@ -736,7 +737,8 @@ def run_map(args):
         return {"all": float(e.mean()), "bump": float(e[bump].mean()), "rest": float(e[~bump].mean())}
 
     ae = aewave.Solver(shape, H, nt, rec, storage="ae", codec=args.codec, n_lat=n_lat, f0=args.f0,
-                       norm=args.norm, act=args.act, beta=args.beta, cmax=args.map_cmax)
+                       norm=args.norm, act=args.act, beta=args.beta, cmax=args.map_cmax,
+                       src_sigma=args.src_sigma)
     ae.codec_set(W)
     d_obs = ae.forward(ctrue)
     w = torch.from_numpy(inputs.white_noise(1, shape, seed=77)[0]).cuda()
@@ -747,7 +749,8 @@ def run_map(args):
     sigma_n = args.noise_rel * float(d_obs[1:].double().pow(2).mean().sqrt())
     alpha = alpha_s * sigma_n
     out = {"config": dict(workload(shape, nt, args.nrec, n_lat, args.codec), f0_hz=args.f0,
-                          norm=args.norm, act=args.act, dt_cmax=args.map_cmax, dt_s=ae.dt),
+                          norm=args.norm, act=args.act, dt_cmax=args.map_cmax, dt_s=ae.dt,
+                          src_sigma_m=args.src_sigma),
            "codec_weights": "trained" if trained else "random-init",
            "prior": {"theta_m2": theta, "sample_std": args.prior_std, "alpha_s": alpha_s,
                      "noise_rel": args.noise_rel, "sigma_n": sigma_n, "alpha_reg": alpha,
@@ -795,7 +798,8 @@ def run_map(args):
     del ae
     torch.cuda.empty_cache()
     if args.map_ref == "full":
-        full = aewave.Solver(shape, H, nt, rec, storage="full", f0=args.f0, cmax=args.map_cmax)
+        full = aewave.Solver(shape, H, nt, rec, storage="full", f0=args.f0, cmax=args.map_cmax,
+                             src_sigma=args.src_sigma)
         c_full, out["map_full"] = solve(full)
         du_ref = (c_full.cpu() - c0.cpu()).double()
         out["map_update_rel_diff"] = float(torch.linalg.vector_norm(c_ae_h.double() - c0.cpu().double() - du_ref)

@@ -122,6 +122,12 @@ typedef struct {
   int norm;               /* time codec: AEW_NORM_POW2 (0) or AEW_NORM_MINMAX (1)     */
   int act;                /* time codec: AEW_ACT_GELU (0) or AEW_ACT_ELU (1)          */
   double beta;            /* AEW_NORM_MINMAX: floor of the range (0 = the paper's 1e-7)*/
+  double src_sigma;       /* source smoothing in space [m] (Sec. 4.1's box problem): 0 is
+                             the point force; > 0 spreads it over the z-faces within
+                             R = ceil(3 src_sigma / h) faces of the source face with
+                             weights exp(-r^2 / (2 src_sigma^2)) normalised to sum 1
+                             (r: distance between face centres); the box must lie in
+                             nodes 1 .. n-2 of every axis                             */
 } aew_config;
 
 typedef struct {

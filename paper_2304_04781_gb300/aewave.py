@@ -44,6 +44,7 @@ class aew_config(ctypes.Structure):
         ("nrec", c_int), ("rec_ijk", POINTER(c_int)),
         ("storage", c_int), ("n_checkpoints", c_int), ("accum_window", c_int), ("n_lat", c_int),
         ("codec", c_int), ("norm", c_int), ("act", c_int), ("beta", c_double),
+        ("src_sigma", c_double),
     ]
 
 
@@ -246,7 +247,7 @@ class Solver:
                  n_checkpoints: int = 20, accum_window: int = 8, n_lat: Optional[int] = None,
                  cfl: float = 0.5, cmax: float = 3000.0, src=None, f0: float = 25.0,
                  t0: Optional[float] = None, codec: str = "space", norm: str = "pow2",
-                 act: str = "gelu", beta: float = 0.0):
+                 act: str = "gelu", beta: float = 0.0, src_sigma: float = 0.0):
         nz, ny, nx = shape
         self.shape = (nz, ny, nx)
         self.nt = nt
@@ -273,6 +274,7 @@ class Solver:
         cfg.norm = {"pow2": 0, "minmax": 1}[norm]
         cfg.act = {"gelu": 0, "elu": 1}[act]
         cfg.beta = beta
+        cfg.src_sigma = src_sigma
         self.norm = norm
         self.n_lat = n_lat
         self.codec = codec

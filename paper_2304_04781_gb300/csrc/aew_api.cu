@@ -105,6 +105,9 @@ struct aew_handle {
   // Armijo gate of a gradient run by the Newton driver: stop after the forward solve
   // when the misfit exceeds it (+inf: never)
   double gate = INFINITY;
+  // the source's spatial weights on the z-faces of a (2 src_r + 1)^3 box (point: {1})
+  float* src_w = nullptr;
+  int src_r = 0;
   Codec* codec = nullptr;
   std::vector<void*> allocs;
   size_t bytes = 0;
@@ -202,6 +205,8 @@ int fwd_step(aew_handle* h, int n, float* const in[4], float* const out[4], cons
   a.si = h->cfg.src[0];
   a.sj = h->cfg.src[1];
   a.sk = wav ? h->cfg.src[2] : -1;
+  a.src_w = h->src_w;
+  a.sr = h->src_r;
   a.krec = d_row ? h->krec : -1;
   a.rec_map = h->rec_map;
   a.d_out = d_row;
@@ -994,6 +999,12 @@ int aew_create(const aew_config* cfg, aew_handle** out) {
   if ((c.norm != AEW_NORM_POW2 || c.act != AEW_ACT_GELU) && c.codec != AEW_CODEC_TIME)
     return bad("min-max normalisation and ELU are variants of the time codec");
   if (!(c.beta >= 0.0)) return bad("beta must be >= 0 (0: the default 1e-7)");
+  if (!(c.src_sigma >= 0.0) || !std::isfinite(c.src_sigma)) return bad("src_sigma must be >= 0");
+  const int src_r = c.src_sigma > 0.0 ? (int)std::ceil(3.0 * c.src_sigma / c.h) : 0;
+  if (src_r > 0 && (c.src[0] - src_r < 1 || c.src[0] + src_r > c.nx - 2 || c.src[1] - src_r < 1 ||
+                    c.src[1] + src_r > c.ny - 2 || c.src[2] - src_r < 1 ||
+                    c.src[2] + src_r > c.nz - 2))
+    return bad("the smoothed source's box (radius ceil(3 src_sigma / h)) must lie in nodes 1 .. n-2");
 
   aew_handle* h = new aew_handle();
   h->cfg = c;
@@ -1021,8 +1032,31 @@ int aew_create(const aew_config* cfg, aew_handle** out) {
   h->wav.resize(c.nt);
   for (int n = 0; n < c.nt; ++n) h->wav[n] = (float)(-ricker(n * h->dt, c.f0, c.t0));
 
+  // the source's spread over the z-faces: Gaussian weights by face-centre distance,
+  // normalised to sum 1 (the point source: one face, weight 1)
+  h->src_r = src_r;
+  const int sw = 2 * src_r + 1;
+  std::vector<float> src_w((size_t)sw * sw * sw, 1.f);
+  if (src_r > 0) {
+    std::vector<double> w(src_w.size());
+    double tot = 0.0;
+    for (int a = 0; a < sw; ++a)
+      for (int b = 0; b < sw; ++b)
+        for (int d = 0; d < sw; ++d) {
+          const double r2 = ((double)(a - src_r) * (a - src_r) + (double)(b - src_r) * (b - src_r) +
+                             (double)(d - src_r) * (d - src_r)) * c.h * c.h;
+          const double v = std::exp(-r2 / (2.0 * c.src_sigma * c.src_sigma));
+          w[((size_t)a * sw + b) * sw + d] = v;
+          tot += v;
+        }
+    for (size_t q = 0; q < w.size(); ++q) src_w[q] = (float)(w[q] / tot);
+  }
+
   const size_t C = h->C, nt = (size_t)c.nt;
-  bool ok = dalloc(h, &h->c, C) && dalloc(h, &h->m, C) && dalloc(h, &h->dm, C) &&
+  bool ok = dalloc(h, &h->src_w, src_w.size()) &&
+            cudaMemcpy(h->src_w, src_w.data(), src_w.size() * sizeof(float),
+                       cudaMemcpyHostToDevice) == cudaSuccess &&
+            dalloc(h, &h->c, C) && dalloc(h, &h->m, C) && dalloc(h, &h->dm, C) &&
             dalloc(h, &h->acc32, C) && dalloc(h, &h->acc64, C) &&
             dalloc(h, &h->d, (nt + 1) * h->nrow) && dalloc(h, &h->R, (nt + 1) * h->nrow) &&
             dalloc(h, &h->dd, (nt + 1) * h->nrow) &&

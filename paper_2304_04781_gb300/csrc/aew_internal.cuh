@@ -32,8 +32,12 @@ struct FwdStep {
   int nx, ny, nz;
   int kc;            // z planes per CTA
   float dth;         // dt / h
-  float dts;         // dt * s^n added to the source z-face
+  float dts;         // dt * s^n added to the source z-face(s)
   int si, sj, sk;    // source node (sk < 0: none)
+  // the source's spread: faces |i - si|, |y - sj|, |k - sk| <= sr get dts times
+  // src_w[(k - sk + sr)][(y - sj + sr)][(i - si + sr)] (a point source: sr = 0, {1})
+  const float* src_w;
+  int sr;
   int krec;          // receiver node plane (-1: none)
   const int* rec_map;  // [ny][nx] receiver index or -1
   float* d_out;        // receiver record row [nrec][3] (or null)

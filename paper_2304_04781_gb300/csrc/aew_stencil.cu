@@ -104,6 +104,20 @@ __device__ __forceinline__ float& comp(float4& v, int c) {
   return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
 }
 __device__ __forceinline__ float4 z4() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+// the source's force on the z-faces of the 4 nodes (k, y, i0 .. i0 + 3): dts times the
+// spread weight of each face inside the source box (a point source: the one face, 1)
+__device__ __forceinline__ void add_source(float4& v, int k, int y, int i0, const FwdStep& a) {
+  if (a.sk < 0) return;
+  const int W = 2 * a.sr + 1;
+  const int dk = k - a.sk + a.sr, dy = y - a.sj + a.sr;
+  if ((unsigned)dk >= (unsigned)W || (unsigned)dy >= (unsigned)W) return;
+  const float* w = a.src_w + ((size_t)dk * W + dy) * W;
+#pragma unroll
+  for (int d = 0; d < 4; ++d) {
+    const int dx = i0 + d - a.si + a.sr;
+    if ((unsigned)dx < (unsigned)W) comp(v, d) += a.dts * __ldg(w + dx);
+  }
+}
 // Products are left to the compiler, which may contract m e into the following
 // subtraction differently in each kernel variant: the plain, packing and incremental
 // steps can then differ in the last FP32 bit (rounding the products on their own with
@@ -278,10 +292,7 @@ __global__ void __launch_bounds__(NTHR, (INCR || PACK) ? 2 : 3)
     const uint8_t* sc = r.at(kbeg);
     vzl = fupd4(dth, me_at<INCR>(sc, qE), me_at<INCR>(sb, qE),
                 reinterpret_cast<const float4*>(sb + FwdLayout::VZ)[qO]);
-    if (kbeg - 1 == a.sk && y == a.sj) {
-      const int d = a.si - i0;
-      if (d >= 0 && d < 4) comp(vzl, d) += a.dts;
-    }
+    add_source(vzl, kbeg - 1, y, i0, a);
   }
 
   const int NBx = nx >> 3, NBy = ny >> 3;
@@ -369,10 +380,7 @@ __global__ void __launch_bounds__(NTHR, (INCR || PACK) ? 2 : 3)
     // z-faces
     float4 vz1 = fupd4(dth, me_n, me_c, vz_c);
     if (k == nz - 1) vz1 = z4();
-    if (k == a.sk && y == a.sj) {
-      const int d = a.si - i0;
-      if (d >= 0 && d < 4) comp(vz1, d) += a.dts;
-    }
+    add_source(vz1, k, y, i0, a);
     // strain update on interior nodes
     float4 e1;
     e1.x = fmaf(dth, ((vx1.x - vxl) + (vy1.x - vyl.x)) + (vz1.x - vzl.x), e_c.x);

@@ -25,7 +25,8 @@ def setup(shape, nt, nrec, seed=0, h=10.0):
 def solver(prob, storage="full", **kw):
     from paper_2304_04781_gb300 import aewave
     return aewave.Solver(prob.shape, prob.h, prob.nt, prob.rec, storage=storage, src=prob.src,
-                         f0=prob.f0, t0=prob.t0, **kw)
+                         f0=prob.f0, t0=prob.t0, cfl=prob.cfl, cmax=prob.cmax,
+                         src_sigma=prob.src_sigma, **kw)
 
 
 def cuda(a) -> torch.Tensor:

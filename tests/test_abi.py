@@ -56,6 +56,8 @@ def _cfg(**kw):
     (dict(codec=1, n_lat=64), "n_lat"),
     (dict(codec=1, storage=2, n_lat=512, nx=20), "multiples of 8"),
     (dict(codec=1, storage=2, n_lat=512, nz=12, ny=20), "multiples of 8"),
+    (dict(src_sigma=-1.0), "src_sigma"),
+    (dict(src_sigma=30.0), "smoothed source's box"),
 ])
 def test_create_rejects_bad_configs(kw, frag):
     L = aewave.lib()
