@@ -261,7 +261,8 @@ __global__ void transpose16_kernel(const uint16_t* __restrict__ src, int rows, i
 
 // bias gradients: the column sums of up to four [rows][cols] FP32 matrices in one
 // launch.  A block takes 32 columns of one matrix: lane = column (coalesced rows), the 8
-// warps split the rows, FP64 partials combined in a fixed order.
+// warps split the rows; each thread keeps four FP32 partial sums (a batch of 512 rows
+// gives each 16 terms), combined in FP64 in a fixed order.
 struct ColSums {
   const float* d[4];
   float* out[4];
@@ -276,10 +277,13 @@ __global__ void colsum_multi_kernel(ColSums cs, int rows) {
   const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
   const int c = (blockIdx.x - cs.tiles[m]) * 32 + lane;
   const int cols = cs.cols[m];
-  double acc = 0.0;
-  if (c < cols)
-    for (int r = wq; r < rows; r += 8) acc += cs.d[m][(size_t)r * cols + c];
-  part[wq][lane] = acc;
+  // four independent FP32 partial sums per thread (a warp's rows r = wq + 8 t), then FP64
+  float a4[4] = {0.f, 0.f, 0.f, 0.f};
+  if (c < cols) {
+    int t = 0;
+    for (int r = wq; r < rows; r += 8, ++t) a4[t & 3] += cs.d[m][(size_t)r * cols + c];
+  }
+  part[wq][lane] = ((double)a4[0] + (double)a4[1]) + ((double)a4[2] + (double)a4[3]);
   __syncthreads();
   if (wq == 0 && c < cols) {
     double t = 0.0;
@@ -295,11 +299,14 @@ struct ToBf16 {
   size_t n[3];
 };
 __global__ void to_bf16_multi_kernel(ToBf16 t) {
-  const float* w = t.w[blockIdx.y];
-  uint16_t* o = t.o[blockIdx.y];
-  const size_t n = t.n[blockIdx.y];
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    o[i] = gemm::bf16_bits(w[i]);
+  // four elements per thread (every size is a multiple of 4)
+  const float4* w = reinterpret_cast<const float4*>(t.w[blockIdx.y]);
+  uint2* o = reinterpret_cast<uint2*>(t.o[blockIdx.y]);
+  const size_t n4 = t.n[blockIdx.y] / 4;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
+    const float4 v = w[i];
+    o[i] = make_uint2(gemm::pack_bf16(v.x, v.y), gemm::pack_bf16(v.z, v.w));
+  }
 }
 
 __global__ void loss_kernel(const double* red, double inv_n, float* out, double* acc) {
@@ -447,7 +454,7 @@ __global__ void lamb1_multi_kernel(LambArgs a, float b1, float b2, float c1, flo
   float4* g = reinterpret_cast<float4*>(a.g[t]);
   float4* m = reinterpret_cast<float4*>(a.m[t]);
   float4* v = reinterpret_cast<float4*>(a.v[t]);
-  double sw = 0.0, su = 0.0;
+  float sw = 0.f, su = 0.f;   // a thread's few terms in FP32; blocks and tensors in FP64
   for (size_t i = (size_t)(blockIdx.x - a.blk[t]) * blockDim.x + threadIdx.x; i < n4;
        i += (size_t)nb * blockDim.x) {
     const float4 gi = g[i], mi0 = m[i], vi0 = v[i], wi = w[i];
@@ -458,14 +465,14 @@ __global__ void lamb1_multi_kernel(LambArgs a, float b1, float b2, float c1, flo
       mm[q] = b1 * mm[q] + (1.f - b1) * gg[q];
       vv[q] = b2 * vv[q] + (1.f - b2) * gg[q] * gg[q];
       uu[q] = (mm[q] / c1) / (sqrtf(vv[q] / c2) + eps);
-      sw += (double)ww[q] * (double)ww[q];
-      su += (double)uu[q] * (double)uu[q];
+      sw = fmaf(ww[q], ww[q], sw);
+      su = fmaf(uu[q], uu[q], su);
     }
     m[i] = make_float4(mm[0], mm[1], mm[2], mm[3]);
     v[i] = make_float4(vv[0], vv[1], vv[2], vv[3]);
     g[i] = make_float4(uu[0], uu[1], uu[2], uu[3]);
   }
-  block_add2(sw, su, norms + 2 * t);
+  block_add2((double)sw, (double)su, norms + 2 * t);
 }
 
 // pass 2: w -= lr * (|w| / |u|) * u
@@ -572,7 +579,7 @@ cudaError_t codec_train_step(Codec* c, const uint16_t* Y, const float* wts, int 
   {
     const ToBf16 tb{{c->w[6], c->w[4], c->w[2]}, {s->W4b, s->W3b, s->W2b},
                     {(size_t)H * I, (size_t)nl * H, (size_t)H * nl}};
-    to_bf16_multi_kernel<<<dim3(nblk((size_t)H * I), 3), 256, 0, st>>>(tb);
+    to_bf16_multi_kernel<<<dim3(nblk((size_t)H * I / 4), 3), 256, 0, st>>>(tb);
     TCK(cudaGetLastError());
   }
   {
