@@ -400,14 +400,16 @@ def run_ours(args):
     decoded = None
     if not args.no_accuracy:
         every = 8 if args.codec == "time" else max(1, nt // 40)
-        k = ae.nvec * ((nt // aewave.WINDOW - 1) // every + 1) if args.codec == "time" \
-            else ae.nblocks * ((nt - 1) // every)
-        vec, mx = ae.snapshots(c, every, k, with_scales=True)
-        decoded = ae.codec_eval(vec, mx)
-        decoded["sample"] = (f"every {every}th {'16-step window' if args.codec == 'time' else 'state'} "
-                             f"of this run, all vectors")
-        del vec, mx
-        torch.cuda.empty_cache()
+        complete = nt // aewave.WINDOW
+        k = (ae.nvec * ((complete - 1) // every + 1) if complete > 0 else 0) \
+            if args.codec == "time" else ae.nblocks * ((nt - 1) // every)
+        if k > 0:    # (a run shorter than one window has no complete window to sample)
+            vec, mx = ae.snapshots(c, every, k, with_scales=True)
+            decoded = ae.codec_eval(vec, mx)
+            decoded["sample"] = (f"every {every}th {'16-step window' if args.codec == 'time' else 'state'} "
+                                 f"of this run, all vectors")
+            del vec, mx
+            torch.cuda.empty_cache()
 
     # ---- the hot-path kernels alone (CUDA events around back-to-back launches)
     nprof = min(nt, 200)
@@ -742,10 +744,24 @@ def run_map(args):
     ae.codec_set(W)
     d_obs = ae.forward(ctrue)
     w = torch.from_numpy(inputs.white_noise(1, shape, seed=77)[0]).cuda()
+    ae.prior_solve(w, 1.0, theta)      # warm-up (first-call allocations)
     a, b = ev(), ev(); a.record()
     x1, its = ae.prior_solve(w, 1.0, theta)
     b.record(); torch.cuda.synchronize()
+    solve_ms = a.elapsed_time(b)
     alpha_s = float(x1.double().std()) / args.prior_std
+    # the prior's HBM-bound kernels alone: A q (8 B per node: read q, write A q) and one
+    # CG iteration (apply 8 + update 24 + direction 12 = 44 B per node)
+    peaks = load_peaks()
+    y1 = torch.empty_like(w)
+    for _ in range(3):
+        ae.prior_apply(w, 1.0, theta, out=y1)
+    a, b = ev(), ev(); a.record()
+    for _ in range(20):
+        ae.prior_apply(w, 1.0, theta, out=y1)
+    b.record(); torch.cuda.synchronize()
+    apply_ms = a.elapsed_time(b) / 20
+    del y1
     sigma_n = args.noise_rel * float(d_obs[1:].double().pow(2).mean().sqrt())
     alpha = alpha_s * sigma_n
     out = {"config": dict(workload(shape, nt, args.nrec, n_lat, args.codec), f0_hz=args.f0,
@@ -754,7 +770,11 @@ def run_map(args):
            "codec_weights": "trained" if trained else "random-init",
            "prior": {"theta_m2": theta, "sample_std": args.prior_std, "alpha_s": alpha_s,
                      "noise_rel": args.noise_rel, "sigma_n": sigma_n, "alpha_reg": alpha,
-                     "solve_ms": a.elapsed_time(b), "solve_cg_iters": its},
+                     "solve_ms": solve_ms, "solve_cg_iters": its,
+                     "apply_ms": apply_ms,
+                     "apply_gbs": 8.0 * c0.numel() / (apply_ms * 1e-3) / 1e9,
+                     "cg_iter_gbs": 44.0 * c0.numel() * its / (solve_ms * 1e-3) / 1e9,
+                     "hbm_peak_gbs": peaks[0]},
            "initial_mean_rel_err": mean_rel(c0)}
     del x1, w
     kw = dict(alpha=alpha, theta=theta, newton_iters=args.newton_iters, cg_max=args.cg_max)
@@ -791,7 +811,8 @@ def run_map(args):
                        "ms_per_sample": a.elapsed_time(b) / args.dias_samples,
                        "eigenvalues": [float(v) for v in lam[:max(args.dias_rank + 3, 8)]],
                        "solve": dias, "map_continued": cont,
-                       "dias_vs_map_continued_rel_diff": nrm(c_dias - c_cont) / nrm(c_cont - c0)}
+                       "dias_vs_map_continued_rel_diff": (nrm(c_dias - c_cont) / nrm(c_cont - c0)
+                                                          if nrm(c_cont - c0) > 0 else None)}
         del W1, c_dias, c_cont
     except aewave.AewError as err:
         out["dias"] = {"error": str(err)}

@@ -501,18 +501,21 @@ typedef struct aew_newton_iter {
   double step;          /* step length taken */
 } aew_newton_iter;
 
-/* out_dev = A q_dev (FP64 arithmetic, FP32 in and out; [nz][ny][nx] of the handle's
- * grid and spacing).  Asynchronous on `stream`.  AEW_E_ARG for NULL pointers, alpha <= 0
- * or theta < 0.  q_dev and out_dev must not overlap. */
+/* out_dev = A q_dev (FP32; [nz][ny][nx] of the handle's grid and spacing).
+ * Asynchronous on `stream`.  AEW_E_ARG for NULL pointers, alpha <= 0 or theta < 0.
+ * q_dev and out_dev must not overlap.  The vectors of aew_prior_solve, aew_newton_cg
+ * and aew_dias_subspace are read as float4: they must be 16-byte aligned (AEW_E_ARG
+ * otherwise; a torch allocation is). */
 int aew_prior_apply(aew_handle* h, double alpha, double theta, const float* q_dev,
                     float* out_dev, void* stream);
 
-/* x_dev = A^{-1} w_dev by conjugate gradients on FP64 vectors (A is SPD with spectrum
- * inside [alpha, alpha (1 + 12 theta / h^2)]), stopped when |w - A x| <= rtol |w| or
+/* x_dev = A^{-1} w_dev by conjugate gradients on FP32 vectors with FP64 inner products
+ * (A is SPD with spectrum inside [alpha, alpha (1 + 12 theta / h^2)]), stopped when the
+ * recursive residual |r| <= rtol |w| (tolerances down to about 1e-7 are reached) or
  * after max_iter iterations; *iters_host (may be NULL) receives the iterations taken.
  * Prior samples are c + A^{-1} w for white noise w.  Synchronises `stream` (the
  * convergence test reads the residual every 8 iterations).  AEW_E_ARG for bad
- * arguments; AEW_E_NOMEM if the four FP64 work vectors cannot be allocated (they are
+ * arguments; AEW_E_NOMEM if the three FP32 work vectors cannot be allocated (they are
  * freed on return); AEW_E_NOCONVERGE if the residual test did not pass within max_iter
  * (x_dev then holds the last iterate). */
 int aew_prior_solve(aew_handle* h, double alpha, double theta, const float* w_dev,

@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <string>
 #include <vector>
@@ -78,52 +79,88 @@ __device__ double block_sum_of(const double* __restrict__ part, int n) {
   return total;
 }
 
-// A x at node n: alpha x_n - alpha theta / h^2 * sum over existing neighbours (x_nb - x_n)
-__device__ __forceinline__ float prior_at(const float* __restrict__ x, size_t n, const Grid& g,
-                                          float alpha, float at) {
-  const int i = (int)(n % (size_t)g.nx);
-  const size_t rest = n / (size_t)g.nx;
-  const int j = (int)(rest % (size_t)g.ny);
-  const int k = (int)(rest / (size_t)g.ny);
-  const size_t sy = (size_t)g.nx, sz = (size_t)g.nx * g.ny;
-  const float xn = x[n];
-  float lap = 0.f;
-  if (i > 0) lap += x[n - 1] - xn;
-  if (i + 1 < g.nx) lap += x[n + 1] - xn;
-  if (j > 0) lap += x[n - sy] - xn;
-  if (j + 1 < g.ny) lap += x[n + sy] - xn;
-  if (k > 0) lap += x[n - sz] - xn;
-  if (k + 1 < g.nz) lap += x[n + sz] - xn;
-  return alpha * xn - at * lap;
-}
+// The prior solve's reductions keep each thread's terms in FP32 and move them into an
+// FP64 accumulator every kFlush terms: one FP64 add per kFlush elements instead of one
+// FP64 FMA per element (GB300's FP64 rate would otherwise bound these passes below HBM
+// speed).  That is safe there because the solve works on vectors scaled to unit rms;
+// the Newton driver's vectors (gradients near 1e-20 per node) would underflow in FP32
+// squares, so its inner products multiply in FP64.
+constexpr int kFlush = 16;
 
-// y = A x (+ yadd); optional per-block partials of sum wdot . (A x)
-// (y may be yadd; x must not overlap y)
-__global__ void prior_kernel(const float* __restrict__ x, float* y, const float* yadd, Grid g,
-                             float alpha, float at,
-                             const float* __restrict__ wdot, double* part) {
-  double acc = 0.0;
-  for (size_t n = blockIdx.x * (size_t)NT + threadIdx.x; n < g.C; n += (size_t)gridDim.x * NT) {
-    float v = prior_at(x, n, g, alpha, at);
-    if (part) acc += (double)wdot[n] * (double)v;
-    if (yadd) v += yadd[n];
-    y[n] = v;
+struct Acc {
+  double d = 0.0;
+  float f = 0.f;
+  int n = 0;
+  __device__ __forceinline__ void add(float x) {
+    f += x;
+    if (++n == kFlush) {
+      d += (double)f;
+      f = 0.f;
+      n = 0;
+    }
   }
-  if (part) block_store(acc, part);
+  __device__ __forceinline__ double total() const { return d + (double)f; }
+};
+
+// y = A x (+ yadd) with A x = alpha x - alpha theta / h^2 * sum over the neighbours a node
+// has of (x_nb - x); optional partials of sum wdot . (A x).  One warp per grid row
+// (k, y) with lanes along x: row indices once per row, coalesced loads, neighbours in
+// other rows through L1/L2.  y may be yadd; x must not overlap y.
+__global__ void prior_kernel(const float* __restrict__ x, float* y, const float* yadd, Grid g,
+                             float alpha, float at, const float* __restrict__ wdot, double* part) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * NT) >> 5;
+  const int nrow = g.ny * g.nz;
+  const size_t sy = (size_t)g.nx, sz = (size_t)g.nx * g.ny;
+  Acc acc;
+  for (int row = (blockIdx.x * NT + threadIdx.x) >> 5; row < nrow; row += warps) {
+    const int j = row % g.ny, k = row / g.ny;
+    const size_t base = (size_t)row * g.nx;
+    for (int i = lane; i < g.nx; i += 32) {
+      const size_t n = base + i;
+      const float xn = x[n];
+      float lap = 0.f;
+      if (i > 0) lap += x[n - 1] - xn;
+      if (i + 1 < g.nx) lap += x[n + 1] - xn;
+      if (j > 0) lap += x[n - sy] - xn;
+      if (j + 1 < g.ny) lap += x[n + sy] - xn;
+      if (k > 0) lap += x[n - sz] - xn;
+      if (k + 1 < g.nz) lap += x[n + sz] - xn;
+      float v = alpha * xn - at * lap;
+      if (part) acc.add(wdot[n] * v);
+      if (yadd) v += yadd[n];
+      y[n] = v;
+    }
+  }
+  if (part) block_store(acc.total(), part);
 }
 
-// out = a x + b y (either of x, y may be out)
+// out = a x + b y (either of x, y may be out); n a multiple of 4
 __global__ void axpby_kernel(float a, const float* x, float b, const float* y, float* out,
                              size_t n) {
-  for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < n; i += (size_t)gridDim.x * NT)
-    out[i] = a * x[i] + b * y[i];
+  const float4* x4 = reinterpret_cast<const float4*>(x);
+  const float4* y4 = reinterpret_cast<const float4*>(y);
+  float4* o4 = reinterpret_cast<float4*>(out);
+  for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < n / 4; i += (size_t)gridDim.x * NT) {
+    const float4 u = x4[i], v = y4[i];
+    o4[i] = make_float4(a * u.x + b * v.x, a * u.y + b * v.y, a * u.z + b * v.z, a * u.w + b * v.w);
+  }
 }
 
+__device__ __forceinline__ float dot4(float4 a, float4 b) {
+  return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
+}
+
+// FP64 products and sums (any magnitudes)
 __global__ void dot_kernel(const float* __restrict__ a, const float* __restrict__ b, size_t n,
                            double* part) {
+  const float4* a4 = reinterpret_cast<const float4*>(a);
+  const float4* b4 = reinterpret_cast<const float4*>(b);
   double acc = 0.0;
-  for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < n; i += (size_t)gridDim.x * NT)
-    acc += (double)a[i] * (double)b[i];
+  for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < n / 4; i += (size_t)gridDim.x * NT) {
+    const float4 u = a4[i], v = b4[i];
+    acc += (double)u.x * v.x + (double)u.y * v.y + (double)u.z * v.z + (double)u.w * v.w;
+  }
   block_store(acc, part);
 }
 
@@ -136,14 +173,21 @@ __global__ void cg_update_kernel(float* __restrict__ x, float* __restrict__ r,
   const double pap = block_sum_of(ppap, nblk);
   const double rr = block_sum_of(prr, nblk);
   const float a = pap > 0.0 ? (float)(rr / pap) : 0.f;
-  double acc = 0.0;
-  for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < n; i += (size_t)gridDim.x * NT) {
-    x[i] += a * p[i];
-    const float ri = r[i] - a * Ap[i];
-    r[i] = ri;
-    acc += (double)ri * (double)ri;
+  float4* x4 = reinterpret_cast<float4*>(x);
+  float4* r4 = reinterpret_cast<float4*>(r);
+  const float4* p4 = reinterpret_cast<const float4*>(p);
+  const float4* q4 = reinterpret_cast<const float4*>(Ap);
+  Acc acc;
+  for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < n / 4; i += (size_t)gridDim.x * NT) {
+    const float4 pi = p4[i], qi = q4[i];
+    float4 xi = x4[i], ri = r4[i];
+    xi.x += a * pi.x; xi.y += a * pi.y; xi.z += a * pi.z; xi.w += a * pi.w;
+    ri.x -= a * qi.x; ri.y -= a * qi.y; ri.z -= a * qi.z; ri.w -= a * qi.w;
+    x4[i] = xi;
+    r4[i] = ri;
+    acc.add(dot4(ri, ri));
   }
-  block_store(acc, prr_new);
+  block_store(acc.total(), prr_new);
 }
 
 // direction: p = r + (rr_new / rr_old) p
@@ -152,18 +196,27 @@ __global__ void cg_dir_kernel(float* __restrict__ p, const float* __restrict__ r
   const double ro = block_sum_of(prr_old, nblk);
   const double rn = block_sum_of(prr_new, nblk);
   const float b = ro > 0.0 ? (float)(rn / ro) : 0.f;
-  for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < n; i += (size_t)gridDim.x * NT)
-    p[i] = r[i] + b * p[i];
+  float4* p4 = reinterpret_cast<float4*>(p);
+  const float4* r4 = reinterpret_cast<const float4*>(r);
+  for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < n / 4; i += (size_t)gridDim.x * NT) {
+    const float4 ri = r4[i];
+    float4 pi = p4[i];
+    pi.x = ri.x + b * pi.x; pi.y = ri.y + b * pi.y; pi.z = ri.z + b * pi.z; pi.w = ri.w + b * pi.w;
+    p4[i] = pi;
+  }
 }
 
 // projection: partial dots of v with the r rows of W1, part[k][nblk]
 __global__ void proj_dots_kernel(const float* __restrict__ W1, int r, const float* __restrict__ v,
                                  size_t n, double* part) {
+  const float4* v4 = reinterpret_cast<const float4*>(v);
   for (int k = 0; k < r; ++k) {
-    const float* w = W1 + (size_t)k * n;
+    const float4* w4 = reinterpret_cast<const float4*>(W1 + (size_t)k * n);
     double acc = 0.0;
-    for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < n; i += (size_t)gridDim.x * NT)
-      acc += (double)w[i] * (double)v[i];
+    for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < n / 4; i += (size_t)gridDim.x * NT) {
+      const float4 u = w4[i], x = v4[i];
+      acc += (double)u.x * x.x + (double)u.y * x.y + (double)u.z * x.z + (double)u.w * x.w;
+    }
     block_store(acc, part + (size_t)k * gridDim.x);
   }
 }
@@ -351,6 +404,9 @@ struct Ops {
   }
 };
 
+// every grid vector is read as float4
+bool aligned16(const void* p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
 int prior_args_ok(aew_handle* h, double alpha, double theta) {
   if (!(alpha > 0.0) || !std::isfinite(alpha))
     return set_error(h, AEW_E_ARG, "prior alpha must be positive and finite");
@@ -372,9 +428,6 @@ int prior_cg(aew_handle* h, const Grid& g, double hh, double alpha, double theta
   double* ppap = part;
   double* prr[2] = {part + kVecBlocks, part + 2 * kVecBlocks};
   const float fa = (float)alpha, fat = (float)(alpha * theta / (hh * hh));
-  NW_CK(cudaMemsetAsync(x, 0, g.C * sizeof(float), s));
-  NW_CK(cudaMemcpyAsync(r, w, g.C * sizeof(float), cudaMemcpyDeviceToDevice, s));
-  NW_CK(cudaMemcpyAsync(p, w, g.C * sizeof(float), cudaMemcpyDeviceToDevice, s));
   dot_kernel<<<nb, NT, 0, s>>>(w, w, g.C, prr[0]);
   NW_CK(cudaGetLastError());
   std::vector<double> hp(nb);
@@ -390,7 +443,20 @@ int prior_cg(aew_handle* h, const Grid& g, double hh, double alpha, double theta
   int rc = host_sum(prr[0], &ww);
   if (rc) return rc;
   if (iters) *iters = 0;
-  if (ww == 0.0) return AEW_OK;   // w = 0: x = 0
+  if (ww == 0.0) {   // w = 0: x = 0
+    NW_CK(cudaMemsetAsync(x, 0, g.C * sizeof(float), s));
+    return AEW_OK;
+  }
+  // solve for the unit-rms right-hand side sc w (the iteration's FP32 squares then stay
+  // far from FP32's range limits), and scale x back at the end
+  const double sc = std::sqrt((double)g.C / ww);
+  NW_CK(cudaMemsetAsync(x, 0, g.C * sizeof(float), s));
+  axpby_kernel<<<nb, NT, 0, s>>>((float)sc, w, 0.f, w, r, g.C);
+  axpby_kernel<<<nb, NT, 0, s>>>((float)sc, w, 0.f, w, p, g.C);
+  NW_CK(cudaGetLastError());
+  dot_kernel<<<nb, NT, 0, s>>>(r, r, g.C, prr[0]);
+  NW_CK(cudaGetLastError());
+  if ((rc = host_sum(prr[0], &ww))) return rc;
   const double tol2 = rtol * rtol * ww;
   int it = 0;
   for (; it < max_iter; ++it) {
@@ -405,11 +471,15 @@ int prior_cg(aew_handle* h, const Grid& g, double hh, double alpha, double theta
       if (rr <= tol2) {
         ++it;
         if (iters) *iters = it;
+        axpby_kernel<<<nb, NT, 0, s>>>((float)(1.0 / sc), x, 0.f, x, x, g.C);
+        NW_CK(cudaGetLastError());
         return AEW_OK;
       }
     }
   }
   if (iters) *iters = it;
+  axpby_kernel<<<nb, NT, 0, s>>>((float)(1.0 / sc), x, 0.f, x, x, g.C);
+  NW_CK(cudaGetLastError());
   char buf[160];
   std::snprintf(buf, sizeof buf, "prior solve: relative residual above %.3g after %d iterations",
                 rtol, max_iter);
@@ -445,6 +515,8 @@ int aew_prior_solve(aew_handle* h, double alpha, double theta, const float* w_de
                     double rtol, int max_iter, int* iters_host, void* stream) {
   if (!h) return AEW_E_ARG;
   if (!w_dev || !x_dev) return set_error(h, AEW_E_ARG, "NULL vector");
+  if (!aew::aligned16(w_dev) || !aew::aligned16(x_dev))
+    return set_error(h, AEW_E_ARG, "vectors must be 16-byte aligned");
   if (!(rtol > 0.0) || max_iter < 1) return set_error(h, AEW_E_ARG, "rtol > 0, max_iter >= 1");
   int rc = aew::prior_args_ok(h, alpha, theta);
   if (rc) return rc;
@@ -459,6 +531,8 @@ int aew_newton_cg(aew_handle* h, float* c_dev, const float* d_obs_dev, const flo
                   aew_newton_iter* hist_host, int* iters_host, void* stream) {
   if (!h) return AEW_E_ARG;
   if (!c_dev || !c0_dev || !cfg) return set_error(h, AEW_E_ARG, "NULL argument");
+  if (!aew::aligned16(c_dev) || !aew::aligned16(c0_dev) || !aew::aligned16(W1_dev))
+    return set_error(h, AEW_E_ARG, "c, c0 and W1 must be 16-byte aligned");
   int rc = aew::prior_args_ok(h, cfg->alpha, cfg->theta);
   if (rc) return rc;
   if (cfg->newton_iters < 1 || cfg->cg_max < 1 || cfg->max_backtracks < 1 ||
@@ -597,6 +671,9 @@ int aew_dias_subspace(aew_handle* h, const float* c_dev, const float* d_obs_dev,
   if (!h) return AEW_E_ARG;
   if (!c_dev || !noise_dev || !G_dev || !W1_dev || !lambda_host)
     return set_error(h, AEW_E_ARG, "NULL argument");
+  if (!aew::aligned16(c_dev) || !aew::aligned16(noise_dev) || !aew::aligned16(G_dev) ||
+      !aew::aligned16(W1_dev))
+    return set_error(h, AEW_E_ARG, "c, noise, G and W1 must be 16-byte aligned");
   if (N < 1 || N > aew::kMaxN || r < 1 || r > N || r > aew::kMaxR)
     return set_error(h, AEW_E_ARG, "need 1 <= r <= N <= 64 and r <= 32");
   int rc = aew::prior_args_ok(h, alpha, theta);
