@@ -36,10 +36,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "gradients/hour at 256^3x2000 steps: AE vs checkpointing; stencil HBM GB/s"
-# DRAM bytes (read + write) of one forward-step launch at 256^3, from an ncu capture of
-# the current kernel (dram__bytes_read.sum + dram__bytes_write.sum); None once the
-# kernel changes until it is captured again
-FWD_TRAFFIC_256 = 586.19e6
+# DRAM bytes (read + write) of one adjoint-step launch at 256^3, from an ncu capture of
+# the current kernel (dram__bytes_read.sum + dram__bytes_write.sum, a window-middle step
+# without the FP64 flush); to be set to None when the kernel changes until it is
+# captured again
+ADJ_TRAFFIC_256 = 768.6e6
 SHAPE = (256, 256, 256)
 NT = 2000
 NREC = 128
@@ -548,7 +549,10 @@ def run_ours(args):
                          "achieved": dom["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
                          "frac": dom["achieved_gbs"] / hbm_peak,
                          "peak_kind": f"{peak_kind} copy bandwidth (burst: kernel timed alone)",
-                         "traffic": None, "bytes_per_launch": dom["bytes_per_launch"],
+                         "traffic": ADJ_TRAFFIC_256 if shape == SHAPE else None,
+                         "traffic_source": "ncu capture of a window-middle adjoint step at 256^3 "
+                                           "(profiles/adj_tma_kernel_256cubed.md)",
+                         "bytes_per_launch": dom["bytes_per_launch"],
                          "timing": f"CUDA events around {nprof} back-to-back launches"},
             "kernels": kernels,
             "stencil": {"cell_updates_per_s": C / (kernels["forward"]["ms_per_launch"] / 1e3),
