@@ -130,9 +130,10 @@ def test_energy_conserved_on_gpu():
 def test_adjoint_identity_on_gpu():
     """<J dc, r> = <dc, J^T r> with the FP32 kernels (incremental forward against the
     adjoint sweep).  A seeded residual, band-limited in time as a data misfit is, must
-    meet 1e-5.  White noise at every sample makes both sweeps carry rough fields whose
-    FP32 rounding adds up over the 200 steps to about 1e-5 (draw-dependent), so that
-    case is held to 1e-4."""
+    meet 1e-5.  A white-noise residual is nearly orthogonal to J dc, so <J dc, r> is a
+    small difference of large terms: the same FP32 rounding of the two sweeps is a larger
+    part of it (draw-dependent, about 1e-5), and that case is held to 1e-4.  Both are
+    also held to 1e-6 of |J dc| |r|, the size of the terms that cancel."""
     from paper_2304_04781_gb300 import aewave
     prob, c, _ = setup((32, 32, 32), 200, 16, seed=0)
     s = solver(prob)
@@ -145,14 +146,20 @@ def test_adjoint_identity_on_gpu():
     w = white.permute(1, 2, 0).reshape(-1, 1, d.shape[0])
     smooth = torch.nn.functional.conv1d(w, torch.full((1, 1, 9), 1.0 / 9, device="cuda"), padding=4)
     smooth = smooth.reshape(d.shape[1], d.shape[2], d.shape[0]).permute(2, 0, 1)
-    for r, tol in ((smooth, 1e-5), (white, 1e-4)):
+    for name, r, tol in (("smooth", smooth, 1e-5), ("white", white, 1e-4)):
         r = (r * d.abs().max()).contiguous()
         r[0] = 0
         _, JTr = s.gradient(cc, (d - r).contiguous())
         Jdc = s.jvp(dc)
         lhs = aewave.dot(Jdc, r)
         rhs = aewave.dot(dc, JTr)
+        # the mismatch against |J dc| |r|: FP32 rounding of the two sweeps, whatever the
+        # cancellation in <J dc, r> (cos) that a white residual brings
+        nrm = float(torch.linalg.vector_norm(Jdc.double()) * torch.linalg.vector_norm(r.double()))
+        print(f"adjoint identity ({name} residual): rel {abs(lhs - rhs) / abs(lhs):.2e}, "
+              f"cos {abs(lhs) / nrm:.2e}, mismatch / (|J dc| |r|) {abs(lhs - rhs) / nrm:.2e}")
         assert abs(lhs - rhs) <= tol * abs(lhs), (tol, lhs, rhs)
+        assert abs(lhs - rhs) <= 1e-6 * nrm
 
 
 def test_gradient_matches_central_differences_through_autograd():
