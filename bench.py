@@ -210,31 +210,41 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- CPU oracle
-def cpu_sample(shape, nt, steps_in_sample=1):
-    """Time the FP64 oracle on a bounded sample of the same workload: `steps_in_sample`
-    forward steps (with the codec encode of each state), then as many adjoint steps
-    (with the decode); scaled to gradients/hour for nt steps."""
+def cpu_sample(shape, nt, codec="time"):
+    """Time the FP64 oracle on a bounded sample of the same workload, one step's share:
+    one forward step, the codec work of one step, one adjoint step; scaled to
+    gradients/hour for nt steps.  The codec work of a step is, for the time codec, the
+    encode and decode of a sixteenth of a window's vectors (one window holds 16 steps),
+    and for the space codec the encode and decode of the step's state.  Returns
+    (gradients/hour, seconds, description)."""
     from oracle import codec as C
     from oracle import wave as W
     from paper_2304_04781_gb300 import inputs
-    rec = inputs.receiver_grid(shape[2], shape[1], NREC)
-    prob = W.Problem(shape=tuple(shape), h=H, nt=steps_in_sample, rec=rec)
+    nz, ny, nx = shape
+    rec = inputs.receiver_grid(nx, ny, NREC)
+    prob = W.Problem(shape=tuple(shape), h=H, nt=1, rec=rec)
     c = inputs.velocity_model(shape, H, seed=2)
-    Wt = inputs.codec_init(seed=0)
     m = c * c
     z = np.zeros(shape)
+    if codec == "time":
+        Wt = inputs.codec_init(seed=0, n_hid=1024, n_lat=512)
+        nvec = (nx // 8) * (ny // 8) * (nz // 2)
+        Y = np.random.default_rng(0).uniform(-1.0, 1.0, (max(nvec // 16, 1), 2048))
+    else:
+        Wt = inputs.codec_init(seed=0)
     t0 = time.perf_counter()
-    st = (z, z.copy(), z.copy(), z.copy())
-    states = []
-    for n in range(steps_in_sample):
-        st = W.forward_step(prob, m, *st, -1.0)
-        states.append(st)
-    ehat = [C.roundtrip_e(Wt, s) for s in states]
-    resid = np.zeros((steps_in_sample + 1, prob.nrec, 3))
-    W.adjoint(prob, c, lambda n: ehat[n], resid)
+    st = W.forward_step(prob, m, z, z.copy(), z.copy(), z.copy(), -1.0)
+    if codec == "time":
+        C.decode(Wt, C.encode(Wt, Y))
+        e_hat = st[0]
+    else:
+        e_hat = C.roundtrip_e(Wt, st)
+    W.adjoint(prob, c, lambda n: e_hat, np.zeros((2, prob.nrec, 3)))
     dt = time.perf_counter() - t0
-    per_step = dt / steps_in_sample
-    return 3600.0 / (per_step * nt), dt
+    what = ("one FP64 forward step + encode/decode of 1/16 of a window's vectors + one adjoint "
+            "step" if codec == "time" else
+            "one FP64 forward step + encode/decode of its state + one adjoint step")
+    return 3600.0 / (dt * nt), dt, f"{what} at the full grid ({dt:.1f} s), scaled to {nt} steps"
 
 
 def run_reference(args):
@@ -244,7 +254,7 @@ def run_reference(args):
     shape, nt = tuple(args.shape), args.nt
     vals = []
     for i in range(args.warmup + args.steps):
-        v, _ = cpu_sample(shape, nt)
+        v, _, what = cpu_sample(shape, nt, args.codec)
         if i >= args.warmup:
             vals.append(v)
     v = float(np.mean(vals))
@@ -255,8 +265,7 @@ def run_reference(args):
         "ms_per_step": 3600e3 / v, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload(shape, nt),
         "cpu_baseline": {"value": v, "unit": "gradients/hour", "cores": cores, "kind": "oracle",
-                         "sample": "per step: one FP64 forward step + encode/decode of its state + one adjoint step "
-                                   "at the full grid, scaled to nt steps"},
+                         "sample": what},
         "e2e": {"value": v, "unit": "gradients/hour", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -526,10 +535,9 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        v, secs = cpu_sample(shape, nt)
+        v, secs, what = cpu_sample(shape, nt, args.codec)
         cpu = {"value": v, "unit": "gradients/hour", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"one FP64 forward step + encode/decode + one adjoint step at the full grid "
-                         f"({secs:.1f} s), scaled to {nt} steps"}
+               "sample": what}
 
     if rank == 0:
         dom = kernels["adjoint"]
