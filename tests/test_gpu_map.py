@@ -175,3 +175,49 @@ def test_dias_subspace_matches_oracle():
     sv = np.linalg.svd(W1g @ W1_ref.T, compute_uv=False)
     print(f"DIAS eigenvalues {lam[:r]}, subspace cosines {sv}")
     assert sv.min() > 1 - 1e-4
+
+
+def test_newton_cg_with_checkpointing_equals_full_storage_bitwise():
+    # revolve's gradient and HVP equal full storage's bit for bit, and its trial
+    # gradients run the adjoint half too (the gate tests the misfit at the end): the
+    # Newton iterates must agree exactly
+    prob, c0, d_obs = _map_case()
+    kw = dict(alpha=1e-10, theta=6400.0, newton_iters=2, cg_max=6)
+    out = []
+    for storage, extra in (("full", {}), ("revolve", {"n_checkpoints": 6})):
+        s = solver(prob, storage=storage, **extra)
+        c = cuda(c0)
+        hist = s.newton_cg(c, cuda(d_obs), cuda(c0), **kw)
+        out.append((host(c), hist))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]
+
+
+def test_newton_cg_with_the_time_codec_tracks_full_storage():
+    # the compressed history (a code fitted to this run's own windows) in every gradient,
+    # trial gradient (stopped after its forward solve when the misfit fails) and HVP
+    from oracle import codec_time as CT
+    prob, c0, _ = setup((32, 32, 32), 96, 16, seed=2)
+    c_true = inputs.bump_model(c0, prob.h, amp=0.1).astype(np.float32).astype(np.float64)
+    d_obs, _, _ = W.forward(prob, c_true)
+    _, states = W.forward_states(prob, c0)
+    e_hist = [st[0] for st in states]
+    Y = []
+    for tb in range(CT.n_windows(prob.nt)):
+        X = CT.window_vectors(e_hist, prob.shape, tb)
+        Y.append(CT.normalise(X, CT.vector_scales(X)))
+    Wt = {k: v.astype(np.float32) for k, v in CT.pca_codec(np.concatenate(Y), 512).items()}
+    kw = dict(alpha=1e-10, theta=6400.0, newton_iters=3, cg_max=6)
+    ae = solver(prob, storage="ae", codec="time")
+    ae.codec_set(Wt)
+    c_ae = cuda(c0)
+    h_ae = ae.newton_cg(c_ae, cuda(d_obs), cuda(c0), **kw)
+    fu = solver(prob, storage="full")
+    c_fu = cuda(c0)
+    h_fu = fu.newton_cg(c_fu, cuda(d_obs), cuda(c0), **kw)
+    assert [h["cg_iters"] for h in h_ae] == [h["cg_iters"] for h in h_fu]
+    assert h_ae[-1]["cost"] < 0.5 * h_ae[0]["cost"]
+    err = relerr(host(c_ae) - c0, host(c_fu) - c0)
+    print(f"Newton-CG, time codec vs full storage: update {err:.2e}; costs "
+          f"{[h['cost'] for h in h_ae]} vs {[h['cost'] for h in h_fu]}")
+    assert err < 2e-2
