@@ -95,7 +95,9 @@ def parse():
     p.add_argument("--dias-samples", type=int, default=30)
     p.add_argument("--dias-rank", type=int, default=5)
     p.add_argument("--dias-iters", type=int, default=2)
-    p.add_argument("--map-ref", default="full", choices=["full", "none"])
+    p.add_argument("--map-ref", default="full", choices=["full", "revolve", "none"],
+                   help="MAP reference: full storage, 20-slot checkpointing (exact states "
+                        "where full storage does not fit) or none")
     p.add_argument("--map-cmax", type=float, default=3000.0,
                    help="MAP / DIAS: the speed that sets dt (stability bound 1.155 x this)")
     p.add_argument("--src-sigma", type=float, default=50.0,
@@ -833,10 +835,13 @@ def run_map(args):
     c_ae_h = c_ae.cpu()
     del ae
     torch.cuda.empty_cache()
-    if args.map_ref == "full":
-        full = aewave.Solver(shape, H, nt, rec, storage="full", f0=args.f0, cmax=args.map_cmax,
-                             src_sigma=args.src_sigma)
+    if args.map_ref != "none":
+        kw_ref = {"storage": "full"} if args.map_ref == "full" else {"storage": "revolve",
+                                                                     "n_checkpoints": 20}
+        full = aewave.Solver(shape, H, nt, rec, f0=args.f0, cmax=args.map_cmax,
+                             src_sigma=args.src_sigma, **kw_ref)
         c_full, out["map_full"] = solve(full)
+        out["map_full"]["storage"] = args.map_ref
         du_ref = (c_full.cpu() - c0.cpu()).double()
         out["map_update_rel_diff"] = float(torch.linalg.vector_norm(c_ae_h.double() - c0.cpu().double() - du_ref)
                                            / torch.linalg.vector_norm(du_ref))
