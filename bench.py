@@ -777,6 +777,9 @@ def run_map(args):
     apply_ms = a.elapsed_time(b) / 20
     del y1
     sigma_n = args.noise_rel * float(d_obs[1:].double().pow(2).mean().sqrt())
+    if not sigma_n > 0:
+        raise SystemExit("the observed data are zero: the wave does not reach the receivers "
+                         "within nt steps (raise --nt)")
     alpha = alpha_s * sigma_n
     out = {"config": dict(workload(shape, nt, args.nrec, n_lat, args.codec), f0_hz=args.f0,
                           norm=args.norm, act=args.act, dt_cmax=args.map_cmax, dt_s=ae.dt,
