@@ -315,10 +315,13 @@ def jacobian_transpose(p: Problem, c: np.ndarray, r: np.ndarray,
 
 
 def hessvec_gn(p: Problem, c: np.ndarray, dc: np.ndarray,
-               e_of: Callable[[int], np.ndarray]) -> np.ndarray:
-    """Gauss-Newton Hessian-vector product J_F^T J_F dc (incremental fwd + adjoint)."""
+               e_of: Callable[[int], np.ndarray],
+               e_adj_of: Optional[Callable[[int], np.ndarray]] = None) -> np.ndarray:
+    """Gauss-Newton Hessian-vector product J_F^T J_F dc (incremental fwd + adjoint).
+    e_adj_of (default e_of) is the forward strain history the incremental adjoint reads,
+    for histories stored at a different precision for the adjoint-type sweeps."""
     dd = incremental_forward(p, c, dc, e_of)
-    return jacobian_transpose(p, c, dd, e_of)
+    return jacobian_transpose(p, c, dd, e_adj_of if e_adj_of is not None else e_of)
 
 
 def incremental_forward_states(p: Problem, c: np.ndarray, dc: np.ndarray,

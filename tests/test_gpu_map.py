@@ -221,3 +221,27 @@ def test_newton_cg_with_the_time_codec_tracks_full_storage():
     print(f"Newton-CG, time codec vs full storage: update {err:.2e}; costs "
           f"{[h['cost'] for h in h_ae]} vs {[h['cost'] for h in h_fu]}")
     assert err < 2e-2
+
+
+def test_argument_errors_of_the_map_calls():
+    import torch
+    from paper_2304_04781_gb300.aewave import AewError
+    prob, c0, d_obs = _map_case()
+    s = solver(prob, storage="full")
+    c, d, q0 = cuda(c0), cuda(d_obs), cuda(c0)
+    n = c0.size
+    noise = torch.zeros((2, n), device="cuda")
+    with pytest.raises(AewError, match="AEW_E_ARG"):           # r > N
+        s.dias_subspace(c, d, noise, 1.0, 100.0, 3)
+    with pytest.raises(AewError, match="AEW_E_ARG"):           # N > 64
+        s.dias_subspace(c, d, torch.zeros((65, n), device="cuda"), 1.0, 100.0, 2)
+    with pytest.raises(AewError, match="AEW_E_ARG"):           # r > 32 rows of W1
+        s.newton_cg(c, d, q0, 1e-10, 6400.0, W1=torch.zeros((33, n), device="cuda"))
+    buf = torch.zeros(n + 1, device="cuda")
+    with pytest.raises(AewError, match="16-byte aligned"):     # a vector off by one float
+        s.prior_solve(buf[1:].view(prob.shape), 1.0, 100.0)
+    with pytest.raises(AewError, match="AEW_E_ARG"):
+        s.newton_cg(c, d, q0, 1e-10, 6400.0, eta_max=0.0)
+    # the handle stays usable after the errors
+    J, _ = s.gradient(c, d)
+    assert J > 0

@@ -327,3 +327,32 @@ def test_minmax_history_with_a_code_exact_on_its_data():
     # mostly squeezed under the floor of the range: the vectors are not scaled to [0, 1]
     mn, r = CT.minmax_scales(CT.window_vectors(e_hist, prob.shape, 1))
     assert np.mean(r == CT.BETA) > 0.5
+
+
+def test_adjoint_history_rounds_to_bf16_and_its_gradient_stays_close():
+    """The adjoint-type sweeps read the decoded strain as BF16 (R34): values already in
+    BF16 pass unchanged, a value halfway between two BF16 numbers goes to the even one,
+    e^0 stays exactly 0, and the gradient computed from the BF16 history differs from the
+    FP64 one by no more than BF16's relative step (2^-8) bounds."""
+    one = np.array([1.0, 1.0 + 2.0 ** -7, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, -2.5, 0.0])
+    out = CT.adjoint_history([one])[0]
+    np.testing.assert_array_equal(out, [1.0, 1.0 + 2.0 ** -7, 1.0, 1.0 + 2 * 2.0 ** -7, -2.5, 0.0])
+    prob, c = _small_problem(nt=40)
+    d, states = W.forward_states(prob, c)
+    e_hist = [st[0] for st in states]
+    eb = CT.adjoint_history(e_hist)
+    assert not np.any(eb[0])
+    rel = max(float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)) for a, b in zip(eb[1:], e_hist[1:]))
+    assert rel <= 2.0 ** -8
+    d_obs, _, _ = W.forward(prob, inputs.bump_model(c))
+    _, g_full, _ = W.gradient(prob, c, d_obs)
+    _, g_b, _ = W.gradient(prob, c, d_obs, e_of=lambda n: eb[n])
+    err = np.linalg.norm(g_b - g_full) / np.linalg.norm(g_full)
+    assert 0 < err < 2.0 ** -8
+    # the Gauss-Newton HVP with a separate adjoint history: the default reads one history
+    dc = inputs.direction(prob.shape, prob.h, seed=3)
+    H1 = W.hessvec_gn(prob, c, dc, lambda n: e_hist[n])
+    H2 = W.hessvec_gn(prob, c, dc, lambda n: e_hist[n], e_adj_of=lambda n: e_hist[n])
+    np.testing.assert_array_equal(H1, H2)
+    H3 = W.hessvec_gn(prob, c, dc, lambda n: e_hist[n], e_adj_of=lambda n: eb[n])
+    assert 0 < np.linalg.norm(H3 - H1) / np.linalg.norm(H1) < 2.0 ** -8
