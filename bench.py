@@ -79,7 +79,8 @@ def parse():
                    help="compare only the first k HVPs with the reference (0: all)")
     p.add_argument("--kernel", default="",
                    choices=["", "forward", "forward_pack", "adjoint", "incremental",
-                            "encode_window", "decode_window"],
+                            "encode_window", "decode_window", "adjoint_bf16",
+                            "decode_window_bf16"],
                    help="instead of the benchmark: time one hot-path kernel alone "
                         "(aew_profile_steps) on an AE handle of --shape, for profiling")
     p.add_argument("--launches", type=int, default=16)
@@ -292,6 +293,7 @@ BYTES_PER_NODE = {
     "forward_pack": 38.0,   # + the output strain as BF16 into its window slot
     "adjoint": 50.0,        # read mu, lam (3), m, e^n, FP32 window acc; write mu, lam, acc;
                             # + 16 B FP64 read-modify-write / 8
+    "adjoint_bf16": 48.0,   # the same with e^n read as BF16 (the time codec's sweeps)
     "incremental": 44.0,    # forward + dm, e^n
 }
 
@@ -426,7 +428,8 @@ def run_ours(args):
     # ---- the hot-path kernels alone (CUDA events around back-to-back launches)
     nprof = min(nt, 200)
     kernels = {}
-    kinds = ["forward", "adjoint", "incremental"] + (["forward_pack"] if args.codec == "time" else [])
+    kinds = ["forward", "adjoint", "incremental"] + (["forward_pack", "adjoint_bf16"]
+                                                     if args.codec == "time" else [])
     for kind in kinds:
         kms = ae.profile(c, kind, nprof)
         b = BYTES_PER_NODE[kind] * C
@@ -436,15 +439,17 @@ def run_ours(args):
         fl = codec_flops_per_window(ae.nvec, n_lat, ae.n_hid)
         sms = torch.cuda.get_device_properties(local).multi_processor_count
         share = (sms // 2) / sms      # the codec GEMMs' CTA cap beside a stencil step
-        for kind in ("encode_window", "decode_window"):
-            kms = ae.profile(c, kind, 8)
+        for kind, prof in (("encode_window", "encode_window"), ("decode_window", "decode_window_bf16")):
+            kms = ae.profile(c, prof, 8)
             tf = fl[kind] / kms / 1e9
             kernels[kind] = {"ms_per_launch": kms, "flops_per_launch": fl[kind],
                              "achieved_tflops": tf, "ctas": sms // 2,
                              "frac_of_bf16_burst_share": tf / (tf_peak * share),
                              "note": f"both layers of one window (two tcgen05 GEMMs on SM pairs) "
                                      f"on {sms // 2} CTAs, the cap they run with beside the "
-                                     f"stencil; frac against that share of the measured peak"}
+                                     f"stencil; frac against that share of the measured peak"
+                                     + ("; the decoder writes BF16 strain, as for the adjoint "
+                                        "sweeps" if kind == "decode_window" else "")}
     del ae
     torch.cuda.empty_cache()
 
@@ -542,7 +547,7 @@ def run_ours(args):
                "sample": what}
 
     if rank == 0:
-        dom = kernels["adjoint"]
+        dom = kernels["adjoint_bf16" if args.codec == "time" else "adjoint"]
         line = {
             "metric": METRIC, "value": value, "unit": "gradients/hour", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
@@ -555,11 +560,13 @@ def run_ours(args):
                            else "one shot on one GPU"),
             "accuracy": accuracy,
             "roofline": {"kernel": "adjoint step (adj_tma_kernel), the longest per-step kernel "
-                                   "of the AE gradient", "bound": "hbm",
+                                   "of the AE gradient" + (", reading its decoded strain as BF16 "
+                                                           "(48 B/node)" if args.codec == "time"
+                                                           else ""), "bound": "hbm",
                          "achieved": dom["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
                          "frac": dom["achieved_gbs"] / hbm_peak,
                          "peak_kind": f"{peak_kind} copy bandwidth (burst: kernel timed alone)",
-                         "traffic": ADJ_TRAFFIC_256 if shape == SHAPE else None,
+                         "traffic": ADJ_TRAFFIC_256 if shape == SHAPE and args.codec != "time" else None,
                          "traffic_source": "ncu capture of a window-middle adjoint step at 256^3 "
                                            "(profiles/adj_tma_kernel_256cubed.md)",
                          "bytes_per_launch": dom["bytes_per_launch"],

@@ -424,7 +424,8 @@ class Solver:
         self._check(lib().aew_test_wait_timeout(self._h, int(wait_ns), _stream()))
 
     PROFILE_KINDS = {"forward": 0, "forward_pack": 1, "adjoint": 2, "incremental": 3,
-                     "encode_window": 4, "decode_window": 5}
+                     "encode_window": 4, "decode_window": 5, "adjoint_bf16": 6,
+                     "decode_window_bf16": 7}
 
     def profile(self, c: torch.Tensor, kind: str, nsteps: int) -> float:
         """aew_profile_steps: mean device ms per launch of one hot-path kernel."""

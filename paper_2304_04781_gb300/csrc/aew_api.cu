@@ -256,7 +256,8 @@ int incr_step(aew_handle* h, float* const in[4], float* const out[4], const floa
 // e^n dt q into (acc32, acc64); qout / qin + dm2: the full Newton HVP's coupling
 int adj_step_x(aew_handle* h, int n, float* const in[4], float* const out[4],
                const float* resid, const float* en, float* acc32, double* acc64, float* qout,
-               const float* qin, const float* dm2, cudaStream_t s) {
+               const float* qin, const float* dm2, cudaStream_t s,
+               const uint16_t* en16 = nullptr) {
   aew::AdjStep a{};
   a.m = h->m;
   a.mu = in[0];
@@ -268,6 +269,7 @@ int adj_step_x(aew_handle* h, int n, float* const in[4], float* const out[4],
   a.ly1 = out[2];
   a.lz1 = out[3];
   a.en = en;
+  a.en16 = en16;
   a.acc32 = acc32;
   a.acc64 = acc64;
   a.qout = qout;
@@ -610,15 +612,17 @@ int encode_window(aew_handle* h, int tb, cudaStream_t s) {
   return AEW_OK;
 }
 
-// decoder of window tb into its 16 strain slices edt[tb % 2]
-int decode_window(aew_handle* h, int tb, cudaStream_t s) {
+// decoder of window tb into its 16 strain slices edt[tb % 2]: FP32, or BF16 for the
+// adjoint-type sweeps (their e^n box then carries half the bytes; the incremental
+// forward's halo boxes stay FP32)
+int decode_window(aew_handle* h, int tb, cudaStream_t s, bool bf16 = false) {
   const size_t nv = nvec_of(h);
   const bool mm = aew::codec_minmax(h->codec);
   cudaError_t e = aew::codec_decode_window(h->codec, h->lat + (size_t)tb * nv * h->cfg.n_lat,
                                            h->vmx + (size_t)tb * nv, h->cfg.nx, h->cfg.ny,
                                            h->cfg.nz, h->edt[tb & 1], s, h->overlap_ctas,
                                            mm ? h->wmn + (size_t)tb * nv : nullptr,
-                                           mm ? h->wr + (size_t)tb * nv : nullptr);
+                                           mm ? h->wr + (size_t)tb * nv : nullptr, bf16);
   if (e != cudaSuccess) return cuda_fail(h, e, "codec_decode_window");
   h->stats.kernel_launches += 2;
   return AEW_OK;
@@ -627,6 +631,12 @@ int decode_window(aew_handle* h, int tb, cudaStream_t s) {
 // decoded strain e^n (n >= 1) of the window being read
 const float* window_e(aew_handle* h, int n) {
   return n >= 1 ? h->edt[(n / aew::kTSteps) & 1] + (size_t)(n % aew::kTSteps) * h->C : nullptr;
+}
+// the same, decoded as BF16
+const uint16_t* window_e16(aew_handle* h, int n) {
+  return n >= 1 ? reinterpret_cast<const uint16_t*>(h->edt[(n / aew::kTSteps) & 1]) +
+                      (size_t)(n % aew::kTSteps) * h->C
+                : nullptr;
 }
 
 // Adjoint sweep with the time codec: entering window tb (in reverse), the decoder of
@@ -638,7 +648,7 @@ int time_adjoint_sweep(aew_handle* h, const float* resid, cudaStream_t s) {
   int rc;
   if ((rc = begin_adjoint(h, s))) return rc;
   if ((rc = join(h, s, h->side, h->ev_sync))) return rc;
-  if ((rc = decode_window(h, W - 1, h->side))) return rc;
+  if ((rc = decode_window(h, W - 1, h->side, true))) return rc;
   AEW_CK(cudaEventRecord(h->ev_b[(W - 1) & 1], h->side));
   int acur = 0;
   for (int n = nt - 1; n >= 0; --n) {
@@ -646,12 +656,14 @@ int time_adjoint_sweep(aew_handle* h, const float* resid, cudaStream_t s) {
     if (n == nt - 1 || n % T == T - 1) {
       if (tb >= 1) {
         if (tb + 1 <= W - 1) AEW_CK(cudaStreamWaitEvent(h->side, h->ev_a[(tb + 1) & 1], 0));
-        if ((rc = decode_window(h, tb - 1, h->side))) return rc;
+        if ((rc = decode_window(h, tb - 1, h->side, true))) return rc;
         AEW_CK(cudaEventRecord(h->ev_b[(tb - 1) & 1], h->side));
       }
       AEW_CK(cudaStreamWaitEvent(s, h->ev_b[tb & 1], 0));
     }
-    if ((rc = adj_step(h, n, acur, resid, window_e(h, n), s))) return rc;
+    if ((rc = adj_step_x(h, n, h->ad[acur], h->ad[acur ^ 1], resid, nullptr, h->acc32, h->acc64,
+                         nullptr, nullptr, nullptr, s, window_e16(h, n))))
+      return rc;
     acur ^= 1;
     if (n % T == 0) AEW_CK(cudaEventRecord(h->ev_a[tb & 1], s));
   }
@@ -1775,11 +1787,13 @@ int aew_codec_init_pca(aew_handle* h, const uint16_t* vectors_dev, const float* 
 int aew_profile_steps(aew_handle* h, const float* c_dev, int kind, int nsteps, double* ms_host,
                       void* stream) {
   if (!h) return AEW_E_ARG;
-  if (kind < 0 || kind > 5 || nsteps < 1 || !ms_host) return fail(h, AEW_E_ARG, "bad argument");
+  if (kind < 0 || kind > 7 || nsteps < 1 || !ms_host) return fail(h, AEW_E_ARG, "bad argument");
   const bool tw = h->cfg.storage == AEW_AE && h->tcodec;
-  if ((kind == 1 || kind >= 4) && !tw)
+  if ((kind == 1 || kind == 4 || kind == 5 || kind == 7) && !tw)
     return fail(h, AEW_E_CONFIG, "this kernel needs AE storage with the time codec");
-  if (kind >= 4 && !aew::codec_ready(h->codec)) return fail(h, AEW_E_NOCODEC, "codec weights not set");
+  if ((kind == 4 || kind == 5 || kind == 7) && !aew::codec_ready(h->codec))
+    return fail(h, AEW_E_NOCODEC, "codec weights not set");
+  if (kind == 6 && h->cfg.nx % 8) return fail(h, AEW_E_CONFIG, "a BF16 strain field needs nx % 8 == 0");
   h->err.clear();
   cudaStream_t s = S(stream);
   int rc = prepare_c(h, c_dev, s);
@@ -1812,6 +1826,14 @@ int aew_profile_steps(aew_handle* h, const float* c_dev, int kind, int nsteps, d
         break;
       case 5:
         rc = decode_window(h, 0, s);
+        break;
+      case 6:   // the adjoint step reading its strain field as BF16 (time-codec sweeps)
+        rc = adj_step_x(h, nt - 1 - n, h->ad[cur], h->ad[cur ^ 1], h->R, nullptr, h->acc32,
+                        h->acc64, nullptr, nullptr, nullptr, s,
+                        reinterpret_cast<const uint16_t*>(h->st[0][0]));
+        break;
+      case 7:
+        rc = decode_window(h, 0, s, true);
         break;
     }
     cur ^= 1;

@@ -153,6 +153,7 @@ struct EpDecWindow {
   size_t slice;           // nx ny nz
   const double* mn;       // min-max normalisation (else null): offset and range
   const double* rr;
+  bool bf16;              // write the slices as BF16 ([16][nz][ny][nx] uint16 from e)
   __device__ __forceinline__ void operator()(long long rw, int col, const float (&v)[32]) const {
     if (rw >= M) return;
     const int r = (int)rw;
@@ -178,9 +179,16 @@ struct EpDecWindow {
         const float val = fmaf(v[yy * 8 + x] + bv[x], sc, off);
         o[x] = (yb || (x == 0 && xlo) || (x == 7 && xhi)) ? 0.f : val;
       }
-      float4* dst = reinterpret_cast<float4*>(base + (size_t)yy * nx);
-      dst[0] = make_float4(o[0], o[1], o[2], o[3]);
-      dst[1] = make_float4(o[4], o[5], o[6], o[7]);
+      if (bf16) {   // the same element index in the BF16 view: one 16-byte store
+        const size_t idx = (size_t)(base - e) + (size_t)yy * nx;
+        *reinterpret_cast<uint4*>(reinterpret_cast<uint16_t*>(e) + idx) =
+            make_uint4(gemm::pack_bf16(o[0], o[1]), gemm::pack_bf16(o[2], o[3]),
+                       gemm::pack_bf16(o[4], o[5]), gemm::pack_bf16(o[6], o[7]));
+      } else {
+        float4* dst = reinterpret_cast<float4*>(base + (size_t)yy * nx);
+        dst[0] = make_float4(o[0], o[1], o[2], o[3]);
+        dst[1] = make_float4(o[4], o[5], o[6], o[7]);
+      }
     }
   }
 };
@@ -922,7 +930,7 @@ cudaError_t codec_encode_window(Codec* c, uint16_t* raw, const unsigned* vmax,
 
 cudaError_t codec_decode_window(Codec* c, const uint16_t* lat, const unsigned* vmax, int nx,
                                 int ny, int nz, float* e_out, cudaStream_t s, int ctas,
-                                const double* mn, const double* rr) {
+                                const double* mn, const double* rr, bool bf16_out) {
   if (c->norm == 1 && (!mn || !rr)) return cudaErrorInvalidValue;
   const int NBx = nx / 8, NBy = ny / 8, NBz = nz / 2;
   const long long nvec = (long long)NBx * NBy * NBz;
@@ -931,7 +939,7 @@ cudaError_t codec_decode_window(Codec* c, const uint16_t* lat, const unsigned* v
   if (e != cudaSuccess) return e;
   const int nh = c->n_hid;
   EpDecWindow ep{c->w[7], vmax, e_out, nx, ny, nz, NBx, NBy, nvec, (size_t)nx * ny * nz,
-                 c->norm == 1 ? mn : nullptr, c->norm == 1 ? rr : nullptr};
+                 c->norm == 1 ? mn : nullptr, c->norm == 1 ? rr : nullptr, bf16_out};
   if (pair_wide(c))
     return gemm2::launch<true>(nvec, kNIn, nh, gemm::Mat{c->H, nvec, nh},
                                gemm::Mat{c->W4t, kNIn, nh}, ep, c->err, s, ctas_of(c, ctas));

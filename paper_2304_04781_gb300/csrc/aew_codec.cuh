@@ -72,9 +72,12 @@ cudaError_t codec_encode_window(Codec* c, uint16_t* raw, const unsigned* vmax,
                                 int ctas = 0, double* mn = nullptr, double* rr = nullptr);
 // Decode one window into 16 strain slices e_out[t][nz][ny][nx] (slice stride nx ny nz):
 // e = s_v * decoded value (min-max: decoded value * rr + mn), 0 on boundary nodes.
+// bf16_out: the slices as BF16 instead ([16][nz][ny][nx] uint16 from e_out), for the
+// adjoint-type sweeps.
 cudaError_t codec_decode_window(Codec* c, const uint16_t* lat, const unsigned* vmax, int nx,
                                 int ny, int nz, float* e_out, cudaStream_t s, int ctas = 0,
-                                const double* mn = nullptr, const double* rr = nullptr);
+                                const double* mn = nullptr, const double* rr = nullptr,
+                                bool bf16_out = false);
 // The paper's min-max normalisation of raw BF16 window vectors (in place allowed):
 // y = (x - min) / r, r = max(max - min, beta); offsets and ranges to mn / rr (FP64).
 cudaError_t window_minmax(const uint16_t* raw, long long nvec, double beta, uint16_t* out,

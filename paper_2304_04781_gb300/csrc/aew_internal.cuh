@@ -80,6 +80,7 @@ struct AdjStep {
   float* ly1;
   float* lz1;
   const float* en;     // forward strain e^n (null: zero)
+  const uint16_t* en16;  // or e^n as BF16 (a decoded window; nx a multiple of 8)
   float* acc32;        // FP32 window accumulator
   double* acc64;       // FP64 accumulator
   int acc_mode;        // bit0: first step of a window, bit1: last step of a window

@@ -492,6 +492,7 @@ __global__ void __launch_bounds__(NTHR, (INCR || PACK) ? 2 : 3)
 // ---------------------------------------------------------------------------------
 struct AdjFlags {
   bool en, w;   // e^n present; FP32 window accumulator read
+  bool enb;     // e^n given as BF16 (its box carries half the bytes)
 };
 
 __device__ void adj_issue(const AdjMaps& mp, const Ring& r, int p, int kbeg, int kend, int nz,
@@ -502,7 +503,9 @@ __device__ void adj_issue(const AdjMaps& mp, const Ring& r, int p, int kbeg, int
   const bool full = p >= kbeg && p < kend;
   const bool below = p == kbeg - 1;
   if (inside)
-    bytes = kTxXY + (full ? kTxX + kTxYm + kTxO * (2 + (f.en ? 1 : 0) + (f.w ? 1 : 0)) : 0) +
+    bytes = kTxXY +
+            (full ? kTxX + kTxYm + kTxO * (2 + (f.w ? 1 : 0)) + (f.en ? (f.enb ? kTxO / 2 : kTxO) : 0)
+                  : 0) +
             (below ? kTxO : 0);
   gemm::mbar_expect_tx(bar, bytes);
   if (!inside) return;
@@ -558,7 +561,7 @@ __global__ void __launch_bounds__(NTHR, 2)
   const float dth = a.dth;
   const bool has_r = a.resid != nullptr && a.krec >= 0;
   const int mode = a.acc_mode;
-  const AdjFlags fl{a.en != nullptr, !(mode & kAccFirst)};
+  const AdjFlags fl{a.en != nullptr || a.en16 != nullptr, !(mode & kAccFirst), a.en16 != nullptr};
 
   Ring r;
   r.base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) &
@@ -626,7 +629,14 @@ __global__ void __launch_bounds__(NTHR, 2)
     float4 ly_m = reinterpret_cast<const float4*>(sc + AdjLayout::LY)[qY - kW4];
     float4 lz_c = reinterpret_cast<const float4*>(sc + AdjLayout::LZ)[qO];
     const float4 m4 = reinterpret_cast<const float4*>(sc + AdjLayout::M)[qO];
-    const float4 en4 = fl.en ? reinterpret_cast<const float4*>(sc + AdjLayout::EN)[qO] : z4();
+    float4 en4 = z4();
+    if (fl.enb) {   // 4 BF16 values, element 0 in the low half
+      const uint2 b = reinterpret_cast<const uint2*>(sc + AdjLayout::EN)[qO];
+      en4 = make_float4(__uint_as_float(b.x << 16), __uint_as_float(b.x & 0xffff0000u),
+                        __uint_as_float(b.y << 16), __uint_as_float(b.y & 0xffff0000u));
+    } else if (fl.en) {
+      en4 = reinterpret_cast<const float4*>(sc + AdjLayout::EN)[qO];
+    }
     const float4 w_c = fl.w ? reinterpret_cast<const float4*>(sc + AdjLayout::W)[qO] : z4();
 
     const bool rplane = has_r && k == a.krec;
@@ -745,6 +755,20 @@ bool field_map(CUtensorMap* map, const float* base, int nx, int ny, int nz, int 
   const cuuint32_t es[3] = {1, 1, 1};
   return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box,
              es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// the same for a BF16 field (nx a multiple of 8: the row stride a multiple of 16 bytes;
+// the boxes start at x multiples of 128)
+bool field_map16(CUtensorMap* map, const uint16_t* base, int nx, int ny, int nz, int bx, int by) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = gemm::tensor_map_encoder();
+  if (!enc || !base || (reinterpret_cast<uintptr_t>(base) & 15) || (nx % 8)) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)nx * 2, (cuuint64_t)nx * ny * 2};
+  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t*>(base), dims, strides,
+             box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -876,7 +900,9 @@ cudaError_t launch_adj_step(const AdjStep& a, cudaStream_t s) {
             field_map(&mp.ly, a.ly, nx, ny, nz, kTXW, TY + 1) &&
             field_map(&mp.lz, a.lz, nx, ny, nz, kTXW, TY) &&
             field_map(&mp.m, a.m, nx, ny, nz, kTXW, TY);
+  if (a.en && a.en16) return cudaErrorInvalidValue;
   if (ok && a.en) ok = field_map(&mp.en, a.en, nx, ny, nz, kTXW, TY);
+  if (ok && a.en16) ok = field_map16(&mp.en, a.en16, nx, ny, nz, kTXW, TY);
   if (ok && !(a.acc_mode & kAccFirst)) ok = field_map(&mp.w, a.acc32, nx, ny, nz, kTXW, TY);
   if (!ok) return cudaErrorInvalidValue;
   if ((a.qin != nullptr) != (a.dm2 != nullptr)) return cudaErrorInvalidValue;
