@@ -40,7 +40,8 @@ METRIC = "gradients/hour at 256^3x2000 steps: AE vs checkpointing; stencil HBM G
 # the current kernel (dram__bytes_read.sum + dram__bytes_write.sum, a window-middle step
 # without the FP64 flush); to be set to None when the kernel changes until it is
 # captured again
-ADJ_TRAFFIC_256 = 768.6e6
+ADJ_TRAFFIC_256 = 768.6e6     # FP32 e^n (full storage / checkpointing)
+ADJ16_TRAFFIC_256 = 665.9e6   # BF16 e^n (the time codec's adjoint sweeps)
 SHAPE = (256, 256, 256)
 NT = 2000
 NREC = 128
@@ -566,9 +567,12 @@ def run_ours(args):
                          "achieved": dom["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
                          "frac": dom["achieved_gbs"] / hbm_peak,
                          "peak_kind": f"{peak_kind} copy bandwidth (burst: kernel timed alone)",
-                         "traffic": ADJ_TRAFFIC_256 if shape == SHAPE and args.codec != "time" else None,
+                         "traffic": ((ADJ16_TRAFFIC_256 if args.codec == "time" else ADJ_TRAFFIC_256)
+                                     if shape == SHAPE else None),
                          "traffic_source": "ncu capture of a window-middle adjoint step at 256^3 "
-                                           "(profiles/adj_tma_kernel_256cubed.md)",
+                                           + ("(profiles/adj_tma_kernel_bf16_256cubed.md)"
+                                              if args.codec == "time" else
+                                              "(profiles/adj_tma_kernel_256cubed.md)"),
                          "bytes_per_launch": dom["bytes_per_launch"],
                          "timing": f"CUDA events around {nprof} back-to-back launches"},
             "kernels": kernels,
