@@ -81,7 +81,7 @@ def parse():
     p.add_argument("--kernel", default="",
                    choices=["", "forward", "forward_pack", "adjoint", "incremental",
                             "encode_window", "decode_window", "adjoint_bf16",
-                            "decode_window_bf16"],
+                            "decode_window_bf16", "incremental_bf16"],
                    help="instead of the benchmark: time one hot-path kernel alone "
                         "(aew_profile_steps) on an AE handle of --shape, for profiling")
     p.add_argument("--launches", type=int, default=16)
@@ -296,6 +296,7 @@ BYTES_PER_NODE = {
                             # + 16 B FP64 read-modify-write / 8
     "adjoint_bf16": 48.0,   # the same with e^n read as BF16 (the time codec's sweeps)
     "incremental": 44.0,    # forward + dm, e^n
+    "incremental_bf16": 42.0,   # the same with e^n read as BF16 (the time codec's GN-HVP)
 }
 
 
@@ -429,7 +430,8 @@ def run_ours(args):
     # ---- the hot-path kernels alone (CUDA events around back-to-back launches)
     nprof = min(nt, 200)
     kernels = {}
-    kinds = ["forward", "adjoint", "incremental"] + (["forward_pack", "adjoint_bf16"]
+    kinds = ["forward", "adjoint", "incremental"] + (["forward_pack", "adjoint_bf16",
+                                                      "incremental_bf16"]
                                                      if args.codec == "time" else [])
     for kind in kinds:
         kms = ae.profile(c, kind, nprof)

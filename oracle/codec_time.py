@@ -187,10 +187,10 @@ def compressed_e_history(W: dict, e_hist, emulate: bool = False, norm: str = "po
     return out
 
 
-def adjoint_history(e_hat):
-    """The decoded strain history as the adjoint-type sweeps (the gradient's adjoint and
-    the Gauss-Newton HVP's incremental adjoint) read it (reading R34): the decoder's FP32
-    output rounded to BF16, round to nearest even.  The incremental forward reads the
+def bf16_history(e_hat):
+    """The decoded strain history as the gradient's adjoint and the Gauss-Newton HVP's
+    incremental forward and incremental adjoint read it (reading R34): the decoder's FP32
+    output rounded to BF16, round to nearest even.  The full-Newton HVP's sweeps read the
     FP32 values themselves."""
     return [C.round_bf16(C.round_fp32(e)) for e in e_hat]
 

@@ -218,7 +218,7 @@ int fwd_step(aew_handle* h, int n, float* const in[4], float* const out[4], cons
 
 int incr_step(aew_handle* h, float* const in[4], float* const out[4], const float* en,
               float* d_row, cudaStream_t s, uint16_t* tpack = nullptr, int tslot = 0,
-              unsigned* vmax = nullptr) {
+              unsigned* vmax = nullptr, const uint16_t* en16 = nullptr) {
   aew::FwdStep a{};
   a.tpack = tpack;
   a.tslot = tslot;
@@ -233,9 +233,10 @@ int incr_step(aew_handle* h, float* const in[4], float* const out[4], const floa
   a.vy1 = out[2];
   a.vz1 = out[3];
   // with e^n = 0 (n = 0) the extra source G(dm e^n) vanishes: plain step, no source
-  const bool incr = en != nullptr;
+  const bool incr = en != nullptr || en16 != nullptr;
   a.dm = incr ? h->dm : nullptr;
   a.ef = en;
+  a.ef16 = en16;
   a.nx = h->cfg.nx;
   a.ny = h->cfg.ny;
   a.nz = h->cfg.nz;
@@ -612,9 +613,9 @@ int encode_window(aew_handle* h, int tb, cudaStream_t s) {
   return AEW_OK;
 }
 
-// decoder of window tb into its 16 strain slices edt[tb % 2]: FP32, or BF16 for the
-// adjoint-type sweeps (their e^n box then carries half the bytes; the incremental
-// forward's halo boxes stay FP32)
+// decoder of window tb into its 16 strain slices edt[tb % 2]: BF16 for the gradient's
+// adjoint and the Gauss-Newton HVP's incremental forward and adjoint (their e^n boxes then
+// carry half the bytes), FP32 for the full-Newton HVP's sweeps and the standalone call
 int decode_window(aew_handle* h, int tb, cudaStream_t s, bool bf16 = false) {
   const size_t nv = nvec_of(h);
   const bool mm = aew::codec_minmax(h->codec);
@@ -1349,19 +1350,20 @@ static int incremental_forward(aew_handle* h, float* dd_out, cudaStream_t s, lon
     // ev_b[w % 2]: window w decoded, ev_a[w % 2]: window w's incremental steps done
     const int W = nwin_of(h), T = aew::kTSteps;
     if ((rc = join(h, s, h->side, h->ev_sync))) return rc;
-    if ((rc = decode_window(h, 0, h->side))) return rc;
+    if ((rc = decode_window(h, 0, h->side, true))) return rc;
     AEW_CK(cudaEventRecord(h->ev_b[0], h->side));
     for (int n = 0; n < nt; ++n) {
       const int tb = n / T;
       if (n % T == 0) {
         if (tb + 1 <= W - 1) {
           if (tb >= 1) AEW_CK(cudaStreamWaitEvent(h->side, h->ev_a[(tb + 1) & 1], 0));
-          if ((rc = decode_window(h, tb + 1, h->side))) return rc;
+          if ((rc = decode_window(h, tb + 1, h->side, true))) return rc;
           AEW_CK(cudaEventRecord(h->ev_b[(tb + 1) & 1], h->side));
         }
         AEW_CK(cudaStreamWaitEvent(s, h->ev_b[tb & 1], 0));
       }
-      if ((rc = incr_step(h, h->ad[cur], h->ad[cur ^ 1], window_e(h, n), drow(h, dd_out, n + 1), s)))
+      if ((rc = incr_step(h, h->ad[cur], h->ad[cur ^ 1], nullptr, drow(h, dd_out, n + 1), s,
+                          nullptr, 0, nullptr, window_e16(h, n))))
         return rc;
       if (n % T == T - 1 || n == nt - 1) AEW_CK(cudaEventRecord(h->ev_a[tb & 1], s));
       cur ^= 1;
@@ -1787,13 +1789,14 @@ int aew_codec_init_pca(aew_handle* h, const uint16_t* vectors_dev, const float* 
 int aew_profile_steps(aew_handle* h, const float* c_dev, int kind, int nsteps, double* ms_host,
                       void* stream) {
   if (!h) return AEW_E_ARG;
-  if (kind < 0 || kind > 7 || nsteps < 1 || !ms_host) return fail(h, AEW_E_ARG, "bad argument");
+  if (kind < 0 || kind > 8 || nsteps < 1 || !ms_host) return fail(h, AEW_E_ARG, "bad argument");
   const bool tw = h->cfg.storage == AEW_AE && h->tcodec;
   if ((kind == 1 || kind == 4 || kind == 5 || kind == 7) && !tw)
     return fail(h, AEW_E_CONFIG, "this kernel needs AE storage with the time codec");
   if ((kind == 4 || kind == 5 || kind == 7) && !aew::codec_ready(h->codec))
     return fail(h, AEW_E_NOCODEC, "codec weights not set");
-  if (kind == 6 && h->cfg.nx % 8) return fail(h, AEW_E_CONFIG, "a BF16 strain field needs nx % 8 == 0");
+  if ((kind == 6 || kind == 8) && h->cfg.nx % 8)
+    return fail(h, AEW_E_CONFIG, "a BF16 strain field needs nx % 8 == 0");
   h->err.clear();
   cudaStream_t s = S(stream);
   int rc = prepare_c(h, c_dev, s);
@@ -1834,6 +1837,10 @@ int aew_profile_steps(aew_handle* h, const float* c_dev, int kind, int nsteps, d
         break;
       case 7:
         rc = decode_window(h, 0, s, true);
+        break;
+      case 8:   // the incremental forward step reading its strain field as BF16
+        rc = incr_step(h, h->ad[cur], h->ad[cur ^ 1], nullptr, nullptr, s, nullptr, 0, nullptr,
+                       reinterpret_cast<const uint16_t*>(h->st[0][0]));
         break;
     }
     cur ^= 1;

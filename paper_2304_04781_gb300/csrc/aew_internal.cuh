@@ -29,6 +29,7 @@ struct FwdStep {
   float* vz1;
   const float* dm;   // incremental only
   const float* ef;   // incremental only: forward strain e^n
+  const uint16_t* ef16;  // or e^n as BF16 (a decoded window; nx a multiple of 8)
   int nx, ny, nz;
   int kc;            // z planes per CTA
   float dth;         // dt / h

@@ -47,6 +47,11 @@ constexpr int kHX = 4;                // x halo width (one float4)
 constexpr int kWE = kTXW + 2 * kHX;   // 136: row width of boxes with an x halo
 constexpr int kW4E = kWE / 4;         // 34 float4 per halo row
 constexpr int kW4 = kTXW / 4;         // 32 float4 per plain row
+// a BF16 e^n box of the incremental forward: an x halo of 8 (16 bytes, TMA's alignment
+// unit) instead of 4, so the row is 144 wide and the FP32 layout's element (r, c) sits at
+// r * 144 + c + 4
+constexpr int kHX16 = 8;
+constexpr int kWE16 = kTXW + 2 * kHX16;
 constexpr uint64_t kWaitNs = 200000000ull;
 constexpr int kMaxStages = 4;
 // PACK: one plane of the CTA's 16 blocks, 4 fields x 8 rows x 8 BF16 each (a 512-byte
@@ -63,6 +68,7 @@ constexpr int kTxXY = kWE * (TY + 2) * 4;   // x halo both sides, y halo both si
 constexpr int kTxX = kWE * TY * 4;          // x halo only
 constexpr int kTxYm = kTXW * (TY + 1) * 4;  // one row below
 constexpr int kTxO = kTXW * TY * 4;         // own nodes only
+constexpr int kTxXY16 = kWE16 * (TY + 2) * 2;   // BF16 e^n of the incremental forward
 // ... and the shared-memory room it takes (128-byte aligned destinations)
 constexpr int al128(int b) { return (b + 127) & ~127; }
 constexpr int kBoxXY = al128(kTxXY);
@@ -190,7 +196,7 @@ struct Ring {
 // fields staged per plane: full planes carry everything, the plane below the chunk
 // e, m (dm, e^n) and vz, the plane above it e, m (dm, e^n); planes outside the grid
 // only complete their barrier phase
-template <bool INCR>
+template <bool INCR, bool EFB>
 __device__ void fwd_issue(const FwdMaps& mp, const Ring& r, int p, int kbeg, int kend, int nz,
                           int x0, int y0) {
   const uint32_t bar = r.bar(p), d = r.sat(p);
@@ -198,15 +204,15 @@ __device__ void fwd_issue(const FwdMaps& mp, const Ring& r, int p, int kbeg, int
   const bool inside = p >= 0 && p < nz;
   const bool full = p >= kbeg && p < kend;
   const bool below = p == kbeg - 1;
-  if (inside) bytes = (INCR ? 4 : 2) * kTxXY + (full ? kTxX + kTxYm + kTxO : 0) +
-                      (below ? kTxO : 0);
+  if (inside) bytes = (INCR ? (EFB ? 3 * kTxXY + kTxXY16 : 4 * kTxXY) : 2 * kTxXY) +
+                      (full ? kTxX + kTxYm + kTxO : 0) + (below ? kTxO : 0);
   gemm::mbar_expect_tx(bar, bytes);
   if (!inside) return;
   tma3(d + FwdLayout::E, &mp.e, x0 - kHX, y0 - 1, p, bar);
   tma3(d + FwdLayout::M, &mp.m, x0 - kHX, y0 - 1, p, bar);
   if (INCR) {
     tma3(d + FwdLayout::DM, &mp.dm, x0 - kHX, y0 - 1, p, bar);
-    tma3(d + FwdLayout::EF, &mp.ef, x0 - kHX, y0 - 1, p, bar);
+    tma3(d + FwdLayout::EF, &mp.ef, x0 - (EFB ? kHX16 : kHX), y0 - 1, p, bar);
   }
   if (full) {
     tma3(d + FwdLayout::VX, &mp.vx, x0 - kHX, y0, p, bar);
@@ -215,23 +221,37 @@ __device__ void fwd_issue(const FwdMaps& mp, const Ring& r, int p, int kbeg, int
   if (full || below) tma3(d + FwdLayout::VZ, &mp.vz, x0, y0, p, bar);
 }
 
+// e^n of float4 number q (element f) of the FP32 halo layout, from the EF box: FP32, or
+// BF16 in the wider box (see kHX16)
+template <bool EFB>
+__device__ __forceinline__ float4 ef_at(const uint8_t* s, int q) {
+  if (!EFB) return reinterpret_cast<const float4*>(s + FwdLayout::EF)[q];
+  const uint2 b = reinterpret_cast<const uint2*>(s + FwdLayout::EF)[(q / kW4E) * (kWE16 / 4) +
+                                                                    q % kW4E + (kHX16 - kHX) / 4];
+  return make_float4(__uint_as_float(b.x << 16), __uint_as_float(b.x & 0xffff0000u),
+                     __uint_as_float(b.y << 16), __uint_as_float(b.y & 0xffff0000u));
+}
+template <bool EFB>
+__device__ __forceinline__ float ef_sc(const uint8_t* s, int f) {
+  if (!EFB) return reinterpret_cast<const float*>(s + FwdLayout::EF)[f];
+  const uint16_t b =
+      reinterpret_cast<const uint16_t*>(s + FwdLayout::EF)[(f / kWE) * kWE16 + f % kWE + kHX16 - kHX];
+  return __uint_as_float((uint32_t)b << 16);
+}
+
 // m e (+ dm e^n) of float4 number q of a halo box in stage s
-template <bool INCR>
+template <bool INCR, bool EFB>
 __device__ __forceinline__ float4 me_at(const uint8_t* s, int q) {
   float4 r = mul4(reinterpret_cast<const float4*>(s + FwdLayout::M)[q],
                   reinterpret_cast<const float4*>(s + FwdLayout::E)[q]);
-  if (INCR)
-    r = fma4(reinterpret_cast<const float4*>(s + FwdLayout::DM)[q],
-             reinterpret_cast<const float4*>(s + FwdLayout::EF)[q], r);
+  if (INCR) r = fma4(reinterpret_cast<const float4*>(s + FwdLayout::DM)[q], ef_at<EFB>(s, q), r);
   return r;
 }
-template <bool INCR>
+template <bool INCR, bool EFB>
 __device__ __forceinline__ float me_sc(const uint8_t* s, int f) {
   float r = reinterpret_cast<const float*>(s + FwdLayout::M)[f] *
             reinterpret_cast<const float*>(s + FwdLayout::E)[f];
-  if (INCR)
-    r = fmaf(reinterpret_cast<const float*>(s + FwdLayout::DM)[f],
-             reinterpret_cast<const float*>(s + FwdLayout::EF)[f], r);
+  if (INCR) r = fmaf(reinterpret_cast<const float*>(s + FwdLayout::DM)[f], ef_sc<EFB>(s, f), r);
   return r;
 }
 
@@ -239,7 +259,7 @@ __device__ __forceinline__ float me_sc(const uint8_t* s, int f) {
 // before the step: the step that wrote the state stored them), go out in one pass.
 // MAXO: the maxima of the output state, reduced inside the CTA (which owns whole
 // blocks: 128 x 8 nodes per plane, chunks of whole 8-plane layers) and stored whole.
-template <bool INCR, bool PACK, bool MAXO, bool TPACK>
+template <bool INCR, bool PACK, bool MAXO, bool TPACK, bool EFB>
 __global__ void __launch_bounds__(NTHR, (INCR || PACK) ? 2 : 3)
     fwd_tma_kernel(const __grid_constant__ FwdMaps mp, const FwdStep a, int S) {
   extern __shared__ uint8_t smem_raw[];
@@ -271,7 +291,7 @@ __global__ void __launch_bounds__(NTHR, (INCR || PACK) ? 2 : 3)
     tc::mbar_fence_init();
     tc::fence_proxy_async();
     for (; next <= pn && next < r.p0 + S; ++next)
-      fwd_issue<INCR>(mp, r, next, kbeg, kend, nz, x0, y0);
+      fwd_issue<INCR, EFB>(mp, r, next, kbeg, kend, nz, x0, y0);
   }
   __syncthreads();
 
@@ -290,7 +310,7 @@ __global__ void __launch_bounds__(NTHR, (INCR || PACK) ? 2 : 3)
   if (kbeg >= 1 && !failed) {
     const uint8_t* sb = r.at(r.p0);
     const uint8_t* sc = r.at(kbeg);
-    vzl = fupd4(dth, me_at<INCR>(sc, qE), me_at<INCR>(sb, qE),
+    vzl = fupd4(dth, me_at<INCR, EFB>(sc, qE), me_at<INCR, EFB>(sb, qE),
                 reinterpret_cast<const float4*>(sb + FwdLayout::VZ)[qO]);
     add_source(vzl, kbeg - 1, y, i0, a);
   }
@@ -333,10 +353,10 @@ __global__ void __launch_bounds__(NTHR, (INCR || PACK) ? 2 : 3)
     const size_t i = (size_t)k * P + row;
 
     const float4 e_c = reinterpret_cast<const float4*>(sc + FwdLayout::E)[qE];
-    const float4 me_c = me_at<INCR>(sc, qE);
-    const float4 me_yp = me_at<INCR>(sc, qE + kW4E);
-    const float4 me_ym = me_at<INCR>(sc, qE - kW4E);
-    const float4 me_n = me_at<INCR>(sn, qE);
+    const float4 me_c = me_at<INCR, EFB>(sc, qE);
+    const float4 me_yp = me_at<INCR, EFB>(sc, qE + kW4E);
+    const float4 me_ym = me_at<INCR, EFB>(sc, qE - kW4E);
+    const float4 me_n = me_at<INCR, EFB>(sn, qE);
     const float4 vx_c = reinterpret_cast<const float4*>(sc + FwdLayout::VX)[qX];
     const float4 vy_c = reinterpret_cast<const float4*>(sc + FwdLayout::VY)[qY];
     const float4 vy_m = reinterpret_cast<const float4*>(sc + FwdLayout::VY)[qY - kW4];
@@ -358,7 +378,7 @@ __global__ void __launch_bounds__(NTHR, (INCR || PACK) ? 2 : 3)
 
     // x-faces of the own nodes; the face x+3 -> x+4 takes m e from the next lane
     float mx1 = __shfl_down_sync(0xffffffffu, me_c.x, 1);
-    if (lane == 31) mx1 = me_sc<INCR>(sc, (ty + 1) * kWE + kHX + kTXW);
+    if (lane == 31) mx1 = me_sc<INCR, EFB>(sc, (ty + 1) * kWE + kHX + kTXW);
     float4 vx1;
     vx1.x = fupd(dth, me_c.y, me_c.x, vx_c.x);
     vx1.y = fupd(dth, me_c.z, me_c.y, vx_c.y);
@@ -369,7 +389,7 @@ __global__ void __launch_bounds__(NTHR, (INCR || PACK) ? 2 : 3)
     if (lane == 0) {
       vxl = 0.f;
       if (i0 >= 1)
-        vxl = fupd(dth, me_c.x, me_sc<INCR>(sc, (ty + 1) * kWE + kHX - 1),
+        vxl = fupd(dth, me_c.x, me_sc<INCR, EFB>(sc, (ty + 1) * kWE + kHX - 1),
                    reinterpret_cast<const float*>(sc + FwdLayout::VX)[ty * kWE + kHX - 1]);
     }
     // y-faces: own, and the one below recomputed as the row below computes it
@@ -447,7 +467,7 @@ __global__ void __launch_bounds__(NTHR, (INCR || PACK) ? 2 : 3)
     failed = __syncthreads_or(failed);
     if (tid == 0 && !failed)
       for (; next <= pn && next <= k + S; ++next)
-        fwd_issue<INCR>(mp, r, next, kbeg, kend, nz, x0, y0);
+        fwd_issue<INCR, EFB>(mp, r, next, kbeg, kend, nz, x0, y0);
     if (MAXO && (k & 7) == 7 && !failed && tid < 64) {
       // the rows' tables are visible after the barrier; they are rewritten eight
       // planes (and barriers) later
@@ -787,17 +807,17 @@ dim3 grid_of(int nx, int ny, int nz, int kc) {
   return dim3((nx + kTXW - 1) / kTXW, (ny + TY - 1) / TY, (nz + kc - 1) / kc);
 }
 
-template <bool INCR, bool PACK, bool MAXO, bool TPACK = false>
+template <bool INCR, bool PACK, bool MAXO, bool TPACK = false, bool EFB = false>
 cudaError_t launch_fwd(const FwdMaps& mp, const FwdStep& a, cudaStream_t s) {
   const int S = stages_for(false);
   const int extra = (PACK ? kPackExtra : 0) + ((MAXO || TPACK) ? kMaxoExtra : 0) + 128;
   const size_t smem = (size_t)S * FwdLayout::bytes(INCR) + extra;
   // once per instantiation (thread-safe static initialisation)
   static const cudaError_t attr = cudaFuncSetAttribute(
-      fwd_tma_kernel<INCR, PACK, MAXO, TPACK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      fwd_tma_kernel<INCR, PACK, MAXO, TPACK, EFB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
       (int)(kMaxStages * FwdLayout::bytes(INCR) + extra));
   if (attr != cudaSuccess) return attr;
-  fwd_tma_kernel<INCR, PACK, MAXO, TPACK>
+  fwd_tma_kernel<INCR, PACK, MAXO, TPACK, EFB>
       <<<grid_of(a.nx, a.ny, a.nz, a.kc), dim3(32, TY), smem, s>>>(mp, a, S);
   return cudaGetLastError();
 }
@@ -850,17 +870,20 @@ cudaError_t launch_fwd_step(const FwdStep& a, bool incremental, cudaStream_t s) 
             field_map(&mp.vx, a.vx, nx, ny, nz, kWE, TY) &&
             field_map(&mp.vy, a.vy, nx, ny, nz, kTXW, TY + 1) &&
             field_map(&mp.vz, a.vz, nx, ny, nz, kTXW, TY);
+  if (incremental && a.ef && a.ef16) return cudaErrorInvalidValue;
   if (ok && incremental)
     ok = field_map(&mp.dm, a.dm, nx, ny, nz, kWE, TY + 2) &&
-         field_map(&mp.ef, a.ef, nx, ny, nz, kWE, TY + 2);
+         (a.ef16 ? field_map16(&mp.ef, a.ef16, nx, ny, nz, kWE16, TY + 2)
+                 : field_map(&mp.ef, a.ef, nx, ny, nz, kWE, TY + 2));
   if (!ok) return cudaErrorInvalidValue;
   if (incremental && a.tpack) {
-    if (nx % 8 || ny % 8 || nz % 2 || !a.vmax || a.tslot < 0 || a.tslot >= 16)
+    if (nx % 8 || ny % 8 || nz % 2 || !a.vmax || a.tslot < 0 || a.tslot >= 16 || a.ef16)
       return cudaErrorInvalidValue;
     FwdStep b = a;
     b.kc = (a.kc + 1) / 2 * 2;
     return launch_fwd<true, false, false, true>(mp, b, s);
   }
+  if (incremental && a.ef16) return launch_fwd<true, false, false, false, true>(mp, a, s);
   if (incremental) return launch_fwd<true, false, false>(mp, a, s);
   if (a.tpack) {
     // window packing works on 2 x 8 x 8-node blocks: whole z pairs inside one CTA

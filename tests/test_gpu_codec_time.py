@@ -134,7 +134,7 @@ def test_time_ae_gradient_jvp_and_hvp_match_oracle(tcase):
     s.codec_set(Wt)
     J, g = s.gradient(cuda(c), cuda(d_obs))
     ehat = CT.compressed_e_history(Wt, e_hist, emulate=True)
-    eadj = CT.adjoint_history(ehat)        # the adjoint-type sweeps read BF16 (R34)
+    eadj = CT.bf16_history(ehat)        # the sweeps read the decoded strain as BF16 (R34)
     J_ref, g_ref, _ = W.gradient(prob, c, d_obs, e_of=lambda n: eadj[n])
     assert abs(J - J_ref) / J_ref < 1e-4
     err_g = relerr(host(g), g_ref)
@@ -144,10 +144,10 @@ def test_time_ae_gradient_jvp_and_hvp_match_oracle(tcase):
     assert err_g < 1e-3
     dc = inputs.direction(prob.shape, prob.h, seed=20).astype(np.float32).astype(np.float64)
     dd = host(s.jvp(cuda(dc)))
-    dd_ref = W.incremental_forward(prob, c, dc, lambda n: ehat[n])
+    dd_ref = W.incremental_forward(prob, c, dc, lambda n: eadj[n])
     assert relerr(dd, dd_ref) < 1e-3
     H = host(s.hessvec(cuda(dc)))
-    H_ref = W.hessvec_gn(prob, c, dc, lambda n: ehat[n], e_adj_of=lambda n: eadj[n])
+    H_ref = W.hessvec_gn(prob, c, dc, lambda n: eadj[n])
     assert relerr(H, H_ref) < 1e-3
     st = s.stats()
     nwin = CT.n_windows(prob.nt)

@@ -96,7 +96,7 @@ def test_minmax_compressed_gradient_matches_oracle():
     s = solver(prob, storage="ae", codec="time", norm="minmax", beta=beta)
     s.codec_set(Wt)
     J, g = s.gradient(cuda(c), cuda(d_obs))
-    ehat = CT.adjoint_history(CT.compressed_e_history(Wt, e_hist, emulate=True, norm="minmax",
+    ehat = CT.bf16_history(CT.compressed_e_history(Wt, e_hist, emulate=True, norm="minmax",
                                                       beta=beta))
     J_ref, g_ref, _ = W.gradient(prob, c, d_obs, e_of=lambda n: ehat[n])
     err = relerr(host(g), g_ref)

@@ -329,18 +329,18 @@ def test_minmax_history_with_a_code_exact_on_its_data():
     assert np.mean(r == CT.BETA) > 0.5
 
 
-def test_adjoint_history_rounds_to_bf16_and_its_gradient_stays_close():
+def test_bf16_history_rounds_to_bf16_and_its_gradient_stays_close():
     """The adjoint-type sweeps read the decoded strain as BF16 (R34): values already in
     BF16 pass unchanged, a value halfway between two BF16 numbers goes to the even one,
     e^0 stays exactly 0, and the gradient computed from the BF16 history differs from the
     FP64 one by no more than BF16's relative step (2^-8) bounds."""
     one = np.array([1.0, 1.0 + 2.0 ** -7, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, -2.5, 0.0])
-    out = CT.adjoint_history([one])[0]
+    out = CT.bf16_history([one])[0]
     np.testing.assert_array_equal(out, [1.0, 1.0 + 2.0 ** -7, 1.0, 1.0 + 2 * 2.0 ** -7, -2.5, 0.0])
     prob, c = _small_problem(nt=40)
     d, states = W.forward_states(prob, c)
     e_hist = [st[0] for st in states]
-    eb = CT.adjoint_history(e_hist)
+    eb = CT.bf16_history(e_hist)
     assert not np.any(eb[0])
     rel = max(float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)) for a, b in zip(eb[1:], e_hist[1:]))
     assert rel <= 2.0 ** -8
