@@ -188,10 +188,9 @@ def compressed_e_history(W: dict, e_hist, emulate: bool = False, norm: str = "po
 
 
 def bf16_history(e_hat):
-    """The decoded strain history as the gradient's adjoint and the Gauss-Newton HVP's
-    incremental forward and incremental adjoint read it (reading R34): the decoder's FP32
-    output rounded to BF16, round to nearest even.  The full-Newton HVP's sweeps read the
-    FP32 values themselves."""
+    """A decoded strain history as the solves that read it (the gradient's adjoint, the
+    Gauss-Newton and full-Newton HVPs' incremental forward and adjoints) see it (reading
+    R34): the decoder's FP32 output rounded to BF16, round to nearest even."""
     return [C.round_bf16(C.round_fp32(e)) for e in e_hat]
 
 

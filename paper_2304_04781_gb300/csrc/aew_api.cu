@@ -613,9 +613,8 @@ int encode_window(aew_handle* h, int tb, cudaStream_t s) {
   return AEW_OK;
 }
 
-// decoder of window tb into its 16 strain slices edt[tb % 2]: BF16 for the gradient's
-// adjoint and the Gauss-Newton HVP's incremental forward and adjoint (their e^n boxes then
-// carry half the bytes), FP32 for the full-Newton HVP's sweeps and the standalone call
+// decoder of window tb into its 16 strain slices edt[tb % 2]: BF16 for every sweep (their
+// e^n boxes then carry half the bytes), FP32 for the profiling hook's FP32 kind
 int decode_window(aew_handle* h, int tb, cudaStream_t s, bool bf16 = false) {
   const size_t nv = nvec_of(h);
   const bool mm = aew::codec_minmax(h->codec);
@@ -797,7 +796,7 @@ int newton_incremental_forward(aew_handle* h, cudaStream_t s) {
     AEW_CK(cudaEventRecord(h->ev_d[tb & 1], h->side));
     return AEW_OK;
   };
-  if ((rc = decode_window(h, 0, h->side))) return rc;
+  if ((rc = decode_window(h, 0, h->side, true))) return rc;
   AEW_CK(cudaEventRecord(h->ev_b[0], h->side));
   if (nt == 1 && (rc = encode_de(0))) return rc;
   for (int n = 0; n < nt; ++n) {
@@ -805,7 +804,7 @@ int newton_incremental_forward(aew_handle* h, cudaStream_t s) {
     if (n % T == 0) {
       if (tb + 1 <= W - 1) {
         if (tb >= 1) AEW_CK(cudaStreamWaitEvent(h->side, h->ev_a[(tb + 1) & 1], 0));
-        if ((rc = decode_window(h, tb + 1, h->side))) return rc;
+        if ((rc = decode_window(h, tb + 1, h->side, true))) return rc;
         AEW_CK(cudaEventRecord(h->ev_b[(tb + 1) & 1], h->side));
       }
       AEW_CK(cudaStreamWaitEvent(s, h->ev_b[tb & 1], 0));
@@ -821,8 +820,8 @@ int newton_incremental_forward(aew_handle* h, cudaStream_t s) {
       tp = h->xt[to & 1];
       vm = h->vmx2 + (size_t)to * nv;
     }
-    if ((rc = incr_step(h, h->ad[cur], h->ad[cur ^ 1], window_e(h, n), drow(h, h->dd, n + 1), s,
-                        tp, slot, vm)))
+    if ((rc = incr_step(h, h->ad[cur], h->ad[cur ^ 1], nullptr, drow(h, h->dd, n + 1), s,
+                        tp, slot, vm, window_e16(h, n))))
       return rc;
     cur ^= 1;
     if (n % T == T - 1 || n == nt - 1) AEW_CK(cudaEventRecord(h->ev_a[tb & 1], s));
@@ -839,7 +838,7 @@ int decode_de_window(aew_handle* h, int tb, cudaStream_t s) {
                                            h->vmx2 + (size_t)tb * nv, h->cfg.nx, h->cfg.ny,
                                            h->cfg.nz, h->edt2[tb & 1], s, h->overlap_ctas,
                                            mm ? h->wmn2 + (size_t)tb * nv : nullptr,
-                                           mm ? h->wr2 + (size_t)tb * nv : nullptr);
+                                           mm ? h->wr2 + (size_t)tb * nv : nullptr, true);
   if (e != cudaSuccess) return cuda_fail(h, e, "codec_decode_window");
   h->stats.kernel_launches += 2;
   return AEW_OK;
@@ -860,7 +859,7 @@ int newton_adjoint_sweep(aew_handle* h, cudaStream_t s) {
   const bool ae = h->cfg.storage == AEW_AE;
   const int W = nwin_of(h);
   auto decode_both = [&](int tb) -> int {
-    int r = decode_window(h, tb, h->side);
+    int r = decode_window(h, tb, h->side, true);
     if (!r) r = decode_de_window(h, tb, h->side);
     return r;
   };
@@ -873,6 +872,8 @@ int newton_adjoint_sweep(aew_handle* h, cudaStream_t s) {
   for (int n = nt - 1; n >= 0; --n) {
     const float* en = nullptr;
     const float* den = nullptr;
+    const uint16_t* en16 = nullptr;    // the time codec's decoded windows, BF16 (R34)
+    const uint16_t* den16 = nullptr;
     if (ae) {
       const int tb = n / T;
       if (n == nt - 1 || n % T == T - 1) {
@@ -883,17 +884,18 @@ int newton_adjoint_sweep(aew_handle* h, cudaStream_t s) {
         }
         AEW_CK(cudaStreamWaitEvent(s, h->ev_b[tb & 1], 0));
       }
-      en = window_e(h, n);
-      den = n >= 1 ? h->edt2[tb & 1] + (size_t)(n % T) * h->C : nullptr;
+      en16 = window_e16(h, n);
+      den16 = n >= 1 ? reinterpret_cast<const uint16_t*>(h->edt2[tb & 1]) + (size_t)(n % T) * h->C
+                     : nullptr;
     } else if (n > 0) {
       en = h->estore + (size_t)n * h->C;
       den = h->desto + (size_t)n * h->C;
     }
     if ((rc = adj_step_x(h, n, h->ad[cur], h->ad[cur ^ 1], h->R, den, h->acc32, h->acc64,
-                         h->qbuf, nullptr, nullptr, s)))
+                         h->qbuf, nullptr, nullptr, s, den16)))
       return rc;
     if ((rc = adj_step_x(h, n, h->ad2[cur], h->ad2[cur ^ 1], h->dd, en, h->acc32b, h->acc64b,
-                         nullptr, h->qbuf, h->dm, s)))
+                         nullptr, h->qbuf, h->dm, s, en16)))
       return rc;
     cur ^= 1;
     if (ae && n % T == 0) AEW_CK(cudaEventRecord(h->ev_a[(n / T) & 1], s));

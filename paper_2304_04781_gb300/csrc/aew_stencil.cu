@@ -877,10 +877,11 @@ cudaError_t launch_fwd_step(const FwdStep& a, bool incremental, cudaStream_t s) 
                  : field_map(&mp.ef, a.ef, nx, ny, nz, kWE, TY + 2));
   if (!ok) return cudaErrorInvalidValue;
   if (incremental && a.tpack) {
-    if (nx % 8 || ny % 8 || nz % 2 || !a.vmax || a.tslot < 0 || a.tslot >= 16 || a.ef16)
+    if (nx % 8 || ny % 8 || nz % 2 || !a.vmax || a.tslot < 0 || a.tslot >= 16)
       return cudaErrorInvalidValue;
     FwdStep b = a;
     b.kc = (a.kc + 1) / 2 * 2;
+    if (a.ef16) return launch_fwd<true, false, false, true, true>(mp, b, s);
     return launch_fwd<true, false, false, true>(mp, b, s);
   }
   if (incremental && a.ef16) return launch_fwd<true, false, false, false, true>(mp, a, s);

@@ -182,3 +182,35 @@ def test_time_codec_configuration_errors():
     with pytest.raises(aewave.AewError) as ei:   # space-codec call on a time-codec handle
         s.codec_encode([torch.zeros(prob.shape, device="cuda")] * 4)
     assert ei.value.code == -1
+
+
+def test_bf16_strain_boxes_across_x_tiles_match_oracle():
+    """The sweeps' BF16 e^n boxes (the adjoint's own-node box and the incremental
+    forward's box with its 8-wide x halo, R34) on a grid two CTA tiles wide in x, so the
+    halo between the tiles carries data: gradient, JVP and GN-HVP against the oracle's
+    BF16-read history.  The source sits at x = 128, on the boundary between the tiles,
+    and in 96 steps the wave reaches the nearest of 64 receivers (the gradient spans
+    x = 109 .. 145)."""
+    prob, c, _ = setup((16, 16, 256), 96, 64, seed=4)
+    ctrue = inputs.bump_model(c, prob.h).astype(np.float32).astype(np.float64)
+    d_obs, _, _ = W.forward(prob, ctrue)
+    _, states = W.forward_states(prob, c)
+    e_hist = [st[0] for st in states]
+    Y = []
+    for tb in range(CT.n_windows(prob.nt)):
+        X = CT.window_vectors(e_hist, prob.shape, tb)
+        Y.append(CT.normalise(X, CT.vector_scales(X)))
+    Wt = _f32(CT.pca_codec(np.concatenate(Y), 512))
+    s = solver(prob, storage="ae", codec="time")
+    s.codec_set(Wt)
+    _, g = s.gradient(cuda(c), cuda(d_obs))
+    eb = CT.bf16_history(CT.compressed_e_history(Wt, e_hist, emulate=True))
+    _, g_ref, _ = W.gradient(prob, c, d_obs, e_of=lambda n: eb[n])
+    dc = inputs.direction(prob.shape, prob.h, seed=21).astype(np.float32).astype(np.float64)
+    dd = host(s.jvp(cuda(dc)))
+    dd_ref = W.incremental_forward(prob, c, dc, lambda n: eb[n])
+    H = host(s.hessvec(cuda(dc)))
+    H_ref = W.hessvec_gn(prob, c, dc, lambda n: eb[n])
+    errs = (relerr(host(g), g_ref), relerr(dd, dd_ref), relerr(H, H_ref))
+    print(f"two x tiles, BF16 boxes: gradient {errs[0]:.2e}, JVP {errs[1]:.2e}, HVP {errs[2]:.2e}")
+    assert max(errs) < 1e-3
