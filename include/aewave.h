@@ -434,7 +434,9 @@ int aew_dot(const float* a_dev, const float* b_dev, size_t n, double* out_host, 
 
 /* Test hook for the codec's activation (Sec. 3.3 layers; GELU, reading R5):
  * y_dev[i] = GELU(x_dev[i]) = x Phi(x) as the encoder and decoder kernels evaluate it
- * (Phi through Abramowitz & Stegun eq. 7.1.28, |error| <= 3e-7, within 1e-6 in FP32),
+ * (Phi through Abramowitz & Stegun eq. 7.1.28, |error| <= 3e-7, within 1e-6 in FP32; two
+ * values at a time on paired FP32 lanes, x_dev[2k] and x_dev[2k+1] together; NaN where
+ * that differs in any bit from the same operations on one value),
  * dy_dev[i] = GELU'(x_dev[i]) = Phi(x) + x phi(x) as the training kernels evaluate it
  * (erff).  Device FP32 arrays of n elements, caller-owned;
  * asynchronous on `stream`.  AEW_E_ARG for n < 0 or NULL pointers with n > 0, AEW_E_CUDA

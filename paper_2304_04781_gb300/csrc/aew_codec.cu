@@ -84,6 +84,21 @@ __device__ __forceinline__ float act_fwd(float a) {
   if (ACT == 1) return a > 0.f ? a : expm1f(a);
   return gemm::gelu_fast(a);
 }
+// bf16x2 of (act(x0), act(x1)); GELU on the paired FP32 lanes
+template <int ACT>
+__device__ __forceinline__ uint32_t act_pack2(float x0, float x1) {
+  if (ACT == 0) gemm::gelu_fast_pair(x0, x1);
+  else x0 = act_fwd<ACT>(x0), x1 = act_fwd<ACT>(x1);
+  return gemm::pack_bf16(x0, x1);
+}
+// (x0 + b0, x1 + b1) and (x0 s + b0, x1 s + b1) on the paired lanes
+__device__ __forceinline__ void add2(float& x0, float& x1, float b0, float b1) {
+  gemm::f2::split(gemm::f2::add(gemm::f2::make(x0, x1), gemm::f2::make(b0, b1)), x0, x1);
+}
+__device__ __forceinline__ void fma2(float& x0, float& x1, float s, float b0, float b1) {
+  gemm::f2::split(gemm::f2::fma(gemm::f2::make(x0, x1), gemm::f2::splat(s), gemm::f2::make(b0, b1)),
+                  x0, x1);
+}
 
 // H[row][col..] = bf16(act(acc + bias)), row stride ld
 template <int ACT>
@@ -99,8 +114,11 @@ struct EpBiasAct {
 #pragma unroll
     for (int j = 0; j < 32; j += 4) {
       const float4 b = __ldg(bq + j / 4);
-      pk[j / 2] = gemm::pack_bf16(act_fwd<ACT>(v[j] + b.x), act_fwd<ACT>(v[j + 1] + b.y));
-      pk[j / 2 + 1] = gemm::pack_bf16(act_fwd<ACT>(v[j + 2] + b.z), act_fwd<ACT>(v[j + 3] + b.w));
+      float x0 = v[j], x1 = v[j + 1], x2 = v[j + 2], x3 = v[j + 3];
+      add2(x0, x1, b.x, b.y);
+      add2(x2, x3, b.z, b.w);
+      pk[j / 2] = act_pack2<ACT>(x0, x1);
+      pk[j / 2 + 1] = act_pack2<ACT>(x2, x3);
     }
     uint4* dst = reinterpret_cast<uint4*>(H + row * ld + col);
 #pragma unroll
@@ -129,10 +147,11 @@ struct EpScaleAct {
 #pragma unroll
     for (int j = 0; j < 32; j += 4) {
       const float4 b = __ldg(bq + j / 4);
-      pk[j / 2] = gemm::pack_bf16(act_fwd<ACT>(fmaf(v[j], is, b.x)),
-                                  act_fwd<ACT>(fmaf(v[j + 1], is, b.y)));
-      pk[j / 2 + 1] = gemm::pack_bf16(act_fwd<ACT>(fmaf(v[j + 2], is, b.z)),
-                                      act_fwd<ACT>(fmaf(v[j + 3], is, b.w)));
+      float x0 = v[j], x1 = v[j + 1], x2 = v[j + 2], x3 = v[j + 3];
+      fma2(x0, x1, is, b.x, b.y);
+      fma2(x2, x3, is, b.z, b.w);
+      pk[j / 2] = act_pack2<ACT>(x0, x1);
+      pk[j / 2 + 1] = act_pack2<ACT>(x2, x3);
     }
     uint4* dst = reinterpret_cast<uint4*>(H + row * ld + col);
 #pragma unroll
@@ -675,7 +694,15 @@ __global__ void activation_probe_kernel(const float* __restrict__ x, float* __re
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     const float v = x[i];
-    y[i] = gemm::gelu_fast(v);
+    // GELU as the epilogues evaluate it, on the pair (x[2k], x[2k+1]) that holds x[i];
+    // NaN where it differs in any bit from the scalar form
+    const long long j = i ^ 1;
+    const float w = j < n ? x[j] : v;
+    float lo = (i & 1) ? w : v, hi = (i & 1) ? v : w;
+    gemm::gelu_fast_pair(lo, hi);
+    const float yp = (i & 1) ? hi : lo;
+    y[i] = __float_as_uint(yp) == __float_as_uint(gemm::gelu_fast(v)) ? yp
+                                                                      : __uint_as_float(0x7fc00000u);
     dy[i] = gemm::gelu_prime_f(v);
   }
 }

@@ -218,8 +218,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int j = 0; j < 32; j += 4) {
           const float4 b = bq[j / 4];
-          pk[j / 2] = gemm::pack_bf16(gemm::gelu_fast(v[j] + b.x), gemm::gelu_fast(v[j + 1] + b.y));
-          pk[j / 2 + 1] = gemm::pack_bf16(gemm::gelu_fast(v[j + 2] + b.z), gemm::gelu_fast(v[j + 3] + b.w));
+          float x0 = v[j] + b.x, x1 = v[j + 1] + b.y, x2 = v[j + 2] + b.z, x3 = v[j + 3] + b.w;
+          gemm::gelu_fast_pair(x0, x1);
+          gemm::gelu_fast_pair(x2, x3);
+          pk[j / 2] = gemm::pack_bf16(x0, x1);
+          pk[j / 2 + 1] = gemm::pack_bf16(x2, x3);
         }
         uint8_t* chunk = hb + (g >> 1) * kChunk;
         const int k0 = (g & 1) * 32;          // column within the 64-wide K chunk

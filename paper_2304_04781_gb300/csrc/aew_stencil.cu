@@ -839,11 +839,15 @@ cudaError_t launch_adj(const AdjMaps& mp, const AdjStep& a, cudaStream_t s) {
 
 int default_kc(int nx, int ny, int nz, bool adjoint) {
   // z planes per CTA: short chunks give many CTAs (several waves, good balance) at the
-  // cost of staging one plane below and one above each chunk; 8 measured best at 256^3
-  // on GB300 (the packing forward step rounds it up to whole 8-plane block layers).
+  // cost of staging one plane below and one above each chunk.  Measured at 256^3 on
+  // GB300: 6 for the forward steps (plain 98.2 us against 100.2 with 8; the window-packing
+  // step 107.1 against 109.6), 8 for the adjoint (129.8 us; 130.4 with 6, 131.0 with 12).
+  // The space codec's packing step rounds it up to whole 8-plane block layers, the time
+  // codec's to whole plane pairs.
   (void)nx;
   (void)ny;
-  int kc = nz < 8 ? nz : 8;
+  const int want = adjoint ? 8 : 6;
+  int kc = nz < want ? nz : want;
   if (const char* env = getenv(adjoint ? "AEW_STENCIL_KC_ADJ" : "AEW_STENCIL_KC_FWD")) {
     const int v = atoi(env);   // tuning override
     if (v > 0) kc = v;

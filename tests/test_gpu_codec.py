@@ -61,13 +61,15 @@ def test_activation_meets_its_error_bound():
     hidden layers see and beyond.  In FP32 the 16th power multiplies the rounding of its
     base by 16, so |dPhi| <= 1e-6 (about 1e-3 of the BF16 rounding the activations take
     next) and |dGELU| <= 1e-6 |x| + one FP32 rounding of the product; both tails go to 0
-    and x, and 0 maps to 0."""
+    and x, and 0 maps to 0.  The kernels take GELU two values at a time on paired FP32
+    lanes; the probe returns NaN wherever that differs in any bit from the scalar form."""
     from scipy.special import erf
     from paper_2304_04781_gb300 import aewave
     x = np.concatenate([np.linspace(-12.0, 12.0, 480001), [0.0, -0.0, 1e-30, -1e-30, 40.0, -40.0,
                                                           1e6, -1e6]]).astype(np.float32)
     y, dy = aewave.activation_probe(torch.from_numpy(x).cuda())
     y, dy = host(y), host(dy)
+    assert not np.any(np.isnan(y)), "paired-lane GELU differs from the scalar form"
     xd = x.astype(np.float64)
     phi = 0.5 * (1.0 + erf(xd / np.sqrt(2.0)))
     g = xd * phi
