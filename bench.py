@@ -81,7 +81,7 @@ def parse():
     p.add_argument("--kernel", default="",
                    choices=["", "forward", "forward_pack", "adjoint", "incremental",
                             "encode_window", "decode_window", "adjoint_bf16",
-                            "decode_window_bf16", "incremental_bf16"],
+                            "decode_window_bf16", "incremental_bf16", "decode_state"],
                    help="instead of the benchmark: time one hot-path kernel alone "
                         "(aew_profile_steps) on an AE handle of --shape, for profiling")
     p.add_argument("--launches", type=int, default=16)

@@ -415,9 +415,10 @@ int aew_codec_init_pca(aew_handle* h, const uint16_t* vectors_dev, const float* 
  * step, 4 encoder of one window (both layers), 5 decoder of one window (both layers,
  * scattered to 16 FP32 strain slices), 6 adjoint step reading its strain field as BF16
  * (as the time codec's adjoint sweeps do; nx a multiple of 8), 7 decoder of one window
- * into BF16 strain slices, 8 incremental forward step reading its strain field as BF16.
- * Kinds 1, 4, 5 and 7 need AE storage with the time codec (AEW_E_CONFIG otherwise), 4, 5
- * and 7 codec weights.  Overwrites the handle's stored
+ * into BF16 strain slices, 8 incremental forward step reading its strain field as BF16,
+ * 9 the space codec's fused strain decoder of one state (both layers, scattered to the
+ * grid).  Kinds 1, 4, 5 and 7 need AE storage with the time codec, 9 with the space codec
+ * (AEW_E_CONFIG otherwise), 4, 5, 7 and 9 codec weights.  Overwrites the handle's stored
  * history (a later aew_hessvec needs a new aew_gradient).  Synchronises the stream. */
 int aew_profile_steps(aew_handle* h, const float* c_dev, int kind, int nsteps, double* ms_host,
                       void* stream);

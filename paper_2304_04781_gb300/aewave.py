@@ -425,7 +425,7 @@ class Solver:
 
     PROFILE_KINDS = {"forward": 0, "forward_pack": 1, "adjoint": 2, "incremental": 3,
                      "encode_window": 4, "decode_window": 5, "adjoint_bf16": 6,
-                     "decode_window_bf16": 7, "incremental_bf16": 8}
+                     "decode_window_bf16": 7, "incremental_bf16": 8, "decode_state": 9}
 
     def profile(self, c: torch.Tensor, kind: str, nsteps: int) -> float:
         """aew_profile_steps: mean device ms per launch of one hot-path kernel."""

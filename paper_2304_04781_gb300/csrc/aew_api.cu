@@ -1791,11 +1791,13 @@ int aew_codec_init_pca(aew_handle* h, const uint16_t* vectors_dev, const float* 
 int aew_profile_steps(aew_handle* h, const float* c_dev, int kind, int nsteps, double* ms_host,
                       void* stream) {
   if (!h) return AEW_E_ARG;
-  if (kind < 0 || kind > 8 || nsteps < 1 || !ms_host) return fail(h, AEW_E_ARG, "bad argument");
+  if (kind < 0 || kind > 9 || nsteps < 1 || !ms_host) return fail(h, AEW_E_ARG, "bad argument");
   const bool tw = h->cfg.storage == AEW_AE && h->tcodec;
   if ((kind == 1 || kind == 4 || kind == 5 || kind == 7) && !tw)
     return fail(h, AEW_E_CONFIG, "this kernel needs AE storage with the time codec");
-  if ((kind == 4 || kind == 5 || kind == 7) && !aew::codec_ready(h->codec))
+  if (kind == 9 && !(h->cfg.storage == AEW_AE && !h->tcodec))
+    return fail(h, AEW_E_CONFIG, "this kernel needs AE storage with the space codec");
+  if ((kind == 4 || kind == 5 || kind == 7 || kind == 9) && !aew::codec_ready(h->codec))
     return fail(h, AEW_E_NOCODEC, "codec weights not set");
   if ((kind == 6 || kind == 8) && h->cfg.nx % 8)
     return fail(h, AEW_E_CONFIG, "a BF16 strain field needs nx % 8 == 0");
@@ -1843,6 +1845,9 @@ int aew_profile_steps(aew_handle* h, const float* c_dev, int kind, int nsteps, d
       case 8:   // the incremental forward step reading its strain field as BF16
         rc = incr_step(h, h->ad[cur], h->ad[cur ^ 1], nullptr, nullptr, s, nullptr, 0, nullptr,
                        reinterpret_cast<const uint16_t*>(h->st[0][0]));
+        break;
+      case 9:   // the space codec's fused strain decoder, step 0's latents
+        rc = decode_e(h, 0, h->st[1][0], s);
         break;
     }
     cur ^= 1;
