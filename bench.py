@@ -40,8 +40,8 @@ METRIC = "gradients/hour at 256^3x2000 steps: AE vs checkpointing; stencil HBM G
 # the current kernel (dram__bytes_read.sum + dram__bytes_write.sum, a window-middle step
 # without the FP64 flush); to be set to None when the kernel changes until it is
 # captured again
-ADJ_TRAFFIC_256 = 768.6e6     # FP32 e^n (full storage / checkpointing)
-ADJ16_TRAFFIC_256 = 665.9e6   # BF16 e^n (the time codec's adjoint sweeps)
+ADJ_TRAFFIC_256 = 701.6e6     # FP32 e^n (full storage / checkpointing)
+ADJ16_TRAFFIC_256 = 665.5e6   # BF16 e^n (the time codec's adjoint sweeps)
 SHAPE = (256, 256, 256)
 NT = 2000
 NREC = 128

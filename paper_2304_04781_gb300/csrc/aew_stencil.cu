@@ -53,7 +53,10 @@ constexpr int kW4 = kTXW / 4;         // 32 float4 per plain row
 constexpr int kHX16 = 8;
 constexpr int kWE16 = kTXW + 2 * kHX16;
 constexpr uint64_t kWaitNs = 200000000ull;
-constexpr int kMaxStages = 4;
+// TMA ring depth: at least 3, since the first plane of a chunk needs the planes below and
+// above it resident at once; 4 measured slower (one CTA fewer per SM).  A compile-time
+// depth keeps the ring's slot and phase arithmetic to a few instructions per plane.
+constexpr int kStages = 3;
 // PACK: one plane of the CTA's 16 blocks, 4 fields x 8 rows x 8 BF16 each (a 512-byte
 // row per block, rows 528 bytes apart so that the 16 lane pairs of a warp, one per
 // block, write distinct banks), double-buffered.  MAXO: the block maxima of the output
@@ -179,9 +182,10 @@ __device__ __forceinline__ bool sticky_error(const int* err) {
 // kend in order; plane p lives in stage (p - p0) % S and completes phase
 // ((p - p0) / S) & 1 of that stage's barrier.
 struct Ring {
+  static constexpr int S = kStages;
   uint8_t* base;
   uint32_t bar0;   // shared address of barrier 0 (8 bytes each)
-  int stage_bytes, S, p0;
+  int stage_bytes, p0;
   __device__ int slot(int p) const { return (p - p0) % S; }
   __device__ uint32_t parity(int p) const { return ((p - p0) / S) & 1; }
   __device__ uint8_t* at(int p) const { return base + (size_t)slot(p) * stage_bytes; }
@@ -261,9 +265,10 @@ __device__ __forceinline__ float me_sc(const uint8_t* s, int f) {
 // blocks: 128 x 8 nodes per plane, chunks of whole 8-plane layers) and stored whole.
 template <bool INCR, bool PACK, bool MAXO, bool TPACK, bool EFB>
 __global__ void __launch_bounds__(NTHR, (INCR || PACK) ? 2 : 3)
-    fwd_tma_kernel(const __grid_constant__ FwdMaps mp, const FwdStep a, int S) {
+    fwd_tma_kernel(const __grid_constant__ FwdMaps mp, const FwdStep a) {
+  constexpr int S = kStages;
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t bars[kMaxStages];
+  __shared__ __align__(8) uint64_t bars[kStages];
   if (sticky_error(a.err)) return;
 
   const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + lane;
@@ -282,7 +287,6 @@ __global__ void __launch_bounds__(NTHR, (INCR || PACK) ? 2 : 3)
                                       ~static_cast<uintptr_t>(127));
   r.bar0 = tc::smem_u32(&bars[0]);
   r.stage_bytes = FwdLayout::bytes(INCR);
-  r.S = S;
   r.p0 = kbeg - 1;
   const int pn = kend;
   int next = r.p0;   // next plane to issue (thread 0)
@@ -347,7 +351,8 @@ __global__ void __launch_bounds__(NTHR, (INCR || PACK) ? 2 : 3)
       if (act && k + 8 < kend)
         mnext = __ldg(reinterpret_cast<const uint4*>(bml + (size_t)((k >> 3) + 1) * NBy * NBx * 4));
     }
-    if (!r.wait(k) || !r.wait(k + 1)) failed = true;
+    // plane k was waited for as plane k + 1 of the previous iteration (or before the loop)
+    if (!r.wait(k + 1)) failed = true;
     const uint8_t* sc = r.at(k);
     const uint8_t* sn = r.at(k + 1);
     const size_t i = (size_t)k * P + row;
@@ -564,9 +569,10 @@ __device__ __forceinline__ void inj4(const AdjStep& a, int y, int i0, float4& lx
 // HVP: the first-order adjoint writes its dt q, the second-order adjoint reads it)
 template <int V>
 __global__ void __launch_bounds__(NTHR, 2)
-    adj_tma_kernel(const __grid_constant__ AdjMaps mp, const AdjStep a, int S) {
+    adj_tma_kernel(const __grid_constant__ AdjMaps mp, const AdjStep a) {
+  constexpr int S = kStages;
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t bars[kMaxStages];
+  __shared__ __align__(8) uint64_t bars[kStages];
   if (sticky_error(a.err)) return;
 
   const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + lane;
@@ -588,7 +594,6 @@ __global__ void __launch_bounds__(NTHR, 2)
                                       ~static_cast<uintptr_t>(127));
   r.bar0 = tc::smem_u32(&bars[0]);
   r.stage_bytes = AdjLayout::BYTES;
-  r.S = S;
   r.p0 = kbeg - 1;
   const int pn = kend;
   int next = r.p0;
@@ -636,7 +641,8 @@ __global__ void __launch_bounds__(NTHR, 2)
     float4 src2 = z4();
     if ((V & 2) && act) src2 = mul4(__ldg(reinterpret_cast<const float4*>(a.dm2 + i)),
                                      __ldg(reinterpret_cast<const float4*>(a.qin + i)));
-    if (!r.wait(k) || !r.wait(k + 1)) failed = true;
+    // plane k was waited for as plane k + 1 of the previous iteration (or before the loop)
+    if (!r.wait(k + 1)) failed = true;
     const uint8_t* sc = r.at(k);
     const uint8_t* sn = r.at(k + 1);
     const float4* MU = reinterpret_cast<const float4*>(sc + AdjLayout::MU);
@@ -792,46 +798,32 @@ bool field_map16(CUtensorMap* map, const uint16_t* base, int nx, int ny, int nz,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// At least 3 stages: the first plane of a chunk needs the planes below and above it
-// resident at once.
-int stages_for(bool adjoint) {
-  int s = 3;
-  if (const char* env = getenv(adjoint ? "AEW_STENCIL_STAGES_ADJ" : "AEW_STENCIL_STAGES_FWD")) {
-    const int v = atoi(env);   // tuning override
-    if (v >= 3 && v <= kMaxStages) s = v;
-  }
-  return s;
-}
-
 dim3 grid_of(int nx, int ny, int nz, int kc) {
   return dim3((nx + kTXW - 1) / kTXW, (ny + TY - 1) / TY, (nz + kc - 1) / kc);
 }
 
 template <bool INCR, bool PACK, bool MAXO, bool TPACK = false, bool EFB = false>
 cudaError_t launch_fwd(const FwdMaps& mp, const FwdStep& a, cudaStream_t s) {
-  const int S = stages_for(false);
   const int extra = (PACK ? kPackExtra : 0) + ((MAXO || TPACK) ? kMaxoExtra : 0) + 128;
-  const size_t smem = (size_t)S * FwdLayout::bytes(INCR) + extra;
+  const size_t smem = (size_t)kStages * FwdLayout::bytes(INCR) + extra;
   // once per instantiation (thread-safe static initialisation)
   static const cudaError_t attr = cudaFuncSetAttribute(
       fwd_tma_kernel<INCR, PACK, MAXO, TPACK, EFB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-      (int)(kMaxStages * FwdLayout::bytes(INCR) + extra));
+      (int)smem);
   if (attr != cudaSuccess) return attr;
   fwd_tma_kernel<INCR, PACK, MAXO, TPACK, EFB>
-      <<<grid_of(a.nx, a.ny, a.nz, a.kc), dim3(32, TY), smem, s>>>(mp, a, S);
+      <<<grid_of(a.nx, a.ny, a.nz, a.kc), dim3(32, TY), smem, s>>>(mp, a);
   return cudaGetLastError();
 }
 
 template <int V>
 cudaError_t launch_adj(const AdjMaps& mp, const AdjStep& a, cudaStream_t s) {
-  const int S = stages_for(true);
-  const size_t smem = (size_t)S * AdjLayout::BYTES + 128;
+  const size_t smem = (size_t)kStages * AdjLayout::BYTES + 128;
   // once per instantiation (thread-safe static initialisation)
   static const cudaError_t attr = cudaFuncSetAttribute(
-      adj_tma_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-      (int)(kMaxStages * AdjLayout::BYTES + 128));
+      adj_tma_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (attr != cudaSuccess) return attr;
-  adj_tma_kernel<V><<<grid_of(a.nx, a.ny, a.nz, a.kc), dim3(32, TY), smem, s>>>(mp, a, S);
+  adj_tma_kernel<V><<<grid_of(a.nx, a.ny, a.nz, a.kc), dim3(32, TY), smem, s>>>(mp, a);
   return cudaGetLastError();
 }
 
