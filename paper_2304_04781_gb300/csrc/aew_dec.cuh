@@ -257,7 +257,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         break;
       }
       tc::fence_before_sync();
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(tfree)) : "memory");
+      // relaxed: it orders only the completed TMEM reads (tcgen05.wait::ld) before the next
+      // tile's MMAs, not the grid stores
+      asm volatile("mbarrier.arrive.relaxed.cta.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(tfree))
+                   : "memory");
     }
   }
   tc::fence_before_sync();

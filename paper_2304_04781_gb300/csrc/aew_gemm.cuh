@@ -372,7 +372,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         ep(row, n0 + col, v);
       }
       tc::fence_before_sync();
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&acce[a])) : "memory");
+      // relaxed: it orders only the warp's completed TMEM reads (tcgen05.wait::ld) before
+      // the MMAs that overwrite the accumulator, not the warp's global stores
+      asm volatile("mbarrier.arrive.relaxed.cta.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&acce[a]))
+                   : "memory");
     }
   }
   tc::fence_before_sync();

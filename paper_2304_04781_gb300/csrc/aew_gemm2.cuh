@@ -116,8 +116,12 @@ __device__ __forceinline__ bool wait_cl(uint32_t mbar, uint32_t parity, uint64_t
     }
   }
 }
+// An epilogue warp's "accumulator drained" signal.  Relaxed: the signal orders only the
+// warp's TMEM reads, which tcgen05.wait::ld has already completed, before the MMAs that
+// overwrite the accumulator; a release would also hold the warp until its global stores
+// of the tile are performed at cluster scope, which nothing in the kernel reads.
 __device__ __forceinline__ void arrive_remote(uint32_t mbar_cluster) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(mbar_cluster)
+  asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(mbar_cluster)
                : "memory");
 }
 
