@@ -213,6 +213,37 @@ def test_revolve_bitwise_equals_full_storage(cfg1, nt, s_slots):
     assert torch.equal(full.hessvec(dc), rev.hessvec(dc))
 
 
+@pytest.mark.parametrize("storage", ["full", "time"])
+def test_results_do_not_depend_on_the_chunk_depth(storage, monkeypatch):
+    """Every face a CTA shares with the chunk below or above is recomputed with the
+    identical expression, so seismograms, gradients and GN-HVPs are bitwise the same for
+    any number of z planes per CTA: the defaults (6 forward, 8 adjoint) against 8 / 5,
+    3 / 3 and one chunk per column.  With the time codec the window-packing step rounds
+    the depth up to whole plane pairs and the incremental forward reads BF16 strain."""
+    prob, c, _ = setup((40, 48, 64), 48, 16, seed=2)
+    d_obs = cuda(W.forward(prob, inputs.bump_model(c, prob.h))[0])
+    dc = cuda(inputs.direction(prob.shape, prob.h, seed=3))
+    kw = {} if storage == "full" else dict(storage="ae", codec="time", n_lat=512)
+    results = []
+    for kf, ka in ((None, None), ("8", "5"), ("3", "3"), ("40", "40")):
+        for name, v in (("AEW_STENCIL_KC_FWD", kf), ("AEW_STENCIL_KC_ADJ", ka)):
+            if v is None:
+                monkeypatch.delenv(name, raising=False)
+            else:
+                monkeypatch.setenv(name, v)   # read when the handle is made
+        s = solver(prob, **kw)
+        if storage == "time":
+            s.codec_set(inputs.codec_init(seed=4, n_hid=1024, n_lat=512))
+        d = s.forward(cuda(c))
+        J, g = s.gradient(cuda(c), d_obs)
+        results.append((d.clone(), g.clone(), s.hessvec(dc).clone(), J))
+        s.close()
+    for r in results[1:]:
+        assert r[3] == results[0][3]
+        for a, b in zip(results[0][:3], r[:3]):
+            assert torch.equal(a, b)
+
+
 def test_config2_full_vs_revolve_and_fd():
     """128^3, 1000 steps, 64 receivers: full storage vs revolve(20) bitwise; the gradient
     against 4-point central differences (error O(eps^4)) of the FP64 misfit in 8 GRF
