@@ -124,14 +124,15 @@ __device__ __forceinline__ void add_source(float4& v, int k, int y, int i0, cons
 #pragma unroll
   for (int d = 0; d < 4; ++d) {
     const int dx = i0 + d - a.si + a.sr;
-    if ((unsigned)dx < (unsigned)W) comp(v, d) += a.dts * __ldg(w + dx);
+    if ((unsigned)dx < (unsigned)W) comp(v, d) = fmaf(a.dts, __ldg(w + dx), comp(v, d));
   }
 }
-// Products are left to the compiler, which may contract m e into the following
-// subtraction differently in each kernel variant: the plain, packing and incremental
-// steps can then differ in the last FP32 bit (rounding the products on their own with
-// __fmul_rn cost the plain step 8% through register spills).  Results within one
-// variant are deterministic.
+// The m e products are plain multiplies; the face updates below subtract them with
+// __fsub_rn, which the compiler never merges with a multiply, so every face is
+// fma(dth, round(m_hi e_hi) - round(m_lo e_lo), v) wherever it is computed: by its
+// owner, or recomputed at a chunk's first plane or by the neighbouring lane.  (Left to
+// the compiler, a subtraction could absorb one product into an FMA at one site and not
+// at another, and the results then depended in the last bit on the z-chunk depth.)
 __device__ __forceinline__ float4 mul4(float4 a, float4 b) {
   return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w);
 }
@@ -157,9 +158,9 @@ __device__ __forceinline__ uint32_t pack2bf(float a, float b) {
   __nv_bfloat162 t = __floats2bfloat162_rn(a, b);
   return *reinterpret_cast<uint32_t*>(&t);
 }
-// face update v' = v + dth (hi - lo)
+// face update v' = v + dth (hi - lo), the difference rounded on its own (see above)
 __device__ __forceinline__ float fupd(float dth, float hi, float lo, float v) {
-  return fmaf(dth, hi - lo, v);
+  return fmaf(dth, __fsub_rn(hi, lo), v);
 }
 __device__ __forceinline__ float4 fupd4(float dth, float4 hi, float4 lo, float4 v) {
   return make_float4(fupd(dth, hi.x, lo.x, v.x), fupd(dth, hi.y, lo.y, v.y),
