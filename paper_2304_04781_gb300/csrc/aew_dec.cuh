@@ -12,12 +12,15 @@
 //                      256 x 64) through a 3-stage ring.
 //   warp 17           TMEM (512 columns) and, on one lane, the MMA issuer: layer 1 as
 //                      two N = 256 MMAs per K step into columns 0-511 (FP16 x FP16),
-//                      then, once the epilogue has written H, layer 2 for output half h
-//                      into columns 256h..256h+255 (BF16 x BF16).
+//                      then layer 2 for output half h into columns 256h..256h+255 (BF16
+//                      x BF16): half 0's first four K chunks as soon as the epilogue has
+//                      written hidden units 0-255 (whose accumulator columns 0-255 are
+//                      then free), the rest once it has written 256-511.
 //   warps 0-15        epilogue.  E1: layer-1 accumulator + b3, GELU, BF16, written into
 //                      the H buffer in the 128-byte-swizzled K-major layout the MMA
-//                      reads (8 K chunks of 128 rows x 128 bytes).  E2: layer-2
-//                      accumulator through the grid-scatter epilogue.
+//                      reads (8 K chunks of 128 rows x 128 bytes), hidden units 0-255
+//                      first.  E2: layer-2 accumulator through the grid-scatter
+//                      epilogue.
 // H buffer, TMEM and ring are each reused tile after tile; mbarriers order every reuse,
 // and every wait is bounded (a timed-out wait aborts the CTA and sets the error flag).
 #pragma once
@@ -60,11 +63,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* empty = full + kRing;
   uint64_t* f1 = empty + kRing;             // layer-1 operands landed
   uint64_t* acc1 = f1 + 1;                  // layer-1 accumulator complete
-  uint64_t* hready = acc1 + 1;              // H written by the epilogue
-  uint64_t* hfree = hready + 1;             // layer-2 MMAs done reading H
+  uint64_t* hready = acc1 + 1;              // [2] H units 256j..256j+255 written
+  uint64_t* hfree = hready + 2;             // layer-2 MMAs done reading H
   uint64_t* acc2 = hfree + 1;               // [2] output half complete
-  uint64_t* tfree = acc2 + 2;               // layer-2 accumulator drained
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(tfree + 1);
+  uint64_t* tfree = acc2 + 2;               // [2] output half drained
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(tfree + 2);
   int* abort_flag = reinterpret_cast<int*>(tslot + 1);
 
   if (*reinterpret_cast<volatile int*>(err) != 0) return;
@@ -88,11 +91,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     tc::mbar_init(tc::smem_u32(f1), 1);
     tc::mbar_init(tc::smem_u32(acc1), 1);
-    tc::mbar_init(tc::smem_u32(hready), kEpi * 32);
+    for (int j = 0; j < 2; ++j) {
+      tc::mbar_init(tc::smem_u32(&hready[j]), kEpi * 32);
+      tc::mbar_init(tc::smem_u32(&acc2[j]), 1);
+      tc::mbar_init(tc::smem_u32(&tfree[j]), kEpi * 32);
+    }
     tc::mbar_init(tc::smem_u32(hfree), 1);
-    tc::mbar_init(tc::smem_u32(&acc2[0]), 1);
-    tc::mbar_init(tc::smem_u32(&acc2[1]), 1);
-    tc::mbar_init(tc::smem_u32(tfree), kEpi * 32);
     *abort_flag = 0;
     tc::mbar_fence_init();
   }
@@ -147,30 +151,42 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t h0 = tc::smem_u32(hb);
       for (int t = blockIdx.x; t < T; t += gridDim.x, ++tl) {
         const uint32_t ph = tl & 1;
-        bool ok = (tl == 0 || tc::mbar_wait(tc::smem_u32(tfree), (tl - 1) & 1, W)) &&
-                  tc::mbar_wait(tc::smem_u32(f1), ph, W);
+        // layer 1: K = 64 in four steps of 16; outputs 256j..256j+255 into columns
+        // 256j.., once the previous tile's output half j has left them.  One commit for
+        // both: the epilogue overwrites the layer-1 operands with H, so it may start
+        // only once every layer-1 MMA has read them.
+        bool ok = tc::mbar_wait(tc::smem_u32(f1), ph, W);
+        for (int j = 0; j < 2 && ok; ++j) {
+          if (tl > 0 && !tc::mbar_wait(tc::smem_u32(&tfree[j]), (tl - 1) & 1, W)) {
+            ok = false;
+            break;
+          }
+          tc::fence_after_sync();
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            tc::mma_f16(tmem + (uint32_t)(j * 256), gemm::sdesc_sw128(h0 + k * 32),
+                        gemm::sdesc_sw128(h0 + kW3Off + j * 256 * 128 + k * 32), ID1,
+                        k > 0 ? 1u : 0u);
+        }
+        if (ok) tc::mma_commit(tc::smem_u32(acc1));
         if (!ok) {
           atomicExch(abort_flag, 1);
           break;
         }
-        tc::fence_after_sync();
-        // layer 1: K = 64 in four steps of 16, outputs 0-255 and 256-511
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const uint64_t ad = gemm::sdesc_sw128(h0 + k * 32);
-          tc::mma_f16(tmem, ad, gemm::sdesc_sw128(h0 + kW3Off + k * 32), ID1, k > 0 ? 1u : 0u);
-          tc::mma_f16(tmem + 256, ad, gemm::sdesc_sw128(h0 + kW3Off + 256 * 128 + k * 32), ID1,
-                      k > 0 ? 1u : 0u);
-        }
-        tc::mma_commit(tc::smem_u32(acc1));
-        if (!tc::mbar_wait(tc::smem_u32(hready), ph, W)) {
-          atomicExch(abort_flag, 1);
-          break;
-        }
-        tc::fence_after_sync();
-        // layer 2: A = H from shared memory, B = W4e chunks from the ring
+        // layer 2: A = H from shared memory, B = W4e chunks from the ring.  K chunks 0-3
+        // read hidden units 0-255 and 4-7 units 256-511, each half once the epilogue has
+        // written it and so drained its accumulator columns (half 0 of the output
+        // accumulates in columns 0-255, half 1 in 256-511).
         for (int h = 0; h < 2 && ok; ++h) {
           for (int kk = 0; kk < 8; ++kk, ++it) {
+            if (h == 0 && (kk & 3) == 0) {
+              if (!tc::mbar_wait(tc::smem_u32(&hready[kk >> 2]), ph, W)) {
+                atomicExch(abort_flag, 1);
+                ok = false;
+                break;
+              }
+              tc::fence_after_sync();
+            }
             const int s = it % kRing;
             if (!tc::mbar_wait(tc::smem_u32(&full[s]), (it / kRing) & 1, W)) {
               atomicExch(abort_flag, 1);
@@ -205,35 +221,39 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) atomicExch(err, 1);
         break;
       }
-      // E1: H = bf16(gelu(acc + b3)), 32 columns at a time
+      // E1: H = bf16(gelu(acc + b3)), 32 columns at a time; hidden units 0-255 (K chunks
+      // 0-3 of layer 2) first, each half released to the MMA issuer once written
+      for (int half = 0; half < 2; ++half) {
 #pragma unroll 1
-      for (int g = cg; g < kHid / 32; g += kEpi / 4) {
-        // the bias loads go out ahead of the TMEM load, so that the two latencies overlap
-        float4 bq[8];
+        for (int g = cg + 8 * half; g < 8 * (half + 1); g += kEpi / 4) {
+          // the bias loads go out ahead of the TMEM load, so that the two latencies overlap
+          float4 bq[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) bq[j] = __ldg(reinterpret_cast<const float4*>(b3 + g * 32) + j);
-        float v[32];
-        tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(g * 32), v);
-        uint32_t pk[16];
+          for (int j = 0; j < 8; ++j) bq[j] = __ldg(reinterpret_cast<const float4*>(b3 + g * 32) + j);
+          float v[32];
+          tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(g * 32), v);
+          uint32_t pk[16];
 #pragma unroll
-        for (int j = 0; j < 32; j += 4) {
-          const float4 b = bq[j / 4];
-          float x0 = v[j] + b.x, x1 = v[j + 1] + b.y, x2 = v[j + 2] + b.z, x3 = v[j + 3] + b.w;
-          gemm::gelu_fast_pair(x0, x1);
-          gemm::gelu_fast_pair(x2, x3);
-          pk[j / 2] = gemm::pack_bf16(x0, x1);
-          pk[j / 2 + 1] = gemm::pack_bf16(x2, x3);
+          for (int j = 0; j < 32; j += 4) {
+            const float4 b = bq[j / 4];
+            float x0 = v[j] + b.x, x1 = v[j + 1] + b.y, x2 = v[j + 2] + b.z, x3 = v[j + 3] + b.w;
+            gemm::gelu_fast_pair(x0, x1);
+            gemm::gelu_fast_pair(x2, x3);
+            pk[j / 2] = gemm::pack_bf16(x0, x1);
+            pk[j / 2 + 1] = gemm::pack_bf16(x2, x3);
+          }
+          uint8_t* chunk = hb + (g >> 1) * kChunk;
+          const int k0 = (g & 1) * 32;          // column within the 64-wide K chunk
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            *reinterpret_cast<uint4*>(chunk + sw128_off(r, k0 + 8 * c)) =
+                make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]);
         }
-        uint8_t* chunk = hb + (g >> 1) * kChunk;
-        const int k0 = (g & 1) * 32;          // column within the 64-wide K chunk
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-          *reinterpret_cast<uint4*>(chunk + sw128_off(r, k0 + 8 * c)) =
-              make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]);
+        tc::fence_proxy_async();                // H visible to the tensor core
+        tc::fence_before_sync();
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&hready[half]))
+                     : "memory");
       }
-      tc::fence_proxy_async();                // H visible to the tensor core
-      tc::fence_before_sync();
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(hready)) : "memory");
       // E2: output halves through the grid epilogue
       const typename EP::Row rc = ep.row((long long)t * kRows + r);
       for (int h = 0; h < 2 && ok; ++h) {
@@ -251,16 +271,17 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * 256 + g * 32), v);
           ep(rc, h * 256 + g * 32, bb, v);
         }
+        tc::fence_before_sync();
+        // relaxed: it orders only the completed TMEM reads (tcgen05.wait::ld) before the
+        // next tile's layer-1 MMAs into these columns, not the grid stores
+        asm volatile("mbarrier.arrive.relaxed.cta.shared::cta.b64 _, [%0];" ::"r"(
+                         tc::smem_u32(&tfree[h]))
+                     : "memory");
       }
       if (!ok) {
         if (lane == 0) atomicExch(err, 1);
         break;
       }
-      tc::fence_before_sync();
-      // relaxed: it orders only the completed TMEM reads (tcgen05.wait::ld) before the next
-      // tile's MMAs, not the grid stores
-      asm volatile("mbarrier.arrive.relaxed.cta.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(tfree))
-                   : "memory");
     }
   }
   tc::fence_before_sync();
