@@ -221,7 +221,8 @@ int aew_codec_get(const aew_handle* h, float* W1_host, float* b1_host,
 
 /* Space codec only (AEW_E_CONFIG otherwise).  Encode one state.
  * fields_dev = {e, vx, vy, vz} device [nz][ny][nx];
- * latents_dev: device FP16 [nblocks][n_lat] (written).  Each field of each block is
+ * latents_dev: device FP16 [nblocks][n_lat] (written; 32-byte aligned, AEW_E_ARG
+ * otherwise: each lane stores 32 bytes of a row at once).  Each field of each block is
  * normalised by its own power-of-two scale s = 2^e, where max |f| over the block is
  * m 2^e with m in [0.5, 1) (the per-vector normalisation of Sec. 3.3); block_max_dev
  * (may be NULL): device FP32 [nblocks][4] receiving the block maxima m 2^e from which
@@ -231,7 +232,7 @@ int aew_codec_encode(aew_handle* h, const float* const fields_dev[4], uint16_t* 
 
 /* Encode normalised block vectors (e.g. training snapshots): vectors_dev = device
  * BF16 bit patterns [n][2048] in the block-vector order above; latents_dev: device
- * FP16 [n][n_lat] (written). */
+ * FP16 [n][n_lat] (written; 32-byte aligned, AEW_E_ARG otherwise). */
 int aew_codec_encode_vectors(aew_handle* h, const uint16_t* vectors_dev, long long n,
                              uint16_t* latents_dev, void* stream);
 
@@ -251,7 +252,7 @@ int aew_codec_decode_e(aew_handle* h, const uint16_t* latents_dev, const float* 
 /* Time codec only (AEW_E_CONFIG otherwise).  Encode one window of nsteps (1..16)
  * strain fields e_dev[nsteps][nz][ny][nx] (device, contiguous, 16-byte aligned; the
  * window's later states are taken as 0) into latents_dev, device FP16 [nvec][n_lat]
- * (nvec = (nz/2)(ny/8)(nx/8)).  scale_dev (may be NULL) receives what fixes each
+ * (nvec = (nz/2)(ny/8)(nx/8); 32-byte aligned, AEW_E_ARG otherwise).  scale_dev (may be NULL) receives what fixes each
  * vector's scale: with AEW_NORM_POW2 device FP32 [nvec], each vector's largest |e|;
  * with AEW_NORM_MINMAX device FP64 [2][nvec], the offsets (minima) then the ranges.
  * Synchronises the stream; AEW_E_OVERFLOW if a latent overflowed FP16. */

@@ -1578,6 +1578,8 @@ int aew_codec_encode(aew_handle* h, const float* const fields_dev[4], uint16_t* 
   if (!h) return AEW_E_ARG;
   if (h->tcodec) return fail(h, AEW_E_CONFIG, "aew_codec_encode needs the space codec");
   if (!fields_dev || !latents_dev) return fail(h, AEW_E_ARG, "NULL argument");
+  if (reinterpret_cast<uintptr_t>(latents_dev) & 31)
+    return fail(h, AEW_E_ARG, "latents_dev must be 32-byte aligned");
   if (h->cfg.nx % 8 || h->cfg.ny % 8 || h->cfg.nz % 8)
     return fail(h, AEW_E_CONFIG, "codec needs nx, ny, nz multiples of 8");
   if (!aew::codec_ready(h->codec)) return fail(h, AEW_E_NOCODEC, "codec weights not set");
@@ -1639,6 +1641,8 @@ int aew_codec_encode_vectors(aew_handle* h, const uint16_t* vectors_dev, long lo
                              uint16_t* latents_dev, void* stream) {
   if (!h) return AEW_E_ARG;
   if (!vectors_dev || !latents_dev || n < 0) return fail(h, AEW_E_ARG, "bad argument");
+  if (reinterpret_cast<uintptr_t>(latents_dev) & 31)
+    return fail(h, AEW_E_ARG, "latents_dev must be 32-byte aligned");
   if (!aew::codec_ready(h->codec)) return fail(h, AEW_E_NOCODEC, "codec weights not set");
   h->err.clear();
   if (n == 0) return AEW_OK;
@@ -1663,6 +1667,8 @@ int aew_codec_encode_window(aew_handle* h, const float* e_dev, int nsteps, uint1
   if (!e_dev || !latents_dev || nsteps < 1 || nsteps > aew::kTSteps)
     return fail(h, AEW_E_ARG, "bad argument");
   if (reinterpret_cast<uintptr_t>(e_dev) & 15) return fail(h, AEW_E_ARG, "e_dev must be 16-byte aligned");
+  if (reinterpret_cast<uintptr_t>(latents_dev) & 31)
+    return fail(h, AEW_E_ARG, "latents_dev must be 32-byte aligned");
   if (h->cfg.nx % 8 || h->cfg.ny % 8 || h->cfg.nz % 2)
     return fail(h, AEW_E_CONFIG, "the time codec needs nx, ny multiples of 8 and nz even");
   if (!aew::codec_ready(h->codec)) return fail(h, AEW_E_NOCODEC, "codec weights not set");

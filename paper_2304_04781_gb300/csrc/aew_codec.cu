@@ -120,9 +120,9 @@ struct EpBiasAct {
       pk[j / 2] = act_pack2<ACT>(x0, x1);
       pk[j / 2 + 1] = act_pack2<ACT>(x2, x3);
     }
-    uint4* dst = reinterpret_cast<uint4*>(H + row * ld + col);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+    uint16_t* dst = H + row * ld + col;   // 32-byte aligned: ld and col multiples of 32
+    gemm::st_global_32B(dst, pk[0], pk[1], pk[2], pk[3], pk[4], pk[5], pk[6], pk[7]);
+    gemm::st_global_32B(dst + 16, pk[8], pk[9], pk[10], pk[11], pk[12], pk[13], pk[14], pk[15]);
   }
 };
 
@@ -153,9 +153,9 @@ struct EpScaleAct {
       pk[j / 2] = act_pack2<ACT>(x0, x1);
       pk[j / 2 + 1] = act_pack2<ACT>(x2, x3);
     }
-    uint4* dst = reinterpret_cast<uint4*>(H + row * ld + col);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+    uint16_t* dst = H + row * ld + col;   // 32-byte aligned: ld and col multiples of 32
+    gemm::st_global_32B(dst, pk[0], pk[1], pk[2], pk[3], pk[4], pk[5], pk[6], pk[7]);
+    gemm::st_global_32B(dst + 16, pk[8], pk[9], pk[10], pk[11], pk[12], pk[13], pk[14], pk[15]);
   }
 };
 
@@ -236,9 +236,9 @@ struct EpLatent {
       }
     }
     if (bad) atomicOr(ovf, 1);
-    uint4* dst = reinterpret_cast<uint4*>(lat + row * nl + col);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+    uint16_t* dst = lat + row * nl + col;   // 32-byte aligned: nl and col multiples of 32
+    gemm::st_global_32B(dst, pk[0], pk[1], pk[2], pk[3], pk[4], pk[5], pk[6], pk[7]);
+    gemm::st_global_32B(dst + 16, pk[8], pk[9], pk[10], pk[11], pk[12], pk[13], pk[14], pk[15]);
   }
 };
 

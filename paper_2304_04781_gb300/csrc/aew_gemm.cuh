@@ -110,6 +110,15 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   __nv_bfloat162 t = __floats2bfloat162_rn(a, b);
   return *reinterpret_cast<uint32_t*>(&t);
 }
+// one 32-byte store (sm_100 family; p 32-byte aligned): a lane's half of a 32-column
+// BF16 row group writes whole 32-byte sectors instead of two 16-byte halves
+__device__ __forceinline__ void st_global_32B(void* p, uint32_t w0, uint32_t w1, uint32_t w2,
+                                              uint32_t w3, uint32_t w4, uint32_t w5, uint32_t w6,
+                                              uint32_t w7) {
+  asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(w0),
+               "r"(w1), "r"(w2), "r"(w3), "r"(w4), "r"(w5), "r"(w6), "r"(w7)
+               : "memory");
+}
 __device__ __forceinline__ uint16_t bf16_bits(float a) {
   __nv_bfloat16 t = __float2bfloat16_rn(a);
   return *reinterpret_cast<uint16_t*>(&t);

@@ -105,6 +105,23 @@ def test_pair_gemm_matches_single_sm_gemm(n, monkeypatch):
     assert relerr(lat["1"].view(torch.float16).double().numpy(), Z) < CODEC_TOL
 
 
+def test_latents_must_be_32_byte_aligned():
+    """The latent epilogue stores 32 bytes per lane at once: an output pointer off a
+    32-byte boundary is refused on the host (AEW_E_ARG), before any kernel runs."""
+    from paper_2304_04781_gb300 import aewave
+    prob, _, _ = setup((32, 32, 32), 4, 16)
+    s = solver(prob, storage="ae")
+    s.codec_set(inputs.codec_init(seed=3, n_lat=64))
+    vec = torch.zeros((64, 2048), dtype=torch.bfloat16, device="cuda")
+    lat = torch.zeros((65, 64), dtype=torch.float16, device="cuda")
+    rc = aewave.lib().aew_codec_encode_vectors(s._h, vec.data_ptr(), 64, lat.data_ptr() + 16,
+                                               aewave._stream())
+    assert aewave._ERRORS[rc] == "AEW_E_ARG"
+    torch.cuda.synchronize()
+    assert not torch.any(lat)   # nothing written
+    s.close()
+
+
 @pytest.mark.parametrize("n_lat", [64, 32])
 def test_decode_matches_oracle(n_lat):
     shape = (40, 48, 56)
