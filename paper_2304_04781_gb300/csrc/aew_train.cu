@@ -89,10 +89,23 @@ TrainState* train_new(Codec* c, int B) {
 // ---------------------------------------------------------------------------------
 // Epilogues
 // ---------------------------------------------------------------------------------
+// 32 16-bit values of one row, as two 32-byte stores (dst 32-byte aligned: every row
+// length here is a multiple of 16 values and every column group starts at a multiple of
+// 32), so each store fills whole sectors
 __device__ __forceinline__ void store_row16(uint16_t* dst, const uint32_t (&pk)[16]) {
-  uint4* d = reinterpret_cast<uint4*>(dst);
+  gemm::st_global_32B(dst, pk[0], pk[1], pk[2], pk[3], pk[4], pk[5], pk[6], pk[7]);
+  gemm::st_global_32B(dst + 16, pk[8], pk[9], pk[10], pk[11], pk[12], pk[13], pk[14], pk[15]);
+}
+
+// 32 FP32 values of one row as four 32-byte stores (dst 32-byte aligned: every row length
+// here is a multiple of 8 values and every column group starts at a multiple of 32)
+__device__ __forceinline__ void store_row32f(float* dst, const float (&x)[32]) {
 #pragma unroll
-  for (int q = 0; q < 4; ++q) d[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+  for (int j = 0; j < 32; j += 8)
+    gemm::st_global_32B(dst + j, __float_as_uint(x[j]), __float_as_uint(x[j + 1]),
+                        __float_as_uint(x[j + 2]), __float_as_uint(x[j + 3]),
+                        __float_as_uint(x[j + 4]), __float_as_uint(x[j + 5]),
+                        __float_as_uint(x[j + 6]), __float_as_uint(x[j + 7]));
 }
 
 // the training kernels' activation and its derivative: GELU by erff (act 0) or ELU
@@ -116,21 +129,26 @@ struct EpFwdGelu {
   __device__ __forceinline__ void operator()(long long row, int col, const float (&v)[32]) const {
     if (row >= M) return;
     uint32_t pk[16];
-    float4* pd = reinterpret_cast<float4*>(pre + row * N + col);
+    float* pd = pre + row * N + col;   // 32-byte aligned: N and col multiples of 32
 #pragma unroll
-    for (int j = 0; j < 32; j += 4) {
-      float a[4];
+    for (int j = 0; j < 32; j += 8) {
+      float a[8];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) a[q] = v[j + q] + __ldg(bias + col + j + q);
-      pd[j / 4] = make_float4(a[0], a[1], a[2], a[3]);
-      const float g0 = act_f(act, a[0]), g1 = act_f(act, a[1]);
-      const float g2 = act_f(act, a[2]), g3 = act_f(act, a[3]);
-      pk[j / 2] = gemm::pack_bf16(g0, g1);
-      pk[j / 2 + 1] = gemm::pack_bf16(g2, g3);
-      hT[(size_t)(col + j + 0) * M + row] = gemm::bf16_bits(g0);
-      hT[(size_t)(col + j + 1) * M + row] = gemm::bf16_bits(g1);
-      hT[(size_t)(col + j + 2) * M + row] = gemm::bf16_bits(g2);
-      hT[(size_t)(col + j + 3) * M + row] = gemm::bf16_bits(g3);
+      for (int q = 0; q < 8; ++q) a[q] = v[j + q] + __ldg(bias + col + j + q);
+      gemm::st_global_32B(pd + j, __float_as_uint(a[0]), __float_as_uint(a[1]),
+                          __float_as_uint(a[2]), __float_as_uint(a[3]), __float_as_uint(a[4]),
+                          __float_as_uint(a[5]), __float_as_uint(a[6]), __float_as_uint(a[7]));
+#pragma unroll
+      for (int q = 0; q < 8; q += 4) {
+        const float g0 = act_f(act, a[q]), g1 = act_f(act, a[q + 1]);
+        const float g2 = act_f(act, a[q + 2]), g3 = act_f(act, a[q + 3]);
+        pk[(j + q) / 2] = gemm::pack_bf16(g0, g1);
+        pk[(j + q) / 2 + 1] = gemm::pack_bf16(g2, g3);
+        hT[(size_t)(col + j + q + 0) * M + row] = gemm::bf16_bits(g0);
+        hT[(size_t)(col + j + q + 1) * M + row] = gemm::bf16_bits(g1);
+        hT[(size_t)(col + j + q + 2) * M + row] = gemm::bf16_bits(g2);
+        hT[(size_t)(col + j + q + 3) * M + row] = gemm::bf16_bits(g3);
+      }
     }
     store_row16(h + row * N + col, pk);
   }
@@ -187,9 +205,7 @@ struct EpMse {
       }
 #pragma unroll
       for (int j = 0; j < 32; j += 2) pk[j / 2] = gemm::pack_bf16(dd[j], dd[j + 1]);
-      float4* pd = reinterpret_cast<float4*>(d4 + row * kNIn + col);
-#pragma unroll
-      for (int j = 0; j < 32; j += 4) pd[j / 4] = make_float4(dd[j], dd[j + 1], dd[j + 2], dd[j + 3]);
+      store_row32f(d4 + row * kNIn + col, dd);
       store_row16(d4b + row * kNIn + col, pk);
     }
 #pragma unroll
@@ -216,9 +232,7 @@ struct EpBack {
       dd[j] = pre ? v[j] * act_prime_f(act, pre[row * N + col + j]) : v[j];
       dT[(size_t)(col + j) * M + row] = gemm::bf16_bits(dd[j]);
     }
-    float4* pd = reinterpret_cast<float4*>(d + row * N + col);
-#pragma unroll
-    for (int j = 0; j < 32; j += 4) pd[j / 4] = make_float4(dd[j], dd[j + 1], dd[j + 2], dd[j + 3]);
+    store_row32f(d + row * N + col, dd);
     if (db) {
       uint32_t pk[16];
 #pragma unroll
@@ -235,9 +249,7 @@ struct EpStore {
   long long M;
   __device__ __forceinline__ void operator()(long long row, int col, const float (&v)[32]) const {
     if (row >= M || col >= N) return;
-    float4* pd = reinterpret_cast<float4*>(G + row * N + col);
-#pragma unroll
-    for (int j = 0; j < 32; j += 4) pd[j / 4] = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+    store_row32f(G + row * N + col, v);
   }
 };
 
