@@ -510,9 +510,9 @@ typedef struct aew_newton_iter {
 
 /* out_dev = A q_dev (FP32; [nz][ny][nx] of the handle's grid and spacing).
  * Asynchronous on `stream`.  AEW_E_ARG for NULL pointers, alpha <= 0 or theta < 0.
- * q_dev and out_dev must not overlap.  The vectors of aew_prior_solve, aew_newton_cg
- * and aew_dias_subspace are read as float4: they must be 16-byte aligned (AEW_E_ARG
- * otherwise; a torch allocation is). */
+ * q_dev and out_dev must not overlap.  The vectors of aew_prior_apply, aew_prior_solve,
+ * aew_newton_cg and aew_dias_subspace are read as float4: they must be 16-byte aligned
+ * (AEW_E_ARG otherwise; a torch allocation is). */
 int aew_prior_apply(aew_handle* h, double alpha, double theta, const float* q_dev,
                     float* out_dev, void* stream);
 

@@ -104,32 +104,68 @@ struct Acc {
 
 // y = A x (+ yadd) with A x = alpha x - alpha theta / h^2 * sum over the neighbours a node
 // has of (x_nb - x); optional partials of sum wdot . (A x).  One warp per grid row
-// (k, y) with lanes along x: row indices once per row, coalesced loads, neighbours in
-// other rows through L1/L2.  y may be yadd; x must not overlap y.
+// (k, y), each lane four consecutive nodes (nx is a multiple of 4 and the vectors are
+// 16-byte aligned): one float4 load per row below, above, in front and behind, and the
+// x neighbours by shuffle, the row's ends of each 128-node stretch loaded by lanes 0 and
+// 31.  y may be yadd; x must not overlap y.
+__device__ __forceinline__ float f4c(const float4& v, int c) {
+  return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
+}
 __global__ void prior_kernel(const float* __restrict__ x, float* y, const float* yadd, Grid g,
                              float alpha, float at, const float* __restrict__ wdot, double* part) {
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * NT) >> 5;
   const int nrow = g.ny * g.nz;
+  const int nq = g.nx >> 2;   // float4 per row
   const size_t sy = (size_t)g.nx, sz = (size_t)g.nx * g.ny;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   Acc acc;
   for (int row = (blockIdx.x * NT + threadIdx.x) >> 5; row < nrow; row += warps) {
     const int j = row % g.ny, k = row / g.ny;
     const size_t base = (size_t)row * g.nx;
-    for (int i = lane; i < g.nx; i += 32) {
-      const size_t n = base + i;
-      const float xn = x[n];
-      float lap = 0.f;
-      if (i > 0) lap += x[n - 1] - xn;
-      if (i + 1 < g.nx) lap += x[n + 1] - xn;
-      if (j > 0) lap += x[n - sy] - xn;
-      if (j + 1 < g.ny) lap += x[n + sy] - xn;
-      if (k > 0) lap += x[n - sz] - xn;
-      if (k + 1 < g.nz) lap += x[n + sz] - xn;
-      float v = alpha * xn - at * lap;
-      if (part) acc.add(wdot[n] * v);
-      if (yadd) v += yadd[n];
-      y[n] = v;
+    for (int q0 = 0; q0 < nq; q0 += 32) {   // the same trip count in every lane
+      const int q = q0 + lane;
+      const bool in = q < nq;
+      const size_t n = base + 4 * (size_t)q;
+      const float4 xc = in ? *reinterpret_cast<const float4*>(x + n) : z4;
+      float xl = __shfl_up_sync(0xffffffffu, xc.w, 1);     // node 4q - 1
+      float xr = __shfl_down_sync(0xffffffffu, xc.x, 1);   // node 4q + 4
+      if (!in) continue;
+      const int i = 4 * q;
+      if (lane == 0 && i > 0) xl = x[n - 1];
+      if (lane == 31 && q + 1 < nq) xr = x[n + 4];
+      const float4 ym = j > 0 ? *reinterpret_cast<const float4*>(x + n - sy) : z4;
+      const float4 yp = j + 1 < g.ny ? *reinterpret_cast<const float4*>(x + n + sy) : z4;
+      const float4 zm = k > 0 ? *reinterpret_cast<const float4*>(x + n - sz) : z4;
+      const float4 zp = k + 1 < g.nz ? *reinterpret_cast<const float4*>(x + n + sz) : z4;
+      float v[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float xn = f4c(xc, c);
+        float lap = 0.f;
+        if (i + c > 0) lap += (c == 0 ? xl : f4c(xc, c - 1)) - xn;
+        if (i + c + 1 < g.nx) lap += (c == 3 ? xr : f4c(xc, c + 1)) - xn;
+        if (j > 0) lap += f4c(ym, c) - xn;
+        if (j + 1 < g.ny) lap += f4c(yp, c) - xn;
+        if (k > 0) lap += f4c(zm, c) - xn;
+        if (k + 1 < g.nz) lap += f4c(zp, c) - xn;
+        v[c] = alpha * xn - at * lap;
+      }
+      if (part) {
+        const float4 w = *reinterpret_cast<const float4*>(wdot + n);
+        acc.add(w.x * v[0]);
+        acc.add(w.y * v[1]);
+        acc.add(w.z * v[2]);
+        acc.add(w.w * v[3]);
+      }
+      if (yadd) {
+        const float4 ya = *reinterpret_cast<const float4*>(yadd + n);
+        v[0] += ya.x;
+        v[1] += ya.y;
+        v[2] += ya.z;
+        v[3] += ya.w;
+      }
+      *reinterpret_cast<float4*>(y + n) = make_float4(v[0], v[1], v[2], v[3]);
     }
   }
   if (part) block_store(acc.total(), part);
@@ -498,6 +534,8 @@ int aew_prior_apply(aew_handle* h, double alpha, double theta, const float* q_de
                     float* out_dev, void* stream) {
   if (!h) return AEW_E_ARG;
   if (!q_dev || !out_dev) return set_error(h, AEW_E_ARG, "NULL vector");
+  if (!aew::aligned16(q_dev) || !aew::aligned16(out_dev))
+    return set_error(h, AEW_E_ARG, "vectors must be 16-byte aligned");
   int rc = aew::prior_args_ok(h, alpha, theta);
   if (rc) return rc;
   const aew::GridInfo gi = aew::grid_of(h);

@@ -20,9 +20,12 @@ def _grid_solver(shape):
     return prob, solver(prob, storage="full")
 
 
+@pytest.mark.parametrize("shape", [(20, 24, 28), (12, 16, 260)])
 @pytest.mark.parametrize("alpha,theta", [(1.0, 0.0), (2e-3, 6400.0), (0.5, 100.0)])
-def test_prior_apply_matches_oracle(alpha, theta):
-    prob, s = _grid_solver((20, 24, 28))
+def test_prior_apply_matches_oracle(alpha, theta, shape):
+    # nx = 260: rows of 65 float4, so a warp takes three passes along x and the
+    # neighbours across each 128-node stretch come from the loads of lanes 0 and 31
+    prob, s = _grid_solver(shape)
     for q in (inputs.velocity_model(prob.shape, prob.h, seed=4),
               inputs.white_noise(1, prob.shape, seed=5)[0]):
         q = q.astype(np.float32).astype(np.float64)
